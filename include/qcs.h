@@ -1,0 +1,192 @@
+/*
+ * qcs.h -- C ABI of the GB300 matchgate-shadow overlap library.
+ *
+ * The library evaluates, on one GPU, the classical post-processing hot path
+ * of QC-AFQMC with matchgate shadows (arXiv 2506.22408):
+ *
+ *   for every walker w (a complex n x ne orbital matrix Phi_w) and every
+ *   shadow snapshot p (an orthogonal Q_p in O(2n) and a measured n-bit
+ *   string b_p) the estimator o_p(Phi_w) of Sec. "Classical shadows and the
+ *   evaluation of overlaps" -- an inverse-channel weighted sum of the
+ *   coefficients of the polynomial pf(A(z)), A(z) = C_0^(s) + z B^(s)
+ *   (Eqs. a_mat, b_mat) -- and the shadow average
+ *   <Psi_T|phi_w> = (1/P) sum_p o_p(Phi_w);
+ *
+ *   the holomorphic gradient d<Psi_T|phi_w>/dPhi_w through
+ *   d pf(A) = pf(A) tr(A^{-1} dA) / 2  (Eq. Pfaffian_der);
+ *
+ *   the AFQMC force bias xbar_gamma = -sqrt(dtau) <Psi_T|v_gamma|phi>/<Psi_T|phi>
+ *   (Eq. force_bias) evaluated as a derivative of the overlap (Eq. force_bias_diff).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are two consecutive doubles (re, im) (the layout of C99
+ *   double complex and of cuDoubleComplex); a "complex array of k entries"
+ *   is 2k doubles.
+ * - Matrices are row-major.  A walker Phi is n x ne with Phi[k][j] the
+ *   coefficient of orbital k in occupied column j; the walker is
+ *   |phi> = prod_j (sum_k Phi[k][j] a_k^dagger) |0>, first factor leftmost.
+ * - Majoranas are gamma_{2j-1} = a_j + a_j^dagger, gamma_{2j} = -i(a_j - a_j^dagger)
+ *   (SI "Reduced Density Matrices"); snapshot p measured |b_p> after the
+ *   matchgate circuit U_Q with U_Q^dagger gamma_mu U_Q = sum_nu Q[mu][nu] gamma_nu.
+ *   b[j] = 1 means mode j was found occupied.
+ * - Every data pointer is a DEVICE pointer owned by the caller unless the
+ *   argument says otherwise.  Nothing is freed by the library except its own
+ *   handles.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous with respect to the host: they enqueue
+ *   kernels on `stream` and return.  Argument errors are detected on the host
+ *   before anything is enqueued and returned synchronously; numerical
+ *   problems found by the kernels (non-finite input, non-finite pivot,
+ *   singular matrix where an inverse is needed) are OR-ed into a device
+ *   status word read by qcs_sync_status().
+ * - Sizes: 1 <= n <= QCS_MAX_N, ne even, 2 <= ne <= n.  An odd ne is
+ *   rejected: measurement outcomes are even operators, so the shadow
+ *   estimator of an odd-particle overlap is identically zero.
+ * - Scratch memory: a context owns one device workspace that grows (with
+ *   cudaMalloc, synchronously) when a call needs more than it holds.  Call
+ *   each entry point once with the largest sizes before capturing it in a
+ *   CUDA graph so that no allocation happens during capture.  Calls on the
+ *   same context must not overlap in time on different streams.
+ */
+#ifndef QCS_H
+#define QCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCS_MAX_N 24
+#define QCS_MAX_NODES 49
+
+typedef struct qcs_ctx qcs_ctx;             /* per-device context (workspace, status word) */
+typedef struct qcs_snapshots qcs_snapshots; /* device-resident snapshot set */
+
+typedef enum {
+    QCS_OK = 0,
+    QCS_ERR_ARG = 1,         /* invalid argument (size, null pointer, odd ne, ...) */
+    QCS_ERR_CUDA = 2,        /* a CUDA runtime call failed; see qcs_last_error() */
+    QCS_ERR_NONFINITE = 4,   /* device: a non-finite input or pivot was met */
+    QCS_ERR_SINGULAR = 8,    /* device: A(z_k) singular where its inverse was needed */
+    QCS_ERR_TIMEOUT = 16,    /* device: a bounded wait expired */
+    QCS_ERR_UNSUPPORTED = 32 /* request outside what this build implements */
+} qcs_status;
+
+typedef enum {
+    QCS_FP64 = 0,  /* every product and the Pfaffians in FP64 */
+    QCS_TF32X3 = 1 /* congruence products as split FP32 on tensor cores (3xTF32), Pfaffian in FP64 */
+} qcs_precision;
+
+/* qcs_opts.flags */
+#define QCS_FLAG_ALL_NODES 1u /* evaluate pf(A(z_k)) at every node and skip no snapshot
+                                 (disables the parity shortcuts described at qcs_overlap) */
+
+typedef struct {
+    int precision; /* qcs_precision */
+    int nodes;     /* number of roots-of-unity nodes N; 0 = minimum n-ne+1 */
+    unsigned flags;
+    int reserved;
+} qcs_opts;
+
+/* ------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  *ctx receives the handle.
+ * Errors: QCS_ERR_ARG (ctx NULL), QCS_ERR_CUDA. */
+qcs_status qcs_create(qcs_ctx **ctx, int device);
+
+/* Free the context and its workspace (synchronises the device first). */
+qcs_status qcs_destroy(qcs_ctx *ctx);
+
+/* Text of the last error raised on this context ("" if none); owned by the context. */
+const char *qcs_last_error(const qcs_ctx *ctx);
+
+/* Wait for all work on `stream`, then return (and clear) the OR of the
+ * device status bits raised since the last call; QCS_OK if none. */
+qcs_status qcs_sync_status(qcs_ctx *ctx, void *stream);
+
+/* Bytes of device workspace currently held by the context. */
+size_t qcs_workspace_bytes(const qcs_ctx *ctx);
+
+/* ---------------------------------------------------------- snapshots */
+
+/* Build the device representation of P snapshots (Q_p, b_p).
+ *   d_Q : P x 2n x 2n doubles, row-major, each Q_p orthogonal (det +-1)
+ *   d_b : P x n bytes, 0 or 1
+ * The library computes per snapshot the rotated covariance factor of
+ * Eq. (b_mat) -- G_p = Q_p^T C_b Q_p with C_b the covariance matrix of SI
+ * item 2 -- in the factorised form Q'_p = P_b Q_p, P_b = diag(1, (-1)^{b_1},
+ * 1, (-1)^{b_2}, ...) so that G_p = Q'^T J Q', and the snapshot parity
+ * pi_p = det Q_p (-1)^{|b_p|} = det Q'_p.  *out is owned by the library
+ * (free with qcs_snapshots_free).  Inputs are only read during the call's
+ * kernels; the caller may reuse them once `stream` has passed this call.
+ * Errors: QCS_ERR_ARG (n out of range, P < 0, null pointers), QCS_ERR_CUDA. */
+qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const double *d_Q, const uint8_t *d_b,
+                               qcs_snapshots **out, void *stream);
+
+qcs_status qcs_snapshots_free(qcs_snapshots *s);
+
+/* Copy the parity pi_p (+1 / -1, one int8 per snapshot, P entries) into the
+ * caller's device buffer d_parity. */
+qcs_status qcs_snapshots_parity(const qcs_snapshots *s, int8_t *d_parity, void *stream);
+
+/* Number of snapshots and modes of the set. */
+int64_t qcs_snapshots_count(const qcs_snapshots *s);
+int qcs_snapshots_modes(const qcs_snapshots *s);
+
+/* ----------------------------------------------------------- overlaps */
+
+/* Shadow overlaps <Psi_T|phi_w> = (1/P) sum_p o_p(Phi_w) for W walkers.
+ *   d_walkers : W x n x ne complex (read only)
+ *   d_overlap : W complex (written)
+ *   d_per_pair: W x P complex (o_p of every pair, row w) or NULL
+ *   opts      : NULL = defaults (FP64, minimum nodes)
+ * o_p = 2 det(R_w) i^{ne/2} / 2^{n-ne/2} sum_x c_x C(2n,2x)/C(n,x), where
+ * Phi_w = U R (QR), V = U^dagger defines M_phi (SI item 3) and c_x are the
+ * coefficients of pf(C_0^(s) + z B^(s)) (Eqs. a_mat, b_mat).  The factor 2
+ * undoes the 1/sqrt2 of the prepared state (|0>+|Psi_T>)/sqrt2, and det R
+ * restores the norm of a non-orthonormal walker.
+ * Parity shortcuts (on unless QCS_FLAG_ALL_NODES): for a pure Gaussian
+ * snapshot state of parity pi the coefficients obey c_{n-x} = pi c_x, and the
+ * weights obey w_{n-x} = w_x, so pairs with pi = -1 are exactly zero (their
+ * per-pair output is written as 0) and pairs with pi = +1 need pf(A(z_k)) at
+ * only floor(N/2)+1 of the N roots of unity.
+ * Errors: QCS_ERR_ARG, QCS_ERR_CUDA; device bits via qcs_sync_status. */
+qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
+                       double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream);
+
+/* Overlaps and their holomorphic walker gradient
+ *   d_grad[w][k][j] = d <Psi_T|phi_w> / d Phi_w[k][j]   (W x n x ne complex).
+ * Each pair's contribution is differentiated through
+ * d pf(A) = pf(A) tr(A^{-1} dA) / 2 (Eq. Pfaffian_der) with A(z_k)^{-1}
+ * recomputed per node (never stored), then chained through the congruence
+ * of Eq. (b_mat) and the QR of the walker.  Same options as qcs_overlap
+ * (precision must be QCS_FP64).  QCS_ERR_SINGULAR is raised when some
+ * A(z_k) is singular. */
+qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
+                            double *d_overlap, double *d_grad, const qcs_opts *opts, void *stream);
+
+/* Force bias from overlaps and gradients (Eqs. force_bias, force_bias_diff):
+ *   G_w = Phi_w g_w^T / O_w (n x n),  <v_gamma> = i tr(L_gamma G_w),
+ *   d_xbar[w][gamma] = -sqrt_dt <v_gamma>   (sqrt_dt == 0: <v_gamma> itself).
+ *   d_L: nchol x n x n complex (any complex matrices; real symmetric in AFQMC)
+ *   d_walkers, d_overlap, d_grad as returned/used by qcs_overlap_grad.
+ * Errors: QCS_ERR_ARG, QCS_ERR_CUDA. */
+qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const double *d_L,
+                          const double *d_walkers, const double *d_overlap, const double *d_grad, double sqrt_dt,
+                          double *d_xbar, void *stream);
+
+/* ----------------------------------------------------------- accounting */
+
+/* Algorithmic FP64 flop count per non-trivial (pi = +1) pair of qcs_overlap
+ * for (n, ne, nodes), as implemented: congruence T = U^T Qtilde^T, the
+ * selected covariance B^(s), and the rank-2 Pfaffian updates at the
+ * evaluated nodes.  Used by the benchmark's roofline. */
+double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCS_H */

@@ -1,0 +1,435 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against the mathematics or an independent
+construction: closed forms, textbook identities, a Fock-space brute force of
+the estimator's definition, an exact group average, and exact finite
+differences.  ``test_planted_mistakes_are_caught`` rebuilds the oracle with
+each planted mistake and confirms that these pins fail for it.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle.oracle as orc
+from fock_brute import Fock, channel_weights, pfaffian_by_matchings
+from paper_2506_22408_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_skew(rng, m):
+    A = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    return A - A.T
+
+
+# ------------------------------------------------------------- Pfaffian
+
+
+def test_pfaffian_4x4_closed_form():
+    rng = np.random.default_rng(10)
+    for _ in range(5):
+        A = rand_skew(rng, 4)
+        ref = A[0, 1] * A[2, 3] - A[0, 2] * A[1, 3] + A[0, 3] * A[1, 2]
+        assert abs(orc.pfaffian(A) - ref) <= 1e-13 * abs(ref)
+
+
+@pytest.mark.parametrize("m", [2, 4, 6, 8])
+def test_pfaffian_perfect_matchings(m):
+    rng = np.random.default_rng(11 + m)
+    A = rand_skew(rng, m)
+    ref = pfaffian_by_matchings(A)
+    assert abs(orc.pfaffian(A) - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("m", [2, 6, 12, 24, 36])
+def test_pfaffian_squared_is_determinant(m):
+    rng = np.random.default_rng(20 + m)
+    A = rand_skew(rng, m)
+    pf = orc.pfaffian(A)
+    sign, logdet = np.linalg.slogdet(A)
+    det = sign * np.exp(logdet)
+    assert abs(pf * pf - det) <= 1e-10 * abs(det)
+
+
+def test_pfaffian_block_canonical_and_congruence():
+    rng = np.random.default_rng(30)
+    m = 10
+    a = rng.standard_normal(m // 2) + 1j * rng.standard_normal(m // 2)
+    D = np.zeros((m, m), complex)
+    for i in range(m // 2):
+        D[2 * i, 2 * i + 1] = a[i]
+        D[2 * i + 1, 2 * i] = -a[i]
+    assert abs(orc.pfaffian(D) - np.prod(a)) <= 1e-13 * abs(np.prod(a))
+    X = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    A = rand_skew(rng, m)
+    lhs = orc.pfaffian(X.T @ A @ X)
+    rhs = np.linalg.det(X) * orc.pfaffian(A)
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs)
+    # a permutation congruence of the canonical form: pf = sign(perm) * prod(a)
+    perm = rng.permutation(m)
+    Pm = np.eye(m)[:, perm]
+    sgn = np.linalg.det(Pm)
+    assert abs(orc.pfaffian(Pm.T @ D @ Pm) - sgn * np.prod(a)) <= 1e-13 * abs(np.prod(a))
+
+
+def test_pfaffian_degenerate():
+    rng = np.random.default_rng(31)
+    A = rand_skew(rng, 6)
+    A[:, 3] = 0
+    A[3, :] = 0
+    assert orc.pfaffian(A) == 0
+    assert orc.pfaffian(np.zeros((0, 0))) == 1
+    assert orc.pfaffian(rand_skew(rng, 5)) == 0
+
+
+# ---------------------------------------------------- walker and snapshot
+
+
+def test_walker_qr_and_snapshot_invariants():
+    rng = np.random.default_rng(40)
+    for n, ne in [(4, 2), (8, 4), (16, 8), (24, 12)]:
+        Phi = rng.standard_normal((n, ne)) + 1j * rng.standard_normal((n, ne))
+        U, R = orc.walker_qr(Phi)
+        assert np.abs(U[:, :ne] @ R - Phi).max() < 1e-13 * np.abs(Phi).max() * n
+        assert np.abs(U.conj().T @ U - np.eye(n)).max() < 1e-13
+        assert np.abs(np.tril(R, -1)).max() == 0
+        Q = synth.haar_orthogonal(rng, 2 * n, 1)[0]
+        b = synth.uniform_bits(rng, n, 1)[0]
+        G = orc.snapshot_G(Q, b)
+        # Q^T C_b Q is real skew-symmetric and orthogonal: G^T = -G, G^2 = -I
+        assert np.abs(G + G.T).max() < 1e-14
+        assert np.abs(G @ G + np.eye(2 * n)).max() < 1e-12
+        # Q = I gives back the covariance of |b> (SI item 2: +(-1)^{b_j} upper right)
+        G0 = orc.snapshot_G(np.eye(2 * n), b)
+        for j in range(n):
+            assert G0[2 * j, 2 * j + 1] == (-1.0) ** b[j]
+
+
+def test_selection_shape():
+    for n in range(2, 9):
+        for ne in range(2, n + 1, 2):
+            idx = orc.selection(n, ne)
+            assert len(idx) == 2 * n - ne
+            assert list(idx) == sorted(idx)
+
+
+# --------------------------------------------- estimator vs brute force
+
+
+def _fock_case(rng, n, ne, det_sign=None, scaled=True):
+    Q = synth.haar_orthogonal(rng, 2 * n, 1)[0]
+    if det_sign is not None and np.sign(np.linalg.det(Q)) != det_sign:
+        Q[:, 0] *= -1
+    b = synth.uniform_bits(rng, n, 1)[0]
+    Phi = synth.walkers(rng, n, ne, 1)[0]
+    if scaled:
+        Phi = Phi @ (rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne)))
+    return Q, b, Phi
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7])
+def test_estimator_matches_fock_bruteforce(n):
+    """o_p of the Pfaffian route equals 2 tr(M^{-1}(|phi><0|) rho_{Q,b}) computed in Fock space."""
+    rng = np.random.default_rng(100 + n)
+    F = Fock(n)
+    for ne in range(2, n + 1, 2):
+        for trial in range(4 if n <= 5 else 2):
+            Q, b, Phi = _fock_case(rng, n, ne, det_sign=(1 if trial % 2 == 0 else -1))
+            psi = F.shadow_state(Q, b)
+            ob = F.estimator(Phi, psi)
+            of, c, scale = orc.pair(Q, b, Phi)
+            # parity-forbidden pairs are zero up to rounding on both sides: bound by the walker's norm
+            mag = max(scale, abs(np.linalg.det(Phi.conj().T @ Phi)) ** 0.5)
+            assert abs(of - ob) <= 1e-10 * mag, (n, ne, trial, of, ob)
+
+
+@pytest.mark.slow
+def test_estimator_matches_fock_bruteforce_n8():
+    rng = np.random.default_rng(108)
+    F = Fock(8)
+    for ne in (4, 6):
+        Q, b, Phi = _fock_case(rng, 8, ne, det_sign=1)
+        pi = np.sign(np.linalg.det(Q)) * (-1) ** int(b.sum())
+        if pi < 0:
+            b[0] ^= 1
+        of, c, scale = orc.pair(Q, b, Phi)
+        ob = F.estimator(Phi, F.shadow_state(Q, b))
+        assert abs(of - ob) <= 1e-10 * scale
+
+
+def test_worked_example_closed_form():
+    """n = 2, eta = 2, Phi = I, b = 00, Q a (gamma_2, gamma_3) rotation: o = 3 i sin(theta)
+    (derivation in tests/golden/worked_n2_rotation.txt)."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "worked_n2_rotation.txt"))
+    F = Fock(2)
+    for th, re, im in rows:
+        c, s = np.cos(th), np.sin(th)
+        Q = np.array([[1, 0, 0, 0], [0, c, s, 0], [0, -s, c, 0], [0, 0, 0, 1.0]])
+        b = np.zeros(2, np.uint8)
+        o, _, _ = orc.pair(Q, b, np.eye(2, dtype=complex))
+        assert abs(o - complex(re, im)) < 1e-13
+        assert abs(F.estimator(np.eye(2, dtype=complex), F.shadow_state(Q, b)) - complex(re, im)) < 1e-13
+
+
+# ------------------------------------------- polynomial structure pins
+
+
+@pytest.mark.parametrize("n,ne", [(4, 2), (6, 4), (8, 4), (12, 6), (16, 8), (16, 4), (20, 10), (24, 12)])
+def test_coefficient_structure(n, ne):
+    """c_x = 0 for x < ne/2 (D vanishes on occupied rows), c_{n-x} = pi c_x with
+    pi = det Q (-1)^{|b|} (parity of the pure Gaussian snapshot state), and
+    parity-forbidden pairs are exactly zero because the weights are symmetric."""
+    rng = np.random.default_rng(200 + n + ne)
+    for trial in range(4):
+        Q, b, Phi = _fock_case(rng, n, ne, det_sign=(1 if trial < 2 else -1))
+        pi = np.sign(np.linalg.det(Q)) * (-1) ** int(b.sum())
+        o, c, scale = orc.pair(Q, b, Phi)
+        cmax = np.abs(c).max()
+        assert np.abs(c[: ne // 2]).max() <= 1e-13 * cmax
+        x = np.arange(ne // 2, n - ne // 2 + 1)
+        assert np.abs(c[n - x] - pi * c[x]).max() <= 1e-12 * cmax
+        w = np.array([comb(2 * n, 2 * k) / comb(n, k) for k in range(n + 1)])
+        assert np.allclose(w, w[::-1])
+        if pi < 0:
+            assert abs(o) <= 1e-12 * scale
+
+
+def test_parity_forbidden_is_exactly_zero_in_fock_space():
+    rng = np.random.default_rng(300)
+    for n, ne in [(3, 2), (4, 2), (4, 4), (5, 4)]:
+        F = Fock(n)
+        for _ in range(3):
+            Q, b, Phi = _fock_case(rng, n, ne)
+            pi = np.sign(np.linalg.det(Q)) * (-1) ** int(b.sum())
+            if pi > 0:
+                b[0] ^= 1
+            assert abs(F.estimator(Phi, F.shadow_state(Q, b))) < 1e-12
+
+
+@pytest.mark.parametrize("n,ne", [(6, 2), (8, 4), (12, 6), (16, 8)])
+def test_interpolation_dft_vs_chebyshev(n, ne):
+    """Roots-of-unity DFT and the paper's Chebyshev nodes with a least-squares
+    Vandermonde fit give the same coefficients."""
+    rng = np.random.default_rng(400 + n)
+    Q, b, Phi = _fock_case(rng, n, ne, det_sign=1)
+    o1, c1, sc = orc.pair(Q, b, Phi, mode=orc.INTERP_ROOTS)
+    o2, c2, _ = orc.pair(Q, b, Phi, mode=orc.INTERP_CHEBYSHEV)
+    o3, c3, _ = orc.pair(Q, b, Phi, mode=orc.INTERP_ROOTS, nodes=n - ne // 2 + 1)
+    cm = np.abs(c1).max()
+    assert np.abs(c1 - c3).max() <= 1e-12 * cm
+    assert np.abs(c1 - c2).max() <= 1e-8 * cm  # monomial Vandermonde on [-1, 1] loses digits
+    assert abs(o1 - o3) <= 1e-11 * sc
+
+
+def test_walker_scaling_invariance():
+    """<Psi_T|phi> for Phi X is det X times that of Phi (the walker is a determinant)."""
+    rng = np.random.default_rng(500)
+    n, ne = 8, 4
+    Q = synth.haar_orthogonal(rng, 2 * n, 16)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 1)
+    X = rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne))
+    o1, p1, s1, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    o2, p2, s2, _ = orc.overlap(Phi @ X, Q, b, per_pair=True)
+    d = np.linalg.det(X)
+    assert np.abs(p2 - d * p1).max() <= 1e-11 * np.abs(d) * s1.max()
+
+
+# ------------------------------------------ unbiasedness (exact averages)
+
+
+def signed_permutation_group(N):
+    for perm in itertools.permutations(range(N)):
+        for signs in itertools.product((-1.0, 1.0), repeat=N):
+            Q = np.zeros((N, N))
+            Q[np.arange(N), perm] = signs
+            yield Q
+
+
+def _born_table(F, group, Psi):
+    """All (Q, b) with non-zero Born weight p(b|Q) for the group, flattened."""
+    n = F.n
+    prob = F.born_probabilities(group, Psi)
+    bits = np.array([[(x >> j) & 1 for j in range(n)] for x in range(1 << n)], np.uint8)
+    g_idx, x_idx = np.nonzero(prob > 1e-15)
+    return group[g_idx], bits[x_idx], prob[g_idx, x_idx]
+
+
+def _random_eta_state(rng, F, ne):
+    """A random normalised state with exactly ne particles (not a Slater determinant)."""
+    v = np.zeros(F.dim, complex)
+    for x in range(F.dim):
+        if bin(x).count("1") == ne:
+            v[x] = rng.standard_normal() + 1j * rng.standard_normal()
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_exact_unbiasedness_signed_permutation_group(n):
+    """Averaged over the whole signed-permutation group of O(2n) with Born weights
+    p(b|Q) = <Psi|rho_{Q,b}|Psi>, Psi = (|0> + |Psi_T>)/sqrt2, the estimator equals
+    <Psi_T|phi> exactly -- this pins the channel weights, kappa and all phases."""
+    rng = np.random.default_rng(600 + n)
+    ne = 2
+    F = Fock(n)
+    PsiT = _random_eta_state(rng, F, ne)
+    Psi = (F.vac + PsiT) / np.sqrt(2)
+    Phi = synth.walkers(rng, n, ne, 1)[0] @ (rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne)))
+    exact = np.vdot(PsiT, F.slater(Phi))
+    group = np.array(list(signed_permutation_group(2 * n)))
+    Qs, bs, ws = _born_table(F, group, Psi)
+    _, per, _, _ = orc.overlap(Phi[None], Qs, bs, per_pair=True)
+    est = np.sum(ws * per[0]) / len(group)
+    assert abs(est - exact) <= 1e-12 * max(1.0, abs(exact)), (est, exact)
+
+
+def test_channel_eigenvalues_signed_permutations():
+    """The measure-and-prepare channel of the signed-permutation ensemble (n = 2)
+    scales gamma_S by lambda_{|S|/2} = C(n,k)/C(2n,2k)."""
+    n = 2
+    F = Fock(n)
+    lam = channel_weights(n)
+    group = list(signed_permutation_group(2 * n))
+    states = {}
+    for gi, Q in enumerate(group):
+        for x in range(1 << n):
+            b = np.array([(x >> j) & 1 for j in range(n)], np.uint8)
+            states[(gi, x)] = F.shadow_state(Q, b)
+    for S in [(0, 1), (0, 2), (1, 3), (0, 1, 2, 3)]:
+        G = np.eye(F.dim, dtype=complex)
+        for mu in S:
+            G = G @ F.gamma[mu]
+        out = np.zeros_like(G)
+        for (gi, x), psi in states.items():
+            rho = np.outer(psi, psi.conj())
+            out += np.trace(G @ rho) * rho
+        out /= len(group)
+        assert np.abs(out - lam[len(S) // 2] * G).max() < 1e-12
+
+
+@pytest.mark.slow
+def test_haar_born_sampling_converges_to_slater_overlap():
+    """Literal shadow protocol at n = 4: Haar Q, b drawn from the Born rule,
+    snapshot mean within 4 standard errors of det(Psi_T^dag Phi)."""
+    rng = np.random.default_rng(700)
+    n, ne, P = 4, 2, 20000
+    F = Fock(n)
+    Psi_orb = synth.walkers(rng, n, ne, 1)[0]
+    Psi_orb /= np.linalg.norm(Psi_orb[:, 0])
+    Psi_orb, _ = np.linalg.qr(Psi_orb)
+    PsiT = F.slater(Psi_orb)
+    PsiT /= np.linalg.norm(PsiT)
+    Psi = (F.vac + PsiT) / np.sqrt(2)
+    Phi = synth.walkers(rng, n, ne, 1)[0]
+    exact = np.linalg.det(Psi_orb.conj().T @ Phi)
+    assert abs(np.vdot(PsiT, F.slater(Phi)) - exact) < 1e-12
+    Q = synth.haar_orthogonal(rng, 2 * n, P)
+    prob = np.clip(F.born_probabilities(Q, Psi), 0.0, None)
+    bs = np.zeros((P, n), np.uint8)
+    for p in range(P):
+        x = rng.choice(1 << n, p=prob[p] / prob[p].sum())
+        bs[p] = [(x >> j) & 1 for j in range(n)]
+    ov, per, _, _ = orc.overlap(Phi[None], Q, bs, per_pair=True)
+    se = np.std(per[0]) / np.sqrt(P)
+    assert abs(ov[0] - exact) < 4 * se, (ov[0], exact, se)
+
+
+# ----------------------------------------------------- gradient pins
+
+
+def test_gradient_exact_linearity_and_euler():
+    rng = np.random.default_rng(800)
+    n, ne, P = 6, 4, 24
+    Q = synth.haar_orthogonal(rng, 2 * n, P)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 2)
+    ov, g, _ = orc.overlap_grad(Phi, Q, b)
+    ov2, _, _, _ = orc.overlap(Phi, Q, b)
+    assert np.allclose(ov, ov2, rtol=0, atol=1e-13 * np.abs(ov).max())
+    for w in range(2):
+        # Euler / antisymmetry identity g^T Phi = O I (O is multilinear and alternating in the columns)
+        M = g[w].T @ Phi[w]
+        assert np.abs(M - ov[w] * np.eye(ne)).max() <= 1e-10 * np.abs(g[w]).max() * np.abs(Phi[w]).max() * n
+        # exact t-polynomial of O(Phi + t E) recovered by a DFT on a circle (degree <= ne)
+        E = rng.standard_normal((n, ne)) + 1j * rng.standard_normal((n, ne))
+        K, r = ne + 1, 0.3
+        ts = r * np.exp(2j * np.pi * np.arange(K) / K)
+        vals = np.array([orc.overlap((Phi[w] + t * E)[None], Q, b)[0][0] for t in ts])
+        c1 = np.sum(vals * np.exp(-2j * np.pi * np.arange(K) / K)) / K / r
+        assert abs(c1 - np.sum(g[w] * E)) <= 1e-9 * np.abs(g[w]).sum() * np.abs(E).max()
+        # holomorphic: D_{iE} = i D_E (central difference, exact for a polynomial up to O(h^2))
+        h = 1e-4
+        dE = (orc.overlap((Phi[w] + h * E)[None], Q, b)[0][0] - orc.overlap((Phi[w] - h * E)[None], Q, b)[0][0]) / (2 * h)
+        diE = (orc.overlap((Phi[w] + 1j * h * E)[None], Q, b)[0][0]
+               - orc.overlap((Phi[w] - 1j * h * E)[None], Q, b)[0][0]) / (2 * h)
+        assert abs(diE - 1j * dE) <= 1e-6 * abs(dE)
+        assert abs(dE - np.sum(g[w] * E)) <= 1e-6 * abs(dE)
+
+
+def test_force_bias_exact_for_slater_trial():
+    """With the exact signed-permutation group average (n = 3), the shadow overlap
+    and gradient are exact, so the force bias equals i tr(L Phi (Psi^dag Phi)^{-1} Psi^dag)."""
+    rng = np.random.default_rng(900)
+    n, ne = 3, 2
+    F = Fock(n)
+    Psi_orb, _ = np.linalg.qr(rng.standard_normal((n, ne)) + 1j * rng.standard_normal((n, ne)))
+    PsiT = F.slater(Psi_orb)
+    Psi = (F.vac + PsiT) / np.sqrt(2)
+    Phi = synth.walkers(rng, n, ne, 1)[0]
+    walkers = [Phi]
+    for k in range(n):
+        for j in range(ne):
+            P2 = Phi.copy()
+            P2[:, j] = 0
+            P2[k, j] = 1
+            walkers.append(P2)
+    walkers = np.array(walkers)
+    group = np.array(list(signed_permutation_group(2 * n)))
+    Qs, bs, ws = _born_table(F, group, Psi)
+    _, per, _, _ = orc.overlap(walkers, Qs, bs, per_pair=True)
+    est = per @ ws / len(group)
+    O = est[0]
+    g = est[1:].reshape(n, ne)
+    S = Psi_orb.conj().T @ Phi
+    assert abs(O - np.linalg.det(S)) < 1e-12
+    L = synth.cholesky_vectors(rng, n, 5)
+    xb = orc.force_bias(L.astype(complex), Phi[None], np.array([O]), g[None], sqrt_dt=0.0)[0]
+    Gf = Phi @ np.linalg.inv(S) @ Psi_orb.conj().T
+    ref = np.array([1j * np.trace(L[c] @ Gf) for c in range(5)])
+    assert np.abs(xb - ref).max() < 1e-11
+    xb2 = orc.force_bias(L.astype(complex), Phi[None], np.array([O]), g[None], sqrt_dt=0.1)[0]
+    assert np.allclose(xb2, -0.1 * ref, atol=1e-12)
+
+
+# ---------------------------------------------- the pins catch mistakes
+
+
+def _pin_suite_passes(v) -> bool:
+    """A compact re-run of the brute-force, closed-form and Pfaffian pins against oracle variant v."""
+    rng = np.random.default_rng(1000)
+    A = rand_skew(rng, 6)
+    if abs(v.pfaffian(A) - pfaffian_by_matchings(A)) > 1e-10 * abs(pfaffian_by_matchings(A)):
+        return False
+    for n, ne in [(3, 2), (4, 2), (4, 4)]:
+        F = Fock(n)
+        for trial in range(3):
+            Q, b, Phi = _fock_case(rng, n, ne, det_sign=1)
+            pi = np.sign(np.linalg.det(Q)) * (-1) ** int(b.sum())
+            if pi < 0:
+                b[0] ^= 1
+            o, _, sc = v.pair(Q, b, Phi)
+            ob = F.estimator(Phi, F.shadow_state(Q, b))
+            if abs(o - ob) > 1e-9 * max(abs(ob), 1e-12):
+                return False
+    return True
+
+
+def test_planted_mistakes_are_caught():
+    assert _pin_suite_passes(orc.variant(0))
+    for k, what in orc.MUTATIONS.items():
+        assert not _pin_suite_passes(orc.variant(k)), f"planted mistake {k} ({what}) went unnoticed"
