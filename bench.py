@@ -1,0 +1,339 @@
+"""Benchmark of the matchgate-shadow overlap hot path on GB300.
+
+One step = one pass of the hot path over one batch: build the device snapshot
+set from (Q, b) (qcs_build_snapshots) and evaluate the shadow overlaps of all
+walkers against all snapshots (qcs_overlap), FP64, at the paper-shaped size
+n = 16 modes, ne = 8 electrons, 1024 walkers x 20000 snapshots (Haar Q,
+uniform 16-bit b, seed 0).  The metric is walker x snapshot pairs per second
+(every pair of the batch counts, including the parity -1 pairs, which are
+exactly zero and skipped).
+
+Printed JSON line (rank 0):
+  value          device-resident throughput (inputs in HBM before the timed region)
+  e2e            the same through the C ABI from pinned HOST buffers: copies of Q, b
+                 and the walkers in, overlaps out, inside the timed region
+  roofline       dominant kernel (pair_overlap_kernel) against the FP64 ALU peak
+  cpu_baseline   the CPU oracle on a bounded sample of the same workload
+  clocks         nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle instead (the reference arm of this
+benchmark).  Under torchrun each rank runs the full workload on its own GPU
+(independent replicas, no collective in the data path); the time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker×snapshot overlap(+grad) pairs/s at n=16; % of FP64 peak vs plain GPU path"
+# FP64 ALU peak of a GB300: 152 SMs x 4 FP64 flop/clk/SM (one 32-lane DFMA issue per
+# 64 clocks per sub-partition, measured) x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qcs_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def traffic_for(kernel_src: str, kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        r = rec.get(kernel)
+        if r and r.get("source_sha256") == sha:
+            return r.get("bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def run_e2e(args, data, dev, step, barrier, ws, wl):
+    """Same metric through the C ABI from pinned HOST buffers: H2D copies of Q, b and
+    the walkers and the D2H copy of the overlaps are inside the timed region."""
+    import torch
+    import torch.distributed as dist
+
+    hQ = torch.from_numpy(data["Q"]).pin_memory()
+    hb = torch.from_numpy(data["b"]).pin_memory()
+    hP = torch.from_numpy(data["Phi"]).pin_memory()
+    hO = torch.empty(wl.W, dtype=torch.complex128).pin_memory()
+    e2e_steps = max(3, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Q = hQ.to(dev, non_blocking=True)
+        b = hb.to(dev, non_blocking=True)
+        Phi = hP.to(dev, non_blocking=True)
+        snaps, ov = step(Q, b, Phi)
+        hO.copy_(ov, non_blocking=True)
+        torch.cuda.synchronize()
+        del snaps
+    t_e2e = time.perf_counter() - t0
+    if ws > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = hQ.numel() * 8 + hb.numel() + hP.numel() * 16
+    d2h = hO.numel() * 16
+    return {"value": ws * wl.W * wl.P * e2e_steps / t_e2e, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+
+def cpu_baseline(wl, data, target_s=10.0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle.oracle as orc
+
+    cores = orc.max_threads()
+    Wc = min(64, wl.W)
+    Pc = min(wl.P, 200)
+    t0 = time.perf_counter()
+    orc.overlap(data["Phi"][:Wc], data["Q"][:Pc], data["b"][:Pc], threads=cores)
+    dt = time.perf_counter() - t0
+    # grow the sample to about target_s seconds of CPU work
+    Pc2 = int(min(wl.P, max(Pc, Pc * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    _, _, _, used = orc.overlap(data["Phi"][:Wc], data["Q"][:Pc2], data["b"][:Pc2], threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": Wc * Pc2 / dt, "unit": "pairs/s", "cores": int(used), "kind": "oracle",
+            "sample": f"{Wc} walkers x {Pc2} snapshots of the same workload (first rows), "
+                      f"{dt:.1f} s, FP64, 2n+1 roots-of-unity nodes, OpenMP over pairs"}
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle.oracle as orc
+
+    data = wl.generate(seed=0, W=64, P=min(wl.P, 4000))
+    cores = orc.max_threads()
+    Wc = 64
+    # size each step at a few seconds of CPU work
+    t0 = time.perf_counter()
+    orc.overlap(data["Phi"][:Wc], data["Q"][:100], data["b"][:100], threads=cores)
+    per_pair = (time.perf_counter() - t0) / (Wc * 100)
+    Pc = int(min(4000, max(100, 4.0 / max(per_pair * Wc, 1e-9))))
+    for _ in range(args.warmup):
+        orc.overlap(data["Phi"][:Wc], data["Q"][:Pc], data["b"][:Pc], threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.overlap(data["Phi"][:Wc], data["Q"][:Pc], data["b"][:Pc], threads=cores)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    val = Wc * Pc * args.steps / T
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "ne": wl.ne, "walkers": wl.W, "snapshots": wl.P,
+                       "sample_per_step": f"{Wc} walkers x {Pc} snapshots"},
+            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{Wc} walkers x {Pc} snapshots per step"},
+            "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--walkers", type=int, default=0, help="override the walker count (profiling cases)")
+    ap.add_argument("--snapshots", type=int, default=0, help="override the snapshot count (profiling cases)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from paper_2506_22408_gb300 import synth
+
+    wl = synth.PAPER_SHAPED
+    if args.walkers or args.snapshots:
+        import dataclasses
+
+        W = args.walkers or wl.W
+        P = args.snapshots or wl.P
+        wl = dataclasses.replace(wl, name=f"n={wl.n} ne={wl.ne} {W}x{P} (reduced profiling case)", W=W, P=P)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_22408_gb300 import qcs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("gloo", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    data = wl.generate(seed=0)
+    ctx = qcs.Context(local)
+    Qd = torch.from_numpy(data["Q"]).to(dev)
+    bd = torch.from_numpy(data["b"]).to(dev)
+    Pd = torch.from_numpy(data["Phi"]).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(Q, b, Phi):
+        snaps = qcs.Snapshots(ctx, Q, b)
+        ov, _ = qcs.overlap(ctx, snaps, Phi)
+        return snaps, ov
+
+    for _ in range(args.warmup):
+        snaps, ov = step(Qd, bd, Pd)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    npar = int((snaps.parity() == 1).sum().item())
+    del snaps
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    ctx.profile(True)
+    ctx.profile_read()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))  # L2 flush between steps, outside the timed events
+            ev[i][0].record(stream)
+            snaps, ov = step(Qd, bd, Pd)
+            ev[i][1].record(stream)
+        barrier()
+    ctx.profile(False)
+    kern_ms, kern_launches = ctx.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    pairs = wl.W * wl.P
+    value = ws * pairs * args.steps / t_total
+    del snaps
+
+    # ---------------- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, data, dev, step, barrier, ws, wl)
+    # ---------------- roofline of the dominant kernel
+    fpp = qcs.flops_per_pair(wl.n, wl.ne)
+    flops_launch = fpp * npar * wl.W
+    avg_ms = kern_ms / max(kern_launches, 1)
+    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+    src = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc", "qcs_overlap.cu")
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for(src, "pair_overlap_kernel"),
+            "kernel": "pair_overlap_kernel", "kernel_ms": avg_ms, "flops_per_launch": flops_launch,
+            "peak_source": "FP64 ALU: 152 SM x 4 flop/clk x 2.07 GHz (derived from unit counts and the maximum "
+                           "clock; MEASURED_PEAKS.json carries no FP64 figure)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "n": wl.n, "ne": wl.ne,
+                       "walkers": wl.W, "snapshots": wl.P, "parity_plus_snapshots": npar,
+                       "nodes": "minimum (n-ne+1 roots of unity, floor/2+1 evaluated)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "snapshot set (164 MB) larger than L2, and L2 flushed between timed steps"},
+            "nontrivial_pairs_per_s": ws * npar * wl.W * args.steps / t_total,
+            "e2e": e2e,
+            "roofline": roof,
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * 5}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, data)
+    if ws > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,17 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
                           const double *d_walkers, const double *d_overlap, const double *d_grad, double sqrt_dt,
                           double *d_xbar, void *stream);
 
+/* ------------------------------------------------------------ profiling */
+
+/* Measurement hooks (no counterpart in the paper).  While enabled, every
+ * launch of a dominant kernel (the pair kernel of qcs_overlap, the adjoint
+ * kernel of qcs_overlap_grad) is bracketed by two CUDA events recorded on the
+ * launch stream.  qcs_profile_read waits for the recorded events, returns
+ * the summed kernel time in milliseconds and the number of launches since the
+ * previous read, and clears the record.  Errors: QCS_ERR_ARG, QCS_ERR_CUDA. */
+qcs_status qcs_profile_enable(qcs_ctx *ctx, int enable);
+qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
+
 /* ----------------------------------------------------------- accounting */
 
 /* Algorithmic FP64 flop count per non-trivial (pi = +1) pair of qcs_overlap

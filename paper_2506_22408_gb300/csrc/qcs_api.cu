@@ -1,0 +1,392 @@
+// qcs_api.cu -- the C ABI of libqcs (declared in include/qcs.h).
+//
+// Host-side argument checking, the per-device context and its workspace, the
+// interpolation-node plan, and the kernel launch sequence of each entry point.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qcs_internal.h"
+
+// ------------------------------------------------------------ helpers
+
+qcs_status qcs_fail(qcs_ctx *ctx, qcs_status code, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+qcs_status qcs_check_launch(qcs_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return QCS_OK;
+}
+
+qcs_status qcs_set_smem(qcs_ctx *ctx, const void *func, size_t bytes) {
+    if (bytes > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "shared memory request too large");
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    return QCS_OK;
+}
+
+qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out) {
+    bytes = align16(bytes < 16 ? 16 : bytes);
+    if (bytes > ctx->work_bytes) {
+        if (ctx->work) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->work);
+            ctx->work = nullptr;
+            ctx->work_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&ctx->work, bytes);
+        if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        ctx->work_bytes = bytes;
+    }
+    *out = ctx->work;
+    return QCS_OK;
+}
+
+void qcs_prof_begin(qcs_ctx *ctx, cudaStream_t st) {
+    if (!ctx->profiling) return;
+    std::pair<cudaEvent_t, cudaEvent_t> ev;
+    if (!ctx->prof_pool.empty()) {
+        ev = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+    } else {
+        cudaEventCreate(&ev.first);
+        cudaEventCreate(&ev.second);
+    }
+    cudaEventRecord(ev.first, st);
+    ctx->prof_events.push_back(ev);
+}
+
+void qcs_prof_end(qcs_ctx *ctx, cudaStream_t st) {
+    if (!ctx->profiling || ctx->prof_events.empty()) return;
+    cudaEventRecord(ctx->prof_events.back().second, st);
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+double binom(int n, int k) {
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return std::floor(r + 0.5);
+}
+
+qcs_status check_sizes(qcs_ctx *ctx, int n, int ne) {
+    if (n < 1 || n > QCS_MAX_N) return qcs_fail(ctx, QCS_ERR_ARG, "n must be in [1, QCS_MAX_N]");
+    if (ne < 2 || ne > n) return qcs_fail(ctx, QCS_ERR_ARG, "ne must satisfy 2 <= ne <= n");
+    if (ne & 1) return qcs_fail(ctx, QCS_ERR_ARG, "ne must be even (odd-particle shadow overlaps vanish)");
+    return QCS_OK;
+}
+
+}  // namespace
+
+// Interpolation plan.  pf(A(z)) = z^{ne/2} q(z) with deg q <= d = n - ne, so N >= d+1
+// roots of unity z_k = w^k determine q exactly: c'_t = (1/N) sum_k q_k w^{-kt}.  The
+// estimator needs sum_t w'_t c'_t with w'_t = C(2n, ne+2t)/C(n, ne/2+t), i.e.
+// sum_k beta_k q_k with beta_k = (1/N) sum_t w'_t w^{-kt}.  The kernels evaluate
+// pf'_k = pf(B + conj(z_k) D) = z_k^{-m/2} pf(A(z_k)), so q_k = z_k^d pf'_k.
+// For parity +1 snapshots c'_{d-t} = c'_t gives q_{N-k} = w^{-kd} q_k, and the
+// pairs (k, N-k) merge: only k = 0..floor(N/2) are evaluated.
+qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node_plan *plan) {
+    const int d = n - ne;
+    int N = nodes > 0 ? nodes : d + 1;
+    if (N < d + 1 || N > QCS_MAX_NODES) return QCS_ERR_ARG;
+    typedef std::complex<double> C;
+    const double tw = 2.0 * M_PI / (double)N;
+    std::vector<C> beta(N);
+    for (int k = 0; k < N; ++k) {
+        C s = 0.0;
+        for (int t = 0; t <= d; ++t) {
+            double wt = binom(2 * n, ne + 2 * t) / binom(n, ne / 2 + t);
+            double ang = -tw * (double)(((long long)k * t) % N);
+            s += wt * C(std::cos(ang), std::sin(ang));
+        }
+        beta[k] = s / (double)N;
+    }
+    auto wpow = [&](long long e) {
+        long long r = ((e % N) + N) % N;
+        double ang = tw * (double)r;
+        return C(std::cos(ang), std::sin(ang));
+    };
+    plan->N = N;
+    plan->all = (flags & QCS_FLAG_ALL_NODES) ? 1 : 0;
+    if (plan->all) {
+        plan->nev = N;
+        for (int k = 0; k < N; ++k) {
+            C wn = wpow(-k), g = beta[k] * wpow((long long)k * d);
+            plan->wnode[k] = cmk(wn.real(), wn.imag());
+            plan->gamma[k] = cmk(g.real(), g.imag());
+        }
+    } else {
+        const int K = N / 2;
+        plan->nev = K + 1;
+        for (int k = 0; k <= K; ++k) {
+            C wn = wpow(-k), g;
+            if (k == 0) g = beta[0];
+            else if (2 * k == N) g = beta[k] * wpow((long long)k * d);
+            else g = beta[k] * wpow((long long)k * d) + beta[N - k];
+            plan->wnode[k] = cmk(wn.real(), wn.imag());
+            plan->gamma[k] = cmk(g.real(), g.imag());
+        }
+    }
+    return QCS_OK;
+}
+
+// ------------------------------------------------------------ context
+
+extern "C" qcs_status qcs_create(qcs_ctx **ctx, int device) {
+    if (!ctx) return QCS_ERR_ARG;
+    *ctx = nullptr;
+    qcs_ctx *c = new qcs_ctx();
+    c->device = device;
+    DeviceGuard g(device);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int optin = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)optin;
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return QCS_ERR_CUDA;
+    }
+    *ctx = c;
+    return QCS_OK;
+}
+
+extern "C" qcs_status qcs_destroy(qcs_ctx *ctx) {
+    if (!ctx) return QCS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->work) cudaFree(ctx->work);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    for (auto &ev : ctx->prof_events) ctx->prof_pool.push_back(ev);
+    for (auto &ev : ctx->prof_pool) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    delete ctx;
+    return QCS_OK;
+}
+
+extern "C" qcs_status qcs_profile_enable(qcs_ctx *ctx, int enable) {
+    if (!ctx) return QCS_ERR_ARG;
+    ctx->profiling = enable != 0;
+    return QCS_OK;
+}
+
+extern "C" qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches) {
+    if (!ctx || !total_ms || !launches) return QCS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    double tot = 0.0;
+    for (auto &ev : ctx->prof_events) {
+        cudaError_t e = cudaEventSynchronize(ev.second);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.first, ev.second);
+        if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string("qcs_profile_read: ") + cudaGetErrorString(e));
+        tot += ms;
+        ctx->prof_pool.push_back(ev);
+    }
+    *launches = (int64_t)ctx->prof_events.size();
+    *total_ms = tot;
+    ctx->prof_events.clear();
+    return QCS_OK;
+}
+
+extern "C" const char *qcs_last_error(const qcs_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+extern "C" size_t qcs_workspace_bytes(const qcs_ctx *ctx) { return ctx ? ctx->work_bytes : 0; }
+
+extern "C" qcs_status qcs_sync_status(qcs_ctx *ctx, void *stream) {
+    if (!ctx) return QCS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string("qcs_sync_status: ") + cudaGetErrorString(e));
+    return (qcs_status)(*ctx->h_status);
+}
+
+// ------------------------------------------------------------ snapshots
+
+extern "C" qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const double *d_Q, const uint8_t *d_b,
+                                          qcs_snapshots **out, void *stream) {
+    if (!ctx || !out) return QCS_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || n > QCS_MAX_N) return qcs_fail(ctx, QCS_ERR_ARG, "n must be in [1, QCS_MAX_N]");
+    if (P < 0 || P > (int64_t)INT32_MAX) return qcs_fail(ctx, QCS_ERR_ARG, "P out of range");
+    if (P > 0 && (!d_Q || !d_b)) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot input");
+    DeviceGuard g(ctx->device);
+    qcs_snapshots *s = new qcs_snapshots();
+    s->n = n;
+    s->P = P;
+    s->device = ctx->device;
+    const int64_t Pa = P > 0 ? P : 1;
+    cudaError_t e = cudaMalloc(&s->Qt, sizeof(cd) * (size_t)Pa * 2 * n * n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->parity, (size_t)Pa);
+    if (e == cudaSuccess) e = cudaMalloc(&s->idx, sizeof(int) * (size_t)Pa);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_count, sizeof(int));
+    if (e != cudaSuccess) {
+        qcs_snapshots_free(s);
+        return qcs_fail(ctx, QCS_ERR_CUDA, std::string("snapshot cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    qcs_status st = qcs_launch_snapshot_build(ctx, s, d_Q, d_b, (cudaStream_t)stream);
+    if (st != QCS_OK) {
+        qcs_snapshots_free(s);
+        return st;
+    }
+    *out = s;
+    return QCS_OK;
+}
+
+extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
+    if (!s) return QCS_ERR_ARG;
+    DeviceGuard g(s->device);
+    cudaDeviceSynchronize();
+    if (s->Qt) cudaFree(s->Qt);
+    if (s->parity) cudaFree(s->parity);
+    if (s->idx) cudaFree(s->idx);
+    if (s->d_count) cudaFree(s->d_count);
+    delete s;
+    return QCS_OK;
+}
+
+extern "C" qcs_status qcs_snapshots_parity(const qcs_snapshots *s, int8_t *d_parity, void *stream) {
+    if (!s || (!d_parity && s->P > 0)) return QCS_ERR_ARG;
+    if (s->P == 0) return QCS_OK;
+    DeviceGuard g(s->device);
+    cudaError_t e = cudaMemcpyAsync(d_parity, s->parity, (size_t)s->P, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? QCS_OK : QCS_ERR_CUDA;
+}
+
+extern "C" int64_t qcs_snapshots_count(const qcs_snapshots *s) { return s ? s->P : -1; }
+extern "C" int qcs_snapshots_modes(const qcs_snapshots *s) { return s ? s->n : -1; }
+
+// ------------------------------------------------------------ overlaps
+
+namespace {
+
+const int kChunk = 8;
+
+struct OverlapWork {
+    cd *Ut, *pref, *partial;
+    int nchunks;
+};
+
+qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
+                          const qcs_opts *opts, cudaStream_t st, qcs_node_plan *plan, OverlapWork *wk) {
+    if (!ctx) return QCS_ERR_ARG;
+    if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set");
+    if (s->device != ctx->device) return qcs_fail(ctx, QCS_ERR_ARG, "snapshot set lives on another device");
+    const int n = s->n;
+    qcs_status c = check_sizes(ctx, n, ne);
+    if (c != QCS_OK) return c;
+    if (W < 0) return qcs_fail(ctx, QCS_ERR_ARG, "W < 0");
+    if (W > 0 && !d_walkers) return qcs_fail(ctx, QCS_ERR_ARG, "null walkers");
+    qcs_opts o = {QCS_FP64, 0, 0u, 0};
+    if (opts) o = *opts;
+    if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "precision mode not built");
+    if (qcs_make_node_plan(n, ne, o.nodes, o.flags, plan) != QCS_OK)
+        return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
+    wk->nchunks = (int)((s->P + kChunk - 1) / kChunk);
+    if (wk->nchunks < 1) wk->nchunks = 1;
+    size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
+    size_t b_pref = align16(sizeof(cd) * (size_t)W);
+    size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nchunks);
+    void *base = nullptr;
+    qcs_status ws = qcs_workspace(ctx, b_ut + b_pref + b_part, &base);
+    if (ws != QCS_OK) return ws;
+    wk->Ut = (cd *)base;
+    wk->pref = (cd *)((char *)base + b_ut);
+    wk->partial = (cd *)((char *)base + b_ut + b_pref);
+    return qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, wk->Ut, wk->pref, st);
+}
+
+}  // namespace
+
+extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
+                                  double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream) {
+    if (!ctx) return QCS_ERR_ARG;
+    if (W > 0 && !d_overlap) return qcs_fail(ctx, QCS_ERR_ARG, "null overlap output");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    qcs_node_plan plan;
+    OverlapWork wk;
+    qcs_status r = overlap_common(ctx, s, ne, W, d_walkers, opts, st, &plan, &wk);
+    if (r != QCS_OK) return r;
+    if (W == 0) return QCS_OK;
+    if (d_per_pair && s->P > 0) {
+        cudaError_t e = cudaMemsetAsync(d_per_pair, 0, sizeof(cd) * (size_t)W * s->P, st);
+        if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "memset per-pair output");
+    }
+    qcs_pair_launch L;
+    L.n = s->n;
+    L.ne = ne;
+    L.W = W;
+    L.P = s->P;
+    L.chunk = kChunk;
+    L.nchunks = wk.nchunks;
+    L.Ut = wk.Ut;
+    L.pref = wk.pref;
+    L.s = s;
+    L.partial = wk.partial;
+    L.per_pair = (cd *)d_per_pair;
+    L.plan = plan;
+    r = qcs_launch_pairs(ctx, L, st);
+    if (r != QCS_OK) return r;
+    return qcs_launch_reduce(ctx, W, s->P, wk.nchunks, wk.partial, wk.pref, (cd *)d_overlap, st);
+}
+
+extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W,
+                                       const double *d_walkers, double *d_overlap, double *d_grad,
+                                       const qcs_opts *opts, void *stream) {
+    (void)s; (void)ne; (void)W; (void)d_walkers; (void)d_overlap; (void)d_grad; (void)opts; (void)stream;
+    return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "qcs_overlap_grad: not built yet");
+}
+
+extern "C" qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const double *d_L,
+                                     const double *d_walkers, const double *d_overlap, const double *d_grad,
+                                     double sqrt_dt, double *d_xbar, void *stream) {
+    (void)n; (void)ne; (void)W; (void)nchol; (void)d_L; (void)d_walkers; (void)d_overlap; (void)d_grad;
+    (void)sqrt_dt; (void)d_xbar; (void)stream;
+    return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "qcs_force_bias: not built yet");
+}
+
+// ------------------------------------------------------------ accounting
+
+extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
+    qcs_node_plan plan;
+    if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
+    if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
+    const int d = n - ne, m = 2 * n - ne;
+    double f = 0.0;
+    f += 8.0 * 2.0 * (double)n * n * n;                       // T: n x 2n x n complex MACs
+    f += 8.0 * 2.0 * (double)n * tri_count(ne);               // B occupied x occupied
+    f += 4.0 * 2.0 * (double)n * ne * 2 * d;                  // B occupied x empty
+    f += 2.0 * 2.0 * (double)n * tri_count(2 * d);            // B empty x empty
+    double node = 0.0;
+    for (int r = m; r > 2; r -= 2) node += 16.0 * tri_count(r - 2) + 6.0 * (r - 2);
+    f += node * plan.nev;
+    return f;
+}

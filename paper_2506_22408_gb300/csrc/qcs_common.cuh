@@ -1,0 +1,84 @@
+// qcs_common.cuh -- device helpers shared by the GB300 kernels of libqcs.
+//
+// Complex numbers are double2 (x = re, y = im), the layout of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qcs.h"
+
+typedef double2 cd;
+
+#define QCS_WARP 32
+#define QCS_FULL 0xffffffffu
+
+__host__ __device__ __forceinline__ cd cmk(double x, double y) { return make_double2(x, y); }
+
+__device__ __forceinline__ cd cmul(cd a, cd b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ cd cadd(cd a, cd b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ cd csub(cd a, cd b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ cd cneg(cd a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ cd cconj(cd a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ cd cscale(cd a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// acc += a * b
+__device__ __forceinline__ void cfma(cd &acc, cd a, cd b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc -= a * b
+__device__ __forceinline__ void cfms(cd &acc, cd a, cd b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += a * r  (r real)
+__device__ __forceinline__ void crfma(cd &acc, cd a, double r) {
+    acc.x = fma(a.x, r, acc.x);
+    acc.y = fma(a.y, r, acc.y);
+}
+
+// 1/a for complex a; returns 0 when a == 0.
+__device__ __forceinline__ cd cinv(cd a) {
+    double d = fma(a.x, a.x, a.y * a.y);
+    if (d == 0.0) return make_double2(0.0, 0.0);
+    double r = 1.0 / d;
+    return make_double2(a.x * r, -a.y * r);
+}
+
+__device__ __forceinline__ bool cfinite(cd a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Pivot magnitude key without floating-point work: the high 32 bits of
+// max(|re|, |im|) (sign, exponent and 20 mantissa bits) order magnitudes to a
+// relative 2^-20, enough for partial pivoting.  NaN/Inf give the largest keys.
+__device__ __forceinline__ unsigned pivot_key(cd a) {
+    unsigned hx = (unsigned)__double2hiint(a.x) & 0x7fffffffu;
+    unsigned hy = (unsigned)__double2hiint(a.y) & 0x7fffffffu;
+    return hx > hy ? hx : hy;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(QCS_FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ cd warp_csum(cd v) {
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    return v;
+}
+
+// Packed strict upper triangle: entry (i, j), i < j, at j(j-1)/2 + i.
+__host__ __device__ __forceinline__ int tri_index(int i, int j) { return (j * (j - 1)) / 2 + i; }
+__host__ __device__ __forceinline__ int tri_count(int m) { return (m * (m - 1)) / 2; }
+
+__device__ __forceinline__ void raise_status(unsigned *status, unsigned bits) {
+    if (status) atomicOr(status, bits);
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }

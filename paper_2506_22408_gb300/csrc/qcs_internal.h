@@ -1,0 +1,77 @@
+// qcs_internal.h -- host-side structures shared by the translation units of libqcs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "qcs_common.cuh"
+
+struct qcs_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    unsigned *d_status = nullptr;  // device status word (OR of qcs_status bits)
+    unsigned *h_status = nullptr;  // pinned host mirror
+    void *work = nullptr;          // device workspace
+    size_t work_bytes = 0;
+    std::string last_error;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;  // recorded around dominant kernels
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;    // reusable event pairs
+};
+
+// Record the opening / closing event of a profiled launch (no-ops unless profiling).
+void qcs_prof_begin(qcs_ctx *ctx, cudaStream_t st);
+void qcs_prof_end(qcs_ctx *ctx, cudaStream_t st);
+
+struct qcs_snapshots {
+    int n = 0;
+    int64_t P = 0;
+    int device = 0;
+    cd *Qt = nullptr;         // P x 2n x n complexified sign-folded rows
+    int8_t *parity = nullptr; // P: +1 / -1 (0: singular or non-finite Q)
+    int *idx = nullptr;       // P: indices with parity +1, ascending (first *d_count valid)
+    int *d_count = nullptr;   // 1: number of parity +1 snapshots
+};
+
+// Helpers implemented in qcs_api.cu
+qcs_status qcs_fail(qcs_ctx *ctx, qcs_status code, const std::string &msg);
+qcs_status qcs_check_launch(qcs_ctx *ctx, const char *what);
+qcs_status qcs_set_smem(qcs_ctx *ctx, const void *func, size_t bytes);
+qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out);
+
+// Launchers implemented in the kernel translation units
+qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const double *d_Q, const uint8_t *d_b,
+                                     cudaStream_t st);
+
+struct qcs_node_plan {
+    int N;                       // roots of unity used
+    int nev;                     // nodes evaluated
+    int all;                     // 1: every node, every snapshot
+    cd wnode[QCS_MAX_NODES];     // multiplier of D at each evaluated node: conj(z_k)
+    cd gamma[QCS_MAX_NODES];     // weight of pf(B + conj(z_k) D) in sum_x w_x c_x
+};
+
+qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node_plan *plan);
+
+qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
+                                  cudaStream_t st);
+
+struct qcs_pair_launch {
+    int n, ne;
+    int64_t W, P;
+    int chunk, nchunks;
+    const cd *Ut;
+    const cd *pref;
+    const qcs_snapshots *s;
+    cd *partial;     // W x nchunks
+    cd *per_pair;    // W x P or null
+    qcs_node_plan plan;
+};
+
+qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t st);
+qcs_status qcs_launch_reduce(qcs_ctx *ctx, int64_t W, int64_t P, int nchunks, const cd *partial, const cd *pref,
+                             cd *overlap, cudaStream_t st);

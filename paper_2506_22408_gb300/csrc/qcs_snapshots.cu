@@ -1,0 +1,153 @@
+// qcs_snapshots.cu -- device representation of the shadow snapshots (Q_p, b_p).
+//
+// Eq. (b_mat) needs G_p = Q_p^T C_b Q_p with C_b the covariance matrix of SI
+// "Matrix Definitions" item 2.  Writing C_b = P_b J P_b with
+// P_b = diag(1, s_1, 1, s_2, ...), s_j = (-1)^{b_j}, and J = (+)_j [[0,1],[-1,0]],
+// gives G_p = Q'^T J Q' with Q' = P_b Q (rows 2j+1 of Q scaled by s_j, 0-based).
+// The overlap kernels use the complexified rows
+//     Qt[c][k] = Q'[c][2k] - i Q'[c][2k+1],   c < 2n, k < n,
+// so that the walker congruence becomes one complex n x n by n x 2n product.
+//
+// Each snapshot also gets its parity pi_p = det(Q_p) (-1)^{|b_p|} = det(Q'_p): the
+// measured state is a pure Gaussian state of that parity, and pairs with
+// pi_p = -1 contribute exactly zero to every overlap (the estimator's
+// coefficient sequence is palindromic up to pi_p while its weights are
+// symmetric).  det(Q_p) = +-1 is obtained from an LU factorisation with
+// partial pivoting (only its sign is used).
+#include "qcs_internal.h"
+
+namespace {
+
+// One warp per snapshot.  Dynamic shared memory: warps * (2n)^2 doubles.
+__global__ void snapshot_prepare_kernel(int n, int64_t P, const double *__restrict__ Q, const uint8_t *__restrict__ b,
+                                        cd *__restrict__ Qt, int8_t *__restrict__ parity, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = 2 * n;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double *A = reinterpret_cast<double *>(smem_raw) + (size_t)warp * N * N;
+    for (int64_t p = (int64_t)blockIdx.x * wpb + warp; p < P; p += (int64_t)gridDim.x * wpb) {
+        const double *Qp = Q + p * N * N;
+        const uint8_t *bp = b + p * n;
+        bool bad = false;
+        int nb = 0;
+        for (int j = lane; j < n; j += 32) nb += (bp[j] & 1);
+        for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(QCS_FULL, nb, o);
+        for (int e = lane; e < N * N; e += 32) {
+            double v = Qp[e];
+            bad |= !isfinite(v);
+            A[e] = v;
+        }
+        // complexified, sign-folded rows
+        cd *Qtp = Qt + p * N * n;
+        for (int e = lane; e < N * n; e += 32) {
+            int c = e / n, k = e - c * n;
+            double sg = (c & 1) ? ((bp[c >> 1] & 1) ? -1.0 : 1.0) : 1.0;
+            double q0 = Qp[c * N + 2 * k], q1 = Qp[c * N + 2 * k + 1];
+            Qtp[e] = cmk(sg * q0, -sg * q1);
+        }
+        bad = __any_sync(QCS_FULL, bad);
+        __syncwarp();
+        // sign of det(Q) by LU with partial pivoting (rows spread over lanes)
+        int sign = 1;
+        bool singular = false;
+        for (int k = 0; k < N && !singular; ++k) {
+            double best = -1.0;
+            int arg = k;
+            for (int i = k + lane; i < N; i += 32) {
+                double a = fabs(A[i * N + k]);
+                if (a > best) {
+                    best = a;
+                    arg = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(QCS_FULL, best, o);
+                int oa = __shfl_xor_sync(QCS_FULL, arg, o);
+                if (ob > best || (ob == best && oa < arg)) {
+                    best = ob;
+                    arg = oa;
+                }
+            }
+            if (!(best > 0.0)) {
+                singular = true;
+                break;
+            }
+            if (arg != k) {
+                for (int j = lane; j < N; j += 32) {
+                    double t = A[k * N + j];
+                    A[k * N + j] = A[arg * N + j];
+                    A[arg * N + j] = t;
+                }
+                sign = -sign;
+            }
+            __syncwarp();
+            double piv = A[k * N + k];
+            if (piv < 0) sign = -sign;
+            double rp = 1.0 / piv;
+            for (int i = k + 1 + lane; i < N; i += 32) {
+                double f = A[i * N + k] * rp;
+                for (int j = k + 1; j < N; ++j) A[i * N + j] = fma(-f, A[k * N + j], A[i * N + j]);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            int8_t pi = 0;
+            if (!singular && !bad) pi = (int8_t)(((nb & 1) ? -1 : 1) * sign);
+            parity[p] = pi;
+            if (bad) raise_status(status, QCS_ERR_NONFINITE);
+            else if (singular) raise_status(status, QCS_ERR_SINGULAR);
+        }
+        __syncwarp();
+    }
+}
+
+// Stable compaction of the snapshots with parity +1 (single block).
+__global__ void snapshot_compact_kernel(int64_t P, const int8_t *__restrict__ parity, int *__restrict__ idx,
+                                        int *__restrict__ count) {
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) base = 0;
+    __syncthreads();
+    for (int64_t s0 = 0; s0 < P; s0 += blockDim.x) {
+        int64_t p = s0 + tid;
+        int flag = (p < P && parity[p] == 1) ? 1 : 0;
+        unsigned bal = __ballot_sync(QCS_FULL, flag);
+        int pre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += warp_tot[w];
+        if (flag) idx[base + off + pre] = (int)p;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += warp_tot[w];
+            base += t;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *count = base;
+}
+
+}  // namespace
+
+qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const double *d_Q, const uint8_t *d_b,
+                                     cudaStream_t st) {
+    const int n = s->n;
+    const int N = 2 * n;
+    if (s->P > 0) {
+        const int wpb = 4;
+        size_t smem = (size_t)wpb * N * N * sizeof(double);
+        if (qcs_set_smem(ctx, (const void *)snapshot_prepare_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+        int64_t blocks = (s->P + wpb - 1) / wpb;
+        if (blocks > 4 * ctx->num_sms * 8) blocks = 4 * ctx->num_sms * 8;
+        snapshot_prepare_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, s->P, d_Q, d_b, s->Qt, s->parity,
+                                                                          ctx->d_status);
+        if (qcs_check_launch(ctx, "snapshot_prepare_kernel") != QCS_OK) return QCS_ERR_CUDA;
+    }
+    snapshot_compact_kernel<<<1, 1024, 0, st>>>(s->P, s->parity, s->idx, s->d_count);
+    return qcs_check_launch(ctx, "snapshot_compact_kernel");
+}

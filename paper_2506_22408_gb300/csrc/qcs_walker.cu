@@ -1,0 +1,109 @@
+// qcs_walker.cu -- per-walker preparation for the overlap kernels.
+//
+// A walker Phi (n x ne, non-orthonormal) is factored Phi = U[:, :ne] R by
+// complex Householder reflections; U (n x n unitary) completes the occupied
+// orbitals.  With V = U^dagger the walker is the Slater determinant
+// a~_1^dagger ... a~_ne^dagger |0> of SI "Matrix Definitions" item 3 times det R.
+//
+// Output per walker:
+//   Ut[j][k] = U[k][j] (row j = orbital j), rows j < ne scaled by 1/sqrt2 -- the
+//              (1, -i)/sqrt2 row of the W^* block of Eq. (b_mat) selected for an
+//              occupied mode contributes conj(V_jk)/sqrt2 = U_kj/sqrt2;
+//   pref     = 2 det(R) i^{ne/2} / 2^{n - ne/2}  (prefactor of the estimator;
+//              the 2 undoes the 1/sqrt2 of the prepared state (|0>+|Psi_T>)/sqrt2).
+#include "qcs_internal.h"
+
+namespace {
+
+__global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restrict__ Phi, cd *__restrict__ Ut,
+                                   cd *__restrict__ pref, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const size_t per_warp = (size_t)n * ne + (size_t)n * n + n;
+    cd *A = reinterpret_cast<cd *>(smem_raw) + warp * per_warp;
+    cd *U = A + n * ne;
+    cd *v = U + n * n;
+    for (int64_t w = (int64_t)blockIdx.x * wpb + warp; w < W; w += (int64_t)gridDim.x * wpb) {
+        const cd *Pw = Phi + w * n * ne;
+        bool bad = false;
+        for (int e = lane; e < n * ne; e += 32) {
+            cd x = Pw[e];
+            bad |= !cfinite(x);
+            A[e] = x;
+        }
+        for (int e = lane; e < n * n; e += 32) U[e] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+        bad = __any_sync(QCS_FULL, bad);
+        __syncwarp();
+        cd detR = cmk(1.0, 0.0);
+        for (int k = 0; k < ne; ++k) {
+            cd x = (lane >= k && lane < n) ? A[lane * ne + k] : cmk(0.0, 0.0);
+            double xn2 = warp_sum(fma(x.x, x.x, x.y * x.y));
+            if (!(xn2 > 0.0)) {  // zero column: R_kk = 0, the determinant vanishes
+                detR = cmk(0.0, 0.0);
+                continue;
+            }
+            double xn = sqrt(xn2);
+            cd x0 = A[k * ne + k];
+            double ax0 = hypot(x0.x, x0.y);
+            cd ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
+            cd alpha = cmk(-ph.x * xn, -ph.y * xn);
+            cd vi = (lane > k && lane < n) ? x : (lane == k ? csub(x0, alpha) : cmk(0.0, 0.0));
+            double vn2 = warp_sum(fma(vi.x, vi.x, vi.y * vi.y));
+            double tau = 2.0 / vn2;
+            if (lane < n) v[lane] = vi;
+            __syncwarp();
+            // A <- (I - tau v v^H) A on columns k..ne-1
+            for (int j = k; j < ne; ++j) {
+                cd a = lane < n ? A[lane * ne + j] : cmk(0.0, 0.0);
+                cd s = warp_csum(cmul(cconj(vi), a));
+                s = cscale(s, tau);
+                if (lane < n) A[lane * ne + j] = csub(a, cmul(vi, s));
+            }
+            // U <- U (I - tau v v^H): row r = lane
+            if (lane < n) {
+                cd sr = cmk(0.0, 0.0);
+                for (int i = k; i < n; ++i) cfma(sr, U[lane * n + i], v[i]);
+                sr = cscale(sr, tau);
+                for (int i = k; i < n; ++i) cfms(U[lane * n + i], sr, cconj(v[i]));
+            }
+            __syncwarp();
+            detR = cmul(detR, alpha);
+        }
+        const double rs2 = 0.70710678118654752440;
+        cd *Uw = Ut + w * n * n;
+        for (int e = lane; e < n * n; e += 32) {
+            int j = e / n, kk = e - j * n;
+            cd u = U[kk * n + j];
+            Uw[e] = (j < ne) ? cscale(u, rs2) : u;
+        }
+        if (lane == 0) {
+            cd ip;  // i^{ne/2}
+            switch ((ne / 2) & 3) {
+                case 0: ip = cmk(1, 0); break;
+                case 1: ip = cmk(0, 1); break;
+                case 2: ip = cmk(-1, 0); break;
+                default: ip = cmk(0, -1); break;
+            }
+            double sc = 2.0 * ldexp(1.0, -(n - ne / 2));
+            pref[w] = cscale(cmul(detR, ip), sc);
+            if (bad || !cfinite(detR)) raise_status(status, QCS_ERR_NONFINITE);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
+                                  cudaStream_t st) {
+    if (W == 0) return QCS_OK;
+    const int wpb = 4;
+    size_t smem = (size_t)wpb * ((size_t)n * ne + (size_t)n * n + n) * sizeof(cd);
+    if (qcs_set_smem(ctx, (const void *)walker_prep_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    int64_t blocks = (W + wpb - 1) / wpb;
+    if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
+    walker_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, ne, W, walkers, Ut, pref, ctx->d_status);
+    return qcs_check_launch(ctx, "walker_prep_kernel");
+}

@@ -1,0 +1,249 @@
+"""Python binding of ``libqcs`` (the C ABI in ``include/qcs.h``).
+
+Argument marshalling only: every step of the overlap path runs in the CUDA
+kernels of ``libqcs.so``.  Tensors are PyTorch CUDA tensors (complex128 for
+walkers, overlaps and gradients; float64 for Q; uint8 for b); the current
+PyTorch stream is passed to the library.  There is no CPU fallback: if the
+library cannot be loaded, or no CUDA device is present, these functions
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+_lib = None
+_lock = threading.Lock()
+
+QCS_OK = 0
+QCS_FP64 = 0
+QCS_TF32X3 = 1
+QCS_FLAG_ALL_NODES = 1
+STATUS_BITS = {1: "ARG", 2: "CUDA", 4: "NONFINITE", 8: "SINGULAR", 16: "TIMEOUT", 32: "UNSUPPORTED"}
+
+EXPORTED = [
+    "qcs_create", "qcs_destroy", "qcs_last_error", "qcs_sync_status", "qcs_workspace_bytes",
+    "qcs_build_snapshots", "qcs_snapshots_free", "qcs_snapshots_parity", "qcs_snapshots_count",
+    "qcs_snapshots_modes", "qcs_overlap", "qcs_overlap_grad", "qcs_force_bias", "qcs_overlap_flops_per_pair",
+    "qcs_profile_enable", "qcs_profile_read",
+]
+
+
+class QCSError(RuntimeError):
+    def __init__(self, code, msg):
+        names = [v for k, v in STATUS_BITS.items() if code & k]
+        super().__init__(f"libqcs error {code} ({'|'.join(names) or 'OK'}): {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("nodes", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("reserved", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqcs.so (building it in-tree with nvcc if missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and _build.stale():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libqcs.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, i32, i64, u32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint, ctypes.c_double
+        lib.qcs_create.argtypes = [ctypes.POINTER(P), i32]
+        lib.qcs_destroy.argtypes = [P]
+        lib.qcs_last_error.argtypes = [P]
+        lib.qcs_last_error.restype = ctypes.c_char_p
+        lib.qcs_sync_status.argtypes = [P, P]
+        lib.qcs_workspace_bytes.argtypes = [P]
+        lib.qcs_workspace_bytes.restype = ctypes.c_size_t
+        lib.qcs_build_snapshots.argtypes = [P, i32, i64, P, P, ctypes.POINTER(P), P]
+        lib.qcs_snapshots_free.argtypes = [P]
+        lib.qcs_snapshots_parity.argtypes = [P, P, P]
+        lib.qcs_snapshots_count.argtypes = [P]
+        lib.qcs_snapshots_count.restype = i64
+        lib.qcs_snapshots_modes.argtypes = [P]
+        lib.qcs_overlap.argtypes = [P, P, i32, i64, P, P, P, ctypes.POINTER(_Opts), P]
+        lib.qcs_overlap_grad.argtypes = [P, P, i32, i64, P, P, P, ctypes.POINTER(_Opts), P]
+        lib.qcs_force_bias.argtypes = [P, i32, i32, i64, i32, P, P, P, P, f64, P, P]
+        lib.qcs_overlap_flops_per_pair.argtypes = [i32, i32, i32, u32]
+        lib.qcs_overlap_flops_per_pair.restype = f64
+        lib.qcs_profile_enable.argtypes = [P, i32]
+        lib.qcs_profile_read.argtypes = [P, ctypes.POINTER(f64), ctypes.POINTER(i64)]
+        _lib = lib
+        return lib
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need_cuda(t, name, dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Context:
+    """A libqcs context on one CUDA device (owns the workspace and status word)."""
+
+    def __init__(self, device: int | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqcs needs a CUDA device; none is visible")
+        self.lib = load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.qcs_create(ctypes.byref(h), self.device)
+        if rc != QCS_OK:
+            raise QCSError(rc, "qcs_create failed")
+        self.h = h
+
+    def check(self, rc):
+        if rc != QCS_OK:
+            raise QCSError(rc, self.lib.qcs_last_error(self.h).decode())
+
+    def sync_status(self) -> int:
+        return int(self.lib.qcs_sync_status(self.h, _stream()))
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.qcs_workspace_bytes(self.h))
+
+    def profile(self, enable: bool = True):
+        self.check(self.lib.qcs_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(summed milliseconds, launches) of the dominant kernels since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self.check(self.lib.qcs_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Snapshots:
+    """Device-resident snapshot set built by qcs_build_snapshots."""
+
+    def __init__(self, ctx: Context, Q: torch.Tensor, b: torch.Tensor):
+        _need_cuda(Q, "Q", torch.float64)
+        _need_cuda(b, "b", torch.uint8)
+        P, N, N2 = Q.shape
+        n = N // 2
+        if N != N2 or N != 2 * n or tuple(b.shape) != (P, n):
+            raise ValueError("Q must be (P, 2n, 2n) and b (P, n)")
+        self.ctx, self.n, self.P = ctx, n, P
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.qcs_build_snapshots(ctx.h, n, P, _ptr(Q), _ptr(b), ctypes.byref(h), _stream()))
+        self.h = h
+
+    def parity(self) -> torch.Tensor:
+        out = torch.empty(self.P, dtype=torch.int8, device=f"cuda:{self.ctx.device}")
+        self.ctx.check(self.ctx.lib.qcs_snapshots_parity(self.h, _ptr(out), _stream()))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.qcs_snapshots_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _opts(nodes=0, flags=0, precision=QCS_FP64):
+    return _Opts(int(precision), int(nodes), int(flags), 0)
+
+
+def overlap(ctx: Context, snaps: Snapshots, walkers: torch.Tensor, per_pair: bool = False, nodes: int = 0,
+            flags: int = 0, precision: int = QCS_FP64):
+    """<Psi_T|phi_w> for walkers (W, n, ne) complex128; returns (overlap[W], per_pair[W, P] or None)."""
+    _need_cuda(walkers, "walkers", torch.complex128)
+    W, n, ne = walkers.shape
+    if n != snaps.n:
+        raise ValueError("walker size does not match the snapshot set")
+    dev = walkers.device
+    out = torch.empty(W, dtype=torch.complex128, device=dev)
+    pp = torch.empty((W, snaps.P), dtype=torch.complex128, device=dev) if per_pair else None
+    o = _opts(nodes, flags, precision)
+    ctx.check(ctx.lib.qcs_overlap(ctx.h, snaps.h, ne, W, _ptr(walkers), _ptr(out), _ptr(pp), ctypes.byref(o),
+                                  _stream()))
+    return out, pp
+
+
+def overlap_grad(ctx: Context, snaps: Snapshots, walkers: torch.Tensor, nodes: int = 0, flags: int = 0):
+    """(overlap[W], grad[W, n, ne]) with grad = d overlap / d walkers (holomorphic)."""
+    _need_cuda(walkers, "walkers", torch.complex128)
+    W, n, ne = walkers.shape
+    dev = walkers.device
+    out = torch.empty(W, dtype=torch.complex128, device=dev)
+    g = torch.empty((W, n, ne), dtype=torch.complex128, device=dev)
+    o = _opts(nodes, flags)
+    ctx.check(ctx.lib.qcs_overlap_grad(ctx.h, snaps.h, ne, W, _ptr(walkers), _ptr(out), _ptr(g), ctypes.byref(o),
+                                       _stream()))
+    return out, g
+
+
+def force_bias(ctx: Context, L: torch.Tensor, walkers: torch.Tensor, ov: torch.Tensor, grad: torch.Tensor,
+               sqrt_dt: float = 0.0):
+    """xbar[W, nchol] = -sqrt_dt * i tr(L_gamma Phi g^T / O)  (sqrt_dt = 0: <v_gamma>)."""
+    for t, nm in ((L, "L"), (walkers, "walkers"), (ov, "overlap"), (grad, "grad")):
+        _need_cuda(t, nm, torch.complex128)
+    W, n, ne = walkers.shape
+    nchol = L.shape[0]
+    xb = torch.empty((W, nchol), dtype=torch.complex128, device=walkers.device)
+    ctx.check(ctx.lib.qcs_force_bias(ctx.h, n, ne, W, nchol, _ptr(L), _ptr(walkers), _ptr(ov), _ptr(grad),
+                                     float(sqrt_dt), _ptr(xb), _stream()))
+    return xb
+
+
+def flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
+    return float(load().qcs_overlap_flops_per_pair(n, ne, nodes, flags))
+
+
+class OverlapFn(torch.autograd.Function):
+    """Differentiable shadow overlap.  Forward: qcs_overlap_grad (the gradient is
+    computed alongside and kept); backward: PyTorch's convention for a
+    holomorphic function, grad_walkers = conj(dO/dPhi) * grad_output."""
+
+    @staticmethod
+    def forward(ctx_, walkers, qctx, snaps):
+        ov, g = overlap_grad(qctx, snaps, walkers.detach().contiguous())
+        ctx_.save_for_backward(g)
+        return ov
+
+    @staticmethod
+    def backward(ctx_, grad_out):
+        (g,) = ctx_.saved_tensors
+        return g.conj() * grad_out[:, None, None], None, None

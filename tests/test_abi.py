@@ -1,0 +1,34 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/qcs.h declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+from paper_2506_22408_gb300 import _build, qcs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qcs.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qcs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 14
+    missing = [nm for nm in names if not hasattr(lib, nm)]
+    assert not missing, missing
+    assert set(qcs.EXPORTED) == set(names)
+
+
+def test_flop_accounting_host_only():
+    lib = qcs.load()
+    f16 = lib.qcs_overlap_flops_per_pair(16, 8, 0, 0)
+    f16_all = lib.qcs_overlap_flops_per_pair(16, 8, 0, 1)
+    assert 1.5e5 < f16 < 2.5e5
+    assert f16_all > f16
+    assert lib.qcs_overlap_flops_per_pair(16, 7, 0, 0) == 0.0  # odd ne rejected
