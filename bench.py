@@ -154,6 +154,65 @@ def run_e2e(args, data, dev, step, barrier, ws, wl):
             "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
 
+def run_grad(args, ctx, dev, barrier, ws):
+    """Differentiation workload: n = 16, ne = 8, 512 walkers x 10000 snapshots; one
+    step = snapshot build + overlaps and holomorphic gradients (qcs_overlap_grad) +
+    force bias over 64 Cholesky vectors (qcs_force_bias)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    wl = synth.DIFFERENTIATION
+    data = wl.generate(seed=0)
+    Q = torch.from_numpy(data["Q"]).to(dev)
+    b = torch.from_numpy(data["b"]).to(dev)
+    Phi = torch.from_numpy(data["Phi"]).to(dev)
+    L = torch.from_numpy(data["L"].astype(np.complex128)).to(dev)
+
+    def step():
+        snaps = qcs.Snapshots(ctx, Q, b)
+        ov, g = qcs.overlap_grad(ctx, snaps, Phi)
+        xb = qcs.force_bias(ctx, L, Phi, ov, g, sqrt_dt=0.1)
+        return snaps, xb
+
+    snaps, _ = step()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    npar = int((snaps.parity() == 1).sum().item())
+    del snaps
+    steps = max(2, min(args.steps, 3))
+    ctx.profile(True)
+    ctx.profile_read()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        snaps, xb = step()
+    e1.record(stream)
+    barrier()
+    ctx.profile(False)
+    kms, kl = ctx.profile_read()
+    t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    fpp = qcs.grad_flops_per_pair(wl.n, wl.ne)
+    avg = kms / max(kl, 1)
+    ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
+    src = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc", "qcs_grad.cu")
+    return {"metric": "walker x snapshot overlap+grad pairs/s (with force bias)", "value": ws * wl.W * wl.P * steps / t,
+            "unit": "pairs/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "parity_plus_snapshots": npar,
+                       "nchol": wl.nchol},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(src, "grad_pair_kernel"),
+                         "kernel": "grad_pair_kernel", "kernel_ms": avg, "flops_per_launch": fpp * npar * wl.W},
+            "gpu_launches_per_step": 6}
+
+
 def cpu_baseline(wl, data, target_s=10.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle.oracle as orc
@@ -217,6 +276,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-grad", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--walkers", type=int, default=0, help="override the walker count (profiling cases)")
     ap.add_argument("--snapshots", type=int, default=0, help="override the snapshot count (profiling cases)")
     args = ap.parse_args()
@@ -299,6 +359,10 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, data, dev, step, barrier, ws, wl)
+    grad = None
+    if not args.no_grad:
+        grad = run_grad(args, ctx, dev, barrier, ws)
+
     # ---------------- roofline of the dominant kernel
     fpp = qcs.flops_per_pair(wl.n, wl.ne)
     flops_launch = fpp * npar * wl.W
@@ -323,6 +387,7 @@ def main():
             "e2e": e2e,
             "roofline": roof,
             "clocks": clk.summary(),
+            "grad": grad,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

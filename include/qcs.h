@@ -197,6 +197,11 @@ qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
  * evaluated nodes.  Used by the benchmark's roofline. */
 double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
 
+/* Same for one non-trivial pair of qcs_overlap_grad: the forward pass plus,
+ * per evaluated node, the backward assembly of A(z_k)^{-1} from the
+ * elimination's Gauss vectors, and the per-pair cotangent products. */
+double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -287,7 +287,7 @@ extern "C" int qcs_snapshots_modes(const qcs_snapshots *s) { return s ? s->n : -
 
 namespace {
 
-const int kChunk = 8;
+const int kChunk = 4;  // snapshots per warp in an overlap tile
 
 struct OverlapWork {
     cd *Ut, *pref, *partial;
@@ -309,11 +309,12 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "precision mode not built");
     if (qcs_make_node_plan(n, ne, o.nodes, o.flags, plan) != QCS_OK)
         return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
-    wk->nchunks = (int)((s->P + kChunk - 1) / kChunk);
+    const int span = kChunk * qcs_pair_warps_per_block();
+    wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
     size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
-    size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nchunks);
+    size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nchunks * qcs_pair_warps_per_block());
     void *base = nullptr;
     qcs_status ws = qcs_workspace(ctx, b_ut + b_pref + b_part, &base);
     if (ws != QCS_OK) return ws;
@@ -355,25 +356,106 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
     L.plan = plan;
     r = qcs_launch_pairs(ctx, L, st);
     if (r != QCS_OK) return r;
-    return qcs_launch_reduce(ctx, W, s->P, wk.nchunks, wk.partial, wk.pref, (cd *)d_overlap, st);
+    return qcs_launch_reduce(ctx, W, s->P, wk.nchunks * qcs_pair_warps_per_block(), wk.partial, wk.pref,
+                             (cd *)d_overlap, st);
 }
 
 extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W,
                                        const double *d_walkers, double *d_overlap, double *d_grad,
                                        const qcs_opts *opts, void *stream) {
-    (void)s; (void)ne; (void)W; (void)d_walkers; (void)d_overlap; (void)d_grad; (void)opts; (void)stream;
-    return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "qcs_overlap_grad: not built yet");
+    if (!ctx) return QCS_ERR_ARG;
+    if (W > 0 && (!d_overlap || !d_grad)) return qcs_fail(ctx, QCS_ERR_ARG, "null overlap or gradient output");
+    if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = s->n;
+    qcs_status c = check_sizes(ctx, n, ne);
+    if (c != QCS_OK) return c;
+    if (W < 0) return qcs_fail(ctx, QCS_ERR_ARG, "W < 0");
+    if (W == 0) return QCS_OK;
+    if (!d_walkers) return qcs_fail(ctx, QCS_ERR_ARG, "null walkers");
+    if (s->device != ctx->device) return qcs_fail(ctx, QCS_ERR_ARG, "snapshot set lives on another device");
+    qcs_opts o = {QCS_FP64, 0, 0u, 0};
+    if (opts) o = *opts;
+    if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "the gradient is FP64 only");
+    qcs_node_plan plan;
+    if (qcs_make_node_plan(n, ne, o.nodes, o.flags, &plan) != QCS_OK)
+        return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
+    // tiles: about 32 per resident warp, at least 8 snapshots per tile
+    int64_t target = (int64_t)ctx->num_sms * 4 * 32;
+    int64_t nch = (target + W - 1) / W;
+    int64_t maxch = (s->P + 7) / 8;
+    if (nch > maxch) nch = maxch;
+    if (nch < 1) nch = 1;
+    int chunk = (int)((s->P + nch - 1) / nch);
+    if (chunk < 1) chunk = 1;
+    int nchunks = (int)((s->P + chunk - 1) / chunk);
+    if (nchunks < 1) nchunks = 1;
+    size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
+    size_t b_pref = align16(sizeof(cd) * (size_t)W);
+    size_t b_u = b_ut;
+    size_t b_r = align16(sizeof(cd) * (size_t)W * ne * ne);
+    size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * (1 + (size_t)n * n));
+    void *base = nullptr;
+    qcs_status ws = qcs_workspace(ctx, b_ut + b_pref + b_u + b_r + b_part, &base);
+    if (ws != QCS_OK) return ws;
+    char *pb = (char *)base;
+    cd *Ut = (cd *)pb;
+    cd *pref = (cd *)(pb + b_ut);
+    cd *U = (cd *)(pb + b_ut + b_pref);
+    cd *R = (cd *)(pb + b_ut + b_pref + b_u);
+    cd *part = (cd *)(pb + b_ut + b_pref + b_u + b_r);
+    qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st, U, R);
+    if (r != QCS_OK) return r;
+    qcs_grad_launch L;
+    L.n = n;
+    L.ne = ne;
+    L.W = W;
+    L.P = s->P;
+    L.chunk = chunk;
+    L.nchunks = nchunks;
+    L.Ut = Ut;
+    L.U = U;
+    L.R = R;
+    L.pref = pref;
+    L.s = s;
+    L.partial = part;
+    L.overlap = (cd *)d_overlap;
+    L.grad = (cd *)d_grad;
+    L.plan = plan;
+    return qcs_launch_grad(ctx, L, st);
 }
 
 extern "C" qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const double *d_L,
                                      const double *d_walkers, const double *d_overlap, const double *d_grad,
                                      double sqrt_dt, double *d_xbar, void *stream) {
-    (void)n; (void)ne; (void)W; (void)nchol; (void)d_L; (void)d_walkers; (void)d_overlap; (void)d_grad;
-    (void)sqrt_dt; (void)d_xbar; (void)stream;
-    return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "qcs_force_bias: not built yet");
+    if (!ctx) return QCS_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    qcs_status c = check_sizes(ctx, n, ne);
+    if (c != QCS_OK) return c;
+    if (W < 0 || nchol < 0) return qcs_fail(ctx, QCS_ERR_ARG, "W and nchol must be >= 0");
+    if (W == 0 || nchol == 0) return QCS_OK;
+    if (!d_L || !d_walkers || !d_overlap || !d_grad || !d_xbar) return qcs_fail(ctx, QCS_ERR_ARG, "null pointer");
+    return qcs_launch_force_bias(ctx, n, ne, W, nchol, (const cd *)d_L, (const cd *)d_walkers,
+                                 (const cd *)d_overlap, (const cd *)d_grad, sqrt_dt, (cd *)d_xbar,
+                                 (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------ accounting
+
+extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
+    qcs_node_plan plan;
+    if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
+    if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
+    const int d = n - ne, m = 2 * n - ne, T = tri_count(m);
+    double f = qcs_overlap_flops_per_pair(n, ne, nodes, flags);  // forward pass
+    double node = 0.0;                                              // backward inverse per node
+    for (int r = m; r > 2; r -= 2) node += 16.0 * (double)(r - 2) * (r - 2) + 8.0 * (r - 2) + 12.0 * (r - 2);
+    f += (node + 8.0 * T) * plan.nev;                               // inverse + Y accumulation
+    f += (double)m * 2 * n * (8.0 * ne + 4.0 * (m - ne));           // G_X = Y (X J)
+    f += (double)n * n * 2 * n * 8.0 + 2.0 * d * 2 * n;             // Gamma1 / Gamma2
+    return f;
+}
 
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
     qcs_node_plan plan;

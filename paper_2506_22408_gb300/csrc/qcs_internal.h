@@ -58,7 +58,26 @@ struct qcs_node_plan {
 qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node_plan *plan);
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st);
+                                  cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr);
+
+struct qcs_grad_launch {
+    int n, ne;
+    int64_t W, P;
+    int chunk, nchunks;
+    const cd *Ut;
+    const cd *U;
+    const cd *R;
+    const cd *pref;
+    const qcs_snapshots *s;
+    cd *partial;     // W x nchunks x (1 + n*n)
+    cd *overlap;     // W
+    cd *grad;        // W x n x ne
+    qcs_node_plan plan;
+};
+
+qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t st);
+qcs_status qcs_launch_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const cd *L, const cd *walkers,
+                                 const cd *overlap, const cd *grad, double sqrt_dt, cd *xbar, cudaStream_t st);
 
 struct qcs_pair_launch {
     int n, ne;
@@ -67,11 +86,12 @@ struct qcs_pair_launch {
     const cd *Ut;
     const cd *pref;
     const qcs_snapshots *s;
-    cd *partial;     // W x nchunks
+    cd *partial;     // W x nchunks x warps-per-block
     cd *per_pair;    // W x P or null
     qcs_node_plan plan;
 };
 
 qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t st);
-qcs_status qcs_launch_reduce(qcs_ctx *ctx, int64_t W, int64_t P, int nchunks, const cd *partial, const cd *pref,
+int qcs_pair_warps_per_block();  // partial sums per overlap tile
+qcs_status qcs_launch_reduce(qcs_ctx *ctx, int64_t W, int64_t P, int nparts, const cd *partial, const cd *pref,
                              cd *overlap, cudaStream_t st);

@@ -29,6 +29,7 @@
 // writes one partial sum per tile, reduced in a fixed order afterwards, so the
 // result does not depend on scheduling.
 #include "qcs_internal.h"
+#include "qcs_pair.cuh"
 
 namespace {
 
@@ -39,6 +40,7 @@ struct PairArgs {
     int64_t W, P;
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
+    int ut_bytes;     // shared bytes of the walker rows Ut (per block)
     int off_R, off_B, off_U, off_V, off_pf, off_inv, off_best, off_int, off_act;  // byte offsets in a warp region
     const cd *Ut;
     const cd *pref;
@@ -51,66 +53,6 @@ struct PairArgs {
     cd wnode[QCS_MAX_NODES];
     cd gamma[QCS_MAX_NODES];
 };
-
-__device__ __forceinline__ void pair_of(const uint16_t *tab, int t, int &a, int &b) {
-    unsigned v = tab[t];
-    a = v & 0xff;
-    b = v >> 8;
-}
-
-// B^(s) (packed upper, m x m) from T (n x 2n).
-__device__ void build_B(const PairArgs &A, const cd *__restrict__ Ts, cd *__restrict__ Bs,
-                        const uint16_t *__restrict__ tab, int lane) {
-    const int n = A.n, ne = A.ne, d = A.d, n2 = 2 * n;
-    // occupied x occupied: complex x complex
-    const int c1 = tri_count(ne);
-    for (int e = lane; e < c1; e += 32) {
-        int a, b;
-        pair_of(tab, e, a, b);
-        const cd *Ta = Ts + a * n2, *Tb = Ts + b * n2;
-        cd acc = cmk(0.0, 0.0);
-        for (int k = 0; k < n; ++k) {
-            cfma(acc, Ta[2 * k], Tb[2 * k + 1]);
-            cfms(acc, Ta[2 * k + 1], Tb[2 * k]);
-        }
-        Bs[tri_index(a, b)] = acc;
-    }
-    // occupied x empty: complex x real.  Empty row r of mode j = ne + r/2 is
-    // Re T_j (r even) or -Im T_j (r odd); the sign is applied once at the end.
-    const int twod = 2 * d;
-    const int c2 = ne * twod;
-    for (int e = lane; e < c2; e += 32) {
-        int a = e / twod, r = e - a * twod;
-        int j = ne + (r >> 1);
-        bool odd = r & 1;
-        const cd *Ta = Ts + a * n2, *Tj = Ts + j * n2;
-        cd acc = cmk(0.0, 0.0);
-        for (int k = 0; k < n; ++k) {
-            cd t0 = Tj[2 * k], t1 = Tj[2 * k + 1];
-            double x0 = odd ? t0.y : t0.x, x1 = odd ? t1.y : t1.x;
-            crfma(acc, Ta[2 * k], x1);
-            crfma(acc, Ta[2 * k + 1], -x0);
-        }
-        Bs[tri_index(a, ne + r)] = odd ? cneg(acc) : acc;
-    }
-    // empty x empty: real x real
-    const int c3 = tri_count(twod);
-    for (int e = lane; e < c3; e += 32) {
-        int a, b;
-        pair_of(tab, e, a, b);
-        const cd *Ta = Ts + (ne + (a >> 1)) * n2, *Tb = Ts + (ne + (b >> 1)) * n2;
-        bool oa = a & 1, ob = b & 1;
-        double acc = 0.0;
-        for (int k = 0; k < n; ++k) {
-            cd a0 = Ta[2 * k], a1 = Ta[2 * k + 1], b0 = Tb[2 * k], b1 = Tb[2 * k + 1];
-            double xa0 = oa ? a0.y : a0.x, xa1 = oa ? a1.y : a1.x;
-            double xb0 = ob ? b0.y : b0.x, xb1 = ob ? b1.y : b1.x;
-            acc = fma(xa0, xb1, acc);
-            acc = fma(-xa1, xb0, acc);
-        }
-        Bs[tri_index(ne + a, ne + b)] = cmk((oa != ob) ? -acc : acc, 0.0);
-    }
-}
 
 // Pfaffians of nb node matrices B + wnode[k0 + v] D held in Ns (packed upper).
 // On return pf[v] holds pf(B + conj(z_{k0+v}) D).
@@ -207,21 +149,12 @@ __global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant
     const int wpb = blockDim.x >> 5;
     const int n = A.n, n2 = 2 * n;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
-    const int T = tri_count(A.m);
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        // invert t = b(b-1)/2 + a
-        int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-        while (b * (b - 1) / 2 > t) --b;
-        while ((b + 1) * b / 2 <= t) ++b;
-        int a = t - b * (b - 1) / 2;
-        tab[t] = (uint16_t)((b << 8) | a);
-    }
-    __syncthreads();
-    unsigned char *wbase = smem_raw + A.tab_bytes + (size_t)warp * A.warp_bytes;
-    cd *Uts = reinterpret_cast<cd *>(wbase);
-    cd *Rg = reinterpret_cast<cd *>(wbase + A.off_R);
+    build_pair_table(tab, tri_count(A.m));
+    cd *Uts = reinterpret_cast<cd *>(smem_raw + A.tab_bytes);  // shared by the block's warps
+    unsigned char *wbase = smem_raw + A.tab_bytes + A.ut_bytes + (size_t)warp * A.warp_bytes;
+    cd *Rg = reinterpret_cast<cd *>(wbase);
     cd *Qs = Rg;
-    cd *Ts = Rg + (size_t)n2 * n;
+    cd *Ts = Rg + (size_t)n2 * ld_qt(n);
     cd *Ns = Rg;
     cd *Bs = reinterpret_cast<cd *>(wbase + A.off_B);
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
@@ -235,33 +168,30 @@ __global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant
 
     const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
     const int64_t ntiles = A.W * A.nchunks;
-    const int64_t gw = (int64_t)blockIdx.x * wpb + warp, GW = (int64_t)gridDim.x * wpb;
-    for (int64_t tile = gw; tile < ntiles; tile += GW) {
+    const int span = A.chunk * wpb;  // snapshots per tile; warp w takes every wpb-th
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t w = tile / A.nchunks;
         const int ch = (int)(tile - w * A.nchunks);
-        const int64_t p0 = (int64_t)ch * A.chunk;
-        const int64_t p1 = p0 + A.chunk < L ? p0 + A.chunk : L;
-        cd acc = cmk(0.0, 0.0);
+        const int64_t p0 = (int64_t)ch * span;
+        const int64_t p1 = p0 + span < L ? p0 + span : L;
+        __syncthreads();  // previous tile's readers of Uts are done
         if (p0 < L) {
             const cd *Utw = A.Ut + w * n * n;
-            for (int e = lane; e < n * n; e += 32) Uts[e] = Utw[e];
+            const int lu = ld_ut(n);
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) Uts[(e / n) * lu + (e % n)] = Utw[e];
+        }
+        __syncthreads();
+        cd acc = cmk(0.0, 0.0);
+        if (p0 < L) {
             const cd prefw = A.pref[w];
-            for (int64_t pq = p0; pq < p1; ++pq) {
+            for (int64_t pq = p0 + warp; pq < p1; pq += wpb) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
-                const cd *Qq = A.Qt + q * n2 * n;
                 __syncwarp();
-                for (int e = lane; e < n2 * n; e += 32) Qs[e] = Qq[e];
+                load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
                 __syncwarp();
-                // T[j][c] = sum_k Ut[j][k] Qt[c][k]
-                for (int e = lane; e < n * n2; e += 32) {
-                    int j = e / n2, c = e - j * n2;
-                    const cd *ur = Uts + j * n, *qr = Qs + c * n;
-                    cd s = cmk(0.0, 0.0);
-                    for (int k = 0; k < n; ++k) cfma(s, ur[k], qr[k]);
-                    Ts[e] = s;
-                }
+                build_T(n, Uts, Qs, Ts, lane);
                 __syncwarp();
-                build_B(A, Ts, Bs, tab, lane);
+                build_B(A.n, A.ne, Ts, Bs, tab, lane);
                 __syncwarp();
                 cd S = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
@@ -278,21 +208,56 @@ __global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant
                 }
             }
         }
-        if (lane == 0) A.partial[tile] = acc;
+        if (lane == 0) A.partial[tile * wpb + warp] = acc;
     }
 }
 
-__global__ void reduce_kernel(int64_t W, int64_t P, int nchunks, const cd *__restrict__ partial,
+// One warp per walker: lanes sum strided partials, then a fixed-order tree.
+__global__ void reduce_kernel(int64_t W, int64_t P, int nparts, const cd *__restrict__ partial,
                               const cd *__restrict__ pref, cd *__restrict__ overlap) {
-    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (w >= W) return;
     cd s = cmk(0.0, 0.0);
-    for (int c = 0; c < nchunks; ++c) s = cadd(s, partial[w * nchunks + c]);
+    for (int c = lane; c < nparts; c += 32) s = cadd(s, partial[w * nparts + c]);
+    s = warp_csum(s);
+    if (lane != 0) return;
     double inv = P > 0 ? 1.0 / (double)P : 0.0;
     overlap[w] = cscale(cmul(pref[w], s), inv);
 }
 
 }  // namespace
+
+namespace {
+
+// Per-warp shared layout for nb node matrices; returns bytes per warp.
+size_t pair_warp_layout(PairArgs &A, int NB) {
+    const int n = A.n, m = A.m, T = tri_count(m);
+    size_t R = (size_t)2 * n * ld_qt(n) + (size_t)n * ld_t(n);  // Qt + T
+    if ((size_t)NB * T > R) R = (size_t)NB * T;
+    size_t o = align16(R * sizeof(cd));
+    A.off_B = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_U = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_V = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_pf = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(cd));
+    A.off_inv = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(cd));
+    A.off_best = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(unsigned long long));
+    A.off_int = (int)o;
+    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
+    A.off_act = (int)o;
+    o = align16(o + (size_t)2 * NB * m);
+    return o;
+}
+
+}  // namespace
+
+int qcs_pair_warps_per_block() { return 4; }
 
 qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t st) {
     PairArgs A;
@@ -307,33 +272,27 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
     A.nchunks = L.nchunks;
     A.W = L.W;
     A.P = L.P;
-    A.NB = L.plan.nev < kMaxNB ? L.plan.nev : kMaxNB;
-    if (A.NB > 5) A.NB = (L.plan.nev + 1) / 2;  // rounds of at most 5 when more nodes are evaluated
-    if (A.NB > kMaxNB) A.NB = kMaxNB;
     const int n = A.n, m = A.m, T = tri_count(m);
-    size_t o = align16((size_t)n * n * sizeof(cd));
-    A.off_R = (int)o;
-    size_t R = (size_t)4 * n * n;  // Qt (2n x n) + T (n x 2n)
-    if ((size_t)A.NB * T > R) R = (size_t)A.NB * T;
-    o = align16(o + R * sizeof(cd));
-    A.off_B = (int)o;
-    o = align16(o + (size_t)T * sizeof(cd));
-    A.off_U = (int)o;
-    o = align16(o + (size_t)A.NB * m * sizeof(cd));
-    A.off_V = (int)o;
-    o = align16(o + (size_t)A.NB * m * sizeof(cd));
-    A.off_pf = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_inv = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_best = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(unsigned long long));
-    A.off_int = (int)o;
-    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
-    A.off_act = (int)o;
-    o = align16(o + (size_t)2 * A.NB * m);
-    A.warp_bytes = (int)o;
+    const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
+    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * sizeof(cd));
+    // Node matrices per round: the largest count (at most kMaxNB, balanced rounds)
+    // for which two blocks of wpb warps fit on an SM, else one block.
+    const size_t sm_budget = ctx->smem_optin;  // per block
+    int NB = 1;
+    for (int rounds = 1; rounds <= A.nev; ++rounds) {
+        int nb = (A.nev + rounds - 1) / rounds;
+        if (nb > kMaxNB) continue;
+        size_t wb = pair_warp_layout(A, nb);
+        size_t blk = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * wb + 1024;
+        if (2 * blk <= sm_budget + 1024) {
+            NB = nb;
+            break;
+        }
+        if (rounds == A.nev) NB = 1;
+    }
+    A.NB = NB;
+    A.warp_bytes = (int)pair_warp_layout(A, NB);
     A.Ut = L.Ut;
     A.pref = L.pref;
     A.Qt = L.s->Qt;
@@ -346,9 +305,7 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
         A.wnode[k] = L.plan.wnode[k];
         A.gamma[k] = L.plan.gamma[k];
     }
-    int wpb = 4;
-    while (wpb > 1 && (size_t)A.tab_bytes + (size_t)wpb * A.warp_bytes > ctx->smem_optin) --wpb;
-    size_t smem = (size_t)A.tab_bytes + (size_t)wpb * A.warp_bytes;
+    size_t smem = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * A.warp_bytes;
     if (smem > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "pair kernel: shared memory too large");
     if (qcs_set_smem(ctx, (const void *)pair_overlap_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
     int per_sm = 0;
@@ -357,8 +314,7 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
         per_sm = 1;
     int64_t ntiles = L.W * L.nchunks;
     int64_t blocks = (int64_t)ctx->num_sms * per_sm;
-    int64_t need = (ntiles + wpb - 1) / wpb;
-    if (blocks > need) blocks = need;
+    if (blocks > ntiles) blocks = ntiles;
     if (blocks < 1) blocks = 1;
     qcs_prof_begin(ctx, st);
     pair_overlap_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(A);
@@ -366,10 +322,10 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
     return qcs_check_launch(ctx, "pair_overlap_kernel");
 }
 
-qcs_status qcs_launch_reduce(qcs_ctx *ctx, int64_t W, int64_t P, int nchunks, const cd *partial, const cd *pref,
+qcs_status qcs_launch_reduce(qcs_ctx *ctx, int64_t W, int64_t P, int nparts, const cd *partial, const cd *pref,
                              cd *overlap, cudaStream_t st) {
     if (W == 0) return QCS_OK;
-    int64_t blocks = (W + 127) / 128;
-    reduce_kernel<<<(unsigned)blocks, 128, 0, st>>>(W, P, nchunks, partial, pref, overlap);
+    int64_t blocks = (W * 32 + 127) / 128;
+    reduce_kernel<<<(unsigned)blocks, 128, 0, st>>>(W, P, nparts, partial, pref, overlap);
     return qcs_check_launch(ctx, "reduce_kernel");
 }

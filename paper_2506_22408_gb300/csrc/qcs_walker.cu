@@ -5,7 +5,7 @@
 // orbitals.  With V = U^dagger the walker is the Slater determinant
 // a~_1^dagger ... a~_ne^dagger |0> of SI "Matrix Definitions" item 3 times det R.
 //
-// Output per walker:
+// Output per walker (U and R optionally, for the gradient):
 //   Ut[j][k] = U[k][j] (row j = orbital j), rows j < ne scaled by 1/sqrt2 -- the
 //              (1, -i)/sqrt2 row of the W^* block of Eq. (b_mat) selected for an
 //              occupied mode contributes conj(V_jk)/sqrt2 = U_kj/sqrt2;
@@ -16,7 +16,8 @@
 namespace {
 
 __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restrict__ Phi, cd *__restrict__ Ut,
-                                   cd *__restrict__ pref, unsigned *status) {
+                                   cd *__restrict__ pref, cd *__restrict__ Uout, cd *__restrict__ Rout,
+                                   unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -78,6 +79,13 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
             cd u = U[kk * n + j];
             Uw[e] = (j < ne) ? cscale(u, rs2) : u;
         }
+        if (Uout)
+            for (int e = lane; e < n * n; e += 32) Uout[w * n * n + e] = U[e];
+        if (Rout)
+            for (int e = lane; e < ne * ne; e += 32) {
+                int i = e / ne, j = e - i * ne;
+                Rout[w * ne * ne + e] = (j >= i) ? A[i * ne + j] : cmk(0.0, 0.0);
+            }
         if (lane == 0) {
             cd ip;  // i^{ne/2}
             switch ((ne / 2) & 3) {
@@ -97,13 +105,14 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
 }  // namespace
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, cd *Uout, cd *Rout) {
     if (W == 0) return QCS_OK;
     const int wpb = 4;
     size_t smem = (size_t)wpb * ((size_t)n * ne + (size_t)n * n + n) * sizeof(cd);
     if (qcs_set_smem(ctx, (const void *)walker_prep_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
     int64_t blocks = (W + wpb - 1) / wpb;
     if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
-    walker_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, ne, W, walkers, Ut, pref, ctx->d_status);
+    walker_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, ne, W, walkers, Ut, pref, Uout, Rout,
+                                                                   ctx->d_status);
     return qcs_check_launch(ctx, "walker_prep_kernel");
 }

@@ -30,7 +30,7 @@ EXPORTED = [
     "qcs_create", "qcs_destroy", "qcs_last_error", "qcs_sync_status", "qcs_workspace_bytes",
     "qcs_build_snapshots", "qcs_snapshots_free", "qcs_snapshots_parity", "qcs_snapshots_count",
     "qcs_snapshots_modes", "qcs_overlap", "qcs_overlap_grad", "qcs_force_bias", "qcs_overlap_flops_per_pair",
-    "qcs_profile_enable", "qcs_profile_read",
+    "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair",
 ]
 
 
@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True):
         lib.qcs_force_bias.argtypes = [P, i32, i32, i64, i32, P, P, P, P, f64, P, P]
         lib.qcs_overlap_flops_per_pair.argtypes = [i32, i32, i32, u32]
         lib.qcs_overlap_flops_per_pair.restype = f64
+        lib.qcs_grad_flops_per_pair.argtypes = [i32, i32, i32, u32]
+        lib.qcs_grad_flops_per_pair.restype = f64
         lib.qcs_profile_enable.argtypes = [P, i32]
         lib.qcs_profile_read.argtypes = [P, ctypes.POINTER(f64), ctypes.POINTER(i64)]
         _lib = lib
@@ -230,6 +232,10 @@ def force_bias(ctx: Context, L: torch.Tensor, walkers: torch.Tensor, ov: torch.T
 
 def flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
     return float(load().qcs_overlap_flops_per_pair(n, ne, nodes, flags))
+
+
+def grad_flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
+    return float(load().qcs_grad_flops_per_pair(n, ne, nodes, flags))
 
 
 class OverlapFn(torch.autograd.Function):
