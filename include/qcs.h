@@ -178,6 +178,37 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
                           const double *d_walkers, const double *d_overlap, const double *d_grad, double sqrt_dt,
                           double *d_xbar, void *stream);
 
+/* -------------------------------------------- allocation-free overlaps */
+
+/* Size of the library's fixed device scratch array used by qcs_overlap_noalloc. */
+#define QCS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Shadow overlaps without any device allocation (the paper has no counterpart:
+ * this is an embedding convenience).  Meant for callers that cannot allocate
+ * device memory when they need overlaps -- code running under CUDA stream
+ * capture, where cudaMalloc is not allowed, and hosts whose device memory is
+ * owned by their own pool and that forbid libraries from allocating.
+ * Computes exactly what qcs_build_snapshots followed by qcs_overlap (default
+ * options: FP64, minimum nodes) computes, with every intermediate buffer in a
+ * fixed file-scope device array of QCS_NOALLOC_SCRATCH_BYTES (32 MiB) that each
+ * GPU loading the library holds until the process exits.  No context is used.
+ *   d_Q       : P x 2n x 2n doubles (device), d_b : P x n bytes (device)
+ *   d_walkers : W x n x ne complex (device), d_overlap : W complex (device, written)
+ *   d_status  : caller-owned device word into which numerical status bits are
+ *               OR-ed (QCS_ERR_NONFINITE, QCS_ERR_SINGULAR), or NULL
+ * The scratch used is 32 n^2 P + 16 n^2 W + 16 W + 64 W ceil(P/16) + 5 P bytes
+ * (each term rounded up to 16 bytes, plus 16); a call needing more than
+ * QCS_NOALLOC_SCRATCH_BYTES returns QCS_ERR_ARG before enqueuing anything
+ * (e.g. n = 16: about 2000 snapshots with 64 walkers).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and leave their intermediates in it: calls whose work
+ * overlaps in time on the GPU (different streams, or different host threads)
+ * race and corrupt each other's results; serialise them.
+ * Errors: QCS_ERR_ARG (sizes, null pointers, odd ne), QCS_ERR_CUDA. */
+qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double *d_Q, const uint8_t *d_b, int64_t W,
+                               const double *d_walkers, double *d_overlap, unsigned *d_status, void *stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Measurement hooks (no counterpart in the paper).  While enabled, every

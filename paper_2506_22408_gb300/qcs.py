@@ -30,8 +30,9 @@ EXPORTED = [
     "qcs_create", "qcs_destroy", "qcs_last_error", "qcs_sync_status", "qcs_workspace_bytes",
     "qcs_build_snapshots", "qcs_snapshots_free", "qcs_snapshots_parity", "qcs_snapshots_count",
     "qcs_snapshots_modes", "qcs_overlap", "qcs_overlap_grad", "qcs_force_bias", "qcs_overlap_flops_per_pair",
-    "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair",
+    "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair", "qcs_overlap_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class QCSError(RuntimeError):
@@ -83,6 +84,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_overlap_flops_per_pair.restype = f64
         lib.qcs_grad_flops_per_pair.argtypes = [i32, i32, i32, u32]
         lib.qcs_grad_flops_per_pair.restype = f64
+        lib.qcs_overlap_noalloc.argtypes = [i32, i32, i64, P, P, i64, P, P, P, P]
         lib.qcs_profile_enable.argtypes = [P, i32]
         lib.qcs_profile_read.argtypes = [P, ctypes.POINTER(f64), ctypes.POINTER(i64)]
         _lib = lib
@@ -228,6 +230,24 @@ def force_bias(ctx: Context, L: torch.Tensor, walkers: torch.Tensor, ov: torch.T
     ctx.check(ctx.lib.qcs_force_bias(ctx.h, n, ne, W, nchol, _ptr(L), _ptr(walkers), _ptr(ov), _ptr(grad),
                                      float(sqrt_dt), _ptr(xb), _stream()))
     return xb
+
+
+def overlap_noalloc(Q: torch.Tensor, b: torch.Tensor, walkers: torch.Tensor, out: torch.Tensor,
+                    status: torch.Tensor | None = None) -> None:
+    """qcs_overlap_noalloc: overlaps into ``out`` (W complex128) with no device allocation by
+    the library (its scratch is a fixed 32 MiB device array).  ``status`` is an optional
+    int32 CUDA tensor of one element into which device status bits are OR-ed."""
+    _need_cuda(Q, "Q", torch.float64)
+    _need_cuda(b, "b", torch.uint8)
+    _need_cuda(walkers, "walkers", torch.complex128)
+    _need_cuda(out, "out", torch.complex128)
+    P, N, _ = Q.shape
+    W, n, ne = walkers.shape
+    rc = load().qcs_overlap_noalloc(n, ne, P, _ptr(Q), _ptr(b), W, _ptr(walkers), _ptr(out), _ptr(status),
+                                    _stream())
+    if rc != QCS_OK:
+        why = ("the sizes need more than the fixed 32 MiB scratch, or invalid arguments" if rc == 1 else "")
+        raise QCSError(rc, f"qcs_overlap_noalloc failed: {why}")
 
 
 def flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
