@@ -164,6 +164,12 @@ def run_grad(args, ctx, dev, barrier, ws):
     from paper_2506_22408_gb300 import qcs, synth
 
     wl = synth.DIFFERENTIATION
+    if args.grad_walkers or args.grad_snapshots:
+        import dataclasses
+
+        W, P = args.grad_walkers or wl.W, args.grad_snapshots or wl.P
+        wl = dataclasses.replace(wl, name=f"n={wl.n} ne={wl.ne} {W}x{P} nchol={wl.nchol} (reduced profiling case)",
+                                 W=W, P=P)
     data = wl.generate(seed=0)
     Q = torch.from_numpy(data["Q"]).to(dev)
     b = torch.from_numpy(data["b"]).to(dev)
@@ -211,6 +217,156 @@ def run_grad(args, ctx, dev, barrier, ws):
                          "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(src, "grad_pair_kernel"),
                          "kernel": "grad_pair_kernel", "kernel_ms": avg, "flops_per_launch": fpp * npar * wl.W},
             "gpu_launches_per_step": 6}
+
+
+def run_batch(args, ctx, dev, barrier, ws):
+    """Batching workload: five active spaces n = 8, 12, 16, 20, 24 (ne = n/2) with
+    1024/512/256/128/64 walkers and 2000/5000/10000/20000/40000 snapshots.  One AFQMC
+    step = a stand-in propagation of every system's walkers (walkers <- U walkers with a
+    fixed small unitary U = exp(eps K) per system, cuBLAS through torch) followed by ONE
+    qcs_overlap_batched call (one persistent pair-kernel launch over all systems);
+    --batch-steps steps are captured in one CUDA graph, which is replayed."""
+    import dataclasses
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    rng = np.random.default_rng(7)
+    systems, Us, outs = [], [], []
+    for wl0 in synth.BATCH_SYSTEMS:
+        wl = dataclasses.replace(wl0, W=max(1, int(round(wl0.W * args.batch_walker_scale))))
+        d = wl.generate(seed=0)
+        ctx.autotune(wl.n, wl.ne)
+        s = qcs.Snapshots(ctx, torch.from_numpy(d["Q"]).to(dev), torch.from_numpy(d["b"]).to(dev))
+        walkers = torch.from_numpy(d["Phi"]).to(dev)
+        K = rng.standard_normal((wl.n, wl.n)) + 1j * rng.standard_normal((wl.n, wl.n))
+        K = 0.01 * (K - K.conj().T)
+        w, v = np.linalg.eigh(-1j * K)
+        Us.append(torch.from_numpy((v * np.exp(1j * w)) @ v.conj().T).to(dev))
+        systems.append((wl, s, walkers))
+        outs.append(torch.empty(wl.W, dtype=torch.complex128, device=dev))
+    pairs_step = sum(wl.W * wl.P for wl, _, _ in systems)
+    arg = [(s, w) for _, s, w in systems]
+
+    def step():
+        for (wl, s, w), U in zip(systems, Us):
+            w.copy_(torch.matmul(U, w))
+        qcs.overlap_batched(ctx, arg, outs=outs)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(args.batch_steps):
+            step()
+    torch.cuda.synchronize()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.replay()
+    e1.record(stream)
+    barrier()
+    t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return {"metric": "walker x snapshot overlap pairs/s, batched active spaces under a CUDA graph",
+            "value": ws * pairs_step * args.batch_steps / t, "unit": "pairs/s",
+            "ms_per_step": 1e3 * t / args.batch_steps, "graph_steps": args.batch_steps,
+            "config": {"systems": [{"n": wl.n, "ne": wl.ne, "walkers": wl.W, "snapshots": wl.P} for wl, _, _ in systems],
+                       "walker_scale": args.batch_walker_scale,
+                       "pairs_per_step": pairs_step,
+                       "step": "stand-in propagation (torch matmul) + one qcs_overlap_batched launch sequence"},
+            "gpu_launches_per_step": 5 + 1 + 5}
+
+
+def run_precision(args, ctx, dev, barrier, ws):
+    """Split-precision workload: n = 16, ne = 8, 2048 walkers x 50000 snapshots; one step =
+    snapshot build + qcs_overlap with QCS_TF32X3 (congruence on tcgen05 tensor cores as
+    three TF32 hi/lo passes, B^(s) in FP32, Pfaffians in FP64).  Errors are measured
+    against the FP64 path on the first 64 walkers x 4000 snapshots."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    wl = synth.PRECISION
+    d = wl.generate(seed=0)
+    Q = torch.from_numpy(d["Q"]).to(dev)
+    b = torch.from_numpy(d["b"]).to(dev)
+    Phi = torch.from_numpy(d["Phi"]).to(dev)
+    del d
+
+    def step():
+        snaps = qcs.Snapshots(ctx, Q, b)
+        ov, _ = qcs.overlap(ctx, snaps, Phi, precision=qcs.QCS_TF32X3)
+        return snaps, ov
+
+    snaps, _ = step()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    npar = int((snaps.parity() == 1).sum().item())
+    del snaps
+    steps = max(2, min(args.steps, 3))
+    ctx.profile(True)
+    ctx.profile_read()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        snaps, ov = step()
+    e1.record(stream)
+    barrier()
+    ctx.profile(False)
+    kms, kl = ctx.profile_read()
+    t = e0.elapsed_time(e1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    # error against the FP64 path on a subset
+    Ws, Ps = 64, 4000
+    sub = qcs.Snapshots(ctx, Q[:Ps].contiguous(), b[:Ps].contiguous())
+    o64, p64 = qcs.overlap(ctx, sub, Phi[:Ws].contiguous(), per_pair=True)
+    o32, p32 = qcs.overlap(ctx, sub, Phi[:Ws].contiguous(), per_pair=True, precision=qcs.QCS_TF32X3)
+    torch.cuda.synchronize()
+    mag = p64.abs().mean(dim=1, keepdim=True)
+    rel_pair = ((p32 - p64).abs() / mag).flatten()
+    rel_walker = ((o32 - o64).abs() / mag.flatten())
+    n, ne = wl.n, wl.ne
+    dd = n - ne
+    f_T = 16.0 * n ** 3
+    f_B = 16.0 * n * ne * (ne - 1) / 2 + 16.0 * n * ne * dd + 4.0 * n * (2 * dd) * (2 * dd - 1) / 2
+    f_pf = qcs.flops_per_pair(n, ne) - f_T - f_B  # FP64 work that stays on the FP64 pipe
+    avg = kms / max(kl, 1)
+    ach = f_pf * npar * wl.W / (avg * 1e-3) / 1e12
+    ngroups = (wl.W + 3) // 4
+    tensor_flops = ngroups * ((npar + 7) // 8) * 3 * 2.0 * 128 * 256 * 32
+    return {"metric": "walker x snapshot overlap pairs/s, split precision (3xTF32 congruence on tensor cores)",
+            "value": ws * wl.W * wl.P * steps / t, "unit": "pairs/s", "ms_per_step": 1e3 * t / steps,
+            "steps": steps, "dtype": "tf32x3 congruence / f32 B / f64 Pfaffian",
+            "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "parity_plus_snapshots": npar},
+            "error_vs_fp64": {"subset": f"{Ws} walkers x {Ps} snapshots",
+                              "pair_rel_max": float(rel_pair.max().item()),
+                              "pair_rel_median": float(rel_pair.median().item()),
+                              "walker_rel_max": float(rel_walker.max().item()),
+                              "normalisation": "mean |o_p| of the walker on the FP64 path"},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "split_pair_kernel", "kernel_ms": avg,
+                         "flops_counted": "FP64 Pfaffian work only (congruence on tensor cores)",
+                         "tensor_tflops_executed": tensor_flops / (avg * 1e-3) / 1e12,
+                         "traffic": traffic_for(os.path.join(ROOT, "paper_2506_22408_gb300", "csrc", "qcs_split.cu"),
+                                                "split_pair_kernel")}}
 
 
 def cpu_baseline(wl, data, target_s=10.0):
@@ -277,6 +433,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the differentiation workload")
+    ap.add_argument("--grad-walkers", type=int, default=0, help="override the differentiation walkers (profiling)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
+    ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
+    ap.add_argument("--batch-steps", type=int, default=50, help="AFQMC steps captured in the batching graph")
+    ap.add_argument("--batch-walker-scale", type=float, default=0.25,
+                    help="scale of the batching walker counts (1.0: 1024/512/256/128/64 walkers)")
+    ap.add_argument("--grad-snapshots", type=int, default=0, help="override the differentiation snapshots")
     ap.add_argument("--walkers", type=int, default=0, help="override the walker count (profiling cases)")
     ap.add_argument("--snapshots", type=int, default=0, help="override the snapshot count (profiling cases)")
     args = ap.parse_args()
@@ -308,6 +471,7 @@ def main():
 
     data = wl.generate(seed=0)
     ctx = qcs.Context(local)
+    tuned = ctx.autotune(wl.n, wl.ne)  # pair-kernel configuration for this GPU (cached)
     Qd = torch.from_numpy(data["Q"]).to(dev)
     bd = torch.from_numpy(data["b"]).to(dev)
     Pd = torch.from_numpy(data["Phi"]).to(dev)
@@ -362,6 +526,12 @@ def main():
     grad = None
     if not args.no_grad:
         grad = run_grad(args, ctx, dev, barrier, ws)
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, ctx, dev, barrier, ws)
+    precision = None
+    if not args.no_precision:
+        precision = run_precision(args, ctx, dev, barrier, ws)
 
     # ---------------- roofline of the dominant kernel
     fpp = qcs.flops_per_pair(wl.n, wl.ne)
@@ -381,6 +551,7 @@ def main():
             "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "n": wl.n, "ne": wl.ne,
                        "walkers": wl.W, "snapshots": wl.P, "parity_plus_snapshots": npar,
                        "nodes": "minimum (n-ne+1 roots of unity, floor/2+1 evaluated)",
+                       "kernel_config": {"node_matrices_per_warp_round": tuned, "picked_by": "qcs_autotune"},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "snapshot set (164 MB) larger than L2, and L2 flushed between timed steps"},
             "nontrivial_pairs_per_s": ws * npar * wl.W * args.steps / t_total,
@@ -388,6 +559,8 @@ def main():
             "roofline": roof,
             "clocks": clk.summary(),
             "grad": grad,
+            "batch": batch,
+            "precision": precision,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

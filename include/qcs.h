@@ -77,7 +77,11 @@ typedef enum {
 
 typedef enum {
     QCS_FP64 = 0,  /* every product and the Pfaffians in FP64 */
-    QCS_TF32X3 = 1 /* congruence products as split FP32 on tensor cores (3xTF32), Pfaffian in FP64 */
+    QCS_TF32X3 = 1 /* qcs_overlap only, n <= 16: the congruence T = U^T Qt^T on tensor cores
+                      (tcgen05 kind::tf32, hi/lo splits, hi*hi + hi*lo + lo*hi accumulated in
+                      FP32), B^(s) in FP32; Pfaffians, pivoting and node sums in FP64.  The
+                      snapshot set gets TF32 operand slabs (8 KB per snapshot, allocated with
+                      cudaMalloc) on its first use in this mode. */
 } qcs_precision;
 
 /* qcs_opts.flags */
@@ -88,7 +92,9 @@ typedef struct {
     int precision; /* qcs_precision */
     int nodes;     /* number of roots-of-unity nodes N; 0 = minimum n-ne+1 */
     unsigned flags;
-    int reserved;
+    int config;    /* kernel configuration: 0 = the context's tuned choice for these sizes
+                      (qcs_autotune / qcs_set_config) or the built-in default;
+                      k >= 1 = k node matrices per warp round in the pair kernel */
 } qcs_opts;
 
 /* ------------------------------------------------------------- context */
@@ -157,6 +163,33 @@ int qcs_snapshots_modes(const qcs_snapshots *s);
 qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                        double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream);
 
+/* ----------------------------------------------------------- batching */
+
+#define QCS_MAX_SYSTEMS 8
+
+/* One system of a batched call: its snapshot set (which fixes n), electron
+ * count, walkers (device, W x n x ne complex) and overlap output (device, W
+ * complex). */
+typedef struct {
+    const qcs_snapshots *snapshots;
+    int ne;
+    int64_t W;
+    const double *d_walkers;
+    double *d_overlap;
+} qcs_system;
+
+/* Overlaps of up to QCS_MAX_SYSTEMS systems with different active spaces, walker
+ * and snapshot counts, with ONE launch of the pair kernel: a persistent grid
+ * pulls (system, walker, snapshot-chunk) tiles from a device counter, costliest
+ * systems first.  Each system's result equals that of qcs_overlap on it (same
+ * per-tile arithmetic and reduction order).  opts (NULL = defaults) applies to
+ * every system; opts->config = 0 takes each system's tuned configuration.
+ * The call allocates nothing once the context workspace has grown to the
+ * batch's size, so after one warm-up call it can be captured in a CUDA graph.
+ * Errors: QCS_ERR_ARG, QCS_ERR_CUDA, QCS_ERR_UNSUPPORTED. */
+qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_system *systems, const qcs_opts *opts,
+                               void *stream);
+
 /* Overlaps and their holomorphic walker gradient
  *   d_grad[w][k][j] = d <Psi_T|phi_w> / d Phi_w[k][j]   (W x n x ne complex).
  * Each pair's contribution is differentiated through
@@ -197,7 +230,7 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
  *   d_status  : caller-owned device word into which numerical status bits are
  *               OR-ed (QCS_ERR_NONFINITE, QCS_ERR_SINGULAR), or NULL
  * The scratch used is 32 n^2 P + 16 n^2 W + 16 W + 64 W ceil(P/16) + 5 P bytes
- * (each term rounded up to 16 bytes, plus 16); a call needing more than
+ * (each term rounded up to 16 bytes, plus 32); a call needing more than
  * QCS_NOALLOC_SCRATCH_BYTES returns QCS_ERR_ARG before enqueuing anything
  * (e.g. n = 16: about 2000 snapshots with 64 walkers).
  * The first call on a device looks up the array's device address (with that
@@ -208,6 +241,20 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
  * Errors: QCS_ERR_ARG (sizes, null pointers, odd ne), QCS_ERR_CUDA. */
 qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double *d_Q, const uint8_t *d_b, int64_t W,
                                const double *d_walkers, double *d_overlap, unsigned *d_status, void *stream);
+
+/* ------------------------------------------------------------ tuning */
+
+/* Autotuner of the pair kernel (no counterpart in the paper).  Times every
+ * configuration (node matrices per warp round, 1..min(nodes evaluated, 8)) of
+ * qcs_overlap for (n, ne, nodes, flags) on a synthetic sample on the context's
+ * device (allocates and frees its own sample; synchronises), records the
+ * fastest in the context and returns it in *config (may be NULL).
+ * Errors: QCS_ERR_ARG, QCS_ERR_CUDA. */
+qcs_status qcs_autotune(qcs_ctx *ctx, int n, int ne, int nodes, unsigned flags, int *config);
+
+/* Record a configuration for (n, ne, nodes, flags) in the context, e.g. one read
+ * from an autotuner cache.  config = 0 clears the entry. */
+qcs_status qcs_set_config(qcs_ctx *ctx, int n, int ne, int nodes, unsigned flags, int config);
 
 /* ------------------------------------------------------------ profiling */
 

@@ -268,6 +268,8 @@ extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
     if (s->parity) cudaFree(s->parity);
     if (s->idx) cudaFree(s->idx);
     if (s->d_count) cudaFree(s->d_count);
+    if (s->split_hi) cudaFree(s->split_hi);
+    if (s->split_lo) cudaFree(s->split_lo);
     delete s;
     return QCS_OK;
 }
@@ -291,7 +293,10 @@ const int kChunk = 4;  // snapshots per warp in an overlap tile
 
 struct OverlapWork {
     cd *Ut, *pref, *partial;
-    int nchunks;
+    unsigned long long *counter;
+    float *Mhi, *Mlo;  // split precision: walker operand slabs
+    int nchunks, nparts;
+    bool split;
 };
 
 qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
@@ -306,21 +311,34 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     if (W > 0 && !d_walkers) return qcs_fail(ctx, QCS_ERR_ARG, "null walkers");
     qcs_opts o = {QCS_FP64, 0, 0u, 0};
     if (opts) o = *opts;
-    if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "precision mode not built");
+    if (o.precision != QCS_FP64 && o.precision != QCS_TF32X3)
+        return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "unknown precision mode");
+    if (o.precision == QCS_TF32X3 && n > 16)
+        return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split precision supports n <= 16");
     if (qcs_make_node_plan(n, ne, o.nodes, o.flags, plan) != QCS_OK)
         return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
-    const int span = kChunk * qcs_pair_warps_per_block();
+    const bool split = o.precision == QCS_TF32X3;
+    wk->split = split;
+    // partial sums: FP64 path one per (walker, 16-snapshot chunk, warp); split path one
+    // per (walker, 8-snapshot chunk)
+    const int span = split ? 8 : kChunk * qcs_pair_warps_per_block();
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
+    wk->nparts = split ? wk->nchunks : wk->nchunks * qcs_pair_warps_per_block();
     size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
-    size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nchunks * qcs_pair_warps_per_block());
+    size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nparts);
+    size_t b_slab = split ? align16(qcs_split_walker_bytes(W)) : 0;
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, b_ut + b_pref + b_part, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab, &base);
     if (ws != QCS_OK) return ws;
-    wk->Ut = (cd *)base;
-    wk->pref = (cd *)((char *)base + b_ut);
-    wk->partial = (cd *)((char *)base + b_ut + b_pref);
+    char *pb = (char *)base;
+    wk->counter = (unsigned long long *)pb;
+    wk->Ut = (cd *)(pb + 16);
+    wk->pref = (cd *)(pb + 16 + b_ut);
+    wk->partial = (cd *)(pb + 16 + b_ut + b_pref);
+    wk->Mhi = split ? (float *)(pb + 16 + b_ut + b_pref + b_part) : nullptr;
+    wk->Mlo = split ? (float *)(pb + 16 + b_ut + b_pref + b_part + b_slab) : nullptr;
     return qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, wk->Ut, wk->pref, st);
 }
 
@@ -354,10 +372,91 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
     L.partial = wk.partial;
     L.per_pair = (cd *)d_per_pair;
     L.plan = plan;
-    r = qcs_launch_pairs(ctx, L, st);
+    L.counter = wk.counter;
+    L.config = opts ? opts->config : 0;
+    if (L.config == 0) {
+        auto it = ctx->tuned.find(std::make_tuple(s->n, ne, opts ? opts->nodes : 0, opts ? opts->flags : 0u));
+        if (it != ctx->tuned.end()) L.config = it->second;
+    }
+    if (wk.split) {
+        r = qcs_split_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
+        if (r != QCS_OK) return r;
+        r = qcs_launch_split(ctx, L, wk.Mhi, wk.Mlo, st);
+    } else {
+        r = qcs_launch_pairs(ctx, L, st);
+    }
     if (r != QCS_OK) return r;
-    return qcs_launch_reduce(ctx, W, s->P, wk.nchunks * qcs_pair_warps_per_block(), wk.partial, wk.pref,
-                             (cd *)d_overlap, st);
+    return qcs_launch_reduce(ctx, W, s->P, wk.nparts, wk.partial, wk.pref, (cd *)d_overlap, st);
+}
+
+extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_system *systems, const qcs_opts *opts,
+                                          void *stream) {
+    if (!ctx) return QCS_ERR_ARG;
+    if (nsys < 1 || nsys > QCS_MAX_SYSTEMS || !systems)
+        return qcs_fail(ctx, QCS_ERR_ARG, "nsys must be in [1, QCS_MAX_SYSTEMS]");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    qcs_opts o = {QCS_FP64, 0, 0u, 0};
+    if (opts) o = *opts;
+    if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "batched calls are FP64");
+    qcs_pair_launch Ls[QCS_MAX_SYSTEMS];
+    size_t off[QCS_MAX_SYSTEMS][3];
+    size_t total = 16;  // the tile counter first
+    const int wpb = qcs_pair_warps_per_block();
+    for (int i = 0; i < nsys; ++i) {
+        const qcs_system &y = systems[i];
+        const qcs_snapshots *s = y.snapshots;
+        if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set in batch");
+        if (s->device != ctx->device) return qcs_fail(ctx, QCS_ERR_ARG, "snapshot set lives on another device");
+        qcs_status c = check_sizes(ctx, s->n, y.ne);
+        if (c != QCS_OK) return c;
+        if (y.W < 0 || (y.W > 0 && (!y.d_walkers || !y.d_overlap)))
+            return qcs_fail(ctx, QCS_ERR_ARG, "bad walkers or output in batch");
+        qcs_pair_launch &L = Ls[i];
+        if (qcs_make_node_plan(s->n, y.ne, o.nodes, o.flags, &L.plan) != QCS_OK)
+            return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES] for every system");
+        L.n = s->n;
+        L.ne = y.ne;
+        L.W = y.W;
+        L.P = s->P;
+        L.chunk = kChunk;
+        L.nchunks = (int)((s->P + kChunk * wpb - 1) / (kChunk * wpb));
+        if (L.nchunks < 1) L.nchunks = 1;
+        L.s = s;
+        L.per_pair = nullptr;
+        L.counter = nullptr;
+        L.config = o.config;
+        if (L.config == 0) {
+            auto it = ctx->tuned.find(std::make_tuple(s->n, y.ne, o.nodes, o.flags));
+            if (it != ctx->tuned.end()) L.config = it->second;
+        }
+        off[i][0] = total;
+        total += align16(sizeof(cd) * (size_t)y.W * s->n * s->n);
+        off[i][1] = total;
+        total += align16(sizeof(cd) * (size_t)y.W);
+        off[i][2] = total;
+        total += align16(sizeof(cd) * (size_t)y.W * L.nchunks * wpb);
+    }
+    void *base = nullptr;
+    qcs_status r = qcs_workspace(ctx, total, &base);
+    if (r != QCS_OK) return r;
+    char *pb = (char *)base;
+    for (int i = 0; i < nsys; ++i) {
+        Ls[i].Ut = (cd *)(pb + off[i][0]);
+        Ls[i].pref = (cd *)(pb + off[i][1]);
+        Ls[i].partial = (cd *)(pb + off[i][2]);
+        r = qcs_launch_walker_prep(ctx, Ls[i].n, Ls[i].ne, Ls[i].W, (const cd *)systems[i].d_walkers,
+                                   (cd *)Ls[i].Ut, (cd *)Ls[i].pref, st);
+        if (r != QCS_OK) return r;
+    }
+    r = qcs_launch_pairs_batched(ctx, nsys, Ls, (unsigned long long *)pb, st);
+    if (r != QCS_OK) return r;
+    for (int i = 0; i < nsys; ++i) {
+        r = qcs_launch_reduce(ctx, Ls[i].W, Ls[i].P, Ls[i].nchunks * wpb, Ls[i].partial, Ls[i].pref,
+                              (cd *)systems[i].d_overlap, st);
+        if (r != QCS_OK) return r;
+    }
+    return QCS_OK;
 }
 
 extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W,
@@ -397,9 +496,10 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     size_t b_r = align16(sizeof(cd) * (size_t)W * ne * ne);
     size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * (1 + (size_t)n * n));
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, b_ut + b_pref + b_u + b_r + b_part, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part, &base);
     if (ws != QCS_OK) return ws;
-    char *pb = (char *)base;
+    unsigned long long *gcounter = (unsigned long long *)base;
+    char *pb = (char *)base + 16;
     cd *Ut = (cd *)pb;
     cd *pref = (cd *)(pb + b_ut);
     cd *U = (cd *)(pb + b_ut + b_pref);
@@ -423,6 +523,7 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     L.overlap = (cd *)d_overlap;
     L.grad = (cd *)d_grad;
     L.plan = plan;
+    L.counter = gcounter;
     return qcs_launch_grad(ctx, L, st);
 }
 

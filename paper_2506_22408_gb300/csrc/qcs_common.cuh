@@ -37,6 +37,20 @@ __device__ __forceinline__ void cfms(cd &acc, cd a, cd b) {
     acc.y = fma(-a.x, b.y, acc.y);
     acc.y = fma(-a.y, b.x, acc.y);
 }
+// -(a * b), with the negation folded into the FP64 operand modifiers
+__device__ __forceinline__ cd cnegmul(cd a, cd b) {
+    return make_double2(fma(-a.x, b.x, a.y * b.y), fma(-a.x, b.y, -(a.y * b.x)));
+}
+
+// Sign flip of both components by integer XOR on the sign bits (no FP64 work).
+__device__ __forceinline__ cd flip_if(cd z, bool f) {
+    if (f) {
+        z.x = __longlong_as_double(__double_as_longlong(z.x) ^ (long long)0x8000000000000000ull);
+        z.y = __longlong_as_double(__double_as_longlong(z.y) ^ (long long)0x8000000000000000ull);
+    }
+    return z;
+}
+
 // acc += a * r  (r real)
 __device__ __forceinline__ void crfma(cd &acc, cd a, double r) {
     acc.x = fma(a.x, r, acc.x);

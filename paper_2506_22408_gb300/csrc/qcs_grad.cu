@@ -45,18 +45,11 @@ struct GradArgs {
     const int *idx;
     const int *d_count;
     cd *partial;
+    unsigned long long *counter;  // tile counter: warps pull tiles dynamically
     unsigned *status;
     cd wnode[QCS_MAX_NODES];
     cd gamma[QCS_MAX_NODES];
 };
-
-__device__ __forceinline__ cd flip_if(cd z, bool f) {
-    if (f) {
-        z.x = __longlong_as_double(__double_as_longlong(z.x) ^ (long long)0x8000000000000000ull);
-        z.y = __longlong_as_double(__double_as_longlong(z.y) ^ (long long)0x8000000000000000ull);
-    }
-    return z;
-}
 
 // Skew matrix entry (i, j) from its packed upper triangle.
 __device__ __forceinline__ cd skew_at(const cd *P, int i, int j) {
@@ -237,9 +230,13 @@ __global__ void __launch_bounds__(128) grad_pair_kernel(const __grid_constant__ 
 
     const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
     const int64_t ntiles = A.W * A.nchunks;
-    const int64_t gw = (int64_t)blockIdx.x * wpb + warp, GW = (int64_t)gridDim.x * wpb;
     const size_t rec = 1 + (size_t)n * n;
-    for (int64_t tile = gw; tile < ntiles; tile += GW) {
+    (void)wpb;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(A.counter, 1ull);
+        const int64_t tile = (int64_t)__shfl_sync(QCS_FULL, tk, 0);
+        if (tile >= ntiles) break;
         const int64_t w = tile / A.nchunks;
         const int ch = (int)(tile - w * A.nchunks);
         const int64_t p0 = (int64_t)ch * A.chunk;
@@ -539,6 +536,7 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     A.idx = L.s->idx;
     A.d_count = L.s->d_count;
     A.partial = L.partial;
+    A.counter = L.counter;
     A.status = ctx->d_status;
     for (int k = 0; k < L.plan.nev; ++k) {
         A.wnode[k] = L.plan.wnode[k];
@@ -558,6 +556,8 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     int64_t need = (ntiles + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
+    if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return qcs_fail(ctx, QCS_ERR_CUDA, "grad tile counter reset");
     qcs_prof_begin(ctx, st);
     grad_pair_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(A);
     qcs_prof_end(ctx, st);

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -18,6 +20,7 @@ struct qcs_ctx {
     void *work = nullptr;          // device workspace
     size_t work_bytes = 0;
     std::string last_error;
+    std::map<std::tuple<int, int, int, unsigned>, int> tuned;  // (n, ne, nodes, flags) -> config
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;  // recorded around dominant kernels
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;    // reusable event pairs
@@ -35,6 +38,8 @@ struct qcs_snapshots {
     int8_t *parity = nullptr; // P: +1 / -1 (0: singular or non-finite Q)
     int *idx = nullptr;       // P: indices with parity +1, ascending (first *d_count valid)
     int *d_count = nullptr;   // 1: number of parity +1 snapshots
+    void *split_hi = nullptr; // P x 4 KB TF32 operand slabs (split precision), built on first use
+    void *split_lo = nullptr;
 };
 
 // Helpers implemented in qcs_api.cu
@@ -73,9 +78,11 @@ struct qcs_grad_launch {
     cd *overlap;     // W
     cd *grad;        // W x n x ne
     qcs_node_plan plan;
+    unsigned long long *counter;  // device tile counter (reset by the launcher)
 };
 
 qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t st);
+
 qcs_status qcs_launch_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const cd *L, const cd *walkers,
                                  const cd *overlap, const cd *grad, double sqrt_dt, cd *xbar, cudaStream_t st);
 
@@ -89,9 +96,18 @@ struct qcs_pair_launch {
     cd *partial;     // W x nchunks x warps-per-block
     cd *per_pair;    // W x P or null
     qcs_node_plan plan;
+    int config;      // node matrices per warp round; 0 = heuristic
+    unsigned long long *counter;  // device tile counter (reset by the launcher)
 };
 
 qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t st);
 int qcs_pair_warps_per_block();  // partial sums per overlap tile
+// Split precision (qcs_split.cu)
+qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
+size_t qcs_split_walker_bytes(int64_t W);
+qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st);
+qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launch *Ls, unsigned long long *counter,
+                                    cudaStream_t st);
+extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
 qcs_status qcs_launch_reduce(qcs_ctx *ctx, int64_t W, int64_t P, int nparts, const cd *partial, const cd *pref,
                              cd *overlap, cudaStream_t st);

@@ -53,6 +53,7 @@ size_t noalloc_bytes(int n, int64_t P, int64_t W) {
     b += align16(sizeof(cd) * (size_t)W * n * n);
     b += align16(sizeof(cd) * (size_t)W);
     b += align16(sizeof(cd) * (size_t)W * nchunks * qcs_pair_warps_per_block());
+    b += 16;  // tile counter
     return b;
 }
 
@@ -105,6 +106,8 @@ extern "C" qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double
     cd *pref = (cd *)p;
     p += align16(sizeof(cd) * (size_t)W);
     cd *partial = (cd *)p;
+    p += align16(sizeof(cd) * (size_t)W * nchunks * qcs_pair_warps_per_block());
+    unsigned long long *counter = (unsigned long long *)p;
 
     r = qcs_launch_snapshot_build(&ctx, &s, d_Q, d_b, st);
     if (r != QCS_OK) return r;
@@ -122,6 +125,8 @@ extern "C" qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double
     L.s = &s;
     L.partial = partial;
     L.per_pair = nullptr;
+    L.config = 0;
+    L.counter = counter;
     if (qcs_make_node_plan(n, ne, 0, 0u, &L.plan) != QCS_OK) return QCS_ERR_ARG;
     r = qcs_launch_pairs(&ctx, L, st);
     if (r != QCS_OK) return r;

@@ -33,7 +33,6 @@
 
 namespace {
 
-constexpr int kMaxNB = 8;
 
 struct PairArgs {
     int n, ne, m, d, nev, NB, all, chunk, nchunks;
@@ -41,7 +40,7 @@ struct PairArgs {
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
     int ut_bytes;     // shared bytes of the walker rows Ut (per block)
-    int off_R, off_B, off_U, off_V, off_pf, off_inv, off_best, off_int, off_act;  // byte offsets in a warp region
+    int off_R, off_B, off_U, off_V, off_pf, off_inv, off_best, off_int, off_act, off_pv;  // byte offsets in a warp region
     const cd *Ut;
     const cd *pref;
     const cd *Qt;
@@ -54,104 +53,12 @@ struct PairArgs {
     cd gamma[QCS_MAX_NODES];
 };
 
-// Pfaffians of nb node matrices B + wnode[k0 + v] D held in Ns (packed upper).
-// On return pf[v] holds pf(B + conj(z_{k0+v}) D).
-__device__ void node_pfaffians(const PairArgs &A, int k0, int nb, const cd *__restrict__ Bs, cd *__restrict__ Ns,
-                               cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ inv,
-                               unsigned long long *__restrict__ best, int *__restrict__ ints,
-                               uint8_t *__restrict__ act0, uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
-                               int lane) {
-    const int m = A.m, ne = A.ne, d = A.d;
-    const int T = tri_count(m);
-    int *pos = ints, *kk = ints + kMaxNB, *pp = ints + 2 * kMaxNB;
-    for (int e = lane; e < nb * T; e += 32) {
-        int v = e / T, t = e - v * T;
-        Ns[v * T + t] = Bs[t];
-    }
-    for (int e = lane; e < nb * m; e += 32) {
-        int v = e / m, a = e - v * m;
-        act0[v * m + a] = (uint8_t)a;
-    }
-    if (lane < nb) pf[lane] = cmk(1.0, 0.0);
-    __syncwarp();
-    for (int e = lane; e < nb * d; e += 32) {
-        int v = e / d, i = e - v * d;
-        cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
-        *x = cadd(*x, A.wnode[k0 + v]);
-    }
-    __syncwarp();
-    uint8_t *cur = act0, *nxt = act1;
-    for (int r = m; r >= 2; r -= 2) {
-        // pivot: largest |A_{k,i}| over the active row of k = cur[0]
-        if (lane < nb) best[lane] = 0ull;
-        __syncwarp();
-        const int rc = r - 1;
-        for (int e = lane; e < nb * rc; e += 32) {
-            int v = e / rc, a = 1 + (e - v * rc);
-            int k = cur[v * m], i = cur[v * m + a];
-            unsigned key = pivot_key(Ns[v * T + tri_index(k, i)]);
-            atomicMax(&best[v], ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a));
-        }
-        __syncwarp();
-        if (lane < nb) {
-            int a = 0xffff - (int)(best[lane] & 0xffffull);
-            int k = cur[lane * m], p = cur[lane * m + a];
-            cd piv = Ns[lane * T + tri_index(k, p)];
-            cd f = cmul(pf[lane], piv);
-            pf[lane] = ((a - 1) & 1) ? cneg(f) : f;
-            inv[lane] = cinv(piv);
-            pos[lane] = a;
-            kk[lane] = k;
-            pp[lane] = p;
-        }
-        __syncwarp();
-        if (r == 2) break;
-        // Gauss vectors over the remaining indices (original order kept)
-        const int rv = r - 2;
-        for (int e = lane; e < nb * rv; e += 32) {
-            int v = e / rv, a2 = e - v * rv;
-            int a = a2 + 1 + ((a2 + 1 >= pos[v]) ? 1 : 0);
-            int i = cur[v * m + a], k = kk[v], p = pp[v];
-            const cd *Nv = Ns + v * T;
-            cd u = Nv[tri_index(k, i)];          // A_{k,i}; A_{i,k} = -u
-            cd ut = cneg(cmul(u, inv[v]));       // A_{i,k} / A_{k,p}
-            cd vv = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);  // A_{i,p}
-            Uv[v * m + a2] = ut;
-            Vv[v * m + a2] = vv;
-            nxt[v * m + a2] = (uint8_t)i;
-        }
-        __syncwarp();
-        // rank-2 update A_ij -= ut_i v_j - v_i ut_j on the remaining pairs
-        const int Tr = tri_count(rv);
-        for (int e = lane; e < nb * Tr; e += 32) {
-            int v = e / Tr, t = e - v * Tr;
-            int a, b;
-            pair_of(tab, t, a, b);
-            int i = nxt[v * m + a], j = nxt[v * m + b];
-            cd *x = Ns + v * T + tri_index(i, j);
-            cd y = *x;
-            const cd *U_ = Uv + v * m, *V_ = Vv + v * m;
-            cfms(y, U_[a], V_[b]);
-            cfma(y, V_[a], U_[b]);
-            *x = y;
-        }
-        __syncwarp();
-        uint8_t *t = cur;
-        cur = nxt;
-        nxt = t;
-    }
-}
-
-__global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant__ PairArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
+// One tile of system A: walker w = tile / nchunks, the tile's snapshots spread
+// over the block's warps; each warp writes one partial sum.  Every thread of the
+// block calls this (it contains block barriers around the shared walker rows).
+__device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned char *wbase, cd *Uts,
+                         const uint16_t *tab, int warp, int wpb, int lane) {
     const int n = A.n, n2 = 2 * n;
-    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
-    build_pair_table(tab, tri_count(A.m));
-    cd *Uts = reinterpret_cast<cd *>(smem_raw + A.tab_bytes);  // shared by the block's warps
-    unsigned char *wbase = smem_raw + A.tab_bytes + A.ut_bytes + (size_t)warp * A.warp_bytes;
     cd *Rg = reinterpret_cast<cd *>(wbase);
     cd *Qs = Rg;
     cd *Ts = Rg + (size_t)n2 * ld_qt(n);
@@ -165,50 +72,87 @@ __global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant
     int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = reinterpret_cast<uint8_t *>(wbase + A.off_act);
     uint8_t *act1 = act0 + A.NB * A.m;
-
-    const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
-    const int64_t ntiles = A.W * A.nchunks;
+    cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
     const int span = A.chunk * wpb;  // snapshots per tile; warp w takes every wpb-th
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t w = tile / A.nchunks;
-        const int ch = (int)(tile - w * A.nchunks);
-        const int64_t p0 = (int64_t)ch * span;
-        const int64_t p1 = p0 + span < L ? p0 + span : L;
-        __syncthreads();  // previous tile's readers of Uts are done
-        if (p0 < L) {
-            const cd *Utw = A.Ut + w * n * n;
-            const int lu = ld_ut(n);
-            for (int e = threadIdx.x; e < n * n; e += blockDim.x) Uts[(e / n) * lu + (e % n)] = Utw[e];
-        }
-        __syncthreads();
-        cd acc = cmk(0.0, 0.0);
-        if (p0 < L) {
-            const cd prefw = A.pref[w];
-            for (int64_t pq = p0 + warp; pq < p1; pq += wpb) {
-                const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+    const int64_t w = tile / A.nchunks;
+    const int ch = (int)(tile - w * A.nchunks);
+    const int64_t p0 = (int64_t)ch * span;
+    const int64_t p1 = p0 + span < L ? p0 + span : L;
+    __syncthreads();  // previous tile's readers of Uts are done
+    if (p0 < L) {
+        const cd *Utw = A.Ut + w * n * n;
+        const int lu = ld_ut(n);
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Uts[(e / n) * lu + (e % n)] = Utw[e];
+    }
+    __syncthreads();
+    cd acc = cmk(0.0, 0.0);
+    if (p0 < L) {
+        const cd prefw = A.pref[w];
+        for (int64_t pq = p0 + warp; pq < p1; pq += wpb) {
+            const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+            __syncwarp();
+            load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
+            __syncwarp();
+            build_T(n, Uts, Qs, Ts, lane);
+            __syncwarp();
+            build_B(A.n, A.ne, Ts, Bs, tab, lane);
+            __syncwarp();
+            cd S = cmk(0.0, 0.0);
+            for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                node_pfaffians(A.m, A.ne, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, best, ints, act0, act1, tab, pv,
+                               lane);
+                if (lane == 0)
+                    for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
                 __syncwarp();
-                load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
-                __syncwarp();
-                build_T(n, Uts, Qs, Ts, lane);
-                __syncwarp();
-                build_B(A.n, A.ne, Ts, Bs, tab, lane);
-                __syncwarp();
-                cd S = cmk(0.0, 0.0);
-                for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
-                    int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                    node_pfaffians(A, k0, nb, Bs, Ns, Uv, Vv, pf, inv, best, ints, act0, act1, tab, lane);
-                    if (lane == 0)
-                        for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
-                    __syncwarp();
-                }
-                if (lane == 0) {
-                    if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
-                    acc = cadd(acc, S);
-                    if (A.per_pair) A.per_pair[w * A.P + q] = cmul(prefw, S);
-                }
+            }
+            if (lane == 0) {
+                if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
+                acc = cadd(acc, S);
+                if (A.per_pair) A.per_pair[w * A.P + q] = cmul(prefw, S);
             }
         }
-        if (lane == 0) A.partial[tile * wpb + warp] = acc;
+    }
+    if (lane == 0) A.partial[tile * wpb + warp] = acc;
+}
+
+// One or several systems (different n, ne, walkers, snapshots) in one persistent
+// launch.  Blocks pull tiles from a global counter (no fixed stride, so no block
+// can be dealt only empty tiles); the tile space lists the systems in decreasing
+// cost per tile, so the largest tiles are handed out first and the small ones
+// fill the tail.
+struct BatchArgs {
+    int nsys;
+    int tab_bytes, ut_bytes, warp_bytes;  // maxima over the systems
+    int max_m;
+    int64_t tile_end[QCS_MAX_SYSTEMS];    // cumulative tile counts in queue order
+    unsigned long long *counter;
+    PairArgs sys[QCS_MAX_SYSTEMS];         // in queue order
+};
+
+__global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant__ BatchArgs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long next_tile;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
+    build_pair_table(tab, tri_count(B.max_m));
+    cd *Uts = reinterpret_cast<cd *>(smem_raw + B.tab_bytes);
+    unsigned char *wbase = smem_raw + B.tab_bytes + B.ut_bytes + (size_t)warp * B.warp_bytes;
+    const int64_t total = B.tile_end[B.nsys - 1];
+    for (;;) {
+        __syncthreads();  // every thread has read the previous tile index
+        if (threadIdx.x == 0) next_tile = (long long)atomicAdd(B.counter, 1ull);
+        __syncthreads();
+        const int64_t t = next_tile;
+        if (t >= total) break;
+        int s = 0;
+        while (t >= B.tile_end[s]) ++s;
+        const int64_t local = t - (s > 0 ? B.tile_end[s - 1] : 0);
+        const PairArgs &A = B.sys[s];
+        const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
+        run_tile(A, local, L, wbase, Uts, tab, warp, wpb, lane);
     }
 }
 
@@ -252,6 +196,8 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * NB * m);
+    A.off_pv = (int)o;
+    o = align16(o + (size_t)NB * (m / 2) * sizeof(cd));
     return o;
 }
 
@@ -259,8 +205,10 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
 
 int qcs_pair_warps_per_block() { return 4; }
 
-qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t st) {
-    PairArgs A;
+namespace {
+
+// Fill the per-system arguments and shared layout of one pair launch.
+void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     memset(&A, 0, sizeof(A));
     A.n = L.n;
     A.ne = L.ne;
@@ -276,20 +224,25 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
     const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
     A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * sizeof(cd));
-    // Node matrices per round: the largest count (at most kMaxNB, balanced rounds)
-    // for which two blocks of wpb warps fit on an SM, else one block.
-    const size_t sm_budget = ctx->smem_optin;  // per block
+    // Node matrices per round: the requested count, or by default the largest
+    // count (balanced rounds, at most kMaxNB) for which two blocks fit on an SM.
     int NB = 1;
-    for (int rounds = 1; rounds <= A.nev; ++rounds) {
-        int nb = (A.nev + rounds - 1) / rounds;
-        if (nb > kMaxNB) continue;
-        size_t wb = pair_warp_layout(A, nb);
-        size_t blk = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * wb + 1024;
-        if (2 * blk <= sm_budget + 1024) {
-            NB = nb;
-            break;
+    if (L.config > 0) {
+        NB = L.config < A.nev ? L.config : A.nev;
+        if (NB > kMaxNB) NB = kMaxNB;
+        while (NB > 1 && (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * pair_warp_layout(A, NB) > ctx->smem_optin)
+            --NB;
+    } else {
+        const size_t sm_budget = ctx->smem_optin;
+        for (int rounds = 1; rounds <= A.nev; ++rounds) {
+            int nb = (A.nev + rounds - 1) / rounds;
+            if (nb > kMaxNB) continue;
+            size_t blk = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * pair_warp_layout(A, nb) + 1024;
+            if (2 * blk <= sm_budget + 1024) {
+                NB = nb;
+                break;
+            }
         }
-        if (rounds == A.nev) NB = 1;
     }
     A.NB = NB;
     A.warp_bytes = (int)pair_warp_layout(A, NB);
@@ -305,19 +258,64 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
         A.wnode[k] = L.plan.wnode[k];
         A.gamma[k] = L.plan.gamma[k];
     }
-    size_t smem = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * A.warp_bytes;
-    if (smem > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "pair kernel: shared memory too large");
+}
+
+}  // namespace
+
+qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t st) {
+    return qcs_launch_pairs_batched(ctx, 1, &L, L.counter, st);
+}
+
+qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launch *Ls, unsigned long long *counter,
+                                    cudaStream_t st) {
+    if (nsys < 1 || nsys > QCS_MAX_SYSTEMS) return QCS_ERR_ARG;
+    BatchArgs B;
+    memset(&B, 0, sizeof(B));
+    B.nsys = nsys;
+    B.counter = counter;
+    // queue order: decreasing estimated cost of one tile
+    int order[QCS_MAX_SYSTEMS];
+    double cost[QCS_MAX_SYSTEMS];
+    for (int i = 0; i < nsys; ++i) {
+        order[i] = i;
+        cost[i] = qcs_overlap_flops_per_pair(Ls[i].n, Ls[i].ne, Ls[i].plan.N, Ls[i].plan.all ? 1u : 0u) *
+                  (double)Ls[i].chunk;
+    }
+    for (int i = 0; i < nsys; ++i)
+        for (int j = i + 1; j < nsys; ++j)
+            if (cost[order[j]] > cost[order[i]]) {
+                int t = order[i];
+                order[i] = order[j];
+                order[j] = t;
+            }
+    int64_t acc = 0;
+    for (int q = 0; q < nsys; ++q) {
+        const qcs_pair_launch &L = Ls[order[q]];
+        setup_pair_args(ctx, L, B.sys[q]);
+        acc += L.W * L.nchunks;
+        B.tile_end[q] = acc;
+        if (B.sys[q].tab_bytes > B.tab_bytes) B.tab_bytes = B.sys[q].tab_bytes;
+        if (B.sys[q].ut_bytes > B.ut_bytes) B.ut_bytes = B.sys[q].ut_bytes;
+        if (B.sys[q].warp_bytes > B.warp_bytes) B.warp_bytes = B.sys[q].warp_bytes;
+        if (B.sys[q].m > B.max_m) B.max_m = B.sys[q].m;
+    }
+    if (acc == 0) return QCS_OK;
+    const int wpb = qcs_pair_warps_per_block();
+    size_t smem = (size_t)B.tab_bytes + B.ut_bytes + (size_t)wpb * B.warp_bytes;
+    if (smem + 64 > ctx->smem_optin)  // + the kernel's static tile index
+        return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "batched kernel: shared memory too large");
     if (qcs_set_smem(ctx, (const void *)pair_overlap_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_overlap_kernel, wpb * 32, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_overlap_kernel, wpb * 32, smem) !=
+            cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    int64_t ntiles = L.W * L.nchunks;
     int64_t blocks = (int64_t)ctx->num_sms * per_sm;
-    if (blocks > ntiles) blocks = ntiles;
-    if (blocks < 1) blocks = 1;
+    if (blocks > acc) blocks = acc;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "batched counter reset");
     qcs_prof_begin(ctx, st);
-    pair_overlap_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(A);
+    pair_overlap_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(B);
     qcs_prof_end(ctx, st);
     return qcs_check_launch(ctx, "pair_overlap_kernel");
 }

@@ -4,6 +4,8 @@
 #pragma once
 #include "qcs_common.cuh"
 
+constexpr int kMaxNB = 8;  // node matrices per warp round, at most
+
 // tab[t] = (b << 8) | a for t = b(b-1)/2 + a, a < b  (pairs in packed-upper order).
 __device__ inline void build_pair_table(uint16_t *tab, int count) {
     for (int t = threadIdx.x; t < count; t += blockDim.x) {
@@ -101,5 +103,123 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
         }
         Bs[tri_index(ne + a, ne + b)] = cmk((oa != ob) ? -acc : acc, 0.0);
     }
+}
+
+
+// Pfaffians of nb node matrices B + wnode[v] D held in Ns (packed upper), m x m with
+// ne occupied rows first.  On return pf[v] holds pf(B + wnode[v] D).
+__device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnode, int nb,
+                                      const cd *__restrict__ Bs, cd *__restrict__ Ns,
+                               cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ inv,
+                               unsigned long long *__restrict__ best, int *__restrict__ ints,
+                               uint8_t *__restrict__ act0, uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
+                               cd *__restrict__ pv, int lane) {
+    const int S = m / 2;  // elimination steps; the signed pivots of node v go to pv[v*S + s]
+    const int d = (m - ne) / 2;
+    const int T = tri_count(m);
+    int *pos = ints, *kk = ints + kMaxNB, *pp = ints + 2 * kMaxNB;
+    for (int e = lane; e < nb * T; e += 32) {
+        int v = e / T, t = e - v * T;
+        Ns[v * T + t] = Bs[t];
+    }
+    for (int e = lane; e < nb * m; e += 32) {
+        int v = e / m, a = e - v * m;
+        act0[v * m + a] = (uint8_t)a;
+    }
+    __syncwarp();
+    for (int e = lane; e < nb * d; e += 32) {
+        int v = e / d, i = e - v * d;
+        cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
+        *x = cadd(*x, wnode[v]);
+    }
+    __syncwarp();
+    uint8_t *cur = act0, *nxt = act1;
+    for (int r = m, s = 0; r >= 2; r -= 2, ++s) {
+        // pivot: largest |A_{k,i}| over the active row of k = cur[0]
+        if (lane < nb) best[lane] = 0ull;
+        __syncwarp();
+        const int rc = r - 1;
+        for (int e = lane; e < nb * rc; e += 32) {
+            int v = e / rc, a = 1 + (e - v * rc);
+            int k = cur[v * m], i = cur[v * m + a];
+            unsigned key = pivot_key(Ns[v * T + tri_index(k, i)]);
+            atomicMax(&best[v], ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a));
+        }
+        __syncwarp();
+        if (lane < nb) {
+            int a = 0xffff - (int)(best[lane] & 0xffffull);
+            int k = cur[lane * m], p = cur[lane * m + a];
+            cd piv = Ns[lane * T + tri_index(k, p)];
+            pv[lane * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
+            inv[lane] = cinv(piv);
+            pos[lane] = a;
+            kk[lane] = k;
+            pp[lane] = p;
+        }
+        __syncwarp();
+        if (r == 2) break;
+        // Gauss vectors over the remaining indices (original order kept)
+        const int rv = r - 2;
+        for (int e = lane; e < nb * rv; e += 32) {
+            int v = e / rv, a2 = e - v * rv;
+            int a = a2 + 1 + ((a2 + 1 >= pos[v]) ? 1 : 0);
+            int i = cur[v * m + a], k = kk[v], p = pp[v];
+            const cd *Nv = Ns + v * T;
+            cd u = Nv[tri_index(k, i)];          // A_{k,i}; A_{i,k} = -u
+            cd ut = cnegmul(u, inv[v]);          // A_{i,k} / A_{k,p}
+            cd vv = (i < p) ? Nv[tri_index(i, p)] : flip_if(Nv[tri_index(p, i)], true);  // A_{i,p}
+            Uv[v * m + a2] = ut;
+            Vv[v * m + a2] = vv;
+            nxt[v * m + a2] = (uint8_t)i;
+        }
+        __syncwarp();
+        // rank-2 update A_ij -= ut_i v_j - v_i ut_j on the remaining pairs
+        const int Tr = tri_count(rv);
+        for (int e = lane; e < nb * Tr; e += 32) {
+            int v = e / Tr, t = e - v * Tr;
+            int a, b;
+            pair_of(tab, t, a, b);
+            int i = nxt[v * m + a], j = nxt[v * m + b];
+            cd *x = Ns + v * T + tri_index(i, j);
+            cd y = *x;
+            const cd *U_ = Uv + v * m, *V_ = Vv + v * m;
+            cfms(y, U_[a], V_[b]);
+            cfma(y, V_[a], U_[b]);
+            *x = y;
+        }
+        __syncwarp();
+        uint8_t *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    // pf[v] = prod_s pv[v][s]: pairwise tree over the lanes; each level reads into
+    // registers, then stores after a __syncwarp (nb * half <= 8 * 23 / 2 < 96 items)
+    for (int len = S; len > 1; len = (len + 1) / 2) {
+        const int half = len / 2;
+        cd r[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int e = lane + 32 * t;
+            if (e < nb * half) {
+                const int v = e / half, i = e - v * half;
+                r[t] = cmul(pv[v * S + 2 * i], pv[v * S + 2 * i + 1]);
+            }
+        }
+        cd tail = cmk(0.0, 0.0);
+        if ((len & 1) && lane < nb) tail = pv[lane * S + len - 1];
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int e = lane + 32 * t;
+            if (e < nb * half) {
+                const int v = e / half, i = e - v * half;
+                pv[v * S + i] = r[t];
+            }
+        }
+        if ((len & 1) && lane < nb) pv[lane * S + half] = tail;
+        __syncwarp();
+    }
+    if (lane < nb) pf[lane] = pv[lane * S];
+    __syncwarp();
 }
 

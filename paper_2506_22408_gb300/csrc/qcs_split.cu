@@ -1,0 +1,459 @@
+// qcs_split.cu -- split-precision overlaps: the congruence on tensor cores.
+//
+// The congruence of Eq. (b_mat), T = Ut Qt^T (walker rows times the snapshot's
+// complexified rows), is a dense contraction.  In real form, with Ut = A + iB and
+// Qt = C + iD,
+//     [T_re; T_im] = M_w N_q^T,   M_w = [[A, -B], [B, A]]  (2n x 2n),
+//                                 N_q = [C, D]             (2n x 2n, rows c),
+// so a tile of 4 walkers x 8 snapshots is one 128 x 256 x 32 GEMM (n <= 16, rows
+// and K padded to 32).  It runs on the 5th-generation tensor cores as three
+// tcgen05.mma kind::tf32 passes over TF32 hi/lo splits of both operands
+// (hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory).  The operand
+// slabs are precomputed once per walker and per snapshot in the K-major core-matrix
+// layout and staged into shared memory by bulk asynchronous copies that complete
+// on an mbarrier.  Each warp then reads its walker's 32 accumulator lanes, forms
+// the selected covariance B^(s) in FP32, and evaluates the Pfaffians of the node
+// matrices in FP64 exactly as the FP64 path does.
+//
+// Accuracy: T carries the ~2^-21 relative error of the split TF32 products
+// accumulated in FP32, B^(s) an FP32 rounding of its 2n-term sums; the Pfaffian
+// elimination, its pivoting and the node sums stay FP64.
+#include "qcs_internal.h"
+#include "qcs_pair.cuh"
+#include "qcs_tc.cuh"
+
+using namespace qcs_tc;
+
+namespace {
+
+constexpr int kK = 32;           // padded contraction length (2n <= 32)
+constexpr int kRows = 32;        // padded rows per walker / snapshot
+constexpr int kSlabBytes = kRows * kK * 4;  // one operand slab (4 KB)
+constexpr int kWalkersPerTile = 4;          // M = 128
+constexpr int kSnapsPerTile = 8;            // N = 256
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kWaitIter = 1u << 26;     // bounded mbarrier waits
+
+// hi/lo TF32 split of x written to slabs at (row, k)
+__device__ __forceinline__ void put_split(float *hi, float *lo, int row, int k, double x) {
+    const float h = to_tf32((float)x);
+    const float l = to_tf32((float)(x - (double)h));
+    const uint32_t o = kmajor_offset(row, k, kK) / 4;
+    hi[o] = h;
+    lo[o] = l;
+}
+
+// Snapshot slabs N_q (rows c < 2n: [Re Qt[c][0..n), Im Qt[c][0..n)]); zero padding.
+__global__ void split_snapshots_kernel(int n, int64_t P, const cd *__restrict__ Qt, float *__restrict__ hi,
+                                       float *__restrict__ lo) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P * kRows * kK;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / (kRows * kK);
+        const int r = (int)(e % (kRows * kK)) / kK, k = (int)(e % kK);
+        double x = 0.0;
+        if (r < 2 * n && k < 2 * n) {
+            const cd v = Qt[q * 2 * n * n + r * n + (k % n)];
+            x = k < n ? v.x : v.y;
+        }
+        put_split(hi + q * (kSlabBytes / 4), lo + q * (kSlabBytes / 4), r, k, x);
+    }
+}
+
+// Walker slabs M_w: row j < n: [A_j, -B_j], row n + j: [B_j, A_j] with Ut = A + iB.
+__global__ void split_walkers_kernel(int n, int64_t W, const cd *__restrict__ Ut, float *__restrict__ hi,
+                                     float *__restrict__ lo) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < W * kRows * kK;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = e / (kRows * kK);
+        const int r = (int)(e % (kRows * kK)) / kK, k = (int)(e % kK);
+        double x = 0.0;
+        if (r < 2 * n && k < 2 * n) {
+            const int j = r % n, kk = k % n;
+            const cd u = Ut[w * n * n + j * n + kk];
+            if (r < n) x = k < n ? u.x : -u.y;
+            else x = k < n ? u.y : u.x;
+        }
+        put_split(hi + w * (kSlabBytes / 4), lo + w * (kSlabBytes / 4), r, k, x);
+    }
+}
+
+struct SplitArgs {
+    int n, ne, m, d, nev, NB, all;
+    int64_t W, P;
+    int nchunks;                 // snapshot chunks of kSnapsPerTile
+    int64_t ngroups;             // walker groups of kWalkersPerTile
+    int region_bytes;            // operand / workspace union
+    int warp_bytes;
+    int off_T, off_B, off_U, off_V, off_pf, off_inv, off_best, off_int, off_act, off_pv;
+    const float *Mhi, *Mlo;      // walker slabs
+    const float *Nhi, *Nlo;      // snapshot slabs
+    const cd *pref;
+    const int *idx;
+    const int *d_count;
+    cd *partial;                 // W x nchunks
+    cd *per_pair;
+    unsigned long long *counter;
+    unsigned *status;
+    cd wnode[QCS_MAX_NODES];
+    cd gamma[QCS_MAX_NODES];
+};
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// B^(s) (FP64 packed upper) from T (FP32 complex, row stride ld) in FP32 arithmetic.
+__device__ void build_B_f32(int n, int ne, const float2 *__restrict__ Ts, int ld, cd *__restrict__ Bs,
+                            const uint16_t *__restrict__ tab, int lane) {
+    const int d = n - ne;
+    const int c1 = tri_count(ne);
+    for (int e = lane; e < c1; e += 32) {
+        int a, b;
+        pair_of(tab, e, a, b);
+        const float2 *Ta = Ts + a * ld, *Tb = Ts + b * ld;
+        float ax = 0.f, ay = 0.f;
+        for (int k = 0; k < n; ++k) {
+            const float2 p = Ta[2 * k], q = Tb[2 * k + 1], r = Ta[2 * k + 1], s = Tb[2 * k];
+            ax = fmaf(p.x, q.x, ax);
+            ax = fmaf(-p.y, q.y, ax);
+            ay = fmaf(p.x, q.y, ay);
+            ay = fmaf(p.y, q.x, ay);
+            ax = fmaf(-r.x, s.x, ax);
+            ax = fmaf(r.y, s.y, ax);
+            ay = fmaf(-r.x, s.y, ay);
+            ay = fmaf(-r.y, s.x, ay);
+        }
+        Bs[tri_index(a, b)] = cmk(ax, ay);
+    }
+    const int twod = 2 * d, c2 = ne * twod;
+    for (int e = lane; e < c2; e += 32) {
+        const int a = e / twod, r = e - a * twod, j = ne + (r >> 1);
+        const bool odd = r & 1;
+        const float2 *Ta = Ts + a * ld, *Tj = Ts + j * ld;
+        float ax = 0.f, ay = 0.f;
+        for (int k = 0; k < n; ++k) {
+            const float2 t0 = Tj[2 * k], t1 = Tj[2 * k + 1];
+            const float x0 = odd ? t0.y : t0.x, x1 = odd ? t1.y : t1.x;
+            const float2 a0 = Ta[2 * k], a1 = Ta[2 * k + 1];
+            ax = fmaf(a0.x, x1, ax);
+            ay = fmaf(a0.y, x1, ay);
+            ax = fmaf(-a1.x, x0, ax);
+            ay = fmaf(-a1.y, x0, ay);
+        }
+        Bs[tri_index(a, ne + r)] = odd ? cmk(-ax, -ay) : cmk(ax, ay);
+    }
+    const int c3 = tri_count(twod);
+    for (int e = lane; e < c3; e += 32) {
+        int a, b;
+        pair_of(tab, e, a, b);
+        const float2 *Ta = Ts + (ne + (a >> 1)) * ld, *Tb = Ts + (ne + (b >> 1)) * ld;
+        const bool oa = a & 1, ob = b & 1;
+        float acc = 0.f;
+        for (int k = 0; k < n; ++k) {
+            const float2 a0 = Ta[2 * k], a1 = Ta[2 * k + 1], b0 = Tb[2 * k], b1 = Tb[2 * k + 1];
+            acc = fmaf(oa ? a0.y : a0.x, ob ? b1.y : b1.x, acc);
+            acc = fmaf(-(oa ? a1.y : a1.x), ob ? b0.y : b0.x, acc);
+        }
+        Bs[tri_index(ne + a, ne + b)] = cmk((oa != ob) ? -acc : acc, 0.0);
+    }
+}
+
+__global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__ SplitArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
+    __shared__ long long next_tile;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = A.n;
+    // region: operands [A_hi 16K | A_lo 16K | B_hi 32K | B_lo 32K], later the warps' workspaces
+    unsigned char *region = smem_raw;
+    float *Ahi = reinterpret_cast<float *>(region);
+    float *Alo = Ahi + kWalkersPerTile * kSlabBytes / 4;
+    float *Bhi = Alo + kWalkersPerTile * kSlabBytes / 4;
+    float *Blo = Bhi + kSnapsPerTile * kSlabBytes / 4;
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw + A.region_bytes);
+    build_pair_table(tab, tri_count(A.m));
+    unsigned char *wbase = region + (size_t)warp * A.warp_bytes;
+    float2 *Ts = reinterpret_cast<float2 *>(wbase + A.off_T);
+    cd *Bs = reinterpret_cast<cd *>(wbase + A.off_B);
+    cd *Ns = reinterpret_cast<cd *>(wbase);  // node matrices start the warp region (T is consumed first)
+    cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
+    cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
+    cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
+    cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(wbase + A.off_best);
+    int *ints = reinterpret_cast<int *>(wbase + A.off_int);
+    uint8_t *act0 = wbase + A.off_act;
+    uint8_t *act1 = act0 + A.NB * A.m;
+    cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
+    const int ldT = 2 * n + 1;
+
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, kTmemCols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&mbar_load, 1);
+        mbar_init(&mbar_mma, 1);
+        abort_flag = 0;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
+    const int64_t ntiles = A.ngroups * A.nchunks;
+    uint32_t phase = 0;
+    uint32_t last_phase = 0;
+    for (;;) {
+        fence_proxy_async_smem();  // this thread's workspace writes precede the next bulk copies
+        __syncthreads();           // previous tile fully consumed (workspaces overlay the operands)
+        if (tid == 0) next_tile = (long long)atomicAdd(A.counter, 1ull);
+        __syncthreads();
+        const int64_t t = next_tile;
+        if (t >= ntiles || abort_flag) break;
+        const int64_t g = t / A.nchunks;
+        const int ch = (int)(t - g * A.nchunks);
+        const int64_t p0 = (int64_t)ch * kSnapsPerTile;
+        if (p0 >= L) {  // no parity +1 snapshot left in this chunk: nothing to accumulate
+            if (lane == 0 && g * kWalkersPerTile + warp < A.W)
+                A.partial[(g * kWalkersPerTile + warp) * A.nchunks + ch] = cmk(0.0, 0.0);
+            continue;
+        }
+        const int nq = (int)((L - p0) < kSnapsPerTile ? (L - p0) : kSnapsPerTile);
+        // stage the operand slabs (bulk asynchronous copies on mbar_load)
+        if (tid == 0) {
+            uint32_t bytes = 0;
+            for (int s = 0; s < kWalkersPerTile; ++s) bytes += (g * kWalkersPerTile + s < A.W) ? 2 * kSlabBytes : 0;
+            bytes += 2 * kSlabBytes * nq;
+            mbar_expect_tx(&mbar_load, bytes);
+            for (int s = 0; s < kWalkersPerTile; ++s) {
+                const int64_t w = g * kWalkersPerTile + s;
+                if (w >= A.W) continue;
+                bulk_copy(Ahi + s * kSlabBytes / 4, A.Mhi + w * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+                bulk_copy(Alo + s * kSlabBytes / 4, A.Mlo + w * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+            }
+            for (int q = 0; q < nq; ++q) {
+                const int64_t sq = A.all ? p0 + q : (int64_t)A.idx[p0 + q];
+                bulk_copy(Bhi + q * kSlabBytes / 4, A.Nhi + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+                bulk_copy(Blo + q * kSlabBytes / 4, A.Nlo + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+            }
+        }
+        last_phase = phase;
+        bool ok = mbar_wait_bounded(&mbar_load, phase, kWaitIter);
+        if (ok && tid == 0) {
+            fence_after_sync();
+            const uint32_t id = idesc_tf32(128, 256);
+            const float *Ap[3] = {Ahi, Ahi, Alo};
+            const float *Bp[3] = {Bhi, Blo, Bhi};
+            for (int pass = 0; pass < 3; ++pass)
+                for (int s = 0; s < kK / 8; ++s) {
+                    const uint64_t ad = desc_kmajor(Ap[pass] + 64 * s, 128, 32 * kK);
+                    const uint64_t bd = desc_kmajor(Bp[pass] + 64 * s, 128, 32 * kK);
+                    mma_tf32(tbase, ad, bd, id, (pass > 0 || s > 0) ? 1u : 0u);
+                }
+            mma_commit(&mbar_mma);
+        }
+        if (ok) ok = mbar_wait_bounded(&mbar_mma, phase, kWaitIter);
+        phase ^= 1u;
+        if (!ok) {
+            if (tid == 0) {
+                abort_flag = 1;
+                raise_status(A.status, QCS_ERR_TIMEOUT);
+            }
+            continue;  // every thread leaves through the abort check above
+        }
+        fence_after_sync();
+        __syncthreads();  // all MMAs complete: the operand region becomes the warps' workspaces
+        const int64_t w = g * kWalkersPerTile + warp;
+        cd acc = cmk(0.0, 0.0);
+        for (int q = 0; q < nq; ++q) {
+            // T rows of this warp's walker for snapshot q: lane r holds row r of [T_re; T_im]
+            float v0[16], v1[16];
+            const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * q);
+            tmem_ld16(ta, v0);
+            tmem_ld16(ta + 16, v1);
+            tmem_ld_wait();
+            __syncwarp();
+            if (lane < 2 * n) {
+                const int j = lane % n;
+                const bool im = lane >= n;
+                for (int c = 0; c < 2 * n; ++c) {
+                    const float x = c < 16 ? v0[c] : v1[c - 16];
+                    if (im) Ts[j * ldT + c].y = x;
+                    else Ts[j * ldT + c].x = x;
+                }
+            }
+            __syncwarp();
+            if (w >= A.W) continue;
+            build_B_f32(n, A.ne, Ts, ldT, Bs, tab, lane);
+            __syncwarp();
+            cd S = cmk(0.0, 0.0);
+            for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                node_pfaffians(A.m, A.ne, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, best, ints, act0, act1, tab, pv,
+                               lane);
+                if (lane == 0)
+                    for (int vv = 0; vv < nb; ++vv) cfma(S, A.gamma[k0 + vv], pf[vv]);
+                __syncwarp();
+            }
+            if (lane == 0) {
+                if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
+                acc = cadd(acc, S);
+                if (A.per_pair) {
+                    const int64_t sq = A.all ? p0 + q : (int64_t)A.idx[p0 + q];
+                    A.per_pair[w * A.P + sq] = cmul(A.pref[w], S);
+                }
+            }
+        }
+        if (lane == 0 && w < A.W) A.partial[w * A.nchunks + ch] = acc;
+        fence_before_sync();
+    }
+    if (abort_flag && tid == 0) {  // a wait gave up: let the copies and MMAs in flight land first
+        mbar_wait_bounded(&mbar_load, last_phase, kWaitIter);
+        mbar_wait_bounded(&mbar_mma, last_phase, kWaitIter);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) tmem_dealloc(tbase, kTmemCols);
+}
+
+// Per-warp workspace of the split kernel for nb node matrices.
+size_t split_warp_layout(SplitArgs &A, int NB) {
+    const int n = A.n, m = A.m, T = tri_count(m);
+    size_t nodes = (size_t)NB * T * sizeof(cd);
+    size_t tbytes = (size_t)n * (2 * n + 1) * sizeof(float2);
+    // T is consumed (into B) before the node matrices are written: they may share
+    size_t o = align16(nodes > tbytes ? nodes : tbytes);
+    A.off_T = 0;
+    A.off_B = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_U = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_V = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_pf = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(cd));
+    A.off_inv = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(cd));
+    A.off_best = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(unsigned long long));
+    A.off_int = (int)o;
+    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
+    A.off_act = (int)o;
+    o = align16(o + (size_t)2 * NB * m);
+    A.off_pv = (int)o;
+    o = align16(o + (size_t)NB * (m / 2) * sizeof(cd));
+    return o;
+}
+
+}  // namespace
+
+qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st) {
+    if (s->split_hi) return QCS_OK;
+    const size_t bytes = (size_t)(s->P > 0 ? s->P : 1) * kSlabBytes;
+    cudaError_t e = cudaMalloc(&s->split_hi, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->split_lo, bytes);
+    if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "split snapshot slabs: cudaMalloc");
+    if (s->P > 0) {
+        int64_t tot = s->P * kRows * kK;
+        int64_t blocks = (tot + 255) / 256;
+        if (blocks > (int64_t)ctx->num_sms * 32) blocks = (int64_t)ctx->num_sms * 32;
+        split_snapshots_kernel<<<(unsigned)blocks, 256, 0, st>>>(s->n, s->P, s->Qt, (float *)s->split_hi,
+                                                                 (float *)s->split_lo);
+    }
+    return qcs_check_launch(ctx, "split_snapshots_kernel");
+}
+
+size_t qcs_split_walker_bytes(int64_t W) { return (size_t)(W > 0 ? W : 1) * kSlabBytes; }
+
+qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st) {
+    const int n = L.n;
+    if (n > 16) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split precision supports n <= 16");
+    {
+        int64_t tot = L.W * kRows * kK;
+        int64_t blocks = (tot + 255) / 256;
+        if (blocks > (int64_t)ctx->num_sms * 32) blocks = (int64_t)ctx->num_sms * 32;
+        if (blocks > 0) split_walkers_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, L.W, L.Ut, Mhi, Mlo);
+        qcs_status r = qcs_check_launch(ctx, "split_walkers_kernel");
+        if (r != QCS_OK) return r;
+    }
+    SplitArgs A;
+    memset(&A, 0, sizeof(A));
+    A.n = n;
+    A.ne = L.ne;
+    A.m = 2 * n - L.ne;
+    A.d = n - L.ne;
+    A.nev = L.plan.nev;
+    A.all = L.plan.all;
+    A.W = L.W;
+    A.P = L.P;
+    A.nchunks = L.nchunks;
+    A.ngroups = (L.W + kWalkersPerTile - 1) / kWalkersPerTile;
+    const int T = tri_count(A.m);
+    const size_t operands = (size_t)(2 * kWalkersPerTile + 2 * kSnapsPerTile) * kSlabBytes;
+    const size_t tab = align16((size_t)T * sizeof(uint16_t));
+    // largest node round (<= kMaxNB, balanced) whose four workspaces fit in the operand
+    // region, so that two blocks fit per SM
+    int NB = 1;
+    for (int rounds = 1; rounds <= A.nev; ++rounds) {
+        int nb = (A.nev + rounds - 1) / rounds;
+        if (nb > kMaxNB) continue;
+        if ((size_t)kWalkersPerTile * split_warp_layout(A, nb) <= operands) {
+            NB = nb;
+            break;
+        }
+    }
+    if (L.config > 0) NB = L.config < A.nev ? (L.config < kMaxNB ? L.config : kMaxNB) : A.nev;
+    A.NB = NB;
+    A.warp_bytes = (int)split_warp_layout(A, NB);
+    size_t region = (size_t)kWalkersPerTile * A.warp_bytes;
+    if (region < operands) region = operands;
+    A.region_bytes = (int)align16(region);
+    A.Mhi = Mhi;
+    A.Mlo = Mlo;
+    A.Nhi = (const float *)L.s->split_hi;
+    A.Nlo = (const float *)L.s->split_lo;
+    A.pref = L.pref;
+    A.idx = L.s->idx;
+    A.d_count = L.s->d_count;
+    A.partial = L.partial;
+    A.per_pair = L.per_pair;
+    A.counter = L.counter;
+    A.status = ctx->d_status;
+    for (int k = 0; k < L.plan.nev; ++k) {
+        A.wnode[k] = L.plan.wnode[k];
+        A.gamma[k] = L.plan.gamma[k];
+    }
+    const size_t smem = (size_t)A.region_bytes + tab;
+    // + the kernel's static words; at least 76 KB per block keeps the blocks per SM at two,
+    // which is what the 2 x 256 tensor-memory columns allow
+    if (smem + 1024 > ctx->smem_optin || smem < (76u << 10))
+        return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split kernel: shared memory");
+    if (qcs_set_smem(ctx, (const void *)split_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_pair_kernel, 128, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (per_sm > 2) per_sm = 2;  // tensor memory: 2 x 256 columns per SM
+    const int64_t ntiles = A.ngroups * A.nchunks;
+    int64_t blocks = (int64_t)ctx->num_sms * per_sm;
+    if (blocks > ntiles) blocks = ntiles;
+    if (blocks < 1) blocks = 1;
+    if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return qcs_fail(ctx, QCS_ERR_CUDA, "split tile counter reset");
+    qcs_prof_begin(ctx, st);
+    split_pair_kernel<<<(unsigned)blocks, 128, smem, st>>>(A);
+    qcs_prof_end(ctx, st);
+    return qcs_check_launch(ctx, "split_pair_kernel");
+}

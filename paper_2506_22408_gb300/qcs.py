@@ -10,6 +10,7 @@ raise.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import threading
 
@@ -31,7 +32,10 @@ EXPORTED = [
     "qcs_build_snapshots", "qcs_snapshots_free", "qcs_snapshots_parity", "qcs_snapshots_count",
     "qcs_snapshots_modes", "qcs_overlap", "qcs_overlap_grad", "qcs_force_bias", "qcs_overlap_flops_per_pair",
     "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair", "qcs_overlap_noalloc",
+    "qcs_autotune", "qcs_set_config", "qcs_overlap_batched",
 ]
+MAX_SYSTEMS = 8
+TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -42,9 +46,14 @@ class QCSError(RuntimeError):
         self.code = code
 
 
+class _System(ctypes.Structure):
+    _fields_ = [("snapshots", ctypes.c_void_p), ("ne", ctypes.c_int), ("W", ctypes.c_int64),
+                ("d_walkers", ctypes.c_void_p), ("d_overlap", ctypes.c_void_p)]
+
+
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nodes", ctypes.c_int), ("flags", ctypes.c_uint),
-                ("reserved", ctypes.c_int)]
+                ("config", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -84,6 +93,9 @@ def load(build_if_missing: bool = True):
         lib.qcs_overlap_flops_per_pair.restype = f64
         lib.qcs_grad_flops_per_pair.argtypes = [i32, i32, i32, u32]
         lib.qcs_grad_flops_per_pair.restype = f64
+        lib.qcs_overlap_batched.argtypes = [P, i32, ctypes.POINTER(_System), ctypes.POINTER(_Opts), P]
+        lib.qcs_autotune.argtypes = [P, i32, i32, i32, u32, ctypes.POINTER(i32)]
+        lib.qcs_set_config.argtypes = [P, i32, i32, i32, u32, i32]
         lib.qcs_overlap_noalloc.argtypes = [i32, i32, i64, P, P, i64, P, P, P, P]
         lib.qcs_profile_enable.argtypes = [P, i32]
         lib.qcs_profile_read.argtypes = [P, ctypes.POINTER(f64), ctypes.POINTER(i64)]
@@ -122,6 +134,31 @@ class Context:
         if rc != QCS_OK:
             raise QCSError(rc, "qcs_create failed")
         self.h = h
+        self.gpu_name = torch.cuda.get_device_name(self.device)
+        for key, cfg in _read_cache().get(self.gpu_name, {}).items():
+            n, ne, nodes, flags = (int(x) for x in key.split(","))
+            self.lib.qcs_set_config(self.h, n, ne, nodes, flags, int(cfg))
+
+    def autotune(self, n: int, ne: int, nodes: int = 0, flags: int = 0, save: bool = True) -> int:
+        """Time the pair-kernel configurations for these sizes on this GPU, keep the
+        fastest in the context, and (save=True) record it in the tuning cache."""
+        cfg = ctypes.c_int()
+        self.check(self.lib.qcs_autotune(self.h, n, ne, nodes, flags, ctypes.byref(cfg)))
+        if save:
+            cache = _read_cache()
+            cache.setdefault(self.gpu_name, {})[f"{n},{ne},{nodes},{flags}"] = cfg.value
+            try:
+                os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
+                tmp = TUNE_CACHE + f".tmp{os.getpid()}"
+                with open(tmp, "w") as f:
+                    json.dump(cache, f, indent=1, sort_keys=True)
+                os.replace(tmp, TUNE_CACHE)
+            except OSError:
+                pass
+        return cfg.value
+
+    def set_config(self, n: int, ne: int, config: int, nodes: int = 0, flags: int = 0):
+        self.check(self.lib.qcs_set_config(self.h, n, ne, nodes, flags, config))
 
     def check(self, rc):
         if rc != QCS_OK:
@@ -152,6 +189,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def _read_cache() -> dict:
+    try:
+        with open(TUNE_CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 class Snapshots:
@@ -186,12 +231,12 @@ class Snapshots:
             pass
 
 
-def _opts(nodes=0, flags=0, precision=QCS_FP64):
-    return _Opts(int(precision), int(nodes), int(flags), 0)
+def _opts(nodes=0, flags=0, precision=QCS_FP64, config=0):
+    return _Opts(int(precision), int(nodes), int(flags), int(config))
 
 
 def overlap(ctx: Context, snaps: Snapshots, walkers: torch.Tensor, per_pair: bool = False, nodes: int = 0,
-            flags: int = 0, precision: int = QCS_FP64):
+            flags: int = 0, precision: int = QCS_FP64, config: int = 0):
     """<Psi_T|phi_w> for walkers (W, n, ne) complex128; returns (overlap[W], per_pair[W, P] or None)."""
     _need_cuda(walkers, "walkers", torch.complex128)
     W, n, ne = walkers.shape
@@ -200,10 +245,30 @@ def overlap(ctx: Context, snaps: Snapshots, walkers: torch.Tensor, per_pair: boo
     dev = walkers.device
     out = torch.empty(W, dtype=torch.complex128, device=dev)
     pp = torch.empty((W, snaps.P), dtype=torch.complex128, device=dev) if per_pair else None
-    o = _opts(nodes, flags, precision)
+    o = _opts(nodes, flags, precision, config)
     ctx.check(ctx.lib.qcs_overlap(ctx.h, snaps.h, ne, W, _ptr(walkers), _ptr(out), _ptr(pp), ctypes.byref(o),
                                   _stream()))
     return out, pp
+
+
+def overlap_batched(ctx: Context, systems, nodes: int = 0, flags: int = 0, outs=None):
+    """Overlaps of several systems [(snaps, walkers), ...] in one pair-kernel launch.
+    Returns a list of overlap tensors (or fills ``outs``)."""
+    if not 1 <= len(systems) <= MAX_SYSTEMS:
+        raise ValueError(f"1..{MAX_SYSTEMS} systems")
+    arr = (_System * len(systems))()
+    res = []
+    for i, (snaps, walkers) in enumerate(systems):
+        _need_cuda(walkers, "walkers", torch.complex128)
+        W, n, ne = walkers.shape
+        if n != snaps.n:
+            raise ValueError("walker size does not match its snapshot set")
+        out = outs[i] if outs is not None else torch.empty(W, dtype=torch.complex128, device=walkers.device)
+        arr[i] = _System(snaps.h.value, ne, W, walkers.data_ptr(), out.data_ptr())
+        res.append(out)
+    o = _opts(nodes, flags)
+    ctx.check(ctx.lib.qcs_overlap_batched(ctx.h, len(systems), arr, ctypes.byref(o), _stream()))
+    return res
 
 
 def overlap_grad(ctx: Context, snaps: Snapshots, walkers: torch.Tensor, nodes: int = 0, flags: int = 0):

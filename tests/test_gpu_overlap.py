@@ -198,3 +198,22 @@ def test_paper_shaped_full_size_sampled(ctx):
     check_walkers(ov[sel], oo, sc)
     # per-walker overlap equals the mean of the per-pair outputs
     assert np.allclose(ov, pp.mean(axis=1), rtol=0, atol=1e-12 * np.abs(pp).mean())
+
+
+def test_every_kernel_configuration_agrees(ctx):
+    """Every node-round size of the pair kernel gives the same overlaps, and the
+    autotuner records one of them."""
+    rng = np.random.default_rng(13)
+    n, ne, W, P = 16, 8, 9, 70
+    data = dict(Phi=synth.walkers(rng, n, ne, W), Q=synth.haar_orthogonal(rng, 2 * n, P),
+                b=synth.uniform_bits(rng, n, P))
+    oo, opp, sc, _ = orc.overlap(data["Phi"], data["Q"], data["b"], per_pair=True)
+    for cfg in range(1, 6):
+        ov, pp, par, st = run_gpu(ctx, data, config=cfg)
+        assert st == 0
+        check_pairs(pp, opp, sc, par)
+        check_walkers(ov, oo, sc)
+    best = ctx.autotune(n, ne, save=False)
+    assert 1 <= best <= 5
+    ov, pp, par, st = run_gpu(ctx, data)
+    check_pairs(pp, opp, sc, par)

@@ -1,0 +1,80 @@
+"""Split-precision overlaps (QCS_TF32X3): the congruence T = U^T Qt^T on tensor
+cores (tcgen05 kind::tf32, three hi/lo passes, FP32 accumulation), B^(s) in
+FP32, the Pfaffians in FP64.
+
+Stated bound: per pair |o_split - o_oracle| <= 2e-5 * s_p, with s_p the magnitude
+of the pair's terms before cancellation (from the oracle).  Derivation: the
+split TF32 products carry a relative error of about 2^-21 (two 11-bit halves of
+each operand, FP32 accumulation over 2n = 32 terms), B^(s) adds FP32 rounding of
+2n-term sums of |T| ~ 1 entries (~2e-6), and the Pfaffian at each node is a
+multilinear form of degree m/2 = 12 in B, which multiplies the relative
+perturbation by at most m/2 for a well-conditioned elimination; the node sum
+and the weights enter through s_p.  The measured maxima sit well below.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.oracle as orc
+from paper_2506_22408_gb300 import qcs, synth
+
+pytestmark = pytest.mark.gpu
+BOUND = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return qcs.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n,ne,W,P", [(16, 8, 13, 91), (16, 4, 6, 40), (12, 6, 7, 45), (8, 4, 9, 61), (10, 4, 5, 23),
+                                      (16, 16, 5, 30)])
+def test_split_matches_oracle_within_bound(ctx, n, ne, W, P):
+    rng = np.random.default_rng(3000 + 10 * n + ne)
+    Q = synth.haar_orthogonal(rng, 2 * n, P)
+    b = synth.uniform_bits(rng, n, P)
+    Phi = synth.walkers(rng, n, ne, W)
+    s = qcs.Snapshots(ctx, dev(Q), dev(b))
+    ov, pp = qcs.overlap(ctx, s, dev(Phi), per_pair=True, precision=qcs.QCS_TF32X3)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    oo, opp, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    par = s.parity().cpu().numpy()
+    ok = par == 1
+    pp = pp.cpu().numpy()
+    err = np.abs(pp[:, ok] - opp[:, ok]) / sc[:, ok]
+    assert err.max() <= BOUND, err.max()
+    assert np.all(pp[:, ~ok] == 0)
+    # the split path is not the FP64 path: its error is visible but bounded
+    werr = np.abs(ov.cpu().numpy() - oo) / sc.mean(axis=1)
+    assert werr.max() <= BOUND
+
+
+def test_split_agrees_with_fp64_path_and_is_deterministic(ctx):
+    wl = synth.Workload("t", 16, 8, 37, 203)
+    d = wl.generate(seed=4)
+    s = qcs.Snapshots(ctx, dev(d["Q"]), dev(d["b"]))
+    Phi = dev(d["Phi"])
+    o64, p64 = qcs.overlap(ctx, s, Phi, per_pair=True)
+    o1, p1 = qcs.overlap(ctx, s, Phi, per_pair=True, precision=qcs.QCS_TF32X3)
+    o2, p2 = qcs.overlap(ctx, s, Phi, per_pair=True, precision=qcs.QCS_TF32X3)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2) and torch.equal(p1, p2)
+    scale = p64.abs().mean(dim=1)
+    assert ((o1 - o64).abs() / scale).max().item() <= BOUND
+
+
+def test_split_rejects_large_n(ctx):
+    n = 20
+    Q = torch.from_numpy(synth.haar_orthogonal(np.random.default_rng(0), 2 * n, 4)).cuda()
+    s = qcs.Snapshots(ctx, Q, torch.zeros((4, n), dtype=torch.uint8, device="cuda"))
+    with pytest.raises(qcs.QCSError) as e:
+        qcs.overlap(ctx, s, torch.zeros((2, n, 10), dtype=torch.complex128, device="cuda"),
+                    precision=qcs.QCS_TF32X3)
+    assert e.value.code == 32
