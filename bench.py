@@ -44,6 +44,18 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
+def max_over_ranks(t: float, ws: int) -> float:
+    """Largest of a per-rank time over all ranks (the whole job ends with the slowest rank)."""
+    if ws <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t], dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -144,10 +156,7 @@ def run_e2e(args, data, dev, step, barrier, ws, wl):
         torch.cuda.synchronize()
         del snaps
     t_e2e = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([t_e2e], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(t_e2e, ws)
     h2d = hQ.numel() * 8 + hb.numel() + hP.numel() * 16
     d2h = hO.numel() * 16
     return {"value": ws * wl.W * wl.P * e2e_steps / t_e2e, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
@@ -201,10 +210,7 @@ def run_grad(args, ctx, dev, barrier, ws):
     ctx.profile(False)
     kms, kl = ctx.profile_read()
     t = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(t, ws)
     fpp = qcs.grad_flops_per_pair(wl.n, wl.ne)
     avg = kms / max(kl, 1)
     ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
@@ -275,10 +281,7 @@ def run_batch(args, ctx, dev, barrier, ws):
     e1.record(stream)
     barrier()
     t = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(t, ws)
     return {"metric": "walker x snapshot overlap pairs/s, batched active spaces under a CUDA graph",
             "value": ws * pairs_step * args.batch_steps / t, "unit": "pairs/s",
             "ms_per_step": 1e3 * t / args.batch_steps, "graph_steps": args.batch_steps,
@@ -300,6 +303,11 @@ def run_precision(args, ctx, dev, barrier, ws):
     from paper_2506_22408_gb300 import qcs, synth
 
     wl = synth.PRECISION
+    if args.prec_walkers:
+        import dataclasses
+
+        wl = dataclasses.replace(wl, name=f"n={wl.n} ne={wl.ne} {args.prec_walkers}x{wl.P} (reduced profiling case)",
+                                 W=args.prec_walkers)
     d = wl.generate(seed=0)
     Q = torch.from_numpy(d["Q"]).to(dev)
     b = torch.from_numpy(d["b"]).to(dev)
@@ -330,10 +338,7 @@ def run_precision(args, ctx, dev, barrier, ws):
     ctx.profile(False)
     kms, kl = ctx.profile_read()
     t = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(t, ws)
     # error against the FP64 path on a subset
     Ws, Ps = 64, 4000
     sub = qcs.Snapshots(ctx, Q[:Ps].contiguous(), b[:Ps].contiguous())
@@ -395,14 +400,15 @@ def run_reference(args, wl):
         return 0
     import oracle.oracle as orc
 
-    data = wl.generate(seed=0, W=64, P=min(wl.P, 4000))
+    Wc = min(64, wl.W)
+    data = wl.generate(seed=0, W=Wc, P=min(wl.P, 4000))
     cores = orc.max_threads()
-    Wc = 64
     # size each step at a few seconds of CPU work
     t0 = time.perf_counter()
-    orc.overlap(data["Phi"][:Wc], data["Q"][:100], data["b"][:100], threads=cores)
-    per_pair = (time.perf_counter() - t0) / (Wc * 100)
-    Pc = int(min(4000, max(100, 4.0 / max(per_pair * Wc, 1e-9))))
+    P0 = min(100, wl.P)
+    orc.overlap(data["Phi"][:Wc], data["Q"][:P0], data["b"][:P0], threads=cores)
+    per_pair = (time.perf_counter() - t0) / (Wc * P0)
+    Pc = int(min(4000, wl.P, max(100, 4.0 / max(per_pair * Wc, 1e-9))))
     for _ in range(args.warmup):
         orc.overlap(data["Phi"][:Wc], data["Q"][:Pc], data["b"][:Pc], threads=cores)
     times = []
@@ -436,6 +442,7 @@ def main():
     ap.add_argument("--grad-walkers", type=int, default=0, help="override the differentiation walkers (profiling)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
+    ap.add_argument("--prec-walkers", type=int, default=0, help="override the split-precision walkers (profiling)")
     ap.add_argument("--batch-steps", type=int, default=50, help="AFQMC steps captured in the batching graph")
     ap.add_argument("--batch-walker-scale", type=float, default=0.25,
                     help="scale of the batching walker counts (1.0: 1024/512/256/128/64 walkers)")
@@ -511,10 +518,7 @@ def main():
     kern_ms, kern_launches = ctx.profile_read()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(t_total, ws)
     pairs = wl.W * wl.P
     value = ws * pairs * args.steps / t_total
     del snaps
