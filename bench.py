@@ -118,16 +118,32 @@ class Clocks:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def traffic_for(kernel_src: str, kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+CSRC = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc")
+# Source files each timed kernel is compiled from; the committed DRAM figure of a
+# kernel is used only while all of them are unchanged.
+KERNEL_SOURCES = {
+    "pair_overlap_kernel": ["qcs_overlap.cu", "qcs_pair.cuh", "qcs_common.cuh"],
+    "split_pair_kernel": ["qcs_split.cu", "qcs_pair.cuh", "qcs_tc.cuh", "qcs_common.cuh"],
+    "grad_pair_kernel": ["qcs_grad.cu", "qcs_pair.cuh", "qcs_common.cuh"],
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch (read + write) from the committed ncu record, if it was
+    taken on the current sources and on this workload; else None."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(path):
         return None
     try:
-        rec = json.load(open(path))
-        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-        r = rec.get(kernel)
-        if r and r.get("source_sha256") == sha:
+        r = json.load(open(path)).get(kernel)
+        if r and r.get("source_sha256") == kernel_source_sha(kernel) and r.get("workload") == workload:
             return r.get("bytes_per_launch")
     except Exception:
         return None
@@ -214,13 +230,12 @@ def run_grad(args, ctx, dev, barrier, ws):
     fpp = qcs.grad_flops_per_pair(wl.n, wl.ne)
     avg = kms / max(kl, 1)
     ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
-    src = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc", "qcs_grad.cu")
     return {"metric": "walker x snapshot overlap+grad pairs/s (with force bias)", "value": ws * wl.W * wl.P * steps / t,
             "unit": "pairs/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
             "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "parity_plus_snapshots": npar,
                        "nchol": wl.nchol},
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(src, "grad_pair_kernel"),
+                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for("grad_pair_kernel", wl.name),
                          "kernel": "grad_pair_kernel", "kernel_ms": avg, "flops_per_launch": fpp * npar * wl.W},
             "gpu_launches_per_step": 6}
 
@@ -370,8 +385,7 @@ def run_precision(args, ctx, dev, barrier, ws):
                          "frac": ach / FP64_PEAK_TFLOPS, "kernel": "split_pair_kernel", "kernel_ms": avg,
                          "flops_counted": "FP64 Pfaffian work only (congruence on tensor cores)",
                          "tensor_tflops_executed": tensor_flops / (avg * 1e-3) / 1e12,
-                         "traffic": traffic_for(os.path.join(ROOT, "paper_2506_22408_gb300", "csrc", "qcs_split.cu"),
-                                                "split_pair_kernel")}}
+                         "traffic": traffic_for("split_pair_kernel", wl.name)}}
 
 
 def cpu_baseline(wl, data, target_s=10.0):
@@ -542,9 +556,8 @@ def main():
     flops_launch = fpp * npar * wl.W
     avg_ms = kern_ms / max(kern_launches, 1)
     achieved = flops_launch / (avg_ms * 1e-3) / 1e12
-    src = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc", "qcs_overlap.cu")
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for(src, "pair_overlap_kernel"),
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for("pair_overlap_kernel", wl.name),
             "kernel": "pair_overlap_kernel", "kernel_ms": avg_ms, "flops_per_launch": flops_launch,
             "peak_source": "FP64 ALU: 152 SM x 4 flop/clk x 2.07 GHz (derived from unit counts and the maximum "
                            "clock; MEASURED_PEAKS.json carries no FP64 figure)"}

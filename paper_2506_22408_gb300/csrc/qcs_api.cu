@@ -27,6 +27,10 @@ qcs_status qcs_check_launch(qcs_ctx *ctx, const char *what) {
 qcs_status qcs_set_smem(qcs_ctx *ctx, const void *func, size_t bytes) {
     if (bytes > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "shared memory request too large");
     cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // prefer the largest shared-memory carveout so that the blocks the occupancy
+    // calculation allows are actually co-resident
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     return QCS_OK;
 }
@@ -161,6 +165,9 @@ extern "C" qcs_status qcs_create(qcs_ctx **ctx, int device) {
     int optin = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)optin;
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    c->smem_per_sm = (size_t)per_sm;
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, sizeof(unsigned));
@@ -374,7 +381,7 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
     L.plan = plan;
     L.counter = wk.counter;
     L.config = opts ? opts->config : 0;
-    if (L.config == 0) {
+    if (L.config == 0 && !wk.split) {  // the tuned table belongs to the FP64 pair kernel
         auto it = ctx->tuned.find(std::make_tuple(s->n, ne, opts ? opts->nodes : 0, opts ? opts->flags : 0u));
         if (it != ctx->tuned.end()) L.config = it->second;
     }

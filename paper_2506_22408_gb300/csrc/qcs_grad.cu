@@ -88,18 +88,30 @@ __device__ void node_factor(const GradArgs &A, int k0, int nb, const cd *__restr
         const int r = m - 2 * s;
         const uint8_t *cur = acth + s * m;
         uint8_t *nxt = acth + (s + 1) * m;
-        if (lane < nb) best[lane] = 0ull;
-        __syncwarp();
-        const int rc = r - 1;
-        for (int e = lane; e < nb * rc; e += 32) {
-            int v = e / rc, a = 1 + (e - v * rc);
-            int k = cur[v * hstride], i = cur[v * hstride + a];
-            unsigned key = pivot_key(Ns[v * T + tri_index(k, i)]);
-            atomicMax(&best[v], ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a));
+        // pivot: largest |A_{k,i}| over the active row of k = cur[0].  Lanes form nb
+        // segments of seg lanes; each lane scans every seg-th candidate, then a
+        // shuffle reduction inside the segment (no atomics, no shared round trip).
+        const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
+        unsigned long long bk = 0ull;
+        {
+            const int v = lane / seg, sl = lane - (lane / seg) * seg;
+            if (v < nb) {
+                const int k = cur[v * hstride];
+                for (int a = 1 + sl; a < r; a += seg) {
+                    const unsigned key = pivot_key(Ns[v * T + tri_index(k, cur[v * hstride + a])]);
+                    const unsigned long long c =
+                        ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
+                    bk = c > bk ? c : bk;
+                }
+            }
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+                bk = ob > bk ? ob : bk;
+            }
+            bk = __shfl_sync(QCS_FULL, bk, (lane < nb ? lane : 0) * seg);
         }
-        __syncwarp();
         if (lane < nb) {
-            int a = 0xffff - (int)(best[lane] & 0xffffull);
+            int a = 0xffff - (int)(bk & 0xffffull);
             int k = cur[lane * hstride], p = cur[lane * hstride + a];
             cd piv = Ns[lane * T + tri_index(k, p)];
             cd f = cmul(pf[lane], piv);
@@ -237,11 +249,11 @@ __global__ void __launch_bounds__(128) grad_pair_kernel(const __grid_constant__ 
         if (lane == 0) tk = atomicAdd(A.counter, 1ull);
         const int64_t tile = (int64_t)__shfl_sync(QCS_FULL, tk, 0);
         if (tile >= ntiles) break;
-        const int64_t w = tile / A.nchunks;
-        const int ch = (int)(tile - w * A.nchunks);
+        const int ch = (int)(tile / A.W);  // chunk-major: a snapshot chunk is fetched once
+        const int64_t w = tile - (int64_t)ch * A.W;
         const int64_t p0 = (int64_t)ch * A.chunk;
         const int64_t p1 = p0 + A.chunk < L ? p0 + A.chunk : L;
-        cd *out = A.partial + tile * rec;
+        cd *out = A.partial + (w * A.nchunks + ch) * rec;
         cd Ssum = cmk(0.0, 0.0);
         for (int e = lane; e < n * n; e += 32) Gs[e] = cmk(0.0, 0.0);
         if (p0 < L) {

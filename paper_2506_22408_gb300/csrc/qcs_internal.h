@@ -14,7 +14,8 @@
 struct qcs_ctx {
     int device = 0;
     int num_sms = 0;
-    size_t smem_optin = 0;
+    size_t smem_optin = 0;     // per block
+    size_t smem_per_sm = 0;    // per SM
     unsigned *d_status = nullptr;  // device status word (OR of qcs_status bits)
     unsigned *h_status = nullptr;  // pinned host mirror
     void *work = nullptr;          // device workspace

@@ -81,6 +81,10 @@ extern "C" qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
         return QCS_ERR_CUDA;
     ctx.smem_optin = (size_t)optin;
+    int per_sm_smem = 0;
+    if (cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess)
+        return QCS_ERR_CUDA;
+    ctx.smem_per_sm = (size_t)per_sm_smem;
     ctx.d_status = d_status;
     cudaStream_t st = (cudaStream_t)stream;
 

@@ -74,8 +74,10 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     uint8_t *act1 = act0 + A.NB * A.m;
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
     const int span = A.chunk * wpb;  // snapshots per tile; warp w takes every wpb-th
-    const int64_t w = tile / A.nchunks;
-    const int ch = (int)(tile - w * A.nchunks);
+    // chunk-major tile order: consecutive tiles share one snapshot chunk and run over
+    // the walkers (whose rows all fit in L2), so each snapshot is fetched from HBM once
+    const int ch = (int)(tile / A.W);
+    const int64_t w = tile - (int64_t)ch * A.W;
     const int64_t p0 = (int64_t)ch * span;
     const int64_t p1 = p0 + span < L ? p0 + span : L;
     __syncthreads();  // previous tile's readers of Uts are done
@@ -113,7 +115,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             }
         }
     }
-    if (lane == 0) A.partial[tile * wpb + warp] = acc;
+    if (lane == 0) A.partial[(w * A.nchunks + ch) * wpb + warp] = acc;
 }
 
 // One or several systems (different n, ne, walkers, snapshots) in one persistent

@@ -135,19 +135,30 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
     __syncwarp();
     uint8_t *cur = act0, *nxt = act1;
     for (int r = m, s = 0; r >= 2; r -= 2, ++s) {
-        // pivot: largest |A_{k,i}| over the active row of k = cur[0]
-        if (lane < nb) best[lane] = 0ull;
-        __syncwarp();
-        const int rc = r - 1;
-        for (int e = lane; e < nb * rc; e += 32) {
-            int v = e / rc, a = 1 + (e - v * rc);
-            int k = cur[v * m], i = cur[v * m + a];
-            unsigned key = pivot_key(Ns[v * T + tri_index(k, i)]);
-            atomicMax(&best[v], ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a));
+        // pivot: largest |A_{k,i}| over the active row of k = cur[0].  Lanes form nb
+        // segments of seg lanes; each lane scans every seg-th candidate, then a
+        // shuffle reduction inside the segment (no atomics, no shared round trip).
+        const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
+        unsigned long long bk = 0ull;
+        {
+            const int v = lane / seg, sl = lane - (lane / seg) * seg;
+            if (v < nb) {
+                const int k = cur[v * m];
+                for (int a = 1 + sl; a < r; a += seg) {
+                    const unsigned key = pivot_key(Ns[v * T + tri_index(k, cur[v * m + a])]);
+                    const unsigned long long c =
+                        ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
+                    bk = c > bk ? c : bk;
+                }
+            }
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+                bk = ob > bk ? ob : bk;
+            }
+            bk = __shfl_sync(QCS_FULL, bk, (lane < nb ? lane : 0) * seg);
         }
-        __syncwarp();
         if (lane < nb) {
-            int a = 0xffff - (int)(best[lane] & 0xffffull);
+            int a = 0xffff - (int)(bk & 0xffffull);
             int k = cur[lane * m], p = cur[lane * m + a];
             cd piv = Ns[lane * T + tri_index(k, p)];
             pv[lane * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion

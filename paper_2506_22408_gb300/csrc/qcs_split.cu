@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
         __syncthreads();
         const int64_t t = next_tile;
         if (t >= ntiles || abort_flag) break;
-        const int64_t g = t / A.nchunks;
-        const int ch = (int)(t - g * A.nchunks);
+        const int ch = (int)(t / A.ngroups);  // chunk-major: a snapshot chunk is fetched once
+        const int64_t g = t - (int64_t)ch * A.ngroups;
         const int64_t p0 = (int64_t)ch * kSnapsPerTile;
         if (p0 >= L) {  // no parity +1 snapshot left in this chunk: nothing to accumulate
             if (lane == 0 && g * kWalkersPerTile + warp < A.W)
@@ -441,11 +441,11 @@ qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, 
     if (smem + 1024 > ctx->smem_optin || smem < (76u << 10))
         return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split kernel: shared memory");
     if (qcs_set_smem(ctx, (const void *)split_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_pair_kernel, 128, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    if (per_sm > 2) per_sm = 2;  // tensor memory: 2 x 256 columns per SM
+    // blocks per SM from the SM's shared memory (static words and the 1 KB the driver
+    // reserves per block included), at most 2 (tensor memory: 2 x 256 columns per SM)
+    int per_sm = (int)(ctx->smem_per_sm / (smem + 1024 + 1024));
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) per_sm = 1;
     const int64_t ntiles = A.ngroups * A.nchunks;
     int64_t blocks = (int64_t)ctx->num_sms * per_sm;
     if (blocks > ntiles) blocks = ntiles;
