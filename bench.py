@@ -388,6 +388,50 @@ def run_precision(args, ctx, dev, barrier, ws):
                          "traffic": traffic_for("split_pair_kernel", wl.name)}}
 
 
+def run_dft_plan(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
+    """Paper-shaped overlaps with the inverse-DFT node plan (n-ne+1 roots of unity,
+    floor/2+1 evaluated) instead of the default Gauss plan: same estimator, more
+    Pfaffians per pair.  Reported beside the headline for comparison."""
+    import torch
+
+    from paper_2506_22408_gb300 import qcs
+
+    flags = qcs.QCS_FLAG_DFT_NODES
+    ctx.autotune(wl.n, wl.ne, 0, flags, use_cache=True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        snaps = qcs.Snapshots(ctx, Qd, bd)
+        qcs.overlap(ctx, snaps, Pd, flags=flags)
+        return snaps
+
+    for _ in range(2):
+        step()
+    barrier()
+    ctx.profile(True)
+    ctx.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    ctx.profile(False)
+    kms, kl = ctx.profile_read()
+    assert ctx.sync_status() == 0
+    t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+    fpp = qcs.flops_per_pair(wl.n, wl.ne, 0, flags)
+    avg = kms / max(kl, 1)
+    ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
+    return {"metric": "walker x snapshot overlap pairs/s, roots-of-unity node plan", "value": ws * wl.W * wl.P * steps / t,
+            "unit": "pairs/s", "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "nodes": f"{len(qcs.node_plan(wl.n, wl.ne, 0, flags)[0])} of {wl.n - wl.ne + 1} roots of unity",
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "pair_overlap_kernel", "kernel_ms": avg,
+                         "flops_per_launch": fpp * npar * wl.W}}
+
+
 def cpu_baseline(wl, data, target_s=10.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle.oracle as orc
@@ -456,6 +500,7 @@ def main():
     ap.add_argument("--grad-walkers", type=int, default=0, help="override the differentiation walkers (profiling)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
+    ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
     ap.add_argument("--prec-walkers", type=int, default=0, help="override the split-precision walkers (profiling)")
     ap.add_argument("--batch-steps", type=int, default=50, help="AFQMC steps captured in the batching graph")
     ap.add_argument("--batch-walker-scale", type=float, default=0.25,
@@ -492,7 +537,7 @@ def main():
 
     data = wl.generate(seed=0)
     ctx = qcs.Context(local)
-    tuned = ctx.autotune(wl.n, wl.ne)  # pair-kernel configuration for this GPU (cached)
+    tuned = ctx.autotune(wl.n, wl.ne, use_cache=True)  # pair-kernel configuration for this GPU (cached)
     Qd = torch.from_numpy(data["Q"]).to(dev)
     bd = torch.from_numpy(data["b"]).to(dev)
     Pd = torch.from_numpy(data["Phi"]).to(dev)
@@ -537,6 +582,11 @@ def main():
     value = ws * pairs * args.steps / t_total
     del snaps
 
+    # ---------------- the same workload with the roots-of-unity node plan
+    dft = None
+    if not args.no_dft_plan:
+        dft = run_dft_plan(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar)
+
     # ---------------- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -567,7 +617,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "n": wl.n, "ne": wl.ne,
                        "walkers": wl.W, "snapshots": wl.P, "parity_plus_snapshots": npar,
-                       "nodes": "minimum (n-ne+1 roots of unity, floor/2+1 evaluated)",
+                       "nodes": f"Gauss plan: {len(qcs.node_plan(wl.n, wl.ne)[0])} Pfaffians per parity +1 pair",
                        "kernel_config": {"node_matrices_per_warp_round": tuned, "picked_by": "qcs_autotune"},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "snapshot set (164 MB) larger than L2, and L2 flushed between timed steps"},
@@ -578,6 +628,7 @@ def main():
             "grad": grad,
             "batch": batch,
             "precision": precision,
+            "roots_of_unity_plan": dft,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

@@ -85,12 +85,27 @@ typedef enum {
 } qcs_precision;
 
 /* qcs_opts.flags */
-#define QCS_FLAG_ALL_NODES 1u /* evaluate pf(A(z_k)) at every node and skip no snapshot
-                                 (disables the parity shortcuts described at qcs_overlap) */
+#define QCS_FLAG_ALL_NODES 1u /* roots of unity: evaluate pf(A(z_k)) at every node and skip no
+                                 snapshot (disables the parity shortcuts described at qcs_overlap) */
+#define QCS_FLAG_DFT_NODES 2u /* roots of unity with the parity shortcuts, also when nodes = 0
+                                 (then N = n-ne+1) */
+
+/* Node plans (how sum_x c_x C(2n,2x)/C(n,x) is obtained from Pfaffians):
+ *  - default (nodes = 0, no node flag): a Gauss rule.  For parity +1 snapshots
+ *    q(z) = pf(A(z))/z^{ne/2} is palindromic of degree d = n-ne, the weighted
+ *    coefficient sum is a linear functional on a space of dimension
+ *    D = floor(d/2)+1, and a Gauss rule with ceil(D/2) nodes on the unit circle
+ *    (positive weights) computes it exactly: 3 Pfaffians per pair at n=16, ne=8.
+ *  - roots of unity (nodes = N >= n-ne+1, or QCS_FLAG_DFT_NODES): the inverse DFT
+ *    of the interpolation step after Eq. (b_mat) on N roots of unity, folded with the weights; with the
+ *    parity shortcuts only floor(N/2)+1 nodes are evaluated.
+ *  - QCS_FLAG_ALL_NODES: roots of unity, every node, every snapshot.
+ * All plans give the same estimator up to rounding. */
 
 typedef struct {
     int precision; /* qcs_precision */
-    int nodes;     /* number of roots-of-unity nodes N; 0 = minimum n-ne+1 */
+    int nodes;     /* 0 = Gauss plan (or N = n-ne+1 roots with a node flag);
+                      N > 0 = N roots of unity, n-ne+1 <= N <= QCS_MAX_NODES */
     unsigned flags;
     int config;    /* kernel configuration: 0 = the context's tuned choice for these sizes
                       (qcs_autotune / qcs_set_config) or the built-in default;
@@ -148,7 +163,7 @@ int qcs_snapshots_modes(const qcs_snapshots *s);
  *   d_walkers : W x n x ne complex (read only)
  *   d_overlap : W complex (written)
  *   d_per_pair: W x P complex (o_p of every pair, row w) or NULL
- *   opts      : NULL = defaults (FP64, minimum nodes)
+ *   opts      : NULL = defaults (FP64, Gauss node plan)
  * o_p = 2 det(R_w) i^{ne/2} / 2^{n-ne/2} sum_x c_x C(2n,2x)/C(n,x), where
  * Phi_w = U R (QR), V = U^dagger defines M_phi (SI item 3) and c_x are the
  * coefficients of pf(C_0^(s) + z B^(s)) (Eqs. a_mat, b_mat).  The factor 2
@@ -158,7 +173,8 @@ int qcs_snapshots_modes(const qcs_snapshots *s);
  * snapshot state of parity pi the coefficients obey c_{n-x} = pi c_x, and the
  * weights obey w_{n-x} = w_x, so pairs with pi = -1 are exactly zero (their
  * per-pair output is written as 0) and pairs with pi = +1 need pf(A(z_k)) at
- * only floor(N/2)+1 of the N roots of unity.
+ * only floor(N/2)+1 of the N roots of unity, or at the ceil(D/2) nodes of the
+ * default Gauss plan.
  * Errors: QCS_ERR_ARG, QCS_ERR_CUDA; device bits via qcs_sync_status. */
 qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                        double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream);
@@ -222,7 +238,7 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
  * capture, where cudaMalloc is not allowed, and hosts whose device memory is
  * owned by their own pool and that forbid libraries from allocating.
  * Computes exactly what qcs_build_snapshots followed by qcs_overlap (default
- * options: FP64, minimum nodes) computes, with every intermediate buffer in a
+ * options: FP64, Gauss node plan) computes, with every intermediate buffer in a
  * fixed file-scope device array of QCS_NOALLOC_SCRATCH_BYTES (32 MiB) that each
  * GPU loading the library holds until the process exits.  No context is used.
  *   d_Q       : P x 2n x 2n doubles (device), d_b : P x n bytes (device)
@@ -274,6 +290,15 @@ qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
  * selected covariance B^(s), and the rank-2 Pfaffian updates at the
  * evaluated nodes.  Used by the benchmark's roofline. */
 double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
+
+/* Host only (no device work): the node plan that (n, ne, nodes, flags) selects.
+ * *nev receives the number of Pfaffians evaluated per pair; wnode and gamma
+ * (host arrays of 2 * QCS_MAX_NODES doubles, interleaved re/im) receive for each
+ * evaluated node the multiplier w_k of D and the weight gamma_k, such that the
+ * pair term is sum_k gamma_k pf(B^(s) + w_k C0^(s)) (Eq. a_mat with z = 1/w_k,
+ * divided by z^{m/2}).  Errors: QCS_ERR_ARG (sizes or nodes out of range,
+ * null pointers). */
+qcs_status qcs_node_plan_get(int n, int ne, int nodes, unsigned flags, int *nev, double *wnode, double *gamma);
 
 /* Same for one non-trivial pair of qcs_overlap_grad: the forward pass plus,
  * per evaluated node, the backward assembly of A(z_k)^{-1} from the

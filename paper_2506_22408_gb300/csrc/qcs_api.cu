@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "qcs_gauss_nodes.h"
 #include "qcs_internal.h"
 
 // ------------------------------------------------------------ helpers
@@ -100,7 +101,16 @@ qcs_status check_sizes(qcs_ctx *ctx, int n, int ne) {
 
 }  // namespace
 
-// Interpolation plan.  pf(A(z)) = z^{ne/2} q(z) with deg q <= d = n - ne, so N >= d+1
+// Node plans.  pf(A(z)) = z^{ne/2} q(z) with deg q <= d = n - ne, and the
+// estimator needs L(q) = sum_t w'_t c'_t, w'_t = C(2n, ne+2t)/C(n, ne/2+t).
+// The kernels evaluate pf'_k = pf(B + wnode_k D) and sum gamma_k pf'_k.
+//
+// Default plan (Gauss): for parity +1 snapshots q is palindromic, so L is a
+// linear functional on a space of dimension D = floor(d/2)+1 and a Gauss rule
+// with ceil(D/2) nodes on the unit circle computes it exactly; the nodes and
+// weights are tabulated in qcs_gauss_nodes.h (derivation in gen_gauss_nodes.py).
+//
+// Roots-of-unity plan (nodes > 0 or QCS_FLAG_DFT_NODES): N >= d+1
 // roots of unity z_k = w^k determine q exactly: c'_t = (1/N) sum_k q_k w^{-kt}.  The
 // estimator needs sum_t w'_t c'_t with w'_t = C(2n, ne+2t)/C(n, ne/2+t), i.e.
 // sum_k beta_k q_k with beta_k = (1/N) sum_t w'_t w^{-kt}.  The kernels evaluate
@@ -109,6 +119,20 @@ qcs_status check_sizes(qcs_ctx *ctx, int n, int ne) {
 // pairs (k, N-k) merge: only k = 0..floor(N/2) are evaluated.
 qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node_plan *plan) {
     const int d = n - ne;
+    if (n < 2 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return QCS_ERR_ARG;
+    if (nodes < 0) return QCS_ERR_ARG;
+    if (nodes == 0 && !(flags & (QCS_FLAG_ALL_NODES | QCS_FLAG_DFT_NODES))) {
+        const qcs_gauss_rule &g = qcs_gauss_rules[n][ne];
+        if (g.k < 1 || g.k > QCS_MAX_NODES) return QCS_ERR_ARG;
+        plan->N = 0;
+        plan->all = 0;
+        plan->nev = g.k;
+        for (int k = 0; k < g.k; ++k) {
+            plan->wnode[k] = cmk(g.node[k][0], g.node[k][1]);
+            plan->gamma[k] = cmk(g.node[k][2], g.node[k][3]);
+        }
+        return QCS_OK;
+    }
     int N = nodes > 0 ? nodes : d + 1;
     if (N < d + 1 || N > QCS_MAX_NODES) return QCS_ERR_ARG;
     typedef std::complex<double> C;
@@ -569,6 +593,10 @@ extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned 
     qcs_node_plan plan;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
+    return qcs_overlap_flops_nev(n, ne, plan.nev);
+}
+
+double qcs_overlap_flops_nev(int n, int ne, int nev) {
     const int d = n - ne, m = 2 * n - ne;
     double f = 0.0;
     f += 8.0 * 2.0 * (double)n * n * n;                       // T: n x 2n x n complex MACs
@@ -577,6 +605,22 @@ extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned 
     f += 2.0 * 2.0 * (double)n * tri_count(2 * d);            // B empty x empty
     double node = 0.0;
     for (int r = m; r > 2; r -= 2) node += 16.0 * tri_count(r - 2) + 6.0 * (r - 2);
-    f += node * plan.nev;
+    f += node * nev;
     return f;
+}
+
+extern "C" qcs_status qcs_node_plan_get(int n, int ne, int nodes, unsigned flags, int *nev, double *wnode,
+                                        double *gamma) {
+    if (!nev || !wnode || !gamma) return QCS_ERR_ARG;
+    qcs_node_plan plan;
+    qcs_status r = qcs_make_node_plan(n, ne, nodes, flags, &plan);
+    if (r != QCS_OK) return r;
+    *nev = plan.nev;
+    for (int k = 0; k < plan.nev; ++k) {
+        wnode[2 * k] = plan.wnode[k].x;
+        wnode[2 * k + 1] = plan.wnode[k].y;
+        gamma[2 * k] = plan.gamma[k].x;
+        gamma[2 * k + 1] = plan.gamma[k].y;
+    }
+    return QCS_OK;
 }

@@ -54,7 +54,7 @@ qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const doubl
                                      cudaStream_t st);
 
 struct qcs_node_plan {
-    int N;                       // roots of unity used
+    int N;                       // roots of unity used (0: Gauss rule)
     int nev;                     // nodes evaluated
     int all;                     // 1: every node, every snapshot
     cd wnode[QCS_MAX_NODES];     // multiplier of D at each evaluated node: conj(z_k)
@@ -62,6 +62,7 @@ struct qcs_node_plan {
 };
 
 qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node_plan *plan);
+double qcs_overlap_flops_nev(int n, int ne, int nev);  // algorithmic FP64 flops per parity +1 pair
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
                                   cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr);

@@ -280,7 +280,7 @@ qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launc
     double cost[QCS_MAX_SYSTEMS];
     for (int i = 0; i < nsys; ++i) {
         order[i] = i;
-        cost[i] = qcs_overlap_flops_per_pair(Ls[i].n, Ls[i].ne, Ls[i].plan.N, Ls[i].plan.all ? 1u : 0u) *
+        cost[i] = qcs_overlap_flops_nev(Ls[i].n, Ls[i].ne, Ls[i].plan.nev) *
                   (double)Ls[i].chunk;
     }
     for (int i = 0; i < nsys; ++i)

@@ -25,6 +25,8 @@ QCS_OK = 0
 QCS_FP64 = 0
 QCS_TF32X3 = 1
 QCS_FLAG_ALL_NODES = 1
+QCS_FLAG_DFT_NODES = 2
+MAX_NODES = 49
 STATUS_BITS = {1: "ARG", 2: "CUDA", 4: "NONFINITE", 8: "SINGULAR", 16: "TIMEOUT", 32: "UNSUPPORTED"}
 
 EXPORTED = [
@@ -32,7 +34,7 @@ EXPORTED = [
     "qcs_build_snapshots", "qcs_snapshots_free", "qcs_snapshots_parity", "qcs_snapshots_count",
     "qcs_snapshots_modes", "qcs_overlap", "qcs_overlap_grad", "qcs_force_bias", "qcs_overlap_flops_per_pair",
     "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair", "qcs_overlap_noalloc",
-    "qcs_autotune", "qcs_set_config", "qcs_overlap_batched",
+    "qcs_autotune", "qcs_set_config", "qcs_overlap_batched", "qcs_node_plan_get",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -93,6 +95,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_overlap_flops_per_pair.restype = f64
         lib.qcs_grad_flops_per_pair.argtypes = [i32, i32, i32, u32]
         lib.qcs_grad_flops_per_pair.restype = f64
+        lib.qcs_node_plan_get.argtypes = [i32, i32, i32, u32, ctypes.POINTER(i32), P, P]
         lib.qcs_overlap_batched.argtypes = [P, i32, ctypes.POINTER(_System), ctypes.POINTER(_Opts), P]
         lib.qcs_autotune.argtypes = [P, i32, i32, i32, u32, ctypes.POINTER(i32)]
         lib.qcs_set_config.argtypes = [P, i32, i32, i32, u32, i32]
@@ -139,9 +142,16 @@ class Context:
             n, ne, nodes, flags = (int(x) for x in key.split(","))
             self.lib.qcs_set_config(self.h, n, ne, nodes, flags, int(cfg))
 
-    def autotune(self, n: int, ne: int, nodes: int = 0, flags: int = 0, save: bool = True) -> int:
+    def autotune(self, n: int, ne: int, nodes: int = 0, flags: int = 0, save: bool = True,
+                 use_cache: bool = False) -> int:
         """Time the pair-kernel configurations for these sizes on this GPU, keep the
-        fastest in the context, and (save=True) record it in the tuning cache."""
+        fastest in the context, and (save=True) record it in the tuning cache.  With
+        use_cache=True a choice already in the cache for this GPU is taken as is
+        (it was loaded into the context when the context was created)."""
+        if use_cache:
+            hit = _read_cache().get(self.gpu_name, {}).get(f"{n},{ne},{nodes},{flags}")
+            if hit is not None:
+                return int(hit)
         cfg = ctypes.c_int()
         self.check(self.lib.qcs_autotune(self.h, n, ne, nodes, flags, ctypes.byref(cfg)))
         if save:
@@ -321,6 +331,23 @@ def flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
 
 def grad_flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
     return float(load().qcs_grad_flops_per_pair(n, ne, nodes, flags))
+
+
+def node_plan(n: int, ne: int, nodes: int = 0, flags: int = 0):
+    """Host-only: (wnode, gamma) complex arrays of the node plan; the pair term
+    is sum_k gamma_k pf(B + wnode_k D)."""
+    import numpy as np
+
+    nev = ctypes.c_int(0)
+    w = (ctypes.c_double * (2 * MAX_NODES))()
+    g = (ctypes.c_double * (2 * MAX_NODES))()
+    rc = load().qcs_node_plan_get(n, ne, nodes, flags, ctypes.byref(nev), w, g)
+    if rc != QCS_OK:
+        raise QCSError(rc, "qcs_node_plan_get: sizes or nodes out of range")
+    k = nev.value
+    wn = np.array(w[: 2 * k]).view(np.complex128)
+    gm = np.array(g[: 2 * k]).view(np.complex128)
+    return wn, gm
 
 
 class OverlapFn(torch.autograd.Function):

@@ -67,7 +67,8 @@ def test_gradient_options_and_overlap_agree(ctx):
     Phi = synth.walkers(rng, n, ne, W)
     oo, og, _ = orc.overlap_grad(Phi, Q, b)
     _, _, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
-    for kw in (dict(), dict(flags=qcs.QCS_FLAG_ALL_NODES), dict(nodes=2 * n + 1)):
+    for kw in (dict(), dict(flags=qcs.QCS_FLAG_DFT_NODES), dict(flags=qcs.QCS_FLAG_ALL_NODES),
+               dict(nodes=2 * n + 1)):
         ov, g, st, s = gpu_grad(ctx, Phi, Q, b, **kw)
         assert st == 0
         check_grad(g, og, ov, oo, sc)

@@ -91,18 +91,19 @@ def test_sizes_with_ragged_tails(ctx, n, ne, W, P):
 
 
 def test_node_options_agree(ctx):
-    """Default (parity shortcuts, minimum nodes), all nodes with no snapshot skipped,
-    and the literal 2n+1 roots of unity all give the same overlaps."""
+    """Default (Gauss plan, 3 nodes at n=16, ne=8), the minimum roots-of-unity plan
+    with parity shortcuts, all nodes with no snapshot skipped, and the literal 2n+1
+    roots of unity all give the same overlaps."""
     rng = np.random.default_rng(7)
     n, ne, W, P = 16, 8, 6, 40
     data = dict(Phi=synth.walkers(rng, n, ne, W), Q=synth.haar_orthogonal(rng, 2 * n, P),
                 b=synth.uniform_bits(rng, n, P))
     oo, opp, sc, _ = orc.overlap(data["Phi"], data["Q"], data["b"], per_pair=True)
-    for kw in (dict(), dict(flags=qcs.QCS_FLAG_ALL_NODES), dict(nodes=2 * n + 1),
-               dict(nodes=2 * n + 1, flags=qcs.QCS_FLAG_ALL_NODES), dict(nodes=12)):
+    for kw in (dict(), dict(flags=qcs.QCS_FLAG_DFT_NODES), dict(flags=qcs.QCS_FLAG_ALL_NODES),
+               dict(nodes=2 * n + 1), dict(nodes=2 * n + 1, flags=qcs.QCS_FLAG_ALL_NODES), dict(nodes=12)):
         ov, pp, par, st = run_gpu(ctx, data, **kw)
         assert st == 0
-        if kw.get("flags"):
+        if kw.get("flags", 0) & qcs.QCS_FLAG_ALL_NODES:
             assert np.all(np.abs(pp - opp) <= TOL * sc)
         else:
             check_pairs(pp, opp, sc, par)
