@@ -432,6 +432,64 @@ def run_dft_plan(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
                          "flops_per_launch": fpp * npar * wl.W}}
 
 
+def run_variants(args, ctx, dev, flush, barrier, ws, steps=3):
+    """The paper-shaped size (1024 x 20000, n=16, ne=8) with other snapshot
+    ensembles: b uniform over the parity-consistent strings (every pair
+    non-trivial), and signed-permutation snapshots (the paper's ensemble; the
+    congruence is then a gather), with uniform and with parity-consistent b."""
+    import dataclasses
+
+    import torch
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for key, ens, bits in (("haar_parity_b", "haar", "parity"), ("signed_perm_uniform_b", "signed_perm", "uniform"),
+                           ("signed_perm_parity_b", "signed_perm", "parity")):
+        wl = dataclasses.replace(synth.PAPER_SHAPED, name=f"paper-shaped {ens} Q, {bits} b", ensemble=ens, bits=bits)
+        if args.walkers or args.snapshots:
+            wl = dataclasses.replace(wl, W=args.walkers or wl.W, P=args.snapshots or wl.P)
+        d = wl.generate(seed=0)
+        Qd, bd, Pd = (torch.from_numpy(d[k]).to(dev) for k in ("Q", "b", "Phi"))
+
+        def step():
+            snaps = qcs.Snapshots(ctx, Qd, bd)
+            qcs.overlap(ctx, snaps, Pd)
+            return snaps
+
+        for _ in range(2):
+            snaps = step()
+        barrier()
+        npar = int((snaps.parity() == 1).sum().item())
+        nsp = snaps.signed_perm_count()
+        del snaps
+        ctx.profile(True)
+        ctx.profile_read()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        barrier()
+        ctx.profile(False)
+        kms, kl = ctx.profile_read()
+        assert ctx.sync_status() == 0
+        t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+        fpp = (qcs.flops_per_pair_signed_perm(wl.n, wl.ne) if nsp == wl.P else qcs.flops_per_pair(wl.n, wl.ne))
+        avg = kms / max(kl, 1)
+        ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
+        out[key] = {"value": ws * wl.W * wl.P * steps / t, "unit": "pairs/s",
+                    "nontrivial_pairs_per_s": ws * wl.W * npar * steps / t, "steps": steps,
+                    "parity_plus_snapshots": npar, "signed_perm_snapshots": nsp,
+                    "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": ach / FP64_PEAK_TFLOPS, "kernel": "pair_overlap_kernel", "kernel_ms": avg,
+                                 "flops_per_pair": fpp}}
+        del Qd, bd, Pd
+    return out
+
+
 def cpu_baseline(wl, data, target_s=10.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle.oracle as orc
@@ -501,6 +559,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
     ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the parity-consistent and signed-permutation snapshot ensembles")
     ap.add_argument("--prec-walkers", type=int, default=0, help="override the split-precision walkers (profiling)")
     ap.add_argument("--batch-steps", type=int, default=50, help="AFQMC steps captured in the batching graph")
     ap.add_argument("--batch-walker-scale", type=float, default=0.25,
@@ -587,6 +647,11 @@ def main():
     if not args.no_dft_plan:
         dft = run_dft_plan(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar)
 
+    # ---------------- other snapshot ensembles at the same size
+    variants = None
+    if not args.no_variants:
+        variants = run_variants(args, ctx, dev, flush, barrier, ws)
+
     # ---------------- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -629,6 +694,7 @@ def main():
             "batch": batch,
             "precision": precision,
             "roots_of_unity_plan": dft,
+            "ensembles": variants,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

@@ -153,6 +153,14 @@ qcs_status qcs_snapshots_free(qcs_snapshots *s);
  * caller's device buffer d_parity. */
 qcs_status qcs_snapshots_parity(const qcs_snapshots *s, int8_t *d_parity, void *stream);
 
+/* Number of snapshots of the set that are signed permutations (every row of Q_p
+ * has one nonzero entry, exactly +-1: the ensemble of the paper's experiment).
+ * For those the pair kernels form the congruence T = U^T Qt^T as a gather with
+ * sign flips (no FP64 work), and the gradient's cotangent product likewise.
+ * Waits for `stream` (the build must have been issued on it or before it).
+ * Errors: QCS_ERR_ARG (null pointers), QCS_ERR_CUDA. */
+qcs_status qcs_snapshots_signed_perm_count(const qcs_snapshots *s, int64_t *count, void *stream);
+
 /* Number of snapshots and modes of the set. */
 int64_t qcs_snapshots_count(const qcs_snapshots *s);
 int qcs_snapshots_modes(const qcs_snapshots *s);
@@ -178,6 +186,31 @@ int qcs_snapshots_modes(const qcs_snapshots *s);
  * Errors: QCS_ERR_ARG, QCS_ERR_CUDA; device bits via qcs_sync_status. */
 qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                        double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream);
+
+/* -------------------------------------------- reduced density matrices */
+
+/* Shadow estimates of Majorana correlators, the one-particle reduced density
+ * matrix and the particle number from the snapshot set alone (Supplementary
+ * "Reduced Density Matrices", Eq. local_fermionic_ob_exp): for rotated Majoranas
+ * g~ = R g, <g~_S> = mean_p C(2n,|S|)/C(n,|S|/2) pf(i (R G_p R^T)|_S) with
+ * G_p = Q_p^T C_b Q_p; every snapshot of the set counts (parity plays no role).
+ *   d_R     : 2n x 2n real orthogonal, row-major (device), or NULL for R = I
+ *   d_gam2  : 2n x 2n doubles or NULL: <g~_mu g~_nu> = i gam2[mu][nu] (mu != nu), 0 on the diagonal
+ *   d_gam4  : C(2n,4) doubles or NULL: <g~_mu g~_nu g~_rho g~_sigma> (real) for
+ *             mu < nu < rho < sigma in lexicographic order, formed from the second
+ *             moments of the covariance entries (a rank-P update, FP64)
+ *   d_rdm1  : n x n complex or NULL: <a~_p^dagger a~_q>, a~_p = (g~_2p + i g~_2p+1)/2
+ *             (Eqs. 1rdm_off_diagonal, 1rdm_diagonal)
+ *   d_npart : 1 double or NULL: the particle number, trace of the 1-RDM
+ * Outputs are device buffers owned by the caller.  The call uses context workspace
+ * (P n (2n-1) doubles for the covariance entries, plus the moment partials).
+ * Errors: QCS_ERR_ARG (empty set, set on another device, d_gam4 with n < 2), QCS_ERR_CUDA. */
+qcs_status qcs_shadow_rdm(qcs_ctx *ctx, const qcs_snapshots *s, const double *d_R, double *d_gam2, double *d_gam4,
+                          double *d_rdm1, double *d_npart, void *stream);
+
+/* Algorithmic FP64 flops of the second-moment update in qcs_shadow_rdm (d_gam4
+ * requested) for n modes and P snapshots. */
+double qcs_shadow_rdm_flops(int n, int64_t P);
 
 /* ----------------------------------------------------------- batching */
 
@@ -291,6 +324,10 @@ qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
  * evaluated nodes.  Used by the benchmark's roofline. */
 double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
 
+/* The same count for a pair whose snapshot is a signed permutation (no FP64
+ * work in the congruence). */
+double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags);
+
 /* Host only (no device work): the node plan that (n, ne, nodes, flags) selects.
  * *nev receives the number of Pfaffians evaluated per pair; wnode and gamma
  * (host arrays of 2 * QCS_MAX_NODES doubles, interleaved re/im) receive for each
@@ -304,6 +341,10 @@ qcs_status qcs_node_plan_get(int n, int ne, int nodes, unsigned flags, int *nev,
  * per evaluated node, the backward assembly of A(z_k)^{-1} from the
  * elimination's Gauss vectors, and the per-pair cotangent products. */
 double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags);
+
+/* The same count for a pair whose snapshot is a signed permutation (no FP64 work
+ * in the congruence; 2 of the 2n terms of each cotangent entry). */
+double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,7 @@ MUTATIONS = {
     7: "channel eigenvalues used as weights instead of their inverses",
     8: "Pfaffian pivot swap without the sign flip",
     9: "V = U^T instead of U^dagger",
+    10: "1-RDM off-diagonal: signs of the mixed Majorana terms swapped",
 }
 
 
@@ -94,6 +95,8 @@ class Oracle:
         lib.orc_overlap_grad.restype = i32
         lib.orc_force_bias.argtypes = [i32, i32, i64, i32, P, P, P, P, f64, P]
         lib.orc_max_threads.restype = i32
+        lib.orc_shadow_rdm.argtypes = [i32, i64, P, P, P, P, P, P, P, P]
+        lib.orc_shadow_rdm.restype = i32
         self.lib = lib
         self.mutation = mutation
 
@@ -202,6 +205,27 @@ class Oracle:
         self.lib.orc_force_bias(n, ne, W, nchol, _p(L), _p(Phi), _p(ov), _p(grad), float(sqrt_dt), _p(xb))
         return xb
 
+    def shadow_rdm(self, Q, b, w=None, R=None, deg4=False):
+        """Shadow estimates (SI "Reduced Density Matrices"): dict(gam2 (2n x 2n real,
+        <g~_mu g~_nu> = i gam2), gam4 (C(2n,4) real, mu<nu<rho<sigma lexicographic) when
+        deg4, rdm1 (n x n complex), npart).  w: optional per-snapshot weights; R: rotation."""
+        Q = _c(Q, np.float64)
+        b = _c(b, np.uint8)
+        P, N2, _ = Q.shape
+        n = N2 // 2
+        w = _c(w, np.float64) if w is not None else None
+        R = _c(R, np.float64) if R is not None else None
+        gam2 = np.zeros((N2, N2))
+        from math import comb
+        gam4 = np.zeros(comb(N2, 4)) if deg4 else None
+        rdm1 = np.zeros((n, n), np.complex128)
+        npart = ctypes.c_double(0.0)
+        rc = self.lib.orc_shadow_rdm(n, P, _p(Q), _p(b), _p(w), _p(R), _p(gam2), _p(gam4), _p(rdm1),
+                                     ctypes.byref(npart))
+        if rc != 0:
+            raise ValueError("orc_shadow_rdm: bad sizes")
+        return dict(gam2=gam2, gam4=gam4, rdm1=rdm1, npart=npart.value)
+
     def max_threads(self) -> int:
         return int(self.lib.orc_max_threads())
 
@@ -258,6 +282,10 @@ def overlap_grad(Phi, Q, b, mode=INTERP_ROOTS, nodes=0, threads=0):
 
 def force_bias(L, Phi, ov, grad, sqrt_dt=0.0):
     return _default().force_bias(L, Phi, ov, grad, sqrt_dt)
+
+
+def shadow_rdm(Q, b, w=None, R=None, deg4=False):
+    return _default().shadow_rdm(Q, b, w, R, deg4)
 
 
 def max_threads() -> int:

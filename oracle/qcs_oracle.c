@@ -617,6 +617,99 @@ void orc_force_bias(int n, int ne, int64_t W, int nchol, const cplx *L, const cp
     free(Gf);
 }
 
+/* --------------------------- 15. shadow estimates of Majorana correlators, 1-RDM, particle number
+ * Supplementary "Reduced Density Matrices", Eq. (local_fermionic_ob_exp): for rotated
+ * Majoranas g~_mu = sum_nu R_{mu nu} g_nu (R in O(2n); identity when R is NULL),
+ *   <g~_S> = mean_p C(2n,|S|)/C(n,|S|/2) pf( i (R G_p R^T)|_S ),   G_p = Q_p^T C_b Q_p (step 2),
+ * the paper's sum over outcomes read as the mean over the measured snapshots.  For
+ * |S| = 2, pf(i X|_S) = i X_{mu nu}; for |S| = 4 it is i^2 (X_01 X_23 - X_02 X_13 + X_03 X_12).
+ * The 1-RDM follows Eqs. (1rdm_off_diagonal), (1rdm_diagonal) with the Majoranas of
+ * Eq. (majorana_op) at 0-based indices 2p, 2p+1:
+ *   a_p^dag a_q = (1/4)(g_2p - i g_2p+1)(g_2q + i g_2q+1)  (p != q),
+ *   a_p^dag a_p = (1 + i g_2p g_2p+1) / 2,
+ * and the particle number is its trace.  Optional weights w_p give the weighted mean
+ * sum_p w_p est_p / sum_p w_p (exact group averages in the tests).
+ * Outputs (each may be NULL):
+ *   gam2  2n x 2n real, <g~_mu g~_nu> = i gam2[mu][nu] for mu != nu (diagonal 0)
+ *   gam4  C(2n,4) real, <g~_mu g~_nu g~_rho g~_sigma> for mu < nu < rho < sigma in
+ *         lexicographic order (the estimate of a product of four distinct Majoranas is real)
+ *   rdm1  n x n complex, <a_p^dag a_q> in the rotated mode basis
+ *   npart particle number */
+int orc_shadow_rdm(int n, int64_t P, const double *Q, const uint8_t *b, const double *w, const double *R,
+                   double *gam2, double *gam4, cplx *rdm1, double *npart) {
+    const int N2 = 2 * n;
+    if (n < 1 || n > ORC_MAXN || P < 1) return -1;
+    const double K2 = binom(N2, 2) / binom(n, 1), K4 = n >= 2 ? binom(N2, 4) / binom(n, 2) : 0.0;
+    const long n4 = N2 >= 4 ? (long)binom(N2, 4) : 0;
+    double *G = malloc(sizeof(double) * N2 * N2), *X = malloc(sizeof(double) * N2 * N2);
+    double *T = malloc(sizeof(double) * N2 * N2), *acc2 = calloc((size_t)N2 * N2, sizeof(double));
+    double *acc4 = gam4 ? calloc((size_t)(n4 > 0 ? n4 : 1), sizeof(double)) : NULL;
+    double wsum = 0.0;
+    for (int64_t p = 0; p < P; ++p) {
+        const double wp = w ? w[p] : 1.0;
+        wsum += wp;
+        orc_snapshot_G(n, Q + p * N2 * N2, b + p * n, G);
+        if (R) { /* X = R G R^T */
+            for (int i = 0; i < N2; ++i)
+                for (int j = 0; j < N2; ++j) {
+                    double s = 0.0;
+                    for (int k = 0; k < N2; ++k) s += G[i * N2 + k] * R[j * N2 + k];
+                    T[i * N2 + j] = s;
+                }
+            for (int i = 0; i < N2; ++i)
+                for (int j = 0; j < N2; ++j) {
+                    double s = 0.0;
+                    for (int k = 0; k < N2; ++k) s += R[i * N2 + k] * T[k * N2 + j];
+                    X[i * N2 + j] = s;
+                }
+        } else {
+            memcpy(X, G, sizeof(double) * N2 * N2);
+        }
+        for (int i = 0; i < N2 * N2; ++i) acc2[i] += wp * K2 * X[i];
+        if (acc4) {
+            long t = 0;
+            for (int a = 0; a < N2; ++a)
+                for (int bb = a + 1; bb < N2; ++bb)
+                    for (int c = bb + 1; c < N2; ++c)
+                        for (int d = c + 1; d < N2; ++d, ++t) {
+                            double pf4 = X[a * N2 + bb] * X[c * N2 + d] - X[a * N2 + c] * X[bb * N2 + d] +
+                                         X[a * N2 + d] * X[bb * N2 + c];
+                            acc4[t] += wp * K4 * (-pf4); /* i^2 pf(X|_S) */
+                        }
+        }
+    }
+    double *g2 = malloc(sizeof(double) * N2 * N2);
+    for (int i = 0; i < N2 * N2; ++i) g2[i] = acc2[i] / wsum;
+    for (int i = 0; i < N2; ++i) g2[i * N2 + i] = 0.0;
+    if (gam2) memcpy(gam2, g2, sizeof(double) * N2 * N2);
+    if (gam4)
+        for (long t = 0; t < n4; ++t) gam4[t] = acc4[t] / wsum;
+    /* E(mu, nu) = <g_mu g_nu> = i gam2[mu][nu] for mu != nu */
+    double np_ = 0.0;
+    for (int pp = 0; pp < n; ++pp)
+        for (int q = 0; q < n; ++q) {
+            cplx d;
+            if (pp == q) {
+                d = 0.5 * (1.0 - g2[(2 * pp) * N2 + 2 * pp + 1]);
+                np_ += creal(d);
+            } else {
+                cplx e00 = I * g2[(2 * pp) * N2 + 2 * q], e01 = I * g2[(2 * pp) * N2 + 2 * q + 1];
+                cplx e10 = I * g2[(2 * pp + 1) * N2 + 2 * q], e11 = I * g2[(2 * pp + 1) * N2 + 2 * q + 1];
+                d = 0.25 * (e00 + I * e01 - I * e10 + e11);
+                if (MUT(10)) d = 0.25 * (e00 - I * e01 + I * e10 + e11);
+            }
+            if (rdm1) rdm1[pp * n + q] = d;
+        }
+    if (npart) *npart = np_;
+    free(G);
+    free(X);
+    free(T);
+    free(acc2);
+    free(acc4);
+    free(g2);
+    return 0;
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

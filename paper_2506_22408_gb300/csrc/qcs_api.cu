@@ -74,17 +74,6 @@ void qcs_prof_end(qcs_ctx *ctx, cudaStream_t st) {
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 double binom(int n, int k) {
     if (k < 0 || k > n) return 0.0;
     double r = 1.0;
@@ -277,7 +266,8 @@ extern "C" qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const 
     cudaError_t e = cudaMalloc(&s->Qt, sizeof(cd) * (size_t)Pa * 2 * n * n);
     if (e == cudaSuccess) e = cudaMalloc(&s->parity, (size_t)Pa);
     if (e == cudaSuccess) e = cudaMalloc(&s->idx, sizeof(int) * (size_t)Pa);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_count, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_count, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&s->gth, (size_t)Pa * 2 * n);
     if (e != cudaSuccess) {
         qcs_snapshots_free(s);
         return qcs_fail(ctx, QCS_ERR_CUDA, std::string("snapshot cudaMalloc: ") + cudaGetErrorString(e));
@@ -291,6 +281,18 @@ extern "C" qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const 
     return QCS_OK;
 }
 
+extern "C" qcs_status qcs_snapshots_signed_perm_count(const qcs_snapshots *s, int64_t *count, void *stream) {
+    if (!s || !count) return QCS_ERR_ARG;
+    DeviceGuard g(s->device);
+    int h = 0;
+    if (cudaMemcpyAsync(&h, s->d_count + 1, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return QCS_ERR_CUDA;
+    *count = s->P > 0 ? (int64_t)h : 0;
+    return QCS_OK;
+}
+
 extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
     if (!s) return QCS_ERR_ARG;
     DeviceGuard g(s->device);
@@ -299,6 +301,7 @@ extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
     if (s->parity) cudaFree(s->parity);
     if (s->idx) cudaFree(s->idx);
     if (s->d_count) cudaFree(s->d_count);
+    if (s->gth) cudaFree(s->gth);
     if (s->split_hi) cudaFree(s->split_hi);
     if (s->split_lo) cudaFree(s->split_lo);
     delete s;
@@ -587,6 +590,18 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     f += (double)m * 2 * n * (8.0 * ne + 4.0 * (m - ne));           // G_X = Y (X J)
     f += (double)n * n * 2 * n * 8.0 + 2.0 * d * 2 * n;             // Gamma1 / Gamma2
     return f;
+}
+
+extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
+    const double f = qcs_overlap_flops_per_pair(n, ne, nodes, flags);
+    return f > 0.0 ? f - 16.0 * (double)n * n * n : 0.0;  // T is a gather
+}
+
+extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
+    const double f = qcs_grad_flops_per_pair(n, ne, nodes, flags);
+    // T is a gather; each of the n x n cotangent entries takes 2 complex additions
+    // instead of 2n complex MACs
+    return f > 0.0 ? f - 16.0 * (double)n * n * n - ((double)n * n * 2 * n * 8.0 - (double)n * n * 2 * 2.0) : 0.0;
 }
 
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {

@@ -32,24 +32,31 @@
 
 namespace {
 
-constexpr int kMaxNBG = 4;
+constexpr int kMaxNBG = 4;  // node matrices per round, at most
+constexpr int kGroup = 64;  // threads (two warps) that share one pair
 
 struct GradArgs {
     int n, ne, m, d, nev, NB, all, chunk, nchunks;
     int64_t W, P;
-    int warp_bytes, tab_bytes;
-    int off_Q, off_T, off_B, off_Y, off_G, off_NZ, off_U, off_V, off_y1, off_y2, off_pf, off_inv, off_cf,
-        off_best, off_int, off_acth, off_kh, off_ph;
+    int group_bytes, tab_bytes;
+    int off_Q, off_T, off_B, off_Y, off_G, off_NZ, off_g1, off_g2, off_y1, off_y2, off_pf, off_cf, off_invh,
+        off_int, off_tile, off_acth, off_kh, off_ph, off_kc;
     const cd *Ut;
     const cd *Qt;
+    const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
     const int *idx;
     const int *d_count;
     cd *partial;
-    unsigned long long *counter;  // tile counter: warps pull tiles dynamically
+    unsigned long long *counter;  // tile counter: groups pull tiles dynamically
     unsigned *status;
     cd wnode[QCS_MAX_NODES];
     cd gamma[QCS_MAX_NODES];
 };
+
+// Barrier of the two warps that share a pair (named barrier `id`, 64 threads).
+__device__ __forceinline__ void group_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kGroup) : "memory");
+}
 
 // Skew matrix entry (i, j) from its packed upper triangle.
 __device__ __forceinline__ cd skew_at(const cd *P, int i, int j) {
@@ -58,43 +65,43 @@ __device__ __forceinline__ cd skew_at(const cd *P, int i, int j) {
     return flip_if(P[tri_index(lo, hi)], i > j);
 }
 
-// Forward Parlett-Reid elimination of nb node matrices with the step history
-// kept for the backward inverse.  pf[v] receives pf(B + wnode[k0+v] D).
+// Forward Parlett-Reid elimination of nb node matrices B + wnode D (packed upper,
+// original index order) by the pair's 64 threads, keeping the step history (active
+// index lists, pivot rows and columns, pivot reciprocals) for the backward inverse.
+// pf[v] receives pf(B + wnode[k0+v] D).
 __device__ void node_factor(const GradArgs &A, int k0, int nb, const cd *__restrict__ Bs, cd *__restrict__ Ns,
-                            cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ inv,
-                            unsigned long long *__restrict__ best, int *__restrict__ ints, uint8_t *__restrict__ acth,
-                            uint8_t *__restrict__ kh, uint8_t *__restrict__ ph, const uint16_t *__restrict__ tab,
-                            int lane) {
+                            cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ invh,
+                            int *__restrict__ pos, uint8_t *__restrict__ acth, uint8_t *__restrict__ kh,
+                            uint8_t *__restrict__ ph, const uint16_t *__restrict__ tab, int t, int bar) {
     const int m = A.m, ne = A.ne, d = A.d, T = tri_count(m), S = m / 2;
     const int hstride = (S + 1) * m;
-    int *pos = ints;
-    for (int e = lane; e < nb * T; e += 32) {
-        int v = e / T, t = e - v * T;
-        Ns[v * T + t] = Bs[t];
+    const int lane = t & 31;
+    for (int e = t; e < nb * T; e += kGroup) {
+        int v = e / T, u = e - v * T;
+        Ns[v * T + u] = Bs[u];
     }
-    for (int e = lane; e < nb * m; e += 32) {
+    for (int e = t; e < nb * m; e += kGroup) {
         int v = e / m, a = e - v * m;
         acth[v * hstride + a] = (uint8_t)a;
     }
-    if (lane < nb) pf[lane] = cmk(1.0, 0.0);
-    __syncwarp();
-    for (int e = lane; e < nb * d; e += 32) {
+    if (t < nb) pf[t] = cmk(1.0, 0.0);
+    group_sync(bar);
+    for (int e = t; e < nb * d; e += kGroup) {
         int v = e / d, i = e - v * d;
         cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
         *x = cadd(*x, A.wnode[k0 + v]);
     }
-    __syncwarp();
+    group_sync(bar);
     for (int s = 0; s < S; ++s) {
         const int r = m - 2 * s;
         const uint8_t *cur = acth + s * m;
         uint8_t *nxt = acth + (s + 1) * m;
-        // pivot: largest |A_{k,i}| over the active row of k = cur[0].  Lanes form nb
-        // segments of seg lanes; each lane scans every seg-th candidate, then a
-        // shuffle reduction inside the segment (no atomics, no shared round trip).
-        const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
-        unsigned long long bk = 0ull;
-        {
-            const int v = lane / seg, sl = lane - (lane / seg) * seg;
+        if (t < 32) {
+            // pivot: largest |A_{k,i}| over the active row of k = cur[0].  Warp 0 alone:
+            // nb segments of seg lanes, a shuffle reduction inside each segment.
+            const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : 8;
+            const int v = lane / seg, sl = lane - v * seg;
+            unsigned long long bk = 0ull;
             if (v < nb) {
                 const int k = cur[v * hstride];
                 for (int a = 1 + sl; a < r; a += seg) {
@@ -109,145 +116,159 @@ __device__ void node_factor(const GradArgs &A, int k0, int nb, const cd *__restr
                 bk = ob > bk ? ob : bk;
             }
             bk = __shfl_sync(QCS_FULL, bk, (lane < nb ? lane : 0) * seg);
+            if (lane < nb) {
+                const int a = 0xffff - (int)(bk & 0xffffull);
+                const int k = cur[lane * hstride], p = cur[lane * hstride + a];
+                const cd piv = Ns[lane * T + tri_index(k, p)];
+                const cd f = cmul(pf[lane], piv);
+                pf[lane] = ((a - 1) & 1) ? cneg(f) : f;
+                invh[lane * S + s] = cinv(piv);
+                pos[lane] = a;
+                kh[lane * S + s] = (uint8_t)k;
+                ph[lane * S + s] = (uint8_t)p;
+            }
         }
-        if (lane < nb) {
-            int a = 0xffff - (int)(bk & 0xffffull);
-            int k = cur[lane * hstride], p = cur[lane * hstride + a];
-            cd piv = Ns[lane * T + tri_index(k, p)];
-            cd f = cmul(pf[lane], piv);
-            pf[lane] = ((a - 1) & 1) ? cneg(f) : f;
-            inv[lane] = cinv(piv);
-            pos[lane] = a;
-            kh[lane * S + s] = (uint8_t)k;
-            ph[lane * S + s] = (uint8_t)p;
-        }
-        __syncwarp();
+        group_sync(bar);
         const int rv = r - 2;
-        for (int e = lane; e < nb * rv; e += 32) {
-            int v = e / rv, a2 = e - v * rv;
-            int a = a2 + 1 + ((a2 + 1 >= pos[v]) ? 1 : 0);
-            int i = cur[v * hstride + a], k = kh[v * S + s], p = ph[v * S + s];
+        for (int e = t; e < nb * rv; e += kGroup) {
+            const int v = e / rv, a2 = e - v * rv;
+            const int a = a2 + 1 + ((a2 + 1 >= pos[v]) ? 1 : 0);
+            const int i = cur[v * hstride + a], k = kh[v * S + s], p = ph[v * S + s];
             const cd *Nv = Ns + v * T;
-            cd u = Nv[tri_index(k, i)];
-            Uv[v * m + a2] = cneg(cmul(u, inv[v]));
+            Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], invh[v * S + s]);
             Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
             nxt[v * hstride + a2] = (uint8_t)i;
         }
-        __syncwarp();
+        group_sync(bar);
         const int Tr = tri_count(rv);
-        for (int e = lane; e < nb * Tr; e += 32) {
-            int v = e / Tr, t = e - v * Tr;
+        for (int e = t; e < nb * Tr; e += kGroup) {
+            const int v = e / Tr, u = e - v * Tr;
             int a, b;
-            pair_of(tab, t, a, b);
-            int i = nxt[v * hstride + a], j = nxt[v * hstride + b];
+            pair_of(tab, u, a, b);
+            const int i = nxt[v * hstride + a], j = nxt[v * hstride + b];
             cd *x = Ns + v * T + tri_index(i, j);
             cd y = *x;
             cfms(y, Uv[v * m + a], Vv[v * m + b]);
             cfma(y, Vv[v * m + a], Uv[v * m + b]);
             *x = y;
         }
-        __syncwarp();
+        group_sync(bar);
     }
 }
 
-// Backward recursion: Zs[v] (packed upper) <- inverse of node matrix v from its factors.
-// Lanes are split into nb segments of 32/nb lanes; segment v serves node v.
-__device__ void node_inverse(const GradArgs &A, int nb, const cd *__restrict__ Ns, cd *__restrict__ Zs,
-                             cd *__restrict__ g1v, cd *__restrict__ g2v, cd *__restrict__ y1v, cd *__restrict__ y2v,
-                             const uint8_t *__restrict__ acth, const uint8_t *__restrict__ kh,
-                             const uint8_t *__restrict__ ph, int lane) {
+// Backward recursion, in place: the factors of node v in Ns become the packed
+// upper triangle of the inverse of node matrix v.  Step s first reads its pivot
+// row and column (entries (k,i) and (i,p) for the indices i still active after
+// the step), then overwrites exactly those entries, and (k,p), with entries of the
+// inverse; the entries among the later indices already hold the inverse of the
+// step's Schur complement Z.
+__device__ void node_inverse(const GradArgs &A, int nb, cd *__restrict__ Ns, cd *__restrict__ g1v,
+                             cd *__restrict__ g2v, cd *__restrict__ y1v, cd *__restrict__ y2v,
+                             const cd *__restrict__ invh, const uint8_t *__restrict__ acth,
+                             const uint8_t *__restrict__ kh, const uint8_t *__restrict__ ph, int t, int bar) {
     const int m = A.m, T = tri_count(m), S = m / 2;
     const int hstride = (S + 1) * m;
-    const int seg = 32 / nb;  // nb in {1, 2, 4}
-    const int v = lane / seg, sl = lane - v * seg;
-    const bool live = v < nb;
+    const int lane = t & 31;
     for (int s = S - 1; s >= 0; --s) {
         const int rv = m - 2 * s - 2;
-        const cd *Nv = Ns + (live ? v : 0) * T;
-        cd *Zv = Zs + (live ? v : 0) * T;
-        const uint8_t *rest = acth + (live ? v : 0) * hstride + (s + 1) * m;
-        const int k = kh[(live ? v : 0) * S + s], p = ph[(live ? v : 0) * S + s];
-        const cd ia = cinv(Nv[tri_index(k, p)]);
         // g1 = v/a, g2 = -u/a with u_i = A_{i,k} = -N(k,i), v_i = A_{i,p}
-        for (int a = sl; a < rv && live; a += seg) {
-            int i = rest[a];
-            cd vi = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
+        for (int e = t; e < nb * rv; e += kGroup) {
+            const int v = e / rv, a = e - v * rv;
+            const cd *Nv = Ns + v * T;
+            const int i = acth[v * hstride + (s + 1) * m + a], k = kh[v * S + s], p = ph[v * S + s];
+            const cd ia = invh[v * S + s];
+            const cd vi = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
             g1v[v * m + a] = cmul(vi, ia);
             g2v[v * m + a] = cmul(Nv[tri_index(k, i)], ia);
         }
-        __syncwarp();
-        cd corner = cmk(0.0, 0.0);
-        for (int a = sl; a < rv && live; a += seg) {
-            int i = rest[a];
-            cd y1 = cmk(0.0, 0.0), y2 = cmk(0.0, 0.0);
+        group_sync(bar);
+        // y1 = Z g1 and y2 = Z g2 over the later indices: one (node, vector, row) item per thread
+        const int per = 2 * rv;
+        for (int e = t; e < nb * per; e += kGroup) {
+            const int v = e / per, r2 = e - v * per;
+            const int vec = r2 >= rv ? 1 : 0, a = r2 - vec * rv;
+            const cd *Zv = Ns + v * T;
+            const uint8_t *rest = acth + v * hstride + (s + 1) * m;
+            const cd *g = (vec ? g2v : g1v) + v * m;
+            const int i = rest[a];
+            cd y = cmk(0.0, 0.0);
             for (int b = 0; b < rv; ++b) {
-                int j = rest[b];
-                cd z = (j == i) ? cmk(0.0, 0.0) : flip_if(Zv[tri_index(i < j ? i : j, i < j ? j : i)], j < i);
-                cfma(y1, z, g1v[v * m + b]);
-                cfma(y2, z, g2v[v * m + b]);
+                const int j = rest[b];
+                if (j == i) continue;
+                cfma(y, flip_if(Zv[tri_index(i < j ? i : j, i < j ? j : i)], j < i), g[b]);
             }
-            y1v[v * m + a] = y1;
-            y2v[v * m + a] = y2;
-            cfma(corner, g1v[v * m + a], y2);
+            (vec ? y2v : y1v)[v * m + a] = y;
         }
-        // segmented sum of the corner term over the segment's lanes
-        for (int o = seg / 2; o > 0; o >>= 1) {
-            corner.x += __shfl_xor_sync(QCS_FULL, corner.x, o);
-            corner.y += __shfl_xor_sync(QCS_FULL, corner.y, o);
+        group_sync(bar);
+        // corner g1^T Z g2 per node (warp 0: segmented shuffle sums), then the new entries
+        if (t < 32) {
+            const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : 8;
+            const int v = lane / seg, sl = lane - v * seg;
+            cd corner = cmk(0.0, 0.0);
+            if (v < nb)
+                for (int a = sl; a < rv; a += seg) cfma(corner, g1v[v * m + a], y2v[v * m + a]);
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                corner.x += __shfl_xor_sync(QCS_FULL, corner.x, o);
+                corner.y += __shfl_xor_sync(QCS_FULL, corner.y, o);
+            }
+            if (v < nb && sl == 0) Ns[v * T + tri_index(kh[v * S + s], ph[v * S + s])] = csub(corner, invh[v * S + s]);
         }
-        __syncwarp();
-        for (int a = sl; a < rv && live; a += seg) {
-            int i = rest[a];
+        for (int e = t; e < nb * rv; e += kGroup) {
+            const int v = e / rv, a = e - v * rv;
+            cd *Zv = Ns + v * T;
+            const int i = acth[v * hstride + (s + 1) * m + a], k = kh[v * S + s], p = ph[v * S + s];
             Zv[tri_index(k, i)] = y1v[v * m + a];  // Z(k,i) = -Z(i,k) = (Z g1)_i
-            cd y2 = y2v[v * m + a];                 // Z(i,p) = -y2_i
+            const cd y2 = y2v[v * m + a];          // Z(i,p) = -y2_i
             if (i < p) Zv[tri_index(i, p)] = cneg(y2);
             else Zv[tri_index(p, i)] = y2;
         }
-        if (live && sl == 0) Zv[tri_index(k, p)] = csub(corner, ia);
-        __syncwarp();
+        group_sync(bar);
     }
 }
 
-__global__ void __launch_bounds__(128) grad_pair_kernel(const __grid_constant__ GradArgs A) {
+// Two warps (a group of 64 threads) per pair; a block holds blockDim/64 groups,
+// each with its own workspace and named barrier.  Groups pull (walker, chunk)
+// tiles from a device counter in chunk-major order.
+__global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant__ GradArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
+    const int gid = threadIdx.x / kGroup;
+    const int t = threadIdx.x - gid * kGroup;
+    const int bar = 1 + gid;
     const int n = A.n, n2 = 2 * n, ne = A.ne, m = A.m, T = tri_count(m);
     const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
     build_pair_table(tab, T);
     __syncthreads();
-    unsigned char *wb = smem_raw + A.tab_bytes + (size_t)warp * A.warp_bytes;
+    unsigned char *wb = smem_raw + A.tab_bytes + (size_t)gid * A.group_bytes;
     cd *Uts = reinterpret_cast<cd *>(wb);
     cd *Qs = reinterpret_cast<cd *>(wb + A.off_Q);
     cd *Ts = reinterpret_cast<cd *>(wb + A.off_T);
     cd *Bs = reinterpret_cast<cd *>(wb + A.off_B);
     cd *Ys = reinterpret_cast<cd *>(wb + A.off_Y);
     cd *Gs = reinterpret_cast<cd *>(wb + A.off_G);
-    cd *NZ = reinterpret_cast<cd *>(wb + A.off_NZ);
-    cd *Ns = NZ, *Zs = NZ + (size_t)A.NB * T, *GX = NZ;
-    cd *Uv = reinterpret_cast<cd *>(wb + A.off_U);
-    cd *Vv = reinterpret_cast<cd *>(wb + A.off_V);
+    cd *Ns = reinterpret_cast<cd *>(wb + A.off_NZ);  // node factors, then their inverses, then G_X
+    cd *GX = Ns;
+    cd *g1v = reinterpret_cast<cd *>(wb + A.off_g1);  // forward: U vectors
+    cd *g2v = reinterpret_cast<cd *>(wb + A.off_g2);  // forward: V vectors
     cd *y1v = reinterpret_cast<cd *>(wb + A.off_y1);
     cd *y2v = reinterpret_cast<cd *>(wb + A.off_y2);
     cd *pf = reinterpret_cast<cd *>(wb + A.off_pf);
-    cd *inv = reinterpret_cast<cd *>(wb + A.off_inv);
     cd *cf = reinterpret_cast<cd *>(wb + A.off_cf);
-    unsigned long long *best = reinterpret_cast<unsigned long long *>(wb + A.off_best);
-    int *ints = reinterpret_cast<int *>(wb + A.off_int);
+    cd *invh = reinterpret_cast<cd *>(wb + A.off_invh);
+    int *pos = reinterpret_cast<int *>(wb + A.off_int);
+    long long *slot = reinterpret_cast<long long *>(wb + A.off_tile);
     uint8_t *acth = wb + A.off_acth;
     uint8_t *kh = wb + A.off_kh;
     uint8_t *ph = wb + A.off_ph;
+    uint8_t *kc = wb + A.off_kc;  // signed-permutation snapshots: the two rows of each column of Qt
 
     const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
     const int64_t ntiles = A.W * A.nchunks;
     const size_t rec = 1 + (size_t)n * n;
-    (void)wpb;
     for (;;) {
-        unsigned long long tk = 0;
-        if (lane == 0) tk = atomicAdd(A.counter, 1ull);
-        const int64_t tile = (int64_t)__shfl_sync(QCS_FULL, tk, 0);
+        if (t == 0) *slot = (long long)atomicAdd(A.counter, 1ull);
+        group_sync(bar);
+        const int64_t tile = (int64_t)*slot;  // rewritten only after the barriers below
         if (tile >= ntiles) break;
         const int ch = (int)(tile / A.W);  // chunk-major: a snapshot chunk is fetched once
         const int64_t w = tile - (int64_t)ch * A.W;
@@ -255,64 +276,89 @@ __global__ void __launch_bounds__(128) grad_pair_kernel(const __grid_constant__ 
         const int64_t p1 = p0 + A.chunk < L ? p0 + A.chunk : L;
         cd *out = A.partial + (w * A.nchunks + ch) * rec;
         cd Ssum = cmk(0.0, 0.0);
-        for (int e = lane; e < n * n; e += 32) Gs[e] = cmk(0.0, 0.0);
+        for (int e = t; e < n * n; e += kGroup) Gs[e] = cmk(0.0, 0.0);
         if (p0 < L) {
             const cd *Utw = A.Ut + w * n * n;
-            for (int e = lane; e < n * n; e += 32) Uts[(e / n) * lu + (e % n)] = Utw[e];
+            for (int e = t; e < n * n; e += kGroup) Uts[(e / n) * lu + (e % n)] = Utw[e];
             for (int64_t pq = p0; pq < p1; ++pq) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
-                __syncwarp();
-                load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
-                for (int e = lane; e < T; e += 32) Ys[e] = cmk(0.0, 0.0);
-                __syncwarp();
-                build_T(n, Uts, Qs, Ts, lane);
-                __syncwarp();
-                build_B(n, ne, Ts, Bs, tab, lane);
-                __syncwarp();
+                const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
+                const bool sp = gq && gq[0] != 0xFF;  // signed permutation: gathers instead of products
+                group_sync(bar);
+                if (sp) {
+                    // column k of Qt has exactly two nonzeros, in rows kc[2k] < kc[2k+1]
+                    for (int c = t; c < n2; c += kGroup) {
+                        const int k = gq[c] >> 2;
+                        int slot = 0;
+                        for (int c2 = 0; c2 < c; ++c2) slot += ((gq[c2] >> 2) == k) ? 1 : 0;
+                        kc[2 * k + slot] = (uint8_t)c;
+                    }
+                } else {
+                    load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
+                }
+                for (int e = t; e < T; e += kGroup) Ys[e] = cmk(0.0, 0.0);
+                group_sync(bar);
+                if (sp) build_T_gather(n, Uts, gq, Ts, t, kGroup);
+                else build_T(n, Uts, Qs, Ts, t, kGroup);
+                group_sync(bar);
+                build_B(n, ne, Ts, Bs, tab, t, kGroup);
+                group_sync(bar);
                 cd S = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
                     const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                    node_factor(A, k0, nb, Bs, Ns, Uv, Vv, pf, inv, best, ints, acth, kh, ph, tab, lane);
-                    node_inverse(A, nb, Ns, Zs, Uv, Vv, y1v, y2v, acth, kh, ph, lane);
-                    if (lane < nb) cf[lane] = cscale(cmul(A.gamma[k0 + lane], pf[lane]), 0.5);
-                    if (lane == 0)
+                    node_factor(A, k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar);
+                    node_inverse(A, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                    if (t < nb) cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
+                    if (t == 0)
                         for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
-                    __syncwarp();
-                    for (int e = lane; e < T; e += 32) {
+                    group_sync(bar);
+                    for (int e = t; e < T; e += kGroup) {
                         cd y = Ys[e];
-                        for (int v = 0; v < nb; ++v) cfma(y, cf[v], Zs[v * T + e]);
+                        for (int v = 0; v < nb; ++v) cfma(y, cf[v], Ns[v * T + e]);
                         Ys[e] = y;
                     }
-                    __syncwarp();
+                    group_sync(bar);
                 }
-                if (lane == 0) {
+                if (t == 0) {
                     if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
                     Ssum = cadd(Ssum, S);
                 }
                 // G_X / 2 = Y (X J): (XJ)[b][2k] = -X[b][2k+1], (XJ)[b][2k+1] = X[b][2k]
-                for (int e = lane; e < m * n2; e += 32) {
+                for (int e = t; e < m * n2; e += kGroup) {
                     const int a = e / n2, c = e - a * n2;
                     const int cx = c ^ 1;
                     const bool neg = !(c & 1);
                     cd acc = cmk(0.0, 0.0);
                     for (int b = 0; b < ne; ++b) cfma(acc, skew_at(Ys, a, b), Ts[b * lt + cx]);
                     for (int r = 0; r < m - ne; ++r) {
-                        cd t = Ts[(ne + (r >> 1)) * lt + cx];
-                        double x = (r & 1) ? -t.y : t.x;
+                        cd tt = Ts[(ne + (r >> 1)) * lt + cx];
+                        double x = (r & 1) ? -tt.y : tt.x;
                         crfma(acc, skew_at(Ys, a, ne + r), x);
                     }
                     GX[e] = neg ? cneg(acc) : acc;
                 }
-                __syncwarp();
+                group_sync(bar);
                 // empty rows: Ht_i = G[ne+2i] - i G[ne+2i+1] into row ne+2i (factor 1/2 applied at the end)
-                for (int e = lane; e < A.d * n2; e += 32) {
+                for (int e = t; e < A.d * n2; e += kGroup) {
                     const int i = e / n2, c = e - i * n2;
                     cd g0 = GX[(ne + 2 * i) * n2 + c], g1 = GX[(ne + 2 * i + 1) * n2 + c];
                     GX[(ne + 2 * i) * n2 + c] = cmk(g0.x + g1.y, g0.y - g1.x);
                 }
-                __syncwarp();
+                group_sync(bar);
                 // Gamma1 (rows < ne) += G[occ] Qt ; Gamma2 (rows >= ne) += Ht conj(Qt)
-                for (int e = lane; e < n * n; e += 32) {
+                if (sp) {
+                    for (int e = t; e < n * n; e += kGroup) {
+                        const int j = e / n, k = e - j * n;
+                        const cd *g = GX + (j < ne ? j : ne + 2 * (j - ne)) * n2;
+                        cd acc = Gs[e];
+                        for (int h = 0; h < 2; ++h) {
+                            const int c = kc[2 * k + h];
+                            const unsigned ph = gq[c] & 3u;
+                            acc = cadd(acc, mul_phase(g[c], j < ne ? ph : ((4u - ph) & 3u)));
+                        }
+                        Gs[e] = acc;
+                    }
+                } else for (int e = t; e < n * n; e += kGroup) {
                     const int j = e / n, k = e - j * n;
                     cd acc = Gs[e];
                     if (j < ne) {
@@ -324,12 +370,11 @@ __global__ void __launch_bounds__(128) grad_pair_kernel(const __grid_constant__ 
                     }
                     Gs[e] = acc;
                 }
-                __syncwarp();
             }
         }
-        __syncwarp();
-        for (int e = lane; e < n * n; e += 32) out[1 + e] = Gs[e];
-        if (lane == 0) out[0] = Ssum;
+        group_sync(bar);
+        for (int e = t; e < n * n; e += kGroup) out[1 + e] = Gs[e];
+        if (t == 0) out[0] = Ssum;
     }
 }
 
@@ -351,8 +396,6 @@ __global__ void grad_epilogue_kernel(int n, int ne, int64_t W, int64_t P, int nc
     cd *Rs = Mm + ne * n;      // R (ne x ne)
     cd *Ad = Rs + ne * ne;     // adj(R)
     cd *Sv = Ad + ne * ne;     // S
-    cd *LU = Sv + 1;           // (Lambda U_occ) scratch (ne x ne) stored in V1 later
-    (void)LU;
     const double sq2 = 1.41421356237309504880;
     const size_t rec = 1 + (size_t)nn;
     for (int64_t w = (int64_t)blockIdx.x * wpb + warp; w < W; w += (int64_t)gridDim.x * wpb) {
@@ -481,7 +524,7 @@ __global__ void force_bias_kernel(int n, int ne, int64_t W, int nchol, const cd 
     }
 }
 
-size_t grad_warp_layout(GradArgs &A) {
+size_t grad_group_layout(GradArgs &A) {
     const int n = A.n, m = A.m, T = tri_count(m), NB = A.NB, S = m / 2;
     size_t o = align16((size_t)n * ld_ut(n) * sizeof(cd));
     A.off_Q = (int)o;
@@ -495,12 +538,12 @@ size_t grad_warp_layout(GradArgs &A) {
     A.off_G = (int)o;
     o = align16(o + (size_t)n * n * sizeof(cd));
     A.off_NZ = (int)o;
-    size_t nz = (size_t)2 * NB * T;
+    size_t nz = (size_t)NB * T;
     if ((size_t)m * 2 * n > nz) nz = (size_t)m * 2 * n;
     o = align16(o + nz * sizeof(cd));
-    A.off_U = (int)o;
+    A.off_g1 = (int)o;
     o = align16(o + (size_t)NB * m * sizeof(cd));
-    A.off_V = (int)o;
+    A.off_g2 = (int)o;
     o = align16(o + (size_t)NB * m * sizeof(cd));
     A.off_y1 = (int)o;
     o = align16(o + (size_t)NB * m * sizeof(cd));
@@ -508,20 +551,22 @@ size_t grad_warp_layout(GradArgs &A) {
     o = align16(o + (size_t)NB * m * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNBG * sizeof(cd));
-    A.off_inv = (int)o;
-    o = align16(o + (size_t)kMaxNBG * sizeof(cd));
     A.off_cf = (int)o;
     o = align16(o + (size_t)kMaxNBG * sizeof(cd));
-    A.off_best = (int)o;
-    o = align16(o + (size_t)kMaxNBG * sizeof(unsigned long long));
+    A.off_invh = (int)o;
+    o = align16(o + (size_t)NB * S * sizeof(cd));
     A.off_int = (int)o;
     o = align16(o + (size_t)kMaxNBG * sizeof(int));
+    A.off_tile = (int)o;
+    o = align16(o + sizeof(long long));
     A.off_acth = (int)o;
     o = align16(o + (size_t)NB * (S + 1) * m);
     A.off_kh = (int)o;
     o = align16(o + (size_t)NB * S);
     A.off_ph = (int)o;
     o = align16(o + (size_t)NB * S);
+    A.off_kc = (int)o;
+    o = align16(o + (size_t)2 * n);
     return o;
 }
 
@@ -540,11 +585,10 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     A.nchunks = L.nchunks;
     A.W = L.W;
     A.P = L.P;
-    A.NB = L.plan.nev >= 2 ? 2 : 1;
-    A.warp_bytes = (int)grad_warp_layout(A);
     A.tab_bytes = (int)align16((size_t)tri_count(A.m) * sizeof(uint16_t));
     A.Ut = L.Ut;
     A.Qt = L.s->Qt;
+    A.gth = L.s->gth;
     A.idx = L.s->idx;
     A.d_count = L.s->d_count;
     A.partial = L.partial;
@@ -554,24 +598,47 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
         A.wnode[k] = L.plan.wnode[k];
         A.gamma[k] = L.plan.gamma[k];
     }
-    int wpb = 4;
-    while (wpb > 1 && (size_t)A.tab_bytes + (size_t)wpb * A.warp_bytes > ctx->smem_optin) --wpb;
-    size_t smem = (size_t)A.tab_bytes + (size_t)wpb * A.warp_bytes;
-    if (smem > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "grad kernel: shared memory too large");
+    // Node matrices per round (NB) and groups per block: the most resident groups
+    // (at most 4 per SM, i.e. two warps per SM sub-partition), then the largest NB.
+    int best_nb = 0, best_g = 1, best_score = -1;
+    const int nbmax = L.plan.nev < kMaxNBG ? L.plan.nev : kMaxNBG;
+    for (int nb = nbmax; nb >= 1; --nb) {
+        A.NB = nb;
+        const size_t gb = grad_group_layout(A);
+        for (int g = 2; g >= 1; --g) {
+            const size_t sm = (size_t)A.tab_bytes + (size_t)g * gb;
+            if (sm > ctx->smem_optin) continue;
+            int per_sm = (int)(ctx->smem_per_sm / (sm + 1024));
+            if (per_sm > 2) per_sm = 2;
+            int groups = per_sm * g;
+            if (groups > 4) groups = 4;
+            const int score = groups * 16 + nb;
+            if (per_sm >= 1 && score > best_score) {
+                best_score = score;
+                best_nb = nb;
+                best_g = g;
+            }
+        }
+    }
+    if (best_nb == 0) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "grad kernel: shared memory too large");
+    A.NB = best_nb;
+    A.group_bytes = (int)grad_group_layout(A);
+    const int threads = best_g * kGroup;
+    size_t smem = (size_t)A.tab_bytes + (size_t)best_g * A.group_bytes;
     if (qcs_set_smem(ctx, (const void *)grad_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_pair_kernel, wpb * 32, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_pair_kernel, threads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     int64_t ntiles = L.W * L.nchunks;
     int64_t blocks = (int64_t)ctx->num_sms * per_sm;
-    int64_t need = (ntiles + wpb - 1) / wpb;
+    int64_t need = (ntiles + best_g - 1) / best_g;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return qcs_fail(ctx, QCS_ERR_CUDA, "grad tile counter reset");
     qcs_prof_begin(ctx, st);
-    grad_pair_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(A);
+    grad_pair_kernel<<<(unsigned)blocks, threads, smem, st>>>(A);
     qcs_prof_end(ctx, st);
     qcs_status r = qcs_check_launch(ctx, "grad_pair_kernel");
     if (r != QCS_OK) return r;

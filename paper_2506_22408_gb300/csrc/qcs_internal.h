@@ -38,9 +38,23 @@ struct qcs_snapshots {
     cd *Qt = nullptr;         // P x 2n x n complexified sign-folded rows
     int8_t *parity = nullptr; // P: +1 / -1 (0: singular or non-finite Q)
     int *idx = nullptr;       // P: indices with parity +1, ascending (first *d_count valid)
-    int *d_count = nullptr;   // 1: number of parity +1 snapshots
+    int *d_count = nullptr;   // 2: number of parity +1 snapshots, number of signed permutations
+    uint8_t *gth = nullptr;   // P x 2n gather codes of signed-permutation snapshots (row c of Qt:
+                              // (k << 2) | phase, phase 0..3 = 1, i, -1, -i); first code 0xFF: dense
     void *split_hi = nullptr; // P x 4 KB TF32 operand slabs (split precision), built on first use
     void *split_lo = nullptr;
+};
+
+// Makes `dev` current for the scope of the guard, then restores the previous device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
 };
 
 // Helpers implemented in qcs_api.cu

@@ -44,6 +44,7 @@ struct PairArgs {
     const cd *Ut;
     const cd *pref;
     const cd *Qt;
+    const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
     const int *idx;
     const int *d_count;
     cd *partial;
@@ -92,10 +93,15 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
         const cd prefw = A.pref[w];
         for (int64_t pq = p0 + warp; pq < p1; pq += wpb) {
             const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+            const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
             __syncwarp();
-            load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
-            __syncwarp();
-            build_T(n, Uts, Qs, Ts, lane);
+            if (gq && gq[0] != 0xFF) {
+                build_T_gather(n, Uts, gq, Ts, lane);  // signed permutation: no products
+            } else {
+                load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
+                __syncwarp();
+                build_T(n, Uts, Qs, Ts, lane);
+            }
             __syncwarp();
             build_B(A.n, A.ne, Ts, Bs, tab, lane);
             __syncwarp();
@@ -251,6 +257,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.Ut = L.Ut;
     A.pref = L.pref;
     A.Qt = L.s->Qt;
+    A.gth = L.s->gth;
     A.idx = L.s->idx;
     A.d_count = L.s->d_count;
     A.partial = L.partial;

@@ -23,11 +23,12 @@ __host__ __device__ __forceinline__ int ld_ut(int n) { return n + 1; }   // Ut: 
 __host__ __device__ __forceinline__ int ld_qt(int n) { return n + 1; }   // Qt: 2n rows of n
 __host__ __device__ __forceinline__ int ld_t(int n) { return 2 * n + 1; }  // T: n rows of 2n
 
-// T[j][c] = sum_k Ut[j][k] Qt[c][k]  (n x 2n; entries spread over the lanes)
+// T[j][c] = sum_k Ut[j][k] Qt[c][k]  (n x 2n; entries spread over the nthr
+// threads that share the pair, lane = this thread's index among them)
 __device__ inline void build_T(int n, const cd *__restrict__ Uts, const cd *__restrict__ Qs, cd *__restrict__ Ts,
-                               int lane) {
+                               int lane, int nthr = 32) {
     const int n2 = 2 * n, lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
-    for (int e = lane; e < n * n2; e += 32) {
+    for (int e = lane; e < n * n2; e += nthr) {
         int j = e / n2, c = e - j * n2;
         const cd *ur = Uts + j * lu, *qr = Qs + c * lq;
         cd s = cmk(0.0, 0.0);
@@ -36,10 +37,32 @@ __device__ inline void build_T(int n, const cd *__restrict__ Uts, const cd *__re
     }
 }
 
+// x * ph for a phase code ph = 0..3 (1, i, -1, -i): a swap of the parts and sign
+// flips of the bit patterns, no floating-point arithmetic.
+__device__ __forceinline__ cd mul_phase(cd x, unsigned ph) {
+    cd r = (ph & 1u) ? cmk(x.y, x.x) : x;
+    const bool fre = ph == 1u || ph == 2u, fim = ph >= 2u;
+    if (fre) r.x = __longlong_as_double(__double_as_longlong(r.x) ^ (long long)0x8000000000000000ull);
+    if (fim) r.y = __longlong_as_double(__double_as_longlong(r.y) ^ (long long)0x8000000000000000ull);
+    return r;
+}
+
+// Signed-permutation snapshot: row c of Qt has one nonzero entry, the phase
+// code & 3 at column code >> 2, so T[j][c] = Ut[j][k_c] ph_c is a gather.
+__device__ inline void build_T_gather(int n, const cd *__restrict__ Uts, const uint8_t *__restrict__ code,
+                                      cd *__restrict__ Ts, int lane, int nthr = 32) {
+    const int n2 = 2 * n, lu = ld_ut(n), lt = ld_t(n);
+    for (int e = lane; e < n * n2; e += nthr) {
+        const int j = e / n2, c = e - j * n2;
+        const unsigned q = code[c];
+        Ts[j * lt + c] = mul_phase(Uts[j * lu + (int)(q >> 2)], q & 3u);
+    }
+}
+
 // Stage a snapshot's rows Qt (2n x n, global) into padded shared rows.
-__device__ inline void load_Qt(int n, const cd *__restrict__ Qg, cd *__restrict__ Qs, int lane) {
+__device__ inline void load_Qt(int n, const cd *__restrict__ Qg, cd *__restrict__ Qs, int lane, int nthr = 32) {
     const int lq = ld_qt(n);
-    for (int e = lane; e < 2 * n * n; e += 32) {
+    for (int e = lane; e < 2 * n * n; e += nthr) {
         int c = e / n, k = e - c * n;
         Qs[c * lq + k] = Qg[e];
     }
@@ -53,11 +76,11 @@ __device__ __forceinline__ void pair_of(const uint16_t *tab, int t, int &a, int 
 
 // B^(s) (packed upper, m x m) from T (n x 2n).
 __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__restrict__ Bs,
-                               const uint16_t *__restrict__ tab, int lane) {
+                               const uint16_t *__restrict__ tab, int lane, int nthr = 32) {
     const int d = n - ne, n2 = ld_t(n);
     // occupied x occupied: complex x complex
     const int c1 = tri_count(ne);
-    for (int e = lane; e < c1; e += 32) {
+    for (int e = lane; e < c1; e += nthr) {
         int a, b;
         pair_of(tab, e, a, b);
         const cd *Ta = Ts + a * n2, *Tb = Ts + b * n2;
@@ -72,7 +95,7 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
     // Re T_j (r even) or -Im T_j (r odd); the sign is applied once at the end.
     const int twod = 2 * d;
     const int c2 = ne * twod;
-    for (int e = lane; e < c2; e += 32) {
+    for (int e = lane; e < c2; e += nthr) {
         int a = e / twod, r = e - a * twod;
         int j = ne + (r >> 1);
         bool odd = r & 1;
@@ -88,7 +111,7 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
     }
     // empty x empty: real x real
     const int c3 = tri_count(twod);
-    for (int e = lane; e < c3; e += 32) {
+    for (int e = lane; e < c3; e += nthr) {
         int a, b;
         pair_of(tab, e, a, b);
         const cd *Ta = Ts + (ne + (a >> 1)) * n2, *Tb = Ts + (ne + (b >> 1)) * n2;

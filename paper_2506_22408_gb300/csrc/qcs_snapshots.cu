@@ -14,13 +14,20 @@
 // coefficient sequence is palindromic up to pi_p while its weights are
 // symmetric).  det(Q_p) = +-1 is obtained from an LU factorisation with
 // partial pivoting (only its sign is used).
+//
+// Snapshots that are signed permutations (every row of Q_p has one nonzero
+// entry, exactly +-1: the ensemble of the paper's experiment) also get gather
+// codes: row c of Qt then has a single nonzero, a phase 1, i, -1 or -i at column
+// k, stored as (k << 2) | phase, and the pair kernels form the congruence by a
+// gather instead of a product.
 #include "qcs_internal.h"
 
 namespace {
 
 // One warp per snapshot.  Dynamic shared memory: warps * (2n)^2 doubles.
 __global__ void snapshot_prepare_kernel(int n, int64_t P, const double *__restrict__ Q, const uint8_t *__restrict__ b,
-                                        cd *__restrict__ Qt, int8_t *__restrict__ parity, unsigned *status) {
+                                        cd *__restrict__ Qt, int8_t *__restrict__ parity, uint8_t *__restrict__ gth,
+                                        int *__restrict__ nsp, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = 2 * n;
     const int lane = threadIdx.x & 31;
@@ -49,6 +56,35 @@ __global__ void snapshot_prepare_kernel(int n, int64_t P, const double *__restri
         }
         bad = __any_sync(QCS_FULL, bad);
         __syncwarp();
+        if (gth) {
+            // signed permutation?  one lane per row of Q; codes of the rows of Qt
+            bool ok = true;
+            for (int c = lane; c < N; c += 32) {
+                int cnt = 0, col = 0;
+                double val = 0.0;
+                for (int j = 0; j < N; ++j) {
+                    const double v = A[c * N + j];
+                    if (v != 0.0) {
+                        ++cnt;
+                        col = j;
+                        val = v;
+                    }
+                }
+                const bool row_ok = cnt == 1 && (val == 1.0 || val == -1.0);
+                ok = ok && row_ok;
+                // Qt[c][k] = s_c Q[c][2k] - i s_c Q[c][2k+1], s_c the sign folded into row c
+                const bool flip = (c & 1) && (bp[c >> 1] & 1);
+                const bool pos = (val > 0.0) != flip;
+                const int ph = (col & 1) ? (pos ? 3 : 1) : (pos ? 0 : 2);
+                gth[p * N + c] = row_ok ? (uint8_t)(((col >> 1) << 2) | ph) : (uint8_t)0xFF;
+            }
+            ok = __all_sync(QCS_FULL, ok);
+            __syncwarp();
+            if (lane == 0) {
+                if (!ok) gth[p * N] = 0xFF;
+                else atomicAdd(nsp, 1);
+            }
+        }
         // sign of det(Q) by LU with partial pivoting (rows spread over lanes)
         int sign = 1;
         bool singular = false;
@@ -144,8 +180,10 @@ qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const doubl
         if (qcs_set_smem(ctx, (const void *)snapshot_prepare_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
         int64_t blocks = (s->P + wpb - 1) / wpb;
         if (blocks > 4 * ctx->num_sms * 8) blocks = 4 * ctx->num_sms * 8;
-        snapshot_prepare_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, s->P, d_Q, d_b, s->Qt, s->parity,
-                                                                          ctx->d_status);
+        if (cudaMemsetAsync(s->d_count + 1, 0, sizeof(int), st) != cudaSuccess)
+            return qcs_fail(ctx, QCS_ERR_CUDA, "snapshot counter reset");
+        snapshot_prepare_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, s->P, d_Q, d_b, s->Qt, s->parity, s->gth,
+                                                                          s->d_count + 1, ctx->d_status);
         if (qcs_check_launch(ctx, "snapshot_prepare_kernel") != QCS_OK) return QCS_ERR_CUDA;
     }
     snapshot_compact_kernel<<<1, 1024, 0, st>>>(s->P, s->parity, s->idx, s->d_count);

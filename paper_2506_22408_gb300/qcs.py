@@ -35,6 +35,8 @@ EXPORTED = [
     "qcs_snapshots_modes", "qcs_overlap", "qcs_overlap_grad", "qcs_force_bias", "qcs_overlap_flops_per_pair",
     "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair", "qcs_overlap_noalloc",
     "qcs_autotune", "qcs_set_config", "qcs_overlap_batched", "qcs_node_plan_get",
+    "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
+    "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -96,6 +98,13 @@ def load(build_if_missing: bool = True):
         lib.qcs_grad_flops_per_pair.argtypes = [i32, i32, i32, u32]
         lib.qcs_grad_flops_per_pair.restype = f64
         lib.qcs_node_plan_get.argtypes = [i32, i32, i32, u32, ctypes.POINTER(i32), P, P]
+        lib.qcs_snapshots_signed_perm_count.argtypes = [P, ctypes.POINTER(i64), P]
+        lib.qcs_shadow_rdm.argtypes = [P, P, P, P, P, P, P, P]
+        lib.qcs_shadow_rdm_flops.argtypes = [i32, i64]
+        lib.qcs_shadow_rdm_flops.restype = f64
+        for fn in ("qcs_overlap_flops_per_pair_signed_perm", "qcs_grad_flops_per_pair_signed_perm"):
+            getattr(lib, fn).argtypes = [i32, i32, i32, u32]
+            getattr(lib, fn).restype = f64
         lib.qcs_overlap_batched.argtypes = [P, i32, ctypes.POINTER(_System), ctypes.POINTER(_Opts), P]
         lib.qcs_autotune.argtypes = [P, i32, i32, i32, u32, ctypes.POINTER(i32)]
         lib.qcs_set_config.argtypes = [P, i32, i32, i32, u32, i32]
@@ -229,6 +238,13 @@ class Snapshots:
         self.ctx.check(self.ctx.lib.qcs_snapshots_parity(self.h, _ptr(out), _stream()))
         return out
 
+    def signed_perm_count(self) -> int:
+        """Snapshots of the set that are signed permutations (gather path); waits for
+        the current stream."""
+        c = ctypes.c_int64(0)
+        self.ctx.check(self.ctx.lib.qcs_snapshots_signed_perm_count(self.h, ctypes.byref(c), _stream()))
+        return int(c.value)
+
     def close(self):
         if getattr(self, "h", None):
             self.ctx.lib.qcs_snapshots_free(self.h)
@@ -331,6 +347,37 @@ def flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
 
 def grad_flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
     return float(load().qcs_grad_flops_per_pair(n, ne, nodes, flags))
+
+
+def flops_per_pair_signed_perm(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
+    return float(load().qcs_overlap_flops_per_pair_signed_perm(n, ne, nodes, flags))
+
+
+def grad_flops_per_pair_signed_perm(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
+    return float(load().qcs_grad_flops_per_pair_signed_perm(n, ne, nodes, flags))
+
+
+def shadow_rdm(ctx: Context, snaps: Snapshots, R: torch.Tensor | None = None, deg4: bool = True):
+    """Shadow estimates from the snapshot set (qcs_shadow_rdm): dict of device tensors
+    gam2 (2n x 2n, <g~_mu g~_nu> = i gam2), gam4 (C(2n,4), when deg4), rdm1 (n x n
+    complex) and npart (scalar)."""
+    from math import comb
+
+    n = snaps.n
+    dev = f"cuda:{ctx.device}"
+    if R is not None:
+        _need_cuda(R, "R", torch.float64)
+    gam2 = torch.empty((2 * n, 2 * n), dtype=torch.float64, device=dev)
+    gam4 = torch.empty(comb(2 * n, 4), dtype=torch.float64, device=dev) if deg4 else None
+    rdm1 = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    npart = torch.empty((), dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.qcs_shadow_rdm(ctx.h, snaps.h, _ptr(R) if R is not None else None, _ptr(gam2),
+                                     _ptr(gam4) if gam4 is not None else None, _ptr(rdm1), _ptr(npart), _stream()))
+    return dict(gam2=gam2, gam4=gam4, rdm1=rdm1, npart=npart)
+
+
+def shadow_rdm_flops(n: int, P: int) -> float:
+    return float(load().qcs_shadow_rdm_flops(n, P))
 
 
 def node_plan(n: int, ne: int, nodes: int = 0, flags: int = 0):

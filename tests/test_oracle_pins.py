@@ -406,6 +406,74 @@ def test_force_bias_exact_for_slater_trial():
     assert np.allclose(xb2, -0.1 * ref, atol=1e-12)
 
 
+# ------------------------------- shadow RDMs (Supplementary "Reduced Density Matrices")
+
+
+def _rotated_ops(F, R):
+    """Rotated Majoranas g~_mu = sum_nu R_{mu nu} g_nu and modes a~_p = (g~_2p + i g~_2p+1)/2."""
+    N2 = 2 * F.n
+    g = F.gamma if R is None else [sum(R[m, v] * F.gamma[v] for v in range(N2)) for m in range(N2)]
+    a = [0.5 * (g[2 * p] + 1j * g[2 * p + 1]) for p in range(F.n)]
+    return g, a
+
+
+def _exact_rdm_quantities(F, Psi, R):
+    g, a = _rotated_ops(F, R)
+    N2 = 2 * F.n
+    E2 = np.array([[np.vdot(Psi, g[m] @ (g[v] @ Psi)) if m != v else 0.0 for v in range(N2)] for m in range(N2)])
+    E4 = np.array([np.vdot(Psi, g[i] @ g[j] @ g[k] @ g[l] @ Psi) for i, j, k, l in itertools.combinations(range(N2), 4)])
+    D = np.array([[np.vdot(Psi, a[p].conj().T @ (a[q] @ Psi)) for q in range(F.n)] for p in range(F.n)])
+    return E2, E4, D
+
+
+def _rdm_group_check(orc_v, n, rng, rotate) -> float:
+    """Largest deviation of the Born-weighted signed-permutation-group average of the
+    shadow estimates from the exact expectation values of a random N-particle state."""
+    F = Fock(n)
+    Psi = _random_eta_state(rng, F, n - 1)
+    group = np.array(list(signed_permutation_group(2 * n)))
+    Qs, bs, ws = _born_table(F, group, Psi)
+    R = synth.haar_orthogonal(rng, 2 * n, 1)[0] if rotate else None
+    est = orc_v.shadow_rdm(Qs, bs, w=ws, R=R, deg4=True)
+    E2, E4, D = _exact_rdm_quantities(F, Psi, R)
+    err = max(np.abs(1j * est["gam2"] - E2).max(), np.abs(est["gam4"] - E4).max(), np.abs(est["rdm1"] - D).max(),
+              abs(est["npart"] - np.trace(D).real))
+    if not rotate:
+        err = max(err, abs(est["npart"] - (n - 1)))
+    return err
+
+
+@pytest.mark.parametrize("n", [2, 3])
+@pytest.mark.parametrize("rotate", [False, True])
+def test_shadow_rdm_exact_group_average(n, rotate):
+    """Averaged over the whole signed-permutation group of O(2n) with Born weights, the
+    shadow estimates of <g_S> (|S| = 2, 4), of the 1-RDM and of the particle number equal
+    the exact expectation values of the measured (n-1)-particle state, computed with
+    Fock-space matrices; with a rotation R the same holds for g~ = R g.  This pins the
+    weights C(2n,|S|)/C(n,|S|/2), the Pfaffian signs and the Majorana-to-mode map."""
+    rng = np.random.default_rng(700 + 10 * n + rotate)
+    assert _rdm_group_check(orc, n, rng, rotate) <= 1e-12
+
+
+def test_shadow_rdm_single_snapshot_closed_form():
+    """One snapshot: gam2 is (2n-1) times the rotated covariance Q^T C_b Q, and a
+    product of four distinct Majoranas gets C(2n,4)/C(n,2) times minus the Pfaffian
+    of the 4 x 4 block."""
+    rng = np.random.default_rng(77)
+    n = 4
+    Q = synth.haar_orthogonal(rng, 2 * n, 1)
+    b = synth.uniform_bits(rng, n, 1)
+    G = Q[0].T @ orc.covariance(n, b[0]) @ Q[0]
+    est = orc.shadow_rdm(Q, b, deg4=True)
+    off = ~np.eye(2 * n, dtype=bool)
+    assert np.abs(est["gam2"][off] - (2 * n - 1) * G[off]).max() < 1e-12
+    K4 = comb(2 * n, 4) / comb(n, 2)
+    for t, (i, j, k, l) in enumerate(itertools.combinations(range(2 * n), 4)):
+        blk = G[np.ix_([i, j, k, l], [i, j, k, l])]
+        pf = pfaffian_by_matchings(blk)
+        assert abs(est["gam4"][t] - K4 * (-pf)) < 1e-11
+
+
 # ---------------------------------------------- the pins catch mistakes
 
 
@@ -426,6 +494,8 @@ def _pin_suite_passes(v) -> bool:
             ob = F.estimator(Phi, F.shadow_state(Q, b))
             if abs(o - ob) > 1e-9 * max(abs(ob), 1e-12):
                 return False
+    if _rdm_group_check(v, 2, rng, rotate=False) > 1e-10:
+        return False
     return True
 
 
