@@ -125,6 +125,7 @@ KERNEL_SOURCES = {
     "pair_overlap_kernel": ["qcs_overlap.cu", "qcs_pair.cuh", "qcs_common.cuh"],
     "split_pair_kernel": ["qcs_split.cu", "qcs_pair.cuh", "qcs_tc.cuh", "qcs_common.cuh"],
     "grad_pair_kernel": ["qcs_grad.cu", "qcs_pair.cuh", "qcs_common.cuh"],
+    "rdm_syrk_kernel": ["qcs_rdm.cu"],
 }
 
 
@@ -490,6 +491,53 @@ def run_variants(args, ctx, dev, flush, barrier, ws, steps=3):
     return out
 
 
+def run_rdm(args, ctx, dev, flush, barrier, ws, steps=3):
+    """Shadow RDM estimates (Supplementary "Reduced Density Matrices") from the
+    paper's shadow count: n=16, 60000 Haar snapshots, uniform b; one step builds the
+    snapshot set and runs qcs_shadow_rdm with the four-Majorana estimates."""
+    import torch
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    n, P = 16, args.rdm_snapshots
+    rng = np.random.default_rng(0)
+    Qd = torch.from_numpy(synth.haar_orthogonal(rng, 2 * n, P)).to(dev)
+    bd = torch.from_numpy(synth.uniform_bits(rng, n, P)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        snaps = qcs.Snapshots(ctx, Qd, bd)
+        return qcs.shadow_rdm(ctx, snaps, deg4=True)
+
+    for _ in range(2):
+        step()
+    barrier()
+    ctx.profile(True)
+    ctx.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        out = step()
+        ev[i][1].record(stream)
+    barrier()
+    ctx.profile(False)
+    kms, kl = ctx.profile_read()
+    assert ctx.sync_status() == 0
+    t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+    avg = kms / max(kl, 1)
+    fl = qcs.shadow_rdm_flops(n, P)
+    ach = fl / (avg * 1e-3) / 1e12
+    return {"metric": "snapshots/s, shadow estimates of the 1-RDM, particle number and all four-Majorana correlators",
+            "value": ws * P * steps / t, "unit": "snapshots/s", "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "config": {"workload": f"shadow RDM n={n} {P} snapshots (Haar Q, uniform b, seed 0)"},
+            "particle_number": float(out["npart"].item()),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "rdm_syrk_kernel", "kernel_ms": avg,
+                         "flops_per_launch": fl,
+                         "traffic": traffic_for("rdm_syrk_kernel", f"shadow RDM n={n} {P} snapshots")}}
+
+
 def cpu_baseline(wl, data, target_s=10.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle.oracle as orc
@@ -559,6 +607,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
     ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
+    ap.add_argument("--no-rdm", action="store_true", help="skip the shadow RDM workload")
+    ap.add_argument("--rdm-snapshots", type=int, default=60000, help="snapshots of the shadow RDM workload")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the parity-consistent and signed-permutation snapshot ensembles")
     ap.add_argument("--prec-walkers", type=int, default=0, help="override the split-precision walkers (profiling)")
@@ -652,6 +702,11 @@ def main():
     if not args.no_variants:
         variants = run_variants(args, ctx, dev, flush, barrier, ws)
 
+    # ---------------- shadow RDM estimates (walker-independent)
+    rdm = None
+    if not args.no_rdm:
+        rdm = run_rdm(args, ctx, dev, flush, barrier, ws)
+
     # ---------------- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -695,6 +750,7 @@ def main():
             "precision": precision,
             "roots_of_unity_plan": dft,
             "ensembles": variants,
+            "rdm": rdm,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

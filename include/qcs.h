@@ -212,6 +212,33 @@ qcs_status qcs_shadow_rdm(qcs_ctx *ctx, const qcs_snapshots *s, const double *d_
  * requested) for n modes and P snapshots. */
 double qcs_shadow_rdm_flops(int n, int64_t P);
 
+/* ------------------------------------ virtual correlation energy (VCE) */
+
+/* Walker transform of the virtual-correlation-energy technique (Eq. vce_overlap,
+ * Supplementary "Virtual Correlation Energy Derivation"), one spin sector.  Orbitals
+ * are ordered core (nc), active (na), virtual (NB - nc - na).  For a trial
+ * Xi_c (x) chi (x) 0_v with every core orbital occupied,
+ *     <Xi_c chi 0_v | phi_w> = factor[w] <chi | act_w>,
+ * where act_w = phi_a V' (na x nea) and factor = conj(det R_c) / det V, from the
+ * complete Householder QR phi_c^dagger = V [R_c; 0] of the walker's core block
+ * (any unitary whose first nc columns span the core block's row space gives the same
+ * product; the paper uses an SVD).  The virtual rows are not read.  act feeds
+ * qcs_overlap on the active space; the overlap is linear in the walker's determinant,
+ * so the full-space overlap is factor times the active one (times the other spin
+ * sector's factor for unrestricted walkers).
+ *   d_walkers : W x NB x (nc + nea) complex, row-major (device)
+ *   d_act     : receives element (r, c) of walker w at
+ *               d_act[w * act_walker_stride + r * act_row_stride + c] (complex
+ *               elements), so that two spin sectors can be written as the diagonal
+ *               blocks of one active walker; other elements are not touched
+ *   d_factor  : W complex (device)
+ * Limits: 1 <= na <= QCS_MAX_N, 0 <= nea <= na, nc >= 0, nc + nea <= 64, NB >= nc + na.
+ * Errors: QCS_ERR_ARG (sizes, strides, null pointers), QCS_ERR_CUDA; a non-finite
+ * result raises QCS_ERR_NONFINITE in the status word. */
+qcs_status qcs_vce_transform(qcs_ctx *ctx, int NB, int nc, int na, int nea, int64_t W, const double *d_walkers,
+                             double *d_act, int64_t act_walker_stride, int act_row_stride, double *d_factor,
+                             void *stream);
+
 /* ----------------------------------------------------------- batching */
 
 #define QCS_MAX_SYSTEMS 8

@@ -97,6 +97,8 @@ class Oracle:
         lib.orc_max_threads.restype = i32
         lib.orc_shadow_rdm.argtypes = [i32, i64, P, P, P, P, P, P, P, P]
         lib.orc_shadow_rdm.restype = i32
+        lib.orc_vce_transform.argtypes = [i32, i32, i32, i32, P, P, P]
+        lib.orc_vce_transform.restype = i32
         self.lib = lib
         self.mutation = mutation
 
@@ -226,6 +228,17 @@ class Oracle:
             raise ValueError("orc_shadow_rdm: bad sizes")
         return dict(gam2=gam2, gam4=gam4, rdm1=rdm1, npart=npart.value)
 
+    def vce_transform(self, Phi, nc, na, nea):
+        """(act[na, nea], factor) of the virtual-correlation-energy transform of one
+        spin sector of a full-space walker Phi (NB x (nc + nea))."""
+        Phi = _c(Phi, np.complex128)
+        NB = Phi.shape[0]
+        act = np.zeros((na, nea), np.complex128)
+        f = np.zeros(1, np.complex128)
+        if self.lib.orc_vce_transform(NB, nc, na, nea, _p(Phi), _p(act), _p(f)) != 0:
+            raise ValueError("orc_vce_transform: bad sizes")
+        return act, f[0]
+
     def max_threads(self) -> int:
         return int(self.lib.orc_max_threads())
 
@@ -286,6 +299,10 @@ def force_bias(L, Phi, ov, grad, sqrt_dt=0.0):
 
 def shadow_rdm(Q, b, w=None, R=None, deg4=False):
     return _default().shadow_rdm(Q, b, w, R, deg4)
+
+
+def vce_transform(Phi, nc, na, nea):
+    return _default().vce_transform(Phi, nc, na, nea)
 
 
 def max_threads() -> int:

@@ -710,6 +710,81 @@ int orc_shadow_rdm(int n, int64_t P, const double *Q, const uint8_t *b, const do
     return 0;
 }
 
+/* --------------------------- 16. virtual-correlation-energy walker transform
+ * Supplementary "Virtual Correlation Energy Derivation", Eq. (vce_overlap), one spin
+ * sector.  Orbitals are ordered core (nc), active (na), virtual; the walker Phi is
+ * NB x ne with ne = nc + nea electrons; the trial is the core Slater determinant Xi_c
+ * (unit vectors of the core orbitals) times an active state chi times the virtual
+ * vacuum.  The virtual rows drop out; with the core block phi_c = Phi[0:nc, :] and the
+ * active block phi_a = Phi[nc:nc+na, :],
+ *   <Xi_c chi 0_v | phi> = det [ phi_c ; chi^dag phi_a ].
+ * The paper takes a unitary V from the SVD of phi_c; any unitary V whose first nc
+ * columns span the row space of phi_c serves: from the complete QR phi_c^dag = V [R_c; 0],
+ * phi_c V = [R_c^dag, 0], so the determinant is block triangular after right
+ * multiplication by V and
+ *   <Xi_c chi 0_v | phi> = conj(det R_c) det(chi^dag phi_a V') / det V,
+ * V' the last nea columns of V.  Outputs: the active walker act = phi_a V' (na x nea)
+ * and factor = conj(det R_c) / det V.  det V by LU with partial pivoting. */
+
+static cplx cdet_lu(int m, const cplx *A) {
+    cplx *B = malloc(sizeof(cplx) * (m > 0 ? m * m : 1));
+    memcpy(B, A, sizeof(cplx) * m * m);
+    cplx d = 1.0;
+    for (int k = 0; k < m; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < m; ++i)
+            if (cabs(B[i * m + k]) > cabs(B[piv * m + k])) piv = i;
+        if (B[piv * m + k] == 0.0) {
+            free(B);
+            return 0.0;
+        }
+        if (piv != k) {
+            for (int j = 0; j < m; ++j) {
+                cplx t = B[k * m + j];
+                B[k * m + j] = B[piv * m + j];
+                B[piv * m + j] = t;
+            }
+            d = -d;
+        }
+        d *= B[k * m + k];
+        for (int i = k + 1; i < m; ++i) {
+            cplx f = B[i * m + k] / B[k * m + k];
+            for (int j = k; j < m; ++j) B[i * m + j] -= f * B[k * m + j];
+        }
+    }
+    free(B);
+    return d;
+}
+
+int orc_vce_transform(int NB, int nc, int na, int nea, const cplx *Phi, cplx *act, cplx *factor) {
+    const int ne = nc + nea;
+    if (nc < 0 || na < 1 || nea < 0 || nea > na || NB < nc + na) return -1;
+    cplx *Ct = malloc(sizeof(cplx) * (ne * (nc > 0 ? nc : 1)));
+    cplx *V = malloc(sizeof(cplx) * ne * ne);
+    cplx *Rc = malloc(sizeof(cplx) * (nc > 0 ? nc * nc : 1));
+    for (int j = 0; j < ne; ++j) /* phi_c^dag: ne x nc */
+        for (int i = 0; i < nc; ++i) Ct[j * nc + i] = conj(Phi[i * ne + j]);
+    cplx detR = 1.0;
+    if (nc > 0) {
+        orc_walker_qr(ne, nc, Ct, V, Rc);
+        for (int i = 0; i < nc; ++i) detR *= Rc[i * nc + i];
+    } else {
+        for (int i = 0; i < ne; ++i)
+            for (int j = 0; j < ne; ++j) V[i * ne + j] = (i == j) ? 1.0 : 0.0;
+    }
+    for (int r = 0; r < na; ++r)
+        for (int c = 0; c < nea; ++c) {
+            cplx s = 0.0;
+            for (int k = 0; k < ne; ++k) s += Phi[(nc + r) * ne + k] * V[k * ne + nc + c];
+            act[r * nea + c] = s;
+        }
+    *factor = conj(detR) / cdet_lu(ne, V);
+    free(Ct);
+    free(V);
+    free(Rc);
+    return 0;
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

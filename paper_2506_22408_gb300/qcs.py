@@ -36,7 +36,7 @@ EXPORTED = [
     "qcs_profile_enable", "qcs_profile_read", "qcs_grad_flops_per_pair", "qcs_overlap_noalloc",
     "qcs_autotune", "qcs_set_config", "qcs_overlap_batched", "qcs_node_plan_get",
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
-    "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops",
+    "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_node_plan_get.argtypes = [i32, i32, i32, u32, ctypes.POINTER(i32), P, P]
         lib.qcs_snapshots_signed_perm_count.argtypes = [P, ctypes.POINTER(i64), P]
         lib.qcs_shadow_rdm.argtypes = [P, P, P, P, P, P, P, P]
+        lib.qcs_vce_transform.argtypes = [P, i32, i32, i32, i32, i64, P, P, i64, i32, P, P]
         lib.qcs_shadow_rdm_flops.argtypes = [i32, i64]
         lib.qcs_shadow_rdm_flops.restype = f64
         for fn in ("qcs_overlap_flops_per_pair_signed_perm", "qcs_grad_flops_per_pair_signed_perm"):
@@ -374,6 +375,28 @@ def shadow_rdm(ctx: Context, snaps: Snapshots, R: torch.Tensor | None = None, de
     ctx.check(ctx.lib.qcs_shadow_rdm(ctx.h, snaps.h, _ptr(R) if R is not None else None, _ptr(gam2),
                                      _ptr(gam4) if gam4 is not None else None, _ptr(rdm1), _ptr(npart), _stream()))
     return dict(gam2=gam2, gam4=gam4, rdm1=rdm1, npart=npart)
+
+
+def vce_transform(ctx: Context, walkers: torch.Tensor, nc: int, na: int, nea: int, act: torch.Tensor | None = None,
+                  row0: int = 0, col0: int = 0):
+    """Virtual-correlation-energy transform of one spin sector (qcs_vce_transform).
+    walkers: (W, NB, nc + nea) complex128.  The active walkers are written into act
+    (W, R, C) complex128 at rows row0.. and columns col0.. (a new (W, na, nea) tensor
+    when act is None); returns (act, factor[W])."""
+    _need_cuda(walkers, "walkers", torch.complex128)
+    W, NB, ne = walkers.shape
+    if ne != nc + nea:
+        raise ValueError("walkers must have nc + nea columns")
+    if act is None:
+        act = torch.zeros((W, na, nea), dtype=torch.complex128, device=walkers.device)
+    _need_cuda(act, "act", torch.complex128)
+    if act.shape[0] != W or row0 + na > act.shape[1] or col0 + nea > act.shape[2]:
+        raise ValueError("act too small for the na x nea block at (row0, col0)")
+    factor = torch.empty(W, dtype=torch.complex128, device=walkers.device)
+    base = ctypes.c_void_p(act.data_ptr() + 16 * (row0 * act.shape[2] + col0)) if nea > 0 else None
+    ctx.check(ctx.lib.qcs_vce_transform(ctx.h, NB, nc, na, nea, W, _ptr(walkers), base,
+                                        act.shape[1] * act.shape[2], act.shape[2], _ptr(factor), _stream()))
+    return act, factor
 
 
 def shadow_rdm_flops(n: int, P: int) -> float:

@@ -474,6 +474,80 @@ def test_shadow_rdm_single_snapshot_closed_form():
         assert abs(est["gam4"][t] - K4 * (-pf)) < 1e-11
 
 
+# ------------------- virtual-correlation-energy transform (Supplementary "VCE Derivation")
+
+
+def _embed_trial(nc, chi, NB):
+    """Full-space orbital matrix of Xi_c (x) chi (x) 0_v: core unit vectors, then chi."""
+    na, nea = chi.shape
+    Psi = np.zeros((NB, nc + nea), complex)
+    Psi[:nc, :nc] = np.eye(nc)
+    Psi[nc:nc + na, nc:] = chi
+    return Psi
+
+
+@pytest.mark.parametrize("NB,nc,na,nea", [(14, 3, 6, 2), (20, 0, 8, 4), (12, 5, 4, 0), (30, 10, 8, 4),
+                                          (9, 4, 5, 5), (40, 24, 16, 8)])
+def test_vce_transform_reproduces_full_space_determinant(NB, nc, na, nea):
+    """For Slater trials the full-space overlap is det(Psi^dag Phi); the transform must
+    give factor * det(chi^dag act) for every active chi, and the virtual rows must drop out."""
+    rng = np.random.default_rng(NB * 100 + nc)
+    ne = nc + nea
+    Phi = rng.standard_normal((NB, ne)) + 1j * rng.standard_normal((NB, ne))
+    act, f = orc.vce_transform(Phi, nc, na, nea)
+    for _ in range(3):
+        chi = rng.standard_normal((na, nea)) + 1j * rng.standard_normal((na, nea))
+        full = np.linalg.det(_embed_trial(nc, chi, NB).conj().T @ Phi)
+        got = f * np.linalg.det(chi.conj().T @ act)
+        assert abs(got - full) <= 1e-12 * max(1.0, abs(full))
+    Phi2 = Phi.copy()
+    Phi2[nc + na:] = rng.standard_normal(Phi2[nc + na:].shape)  # virtual rows
+    act2, f2 = orc.vce_transform(Phi2, nc, na, nea)
+    assert np.allclose(act2, act, rtol=0, atol=1e-14 * np.abs(act).max(initial=1.0)) and abs(f2 - f) <= 1e-14 * abs(f)
+
+
+def test_vce_transform_multi_determinant_two_spins():
+    """Unrestricted walker, multi-determinant active trial sum_i c_i chi_i^a chi_i^b: the
+    full-space overlap equals f_a f_b sum_i c_i det(chi_i^a^dag act_a) det(chi_i^b^dag act_b)."""
+    rng = np.random.default_rng(17)
+    NB, nc, na, nea = 18, 4, 6, 3
+    Pa = rng.standard_normal((NB, nc + nea)) + 1j * rng.standard_normal((NB, nc + nea))
+    Pb = rng.standard_normal((NB, nc + nea)) + 1j * rng.standard_normal((NB, nc + nea))
+    aa, fa = orc.vce_transform(Pa, nc, na, nea)
+    ab, fb = orc.vce_transform(Pb, nc, na, nea)
+    full = via = 0.0
+    for _ in range(4):
+        c = rng.standard_normal() + 1j * rng.standard_normal()
+        xa = rng.standard_normal((na, nea)) + 1j * rng.standard_normal((na, nea))
+        xb = rng.standard_normal((na, nea)) + 1j * rng.standard_normal((na, nea))
+        full += c * np.linalg.det(_embed_trial(nc, xa, NB).conj().T @ Pa) * np.linalg.det(
+            _embed_trial(nc, xb, NB).conj().T @ Pb)
+        via += c * np.linalg.det(xa.conj().T @ aa) * np.linalg.det(xb.conj().T @ ab)
+    assert abs(fa * fb * via - full) <= 1e-12 * abs(full)
+
+
+def test_vce_transform_fock_space_general_active_state():
+    """Fock space of NB = 7 modes: trial a^dag_0 .. a^dag_{nc-1} |Psi_act> with a random
+    (non-Slater) nea-particle active state; <trial|phi> = factor <Psi_act|act>."""
+    rng = np.random.default_rng(23)
+    NB, nc, na, nea = 7, 2, 4, 2
+    F, Fa = Fock(NB), Fock(na)
+    Phi = rng.standard_normal((NB, nc + nea)) + 1j * rng.standard_normal((NB, nc + nea))
+    act, f = orc.vce_transform(Phi, nc, na, nea)
+    psi_a = _random_eta_state(rng, Fa, nea)
+    emb = np.zeros(F.dim, complex)  # active modes nc..nc+na-1 of the full space, rest empty
+    for x in range(Fa.dim):
+        emb[x << nc] = psi_a[x]
+    # Jordan-Wigner signs: the embedding shifts every active mode past nc empty modes
+    # (no sign); the core creators act after it
+    trial = emb
+    for c in reversed(range(nc)):
+        trial = F.a[c].conj().T @ trial
+    full = np.vdot(trial, F.slater(Phi))
+    act_ov = np.vdot(psi_a, Fa.slater(act))
+    assert abs(f * act_ov - full) <= 1e-12 * max(1.0, abs(full))
+
+
 # ---------------------------------------------- the pins catch mistakes
 
 
