@@ -538,6 +538,63 @@ def run_rdm(args, ctx, dev, flush, barrier, ws, steps=3):
                          "traffic": traffic_for("rdm_syrk_kernel", f"shadow RDM n={n} {P} snapshots")}}
 
 
+def run_vce(args, ctx, dev, flush, barrier, ws, steps=3):
+    """Virtual-correlation-energy path: full-space unrestricted walkers (200 orbitals
+    and 20 + 4 electrons per spin, 20 core orbitals) mapped by qcs_vce_transform onto
+    the paper-shaped active space (8 orbitals and 4 electrons per spin: n=16, ne=8),
+    then the shadow overlap with 20000 snapshots; one step = both transforms and the
+    overlap.  The transform alone is also timed."""
+    import torch
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    NB, nc, na, nea, W, P = 200, 20, 8, 4, 1024, 20000
+    rng = np.random.default_rng(0)
+    Pa = torch.from_numpy(rng.standard_normal((W, NB, nc + nea)) + 1j * rng.standard_normal((W, NB, nc + nea))).to(dev)
+    Pb = torch.from_numpy(rng.standard_normal((W, NB, nc + nea)) + 1j * rng.standard_normal((W, NB, nc + nea))).to(dev)
+    Qd = torch.from_numpy(synth.haar_orthogonal(rng, 4 * na, P)).to(dev)
+    bd = torch.from_numpy(synth.uniform_bits(rng, 2 * na, P)).to(dev)
+    act = torch.zeros((W, 2 * na, 2 * nea), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def transform():
+        _, fa = qcs.vce_transform(ctx, Pa, nc, na, nea, act=act, row0=0, col0=0)
+        _, fb = qcs.vce_transform(ctx, Pb, nc, na, nea, act=act, row0=na, col0=nea)
+        return fa, fb
+
+    def step():
+        fa, fb = transform()
+        snaps = qcs.Snapshots(ctx, Qd, bd)
+        ov, _ = qcs.overlap(ctx, snaps, act)
+        return ov * fa * fb
+
+    for _ in range(2):
+        step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    assert ctx.sync_status() == 0
+    t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        transform()
+    e1.record(stream)
+    barrier()
+    tt = e0.elapsed_time(e1) / 1e3 / reps
+    return {"metric": "full-space walker x snapshot overlap pairs/s through the VCE transform", "unit": "pairs/s",
+            "value": ws * W * P * steps / t, "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "transform_walkers_per_s": ws * 2 * W / tt,
+            "config": {"workload": f"VCE NB={NB} per spin, {nc} core, active {na} orbitals / {nea} electrons "
+                                   f"per spin (n=16, ne=8), {W} walkers x {P} snapshots"}}
+
+
 def cpu_baseline(wl, data, target_s=10.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle.oracle as orc
@@ -608,6 +665,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
     ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
     ap.add_argument("--no-rdm", action="store_true", help="skip the shadow RDM workload")
+    ap.add_argument("--no-vce", action="store_true", help="skip the virtual-correlation-energy workload")
     ap.add_argument("--rdm-snapshots", type=int, default=60000, help="snapshots of the shadow RDM workload")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the parity-consistent and signed-permutation snapshot ensembles")
@@ -707,6 +765,11 @@ def main():
     if not args.no_rdm:
         rdm = run_rdm(args, ctx, dev, flush, barrier, ws)
 
+    # ---------------- virtual-correlation-energy path
+    vce = None
+    if not args.no_vce:
+        vce = run_vce(args, ctx, dev, flush, barrier, ws)
+
     # ---------------- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -751,6 +814,7 @@ def main():
             "roots_of_unity_plan": dft,
             "ensembles": variants,
             "rdm": rdm,
+            "vce": vce,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

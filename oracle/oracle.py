@@ -99,6 +99,8 @@ class Oracle:
         lib.orc_shadow_rdm.restype = i32
         lib.orc_vce_transform.argtypes = [i32, i32, i32, i32, P, P, P]
         lib.orc_vce_transform.restype = i32
+        lib.orc_local_energy.argtypes = [i32, i32, i64, i64, P, P, P, P, P, i32, P, i32, P, P, P]
+        lib.orc_local_energy.restype = i32
         self.lib = lib
         self.mutation = mutation
 
@@ -239,6 +241,24 @@ class Oracle:
             raise ValueError("orc_vce_transform: bad sizes")
         return act, f[0]
 
+    def local_energy(self, Phi, Q, b, L, h=None, threads=0, w=None):
+        """(overlap[W], e1[W], e2[W]): e1 = <Psi_T|hhat|phi>/O (zeros without h),
+        e2 = sum_gamma <Psi_T|Lhat_gamma^2|phi>/O, by walker-side column substitution."""
+        Phi = _c(Phi, np.complex128)
+        Q = _c(Q, np.float64)
+        b = _c(b, np.uint8)
+        L = _c(L, np.complex128)
+        hh = _c(h, np.complex128) if h is not None else None
+        w = _c(w, np.float64) if w is not None else None
+        W, n, ne = Phi.shape
+        P = Q.shape[0]
+        ov = np.zeros(W, np.complex128)
+        e1 = np.zeros(W, np.complex128)
+        e2 = np.zeros(W, np.complex128)
+        self.lib.orc_local_energy(n, ne, W, P, _p(Phi), _p(Q), _p(b), _p(w), _p(hh), L.shape[0], _p(L), threads,
+                                  _p(ov), _p(e1), _p(e2))
+        return ov, e1, e2
+
     def max_threads(self) -> int:
         return int(self.lib.orc_max_threads())
 
@@ -303,6 +323,10 @@ def shadow_rdm(Q, b, w=None, R=None, deg4=False):
 
 def vce_transform(Phi, nc, na, nea):
     return _default().vce_transform(Phi, nc, na, nea)
+
+
+def local_energy(Phi, Q, b, L, h=None, threads=0, w=None):
+    return _default().local_energy(Phi, Q, b, L, h, threads, w)
 
 
 def max_threads() -> int:

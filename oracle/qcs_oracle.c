@@ -785,6 +785,118 @@ int orc_vce_transform(int NB, int nc, int na, int nea, const cplx *Phi, cplx *ac
     return 0;
 }
 
+/* --------------------------- 17. local-energy terms by derivatives of the overlap
+ * Eqs. (force_bias_diff), (energy_tb_diff): for a one-body operator
+ * Lhat = sum_pq L_pq a_p^dag a_q, e^{lambda Lhat} maps the walker's orbitals Phi to
+ * e^{lambda L} Phi (Thouless), so with O the shadow overlap,
+ *   <Psi_T| Lhat |phi>      = d/dlambda   O(e^{lambda L} Phi) at 0 = D O[L Phi],
+ *   <Psi_T| Lhat Lhat |phi> = d^2/dlambda^2 O(e^{lambda L} Phi) at 0
+ *                           = D^2 O[L Phi, L Phi] + D O[L^2 Phi].
+ * Each pair term o_p is linear in every column of Phi (step 13), so these derivatives
+ * are exact column substitutions:
+ *   D o_p[X]     = sum_j o_p(Phi with column j replaced by X_j),
+ *   D^2 o_p[X,X] = 2 sum_{j<j'} o_p(Phi with columns j, j' replaced by X_j, X_j').
+ * Outputs per walker (each output may be NULL): ov = O, e1 = <Psi_T|hhat|phi>/O (h may be
+ * NULL) and e2 = sum_gamma <Psi_T|Lhat_gamma Lhat_gamma|phi>/O, ratios of shadow means
+ * (weighted means sum_p w_p o_p / sum_p w_p when wts is given: exact group averages). */
+int orc_local_energy(int n, int ne, int64_t W, int64_t P, const cplx *Phi, const double *Q, const uint8_t *b,
+                     const double *wts, const cplx *h, int nchol, const cplx *L, int threads, cplx *ov, cplx *e1,
+                     cplx *e2) {
+    const int N2 = 2 * n;
+    int used = 1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    used = omp_get_max_threads();
+#endif
+    double *G = malloc(sizeof(double) * (size_t)(P > 0 ? P : 1) * N2 * N2);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t p = 0; p < P; ++p) orc_snapshot_G(n, Q + p * N2 * N2, b + p * n, G + p * N2 * N2);
+    /* variants of one walker: 0 base; per operator (h first when given, then each L_gamma):
+       ne single substitutions by columns of X2 (h: X1 = h Phi), then ne(ne-1)/2 pairs by X1 */
+    const int nsingle = ne, npair = ne * (ne - 1) / 2;
+    const int nop = (h ? 1 : 0) + nchol;
+    const int64_t per_op = nsingle + npair;
+    const int64_t nvar = 1 + (int64_t)nop * per_op;
+    cplx *val = malloc(sizeof(cplx) * (size_t)(W * nvar > 0 ? W * nvar : 1));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < W * nvar; ++t) {
+        const int64_t w = t / nvar, v = t % nvar;
+        const cplx *Pw = Phi + w * n * ne;
+        cplx *Pm = malloc(sizeof(cplx) * n * ne);
+        memcpy(Pm, Pw, sizeof(cplx) * n * ne);
+        if (v > 0) {
+            const int op = (int)((v - 1) / per_op), r = (int)((v - 1) % per_op);
+            const int is_h = h && op == 0;
+            const cplx *Lo = is_h ? h : L + (size_t)(op - (h ? 1 : 0)) * n * n;
+            cplx *X1 = malloc(sizeof(cplx) * n * ne), *X2 = malloc(sizeof(cplx) * n * ne);
+            for (int i = 0; i < n; ++i) /* X1 = Lo Phi */
+                for (int j = 0; j < ne; ++j) {
+                    cplx s = 0.0;
+                    for (int k = 0; k < n; ++k) s += Lo[i * n + k] * Pw[k * ne + j];
+                    X1[i * ne + j] = s;
+                }
+            for (int i = 0; i < n; ++i) /* X2 = Lo X1 = Lo^2 Phi */
+                for (int j = 0; j < ne; ++j) {
+                    cplx s = 0.0;
+                    for (int k = 0; k < n; ++k) s += Lo[i * n + k] * X1[k * ne + j];
+                    X2[i * ne + j] = s;
+                }
+            if (r < nsingle) { /* first derivative (h) or the D O[L^2 Phi] term (L_gamma) */
+                const cplx *Xs = is_h ? X1 : X2;
+                for (int i = 0; i < n; ++i) Pm[i * ne + r] = Xs[i * ne + r];
+            } else { /* pair (j, j') of the second-derivative term; h has no such term */
+                int q = r - nsingle, j = 0;
+                while (q >= ne - 1 - j) {
+                    q -= ne - 1 - j;
+                    ++j;
+                }
+                const int j2 = j + 1 + q;
+                for (int i = 0; i < n; ++i) {
+                    Pm[i * ne + j] = X1[i * ne + j];
+                    Pm[i * ne + j2] = X1[i * ne + j2];
+                }
+            }
+            free(X1);
+            free(X2);
+        }
+        const int skip = v > 0 && h && (v - 1) / per_op == 0 && (v - 1) % per_op >= nsingle;
+        cplx s = 0.0;
+        if (!skip) {
+            walker_t wk;
+            walker_setup(n, ne, Pm, &wk);
+            double ws = 0.0;
+            for (int64_t p = 0; p < P; ++p) {
+                const double wp = wts ? wts[p] : 1.0;
+                s += wp * pair_estimate(&wk, G + p * N2 * N2, ORC_INTERP_ROOTS, 0, NULL, NULL);
+                ws += wp;
+            }
+            walker_free(&wk);
+            s = (ws != 0.0) ? s / ws : 0.0;
+        }
+        val[t] = s;
+        free(Pm);
+    }
+    for (int64_t w = 0; w < W; ++w) {
+        const cplx *vw = val + w * nvar;
+        const cplx O = vw[0];
+        if (ov) ov[w] = O;
+        cplx n1 = 0.0, n2 = 0.0;
+        for (int op = 0; op < nop; ++op) {
+            const cplx *vo = vw + 1 + (int64_t)op * per_op;
+            cplx d1 = 0.0, d2 = 0.0;
+            for (int r = 0; r < nsingle; ++r) d1 += vo[r];
+            for (int r = 0; r < npair; ++r) d2 += vo[nsingle + r];
+            if (h && op == 0) n1 = d1;
+            else n2 += 2.0 * d2 + d1;
+        }
+        if (e1) e1[w] = (h && O != 0.0) ? n1 / O : 0.0;
+        if (e2) e2[w] = (O != 0.0) ? n2 / O : 0.0;
+    }
+    free(G);
+    free(val);
+    return used;
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -548,6 +548,52 @@ def test_vce_transform_fock_space_general_active_state():
     assert abs(f * act_ov - full) <= 1e-12 * max(1.0, abs(full))
 
 
+# ----------------------- local-energy terms (Eqs. force_bias_diff, energy_tb_diff)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_local_energy_terms_exact_group_average(n):
+    """Averaged over the signed-permutation group with Born weights for
+    (|0> + |Psi_T>)/sqrt2, the shadow estimates of <Psi_T|hhat|phi>/<Psi_T|phi> and
+    sum_gamma <Psi_T|Lhat_gamma Lhat_gamma|phi>/<Psi_T|phi> equal the Fock-space values
+    for a non-Slater Psi_T, a non-orthonormal walker and complex one-body operators."""
+    rng = np.random.default_rng(800 + n)
+    ne = 2
+    F = Fock(n)
+    PsiT = _random_eta_state(rng, F, ne)
+    Psi = (F.vac + PsiT) / np.sqrt(2)
+    Phi = synth.walkers(rng, n, ne, 1)[0] @ (rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne)))
+    h = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    L = rng.standard_normal((2, n, n)) + 1j * rng.standard_normal((2, n, n))
+    group = np.array(list(signed_permutation_group(2 * n)))
+    Qs, bs, ws = _born_table(F, group, Psi)
+    ov, e1, e2 = orc.local_energy(Phi[None], Qs, bs, L, h=h, w=ws)
+    phi = F.slater(Phi)
+    op = lambda M: sum(M[p, q] * F.a[p].conj().T @ F.a[q] for p in range(n) for q in range(n))  # noqa: E731
+    O = np.vdot(PsiT, phi)
+    ref1 = np.vdot(PsiT, op(h) @ phi) / O
+    ref2 = sum(np.vdot(PsiT, op(Lg) @ (op(Lg) @ phi)) for Lg in L) / O
+    assert abs(ov[0] - O) <= 1e-12 * max(1.0, abs(O))
+    assert abs(e1[0] - ref1) <= 1e-11 * max(1.0, abs(ref1))
+    assert abs(e2[0] - ref2) <= 1e-11 * max(1.0, abs(ref2))
+
+
+def test_local_energy_one_body_term_matches_gradient():
+    """D O[h Phi] = sum_kj g_kj (h Phi)_kj with the oracle's gradient: two routes through
+    the same column substitution agree, and e1 equals tr(h G) with G = Phi g^T / O."""
+    rng = np.random.default_rng(81)
+    n, ne, P = 6, 4, 30
+    Q = synth.haar_orthogonal(rng, 2 * n, P)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 2)
+    h = synth.cholesky_vectors(rng, n, 1)[0].astype(complex)
+    ov, e1, _ = orc.local_energy(Phi, Q, b, h[None] * 0.0, h=h)
+    oo, g, _ = orc.overlap_grad(Phi, Q, b)
+    for w in range(2):
+        Gf = Phi[w] @ g[w].T / oo[w]
+        assert abs(e1[w] - np.trace(h @ Gf)) <= 1e-11 * max(1.0, abs(e1[w]))
+
+
 # ---------------------------------------------- the pins catch mistakes
 
 
