@@ -124,8 +124,9 @@ CSRC = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc")
 KERNEL_SOURCES = {
     "pair_overlap_kernel": ["qcs_overlap.cu", "qcs_pair.cuh", "qcs_common.cuh"],
     "split_pair_kernel": ["qcs_split.cu", "qcs_pair.cuh", "qcs_tc.cuh", "qcs_common.cuh"],
-    "grad_pair_kernel": ["qcs_grad.cu", "qcs_pair.cuh", "qcs_common.cuh"],
+    "grad_pair_kernel": ["qcs_grad.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
     "rdm_syrk_kernel": ["qcs_rdm.cu"],
+    "energy_pair_kernel": ["qcs_energy.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
 }
 
 
@@ -595,6 +596,57 @@ def run_vce(args, ctx, dev, flush, barrier, ws, steps=3):
                                    f"per spin (n=16, ne=8), {W} walkers x {P} snapshots"}}
 
 
+def run_energy(args, ctx, dev, flush, barrier, ws, steps=2):
+    """Local-energy terms (Eqs. energy_tb_diff, Pfaffian_2nd_der): n=16, ne=8, 64 walkers
+    x 1000 snapshots, 64 Cholesky vectors and a one-body operator; one step = snapshot
+    build + qcs_local_energy."""
+    import torch
+
+    from paper_2506_22408_gb300 import qcs, synth
+
+    n, ne, W, P, nchol = 16, 8, args.energy_walkers, 1000, 64
+    rng = np.random.default_rng(0)
+    Qd = torch.from_numpy(synth.haar_orthogonal(rng, 2 * n, P)).to(dev)
+    bd = torch.from_numpy(synth.uniform_bits(rng, n, P)).to(dev)
+    Pd = torch.from_numpy(synth.walkers(rng, n, ne, W)).to(dev)
+    Ld = torch.from_numpy(synth.cholesky_vectors(rng, n, nchol).astype(complex)).to(dev)
+    hd = torch.from_numpy(synth.cholesky_vectors(rng, n, 1)[0].astype(complex)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        snaps = qcs.Snapshots(ctx, Qd, bd)
+        qcs.local_energy(ctx, snaps, Pd, Ld, hd)
+        return snaps
+
+    snaps = step()
+    barrier()
+    npar = int((snaps.parity() == 1).sum().item())
+    ctx.profile(True)
+    ctx.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    ctx.profile(False)
+    kms, kl = ctx.profile_read()
+    assert ctx.sync_status() == 0
+    t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+    fpp = qcs.local_energy_flops_per_pair(n, ne, nchol, True)
+    avg = kms / max(kl, 1)
+    ach = fpp * npar * W / (avg * 1e-3) / 1e12
+    return {"metric": "walker x snapshot pairs/s, local-energy terms (overlap, one-body and two-body)",
+            "value": ws * W * P * steps / t, "unit": "pairs/s", "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "config": {"workload": f"local energy n={n} ne={ne} {W}x{P} nchol={nchol} (Haar Q, uniform b, seed 0)",
+                       "parity_plus_snapshots": npar},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "energy_pair_kernel", "kernel_ms": avg,
+                         "flops_per_launch": fpp * npar * W,
+                         "traffic": traffic_for("energy_pair_kernel", f"local energy n={n} ne={ne} {W}x{P} nchol={nchol}")}}
+
+
 def cpu_baseline(wl, data, target_s=10.0):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle.oracle as orc
@@ -666,6 +718,8 @@ def main():
     ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
     ap.add_argument("--no-rdm", action="store_true", help="skip the shadow RDM workload")
     ap.add_argument("--no-vce", action="store_true", help="skip the virtual-correlation-energy workload")
+    ap.add_argument("--no-energy", action="store_true", help="skip the local-energy workload")
+    ap.add_argument("--energy-walkers", type=int, default=64, help="walkers of the local-energy workload")
     ap.add_argument("--rdm-snapshots", type=int, default=60000, help="snapshots of the shadow RDM workload")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the parity-consistent and signed-permutation snapshot ensembles")
@@ -770,6 +824,11 @@ def main():
     if not args.no_vce:
         vce = run_vce(args, ctx, dev, flush, barrier, ws)
 
+    # ---------------- local-energy terms
+    energy = None
+    if not args.no_energy:
+        energy = run_energy(args, ctx, dev, flush, barrier, ws)
+
     # ---------------- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -815,6 +874,7 @@ def main():
             "ensembles": variants,
             "rdm": rdm,
             "vce": vce,
+            "local_energy": energy,
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)

@@ -187,6 +187,32 @@ int qcs_snapshots_modes(const qcs_snapshots *s);
 qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                        double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream);
 
+/* ---------------------------------------------------- local energy terms */
+
+/* Local-energy terms of the shadow overlap by Pfaffian derivatives (Eqs.
+ * force_bias_diff, energy_tb_diff, Pfaffian_der, Pfaffian_2nd_der): for W walkers,
+ *   e1[w] = <Psi_T| hhat |phi_w> / <Psi_T|phi_w>,                  hhat = sum_pq h_pq a_p^dag a_q
+ *   e2[w] = sum_gamma <Psi_T| Lhat_gamma Lhat_gamma |phi_w> / <Psi_T|phi_w>,
+ * with numerators and the overlap as shadow means over the snapshot set.  The
+ * one-body moves e^{lambda Lhat} of the walker are carried to the snapshot side
+ * (the inverse channel commutes with degree-preserving similarities), so every
+ * derivative is a derivative of the pair Pfaffians with respect to the selected
+ * rows; A^-1 of each node matrix is rebuilt per pair (never stored), and each
+ * Cholesky vector costs O(m (2n)^2 + nodes m^3) per pair.  The Hamiltonian's own
+ * factors (e.g. 1/2 on the two-body sum) are the caller's.
+ *   d_walkers : W x n x ne complex (device)
+ *   d_L       : nchol x n x n complex (device), Lhat_gamma = sum_pq L[gamma][p][q] a_p^dag a_q
+ *   d_h       : n x n complex (device) or NULL (then e1 is not computed)
+ *   d_overlap, d_e1, d_e2 : W complex each, or NULL
+ * Same node options as qcs_overlap; FP64 only.
+ * Errors: QCS_ERR_ARG, QCS_ERR_UNSUPPORTED (precision, shared memory), QCS_ERR_CUDA. */
+qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
+                            int nchol, const double *d_L, const double *d_h, double *d_overlap, double *d_e1,
+                            double *d_e2, const qcs_opts *opts, void *stream);
+
+/* Algorithmic FP64 flops of qcs_local_energy per parity +1 pair. */
+double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int has_h, int nodes, unsigned flags);
+
 /* -------------------------------------------- reduced density matrices */
 
 /* Shadow estimates of Majorana correlators, the one-particle reduced density

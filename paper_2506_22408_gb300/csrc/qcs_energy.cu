@@ -1,0 +1,526 @@
+// qcs_energy.cu -- local-energy terms of the shadow overlap by Pfaffian derivatives
+// (Eqs. force_bias_diff, energy_tb_diff, Pfaffian_der, Pfaffian_2nd_der).
+//
+// For a one-body operator Lhat = sum_pq L_pq a_p^dag a_q the walker moves as
+// Phi -> e^{lambda L} Phi.  Because <0| Lhat = 0, e^{lambda Lhat}|phi><0| is the
+// similarity e^{lambda Lhat} (|phi><0|) e^{-lambda Lhat}; the inverse shadow channel
+// only rescales Majorana degrees, which such similarities preserve, so the pair
+// estimate of the moved walker equals that of the fixed walker against the snapshot
+// e^{-lambda Lhat} rho_p e^{lambda Lhat}, whose covariance is R G_p R^T with
+// R = e^{lambda ell}, [Lhat, g_mu] = sum_a ell_{mu a} g_a.  In the pair matrices
+// B = K G K^T (K: the walker's selected rows, m x 2n) this is K -> K e^{lambda ell}:
+//     A'  = X' J X^T + X J X'^T,                 X'  = (K ell) Q'^T,
+//     A'' = X'' J X^T + 2 X' J X'^T + X J X''^T,  X'' = (K ell^2) Q'^T,
+// with X = K Q'^T the rows the overlap kernels already form from T.  Eq.
+// (Pfaffian_2nd_der) then gives per node matrix A_k = B + w_k D
+//     d^2 pf = (pf/2) [ tr(A^-1 A'') - tr(A^-1 A' A^-1 A') + tr(A^-1 A')^2 / 2 ],
+// and Eq. (Pfaffian_der) d pf = (pf/2) tr(A^-1 A').  The walker prefactor cancels in
+//     e1 = sum_p D o_p[hhat] / sum_p o_p,   e2 = sum_gamma sum_p D^2 o_p[Lhat_gamma] / sum_p o_p.
+// A^-1 is rebuilt per pair and node by the in-place backward recursion (qcs_group.cuh);
+// per Cholesky vector the pair costs O(m (2n)^2 + nodes m^3).
+#include "qcs_group.cuh"
+#include "qcs_internal.h"
+
+namespace {
+
+struct EnergyArgs {
+    int n, ne, m, d, nev, NB, nop, nchol, has_h, all, chunk, nchunks;
+    int64_t W, P;
+    int group_bytes, tab_bytes;
+    int off_Q, off_T, off_B, off_NZ, off_g1, off_g2, off_y1, off_y2, off_pf, off_cf, off_invh, off_int, off_tile,
+        off_acth, off_kh, off_ph, off_X1, off_Ap, off_Sacc, off_red, off_acc;
+    const cd *Ut;
+    const cd *Qt;
+    const int *idx;
+    const int *d_count;
+    const cd *Kop;  // W x nop x m x 2n: K ell_o (o < nchol: Cholesky vectors; o = nchol: h)
+    const cd *K2;   // W x m x 2n: sum_gamma K ell_gamma^2
+    cd *partial;    // W x nchunks x 3: (sum o_p, sum first-derivative term, sum second-derivative term)
+    unsigned long long *counter;
+    unsigned *status;
+    cd wnode[QCS_MAX_NODES];
+    cd gamma[QCS_MAX_NODES];
+};
+
+// Row a of X (m x 2n) from T: occupied rows are rows of T, each empty mode gives
+// (Re T_j, -Im T_j).
+__device__ __forceinline__ cd x_at(const cd *Ts, int lt, int ne, int a, int c) {
+    if (a < ne) return Ts[a * lt + c];
+    const int r = a - ne;
+    const cd t = Ts[(ne + (r >> 1)) * lt + c];
+    return (r & 1) ? cmk(-t.y, 0.0) : cmk(t.x, 0.0);
+}
+
+// (Y J Z^T)_{ab} = sum_j Y[a][2j] Z[b][2j+1] - Y[a][2j+1] Z[b][2j]
+template <class FY, class FZ>
+__device__ __forceinline__ cd yjz(int n, FY y, FZ z) {
+    cd s = cmk(0.0, 0.0);
+    for (int j = 0; j < n; ++j) {
+        cfma(s, y(2 * j), z(2 * j + 1));
+        cfms(s, y(2 * j + 1), z(2 * j));
+    }
+    return s;
+}
+
+// Sum of one complex value per thread over the 64 threads of a group, in a fixed
+// order (warp shuffles, then the two warp sums in order).  Every thread gets the sum.
+__device__ __forceinline__ cd group_sum(cd v, cd *red, int t, int bar) {
+    v = warp_csum(v);
+    if ((t & 31) == 0) red[t >> 5] = v;
+    group_sync(bar);
+    const cd s = cadd(red[0], red[1]);
+    group_sync(bar);
+    return s;
+}
+
+__global__ void __launch_bounds__(128, 1) energy_pair_kernel(const __grid_constant__ EnergyArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int gid = threadIdx.x / kGroup;
+    const int t = threadIdx.x - gid * kGroup;
+    const int bar = 1 + gid;
+    const int n = A.n, n2 = 2 * n, ne = A.ne, m = A.m, T = tri_count(m);
+    const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n), lx = n2 + 1;
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
+    build_pair_table(tab, T);
+    __syncthreads();
+    unsigned char *wb = smem_raw + A.tab_bytes + (size_t)gid * A.group_bytes;
+    cd *Uts = reinterpret_cast<cd *>(wb);
+    cd *Qs = reinterpret_cast<cd *>(wb + A.off_Q);
+    cd *Ts = reinterpret_cast<cd *>(wb + A.off_T);
+    cd *Bs = reinterpret_cast<cd *>(wb + A.off_B);
+    cd *Ns = reinterpret_cast<cd *>(wb + A.off_NZ);  // node factors, then their inverses (packed)
+    cd *g1v = reinterpret_cast<cd *>(wb + A.off_g1);
+    cd *g2v = reinterpret_cast<cd *>(wb + A.off_g2);
+    cd *y1v = reinterpret_cast<cd *>(wb + A.off_y1);
+    cd *y2v = reinterpret_cast<cd *>(wb + A.off_y2);
+    cd *pf = reinterpret_cast<cd *>(wb + A.off_pf);
+    cd *cf = reinterpret_cast<cd *>(wb + A.off_cf);
+    cd *invh = reinterpret_cast<cd *>(wb + A.off_invh);
+    int *pos = reinterpret_cast<int *>(wb + A.off_int);
+    long long *slot = reinterpret_cast<long long *>(wb + A.off_tile);
+    uint8_t *acth = wb + A.off_acth;
+    uint8_t *kh = wb + A.off_kh;
+    uint8_t *ph = wb + A.off_ph;
+    cd *X1 = reinterpret_cast<cd *>(wb + A.off_X1);     // X' (or X'') rows, m x (2n+1)
+    cd *Ap = reinterpret_cast<cd *>(wb + A.off_Ap);     // A' (packed upper skew)
+    cd *Sacc = reinterpret_cast<cd *>(wb + A.off_Sacc); // sum_gamma X'_g J X'_g^T (packed)
+    cd *red = reinterpret_cast<cd *>(wb + A.off_red);   // 2 entries
+    cd *acc = reinterpret_cast<cd *>(wb + A.off_acc);   // 2 x NB: first / second derivative terms per node
+
+    const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
+    const int64_t ntiles = A.W * A.nchunks;
+    for (;;) {
+        if (t == 0) *slot = (long long)atomicAdd(A.counter, 1ull);
+        group_sync(bar);
+        const int64_t tile = (int64_t)*slot;
+        if (tile >= ntiles) break;
+        const int ch = (int)(tile / A.W);  // chunk-major order
+        const int64_t w = tile - (int64_t)ch * A.W;
+        const int64_t p0 = (int64_t)ch * A.chunk;
+        const int64_t p1 = p0 + A.chunk < L ? p0 + A.chunk : L;
+        cd So = cmk(0.0, 0.0), S1 = cmk(0.0, 0.0), S2 = cmk(0.0, 0.0);
+        if (p0 < L) {
+            const cd *Utw = A.Ut + w * n * n;
+            for (int e = t; e < n * n; e += kGroup) Uts[(e / n) * lu + (e % n)] = Utw[e];
+            const cd *Kw = A.Kop + (size_t)w * A.nop * m * n2;
+            const cd *K2w = A.K2 + (size_t)w * m * n2;
+            for (int64_t pq = p0; pq < p1; ++pq) {
+                const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+                group_sync(bar);
+                load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
+                for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
+                group_sync(bar);
+                build_T(n, Uts, Qs, Ts, t, kGroup);
+                group_sync(bar);
+                build_B(n, ne, Ts, Bs, tab, t, kGroup);
+                group_sync(bar);
+                cd Sop = cmk(0.0, 0.0), S1p = cmk(0.0, 0.0), S2p = cmk(0.0, 0.0);
+                for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                    const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                    node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar);
+                    node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                    if (t < nb) {
+                        cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
+                        acc[t] = cmk(0.0, 0.0);
+                        acc[A.NB + t] = cmk(0.0, 0.0);
+                    }
+                    if (t == 0)
+                        for (int v = 0; v < nb; ++v) cfma(Sop, A.gamma[k0 + v], pf[v]);
+                    group_sync(bar);
+                    // operators: Cholesky vectors (second derivative), then h (first derivative);
+                    // the last pass (o = nop) forms A'' = X'' J X^T + X J X''^T + 2 Sacc
+                    for (int o = 0; o <= A.nop; ++o) {
+                        const bool is_h = A.has_h && o == A.nchol;
+                        const bool last = o == A.nop;
+                        const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
+                        // X1 = Ko Q'^T: X1[a][c] = sum_k Ko[a][2k] Re Qt[c][k] - Ko[a][2k+1] Im Qt[c][k]
+                        for (int e = t; e < m * n2; e += kGroup) {
+                            const int a = e / n2, c = e - a * n2;
+                            const cd *kr = Ko + a * n2;
+                            const cd *qr = Qs + c * lq;
+                            cd s = cmk(0.0, 0.0);
+                            for (int k = 0; k < n; ++k) {
+                                crfma(s, kr[2 * k], qr[k].x);
+                                crfma(s, kr[2 * k + 1], -qr[k].y);
+                            }
+                            X1[a * lx + c] = s;
+                        }
+                        group_sync(bar);
+                        // Ap = X1 J X^T + X J X1^T (+ 2 Sacc on the last pass); Sacc += X1 J X1^T
+                        for (int e = t; e < T; e += kGroup) {
+                            int a, b;
+                            pair_of(tab, e, a, b);
+                            cd v = cadd(yjz(n, [&](int c) { return X1[a * lx + c]; },
+                                            [&](int c) { return x_at(Ts, lt, ne, b, c); }),
+                                        yjz(n, [&](int c) { return x_at(Ts, lt, ne, a, c); },
+                                            [&](int c) { return X1[b * lx + c]; }));
+                            if (last) {
+                                v = cadd(v, cscale(Sacc[e], 2.0));
+                            } else if (!is_h && k0 == 0) {
+                                Sacc[e] = cadd(Sacc[e], yjz(n, [&](int c) { return X1[a * lx + c]; },
+                                                            [&](int c) { return X1[b * lx + c]; }));
+                            }
+                            Ap[tri_index(a, b)] = v;
+                        }
+                        group_sync(bar);
+                        for (int v = 0; v < nb; ++v) {
+                            const cd *Zv = Ns + v * T;  // A_v^-1
+                            // t1 = tr(A^-1 Ap) = -2 sum_{a<b} Z_ab Ap_ab
+                            cd t1 = cmk(0.0, 0.0);
+                            for (int e = t; e < T; e += kGroup) cfma(t1, Zv[e], Ap[e]);
+                            t1 = cscale(group_sum(t1, red, t, bar), -2.0);
+                            if (last) {
+                                if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], t1);
+                                continue;
+                            }
+                            if (is_h) {
+                                if (t == 0) acc[v] = cadd(acc[v], t1);
+                                continue;
+                            }
+                            // t2 = tr((A^-1 Ap)^2) = sum_{a,b} P_ab P_ba, P = A^-1 Ap: one unordered
+                            // pair {a, b} (a <= b) per item, both products formed by the same thread
+                            cd t2 = cmk(0.0, 0.0);
+                            const int npairs = m * (m + 1) / 2;
+                            for (int e = t; e < npairs; e += kGroup) {
+                                int a = 0, r = e;
+                                while (r >= m - a) {
+                                    r -= m - a;
+                                    ++a;
+                                }
+                                const int b = a + r;
+                                cd pab = cmk(0.0, 0.0), pba = cmk(0.0, 0.0);
+                                for (int c = 0; c < m; ++c) {
+                                    cfma(pab, skew_at(Zv, a, c), skew_at(Ap, c, b));
+                                    cfma(pba, skew_at(Zv, b, c), skew_at(Ap, c, a));
+                                }
+                                const cd pr = cmul(pab, pba);
+                                t2 = (a == b) ? cadd(t2, pr) : cadd(t2, cscale(pr, 2.0));
+                            }
+                            t2 = group_sum(t2, red, t, bar);
+                            if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], csub(cscale(cmul(t1, t1), 0.5), t2));
+                        }
+                        group_sync(bar);
+                    }
+                    if (t == 0)
+                        for (int v = 0; v < nb; ++v) {
+                            cfma(S1p, cf[v], acc[v]);
+                            cfma(S2p, cf[v], acc[A.NB + v]);
+                        }
+                    group_sync(bar);
+                }
+                if (t == 0) {
+                    if (!cfinite(Sop) || !cfinite(S1p) || !cfinite(S2p)) raise_status(A.status, QCS_ERR_NONFINITE);
+                    So = cadd(So, Sop);
+                    S1 = cadd(S1, S1p);
+                    S2 = cadd(S2, S2p);
+                }
+            }
+        }
+        group_sync(bar);
+        if (t == 0) {
+            cd *out = A.partial + (w * A.nchunks + ch) * 3;
+            out[0] = So;
+            out[1] = S1;
+            out[2] = S2;
+        }
+    }
+}
+
+// Per walker: K (m x 2n) from the rotated rows Ut, and for each operator o the
+// Majorana form ell_o of its one-body matrix, [Lhat, g_mu] = sum_a ell_{mu a} g_a:
+//   ell[2r][2q] = ell[2r+1][2q+1] = (L_qr - L_rq)/2,
+//   ell[2r][2q+1] = -i (L_rq + L_qr)/2,  ell[2r+1][2q] = i (L_rq + L_qr)/2;
+// Kop[w][o] = K ell_o and K2[w] = sum_gamma K ell_gamma^2.  One block per walker.
+__global__ void energy_prep_kernel(int n, int ne, int64_t W, int nchol, int has_h, const cd *__restrict__ Ut,
+                                   const cd *__restrict__ Lg, const cd *__restrict__ h, cd *__restrict__ Kop,
+                                   cd *__restrict__ K2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = 2 * n, m = 2 * n - ne, nop = nchol + has_h;
+    cd *K = reinterpret_cast<cd *>(smem_raw);   // m x 2n
+    cd *ell = K + m * n2;                       // 2n x 2n
+    cd *K1 = ell + n2 * n2;                     // m x 2n (K ell)
+    cd *Ka = K1 + m * n2;                       // m x 2n (sum K ell^2)
+    for (int64_t w = blockIdx.x; w < W; w += gridDim.x) {
+        const cd *U = Ut + w * n * n;
+        // Ut~[j][2k] = Ut[j][k], Ut~[j][2k+1] = -i Ut[j][k]; K rows: occupied j -> Ut~_j,
+        // empty j -> Re Ut~_j, -Im Ut~_j
+        for (int e = threadIdx.x; e < m * n2; e += blockDim.x) {
+            const int a = e / n2, c = e - a * n2, k = c >> 1;
+            const int j = a < ne ? a : ne + ((a - ne) >> 1);
+            const cd u = U[j * n + k];
+            const cd ut = (c & 1) ? cmk(u.y, -u.x) : u;
+            K[e] = a < ne ? ut : (((a - ne) & 1) ? cmk(-ut.y, 0.0) : cmk(ut.x, 0.0));
+            Ka[e] = cmk(0.0, 0.0);
+        }
+        __syncthreads();
+        for (int o = 0; o < nop; ++o) {
+            const cd *Lo = o < nchol ? Lg + (size_t)o * n * n : h;
+            for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+                const int mu = e / n2, a = e - mu * n2, r = mu >> 1, q = a >> 1;
+                const cd lrq = Lo[r * n + q], lqr = Lo[q * n + r];
+                const cd dif = cscale(csub(lqr, lrq), 0.5), sum = cscale(cadd(lrq, lqr), 0.5);
+                cd v;
+                if ((mu & 1) == (a & 1)) v = dif;
+                else if ((mu & 1) == 0) v = cmk(sum.y, -sum.x);  // -i sum
+                else v = cmk(-sum.y, sum.x);                     // i sum
+                ell[e] = v;
+            }
+            __syncthreads();
+            cd *Ko = Kop + ((size_t)w * nop + o) * m * n2;
+            for (int e = threadIdx.x; e < m * n2; e += blockDim.x) {
+                const int a = e / n2, c = e - a * n2;
+                cd s = cmk(0.0, 0.0);
+                for (int k = 0; k < n2; ++k) cfma(s, K[a * n2 + k], ell[k * n2 + c]);
+                K1[e] = s;
+                Ko[e] = s;
+            }
+            __syncthreads();
+            if (o < nchol)
+                for (int e = threadIdx.x; e < m * n2; e += blockDim.x) {
+                    const int a = e / n2, c = e - a * n2;
+                    cd s = Ka[e];
+                    for (int k = 0; k < n2; ++k) cfma(s, K1[a * n2 + k], ell[k * n2 + c]);
+                    Ka[e] = s;
+                }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < m * n2; e += blockDim.x) K2[(size_t)w * m * n2 + e] = Ka[e];
+        __syncthreads();
+    }
+}
+
+// Per walker: sums of the tile records in order; O = pref sum So / P,
+// e1 = sum S1 / sum So, e2 = sum S2 / sum So.
+__global__ void energy_reduce_kernel(int64_t W, int64_t P, int nchunks, const cd *__restrict__ partial,
+                                     const cd *__restrict__ pref, cd *__restrict__ ov, cd *__restrict__ e1,
+                                     cd *__restrict__ e2) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    cd so = cmk(0.0, 0.0), s1 = cmk(0.0, 0.0), s2 = cmk(0.0, 0.0);
+    for (int c = 0; c < nchunks; ++c) {
+        const cd *r = partial + (w * nchunks + c) * 3;
+        so = cadd(so, r[0]);
+        s1 = cadd(s1, r[1]);
+        s2 = cadd(s2, r[2]);
+    }
+    const double invP = P > 0 ? 1.0 / (double)P : 0.0;
+    if (ov) ov[w] = cscale(cmul(pref[w], so), invP);
+    const cd iso = cinv(so);
+    if (e1) e1[w] = cmul(s1, iso);
+    if (e2) e2[w] = cmul(s2, iso);
+}
+
+size_t energy_group_layout(EnergyArgs &A) {
+    const int n = A.n, m = A.m, T = tri_count(m), NB = A.NB, S = m / 2;
+    size_t o = align16((size_t)n * ld_ut(n) * sizeof(cd));
+    A.off_Q = (int)o;
+    o = align16(o + (size_t)2 * n * ld_qt(n) * sizeof(cd));
+    A.off_T = (int)o;
+    o = align16(o + (size_t)n * ld_t(n) * sizeof(cd));
+    A.off_B = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_NZ = (int)o;
+    o = align16(o + (size_t)NB * T * sizeof(cd));
+    A.off_g1 = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_g2 = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_y1 = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_y2 = (int)o;
+    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_pf = (int)o;
+    o = align16(o + (size_t)kMaxNBG * sizeof(cd));
+    A.off_cf = (int)o;
+    o = align16(o + (size_t)kMaxNBG * sizeof(cd));
+    A.off_invh = (int)o;
+    o = align16(o + (size_t)NB * S * sizeof(cd));
+    A.off_int = (int)o;
+    o = align16(o + (size_t)kMaxNBG * sizeof(int));
+    A.off_tile = (int)o;
+    o = align16(o + sizeof(long long));
+    A.off_acth = (int)o;
+    o = align16(o + (size_t)NB * (S + 1) * m);
+    A.off_kh = (int)o;
+    o = align16(o + (size_t)NB * S);
+    A.off_ph = (int)o;
+    o = align16(o + (size_t)NB * S);
+    A.off_X1 = (int)o;
+    o = align16(o + (size_t)m * (2 * n + 1) * sizeof(cd));
+    A.off_Ap = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_Sacc = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_red = (int)o;
+    o = align16(o + (size_t)2 * sizeof(cd));
+    A.off_acc = (int)o;
+    o = align16(o + (size_t)2 * kMaxNBG * sizeof(cd));
+    return o;
+}
+
+}  // namespace
+
+extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W,
+                                       const double *d_walkers, int nchol, const double *d_L, const double *d_h,
+                                       double *d_overlap, double *d_e1, double *d_e2, const qcs_opts *opts,
+                                       void *stream) {
+    if (!ctx) return QCS_ERR_ARG;
+    if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set");
+    const int n = s->n;
+    if (n < 2 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1))
+        return qcs_fail(ctx, QCS_ERR_ARG, "ne must be even with 2 <= ne <= n");
+    if (nchol < 0 || (nchol > 0 && !d_L)) return qcs_fail(ctx, QCS_ERR_ARG, "nchol < 0 or null Cholesky vectors");
+    if (W < 0) return qcs_fail(ctx, QCS_ERR_ARG, "W < 0");
+    if (W == 0) return QCS_OK;
+    if (!d_walkers) return qcs_fail(ctx, QCS_ERR_ARG, "null walkers");
+    if (s->device != ctx->device) return qcs_fail(ctx, QCS_ERR_ARG, "snapshot set lives on another device");
+    qcs_opts o = {QCS_FP64, 0, 0u, 0};
+    if (opts) o = *opts;
+    if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "local energies are FP64 only");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    qcs_node_plan plan;
+    if (qcs_make_node_plan(n, ne, o.nodes, o.flags, &plan) != QCS_OK)
+        return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
+    const int m = 2 * n - ne, n2 = 2 * n, has_h = d_h ? 1 : 0, nop = nchol + has_h;
+    // tiles: about 8 per resident group, one snapshot chunk per tile
+    int64_t target = (int64_t)ctx->num_sms * 2 * 8;
+    int64_t nch = (target + W - 1) / W;
+    if (nch > s->P) nch = s->P;
+    if (nch < 1) nch = 1;
+    int chunk = (int)((s->P + nch - 1) / nch);
+    if (chunk < 1) chunk = 1;
+    int nchunks = (int)((s->P + chunk - 1) / chunk);
+    if (nchunks < 1) nchunks = 1;
+    const size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
+    const size_t b_pref = align16(sizeof(cd) * (size_t)W);
+    const size_t b_kop = align16(sizeof(cd) * (size_t)W * (nop > 0 ? nop : 1) * m * n2);
+    const size_t b_k2 = align16(sizeof(cd) * (size_t)W * m * n2);
+    const size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * 3);
+    void *base = nullptr;
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_kop + b_k2 + b_part, &base);
+    if (ws != QCS_OK) return ws;
+    char *pb = (char *)base;
+    unsigned long long *counter = (unsigned long long *)pb;
+    cd *Ut = (cd *)(pb + 16);
+    cd *pref = (cd *)(pb + 16 + b_ut);
+    cd *Kop = (cd *)(pb + 16 + b_ut + b_pref);
+    cd *K2 = (cd *)(pb + 16 + b_ut + b_pref + b_kop);
+    cd *part = (cd *)(pb + 16 + b_ut + b_pref + b_kop + b_k2);
+    qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st);
+    if (r != QCS_OK) return r;
+    {
+        const size_t sm = sizeof(cd) * ((size_t)3 * m * n2 + (size_t)n2 * n2);
+        if (qcs_set_smem(ctx, (const void *)energy_prep_kernel, sm) != QCS_OK) return QCS_ERR_CUDA;
+        int64_t blocks = W < (int64_t)ctx->num_sms * 4 ? W : (int64_t)ctx->num_sms * 4;
+        energy_prep_kernel<<<(unsigned)blocks, 256, sm, st>>>(n, ne, W, nchol, has_h, Ut, (const cd *)d_L,
+                                                               (const cd *)d_h, Kop, K2);
+        r = qcs_check_launch(ctx, "energy_prep_kernel");
+        if (r != QCS_OK) return r;
+    }
+    EnergyArgs A;
+    memset(&A, 0, sizeof(A));
+    A.n = n;
+    A.ne = ne;
+    A.m = m;
+    A.d = n - ne;
+    A.nev = plan.nev;
+    A.nop = nop;
+    A.nchol = nchol;
+    A.has_h = has_h;
+    A.all = plan.all;
+    A.chunk = chunk;
+    A.nchunks = nchunks;
+    A.W = W;
+    A.P = s->P;
+    A.tab_bytes = (int)align16((size_t)tri_count(m) * sizeof(uint16_t));
+    A.Ut = Ut;
+    A.Qt = s->Qt;
+    A.idx = s->idx;
+    A.d_count = s->d_count;
+    A.Kop = Kop;
+    A.K2 = K2;
+    A.partial = part;
+    A.counter = counter;
+    A.status = ctx->d_status;
+    for (int k = 0; k < plan.nev; ++k) {
+        A.wnode[k] = plan.wnode[k];
+        A.gamma[k] = plan.gamma[k];
+    }
+    // node matrices per round: all when they fit, else fewer (rounds then repeat the
+    // per-operator work); one or two groups per block
+    int NB = plan.nev < kMaxNBG ? plan.nev : kMaxNBG, gpb = 2;
+    for (;;) {
+        A.NB = NB;
+        A.group_bytes = (int)energy_group_layout(A);
+        if ((size_t)A.tab_bytes + (size_t)gpb * A.group_bytes <= ctx->smem_optin) break;
+        if (gpb == 2) gpb = 1;
+        else if (NB > 1) {
+            --NB;
+            gpb = 2;
+        } else {
+            return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "local-energy kernel: shared memory too large");
+        }
+    }
+    const size_t smem = (size_t)A.tab_bytes + (size_t)gpb * A.group_bytes;
+    if (qcs_set_smem(ctx, (const void *)energy_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, energy_pair_kernel, gpb * kGroup, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t ntiles = W * nchunks;
+    int64_t blocks = (int64_t)ctx->num_sms * per_sm;
+    const int64_t need = (ntiles + gpb - 1) / gpb;
+    if (blocks > need) blocks = need;
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return qcs_fail(ctx, QCS_ERR_CUDA, "energy tile counter reset");
+    qcs_prof_begin(ctx, st);
+    energy_pair_kernel<<<(unsigned)blocks, gpb * kGroup, smem, st>>>(A);
+    qcs_prof_end(ctx, st);
+    r = qcs_check_launch(ctx, "energy_pair_kernel");
+    if (r != QCS_OK) return r;
+    energy_reduce_kernel<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(W, s->P, nchunks, part, pref,
+                                                                      (cd *)d_overlap, (cd *)d_e1, (cd *)d_e2);
+    return qcs_check_launch(ctx, "energy_reduce_kernel");
+}
+
+extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int has_h, int nodes, unsigned flags) {
+    qcs_node_plan plan;
+    if (n < 2 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1) || nchol < 0) return 0.0;
+    if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
+    const double m = 2.0 * n - ne, n2 = 2.0 * n, T = m * (m - 1) / 2;
+    double f = qcs_overlap_flops_nev(n, ne, plan.nev);  // T, B and the Pfaffians
+    double inv = 0.0;                                      // backward inverse per node
+    for (int r = (int)m; r > 2; r -= 2) inv += 16.0 * (r - 2) * (r - 2) + 20.0 * (r - 2);
+    f += inv * plan.nev;
+    const double xprime = 4.0 * m * n2 * n2;      // X' = (K ell) Q'^T, complex x real
+    const double aprime = 8.0 * T * 2.0 * n2;     // A' = X' J X^T + X J X'^T (upper triangle)
+    const double sacc = 8.0 * T * n2;             // X' J X'^T
+    const double t1 = 8.0 * T;                    // tr(A^-1 A') per node
+    const double t2 = 8.0 * (m * (m + 1) / 2) * 2.0 * m;  // P_ab, P_ba per unordered pair, per node
+    f += nchol * (xprime + aprime + sacc + plan.nev * (t1 + t2));
+    f += has_h * (xprime + aprime + plan.nev * t1);
+    f += xprime + aprime + plan.nev * t1;  // the A'' pass
+    return f;
+}

@@ -1,0 +1,184 @@
+// qcs_group.cuh -- per-pair building blocks for kernels in which two warps (a group
+// of 64 threads with its own named barrier) share one walker-snapshot pair: the
+// forward Parlett-Reid elimination of a round of node matrices that keeps its step
+// history, and the backward recursion that assembles each node matrix's inverse in
+// place over its factors (used by the adjoint and the local-energy kernels).
+#pragma once
+#include "qcs_pair.cuh"
+
+constexpr int kMaxNBG = 4;  // node matrices per round, at most
+constexpr int kGroup = 64;  // threads (two warps) that share one pair
+
+// Barrier of the two warps that share a pair (named barrier `id`, 64 threads).
+__device__ __forceinline__ void group_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kGroup) : "memory");
+}
+
+// Skew matrix entry (i, j) from its packed upper triangle.
+__device__ __forceinline__ cd skew_at(const cd *P, int i, int j) {
+    if (i == j) return cmk(0.0, 0.0);
+    int lo = i < j ? i : j, hi = i < j ? j : i;
+    return flip_if(P[tri_index(lo, hi)], i > j);
+}
+
+// Forward Parlett-Reid elimination of nb node matrices B + wnode D (packed upper,
+// original index order) by the pair's 64 threads, keeping the step history (active
+// index lists, pivot rows and columns, pivot reciprocals) for the backward inverse.
+// pf[v] receives pf(B + wnode[v] D).
+__device__ inline void node_factor(int m, int ne, const cd *__restrict__ wnode, int nb, const cd *__restrict__ Bs,
+                                   cd *__restrict__ Ns,
+                            cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ invh,
+                            int *__restrict__ pos, uint8_t *__restrict__ acth, uint8_t *__restrict__ kh,
+                            uint8_t *__restrict__ ph, const uint16_t *__restrict__ tab, int t, int bar) {
+    const int d = (m - ne) / 2, T = tri_count(m), S = m / 2;
+    const int hstride = (S + 1) * m;
+    const int lane = t & 31;
+    for (int e = t; e < nb * T; e += kGroup) {
+        int v = e / T, u = e - v * T;
+        Ns[v * T + u] = Bs[u];
+    }
+    for (int e = t; e < nb * m; e += kGroup) {
+        int v = e / m, a = e - v * m;
+        acth[v * hstride + a] = (uint8_t)a;
+    }
+    if (t < nb) pf[t] = cmk(1.0, 0.0);
+    group_sync(bar);
+    for (int e = t; e < nb * d; e += kGroup) {
+        int v = e / d, i = e - v * d;
+        cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
+        *x = cadd(*x, wnode[v]);
+    }
+    group_sync(bar);
+    for (int s = 0; s < S; ++s) {
+        const int r = m - 2 * s;
+        const uint8_t *cur = acth + s * m;
+        uint8_t *nxt = acth + (s + 1) * m;
+        if (t < 32) {
+            // pivot: largest |A_{k,i}| over the active row of k = cur[0].  Warp 0 alone:
+            // nb segments of seg lanes, a shuffle reduction inside each segment.
+            const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : 8;
+            const int v = lane / seg, sl = lane - v * seg;
+            unsigned long long bk = 0ull;
+            if (v < nb) {
+                const int k = cur[v * hstride];
+                for (int a = 1 + sl; a < r; a += seg) {
+                    const unsigned key = pivot_key(Ns[v * T + tri_index(k, cur[v * hstride + a])]);
+                    const unsigned long long c =
+                        ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
+                    bk = c > bk ? c : bk;
+                }
+            }
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+                bk = ob > bk ? ob : bk;
+            }
+            bk = __shfl_sync(QCS_FULL, bk, (lane < nb ? lane : 0) * seg);
+            if (lane < nb) {
+                const int a = 0xffff - (int)(bk & 0xffffull);
+                const int k = cur[lane * hstride], p = cur[lane * hstride + a];
+                const cd piv = Ns[lane * T + tri_index(k, p)];
+                const cd f = cmul(pf[lane], piv);
+                pf[lane] = ((a - 1) & 1) ? cneg(f) : f;
+                invh[lane * S + s] = cinv(piv);
+                pos[lane] = a;
+                kh[lane * S + s] = (uint8_t)k;
+                ph[lane * S + s] = (uint8_t)p;
+            }
+        }
+        group_sync(bar);
+        const int rv = r - 2;
+        for (int e = t; e < nb * rv; e += kGroup) {
+            const int v = e / rv, a2 = e - v * rv;
+            const int a = a2 + 1 + ((a2 + 1 >= pos[v]) ? 1 : 0);
+            const int i = cur[v * hstride + a], k = kh[v * S + s], p = ph[v * S + s];
+            const cd *Nv = Ns + v * T;
+            Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], invh[v * S + s]);
+            Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
+            nxt[v * hstride + a2] = (uint8_t)i;
+        }
+        group_sync(bar);
+        const int Tr = tri_count(rv);
+        for (int e = t; e < nb * Tr; e += kGroup) {
+            const int v = e / Tr, u = e - v * Tr;
+            int a, b;
+            pair_of(tab, u, a, b);
+            const int i = nxt[v * hstride + a], j = nxt[v * hstride + b];
+            cd *x = Ns + v * T + tri_index(i, j);
+            cd y = *x;
+            cfms(y, Uv[v * m + a], Vv[v * m + b]);
+            cfma(y, Vv[v * m + a], Uv[v * m + b]);
+            *x = y;
+        }
+        group_sync(bar);
+    }
+}
+
+// Backward recursion, in place: the factors of node v in Ns become the packed
+// upper triangle of the inverse of node matrix v.  Step s first reads its pivot
+// row and column (entries (k,i) and (i,p) for the indices i still active after
+// the step), then overwrites exactly those entries, and (k,p), with entries of the
+// inverse; the entries among the later indices already hold the inverse of the
+// step's Schur complement Z.
+__device__ inline void node_inverse(int m, int nb, cd *__restrict__ Ns, cd *__restrict__ g1v,
+                             cd *__restrict__ g2v, cd *__restrict__ y1v, cd *__restrict__ y2v,
+                             const cd *__restrict__ invh, const uint8_t *__restrict__ acth,
+                             const uint8_t *__restrict__ kh, const uint8_t *__restrict__ ph, int t, int bar) {
+    const int T = tri_count(m), S = m / 2;
+    const int hstride = (S + 1) * m;
+    const int lane = t & 31;
+    for (int s = S - 1; s >= 0; --s) {
+        const int rv = m - 2 * s - 2;
+        // g1 = v/a, g2 = -u/a with u_i = A_{i,k} = -N(k,i), v_i = A_{i,p}
+        for (int e = t; e < nb * rv; e += kGroup) {
+            const int v = e / rv, a = e - v * rv;
+            const cd *Nv = Ns + v * T;
+            const int i = acth[v * hstride + (s + 1) * m + a], k = kh[v * S + s], p = ph[v * S + s];
+            const cd ia = invh[v * S + s];
+            const cd vi = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
+            g1v[v * m + a] = cmul(vi, ia);
+            g2v[v * m + a] = cmul(Nv[tri_index(k, i)], ia);
+        }
+        group_sync(bar);
+        // y1 = Z g1 and y2 = Z g2 over the later indices: one (node, vector, row) item per thread
+        const int per = 2 * rv;
+        for (int e = t; e < nb * per; e += kGroup) {
+            const int v = e / per, r2 = e - v * per;
+            const int vec = r2 >= rv ? 1 : 0, a = r2 - vec * rv;
+            const cd *Zv = Ns + v * T;
+            const uint8_t *rest = acth + v * hstride + (s + 1) * m;
+            const cd *g = (vec ? g2v : g1v) + v * m;
+            const int i = rest[a];
+            cd y = cmk(0.0, 0.0);
+            for (int b = 0; b < rv; ++b) {
+                const int j = rest[b];
+                if (j == i) continue;
+                cfma(y, flip_if(Zv[tri_index(i < j ? i : j, i < j ? j : i)], j < i), g[b]);
+            }
+            (vec ? y2v : y1v)[v * m + a] = y;
+        }
+        group_sync(bar);
+        // corner g1^T Z g2 per node (warp 0: segmented shuffle sums), then the new entries
+        if (t < 32) {
+            const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : 8;
+            const int v = lane / seg, sl = lane - v * seg;
+            cd corner = cmk(0.0, 0.0);
+            if (v < nb)
+                for (int a = sl; a < rv; a += seg) cfma(corner, g1v[v * m + a], y2v[v * m + a]);
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                corner.x += __shfl_xor_sync(QCS_FULL, corner.x, o);
+                corner.y += __shfl_xor_sync(QCS_FULL, corner.y, o);
+            }
+            if (v < nb && sl == 0) Ns[v * T + tri_index(kh[v * S + s], ph[v * S + s])] = csub(corner, invh[v * S + s]);
+        }
+        for (int e = t; e < nb * rv; e += kGroup) {
+            const int v = e / rv, a = e - v * rv;
+            cd *Zv = Ns + v * T;
+            const int i = acth[v * hstride + (s + 1) * m + a], k = kh[v * S + s], p = ph[v * S + s];
+            Zv[tri_index(k, i)] = y1v[v * m + a];  // Z(k,i) = -Z(i,k) = (Z g1)_i
+            const cd y2 = y2v[v * m + a];          // Z(i,p) = -y2_i
+            if (i < p) Zv[tri_index(i, p)] = cneg(y2);
+            else Zv[tri_index(p, i)] = y2;
+        }
+        group_sync(bar);
+    }
+}

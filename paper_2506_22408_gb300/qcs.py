@@ -37,6 +37,7 @@ EXPORTED = [
     "qcs_autotune", "qcs_set_config", "qcs_overlap_batched", "qcs_node_plan_get",
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
+    "qcs_local_energy", "qcs_local_energy_flops_per_pair",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -101,6 +102,9 @@ def load(build_if_missing: bool = True):
         lib.qcs_snapshots_signed_perm_count.argtypes = [P, ctypes.POINTER(i64), P]
         lib.qcs_shadow_rdm.argtypes = [P, P, P, P, P, P, P, P]
         lib.qcs_vce_transform.argtypes = [P, i32, i32, i32, i32, i64, P, P, i64, i32, P, P]
+        lib.qcs_local_energy.argtypes = [P, P, i32, i64, P, i32, P, P, P, P, P, ctypes.POINTER(_Opts), P]
+        lib.qcs_local_energy_flops_per_pair.argtypes = [i32, i32, i32, i32, i32, u32]
+        lib.qcs_local_energy_flops_per_pair.restype = f64
         lib.qcs_shadow_rdm_flops.argtypes = [i32, i64]
         lib.qcs_shadow_rdm_flops.restype = f64
         for fn in ("qcs_overlap_flops_per_pair_signed_perm", "qcs_grad_flops_per_pair_signed_perm"):
@@ -397,6 +401,30 @@ def vce_transform(ctx: Context, walkers: torch.Tensor, nc: int, na: int, nea: in
     ctx.check(ctx.lib.qcs_vce_transform(ctx.h, NB, nc, na, nea, W, _ptr(walkers), base,
                                         act.shape[1] * act.shape[2], act.shape[2], _ptr(factor), _stream()))
     return act, factor
+
+
+def local_energy(ctx: Context, snaps: Snapshots, walkers: torch.Tensor, L: torch.Tensor,
+                 h: torch.Tensor | None = None, nodes: int = 0, flags: int = 0):
+    """(overlap, e1, e2) per walker (qcs_local_energy): e1 = <Psi_T|hhat|phi>/O (None
+    without h), e2 = sum_gamma <Psi_T|Lhat_gamma^2|phi>/O.  L: (nchol, n, n) complex128."""
+    _need_cuda(walkers, "walkers", torch.complex128)
+    _need_cuda(L, "L", torch.complex128)
+    if h is not None:
+        _need_cuda(h, "h", torch.complex128)
+    W, n, ne = walkers.shape
+    dev = walkers.device
+    ov = torch.empty(W, dtype=torch.complex128, device=dev)
+    e1 = torch.empty(W, dtype=torch.complex128, device=dev) if h is not None else None
+    e2 = torch.empty(W, dtype=torch.complex128, device=dev)
+    o = _opts(nodes, flags)
+    ctx.check(ctx.lib.qcs_local_energy(ctx.h, snaps.h, ne, W, _ptr(walkers), L.shape[0], _ptr(L), _ptr(h),
+                                       _ptr(ov), _ptr(e1), _ptr(e2), ctypes.byref(o), _stream()))
+    return ov, e1, e2
+
+
+def local_energy_flops_per_pair(n: int, ne: int, nchol: int, has_h: bool = True, nodes: int = 0,
+                                flags: int = 0) -> float:
+    return float(load().qcs_local_energy_flops_per_pair(n, ne, nchol, int(has_h), nodes, flags))
 
 
 def shadow_rdm_flops(n: int, P: int) -> float:
