@@ -73,7 +73,7 @@ __device__ __forceinline__ cd group_sum(cd v, cd *red, int t, int bar) {
     return s;
 }
 
-__global__ void __launch_bounds__(128, 1) energy_pair_kernel(const __grid_constant__ EnergyArgs A) {
+__global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_constant__ EnergyArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gid = threadIdx.x / kGroup;
     const int t = threadIdx.x - gid * kGroup;
@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(128, 1) energy_pair_kernel(const __grid_consta
     build_pair_table(tab, T);
     __syncthreads();
     unsigned char *wb = smem_raw + A.tab_bytes + (size_t)gid * A.group_bytes;
-    cd *Uts = reinterpret_cast<cd *>(wb);
+    // region X1R holds, in turn, the walker rows Ut (until T is built), the backward
+    // recursion's vectors (node rounds) and X' (operator loop)
+    cd *Uts = reinterpret_cast<cd *>(wb + A.off_X1);
     cd *Qs = reinterpret_cast<cd *>(wb + A.off_Q);
     cd *Ts = reinterpret_cast<cd *>(wb + A.off_T);
     cd *Bs = reinterpret_cast<cd *>(wb + A.off_B);
@@ -121,14 +123,13 @@ __global__ void __launch_bounds__(128, 1) energy_pair_kernel(const __grid_consta
         cd So = cmk(0.0, 0.0), S1 = cmk(0.0, 0.0), S2 = cmk(0.0, 0.0);
         if (p0 < L) {
             const cd *Utw = A.Ut + w * n * n;
-            for (int e = t; e < n * n; e += kGroup) Uts[(e / n) * lu + (e % n)] = Utw[e];
             const cd *Kw = A.Kop + (size_t)w * A.nop * m * n2;
             const cd *K2w = A.K2 + (size_t)w * m * n2;
             for (int64_t pq = p0; pq < p1; ++pq) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
                 group_sync(bar);
                 load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
-                for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
+                for (int e = t; e < n * n; e += kGroup) Uts[(e / n) * lu + (e % n)] = Utw[e];
                 group_sync(bar);
                 build_T(n, Uts, Qs, Ts, t, kGroup);
                 group_sync(bar);
@@ -139,6 +140,8 @@ __global__ void __launch_bounds__(128, 1) energy_pair_kernel(const __grid_consta
                     const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
                     node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar);
                     node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                    if (k0 == 0)  // B has been copied into the node matrices; Sacc may share its storage
+                        for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
                     if (t < nb) {
                         cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
                         acc[t] = cmk(0.0, 0.0);
@@ -332,7 +335,7 @@ __global__ void energy_reduce_kernel(int64_t W, int64_t P, int nchunks, const cd
 
 size_t energy_group_layout(EnergyArgs &A) {
     const int n = A.n, m = A.m, T = tri_count(m), NB = A.NB, S = m / 2;
-    size_t o = align16((size_t)n * ld_ut(n) * sizeof(cd));
+    size_t o = 0;
     A.off_Q = (int)o;
     o = align16(o + (size_t)2 * n * ld_qt(n) * sizeof(cd));
     A.off_T = (int)o;
@@ -341,14 +344,16 @@ size_t energy_group_layout(EnergyArgs &A) {
     o = align16(o + (size_t)T * sizeof(cd));
     A.off_NZ = (int)o;
     o = align16(o + (size_t)NB * T * sizeof(cd));
+    // shared region: Ut rows, then the recursion vectors, then X'
+    size_t r = (size_t)m * (2 * n + 1);
+    if ((size_t)n * ld_ut(n) > r) r = (size_t)n * ld_ut(n);
+    if ((size_t)4 * NB * m > r) r = (size_t)4 * NB * m;
+    A.off_X1 = (int)o;
     A.off_g1 = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
-    A.off_g2 = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
-    A.off_y1 = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
-    A.off_y2 = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
+    A.off_g2 = (int)(o + (size_t)NB * m * sizeof(cd));
+    A.off_y1 = (int)(o + (size_t)2 * NB * m * sizeof(cd));
+    A.off_y2 = (int)(o + (size_t)3 * NB * m * sizeof(cd));
+    o = align16(o + r * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNBG * sizeof(cd));
     A.off_cf = (int)o;
@@ -365,12 +370,14 @@ size_t energy_group_layout(EnergyArgs &A) {
     o = align16(o + (size_t)NB * S);
     A.off_ph = (int)o;
     o = align16(o + (size_t)NB * S);
-    A.off_X1 = (int)o;
-    o = align16(o + (size_t)m * (2 * n + 1) * sizeof(cd));
     A.off_Ap = (int)o;
     o = align16(o + (size_t)T * sizeof(cd));
-    A.off_Sacc = (int)o;
-    o = align16(o + (size_t)T * sizeof(cd));
+    if (NB >= A.nev) {
+        A.off_Sacc = A.off_B;  // one node round: B is dead once copied into the node matrices
+    } else {
+        A.off_Sacc = (int)o;
+        o = align16(o + (size_t)T * sizeof(cd));
+    }
     A.off_red = (int)o;
     o = align16(o + (size_t)2 * sizeof(cd));
     A.off_acc = (int)o;
