@@ -271,6 +271,9 @@ def run_batch(args, ctx, dev, barrier, ws):
         systems.append((wl, s, walkers))
         outs.append(torch.empty(wl.W, dtype=torch.complex128, device=dev))
     pairs_step = sum(wl.W * wl.P for wl, _, _ in systems)
+    # algorithmic FP64 flops of one step: parity +1 pairs of every system times its per-pair count
+    flops_step = sum(wl.W * int((s.parity() == 1).sum().item()) * qcs.flops_per_pair(wl.n, wl.ne)
+                     for wl, s, _ in systems)
     arg = [(s, w) for _, s, w in systems]
 
     def step():
@@ -306,6 +309,10 @@ def run_batch(args, ctx, dev, barrier, ws):
                        "walker_scale": args.batch_walker_scale,
                        "pairs_per_step": pairs_step,
                        "step": "stand-in propagation (torch matmul) + one qcs_overlap_batched launch sequence"},
+            "roofline": {"bound": "alu", "achieved": flops_step * args.batch_steps / t / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops_step * args.batch_steps / t / 1e12 / FP64_PEAK_TFLOPS,
+                         "kernel": "pair_overlap_kernel (batched)",
+                         "timing": "whole graph step (propagation, walker prep, pair kernel, reductions)"},
             "gpu_launches_per_step": 5 + 1 + 5}
 
 

@@ -16,7 +16,14 @@
  *   d pf(A) = pf(A) tr(A^{-1} dA) / 2  (Eq. Pfaffian_der);
  *
  *   the AFQMC force bias xbar_gamma = -sqrt(dtau) <Psi_T|v_gamma|phi>/<Psi_T|phi>
- *   (Eq. force_bias) evaluated as a derivative of the overlap (Eq. force_bias_diff).
+ *   (Eq. force_bias) evaluated as a derivative of the overlap (Eq. force_bias_diff);
+ *
+ *   the local-energy terms <Psi_T|hhat|phi>/O and sum_gamma <Psi_T|Lhat_gamma^2|phi>/O
+ *   by first and second Pfaffian derivatives (Eqs. energy_tb_diff, Pfaffian_2nd_der);
+ *
+ *   shadow estimates of Majorana correlators, the one-particle RDM and the particle
+ *   number (Supplementary "Reduced Density Matrices"), and the virtual-correlation-
+ *   energy walker transform (Eq. vce_overlap).
  *
  * Conventions shared by every entry point
  * ---------------------------------------

@@ -12,14 +12,15 @@
 //
 // Kernels: rdm_cov_kernel (warp per snapshot: X_p = (Q' R^T)^T J (Q' R^T) from the
 // stored rows Qt, upper triangle to global), rdm_colsum_kernel (deterministic
-// column sums), rdm_syrk_kernel (64 x 64 FP64 tiles of S2, split over snapshot
+// column sums), rdm_syrk_kernel (32 x 32 FP64 tiles of S2, split over snapshot
 // ranges, upper tiles only), rdm_finalize_kernel (gam2, rdm1, particle number,
 // gam4 from the reduced S2).
 #include "qcs_internal.h"
 
 namespace {
 
-constexpr int kTile = 64;     // S2 tile edge
+constexpr int kTile = 32;     // S2 tile edge (small tiles: less work in the lower halves of diagonal tiles)
+constexpr int kTThreads = 64; // threads per S2 tile: 8 x 8, each 4 x 4 entries
 constexpr int kKStep = 16;    // snapshots staged per step
 constexpr int kColRows = 256; // rows per column-sum partial (at least)
 
@@ -88,10 +89,10 @@ __global__ void rdm_colsum_kernel(int64_t P, int npair, int64_t rows, const doub
     part[r * npair + t] = s;
 }
 
-// S2 partials: block (ti, tj, ks) with ti <= tj computes the 64 x 64 tile
-// sum_{p in range ks} Gu[p][i] Gu[p][j]; each of the 256 threads owns 4 x 4 entries.
-__global__ void __launch_bounds__(256) rdm_syrk_kernel(int64_t P, int npair, int ntile, int64_t krange,
-                                                       const double *__restrict__ Gu, double *__restrict__ S2p) {
+// S2 partials: block (ti, tj, ks) with ti <= tj computes the 32 x 32 tile
+// sum_{p in range ks} Gu[p][i] Gu[p][j]; each of the 64 threads owns 4 x 4 entries.
+__global__ void __launch_bounds__(kTThreads) rdm_syrk_kernel(int64_t P, int npair, int ntile, int64_t krange,
+                                                             const double *__restrict__ Gu, double *__restrict__ S2p) {
     __shared__ double As[kKStep][kTile + 1];
     __shared__ double Bs[kKStep][kTile + 1];
     // upper-triangle tile (ti, tj) from the linear block index
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(256) rdm_syrk_kernel(int64_t P, int npair, int
     const int tj = ti + lin;
     const int64_t ks = blockIdx.y;
     const int64_t p0 = ks * krange, p1 = p0 + krange < P ? p0 + krange : P;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
     const int i0 = ti * kTile, j0 = tj * kTile;
     double acc[4][4];
 #pragma unroll
@@ -124,8 +125,8 @@ __global__ void __launch_bounds__(256) rdm_syrk_kernel(int64_t P, int npair, int
             double a[4], bb[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                a[u] = As[kk][ty + 16 * u];
-                bb[u] = Bs[kk][tx + 16 * u];
+                a[u] = As[kk][ty + 8 * u];
+                bb[u] = Bs[kk][tx + 8 * u];
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) rdm_syrk_kernel(int64_t P, int npair, int
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+            const int i = i0 + ty + 8 * u, j = j0 + tx + 8 * v;
             if (i < npair && j < npair && i <= j) out[(size_t)i * npair + j] = acc[u][v];
         }
 }
@@ -256,7 +257,7 @@ extern "C" qcs_status qcs_shadow_rdm(qcs_ctx *ctx, const qcs_snapshots *s, const
     const int nut = ntile * (ntile + 1) / 2;
     int nks = 1;
     if (d_gam4) {
-        nks = (int)((4 * (int64_t)ctx->num_sms + nut - 1) / nut);
+        nks = (int)((16 * (int64_t)ctx->num_sms + nut - 1) / nut);  // 16 blocks of 2 warps per SM
         const int64_t maxks = (P + 4 * kKStep - 1) / (4 * kKStep);
         if (nks > maxks) nks = (int)maxks;
         if (nks < 1) nks = 1;
@@ -288,7 +289,7 @@ extern "C" qcs_status qcs_shadow_rdm(qcs_ctx *ctx, const qcs_snapshots *s, const
     if (d_gam4) {
         if (cudaMemsetAsync(S2p, 0, b_s2, st) != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "S2 reset");
         qcs_prof_begin(ctx, st);
-        rdm_syrk_kernel<<<dim3((unsigned)nut, (unsigned)nks), 256, 0, st>>>(P, npair, ntile, krange, Gu, S2p);
+        rdm_syrk_kernel<<<dim3((unsigned)nut, (unsigned)nks), kTThreads, 0, st>>>(P, npair, ntile, krange, Gu, S2p);
         qcs_prof_end(ctx, st);
         r = qcs_check_launch(ctx, "rdm_syrk_kernel");
         if (r != QCS_OK) return r;
