@@ -38,10 +38,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "walker×snapshot overlap(+grad) pairs/s at n=16; % of FP64 peak vs plain GPU path"
-# FP64 ALU peak of a GB300: 152 SMs x 4 FP64 flop/clk/SM (one 32-lane DFMA issue per
-# 64 clocks per sub-partition, measured) x 2.07 GHz maximum SM clock.
+# FP64 ALU peak of a GB300 from unit counts: 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
+# maximum SM clock.  The sustained rate of register-only DFMA chains measured on this
+# pool's GB300 at 2070 MHz (paper_2506_22408_gb300/csrc/probes/fp64_fma_ceiling.cu) is
+# reported beside every FP64 roofline as context.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+FP64_DFMA_MEASURED_TFLOPS = 1.056
 L2_FLUSH_BYTES = 256 << 20
+
+
+def add_dfma_context(obj):
+    """Beside every FP64 ("alu") roofline, the fraction of the measured DFMA rate."""
+    if isinstance(obj, dict):
+        if obj.get("bound") == "alu" and isinstance(obj.get("achieved"), float):
+            obj["dfma_probe"] = {"tflops": FP64_DFMA_MEASURED_TFLOPS,
+                                 "frac": obj["achieved"] / FP64_DFMA_MEASURED_TFLOPS,
+                                 "source": "register-only DFMA chains at 2070 MHz "
+                                           "(csrc/probes/fp64_fma_ceiling.cu, profiles/fp64_fma_ceiling.md)"}
+        for v in list(obj.values()):
+            add_dfma_context(v)
+    elif isinstance(obj, list):
+        for v in obj:
+            add_dfma_context(v)
 
 
 def max_over_ranks(t: float, ws: int) -> float:
@@ -885,6 +903,7 @@ def main():
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)
+    add_dfma_context(line)
     if ws > 1:
         dist.barrier()
     if rank == 0:
