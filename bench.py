@@ -687,9 +687,37 @@ def cpu_baseline(wl, data, target_s=10.0):
     t0 = time.perf_counter()
     _, _, _, used = orc.overlap(data["Phi"][:Wc], data["Q"][:Pc2], data["b"][:Pc2], threads=cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one host thread, on a smaller sample (about 2 s)
+    P1 = max(1, min(Pc2, int(Pc2 * 2.0 / max(dt * used, 1e-3))))
+    t0 = time.perf_counter()
+    orc.overlap(data["Phi"][:Wc], data["Q"][:P1], data["b"][:P1], threads=1)
+    dt1 = time.perf_counter() - t0
+    orc.overlap(data["Phi"][:1], data["Q"][:1], data["b"][:1], threads=cores)  # restore the thread count
     return {"value": Wc * Pc2 / dt, "unit": "pairs/s", "cores": int(used), "kind": "oracle",
             "sample": f"{Wc} walkers x {Pc2} snapshots of the same workload (first rows), "
-                      f"{dt:.1f} s, FP64, 2n+1 roots-of-unity nodes, OpenMP over pairs"}
+                      f"{dt:.1f} s, FP64, 2n+1 roots-of-unity nodes, OpenMP over pairs",
+            "one_thread": {"value": Wc * P1 / dt1, "unit": "pairs/s",
+                           "sample": f"{Wc} walkers x {P1} snapshots, {dt1:.1f} s"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (Linux), else the platform's processor string."""
+    import platform
+
+    part = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    return line.split(":", 1)[1].strip()
+                if key == "cpu part" and part is None:  # Arm cores list an implementer part number
+                    part = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    base = platform.processor() or platform.machine()
+    return f"{base}, CPU part {part}" if part else base
 
 
 def run_reference(args, wl):
