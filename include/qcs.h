@@ -380,8 +380,15 @@ qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
 
 /* Algorithmic FP64 flop count per non-trivial (pi = +1) pair of qcs_overlap
  * for (n, ne, nodes), as implemented: congruence T = U^T Qtilde^T, the
- * selected covariance B^(s), and the rank-2 Pfaffian updates at the
- * evaluated nodes.  Used by the benchmark's roofline. */
+ * selected covariance B^(s), and the rank-2 Pfaffian updates.  The walker's
+ * orbitals are first rotated to echelon form (a reflection of the occupied
+ * columns changes det R by its sign, one of the complement changes nothing),
+ * which makes ne(ne-1)/2 + d(d-1)/2 entries of U exact zeros that T skips.
+ * The node matrices differ only in their empty x empty block, so the occupied
+ * block is eliminated once per pair and each node then costs a 2d x 2d
+ * Pfaffian; the count is that of this path (pairs whose occupied block would
+ * grow the complement more than 32-fold, a few percent, take the full
+ * elimination per node instead).  Used by the benchmark's roofline. */
 double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
 
 /* The same count for a pair whose snapshot is a signed permutation (no FP64

@@ -373,7 +373,8 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     wk->partial = (cd *)(pb + 16 + b_ut + b_pref);
     wk->Mhi = split ? (float *)(pb + 16 + b_ut + b_pref + b_part) : nullptr;
     wk->Mlo = split ? (float *)(pb + 16 + b_ut + b_pref + b_part + b_slab) : nullptr;
-    return qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, wk->Ut, wk->pref, st);
+    return qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, wk->Ut, wk->pref, st, nullptr, nullptr,
+                                  true);
 }
 
 }  // namespace
@@ -480,7 +481,7 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         Ls[i].pref = (cd *)(pb + off[i][1]);
         Ls[i].partial = (cd *)(pb + off[i][2]);
         r = qcs_launch_walker_prep(ctx, Ls[i].n, Ls[i].ne, Ls[i].W, (const cd *)systems[i].d_walkers,
-                                   (cd *)Ls[i].Ut, (cd *)Ls[i].pref, st);
+                                   (cd *)Ls[i].Ut, (cd *)Ls[i].pref, st, nullptr, nullptr, true);
         if (r != QCS_OK) return r;
     }
     r = qcs_launch_pairs_batched(ctx, nsys, Ls, (unsigned long long *)pb, st);
@@ -583,7 +584,7 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
     const int d = n - ne, m = 2 * n - ne, T = tri_count(m);
-    double f = qcs_overlap_flops_per_pair(n, ne, nodes, flags);  // forward pass
+    double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);    // forward pass (dense T)
     double node = 0.0;                                              // backward inverse per node
     for (int r = m; r > 2; r -= 2) node += 16.0 * (double)(r - 2) * (r - 2) + 8.0 * (r - 2) + 12.0 * (r - 2);
     f += (node + 8.0 * T) * plan.nev;                               // inverse + Y accumulation
@@ -593,8 +594,11 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
 }
 
 extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
-    const double f = qcs_overlap_flops_per_pair(n, ne, nodes, flags);
-    return f > 0.0 ? f - 16.0 * (double)n * n * n : 0.0;  // T is a gather
+    qcs_node_plan plan;
+    if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
+    if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
+    const double t_flops = 16.0 * (double)n * ((double)n * n - tri_count(ne) - tri_count(n - ne));
+    return qcs_overlap_flops_nev(n, ne, plan.nev, true) - t_flops;  // T is a gather
 }
 
 extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
@@ -608,19 +612,32 @@ extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned 
     qcs_node_plan plan;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
-    return qcs_overlap_flops_nev(n, ne, plan.nev);
+    return qcs_overlap_flops_nev(n, ne, plan.nev, true);
 }
 
-double qcs_overlap_flops_nev(int n, int ne, int nev) {
+namespace {
+// One elimination step of an r x r Pfaffian (r > 2): Gauss vectors and rank-2 update.
+double pf_step_flops(int r) { return 16.0 * tri_count(r - 2) + 6.0 * (r - 2); }
+}  // namespace
+
+double qcs_overlap_flops_nev(int n, int ne, int nev, bool overlap_kernel) {
     const int d = n - ne, m = 2 * n - ne;
     double f = 0.0;
-    f += 8.0 * 2.0 * (double)n * n * n;                       // T: n x 2n x n complex MACs
+    const double zeros = overlap_kernel ? tri_count(ne) + tri_count(d) : 0.0;  // skipped entries of Ut
+    f += 8.0 * 2.0 * (double)n * ((double)n * n - zeros);     // T: 2n columns x (n^2 - zeros) complex MACs
     f += 8.0 * 2.0 * (double)n * tri_count(ne);               // B occupied x occupied
     f += 4.0 * 2.0 * (double)n * ne * 2 * d;                  // B occupied x empty
     f += 2.0 * 2.0 * (double)n * tri_count(2 * d);            // B empty x empty
-    double node = 0.0;
-    for (int r = m; r > 2; r -= 2) node += 16.0 * tri_count(r - 2) + 6.0 * (r - 2);
-    f += node * nev;
+    if (overlap_kernel) {  // occupied block once, then each node's 2d x 2d complement
+        for (int r = m; r > 2 * d && r > 2; r -= 2) f += pf_step_flops(r);
+        double node = 0.0;
+        for (int r = 2 * d; r > 2; r -= 2) node += pf_step_flops(r);
+        f += node * nev;
+    } else {
+        double node = 0.0;
+        for (int r = m; r > 2; r -= 2) node += pf_step_flops(r);
+        f += node * nev;
+    }
     return f;
 }
 

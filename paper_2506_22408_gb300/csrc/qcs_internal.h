@@ -76,10 +76,14 @@ struct qcs_node_plan {
 };
 
 qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node_plan *plan);
-double qcs_overlap_flops_nev(int n, int ne, int nev);  // algorithmic FP64 flops per parity +1 pair
+// algorithmic FP64 flops per parity +1 pair.  overlap_kernel: as the overlap kernels
+// compute it (the congruence skips the zeros of the echelon-form walker rows; the
+// occupied block is eliminated once for all nodes); otherwise a dense congruence and a
+// full elimination per node, as the adjoint and local-energy kernels compute it.
+double qcs_overlap_flops_nev(int n, int ne, int nev, bool overlap_kernel = false);
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr);
+                                  cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr, bool echelon = false);
 
 struct qcs_grad_launch {
     int n, ne;

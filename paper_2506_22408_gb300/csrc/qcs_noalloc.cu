@@ -115,7 +115,7 @@ extern "C" qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double
 
     r = qcs_launch_snapshot_build(&ctx, &s, d_Q, d_b, st);
     if (r != QCS_OK) return r;
-    r = qcs_launch_walker_prep(&ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st);
+    r = qcs_launch_walker_prep(&ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st, nullptr, nullptr, true);
     if (r != QCS_OK) return r;
     qcs_pair_launch L;
     L.n = n;

@@ -40,7 +40,7 @@ struct PairArgs {
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
     int ut_bytes;     // shared bytes of the walker rows Ut (per block)
-    int off_R, off_B, off_U, off_V, off_pf, off_inv, off_best, off_int, off_act, off_pv;  // byte offsets in a warp region
+    int off_R, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // byte offsets in a warp region
     const cd *Ut;
     const cd *pref;
     const cd *Qt;
@@ -69,7 +69,6 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
     cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
     cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
-    unsigned long long *best = reinterpret_cast<unsigned long long *>(wbase + A.off_best);
     int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = reinterpret_cast<uint8_t *>(wbase + A.off_act);
     uint8_t *act1 = act0 + A.NB * A.m;
@@ -100,21 +99,26 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             } else {
                 load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
                 __syncwarp();
-                build_T(n, Uts, Qs, Ts, lane);
+                build_T_echelon(n, A.ne, Uts, Qs, Ts, lane);  // walker rows in echelon form
             }
             __syncwarp();
             build_B(A.n, A.ne, Ts, Bs, tab, lane);
             __syncwarp();
+            // occupied block eliminated once for all nodes when that is stable
+            cd pf0;
+            const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
+            const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
             cd S = cmk(0.0, 0.0);
             for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
                 int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                node_pfaffians(A.m, A.ne, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, best, ints, act0, act1, tab, pv,
+                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
                     for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
                 __syncwarp();
             }
             if (lane == 0) {
+                if (shared) S = cmul(S, pf0);
                 if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
                 acc = cadd(acc, S);
                 if (A.per_pair) A.per_pair[w * A.P + q] = cmul(prefw, S);
@@ -198,8 +202,6 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_inv = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_best = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(unsigned long long));
     A.off_int = (int)o;
     o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
@@ -287,7 +289,7 @@ qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launc
     double cost[QCS_MAX_SYSTEMS];
     for (int i = 0; i < nsys; ++i) {
         order[i] = i;
-        cost[i] = qcs_overlap_flops_nev(Ls[i].n, Ls[i].ne, Ls[i].plan.nev) *
+        cost[i] = qcs_overlap_flops_nev(Ls[i].n, Ls[i].ne, Ls[i].plan.nev, true) *
                   (double)Ls[i].chunk;
     }
     for (int i = 0; i < nsys; ++i)

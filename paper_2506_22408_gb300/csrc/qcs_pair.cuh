@@ -37,6 +37,26 @@ __device__ inline void build_T(int n, const cd *__restrict__ Uts, const cd *__re
     }
 }
 
+// T from walker rows in echelon form (see qcs_walker.cu): row j < ne of Ut is zero in
+// columns k < j, row ne + j' zero in columns [ne, ne + j'); those products are skipped.
+// With 2n = 32 every warp pass covers one row, so the loop bounds are warp-uniform.
+__device__ inline void build_T_echelon(int n, int ne, const cd *__restrict__ Uts, const cd *__restrict__ Qs,
+                                       cd *__restrict__ Ts, int lane, int nthr = 32) {
+    const int n2 = 2 * n, lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
+    for (int e = lane; e < n * n2; e += nthr) {
+        const int j = e / n2, c = e - j * n2;
+        const cd *ur = Uts + j * lu, *qr = Qs + c * lq;
+        cd s = cmk(0.0, 0.0);
+        if (j < ne) {
+            for (int k = j; k < n; ++k) cfma(s, ur[k], qr[k]);
+        } else {
+            for (int k = 0; k < ne; ++k) cfma(s, ur[k], qr[k]);
+            for (int k = j; k < n; ++k) cfma(s, ur[k], qr[k]);  // j = ne + j'
+        }
+        Ts[j * lt + c] = s;
+    }
+}
+
 // x * ph for a phase code ph = 0..3 (1, i, -1, -i): a swap of the parts and sign
 // flips of the bit patterns, no floating-point arithmetic.
 __device__ __forceinline__ cd mul_phase(cd x, unsigned ph) {
@@ -129,14 +149,117 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
 }
 
 
+// Elimination of the occupied block, shared by every node matrix.  The node matrices
+// B + w D differ only in their empty x empty block (D pairs the empty modes), so
+// eliminating the ne occupied indices first is the same for all of them:
+// pf(B + w D) = pf0 pf(S + w D_ee), S the Schur complement of the occupied block.
+// Pivots are taken inside the occupied block (its largest active entry, ties to the
+// first pair in packed order); a pivot pair at positions ak < ap of the active list
+// contributes (-1)^(ak+ap-1) A_kp, the sign of moving k and p to the front.  Works on a
+// copy of B in Ns.  Returns false, with Bs untouched, when a pivot is zero or the
+// largest entry of S exceeds 2^5 times the largest entry of B (the caller then
+// eliminates each node matrix in full); on success Bs holds S, packed upper 2d x 2d.
+__device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__restrict__ Ns,
+                                      cd *__restrict__ Uv, cd *__restrict__ Vv, uint8_t *__restrict__ act0,
+                                      uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab, cd &pf0,
+                                      int lane) {
+    const int T = tri_count(m);
+    unsigned kb = 0u;
+    for (int e = lane; e < T; e += 32) {
+        const cd x = Bs[e];
+        Ns[e] = x;
+        const unsigned k = pivot_key(x);
+        kb = k > kb ? k : kb;
+    }
+    for (int a = lane; a < m; a += 32) act0[a] = (uint8_t)a;
+    kb = __reduce_max_sync(QCS_FULL, kb);
+    __syncwarp();
+    pf0 = cmk(1.0, 0.0);
+    uint8_t *cur = act0, *nxt = act1;
+    for (int s = 0, r = m; s < ne / 2; ++s, r -= 2) {
+        const int ro = ne - 2 * s;  // the active occupied indices sit at positions 0 .. ro-1
+        unsigned long long bk = 0ull;
+        for (int t = lane; t < tri_count(ro); t += 32) {
+            int a, b;
+            pair_of(tab, t, a, b);
+            const unsigned key = pivot_key(Ns[tri_index(cur[a], cur[b])]);
+            const unsigned long long c = ((unsigned long long)key << 32) | (unsigned long long)(0xffffffffu - (unsigned)t);
+            bk = c > bk ? c : bk;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+            bk = ob > bk ? ob : bk;
+        }
+        if ((bk >> 32) == 0ull) return false;  // the active occupied block is zero
+        int ak, ap;
+        pair_of(tab, (int)(0xffffffffu - (unsigned)(bk & 0xffffffffull)), ak, ap);
+        const int k = cur[ak], p = cur[ap];
+        const cd piv = Ns[tri_index(k, p)];
+        pf0 = cmul(pf0, flip_if(piv, ((ak + ap - 1) & 1) != 0));
+        if (r == 2) break;  // no empty modes: the last pivot closes the Pfaffian
+        const cd iv = cinv(piv);
+        const int rv = r - 2;
+        for (int a2 = lane; a2 < rv; a2 += 32) {
+            int a = a2;
+            if (a >= ak) ++a;
+            if (a >= ap) ++a;
+            const int i = cur[a];
+            const cd aik = i < k ? Ns[tri_index(i, k)] : cneg(Ns[tri_index(k, i)]);  // A_{i,k}
+            const cd aip = i < p ? Ns[tri_index(i, p)] : cneg(Ns[tri_index(p, i)]);  // A_{i,p}
+            Uv[a2] = cmul(aik, iv);
+            Vv[a2] = aip;
+            nxt[a2] = (uint8_t)i;
+        }
+        __syncwarp();
+        // A_ij -= u_i v_j - v_i u_j with u = A_{.,k}/A_kp, v = A_{.,p}
+        const int Tr = tri_count(rv);
+        for (int t = lane; t < Tr; t += 32) {
+            int a, b;
+            pair_of(tab, t, a, b);
+            cd *x = Ns + tri_index(nxt[a], nxt[b]);
+            cd y = *x;
+            cfms(y, Uv[a], Vv[b]);
+            cfma(y, Vv[a], Uv[b]);
+            *x = y;
+        }
+        __syncwarp();
+        uint8_t *tt = cur;
+        cur = nxt;
+        nxt = tt;
+    }
+    // the active list is now the empty indices ne .. m-1 in order
+    const int T2 = tri_count(m - ne);
+    unsigned ks = 0u;
+    for (int t = lane; t < T2; t += 32) {
+        int a, b;
+        pair_of(tab, t, a, b);
+        const unsigned k = pivot_key(Ns[tri_index(ne + a, ne + b)]);
+        ks = k > ks ? k : ks;
+    }
+    ks = __reduce_max_sync(QCS_FULL, ks);
+    if (ks > kb + (5u << 20)) return false;  // keys order like |x|; +5 in the exponent field is x 2^5
+    for (int t = lane; t < T2; t += 32) {
+        int a, b;
+        pair_of(tab, t, a, b);
+        Bs[t] = Ns[tri_index(ne + a, ne + b)];
+    }
+    __syncwarp();
+    return true;
+}
+
 // Pfaffians of nb node matrices B + wnode[v] D held in Ns (packed upper), m x m with
-// ne occupied rows first.  On return pf[v] holds pf(B + wnode[v] D).
+// ne occupied rows first.  On return pf[v] holds pf(B + wnode[v] D); m = 0 gives 1.
 __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnode, int nb,
                                       const cd *__restrict__ Bs, cd *__restrict__ Ns,
                                cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ inv,
-                               unsigned long long *__restrict__ best, int *__restrict__ ints,
+                               int *__restrict__ ints,
                                uint8_t *__restrict__ act0, uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
                                cd *__restrict__ pv, int lane) {
+    if (m == 0) {
+        if (lane < nb) pf[lane] = cmk(1.0, 0.0);
+        __syncwarp();
+        return;
+    }
     const int S = m / 2;  // elimination steps; the signed pivots of node v go to pv[v*S + s]
     const int d = (m - ne) / 2;
     const int T = tri_count(m);
@@ -185,7 +308,7 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
             int k = cur[lane * m], p = cur[lane * m + a];
             cd piv = Ns[lane * T + tri_index(k, p)];
             pv[lane * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
-            inv[lane] = cinv(piv);
+            if (r > 2) inv[lane] = cinv(piv);  // the last step has no Gauss vectors
             pos[lane] = a;
             kk[lane] = k;
             pp[lane] = p;

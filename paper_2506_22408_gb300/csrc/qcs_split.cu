@@ -84,7 +84,7 @@ struct SplitArgs {
     int64_t ngroups;             // walker groups of kWalkersPerTile
     int region_bytes;            // operand / workspace union
     int warp_bytes;
-    int off_T, off_B, off_U, off_V, off_pf, off_inv, off_best, off_int, off_act, off_pv;
+    int off_T, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;
     const float *Mhi, *Mlo;      // walker slabs
     const float *Nhi, *Nlo;      // snapshot slabs
     const cd *pref;
@@ -190,7 +190,6 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
     cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
     cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
-    unsigned long long *best = reinterpret_cast<unsigned long long *>(wbase + A.off_best);
     int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = wbase + A.off_act;
     uint8_t *act1 = act0 + A.NB * A.m;
@@ -297,16 +296,21 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
             if (w >= A.W) continue;
             build_B_f32(n, A.ne, Ts, ldT, Bs, tab, lane);
             __syncwarp();
+            // occupied block eliminated once for all nodes when that is stable
+            cd pf0;
+            const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
+            const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
             cd S = cmk(0.0, 0.0);
             for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
                 const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                node_pfaffians(A.m, A.ne, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, best, ints, act0, act1, tab, pv,
+                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
                     for (int vv = 0; vv < nb; ++vv) cfma(S, A.gamma[k0 + vv], pf[vv]);
                 __syncwarp();
             }
             if (lane == 0) {
+                if (shared) S = cmul(S, pf0);
                 if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
                 acc = cadd(acc, S);
                 if (A.per_pair) {
@@ -346,8 +350,6 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_inv = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_best = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(unsigned long long));
     A.off_int = (int)o;
     o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;

@@ -11,12 +11,20 @@
 //              occupied mode contributes conj(V_jk)/sqrt2 = U_kj/sqrt2;
 //   pref     = 2 det(R) i^{ne/2} / 2^{n - ne/2}  (prefactor of the estimator;
 //              the 2 undoes the 1/sqrt2 of the prepared state (|0>+|Psi_T>)/sqrt2).
+//
+// Echelon form (echelon = true, for the overlap kernels): the estimator is linear and
+// alternating in the occupied orbitals, o_p(U_occ W) = det(W) o_p(U_occ), and does not
+// depend on which orthonormal basis completes them.  Column reflections (det -1
+// each) therefore bring the top ne x ne block of U_occ and the bottom d x d block of
+// the completion to lower-triangular form, det R taking the reflections' sign:
+// row j < ne of Ut is then zero in columns k < j, row ne + j' zero in columns
+// [ne, ne + j'), ne(ne-1)/2 + d(d-1)/2 exact zeros that the congruence skips.
 #include "qcs_internal.h"
 
 namespace {
 
 __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restrict__ Phi, cd *__restrict__ Ut,
-                                   cd *__restrict__ pref, cd *__restrict__ Uout, cd *__restrict__ Rout,
+                                   cd *__restrict__ pref, cd *__restrict__ Uout, cd *__restrict__ Rout, int echelon,
                                    unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -72,6 +80,38 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
             __syncwarp();
             detR = cmul(detR, alpha);
         }
+        if (echelon) {
+            int nref = 0;  // reflections on the occupied columns (det -1 each)
+            for (int blk = 0; blk < 2; ++blk) {
+                const int c0 = blk == 0 ? 0 : ne, c1 = blk == 0 ? ne : n;
+                for (int r = 0; r + 1 < c1 - c0; ++r) {
+                    const int row = c0 + r, cs = c0 + r;  // zero U[row][cs+1 .. c1-1]
+                    const cd y = (lane >= cs && lane < c1) ? cconj(U[row * n + lane]) : cmk(0.0, 0.0);
+                    const double tail = warp_sum(lane > cs && lane < c1 ? fma(y.x, y.x, y.y * y.y) : 0.0);
+                    if (!(tail > 0.0)) continue;  // the row is already in echelon form
+                    const cd y0 = cconj(U[row * n + cs]);
+                    const double yn = sqrt(tail + fma(y0.x, y0.x, y0.y * y0.y));
+                    const double a0 = hypot(y0.x, y0.y);
+                    const cd ph = a0 > 0.0 ? cmk(y0.x / a0, y0.y / a0) : cmk(1.0, 0.0);
+                    const cd alpha = cmk(-ph.x * yn, -ph.y * yn);
+                    const cd vi = (lane == cs) ? csub(y0, alpha) : y;  // v = y - alpha e_cs
+                    const double tau = 2.0 / warp_sum(fma(vi.x, vi.x, vi.y * vi.y));
+                    if (lane < n) v[lane] = vi;
+                    __syncwarp();
+                    if (lane < n) {  // U <- U (I - tau v v^H) on columns cs .. c1-1: row = lane
+                        cd sr = cmk(0.0, 0.0);
+                        for (int c = cs; c < c1; ++c) cfma(sr, U[lane * n + c], v[c]);
+                        sr = cscale(sr, tau);
+                        for (int c = cs; c < c1; ++c) cfms(U[lane * n + c], sr, cconj(v[c]));
+                    }
+                    __syncwarp();
+                    if (lane > cs && lane < c1) U[row * n + lane] = cmk(0.0, 0.0);  // exact zeros
+                    __syncwarp();
+                    if (blk == 0) ++nref;
+                }
+            }
+            if (nref & 1) detR = cneg(detR);  // det R' = conj(det W) det R, det W = (-1)^nref
+        }
         const double rs2 = 0.70710678118654752440;
         cd *Uw = Ut + w * n * n;
         for (int e = lane; e < n * n; e += 32) {
@@ -105,7 +145,7 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
 }  // namespace
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st, cd *Uout, cd *Rout) {
+                                  cudaStream_t st, cd *Uout, cd *Rout, bool echelon) {
     if (W == 0) return QCS_OK;
     const int wpb = 4;
     size_t smem = (size_t)wpb * ((size_t)n * ne + (size_t)n * n + n) * sizeof(cd);
@@ -113,6 +153,6 @@ qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const 
     int64_t blocks = (W + wpb - 1) / wpb;
     if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
     walker_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, ne, W, walkers, Ut, pref, Uout, Rout,
-                                                                   ctx->d_status);
+                                                                   echelon ? 1 : 0, ctx->d_status);
     return qcs_check_launch(ctx, "walker_prep_kernel");
 }

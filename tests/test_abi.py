@@ -30,5 +30,21 @@ def test_flop_accounting_host_only():
     f16 = lib.qcs_overlap_flops_per_pair(16, 8, 0, 0)       # Gauss plan: 3 Pfaffians
     f16_dft = lib.qcs_overlap_flops_per_pair(16, 8, 0, 2)   # 5 of 9 roots of unity
     f16_all = lib.qcs_overlap_flops_per_pair(16, 8, 0, 1)   # all 9 roots
-    assert 1.2e5 < f16 < f16_dft < f16_all < 3.0e5
+    assert 0.9e5 < f16 < f16_dft < f16_all < 3.0e5
+
+    def tri(k):
+        return k * (k - 1) // 2
+
+    def step(r):  # one elimination step of an r x r Pfaffian: Gauss vectors + rank-2 update
+        return 16 * tri(r - 2) + 6 * (r - 2)
+
+    n, ne = 16, 8
+    d, m = n - ne, 2 * n - ne
+    t_echelon = 16 * n * (n * n - tri(ne) - tri(d))
+    b_flops = 16 * n * tri(ne) + 8 * n * ne * 2 * d + 4 * n * tri(2 * d)
+    shared = sum(step(r) for r in range(m, 2 * d, -2))
+    node = sum(step(r) for r in range(2 * d, 2, -2))
+    assert f16 == t_echelon + b_flops + shared + 3 * node
+    assert f16_dft == t_echelon + b_flops + shared + 5 * node
+    assert lib.qcs_overlap_flops_per_pair_signed_perm(16, 8, 0, 0) == b_flops + shared + 3 * node
     assert lib.qcs_overlap_flops_per_pair(16, 7, 0, 0) == 0.0  # odd ne rejected

@@ -150,6 +150,35 @@ def test_degenerate_inputs(ctx):
     assert np.all(parf == -1) and ovf[0] == 0 and np.all(ppf == 0)
 
 
+@pytest.mark.parametrize("n,ne", [(16, 8), (8, 8), (9, 2), (12, 6)])
+def test_structured_walkers(ctx, n, ne):
+    """Walkers whose orbital matrix is already in echelon form, is a reversed unit basis
+    (zero leading entries), lives on the last modes only, or has a zero top-left entry:
+    the column reflections that bring the walker rows to echelon form meet each of
+    their special cases (nothing to zero, a zero pivot, a zero row)."""
+    rng = np.random.default_rng(n * 31 + ne)
+    Q = synth.haar_orthogonal(rng, 2 * n, 24)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 6)
+    eye = np.eye(n, dtype=complex)
+    R = np.triu(rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne))) + 2 * np.eye(ne)
+    Phi[0] = eye[:, :ne] @ R                        # echelon already
+    Phi[1] = eye[:, ne - 1::-1]                     # reversed unit basis
+    Phi[2] = eye[:, n - ne:] @ R                    # only the last ne modes
+    Phi[3][0, :] = 0                                # zero first row
+    Phi[4][:, 0] = 0                                # zero first column: overlap exactly 0
+    Phi[4][0, 1] = 0
+    ov, pp, par, st = run_gpu(ctx, dict(Phi=Phi, Q=Q, b=b))
+    assert st == 0
+    oo, opp, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    live = [0, 1, 2, 5] + ([3] if ne < n else [])  # with ne = n a zero row makes the walker singular
+    check_pairs(pp[live], opp[live], sc[live], par)
+    check_walkers(ov[live], oo[live], sc[live])
+    assert np.all(pp[4] == 0) and ov[4] == 0
+    if ne == n:
+        assert abs(ov[3]) <= 1e-12 * sc[0].mean()
+
+
 def test_argument_errors(ctx):
     n = 6
     Q = torch.from_numpy(synth.haar_orthogonal(np.random.default_rng(0), 2 * n, 4)).cuda()
