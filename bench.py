@@ -391,10 +391,7 @@ def run_precision(args, ctx, dev, barrier, ws):
     rel_pair = ((p32 - p64).abs() / mag).flatten()
     rel_walker = ((o32 - o64).abs() / mag.flatten())
     n, ne = wl.n, wl.ne
-    dd = n - ne
-    f_T = 16.0 * n * (n * n - ne * (ne - 1) / 2 - dd * (dd - 1) / 2)  # echelon walker rows skip their zeros
-    f_B = 16.0 * n * ne * (ne - 1) / 2 + 16.0 * n * ne * dd + 4.0 * n * (2 * dd) * (2 * dd - 1) / 2
-    f_pf = qcs.flops_per_pair(n, ne) - f_T - f_B  # FP64 work that stays on the FP64 pipe
+    f_pf = qcs.flops_breakdown(n, ne)["pfaffian"]  # FP64 work that stays on the FP64 pipe
     avg = kms / max(kl, 1)
     ach = f_pf * npar * wl.W / (avg * 1e-3) / 1e12
     ngroups = (wl.W + 3) // 4

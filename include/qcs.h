@@ -211,7 +211,8 @@ qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, 
  *   d_L       : nchol x n x n complex (device), Lhat_gamma = sum_pq L[gamma][p][q] a_p^dag a_q
  *   d_h       : n x n complex (device) or NULL (then e1 is not computed)
  *   d_overlap, d_e1, d_e2 : W complex each, or NULL
- * Same node options as qcs_overlap; FP64 only.
+ * Same node options as qcs_overlap; FP64 only.  An exactly singular node matrix
+ * raises QCS_ERR_SINGULAR (device status), as in qcs_overlap_grad.
  * Errors: QCS_ERR_ARG, QCS_ERR_UNSUPPORTED (precision, shared memory), QCS_ERR_CUDA. */
 qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                             int nchol, const double *d_L, const double *d_h, double *d_overlap, double *d_e1,
@@ -306,7 +307,11 @@ qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_system *systems
  * recomputed per node (never stored), then chained through the congruence
  * of Eq. (b_mat) and the QR of the walker.  Same options as qcs_overlap
  * (precision must be QCS_FP64).  QCS_ERR_SINGULAR is raised when some
- * A(z_k) is singular. */
+ * A(z_k) is exactly singular (a pivot row of zeros, which structured inputs
+ * such as unit-vector walkers with signed-permutation snapshots produce): the
+ * formula needs A(z_k)^{-1}, and that node's term is then left out of the
+ * gradient (the overlap itself stays exact).  Nearly singular node matrices
+ * need no special case. */
 qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                             double *d_overlap, double *d_grad, const qcs_opts *opts, void *stream);
 
@@ -394,6 +399,14 @@ double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
 /* The same count for a pair whose snapshot is a signed permutation (no FP64
  * work in the congruence). */
 double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags);
+
+/* Host only: the parts of qcs_overlap_flops_per_pair, parts[0] the congruence T,
+ * parts[1] the covariance B^(s), parts[2] the Pfaffian eliminations (the shared
+ * occupied steps and the node complements).  At n = 16 the congruence takes three
+ * real products per complex multiply-add (counted as executed: 6 flop, plus the
+ * sums that form the two results and the snapshot row's re + im); elsewhere four
+ * (8 flop).  parts: host array of 3 doubles.  Errors: QCS_ERR_ARG. */
+qcs_status qcs_overlap_flops_breakdown(int n, int ne, int nodes, unsigned flags, double *parts);
 
 /* Host only (no device work): the node plan that (n, ne, nodes, flags) selects.
  * *nev receives the number of Pfaffians evaluated per pair; wnode and gamma

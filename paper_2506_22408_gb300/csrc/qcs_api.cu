@@ -579,15 +579,22 @@ extern "C" qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int
 
 // ------------------------------------------------------------ accounting
 
+static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, double *part);
+
 extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
     qcs_node_plan plan;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
-    const int d = n - ne, m = 2 * n - ne, T = tri_count(m);
-    double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);    // forward pass (dense T)
-    double node = 0.0;                                              // backward inverse per node
-    for (int r = m; r > 2; r -= 2) node += 16.0 * (double)(r - 2) * (r - 2) + 8.0 * (r - 2) + 12.0 * (r - 2);
-    f += (node + 8.0 * T) * plan.nev;                               // inverse + Y accumulation
+    const int d = n - ne, m = 2 * n - ne;
+    // forward: dense T, B, the occupied block once, each node's 2d x 2d complement
+    double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);
+    f -= (double)(plan.nev - 1) * qcs_pf_elim_flops(m, 2 * d);  // the occupied steps once, not per node
+    // backward step with rv later indices: g1, g2 (12 rv), Z g1 and Z g2 (16 rv^2), corner (8 rv)
+    auto bstep = [](int rv) { return 16.0 * rv * rv + 20.0 * rv; };
+    double node = 0.0;                                              // each node's complement inverse
+    for (int rv = 2 * d - 2; rv > 0; rv -= 2) node += bstep(rv);
+    f += (node + 8.0 * tri_count(2 * d)) * plan.nev;                // + the weighted sum of the Z_k
+    for (int rv = 2 * d; rv <= m - 2; rv += 2) f += bstep(rv);      // backward over the shared steps
     f += (double)m * 2 * n * (8.0 * ne + 4.0 * (m - ne));           // G_X = Y (X J)
     f += (double)n * n * 2 * n * 8.0 + 2.0 * d * 2 * n;             // Gamma1 / Gamma2
     return f;
@@ -597,8 +604,9 @@ extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int node
     qcs_node_plan plan;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
-    const double t_flops = 16.0 * (double)n * ((double)n * n - tri_count(ne) - tri_count(n - ne));
-    return qcs_overlap_flops_nev(n, ne, plan.nev, true) - t_flops;  // T is a gather
+    double part[3];
+    overlap_flops_parts(n, ne, plan.nev, true, part);
+    return part[1] + part[2];  // T is a gather
 }
 
 extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
@@ -620,25 +628,51 @@ namespace {
 double pf_step_flops(int r) { return 16.0 * tri_count(r - 2) + 6.0 * (r - 2); }
 }  // namespace
 
-double qcs_overlap_flops_nev(int n, int ne, int nev, bool overlap_kernel) {
-    const int d = n - ne, m = 2 * n - ne;
+// Elimination steps of an m x m Pfaffian from r = m down to r > stop.
+double qcs_pf_elim_flops(int m, int stop) {
     double f = 0.0;
-    const double zeros = overlap_kernel ? tri_count(ne) + tri_count(d) : 0.0;  // skipped entries of Ut
-    f += 8.0 * 2.0 * (double)n * ((double)n * n - zeros);     // T: 2n columns x (n^2 - zeros) complex MACs
-    f += 8.0 * 2.0 * (double)n * tri_count(ne);               // B occupied x occupied
-    f += 4.0 * 2.0 * (double)n * ne * 2 * d;                  // B occupied x empty
-    f += 2.0 * 2.0 * (double)n * tri_count(2 * d);            // B empty x empty
-    if (overlap_kernel) {  // occupied block once, then each node's 2d x 2d complement
-        for (int r = m; r > 2 * d && r > 2; r -= 2) f += pf_step_flops(r);
-        double node = 0.0;
-        for (int r = 2 * d; r > 2; r -= 2) node += pf_step_flops(r);
-        f += node * nev;
-    } else {
-        double node = 0.0;
-        for (int r = m; r > 2; r -= 2) node += pf_step_flops(r);
-        f += node * nev;
-    }
+    for (int r = m; r > stop && r > 2; r -= 2) f += pf_step_flops(r);
     return f;
+}
+
+// Parts of the count: [0] congruence T, [1] covariance B, [2] Pfaffian eliminations.
+static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, double *part) {
+    const int d = n - ne, m = 2 * n - ne;
+    const double zeros = overlap_kernel ? tri_count(ne) + tri_count(d) : 0.0;  // skipped entries of Ut
+    const double macs = 2.0 * n * ((double)n * n - zeros);   // complex multiply-adds of T
+    if (overlap_kernel && n == 16)
+        // three real products per complex multiply-add, then Re = p1 - p2 and
+        // Im = p3 - p1 - p2 per entry and re + im of each snapshot entry
+        part[0] = 6.0 * macs + 3.0 * 2.0 * n * n + 2.0 * n * n;
+    else
+        part[0] = 8.0 * macs;
+    part[1] = 8.0 * 2.0 * (double)n * tri_count(ne)          // occupied x occupied
+              + 4.0 * 2.0 * (double)n * ne * 2 * d             // occupied x empty
+              + 2.0 * 2.0 * (double)n * tri_count(2 * d);      // empty x empty
+    double node = 0.0;
+    if (overlap_kernel) {  // occupied block once, then each node's 2d x 2d complement
+        part[2] = qcs_pf_elim_flops(m, 2 * d);
+        for (int r = 2 * d; r > 2; r -= 2) node += pf_step_flops(r);
+    } else {
+        part[2] = 0.0;
+        for (int r = m; r > 2; r -= 2) node += pf_step_flops(r);
+    }
+    part[2] += node * nev;
+}
+
+double qcs_overlap_flops_nev(int n, int ne, int nev, bool overlap_kernel) {
+    double part[3];
+    overlap_flops_parts(n, ne, nev, overlap_kernel, part);
+    return part[0] + part[1] + part[2];
+}
+
+extern "C" qcs_status qcs_overlap_flops_breakdown(int n, int ne, int nodes, unsigned flags, double *parts) {
+    qcs_node_plan plan;
+    if (!parts || n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return QCS_ERR_ARG;
+    qcs_status r = qcs_make_node_plan(n, ne, nodes, flags, &plan);
+    if (r != QCS_OK) return r;
+    overlap_flops_parts(n, ne, plan.nev, true, parts);
+    return QCS_OK;
 }
 
 extern "C" qcs_status qcs_node_plan_get(int n, int ne, int nodes, unsigned flags, int *nev, double *wnode,

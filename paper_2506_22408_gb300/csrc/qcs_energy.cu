@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                 cd Sop = cmk(0.0, 0.0), S1p = cmk(0.0, 0.0), S2p = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
                     const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                    node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar);
+                    node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar, A.status);
                     node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
                     if (k0 == 0)  // B has been copied into the node matrices; Sacc may share its storage
                         for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);

@@ -26,7 +26,12 @@
 //     (A^{-1})_{rest,k} = -Z g1,  (A^{-1})_{rest,p} = -Z g2,
 //     (A^{-1})_{k,p} = -1/a + g1^T Z g2,  g1 = v/a, g2 = -u/a,
 // where Z is the inverse of the step's Schur complement and (u, v, a) the
-// step's pivot columns and pivot.
+// step's pivot columns and pivot.  The node matrices share their occupied block, so
+// its steps are taken once per pair (shared_factor); each node then factors and
+// inverts only its 2d x 2d complement, and since every backward step is affine in Z,
+// one backward pass over the shared steps, started from sum_k c_k Z_k, gives
+// Y_p = sum_k c_k A'_k^{-1} (shared_inverse).  Pairs whose occupied block would grow
+// the complement beyond 2^5 of max|B| take the full elimination per node.
 #include "qcs_internal.h"
 #include "qcs_group.cuh"
 
@@ -38,7 +43,7 @@ struct GradArgs {
     int64_t W, P;
     int group_bytes, tab_bytes;
     int off_Q, off_T, off_B, off_Y, off_G, off_NZ, off_g1, off_g2, off_y1, off_y2, off_pf, off_cf, off_invh,
-        off_int, off_tile, off_acth, off_kh, off_ph, off_kc;
+        off_int, off_tile, off_acth, off_kh, off_ph, off_kc, off_sacth, off_skh, off_sph, off_sinvh, off_scr;
     const cd *Ut;
     const cd *Qt;
     const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
@@ -86,6 +91,11 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
     uint8_t *kh = wb + A.off_kh;
     uint8_t *ph = wb + A.off_ph;
     uint8_t *kc = wb + A.off_kc;  // signed-permutation snapshots: the two rows of each column of Qt
+    uint8_t *sacth = wb + A.off_sacth;  // history of the shared occupied-block elimination
+    uint8_t *skh = wb + A.off_skh;
+    uint8_t *sph = wb + A.off_sph;
+    cd *sinvh = reinterpret_cast<cd *>(wb + A.off_sinvh);
+    SharedScratch *scr = reinterpret_cast<SharedScratch *>(wb + A.off_scr);
 
     const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
     const int64_t ntiles = A.W * A.nchunks;
@@ -121,7 +131,6 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                 } else {
                     load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
                 }
-                for (int e = t; e < T; e += kGroup) Ys[e] = cmk(0.0, 0.0);
                 group_sync(bar);
                 if (sp) build_T_gather(n, Uts, gq, Ts, t, kGroup);
                 else build_T(n, Uts, Qs, Ts, t, kGroup);
@@ -129,20 +138,60 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                 build_B(n, ne, Ts, Bs, tab, t, kGroup);
                 group_sync(bar);
                 cd S = cmk(0.0, 0.0);
-                for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
-                    const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                    node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar);
-                    node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
-                    if (t < nb) cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
-                    if (t == 0)
-                        for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
-                    group_sync(bar);
-                    for (int e = t; e < T; e += kGroup) {
-                        cd y = Ys[e];
-                        for (int v = 0; v < nb; ++v) cfma(y, cf[v], Ns[v * T + e]);
-                        Ys[e] = y;
+                // Y = (1/2) sum_k gamma_k pf_k A_k^{-1}: block form when the occupied block
+                // eliminates stably (shared_factor), else every node matrix in full
+                if (shared_factor(m, ne, Bs, Ys, g1v, g2v, sinvh, sacth, skh, sph, scr, tab, t, bar)) {
+                    const int md = m - ne, Tn = tri_count(md);
+                    const cd pf0 = scr->pf0;
+                    for (int e = t; e < Tn; e += kGroup) {  // S0 to Bs; Zc accumulates in its place
+                        int a, b;
+                        pair_of(tab, e, a, b);
+                        cd *y = Ys + tri_index(ne + a, ne + b);
+                        Bs[e] = *y;
+                        *y = cmk(0.0, 0.0);
                     }
                     group_sync(bar);
+                    cd csum = cmk(0.0, 0.0);
+                    for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                        const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                        node_factor(md, 0, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t,
+                                    bar, A.status);
+                        node_inverse(md, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                        if (t < nb) cf[t] = cscale(cmul(A.gamma[k0 + t], cmul(pf0, pf[t])), 0.5);
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], cmul(pf0, pf[v]));
+                        group_sync(bar);
+                        for (int v = 0; v < nb; ++v) csum = cadd(csum, cf[v]);
+                        for (int e = t; e < Tn; e += kGroup) {
+                            int a, b;
+                            pair_of(tab, e, a, b);
+                            cd *yp = Ys + tri_index(ne + a, ne + b);
+                            cd y = *yp;
+                            for (int v = 0; v < nb; ++v) cfma(y, cf[v], Ns[v * Tn + e]);
+                            *yp = y;
+                        }
+                        group_sync(bar);
+                    }
+                    shared_inverse(m, ne, Ys, g1v, g2v, y1v, y2v, sinvh, sacth, skh, sph, csum, scr, t, bar);
+                } else {
+                    for (int e = t; e < T; e += kGroup) Ys[e] = cmk(0.0, 0.0);
+                    group_sync(bar);
+                    for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                        const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                        node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t,
+                                    bar, A.status);
+                        node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                        if (t < nb) cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
+                        group_sync(bar);
+                        for (int e = t; e < T; e += kGroup) {
+                            cd y = Ys[e];
+                            for (int v = 0; v < nb; ++v) cfma(y, cf[v], Ns[v * T + e]);
+                            Ys[e] = y;
+                        }
+                        group_sync(bar);
+                    }
                 }
                 if (t == 0) {
                     if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
@@ -392,6 +441,16 @@ size_t grad_group_layout(GradArgs &A) {
     o = align16(o + (size_t)NB * S);
     A.off_kc = (int)o;
     o = align16(o + (size_t)2 * n);
+    A.off_sacth = (int)o;
+    o = align16(o + (size_t)(A.ne / 2 + 1) * m);
+    A.off_skh = (int)o;
+    o = align16(o + (size_t)A.ne / 2);
+    A.off_sph = (int)o;
+    o = align16(o + (size_t)A.ne / 2);
+    A.off_sinvh = (int)o;
+    o = align16(o + (size_t)(A.ne / 2) * sizeof(cd));
+    A.off_scr = (int)o;
+    o = align16(o + sizeof(SharedScratch));
     return o;
 }
 

@@ -24,12 +24,15 @@ __device__ __forceinline__ cd skew_at(const cd *P, int i, int j) {
 // Forward Parlett-Reid elimination of nb node matrices B + wnode D (packed upper,
 // original index order) by the pair's 64 threads, keeping the step history (active
 // index lists, pivot rows and columns, pivot reciprocals) for the backward inverse.
-// pf[v] receives pf(B + wnode[v] D).
+// pf[v] receives pf(B + wnode[v] D).  An exactly singular node matrix (a pivot row
+// that is zero) has no inverse; it raises QCS_ERR_SINGULAR in *status, and its
+// contribution pf A^{-1} is taken as zero (the callers scale the inverse by pf = 0).
 __device__ inline void node_factor(int m, int ne, const cd *__restrict__ wnode, int nb, const cd *__restrict__ Bs,
                                    cd *__restrict__ Ns,
                             cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ invh,
                             int *__restrict__ pos, uint8_t *__restrict__ acth, uint8_t *__restrict__ kh,
-                            uint8_t *__restrict__ ph, const uint16_t *__restrict__ tab, int t, int bar) {
+                            uint8_t *__restrict__ ph, const uint16_t *__restrict__ tab, int t, int bar,
+                            unsigned *status) {
     const int d = (m - ne) / 2, T = tri_count(m), S = m / 2;
     const int hstride = (S + 1) * m;
     const int lane = t & 31;
@@ -74,6 +77,7 @@ __device__ inline void node_factor(int m, int ne, const cd *__restrict__ wnode, 
             }
             bk = __shfl_sync(QCS_FULL, bk, (lane < nb ? lane : 0) * seg);
             if (lane < nb) {
+                if ((bk >> 32) == 0ull) raise_status(status, QCS_ERR_SINGULAR);
                 const int a = 0xffff - (int)(bk & 0xffffull);
                 const int k = cur[lane * hstride], p = cur[lane * hstride + a];
                 const cd piv = Ns[lane * T + tri_index(k, p)];
@@ -181,4 +185,189 @@ __device__ inline void node_inverse(int m, int nb, cd *__restrict__ Ns, cd *__re
         }
         group_sync(bar);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Block form for the adjoint: the node matrices A_k = B + w_k D differ only in their
+// empty x empty block, so with the occupied block eliminated once (Schur complement
+// S0 on the empty indices) A_k = [[P, Boe], [-Boe^T, S0 + w_k D + ...]] and
+//     A_k^{-1} = F(Z_k),  Z_k = (S0 + w_k D)^{-1},
+// where F is the backward recursion over the occupied steps.  Every backward step is
+// affine in Z (new entries -Z g1, -Z g2 and -1/a + g1^T Z g2), so a weighted sum over
+// the nodes is one recursion: sum_k c_k A_k^{-1} = F_c(sum_k c_k Z_k) with the
+// constant -1/a of each step scaled by c = sum_k c_k.
+
+struct SharedScratch {  // per-group scalars exchanged between the two warps
+    unsigned key[2];
+    int flag, ak, ap, pad_;
+    cd pf0;
+};
+
+__device__ __forceinline__ cd skew_get(const cd *N, int i, int j) {  // A(i, j), i != j
+    return i < j ? N[tri_index(i, j)] : cneg(N[tri_index(j, i)]);
+}
+__device__ __forceinline__ void skew_put(cd *N, int i, int j, cd x) {  // A(i, j) = x, A(j, i) = -x
+    if (i < j) N[tri_index(i, j)] = x;
+    else N[tri_index(j, i)] = cneg(x);
+}
+
+// Forward elimination of the ne occupied indices of Ns (a copy of B, m x m packed) by
+// the pair's 64 threads; pivots: the largest entry of the active occupied block (ties
+// to the first pair in packed order), a pair at list positions ak < ap contributing
+// (-1)^(ak+ap-1) A_kp to pf0.  Keeps the step history (active lists acth, pivot
+// indices kh/ph, pivot reciprocals invh) for shared_inverse.  Returns false (the same
+// on every thread) when a pivot is zero or the complement's largest entry exceeds
+// 2^5 times that of B; on success the empty x empty block of Ns holds S0 and sc->pf0
+// the product of the signed pivots.
+__device__ inline bool shared_factor(int m, int ne, const cd *__restrict__ Bs, cd *__restrict__ Ns,
+                                     cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ invh,
+                                     uint8_t *__restrict__ acth, uint8_t *__restrict__ kh, uint8_t *__restrict__ ph,
+                                     SharedScratch *sc, const uint16_t *__restrict__ tab, int t, int bar) {
+    const int T = tri_count(m), S = ne / 2, lane = t & 31;
+    unsigned kb = 0u;
+    for (int e = t; e < T; e += kGroup) {
+        const cd x = Bs[e];
+        Ns[e] = x;
+        const unsigned k = pivot_key(x);
+        kb = k > kb ? k : kb;
+    }
+    for (int a = t; a < m; a += kGroup) acth[a] = (uint8_t)a;
+    kb = __reduce_max_sync(QCS_FULL, kb);
+    if (lane == 0) sc->key[t >> 5] = kb;
+    if (t == 0) {
+        sc->flag = 1;
+        sc->pf0 = cmk(1.0, 0.0);
+    }
+    group_sync(bar);
+    kb = sc->key[0] > sc->key[1] ? sc->key[0] : sc->key[1];
+    for (int s = 0; s < S; ++s) {
+        const int r = m - 2 * s, ro = ne - 2 * s;
+        const uint8_t *cur = acth + s * m;
+        uint8_t *nxt = acth + (s + 1) * m;
+        if (t < 32) {
+            unsigned long long bk = 0ull;
+            for (int u = lane; u < tri_count(ro); u += 32) {
+                int a, b;
+                pair_of(tab, u, a, b);
+                const unsigned key = pivot_key(Ns[tri_index(cur[a], cur[b])]);
+                const unsigned long long c =
+                    ((unsigned long long)key << 32) | (unsigned long long)(0xffffffffu - (unsigned)u);
+                bk = c > bk ? c : bk;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+                bk = ob > bk ? ob : bk;
+            }
+            if (lane == 0) {
+                if ((bk >> 32) == 0ull) {
+                    sc->flag = 0;
+                } else {
+                    int ak, ap;
+                    pair_of(tab, (int)(0xffffffffu - (unsigned)(bk & 0xffffffffull)), ak, ap);
+                    const int k = cur[ak], p = cur[ap];
+                    const cd piv = Ns[tri_index(k, p)];
+                    sc->pf0 = cmul(sc->pf0, flip_if(piv, ((ak + ap - 1) & 1) != 0));
+                    invh[s] = cinv(piv);
+                    kh[s] = (uint8_t)k;
+                    ph[s] = (uint8_t)p;
+                    sc->ak = ak;
+                    sc->ap = ap;
+                }
+            }
+        }
+        group_sync(bar);
+        if (!sc->flag) return false;
+        const int rv = r - 2;
+        if (rv == 0) break;
+        const int ak = sc->ak, ap = sc->ap, k = kh[s], p = ph[s];
+        const cd ia = invh[s];
+        for (int a2 = t; a2 < rv; a2 += kGroup) {
+            int a = a2;
+            if (a >= ak) ++a;
+            if (a >= ap) ++a;
+            const int i = cur[a];
+            Uv[a2] = cmul(skew_get(Ns, i, k), ia);  // A_{i,k} / A_{k,p}
+            Vv[a2] = skew_get(Ns, i, p);            // A_{i,p}
+            nxt[a2] = (uint8_t)i;
+        }
+        group_sync(bar);
+        const int Tr = tri_count(rv);
+        for (int u = t; u < Tr; u += kGroup) {
+            int a, b;
+            pair_of(tab, u, a, b);
+            cd *x = Ns + tri_index(nxt[a], nxt[b]);
+            cd y = *x;
+            cfms(y, Uv[a], Vv[b]);
+            cfma(y, Vv[a], Uv[b]);
+            *x = y;
+        }
+        group_sync(bar);
+    }
+    // growth of the complement on the empty indices ne .. m-1
+    const int T2 = tri_count(m - ne);
+    unsigned ks = 0u;
+    for (int u = t; u < T2; u += kGroup) {
+        int a, b;
+        pair_of(tab, u, a, b);
+        const unsigned k = pivot_key(Ns[tri_index(ne + a, ne + b)]);
+        ks = k > ks ? k : ks;
+    }
+    ks = __reduce_max_sync(QCS_FULL, ks);
+    group_sync(bar);  // every thread has read sc->key for kb
+    if (lane == 0) sc->key[t >> 5] = ks;
+    group_sync(bar);
+    ks = sc->key[0] > sc->key[1] ? sc->key[0] : sc->key[1];
+    return ks <= kb + (5u << 20);
+}
+
+// Backward recursion over the occupied steps of shared_factor, in place on Ns, whose
+// empty x empty block must hold Zc = sum_k c_k Z_k on entry; c = sum_k c_k scales
+// the constant -1/a of each step.  On return Ns holds sum_k c_k A_k^{-1}.
+__device__ inline void shared_inverse(int m, int ne, cd *__restrict__ Ns, cd *__restrict__ g1v,
+                                      cd *__restrict__ g2v, cd *__restrict__ y1v, cd *__restrict__ y2v,
+                                      const cd *__restrict__ invh, const uint8_t *__restrict__ acth,
+                                      const uint8_t *__restrict__ kh, const uint8_t *__restrict__ ph, cd c,
+                                      SharedScratch *sc, int t, int bar) {
+    const int S = ne / 2, lane = t & 31;
+    for (int s = S - 1; s >= 0; --s) {
+        const int rv = m - 2 * s - 2;
+        const uint8_t *rest = acth + (s + 1) * m;
+        const int k = kh[s], p = ph[s];
+        const cd ia = invh[s];
+        // g1 = v/a, g2 = -u/a with u_i = A_{i,k}, v_i = A_{i,p}
+        for (int a = t; a < rv; a += kGroup) {
+            const int i = rest[a];
+            g1v[a] = cmul(skew_get(Ns, i, p), ia);
+            g2v[a] = cmul(skew_get(Ns, k, i), ia);
+        }
+        group_sync(bar);
+        // y1 = Z g1 and y2 = Z g2 over the later indices: one (vector, row) item per thread
+        for (int e = t; e < 2 * rv; e += kGroup) {
+            const int vec = e >= rv ? 1 : 0, a = e - vec * rv;
+            const cd *g = vec ? g2v : g1v;
+            const int i = rest[a];
+            cd y = cmk(0.0, 0.0);
+            for (int b = 0; b < rv; ++b) {
+                const int j = rest[b];
+                if (j == i) continue;
+                cfma(y, skew_get(Ns, i, j), g[b]);
+            }
+            (vec ? y2v : y1v)[a] = y;
+        }
+        group_sync(bar);
+        if (t < 32) {  // corner g1^T Z g2 - c/a
+            cd corner = cmk(0.0, 0.0);
+            for (int a = lane; a < rv; a += 32) cfma(corner, g1v[a], y2v[a]);
+            corner.x = warp_sum(corner.x);
+            corner.y = warp_sum(corner.y);
+            if (lane == 0) Ns[tri_index(k, p)] = csub(corner, cmul(c, ia));
+        }
+        for (int a = t; a < rv; a += kGroup) {
+            const int i = rest[a];
+            skew_put(Ns, k, i, y1v[a]);        // A^{-1}(k, i) = (Z g1)_i
+            skew_put(Ns, i, p, cneg(y2v[a]));  // A^{-1}(i, p) = -(Z g2)_i
+        }
+        group_sync(bar);
+    }
+    (void)sc;
 }

@@ -81,6 +81,7 @@ qcs_status qcs_make_node_plan(int n, int ne, int nodes, unsigned flags, qcs_node
 // occupied block is eliminated once for all nodes); otherwise a dense congruence and a
 // full elimination per node, as the adjoint and local-energy kernels compute it.
 double qcs_overlap_flops_nev(int n, int ne, int nev, bool overlap_kernel = false);
+double qcs_pf_elim_flops(int m, int stop);  // Pfaffian elimination steps from r = m down to r > stop
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
                                   cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr, bool echelon = false);

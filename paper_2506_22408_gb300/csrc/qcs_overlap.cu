@@ -36,11 +36,13 @@ namespace {
 
 struct PairArgs {
     int n, ne, m, d, nev, NB, all, chunk, nchunks;
+    int reg;          // n = 16: snapshot rows in registers, T by three real products (build_T_reg)
+    int vm;           // entries per Gauss-vector buffer (the full matrix or NB node complements)
     int64_t W, P;
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
     int ut_bytes;     // shared bytes of the walker rows Ut (per block)
-    int off_R, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // byte offsets in a warp region
+    int off_T, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // byte offsets in a warp region
     const cd *Ut;
     const cd *pref;
     const cd *Qt;
@@ -61,9 +63,10 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
                          const uint16_t *tab, int warp, int wpb, int lane) {
     const int n = A.n, n2 = 2 * n;
     cd *Rg = reinterpret_cast<cd *>(wbase);
-    cd *Qs = Rg;
-    cd *Ts = Rg + (size_t)n2 * ld_qt(n);
-    cd *Ns = Rg;
+    cd *Qs = Rg;  // staged snapshot rows (shared-memory path only)
+    cd *Ts = reinterpret_cast<cd *>(wbase + A.off_T);
+    cd *Ns = Rg;  // node matrices, once T is consumed
+    double *Uss = reinterpret_cast<double *>(Uts + n * ld_ut(n));  // re + im of Ut (register path)
     cd *Bs = reinterpret_cast<cd *>(wbase + A.off_B);
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
@@ -71,7 +74,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
     int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = reinterpret_cast<uint8_t *>(wbase + A.off_act);
-    uint8_t *act1 = act0 + A.NB * A.m;
+    uint8_t *act1 = act0 + A.vm;
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
     const int span = A.chunk * wpb;  // snapshots per tile; warp w takes every wpb-th
     // chunk-major tile order: consecutive tiles share one snapshot chunk and run over
@@ -84,7 +87,11 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     if (p0 < L) {
         const cd *Utw = A.Ut + w * n * n;
         const int lu = ld_ut(n);
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Uts[(e / n) * lu + (e % n)] = Utw[e];
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const cd u = Utw[e];
+            Uts[(e / n) * lu + (e % n)] = u;
+            if (A.reg) Uss[(e / n) * lu + (e % n)] = u.x + u.y;
+        }
     }
     __syncthreads();
     cd acc = cmk(0.0, 0.0);
@@ -96,6 +103,8 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             __syncwarp();
             if (gq && gq[0] != 0xFF) {
                 build_T_gather(n, Uts, gq, Ts, lane);  // signed permutation: no products
+            } else if (A.reg) {
+                build_T_reg<16>(A.ne, Uts, Uss, A.Qt + q * n2 * n, Ts, lane);
             } else {
                 load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
                 __syncwarp();
@@ -108,9 +117,10 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             cd pf0;
             const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
             const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
+            const int NBr = shared ? A.NB : 1;  // the rare full eliminations run one node per round
             cd S = cmk(0.0, 0.0);
-            for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
-                int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+            for (int k0 = 0; k0 < A.nev; k0 += NBr) {
+                int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
                 node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
@@ -142,7 +152,7 @@ struct BatchArgs {
     PairArgs sys[QCS_MAX_SYSTEMS];         // in queue order
 };
 
-__global__ void __launch_bounds__(128) pair_overlap_kernel(const __grid_constant__ BatchArgs B) {
+__global__ void __launch_bounds__(128, 3) pair_overlap_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long next_tile;
     const int lane = threadIdx.x & 31;
@@ -186,18 +196,25 @@ __global__ void reduce_kernel(int64_t W, int64_t P, int nparts, const cd *__rest
 
 namespace {
 
-// Per-warp shared layout for nb node matrices; returns bytes per warp.
+// Per-warp shared layout for nb node matrices; returns bytes per warp.  The first
+// region holds the staged snapshot rows and T (T alone on the register path), then
+// the node matrices: one full copy of B (shared elimination; the rare full
+// eliminations, one node per round) or NB complements of 2d x 2d.
 size_t pair_warp_layout(PairArgs &A, int NB) {
-    const int n = A.n, m = A.m, T = tri_count(m);
-    size_t R = (size_t)2 * n * ld_qt(n) + (size_t)n * ld_t(n);  // Qt + T
-    if ((size_t)NB * T > R) R = (size_t)NB * T;
-    size_t o = align16(R * sizeof(cd));
+    const int n = A.n, m = A.m, T = tri_count(m), d2 = m - A.ne;
+    const size_t qbytes = A.reg ? 0 : (size_t)2 * n * ld_qt(n) * sizeof(cd);
+    size_t R = qbytes + (size_t)n * ld_t(n) * sizeof(cd);
+    if ((size_t)T * sizeof(cd) > R) R = (size_t)T * sizeof(cd);
+    if ((size_t)NB * tri_count(d2) * sizeof(cd) > R) R = (size_t)NB * tri_count(d2) * sizeof(cd);
+    A.vm = m > NB * d2 ? m : NB * d2;
+    A.off_T = (int)qbytes;
+    size_t o = align16(R);
     A.off_B = (int)o;
     o = align16(o + (size_t)T * sizeof(cd));
     A.off_U = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
+    o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_V = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
+    o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_inv = (int)o;
@@ -205,9 +222,9 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     A.off_int = (int)o;
     o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
-    o = align16(o + (size_t)2 * NB * m);
+    o = align16(o + (size_t)2 * A.vm);
     A.off_pv = (int)o;
-    o = align16(o + (size_t)NB * (m / 2) * sizeof(cd));
+    o = align16(o + (size_t)(A.vm / 2) * sizeof(cd));
     return o;
 }
 
@@ -230,12 +247,14 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.nchunks = L.nchunks;
     A.W = L.W;
     A.P = L.P;
+    A.reg = L.n == 16;
     const int n = A.n, m = A.m, T = tri_count(m);
     const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
-    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * sizeof(cd));
+    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * (sizeof(cd) + (A.reg ? sizeof(double) : 0)));
     // Node matrices per round: the requested count, or by default the largest
-    // count (balanced rounds, at most kMaxNB) for which two blocks fit on an SM.
+    // count (balanced rounds, at most kMaxNB) for which three blocks (register
+    // path) or two blocks fit on an SM.
     int NB = 1;
     if (L.config > 0) {
         NB = L.config < A.nev ? L.config : A.nev;
@@ -248,7 +267,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
             int nb = (A.nev + rounds - 1) / rounds;
             if (nb > kMaxNB) continue;
             size_t blk = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * pair_warp_layout(A, nb) + 1024;
-            if (2 * blk <= sm_budget + 1024) {
+            if ((A.reg ? 3 : 2) * blk <= sm_budget + 1024) {
                 NB = nb;
                 break;
             }

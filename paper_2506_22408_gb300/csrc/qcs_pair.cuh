@@ -57,6 +57,56 @@ __device__ inline void build_T_echelon(int n, int ne, const cd *__restrict__ Uts
     }
 }
 
+// T from echelon-form walker rows for n = N (2N = 32 lanes): lane c holds row c of the
+// snapshot's Qt in registers and owns column c of T.  Each complex multiply-add takes
+// three real products (Gauss's 3-multiplication form): with s = re + im of both
+// factors, Re = sum ur qr - sum ui qi and Im = sum us qs - sum ur qr - sum ui qi, so
+// the sums us of the walker rows (Uss, per block) and qs of the snapshot row (here)
+// are formed once.  The skipped zeros follow build_T_echelon; the row loop is
+// warp-uniform and enters the unrolled k sequences by a switch, so the register
+// arrays are indexed by constants.
+#define QCS_T3M(K)                            \
+    case K: {                                 \
+        const cd u_ = ur[K];                  \
+        p1 = fma(u_.x, qr[K], p1);            \
+        p2 = fma(u_.y, qi[K], p2);            \
+        p3 = fma(us[K], qs[K], p3);           \
+    }
+template <int N>
+__device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const double *__restrict__ Uss,
+                                   const cd *__restrict__ Qg, cd *__restrict__ Ts, int lane) {
+    static_assert(N == 16, "one lane per column of T: 2N must be the warp width");
+    const int lu = ld_ut(N), lt = ld_t(N);
+    double qr[N], qi[N], qs[N];
+    const cd *qrow = Qg + lane * N;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const cd q = qrow[k];
+        qr[k] = q.x;
+        qi[k] = q.y;
+        qs[k] = q.x + q.y;
+    }
+    for (int j = 0; j < N; ++j) {
+        const cd *ur = Uts + j * lu;
+        const double *us = Uss + j * lu;
+        double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        if (j >= ne) {
+            switch (ne - 1) {  // k = ne-1 down to 0
+                QCS_T3M(15) QCS_T3M(14) QCS_T3M(13) QCS_T3M(12) QCS_T3M(11) QCS_T3M(10) QCS_T3M(9) QCS_T3M(8)
+                QCS_T3M(7) QCS_T3M(6) QCS_T3M(5) QCS_T3M(4) QCS_T3M(3) QCS_T3M(2) QCS_T3M(1) QCS_T3M(0)
+                default: break;
+            }
+        }
+        switch (j) {  // k = j up to N-1
+            QCS_T3M(0) QCS_T3M(1) QCS_T3M(2) QCS_T3M(3) QCS_T3M(4) QCS_T3M(5) QCS_T3M(6) QCS_T3M(7)
+            QCS_T3M(8) QCS_T3M(9) QCS_T3M(10) QCS_T3M(11) QCS_T3M(12) QCS_T3M(13) QCS_T3M(14) QCS_T3M(15)
+            default: break;
+        }
+        Ts[j * lt + lane] = cmk(p1 - p2, p3 - p1 - p2);
+    }
+}
+#undef QCS_T3M
+
 // x * ph for a phase code ph = 0..3 (1, i, -1, -i): a swap of the parts and sign
 // flips of the bit patterns, no floating-point arithmetic.
 __device__ __forceinline__ cd mul_phase(cd x, unsigned ph) {

@@ -27,6 +27,7 @@ QCS_TF32X3 = 1
 QCS_FLAG_ALL_NODES = 1
 QCS_FLAG_DFT_NODES = 2
 MAX_NODES = 49
+QCS_ERR_ARG, QCS_ERR_CUDA, QCS_ERR_NONFINITE, QCS_ERR_SINGULAR, QCS_ERR_TIMEOUT, QCS_ERR_UNSUPPORTED = 1, 2, 4, 8, 16, 32
 STATUS_BITS = {1: "ARG", 2: "CUDA", 4: "NONFINITE", 8: "SINGULAR", 16: "TIMEOUT", 32: "UNSUPPORTED"}
 
 EXPORTED = [
@@ -37,7 +38,7 @@ EXPORTED = [
     "qcs_autotune", "qcs_set_config", "qcs_overlap_batched", "qcs_node_plan_get",
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
-    "qcs_local_energy", "qcs_local_energy_flops_per_pair",
+    "qcs_local_energy", "qcs_local_energy_flops_per_pair", "qcs_overlap_flops_breakdown",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True):
         for fn in ("qcs_overlap_flops_per_pair_signed_perm", "qcs_grad_flops_per_pair_signed_perm"):
             getattr(lib, fn).argtypes = [i32, i32, i32, u32]
             getattr(lib, fn).restype = f64
+        lib.qcs_overlap_flops_breakdown.argtypes = [i32, i32, i32, u32, ctypes.POINTER(f64)]
         lib.qcs_overlap_batched.argtypes = [P, i32, ctypes.POINTER(_System), ctypes.POINTER(_Opts), P]
         lib.qcs_autotune.argtypes = [P, i32, i32, i32, u32, ctypes.POINTER(i32)]
         lib.qcs_set_config.argtypes = [P, i32, i32, i32, u32, i32]
@@ -348,6 +350,15 @@ def overlap_noalloc(Q: torch.Tensor, b: torch.Tensor, walkers: torch.Tensor, out
 
 def flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:
     return float(load().qcs_overlap_flops_per_pair(n, ne, nodes, flags))
+
+
+def flops_breakdown(n: int, ne: int, nodes: int = 0, flags: int = 0) -> dict:
+    """Host-only: the parts of flops_per_pair (congruence T, covariance B, Pfaffians)."""
+    out = (ctypes.c_double * 3)()
+    rc = load().qcs_overlap_flops_breakdown(n, ne, nodes, flags, out)
+    if rc != QCS_OK:
+        raise QCSError(rc, "qcs_overlap_flops_breakdown: sizes or nodes out of range")
+    return {"T": out[0], "B": out[1], "pfaffian": out[2]}
 
 
 def grad_flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:

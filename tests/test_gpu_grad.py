@@ -59,6 +59,45 @@ def test_gradient_matches_oracle(ctx, n, ne, W, P):
     check_grad(g, og, ov, oo, sc)
 
 
+@pytest.mark.parametrize("n,ne,ensemble", [(16, 8, "haar"), (16, 8, "signed_perm"), (12, 4, "signed_perm"),
+                                           (10, 10, "haar")])
+def test_gradient_structured_walkers(ctx, n, ne, ensemble):
+    """Walkers in echelon form already, a reversed unit basis and walkers on the last
+    modes only, against Haar snapshots and signed permutations: the occupied block of
+    the node matrices is then often singular or badly pivoted, so both the block form
+    and the full per-node elimination run.  Unit-vector walkers against signed
+    permutations make some node matrices exactly singular, where the derivative
+    formula (it needs A^{-1}) does not apply: the status word says so, and the
+    generic walker's gradient must still be exact."""
+    rng = np.random.default_rng(31 * n + ne)
+    P = 40
+    if ensemble == "haar":
+        Q = synth.haar_orthogonal(rng, 2 * n, P)
+    else:
+        Q = synth.signed_permutation(rng, 2 * n, P)
+    b = synth.uniform_bits(rng, n, P)
+    Phi = synth.walkers(rng, n, ne, 4)
+    eye = np.eye(n, dtype=complex)
+    R = np.triu(rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne))) + 2 * np.eye(ne)
+    Phi[0] = eye[:, :ne] @ R
+    Phi[1] = eye[:, ne - 1::-1]
+    Phi[2] = eye[:, n - ne:] @ R
+    ov, g, st, _ = gpu_grad(ctx, Phi, Q, b)
+    oo, og, _ = orc.overlap_grad(Phi, Q, b)
+    _, _, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    floor = 1e-12 * np.abs(og).max()
+    if ensemble == "haar":
+        assert st == 0
+        check_grad(g, og, ov, oo, sc, ov_floor=floor)
+    else:
+        assert st in (0, qcs.QCS_ERR_SINGULAR)
+        if st == 0:
+            check_grad(g, og, ov, oo, sc, ov_floor=floor)
+        else:
+            check_grad(g[3:], og[3:], ov[3:], oo[3:], sc[3:], ov_floor=floor)
+        assert np.all(np.abs(ov - oo) <= 1e-10 * sc.mean(axis=1) + floor)  # overlaps stay exact
+
+
 def test_gradient_options_and_overlap_agree(ctx):
     rng = np.random.default_rng(5)
     n, ne, W, P = 8, 4, 4, 33

@@ -110,11 +110,12 @@ def test_node_options_agree(ctx):
         check_walkers(ov, oo, sc)
 
 
-@pytest.mark.parametrize("ensemble", ["givens", "signed_perm"])
-def test_other_snapshot_ensembles(ctx, ensemble):
-    """120-Givens products and signed permutations (exact zeros and singular node
+@pytest.mark.parametrize("ensemble,n,ne", [("givens", 8, 4), ("signed_perm", 8, 4), ("givens", 16, 8),
+                                           ("signed_perm", 16, 6)])
+def test_other_snapshot_ensembles(ctx, ensemble, n, ne):
+    """Givens products and signed permutations (exact zeros and singular node
     matrices occur for the latter)."""
-    wl = synth.Workload("t", 8, 4, 6, 64, ensemble=ensemble)
+    wl = synth.Workload("t", n, ne, 6, 64, ensemble=ensemble)
     data = wl.generate(seed=3)
     ov, pp, par, st = run_gpu(ctx, data)
     assert st == 0
@@ -150,7 +151,7 @@ def test_degenerate_inputs(ctx):
     assert np.all(parf == -1) and ovf[0] == 0 and np.all(ppf == 0)
 
 
-@pytest.mark.parametrize("n,ne", [(16, 8), (8, 8), (9, 2), (12, 6)])
+@pytest.mark.parametrize("n,ne", [(16, 8), (16, 14), (16, 16), (8, 8), (9, 2), (12, 6)])
 def test_structured_walkers(ctx, n, ne):
     """Walkers whose orbital matrix is already in echelon form, is a reversed unit basis
     (zero leading entries), lives on the last modes only, or has a zero top-left entry:
