@@ -16,8 +16,16 @@
 //     d^2 pf = (pf/2) [ tr(A^-1 A'') - tr(A^-1 A' A^-1 A') + tr(A^-1 A')^2 / 2 ],
 // and Eq. (Pfaffian_der) d pf = (pf/2) tr(A^-1 A').  The walker prefactor cancels in
 //     e1 = sum_p D o_p[hhat] / sum_p o_p,   e2 = sum_gamma sum_p D^2 o_p[Lhat_gamma] / sum_p o_p.
-// A^-1 is rebuilt per pair and node by the in-place backward recursion (qcs_group.cuh);
-// per Cholesky vector the pair costs O(m (2n)^2 + nodes m^3).
+// The node matrices share their occupied block P (ne x ne): with E = P^-1 B_oe,
+// F = [-E; I], F0 = [[P^-1, 0], [0, 0]] and Z_k the inverse of the node's 2d x 2d
+// complement, A_k^-1 = F0 + F Z_k F^T, so with W = A' F, G = F^T W and
+// H = -W_o^T P^-1 W_o the traces need only 2d x 2d work per node:
+//     tr(A_k^-1 A') = tr(P^-1 A'_oo) + tr(Z_k G),
+//     tr((A_k^-1 A')^2) = tr((P^-1 A'_oo)^2) + 2 tr(Z_k H) + tr((Z_k G)^2).
+// P^-1 comes from the backward recursion over the shared steps (qcs_group.cuh) run
+// with Z = 0; pairs whose occupied block would grow the complement beyond 2^5 take
+// the full inverse per node.  Per Cholesky vector the pair costs
+// O(m (2n)^2 + m^2 d + nodes d^3).
 #include "qcs_group.cuh"
 #include "qcs_internal.h"
 
@@ -28,7 +36,7 @@ struct EnergyArgs {
     int64_t W, P;
     int group_bytes, tab_bytes;
     int off_Q, off_T, off_B, off_NZ, off_g1, off_g2, off_y1, off_y2, off_pf, off_cf, off_invh, off_int, off_tile,
-        off_acth, off_kh, off_ph, off_X1, off_Ap, off_Sacc, off_red, off_acc;
+        off_acth, off_kh, off_ph, off_X1, off_Ap, off_Sacc, off_red, off_acc, off_scr;
     const cd *Ut;
     const cd *Qt;
     const int *idx;
@@ -108,6 +116,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
     cd *Sacc = reinterpret_cast<cd *>(wb + A.off_Sacc); // sum_gamma X'_g J X'_g^T (packed)
     cd *red = reinterpret_cast<cd *>(wb + A.off_red);   // 2 entries
     cd *acc = reinterpret_cast<cd *>(wb + A.off_acc);   // 2 x NB: first / second derivative terms per node
+    SharedScratch *scr = reinterpret_cast<SharedScratch *>(wb + A.off_scr);
 
     const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
     const int64_t ntiles = A.W * A.nchunks;
@@ -136,100 +145,284 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                 build_B(n, ne, Ts, Bs, tab, t, kGroup);
                 group_sync(bar);
                 cd Sop = cmk(0.0, 0.0), S1p = cmk(0.0, 0.0), S2p = cmk(0.0, 0.0);
-                for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
-                    const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                    node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar, A.status);
-                    node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
-                    if (k0 == 0)  // B has been copied into the node matrices; Sacc may share its storage
-                        for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
-                    if (t < nb) {
-                        cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
-                        acc[t] = cmk(0.0, 0.0);
-                        acc[A.NB + t] = cmk(0.0, 0.0);
+                if (shared_factor(m, ne, Bs, Ns, g1v, g2v, invh, acth, kh, ph, scr, tab, t, bar)) {
+                    // Block form: A_k^{-1} = F0 + F Z_k F^T with F0 = [[P^-1, 0], [0, 0]],
+                    // F = [-E; I], E = P^-1 B_oe, Z_k = (S0 + w_k D)^{-1} (2d x 2d).  Per
+                    // operator, with W = A' F and G = F^T A' F, H = F^T A' F0 A' F = -W_o^T P^-1 W_o:
+                    //   tr(A_k^-1 A')       = tr(P^-1 A'_oo) + tr(Z_k G)
+                    //   tr((A_k^-1 A')^2)   = tr((P^-1 A'_oo)^2) + 2 tr(Z_k H) + tr((Z_k G)^2)
+                    const int d2 = m - ne, Tn = tri_count(d2), To = tri_count(ne);
+                    const int zoff = T > A.NB * Tn ? T : A.NB * Tn;
+                    cd *Pinv = Ns + zoff;       // P^-1, packed upper (ne x ne)
+                    cd *Es = Pinv + To;         // E, ne x 2d
+                    cd *Sc = Es + ne * d2;      // S0, packed upper (2d x 2d)
+                    const cd pf0 = scr->pf0;
+                    for (int e = t; e < Tn; e += kGroup) {
+                        int a, b;
+                        pair_of(tab, e, a, b);
+                        cd *y = Ns + tri_index(ne + a, ne + b);
+                        Sc[e] = *y;
+                        *y = cmk(0.0, 0.0);
                     }
-                    if (t == 0)
-                        for (int v = 0; v < nb; ++v) cfma(Sop, A.gamma[k0 + v], pf[v]);
                     group_sync(bar);
-                    // operators: Cholesky vectors (second derivative), then h (first derivative);
-                    // the last pass (o = nop) forms A'' = X'' J X^T + X J X''^T + 2 Sacc
-                    for (int o = 0; o <= A.nop; ++o) {
-                        const bool is_h = A.has_h && o == A.nchol;
-                        const bool last = o == A.nop;
-                        const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
-                        // X1 = Ko Q'^T: X1[a][c] = sum_k Ko[a][2k] Re Qt[c][k] - Ko[a][2k+1] Im Qt[c][k]
-                        for (int e = t; e < m * n2; e += kGroup) {
-                            const int a = e / n2, c = e - a * n2;
-                            const cd *kr = Ko + a * n2;
-                            const cd *qr = Qs + c * lq;
-                            cd s = cmk(0.0, 0.0);
-                            for (int k = 0; k < n; ++k) {
-                                crfma(s, kr[2 * k], qr[k].x);
-                                crfma(s, kr[2 * k + 1], -qr[k].y);
-                            }
-                            X1[a * lx + c] = s;
+                    // with Z = 0 and unit constant the backward pass gives F0
+                    shared_inverse(m, ne, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, cmk(1.0, 0.0), scr, t, bar);
+                    for (int e = t; e < To; e += kGroup) Pinv[e] = Ns[e];
+                    group_sync(bar);
+                    for (int e = t; e < ne * d2; e += kGroup) {
+                        const int i = e / d2, j = e - i * d2;
+                        cd s = cmk(0.0, 0.0);
+                        for (int l = 0; l < ne; ++l)
+                            if (l != i) cfma(s, skew_get(Pinv, i, l), Bs[tri_index(l, ne + j)]);
+                        Es[e] = s;
+                    }
+                    group_sync(bar);
+                    for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                        const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                        node_factor(d2, 0, A.wnode + k0, nb, Sc, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t,
+                                    bar, A.status);
+                        node_inverse(d2, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                        if (k0 == 0)  // B is consumed (E formed); Sacc may share its storage
+                            for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
+                        if (t < nb) {
+                            cf[t] = cscale(cmul(A.gamma[k0 + t], cmul(pf0, pf[t])), 0.5);
+                            acc[t] = cmk(0.0, 0.0);
+                            acc[A.NB + t] = cmk(0.0, 0.0);
                         }
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) cfma(Sop, A.gamma[k0 + v], cmul(pf0, pf[v]));
                         group_sync(bar);
-                        // Ap = X1 J X^T + X J X1^T (+ 2 Sacc on the last pass); Sacc += X1 J X1^T
-                        for (int e = t; e < T; e += kGroup) {
-                            int a, b;
-                            pair_of(tab, e, a, b);
-                            cd v = cadd(yjz(n, [&](int c) { return X1[a * lx + c]; },
-                                            [&](int c) { return x_at(Ts, lt, ne, b, c); }),
-                                        yjz(n, [&](int c) { return x_at(Ts, lt, ne, a, c); },
-                                            [&](int c) { return X1[b * lx + c]; }));
-                            if (last) {
-                                v = cadd(v, cscale(Sacc[e], 2.0));
-                            } else if (!is_h && k0 == 0) {
-                                Sacc[e] = cadd(Sacc[e], yjz(n, [&](int c) { return X1[a * lx + c]; },
-                                                            [&](int c) { return X1[b * lx + c]; }));
-                            }
-                            Ap[tri_index(a, b)] = v;
-                        }
-                        group_sync(bar);
-                        for (int v = 0; v < nb; ++v) {
-                            const cd *Zv = Ns + v * T;  // A_v^-1
-                            // t1 = tr(A^-1 Ap) = -2 sum_{a<b} Z_ab Ap_ab
-                            cd t1 = cmk(0.0, 0.0);
-                            for (int e = t; e < T; e += kGroup) cfma(t1, Zv[e], Ap[e]);
-                            t1 = cscale(group_sum(t1, red, t, bar), -2.0);
-                            if (last) {
-                                if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], t1);
-                                continue;
-                            }
-                            if (is_h) {
-                                if (t == 0) acc[v] = cadd(acc[v], t1);
-                                continue;
-                            }
-                            // t2 = tr((A^-1 Ap)^2) = sum_{a,b} P_ab P_ba, P = A^-1 Ap: one unordered
-                            // pair {a, b} (a <= b) per item, both products formed by the same thread
-                            cd t2 = cmk(0.0, 0.0);
-                            const int npairs = m * (m + 1) / 2;
-                            for (int e = t; e < npairs; e += kGroup) {
-                                int a = 0, r = e;
-                                while (r >= m - a) {
-                                    r -= m - a;
-                                    ++a;
+                        for (int o = 0; o <= A.nop; ++o) {
+                            const bool is_h = A.has_h && o == A.nchol;
+                            const bool last = o == A.nop;
+                            const bool second = !is_h && !last;  // a Cholesky vector: second derivative
+                            const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
+                            for (int e = t; e < m * n2; e += kGroup) {
+                                const int a = e / n2, c = e - a * n2;
+                                const cd *kr = Ko + a * n2;
+                                const cd *qr = Qs + c * lq;
+                                cd s = cmk(0.0, 0.0);
+                                for (int k = 0; k < n; ++k) {
+                                    crfma(s, kr[2 * k], qr[k].x);
+                                    crfma(s, kr[2 * k + 1], -qr[k].y);
                                 }
-                                const int b = a + r;
-                                cd pab = cmk(0.0, 0.0), pba = cmk(0.0, 0.0);
-                                for (int c = 0; c < m; ++c) {
-                                    cfma(pab, skew_at(Zv, a, c), skew_at(Ap, c, b));
-                                    cfma(pba, skew_at(Zv, b, c), skew_at(Ap, c, a));
-                                }
-                                const cd pr = cmul(pab, pba);
-                                t2 = (a == b) ? cadd(t2, pr) : cadd(t2, cscale(pr, 2.0));
+                                X1[a * lx + c] = s;
                             }
-                            t2 = group_sum(t2, red, t, bar);
-                            if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], csub(cscale(cmul(t1, t1), 0.5), t2));
+                            group_sync(bar);
+                            for (int e = t; e < T; e += kGroup) {
+                                int a, b;
+                                pair_of(tab, e, a, b);
+                                cd v = cadd(yjz(n, [&](int c) { return X1[a * lx + c]; },
+                                                [&](int c) { return x_at(Ts, lt, ne, b, c); }),
+                                            yjz(n, [&](int c) { return x_at(Ts, lt, ne, a, c); },
+                                                [&](int c) { return X1[b * lx + c]; }));
+                                if (last) {
+                                    v = cadd(v, cscale(Sacc[e], 2.0));
+                                } else if (second && k0 == 0) {
+                                    Sacc[e] = cadd(Sacc[e], yjz(n, [&](int c) { return X1[a * lx + c]; },
+                                                                [&](int c) { return X1[b * lx + c]; }));
+                                }
+                                Ap[tri_index(a, b)] = v;
+                            }
+                            group_sync(bar);
+                            // X' is consumed: its region holds W, G, V, H
+                            cd *Wm = X1, *Gp = X1 + m * d2, *Vm = Gp + Tn, *Hp = Vm + ne * d2;
+                            for (int e = t; e < m * d2; e += kGroup) {
+                                const int a = e / d2, j = e - a * d2;
+                                cd s = (a == ne + j) ? cmk(0.0, 0.0) : skew_get(Ap, a, ne + j);
+                                for (int l = 0; l < ne; ++l)
+                                    if (l != a) cfms(s, skew_get(Ap, a, l), Es[l * d2 + j]);
+                                Wm[e] = s;
+                            }
+                            group_sync(bar);
+                            for (int e = t; e < Tn; e += kGroup) {
+                                int i, j;
+                                pair_of(tab, e, i, j);
+                                cd s = Wm[(ne + i) * d2 + j];
+                                for (int l = 0; l < ne; ++l) cfms(s, Es[l * d2 + i], Wm[l * d2 + j]);
+                                Gp[e] = s;
+                            }
+                            if (second)
+                                for (int e = t; e < ne * d2; e += kGroup) {
+                                    const int i = e / d2, j = e - i * d2;
+                                    cd s = cmk(0.0, 0.0);
+                                    for (int l = 0; l < ne; ++l)
+                                        if (l != i) cfma(s, skew_get(Pinv, i, l), Wm[l * d2 + j]);
+                                    Vm[e] = s;
+                                }
+                            // tr(P^-1 A'_oo) = -2 sum_{a<b} P^-1_ab A'_ab
+                            cd tP = cmk(0.0, 0.0);
+                            for (int e = t; e < To; e += kGroup) cfma(tP, Pinv[e], Ap[e]);
+                            group_sync(bar);
+                            tP = cscale(group_sum(tP, red, t, bar), -2.0);
+                            cd c0 = cmk(0.0, 0.0);
+                            if (second) {
+                                for (int e = t; e < Tn; e += kGroup) {
+                                    int i, j;
+                                    pair_of(tab, e, i, j);
+                                    cd s = cmk(0.0, 0.0);
+                                    for (int l = 0; l < ne; ++l) cfms(s, Wm[l * d2 + i], Vm[l * d2 + j]);
+                                    Hp[e] = s;
+                                }
+                                // tr((P^-1 A'_oo)^2): one unordered pair {a, b} of occupied indices per item
+                                for (int e = t; e < ne * (ne + 1) / 2; e += kGroup) {
+                                    int a = 0, r = e;
+                                    while (r >= ne - a) {
+                                        r -= ne - a;
+                                        ++a;
+                                    }
+                                    const int b = a + r;
+                                    cd pab = cmk(0.0, 0.0), pba = cmk(0.0, 0.0);
+                                    for (int c = 0; c < ne; ++c) {
+                                        if (c != a && c != b) cfma(pab, skew_get(Pinv, a, c), skew_get(Ap, c, b));
+                                        if (c != b && c != a) cfma(pba, skew_get(Pinv, b, c), skew_get(Ap, c, a));
+                                    }
+                                    const cd pr = cmul(pab, pba);
+                                    c0 = (a == b) ? cadd(c0, pr) : cadd(c0, cscale(pr, 2.0));
+                                }
+                                c0 = group_sum(c0, red, t, bar);
+                            }
+                            for (int v = 0; v < nb; ++v) {
+                                const cd *Zv = Ns + v * Tn;  // Z_v, packed upper
+                                cd zg = cmk(0.0, 0.0), zh = cmk(0.0, 0.0);
+                                for (int e = t; e < Tn; e += kGroup) {
+                                    cfma(zg, Zv[e], Gp[e]);
+                                    if (second) cfma(zh, Zv[e], Hp[e]);
+                                }
+                                const cd t1 = cadd(tP, cscale(group_sum(zg, red, t, bar), -2.0));
+                                if (last) {
+                                    if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], t1);
+                                    continue;
+                                }
+                                if (is_h) {
+                                    if (t == 0) acc[v] = cadd(acc[v], t1);
+                                    continue;
+                                }
+                                // tr((Z G)^2): one unordered pair {a, b} of empty indices per item
+                                cd t2 = cscale(zh, -4.0);  // 2 tr(Z H) = -4 sum_{a<b} Z_ab H_ab
+                                for (int e = t; e < d2 * (d2 + 1) / 2; e += kGroup) {
+                                    int a = 0, r = e;
+                                    while (r >= d2 - a) {
+                                        r -= d2 - a;
+                                        ++a;
+                                    }
+                                    const int b = a + r;
+                                    cd pab = cmk(0.0, 0.0), pba = cmk(0.0, 0.0);
+                                    for (int c = 0; c < d2; ++c) {
+                                        if (c != a && c != b) cfma(pab, skew_get(Zv, a, c), skew_get(Gp, c, b));
+                                        if (c != b && c != a) cfma(pba, skew_get(Zv, b, c), skew_get(Gp, c, a));
+                                    }
+                                    const cd pr = cmul(pab, pba);
+                                    t2 = (a == b) ? cadd(t2, pr) : cadd(t2, cscale(pr, 2.0));
+                                }
+                                t2 = cadd(group_sum(t2, red, t, bar), c0);
+                                if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], csub(cscale(cmul(t1, t1), 0.5), t2));
+                            }
+                            group_sync(bar);
                         }
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) {
+                                cfma(S1p, cf[v], acc[v]);
+                                cfma(S2p, cf[v], acc[A.NB + v]);
+                            }
                         group_sync(bar);
                     }
-                    if (t == 0)
-                        for (int v = 0; v < nb; ++v) {
-                            cfma(S1p, cf[v], acc[v]);
-                            cfma(S2p, cf[v], acc[A.NB + v]);
+                } else {
+                    for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                        const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                        node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar, A.status);
+                        node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
+                        if (k0 == 0)  // B has been copied into the node matrices; Sacc may share its storage
+                            for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
+                        if (t < nb) {
+                            cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
+                            acc[t] = cmk(0.0, 0.0);
+                            acc[A.NB + t] = cmk(0.0, 0.0);
                         }
-                    group_sync(bar);
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) cfma(Sop, A.gamma[k0 + v], pf[v]);
+                        group_sync(bar);
+                        // operators: Cholesky vectors (second derivative), then h (first derivative);
+                        // the last pass (o = nop) forms A'' = X'' J X^T + X J X''^T + 2 Sacc
+                        for (int o = 0; o <= A.nop; ++o) {
+                            const bool is_h = A.has_h && o == A.nchol;
+                            const bool last = o == A.nop;
+                            const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
+                            // X1 = Ko Q'^T: X1[a][c] = sum_k Ko[a][2k] Re Qt[c][k] - Ko[a][2k+1] Im Qt[c][k]
+                            for (int e = t; e < m * n2; e += kGroup) {
+                                const int a = e / n2, c = e - a * n2;
+                                const cd *kr = Ko + a * n2;
+                                const cd *qr = Qs + c * lq;
+                                cd s = cmk(0.0, 0.0);
+                                for (int k = 0; k < n; ++k) {
+                                    crfma(s, kr[2 * k], qr[k].x);
+                                    crfma(s, kr[2 * k + 1], -qr[k].y);
+                                }
+                                X1[a * lx + c] = s;
+                            }
+                            group_sync(bar);
+                            // Ap = X1 J X^T + X J X1^T (+ 2 Sacc on the last pass); Sacc += X1 J X1^T
+                            for (int e = t; e < T; e += kGroup) {
+                                int a, b;
+                                pair_of(tab, e, a, b);
+                                cd v = cadd(yjz(n, [&](int c) { return X1[a * lx + c]; },
+                                                [&](int c) { return x_at(Ts, lt, ne, b, c); }),
+                                            yjz(n, [&](int c) { return x_at(Ts, lt, ne, a, c); },
+                                                [&](int c) { return X1[b * lx + c]; }));
+                                if (last) {
+                                    v = cadd(v, cscale(Sacc[e], 2.0));
+                                } else if (!is_h && k0 == 0) {
+                                    Sacc[e] = cadd(Sacc[e], yjz(n, [&](int c) { return X1[a * lx + c]; },
+                                                                [&](int c) { return X1[b * lx + c]; }));
+                                }
+                                Ap[tri_index(a, b)] = v;
+                            }
+                            group_sync(bar);
+                            for (int v = 0; v < nb; ++v) {
+                                const cd *Zv = Ns + v * T;  // A_v^-1
+                                // t1 = tr(A^-1 Ap) = -2 sum_{a<b} Z_ab Ap_ab
+                                cd t1 = cmk(0.0, 0.0);
+                                for (int e = t; e < T; e += kGroup) cfma(t1, Zv[e], Ap[e]);
+                                t1 = cscale(group_sum(t1, red, t, bar), -2.0);
+                                if (last) {
+                                    if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], t1);
+                                    continue;
+                                }
+                                if (is_h) {
+                                    if (t == 0) acc[v] = cadd(acc[v], t1);
+                                    continue;
+                                }
+                                // t2 = tr((A^-1 Ap)^2) = sum_{a,b} P_ab P_ba, P = A^-1 Ap: one unordered
+                                // pair {a, b} (a <= b) per item, both products formed by the same thread
+                                cd t2 = cmk(0.0, 0.0);
+                                const int npairs = m * (m + 1) / 2;
+                                for (int e = t; e < npairs; e += kGroup) {
+                                    int a = 0, r = e;
+                                    while (r >= m - a) {
+                                        r -= m - a;
+                                        ++a;
+                                    }
+                                    const int b = a + r;
+                                    cd pab = cmk(0.0, 0.0), pba = cmk(0.0, 0.0);
+                                    for (int c = 0; c < m; ++c) {
+                                        cfma(pab, skew_at(Zv, a, c), skew_at(Ap, c, b));
+                                        cfma(pba, skew_at(Zv, b, c), skew_at(Ap, c, a));
+                                    }
+                                    const cd pr = cmul(pab, pba);
+                                    t2 = (a == b) ? cadd(t2, pr) : cadd(t2, cscale(pr, 2.0));
+                                }
+                                t2 = group_sum(t2, red, t, bar);
+                                if (t == 0) acc[A.NB + v] = cadd(acc[A.NB + v], csub(cscale(cmul(t1, t1), 0.5), t2));
+                            }
+                            group_sync(bar);
+                        }
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) {
+                                cfma(S1p, cf[v], acc[v]);
+                                cfma(S2p, cf[v], acc[A.NB + v]);
+                            }
+                        group_sync(bar);
+                    }
                 }
                 if (t == 0) {
                     if (!cfinite(Sop) || !cfinite(S1p) || !cfinite(S2p)) raise_status(A.status, QCS_ERR_NONFINITE);
@@ -343,11 +536,17 @@ size_t energy_group_layout(EnergyArgs &A) {
     A.off_B = (int)o;
     o = align16(o + (size_t)T * sizeof(cd));
     A.off_NZ = (int)o;
-    o = align16(o + (size_t)NB * T * sizeof(cd));
-    // shared region: Ut rows, then the recursion vectors, then X'
+    // node matrices; in the block form the complements' inverses, then P^-1, E and S0
+    const int d2 = m - A.ne, Tn = tri_count(d2), To = tri_count(A.ne);
+    size_t nz = (size_t)NB * T;
+    const size_t zoff = (size_t)(T > NB * Tn ? T : NB * Tn);
+    if (zoff + To + (size_t)A.ne * d2 + Tn > nz) nz = zoff + To + (size_t)A.ne * d2 + Tn;
+    o = align16(o + nz * sizeof(cd));
+    // shared region: Ut rows, then the recursion vectors, then X' (then W, G, V, H)
     size_t r = (size_t)m * (2 * n + 1);
     if ((size_t)n * ld_ut(n) > r) r = (size_t)n * ld_ut(n);
     if ((size_t)4 * NB * m > r) r = (size_t)4 * NB * m;
+    if ((size_t)d2 * (m + A.ne) + 2 * (size_t)Tn > r) r = (size_t)d2 * (m + A.ne) + 2 * (size_t)Tn;
     A.off_X1 = (int)o;
     A.off_g1 = (int)o;
     A.off_g2 = (int)(o + (size_t)NB * m * sizeof(cd));
@@ -382,6 +581,8 @@ size_t energy_group_layout(EnergyArgs &A) {
     o = align16(o + (size_t)2 * sizeof(cd));
     A.off_acc = (int)o;
     o = align16(o + (size_t)2 * kMaxNBG * sizeof(cd));
+    A.off_scr = (int)o;
+    o = align16(o + sizeof(SharedScratch));
     return o;
 }
 
@@ -516,18 +717,28 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     qcs_node_plan plan;
     if (n < 2 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1) || nchol < 0) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
-    const double m = 2.0 * n - ne, n2 = 2.0 * n, T = m * (m - 1) / 2;
-    double f = qcs_overlap_flops_nev(n, ne, plan.nev);  // T, B and the Pfaffians
-    double inv = 0.0;                                      // backward inverse per node
-    for (int r = (int)m; r > 2; r -= 2) inv += 16.0 * (r - 2) * (r - 2) + 20.0 * (r - 2);
-    f += inv * plan.nev;
+    // the block form (occupied block shared by the nodes), as the kernel runs it
+    const int mi = 2 * n - ne, d2i = mi - ne;
+    const double m = mi, n2 = 2.0 * n, T = m * (m - 1) / 2, d2 = d2i, Tn = d2 * (d2 - 1) / 2,
+                 To = ne * (ne - 1) / 2.0, nev = plan.nev;
+    auto bstep = [](int rv) { return 16.0 * rv * rv + 20.0 * rv; };  // one backward step
+    double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);        // dense T, B, full eliminations
+    f -= (nev - 1.0) * qcs_pf_elim_flops(mi, d2i);                    // ... the occupied steps once
+    for (int rv = d2i; rv <= mi - 2; rv += 2) f += bstep(rv);        // F0 = [[P^-1, 0], [0, 0]]
+    f += 8.0 * ne * d2 * (ne - 1);                                    // E = P^-1 B_oe
+    double inv = 0.0;                                                 // each complement's inverse
+    for (int rv = d2i - 2; rv > 0; rv -= 2) inv += bstep(rv);
+    f += inv * nev;
     const double xprime = 4.0 * m * n2 * n2;      // X' = (K ell) Q'^T, complex x real
     const double aprime = 8.0 * T * 2.0 * n2;     // A' = X' J X^T + X J X'^T (upper triangle)
     const double sacc = 8.0 * T * n2;             // X' J X'^T
-    const double t1 = 8.0 * T;                    // tr(A^-1 A') per node
-    const double t2 = 8.0 * (m * (m + 1) / 2) * 2.0 * m;  // P_ab, P_ba per unordered pair, per node
-    f += nchol * (xprime + aprime + sacc + plan.nev * (t1 + t2));
-    f += has_h * (xprime + aprime + plan.nev * t1);
-    f += xprime + aprime + plan.nev * t1;  // the A'' pass
+    const double wg = 8.0 * m * d2 * ne + 8.0 * Tn * ne + 8.0 * To;  // W = A'F, G = F^T W, tr(P^-1 A'_oo)
+    const double vh = 8.0 * ne * d2 * (ne - 1) + 8.0 * Tn * ne       // V = P^-1 W_o, H = -W_o^T V
+                      + 8.0 * (ne * (ne + 1) / 2.0) * 2.0 * (ne - 1);  // tr((P^-1 A'_oo)^2)
+    const double t1 = 8.0 * Tn;                                       // tr(Z_k G) per node
+    const double t2 = 8.0 * Tn + 8.0 * (d2 * (d2 + 1) / 2) * 2.0 * (d2 - 1);  // tr(Z_k H), tr((Z_k G)^2)
+    const double npass = nchol + has_h + 1.0;                         // operators and the A'' pass
+    f += npass * (xprime + aprime + wg + nev * t1);
+    f += nchol * (sacc + vh + nev * t2);
     return f;
 }
