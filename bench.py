@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -140,7 +141,7 @@ CSRC = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc")
 # Source files each timed kernel is compiled from; the committed DRAM figure of a
 # kernel is used only while all of them are unchanged.
 KERNEL_SOURCES = {
-    "pair_overlap_kernel": ["qcs_overlap.cu", "qcs_pair.cuh", "qcs_common.cuh"],
+    "pair_overlap_kernel": ["qcs_overlap.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
     "split_pair_kernel": ["qcs_split.cu", "qcs_pair.cuh", "qcs_tc.cuh", "qcs_common.cuh"],
     "grad_pair_kernel": ["qcs_grad.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
     "rdm_syrk_kernel": ["qcs_rdm.cu"],
@@ -149,9 +150,14 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_sha(kernel: str) -> str:
+    """Hash of the kernel's sources with comments and blank space removed, so that a
+    traffic record stays valid across comment edits and lapses with any code change."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(CSRC, f), "rb").read())
+        src = open(os.path.join(CSRC, f), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -8,28 +8,34 @@
 //     U^T, occupied rows / sqrt2), Qt the snapshot's complexified sign-folded
 //     rows.  Row j of T is the selected row of W^* M_phi Q'^T for an occupied
 //     mode j; for an empty mode the two selected real rows are (Re T_j, -Im T_j).
+//     The walker prep leaves the orbitals in echelon form, so T skips the exact
+//     zeros of Ut; at n = 16 each lane holds one snapshot row in registers and
+//     takes three real products per complex multiply-add (build_T_reg).
 //  2. B^(s)_ab = sum_k X_a,2k X_b,2k+1 - X_a,2k+1 X_b,2k  (X = selected rows),
 //     i.e. X J X^T with J the canonical skew form (C_b was folded into Qt).
 //     Computed as three classes (complex x complex, complex x real, real x real)
 //     so that every FP64 instruction runs with all 32 lanes busy.
-//  3. pf(B + conj(z_k) D) at the evaluated roots of unity z_k, D = C_0^(s)
-//     (pf(A(z_k)) = z_k^{m/2} pf(B + conj(z_k) D) on |z| = 1): a warp runs
-//     Parlett-Reid elimination with partial pivoting on several node matrices
-//     in lockstep.  The matrices (packed upper triangles) stay in shared memory;
-//     the elimination keeps the original index order (no physical swaps) and
-//     tracks the sign (-1)^{(position of the pivot) - 1}; every rank-2 update
-//     step spreads (node, entry) items over the 32 lanes.  Pivot magnitudes are
-//     compared as integer keys (no FP64 work).
-//  4. S_p = sum_k gamma_k pf_k, where gamma_k folds the inverse DFT, the
-//     inverse-channel weights C(2n,2x)/C(n,x) and, by default, the palindromic
-//     symmetry c_{n-x} = c_x of parity +1 snapshots (only floor(N/2)+1 of the
-//     N nodes are evaluated; parity -1 snapshots are exactly zero and skipped).
+//  3. pf(B + w_k D) at the node plan's evaluation points w_k (a Gauss rule on the
+//     unit circle by default, roots of unity on request), D = C_0^(s): the node
+//     matrices differ only in their empty x empty block, so the occupied block is
+//     eliminated once (schur_occupied, pivots inside that block) and each node's
+//     2d x 2d complement is eliminated by Parlett-Reid with partial pivoting, the
+//     nodes in lockstep.  The matrices (packed upper triangles) stay in shared
+//     memory; the elimination keeps the original index order (no physical swaps)
+//     and tracks the sign of each pivot's position; every rank-2 update step
+//     spreads (node, entry) items over the lanes.  Pivot magnitudes are compared
+//     as integer keys (no FP64 work).
+//  4. S_p = sum_k gamma_k pf_k, where gamma_k folds the node plan's weights, the
+//     inverse-channel weights C(2n,2x)/C(n,x) and the palindromic symmetry
+//     c_{n-x} = c_x of parity +1 snapshots (parity -1 snapshots are exactly zero
+//     and skipped).
 //
-// Tiles are (walker, chunk of snapshots); each warp owns a tile at a time and
-// writes one partial sum per tile, reduced in a fixed order afterwards, so the
-// result does not depend on scheduling.
+// Tiles are (walker, chunk of snapshots) owned by a block of four warps; each warp
+// (n <= 16) or each pair of warps (n > 16, 64-thread groups) takes every
+// snapshot of the tile in turn and writes one partial sum per warp slot, reduced
+// in a fixed order afterwards, so the result does not depend on scheduling.
 #include "qcs_internal.h"
-#include "qcs_pair.cuh"
+#include "qcs_group.cuh"
 
 namespace {
 
@@ -37,7 +43,9 @@ namespace {
 struct PairArgs {
     int n, ne, m, d, nev, NB, all, chunk, nchunks;
     int reg;          // n = 16: snapshot rows in registers, T by three real products (build_T_reg)
+    int grp;          // n > 16: two warps share a pair (64-thread groups, qcs_group.cuh)
     int vm;           // entries per Gauss-vector buffer (the full matrix or NB node complements)
+    int off_kh, off_ph, off_scr, gz;  // group path: pivot history, scratch, S0 offset (entries) in Ns
     int64_t W, P;
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
@@ -59,7 +67,10 @@ struct PairArgs {
 // One tile of system A: walker w = tile / nchunks, the tile's snapshots spread
 // over the block's warps; each warp writes one partial sum.  Every thread of the
 // block calls this (it contains block barriers around the shared walker rows).
-__device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned char *wbase, cd *Uts,
+// GRP: the launch holds a system on the two-warp group path (n > 16); without one
+// the group code is left out of the kernel and its registers.
+template <bool GRP>
+__device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned char *wbase, size_t wstride, cd *Uts,
                          const uint16_t *tab, int warp, int wpb, int lane) {
     const int n = A.n, n2 = 2 * n;
     cd *Rg = reinterpret_cast<cd *>(wbase);
@@ -95,6 +106,82 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     }
     __syncthreads();
     cd acc = cmk(0.0, 0.0);
+    if (GRP && A.grp) {
+        // two warps per pair: group g = warps 2g, 2g+1 with the two warp regions as its
+        // workspace; group g takes every (wpb/2)-th snapshot of the tile
+        const int g = warp >> 1, t = ((warp & 1) << 5) + lane, bar = 1 + g, ng = wpb >> 1;
+        unsigned char *gb = wbase - (size_t)(warp & 1) * wstride;
+        cd *gQs = reinterpret_cast<cd *>(gb);
+        cd *gTs = reinterpret_cast<cd *>(gb + A.off_T);
+        cd *gNs = reinterpret_cast<cd *>(gb);
+        cd *gSc = gNs + A.gz;
+        cd *gBs = reinterpret_cast<cd *>(gb + A.off_B);
+        cd *gUv = reinterpret_cast<cd *>(gb + A.off_U);
+        cd *gVv = reinterpret_cast<cd *>(gb + A.off_V);
+        cd *gpf = reinterpret_cast<cd *>(gb + A.off_pf);
+        cd *ginvh = reinterpret_cast<cd *>(gb + A.off_inv);
+        int *gpos = reinterpret_cast<int *>(gb + A.off_int);
+        uint8_t *gacth = gb + A.off_act;
+        uint8_t *gkh = gb + A.off_kh;
+        uint8_t *gph = gb + A.off_ph;
+        SharedScratch *gscr = reinterpret_cast<SharedScratch *>(gb + A.off_scr);
+        const int m = A.m, ne = A.ne, d2 = A.m - A.ne, Tn = tri_count(d2);
+        if (p0 < L) {
+            const cd prefw = A.pref[w];
+            for (int64_t pq = p0 + g; pq < p1; pq += ng) {
+                const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+                const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
+                group_sync(bar);
+                if (gq && gq[0] != 0xFF) {
+                    build_T_gather(n, Uts, gq, gTs, t, kGroup);
+                } else {
+                    for (int h = 0; h < 2; ++h) {  // T by column halves: half of Qt staged at a time
+                        load_Qt_rows(n, A.Qt + (q * n2 + (int64_t)h * n) * n, gQs, t, kGroup);
+                        group_sync(bar);
+                        build_T_echelon_half(n, ne, Uts, gQs, gTs, h * n, t, kGroup);
+                        group_sync(bar);
+                    }
+                }
+                group_sync(bar);
+                build_B(n, ne, gTs, gBs, tab, t, kGroup);
+                group_sync(bar);
+                cd S = cmk(0.0, 0.0);
+                if (shared_factor(m, ne, gBs, gNs, gUv, gVv, ginvh, gacth, gkh, gph, gscr, tab, t, bar)) {
+                    const cd pf0 = gscr->pf0;
+                    for (int e = t; e < Tn; e += kGroup) {
+                        int a, b;
+                        pair_of(tab, e, a, b);
+                        gSc[e] = gNs[tri_index(ne + a, ne + b)];
+                    }
+                    group_sync(bar);
+                    for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
+                        const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+                        node_factor(d2, 0, A.wnode + k0, nb, gSc, gNs, gUv, gVv, gpf, ginvh, gpos, gacth, gkh, gph,
+                                    tab, t, bar, nullptr);
+                        if (t == 0)
+                            for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], gpf[v]);
+                        group_sync(bar);
+                    }
+                    S = cmul(S, pf0);
+                } else {  // the rare full eliminations: one node matrix per round
+                    for (int k0 = 0; k0 < A.nev; ++k0) {
+                        node_factor(m, ne, A.wnode + k0, 1, gBs, gNs, gUv, gVv, gpf, ginvh, gpos, gacth, gkh, gph,
+                                    tab, t, bar, nullptr);
+                        if (t == 0) cfma(S, A.gamma[k0], gpf[0]);
+                        group_sync(bar);
+                    }
+                }
+                if (t == 0) {
+                    if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
+                    acc = cadd(acc, S);
+                    if (A.per_pair) A.per_pair[w * A.P + q] = cmul(prefw, S);
+                }
+            }
+        }
+        // one partial per warp slot: the group's sum in its first warp's slot, zero in the second
+        if (lane == 0) A.partial[(w * A.nchunks + ch) * wpb + warp] = (warp & 1) ? cmk(0.0, 0.0) : acc;
+        return;
+    }
     if (p0 < L) {
         const cd prefw = A.pref[w];
         for (int64_t pq = p0 + warp; pq < p1; pq += wpb) {
@@ -152,7 +239,8 @@ struct BatchArgs {
     PairArgs sys[QCS_MAX_SYSTEMS];         // in queue order
 };
 
-__global__ void __launch_bounds__(128, 3) pair_overlap_kernel(const __grid_constant__ BatchArgs B) {
+template <bool GRP>
+__global__ void __launch_bounds__(128, GRP ? 2 : 3) pair_overlap_kernel(const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long next_tile;
     const int lane = threadIdx.x & 31;
@@ -174,7 +262,7 @@ __global__ void __launch_bounds__(128, 3) pair_overlap_kernel(const __grid_const
         const int64_t local = t - (s > 0 ? B.tile_end[s - 1] : 0);
         const PairArgs &A = B.sys[s];
         const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
-        run_tile(A, local, L, wbase, Uts, tab, warp, wpb, lane);
+        run_tile<GRP>(A, local, L, wbase, B.warp_bytes, Uts, tab, warp, wpb, lane);
     }
 }
 
@@ -200,7 +288,10 @@ namespace {
 // region holds the staged snapshot rows and T (T alone on the register path), then
 // the node matrices: one full copy of B (shared elimination; the rare full
 // eliminations, one node per round) or NB complements of 2d x 2d.
+size_t pair_group_layout(PairArgs &A, int NB);
+
 size_t pair_warp_layout(PairArgs &A, int NB) {
+    if (A.grp) return align16((pair_group_layout(A, NB) + 1) / 2);  // a group spans two warp regions
     const int n = A.n, m = A.m, T = tri_count(m), d2 = m - A.ne;
     const size_t qbytes = A.reg ? 0 : (size_t)2 * n * ld_qt(n) * sizeof(cd);
     size_t R = qbytes + (size_t)n * ld_t(n) * sizeof(cd);
@@ -228,6 +319,45 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     return o;
 }
 
+// Workspace of one 64-thread group (two warp regions) on the group path: half of the
+// snapshot rows and T, aliased by the node matrices (a full copy of B for the shared
+// elimination, NB complements, S0 after them), then B, the Gauss vectors and the
+// step history of qcs_group.cuh; returns bytes per group.
+size_t pair_group_layout(PairArgs &A, int NB) {
+    const int n = A.n, m = A.m, ne = A.ne, T = tri_count(m), d2 = m - ne, Tn = tri_count(d2), S = m / 2;
+    const size_t qbytes = (size_t)n * ld_qt(n) * sizeof(cd);
+    A.off_T = (int)align16(qbytes);
+    size_t R = (size_t)A.off_T + (size_t)n * ld_t(n) * sizeof(cd);
+    A.gz = T > NB * Tn ? T : NB * Tn;
+    if ((size_t)(A.gz + Tn) * sizeof(cd) > R) R = (size_t)(A.gz + Tn) * sizeof(cd);
+    A.vm = m > NB * d2 ? m : NB * d2;
+    size_t o = align16(R);
+    A.off_B = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_U = (int)o;
+    o = align16(o + (size_t)A.vm * sizeof(cd));
+    A.off_V = (int)o;
+    o = align16(o + (size_t)A.vm * sizeof(cd));
+    A.off_pf = (int)o;
+    o = align16(o + (size_t)kMaxNBG * sizeof(cd));
+    const int hs = S > NB * (d2 / 2) ? S : NB * (d2 / 2);  // history steps
+    A.off_inv = (int)o;
+    o = align16(o + (size_t)hs * sizeof(cd));
+    A.off_int = (int)o;
+    o = align16(o + (size_t)kMaxNBG * sizeof(int));
+    size_t ha = (size_t)(S + 1) * m;  // active lists: full matrix, one node
+    if ((size_t)NB * (d2 / 2 + 1) * d2 > ha) ha = (size_t)NB * (d2 / 2 + 1) * d2;
+    A.off_act = (int)o;
+    o = align16(o + ha);
+    A.off_kh = (int)o;
+    o = align16(o + (size_t)hs);
+    A.off_ph = (int)o;
+    o = align16(o + (size_t)hs);
+    A.off_scr = (int)o;
+    o = align16(o + sizeof(SharedScratch));
+    return o;
+}
+
 }  // namespace
 
 int qcs_pair_warps_per_block() { return 4; }
@@ -248,6 +378,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.W = L.W;
     A.P = L.P;
     A.reg = L.n == 16;
+    A.grp = L.n > 16;
     const int n = A.n, m = A.m, T = tri_count(m);
     const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
@@ -256,16 +387,17 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     // count (balanced rounds, at most kMaxNB) for which three blocks (register
     // path) or two blocks fit on an SM.
     int NB = 1;
+    const int nbmax = A.grp ? kMaxNBG : kMaxNB;
     if (L.config > 0) {
         NB = L.config < A.nev ? L.config : A.nev;
-        if (NB > kMaxNB) NB = kMaxNB;
+        if (NB > nbmax) NB = nbmax;
         while (NB > 1 && (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * pair_warp_layout(A, NB) > ctx->smem_optin)
             --NB;
     } else {
         const size_t sm_budget = ctx->smem_optin;
         for (int rounds = 1; rounds <= A.nev; ++rounds) {
             int nb = (A.nev + rounds - 1) / rounds;
-            if (nb > kMaxNB) continue;
+            if (nb > nbmax) continue;
             size_t blk = (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * pair_warp_layout(A, nb) + 1024;
             if ((A.reg ? 3 : 2) * blk <= sm_budget + 1024) {
                 NB = nb;
@@ -334,9 +466,12 @@ qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launc
     size_t smem = (size_t)B.tab_bytes + B.ut_bytes + (size_t)wpb * B.warp_bytes;
     if (smem + 64 > ctx->smem_optin)  // + the kernel's static tile index
         return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "batched kernel: shared memory too large");
-    if (qcs_set_smem(ctx, (const void *)pair_overlap_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    bool grp = false;
+    for (int q = 0; q < nsys; ++q) grp |= B.sys[q].grp != 0;
+    const void *kfn = grp ? (const void *)pair_overlap_kernel<true> : (const void *)pair_overlap_kernel<false>;
+    if (qcs_set_smem(ctx, kfn, smem) != QCS_OK) return QCS_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_overlap_kernel, wpb * 32, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, wpb * 32, smem) !=
             cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
@@ -345,7 +480,8 @@ qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launc
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "batched counter reset");
     qcs_prof_begin(ctx, st);
-    pair_overlap_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(B);
+    if (grp) pair_overlap_kernel<true><<<(unsigned)blocks, wpb * 32, smem, st>>>(B);
+    else pair_overlap_kernel<false><<<(unsigned)blocks, wpb * 32, smem, st>>>(B);
     qcs_prof_end(ctx, st);
     return qcs_check_launch(ctx, "pair_overlap_kernel");
 }

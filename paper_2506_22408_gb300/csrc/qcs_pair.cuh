@@ -107,6 +107,25 @@ __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const dou
 }
 #undef QCS_T3M
 
+// Columns c0 .. c0+n-1 of T from n staged rows of Qt (Qs rows 0 .. n-1 hold rows
+// c0 .. c0+n-1), walker rows in echelon form as in build_T_echelon.
+__device__ inline void build_T_echelon_half(int n, int ne, const cd *__restrict__ Uts, const cd *__restrict__ Qs,
+                                            cd *__restrict__ Ts, int c0, int lane, int nthr) {
+    const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
+    for (int e = lane; e < n * n; e += nthr) {
+        const int j = e / n, c = e - j * n;
+        const cd *ur = Uts + j * lu, *qr = Qs + c * lq;
+        cd s = cmk(0.0, 0.0);
+        if (j < ne) {
+            for (int k = j; k < n; ++k) cfma(s, ur[k], qr[k]);
+        } else {
+            for (int k = 0; k < ne; ++k) cfma(s, ur[k], qr[k]);
+            for (int k = j; k < n; ++k) cfma(s, ur[k], qr[k]);
+        }
+        Ts[j * lt + c0 + c] = s;
+    }
+}
+
 // x * ph for a phase code ph = 0..3 (1, i, -1, -i): a swap of the parts and sign
 // flips of the bit patterns, no floating-point arithmetic.
 __device__ __forceinline__ cd mul_phase(cd x, unsigned ph) {
@@ -133,6 +152,15 @@ __device__ inline void build_T_gather(int n, const cd *__restrict__ Uts, const u
 __device__ inline void load_Qt(int n, const cd *__restrict__ Qg, cd *__restrict__ Qs, int lane, int nthr = 32) {
     const int lq = ld_qt(n);
     for (int e = lane; e < 2 * n * n; e += nthr) {
+        int c = e / n, k = e - c * n;
+        Qs[c * lq + k] = Qg[e];
+    }
+}
+
+// Stage n consecutive rows of a snapshot's Qt (n x n, global) into padded shared rows.
+__device__ inline void load_Qt_rows(int n, const cd *__restrict__ Qg, cd *__restrict__ Qs, int lane, int nthr) {
+    const int lq = ld_qt(n);
+    for (int e = lane; e < n * n; e += nthr) {
         int c = e / n, k = e - c * n;
         Qs[c * lq + k] = Qg[e];
     }

@@ -180,6 +180,28 @@ def test_structured_walkers(ctx, n, ne):
         assert abs(ov[3]) <= 1e-12 * sc[0].mean()
 
 
+@pytest.mark.parametrize("n,ne", [(20, 10), (24, 6), (20, 2), (18, 4), (16, 8), (12, 4)])
+def test_unit_walkers_signed_permutations(ctx, n, ne):
+    """Unit-vector walkers against signed-permutation snapshots: the occupied block of
+    the node matrices is often exactly zero or singular, so the shared elimination gives
+    way to the full one per node (n > 16 runs on two-warp groups, n = 16 on the
+    register path); exact zeros and singular node matrices must still give the oracle's
+    pair values."""
+    rng = np.random.default_rng(7 * n + ne)
+    P = 64
+    Q = synth.signed_permutation(rng, 2 * n, P)
+    b = synth.parity_consistent_bits(rng, Q)
+    eye = np.eye(n, dtype=complex)
+    R = np.triu(rng.standard_normal((ne, ne)) + 1j * rng.standard_normal((ne, ne))) + 2 * np.eye(ne)
+    Phi = np.stack([eye[:, rng.permutation(n)[:ne]] @ R for _ in range(3)] + [synth.walkers(rng, n, ne, 1)[0]])
+    ov, pp, par, st = run_gpu(ctx, dict(Phi=Phi, Q=Q, b=b))
+    assert st == 0
+    oo, opp, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    floor = 1e-10 * np.abs(Phi).max() ** 4
+    assert np.all(np.abs(pp - opp) <= TOL * sc + floor)
+    assert np.all(np.abs(ov - oo) <= TOL * sc.mean(axis=1) + floor)
+
+
 def test_argument_errors(ctx):
     n = 6
     Q = torch.from_numpy(synth.haar_orthogonal(np.random.default_rng(0), 2 * n, 4)).cuda()
