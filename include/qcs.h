@@ -391,6 +391,11 @@ qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
  * orbitals are first rotated to echelon form (a reflection of the occupied
  * columns changes det R by its sign, one of the complement changes nothing),
  * which makes ne(ne-1)/2 + d(d-1)/2 entries of U exact zeros that T skips.
+ * At n = 16 the occupied orbitals are further taken in reduced form [I; X]
+ * (an invertible change of basis, det folded into det R), leaving one non-zero
+ * among the first ne entries of each occupied row; walkers whose X would exceed
+ * 16 in magnitude (about 3 % of random walkers) keep the echelon form and do
+ * ne(ne-1)/2 more products than counted.
  * The node matrices differ only in their empty x empty block, so the occupied
  * block is eliminated once per pair and each node then costs a 2d x 2d
  * Pfaffian; the count is that of this path (pairs whose occupied block would

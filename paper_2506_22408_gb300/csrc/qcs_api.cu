@@ -329,6 +329,7 @@ struct OverlapWork {
     cd *Ut, *pref, *partial;
     unsigned long long *counter;
     float *Mhi, *Mlo;  // split precision: walker operand slabs
+    int *mode;         // FP64 path: per-walker form of the occupied rows (walker prep)
     int nchunks, nparts;
     bool split;
 };
@@ -363,8 +364,9 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
     size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nparts);
     size_t b_slab = split ? align16(qcs_split_walker_bytes(W)) : 0;
+    size_t b_mode = split ? 0 : align16(sizeof(int) * (size_t)(W > 0 ? W : 1));
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab + b_mode, &base);
     if (ws != QCS_OK) return ws;
     char *pb = (char *)base;
     wk->counter = (unsigned long long *)pb;
@@ -373,8 +375,11 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     wk->partial = (cd *)(pb + 16 + b_ut + b_pref);
     wk->Mhi = split ? (float *)(pb + 16 + b_ut + b_pref + b_part) : nullptr;
     wk->Mlo = split ? (float *)(pb + 16 + b_ut + b_pref + b_part + b_slab) : nullptr;
+    // the reduced form of the occupied rows serves the FP64 pair kernel; the split path's
+    // TF32 operands keep the orthonormal echelon form
+    wk->mode = split ? nullptr : (int *)(pb + 16 + b_ut + b_pref + b_part + 2 * b_slab);
     return qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, wk->Ut, wk->pref, st, nullptr, nullptr,
-                                  true);
+                                  true, wk->mode);
 }
 
 }  // namespace
@@ -403,6 +408,7 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
     L.nchunks = wk.nchunks;
     L.Ut = wk.Ut;
     L.pref = wk.pref;
+    L.mode = wk.mode;
     L.s = s;
     L.partial = wk.partial;
     L.per_pair = (cd *)d_per_pair;
@@ -435,7 +441,7 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
     if (opts) o = *opts;
     if (o.precision != QCS_FP64) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "batched calls are FP64");
     qcs_pair_launch Ls[QCS_MAX_SYSTEMS];
-    size_t off[QCS_MAX_SYSTEMS][3];
+    size_t off[QCS_MAX_SYSTEMS][4];
     size_t total = 16;  // the tile counter first
     const int wpb = qcs_pair_warps_per_block();
     for (int i = 0; i < nsys; ++i) {
@@ -471,6 +477,8 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         total += align16(sizeof(cd) * (size_t)y.W);
         off[i][2] = total;
         total += align16(sizeof(cd) * (size_t)y.W * L.nchunks * wpb);
+        off[i][3] = total;
+        total += align16(sizeof(int) * (size_t)(y.W > 0 ? y.W : 1));
     }
     void *base = nullptr;
     qcs_status r = qcs_workspace(ctx, total, &base);
@@ -480,8 +488,10 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         Ls[i].Ut = (cd *)(pb + off[i][0]);
         Ls[i].pref = (cd *)(pb + off[i][1]);
         Ls[i].partial = (cd *)(pb + off[i][2]);
+        int *mode = (int *)(pb + off[i][3]);
+        Ls[i].mode = mode;
         r = qcs_launch_walker_prep(ctx, Ls[i].n, Ls[i].ne, Ls[i].W, (const cd *)systems[i].d_walkers,
-                                   (cd *)Ls[i].Ut, (cd *)Ls[i].pref, st, nullptr, nullptr, true);
+                                   (cd *)Ls[i].Ut, (cd *)Ls[i].pref, st, nullptr, nullptr, true, mode);
         if (r != QCS_OK) return r;
     }
     r = qcs_launch_pairs_batched(ctx, nsys, Ls, (unsigned long long *)pb, st);
@@ -638,7 +648,10 @@ double qcs_pf_elim_flops(int m, int stop) {
 // Parts of the count: [0] congruence T, [1] covariance B, [2] Pfaffian eliminations.
 static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, double *part) {
     const int d = n - ne, m = 2 * n - ne;
-    const double zeros = overlap_kernel ? tri_count(ne) + tri_count(d) : 0.0;  // skipped entries of Ut
+    // skipped entries of Ut: echelon form, or at n = 16 the reduced form of the occupied
+    // rows ([I; X], all but one of the columns k < ne zero)
+    const double occ_zeros = (overlap_kernel && n == 16) ? (double)ne * (ne - 1) : (double)tri_count(ne);
+    const double zeros = overlap_kernel ? occ_zeros + tri_count(d) : 0.0;
     const double macs = 2.0 * n * ((double)n * n - zeros);   // complex multiply-adds of T
     if (overlap_kernel && n == 16)
         // three real products per complex multiply-add, then Re = p1 - p2 and

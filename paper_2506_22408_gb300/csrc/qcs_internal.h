@@ -84,7 +84,8 @@ double qcs_overlap_flops_nev(int n, int ne, int nev, bool overlap_kernel = false
 double qcs_pf_elim_flops(int m, int stop);  // Pfaffian elimination steps from r = m down to r > stop
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr, bool echelon = false);
+                                  cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr, bool echelon = false,
+                                  int *mode = nullptr);
 
 struct qcs_grad_launch {
     int n, ne;
@@ -113,6 +114,7 @@ struct qcs_pair_launch {
     int chunk, nchunks;
     const cd *Ut;
     const cd *pref;
+    const int *mode;  // per walker: 1 = occupied rows in reduced form (walker prep), or null
     const qcs_snapshots *s;
     cd *partial;     // W x nchunks x warps-per-block
     cd *per_pair;    // W x P or null

@@ -126,6 +126,7 @@ extern "C" qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double
     L.nchunks = nchunks;
     L.Ut = Ut;
     L.pref = pref;
+    L.mode = nullptr;  // echelon form only (no scratch for the per-walker form flags)
     L.s = &s;
     L.partial = partial;
     L.per_pair = nullptr;

@@ -53,6 +53,7 @@ struct PairArgs {
     int off_T, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // byte offsets in a warp region
     const cd *Ut;
     const cd *pref;
+    const int *wmode;  // per walker: occupied rows in reduced form (register path), or null
     const cd *Qt;
     const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
     const int *idx;
@@ -106,6 +107,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     }
     __syncthreads();
     cd acc = cmk(0.0, 0.0);
+    const bool redw = A.wmode != nullptr && A.wmode[w] != 0;
     if (GRP && A.grp) {
         // two warps per pair: group g = warps 2g, 2g+1 with the two warp regions as its
         // workspace; group g takes every (wpb/2)-th snapshot of the tile
@@ -191,7 +193,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             if (gq && gq[0] != 0xFF) {
                 build_T_gather(n, Uts, gq, Ts, lane);  // signed permutation: no products
             } else if (A.reg) {
-                build_T_reg<16>(A.ne, Uts, Uss, A.Qt + q * n2 * n, Ts, lane);
+                build_T_reg<16>(A.ne, Uts, Uss, A.Qt + q * n2 * n, Ts, lane, redw);
             } else {
                 load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
                 __syncwarp();
@@ -409,6 +411,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.warp_bytes = (int)pair_warp_layout(A, NB);
     A.Ut = L.Ut;
     A.pref = L.pref;
+    A.wmode = L.mode;
     A.Qt = L.s->Qt;
     A.gth = L.s->gth;
     A.idx = L.s->idx;

@@ -62,8 +62,10 @@ __device__ inline void build_T_echelon(int n, int ne, const cd *__restrict__ Uts
 // three real products (Gauss's 3-multiplication form): with s = re + im of both
 // factors, Re = sum ur qr - sum ui qi and Im = sum us qs - sum ur qr - sum ui qi, so
 // the sums us of the walker rows (Uss, per block) and qs of the snapshot row (here)
-// are formed once.  The skipped zeros follow build_T_echelon; the row loop is
-// warp-uniform and enters the unrolled k sequences by a switch, so the register
+// are formed once.  The skipped zeros follow build_T_echelon, or for a walker in
+// reduced form (occupied rows [I; X]: row j < ne has its one entry at column j
+// among the columns k < ne) that single entry and the columns k >= ne; the row loop
+// is warp-uniform and enters the unrolled k sequences by a switch, so the register
 // arrays are indexed by constants.
 #define QCS_T3M(K)                            \
     case K: {                                 \
@@ -72,9 +74,17 @@ __device__ inline void build_T_echelon(int n, int ne, const cd *__restrict__ Uts
         p2 = fma(u_.y, qi[K], p2);            \
         p3 = fma(us[K], qs[K], p3);           \
     }
+#define QCS_T3M1(K)                           \
+    case K: {                                 \
+        const cd u_ = ur[K];                  \
+        p1 = fma(u_.x, qr[K], p1);            \
+        p2 = fma(u_.y, qi[K], p2);            \
+        p3 = fma(us[K], qs[K], p3);           \
+        break;                                \
+    }
 template <int N>
 __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const double *__restrict__ Uss,
-                                   const cd *__restrict__ Qg, cd *__restrict__ Ts, int lane) {
+                                   const cd *__restrict__ Qg, cd *__restrict__ Ts, int lane, bool reduced) {
     static_assert(N == 16, "one lane per column of T: 2N must be the warp width");
     const int lu = ld_ut(N), lt = ld_t(N);
     double qr[N], qi[N], qs[N];
@@ -90,6 +100,16 @@ __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const dou
         const cd *ur = Uts + j * lu;
         const double *us = Uss + j * lu;
         double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        int kstart = j;
+        if (j < ne && reduced) {
+            switch (j) {  // the single entry among the columns k < ne
+                QCS_T3M1(0) QCS_T3M1(1) QCS_T3M1(2) QCS_T3M1(3) QCS_T3M1(4) QCS_T3M1(5) QCS_T3M1(6) QCS_T3M1(7)
+                QCS_T3M1(8) QCS_T3M1(9) QCS_T3M1(10) QCS_T3M1(11) QCS_T3M1(12) QCS_T3M1(13) QCS_T3M1(14)
+                QCS_T3M1(15)
+                default: break;
+            }
+            kstart = ne;
+        }
         if (j >= ne) {
             switch (ne - 1) {  // k = ne-1 down to 0
                 QCS_T3M(15) QCS_T3M(14) QCS_T3M(13) QCS_T3M(12) QCS_T3M(11) QCS_T3M(10) QCS_T3M(9) QCS_T3M(8)
@@ -97,7 +117,7 @@ __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const dou
                 default: break;
             }
         }
-        switch (j) {  // k = j up to N-1
+        switch (kstart) {  // k = kstart up to N-1
             QCS_T3M(0) QCS_T3M(1) QCS_T3M(2) QCS_T3M(3) QCS_T3M(4) QCS_T3M(5) QCS_T3M(6) QCS_T3M(7)
             QCS_T3M(8) QCS_T3M(9) QCS_T3M(10) QCS_T3M(11) QCS_T3M(12) QCS_T3M(13) QCS_T3M(14) QCS_T3M(15)
             default: break;
@@ -106,6 +126,7 @@ __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const dou
     }
 }
 #undef QCS_T3M
+#undef QCS_T3M1
 
 // Columns c0 .. c0+n-1 of T from n staged rows of Qt (Qs rows 0 .. n-1 hold rows
 // c0 .. c0+n-1), walker rows in echelon form as in build_T_echelon.

@@ -19,13 +19,20 @@
 // the completion to lower-triangular form, det R taking the reflections' sign:
 // row j < ne of Ut is then zero in columns k < j, row ne + j' zero in columns
 // [ne, ne + j'), ne(ne-1)/2 + d(d-1)/2 exact zeros that the congruence skips.
+//
+// Reduced form (mode != null): the alternation holds for any invertible W, so the
+// occupied orbitals may also be taken as U_occ L^{-1} = [I; X], L the (lower
+// triangular) top block, with det R multiplied by det L.  Row j < ne of Ut then has
+// one entry 1/sqrt2 at column j and zeros in the other columns k < ne.  A walker
+// whose X would exceed 16 in magnitude (an ill-conditioned top block) keeps the
+// echelon form; mode[w] records which (1: reduced).
 #include "qcs_internal.h"
 
 namespace {
 
 __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restrict__ Phi, cd *__restrict__ Ut,
                                    cd *__restrict__ pref, cd *__restrict__ Uout, cd *__restrict__ Rout, int echelon,
-                                   unsigned *status) {
+                                   int *__restrict__ mode, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -111,6 +118,36 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
                 }
             }
             if (nref & 1) detR = cneg(detR);  // det R' = conj(det W) det R, det W = (-1)^nref
+            if (mode) {
+                // X L = U_bot by back substitution over the columns (lane = row of U_bot)
+                bool ok = true;
+                for (int j = 0; j < ne; ++j) ok &= cmul(U[j * n + j], cconj(U[j * n + j])).x > 0.0;
+                cd xr[QCS_MAX_N];
+                double xmax = 0.0;
+                if (ok && lane >= ne && lane < n) {
+                    for (int j = ne - 1; j >= 0; --j) {
+                        cd s = U[lane * n + j];
+                        for (int l = j + 1; l < ne; ++l) cfms(s, xr[l], U[l * n + j]);
+                        const cd x = cmul(s, cinv(U[j * n + j]));
+                        xr[j] = x;
+                        const double ax = fmax(fabs(x.x), fabs(x.y));
+                        xmax = ax > xmax ? ax : xmax;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(QCS_FULL, xmax, o));
+                const bool red = ok && xmax <= 16.0;
+                __syncwarp();
+                if (red) {
+                    cd dl = cmk(1.0, 0.0);  // det L
+                    for (int j = 0; j < ne; ++j) dl = cmul(dl, U[j * n + j]);
+                    detR = cmul(detR, dl);
+                    if (lane < n)
+                        for (int j = 0; j < ne; ++j)
+                            U[lane * n + j] = lane < ne ? cmk(lane == j ? 1.0 : 0.0, 0.0) : xr[j];
+                }
+                __syncwarp();
+                if (lane == 0) mode[w] = red ? 1 : 0;
+            }
         }
         const double rs2 = 0.70710678118654752440;
         cd *Uw = Ut + w * n * n;
@@ -145,7 +182,7 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
 }  // namespace
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st, cd *Uout, cd *Rout, bool echelon) {
+                                  cudaStream_t st, cd *Uout, cd *Rout, bool echelon, int *mode) {
     if (W == 0) return QCS_OK;
     const int wpb = 4;
     size_t smem = (size_t)wpb * ((size_t)n * ne + (size_t)n * n + n) * sizeof(cd);
@@ -153,6 +190,7 @@ qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const 
     int64_t blocks = (W + wpb - 1) / wpb;
     if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
     walker_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, ne, W, walkers, Ut, pref, Uout, Rout,
-                                                                   echelon ? 1 : 0, ctx->d_status);
+                                                                   echelon ? 1 : 0, echelon ? mode : nullptr,
+                                                                   ctx->d_status);
     return qcs_check_launch(ctx, "walker_prep_kernel");
 }

@@ -42,7 +42,7 @@ def test_flop_accounting_host_only():
     d, m = n - ne, 2 * n - ne
     # n = 16: three real products per complex multiply-add over the non-zero walker
     # entries, 3 sums per entry of T and re + im of each snapshot entry
-    t_3m = 6 * 2 * n * (n * n - tri(ne) - tri(d)) + 3 * 2 * n * n + 2 * n * n
+    t_3m = 6 * 2 * n * (n * n - ne * (ne - 1) - tri(d)) + 3 * 2 * n * n + 2 * n * n  # reduced form
     b_flops = 16 * n * tri(ne) + 8 * n * ne * 2 * d + 4 * n * tri(2 * d)
     shared = sum(step(r) for r in range(m, 2 * d, -2))
     node = sum(step(r) for r in range(2 * d, 2, -2))

@@ -154,9 +154,10 @@ def test_degenerate_inputs(ctx):
 @pytest.mark.parametrize("n,ne", [(16, 8), (16, 14), (16, 16), (8, 8), (9, 2), (12, 6)])
 def test_structured_walkers(ctx, n, ne):
     """Walkers whose orbital matrix is already in echelon form, is a reversed unit basis
-    (zero leading entries), lives on the last modes only, or has a zero top-left entry:
-    the column reflections that bring the walker rows to echelon form meet each of
-    their special cases (nothing to zero, a zero pivot, a zero row)."""
+    (zero leading entries), lives on the last modes only, has a zero top-left entry or
+    a nearly zero top block: the column reflections that bring the walker rows to
+    echelon form meet each of their special cases (nothing to zero, a zero pivot, a
+    zero row), and the reduced form [I; X] is taken or refused (zero or tiny top block)."""
     rng = np.random.default_rng(n * 31 + ne)
     Q = synth.haar_orthogonal(rng, 2 * n, 24)
     b = synth.parity_consistent_bits(rng, Q)
@@ -169,6 +170,7 @@ def test_structured_walkers(ctx, n, ne):
     Phi[3][0, :] = 0                                # zero first row
     Phi[4][:, 0] = 0                                # zero first column: overlap exactly 0
     Phi[4][0, 1] = 0
+    Phi[5][:ne] *= 1e-3                             # ill-conditioned top block: echelon, not reduced form
     ov, pp, par, st = run_gpu(ctx, dict(Phi=Phi, Q=Q, b=b))
     assert st == 0
     oo, opp, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
