@@ -50,26 +50,6 @@ struct EnergyArgs {
     cd gamma[QCS_MAX_NODES];
 };
 
-// Row a of X (m x 2n) from T: occupied rows are rows of T, each empty mode gives
-// (Re T_j, -Im T_j).
-__device__ __forceinline__ cd x_at(const cd *Ts, int lt, int ne, int a, int c) {
-    if (a < ne) return Ts[a * lt + c];
-    const int r = a - ne;
-    const cd t = Ts[(ne + (r >> 1)) * lt + c];
-    return (r & 1) ? cmk(-t.y, 0.0) : cmk(t.x, 0.0);
-}
-
-// (Y J Z^T)_{ab} = sum_j Y[a][2j] Z[b][2j+1] - Y[a][2j+1] Z[b][2j]
-template <class FY, class FZ>
-__device__ __forceinline__ cd yjz(int n, FY y, FZ z) {
-    cd s = cmk(0.0, 0.0);
-    for (int j = 0; j < n; ++j) {
-        cfma(s, y(2 * j), z(2 * j + 1));
-        cfms(s, y(2 * j + 1), z(2 * j));
-    }
-    return s;
-}
-
 // Sum of one complex value per thread over the 64 threads of a group, in a fixed
 // order (warp shuffles, then the two warp sums in order).  Every thread gets the sum.
 __device__ __forceinline__ cd group_sum(cd v, cd *red, int t, int bar) {
@@ -79,6 +59,74 @@ __device__ __forceinline__ cd group_sum(cd v, cd *red, int t, int bar) {
     const cd s = cadd(red[0], red[1]);
     group_sync(bar);
     return s;
+}
+
+// A' = X' J X^T + X J X'^T (plus 2 Sacc on the A'' pass) and, when acc_s, Sacc += X' J X'^T,
+// in three uniform loops over the pairs a < b: both occupied, occupied x empty, both empty.
+// The rows of X for empty modes are real (Re T_j, -Im T_j), so products with them take
+// two real multiply-adds instead of four.
+__device__ inline void build_Ap(int n, int ne, int m, const cd *__restrict__ X1, int lx, const cd *__restrict__ Ts,
+                                int lt, cd *__restrict__ Ap, cd *__restrict__ Sacc, bool last, bool acc_s,
+                                const uint16_t *__restrict__ tab, int t) {
+    const int d2 = m - ne, c1 = tri_count(ne), c2 = ne * d2, c3 = tri_count(d2);
+    auto xre = [&](int r, int c) {  // X row ne + r (real) at column c
+        const cd v = Ts[(ne + (r >> 1)) * lt + c];
+        return (r & 1) ? -v.y : v.x;
+    };
+    auto finish = [&](int a, int b, cd v) {
+        const int e = tri_index(a, b);
+        if (last) {
+            v = cadd(v, cscale(Sacc[e], 2.0));
+        } else if (acc_s) {
+            const cd *xa = X1 + a * lx, *xb = X1 + b * lx;
+            cd s = cmk(0.0, 0.0);
+            for (int j = 0; j < n; ++j) {
+                cfma(s, xa[2 * j], xb[2 * j + 1]);
+                cfms(s, xa[2 * j + 1], xb[2 * j]);
+            }
+            Sacc[e] = cadd(Sacc[e], s);
+        }
+        Ap[e] = v;
+    };
+    for (int u = t; u < c1; u += kGroup) {  // occupied x occupied: complex rows
+        int a, b;
+        pair_of(tab, u, a, b);
+        const cd *xa = X1 + a * lx, *xb = X1 + b * lx, *ta = Ts + a * lt, *tb = Ts + b * lt;
+        cd v = cmk(0.0, 0.0);
+        for (int j = 0; j < n; ++j) {
+            cfma(v, xa[2 * j], tb[2 * j + 1]);
+            cfms(v, xa[2 * j + 1], tb[2 * j]);
+            cfma(v, ta[2 * j], xb[2 * j + 1]);
+            cfms(v, ta[2 * j + 1], xb[2 * j]);
+        }
+        finish(a, b, v);
+    }
+    for (int u = t; u < c2; u += kGroup) {  // occupied a x empty b = ne + r
+        const int a = u / d2, r = u - a * d2, b = ne + r;
+        const cd *xa = X1 + a * lx, *xb = X1 + b * lx, *ta = Ts + a * lt;
+        cd v = cmk(0.0, 0.0);
+        for (int j = 0; j < n; ++j) {
+            crfma(v, xa[2 * j], xre(r, 2 * j + 1));
+            crfma(v, xa[2 * j + 1], -xre(r, 2 * j));
+            cfma(v, ta[2 * j], xb[2 * j + 1]);
+            cfms(v, ta[2 * j + 1], xb[2 * j]);
+        }
+        finish(a, b, v);
+    }
+    for (int u = t; u < c3; u += kGroup) {  // empty x empty: real rows of X
+        int ra, rb;
+        pair_of(tab, u, ra, rb);
+        const int a = ne + ra, b = ne + rb;
+        const cd *xa = X1 + a * lx, *xb = X1 + b * lx;
+        cd v = cmk(0.0, 0.0);
+        for (int j = 0; j < n; ++j) {
+            crfma(v, xa[2 * j], xre(rb, 2 * j + 1));
+            crfma(v, xa[2 * j + 1], -xre(rb, 2 * j));
+            crfma(v, xb[2 * j + 1], xre(ra, 2 * j));
+            crfma(v, xb[2 * j], -xre(ra, 2 * j + 1));
+        }
+        finish(a, b, v);
+    }
 }
 
 __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_constant__ EnergyArgs A) {
@@ -209,21 +257,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                                 X1[a * lx + c] = s;
                             }
                             group_sync(bar);
-                            for (int e = t; e < T; e += kGroup) {
-                                int a, b;
-                                pair_of(tab, e, a, b);
-                                cd v = cadd(yjz(n, [&](int c) { return X1[a * lx + c]; },
-                                                [&](int c) { return x_at(Ts, lt, ne, b, c); }),
-                                            yjz(n, [&](int c) { return x_at(Ts, lt, ne, a, c); },
-                                                [&](int c) { return X1[b * lx + c]; }));
-                                if (last) {
-                                    v = cadd(v, cscale(Sacc[e], 2.0));
-                                } else if (second && k0 == 0) {
-                                    Sacc[e] = cadd(Sacc[e], yjz(n, [&](int c) { return X1[a * lx + c]; },
-                                                                [&](int c) { return X1[b * lx + c]; }));
-                                }
-                                Ap[tri_index(a, b)] = v;
-                            }
+                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, second && k0 == 0, tab, t);
                             group_sync(bar);
                             // X' is consumed: its region holds W, G, V, H
                             cd *Wm = X1, *Gp = X1 + m * d2, *Vm = Gp + Tn, *Hp = Vm + ne * d2;
@@ -362,21 +396,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                             }
                             group_sync(bar);
                             // Ap = X1 J X^T + X J X1^T (+ 2 Sacc on the last pass); Sacc += X1 J X1^T
-                            for (int e = t; e < T; e += kGroup) {
-                                int a, b;
-                                pair_of(tab, e, a, b);
-                                cd v = cadd(yjz(n, [&](int c) { return X1[a * lx + c]; },
-                                                [&](int c) { return x_at(Ts, lt, ne, b, c); }),
-                                            yjz(n, [&](int c) { return x_at(Ts, lt, ne, a, c); },
-                                                [&](int c) { return X1[b * lx + c]; }));
-                                if (last) {
-                                    v = cadd(v, cscale(Sacc[e], 2.0));
-                                } else if (!is_h && k0 == 0) {
-                                    Sacc[e] = cadd(Sacc[e], yjz(n, [&](int c) { return X1[a * lx + c]; },
-                                                                [&](int c) { return X1[b * lx + c]; }));
-                                }
-                                Ap[tri_index(a, b)] = v;
-                            }
+                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, !is_h && k0 == 0, tab, t);
                             group_sync(bar);
                             for (int v = 0; v < nb; ++v) {
                                 const cd *Zv = Ns + v * T;  // A_v^-1
@@ -730,7 +750,10 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     for (int rv = d2i - 2; rv > 0; rv -= 2) inv += bstep(rv);
     f += inv * nev;
     const double xprime = 4.0 * m * n2 * n2;      // X' = (K ell) Q'^T, complex x real
-    const double aprime = 8.0 * T * 2.0 * n2;     // A' = X' J X^T + X J X'^T (upper triangle)
+    // A' = X' J X^T + X J X'^T (upper triangle): complex x complex products where both
+    // rows are occupied, complex x real where a row of X belongs to an empty mode
+    const double c1 = ne * (ne - 1) / 2.0, c2 = ne * d2, c3 = d2 * (d2 - 1) / 2;
+    const double aprime = 8.0 * n2 * (2.0 * c1 + c2) + 4.0 * n2 * (c2 + 2.0 * c3);
     const double sacc = 8.0 * T * n2;             // X' J X'^T
     const double wg = 8.0 * m * d2 * ne + 8.0 * Tn * ne + 8.0 * To;  // W = A'F, G = F^T W, tr(P^-1 A'_oo)
     const double vh = 8.0 * ne * d2 * (ne - 1) + 8.0 * Tn * ne       // V = P^-1 W_o, H = -W_o^T V
