@@ -207,7 +207,8 @@ qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, 
  * rows.  The node matrices share their occupied block, so per pair it is
  * eliminated once and each node keeps only the inverse of its 2d x 2d complement
  * (never stored beyond the pair); each Cholesky vector then costs
- * O(m (2n)^2 + m^2 d + nodes d^3) per pair.  The Hamiltonian's own
+ * O(m (2n)^2 + m^2 d + nodes d^3) per pair.  The sum over the vectors of
+ * X' J X'^T is taken per snapshot, for all walkers at once.  The Hamiltonian's own
  * factors (e.g. 1/2 on the two-body sum) are the caller's.
  *   d_walkers : W x n x ne complex (device)
  *   d_L       : nchol x n x n complex (device), Lhat_gamma = sum_pq L[gamma][p][q] a_p^dag a_q

@@ -25,7 +25,9 @@
 // P^-1 comes from the backward recursion over the shared steps (qcs_group.cuh) run
 // with Z = 0; pairs whose occupied block would grow the complement beyond 2^5 take
 // the full inverse per node.  Per Cholesky vector the pair costs
-// O(m (2n)^2 + m^2 d + nodes d^3).
+// O(m (2n)^2 + m^2 d + nodes d^3).  The second-order term's sum_gamma X'_g J X'_g^T is
+// K Lambda_p K^T with Lambda_p = sum_gamma ell_gamma G_p ell_gamma^T formed once per
+// snapshot (energy_lambda_kernel).
 #include "qcs_group.cuh"
 #include "qcs_internal.h"
 
@@ -43,6 +45,8 @@ struct EnergyArgs {
     const int *d_count;
     const cd *Kop;  // W x nop x m x 2n: K ell_o (o < nchol: Cholesky vectors; o = nchol: h)
     const cd *K2;   // W x m x 2n: sum_gamma K ell_gamma^2
+    const cd *Kg;   // W x m x 2n: K, the walker's selected rows
+    const cd *Lam;  // per parity +1 snapshot (list order): Lambda_p, packed upper 2n x 2n
     cd *partial;    // W x nchunks x 3: (sum o_p, sum first-derivative term, sum second-derivative term)
     unsigned long long *counter;
     unsigned *status;
@@ -59,6 +63,34 @@ __device__ __forceinline__ cd group_sum(cd v, cd *red, int t, int bar) {
     const cd s = cadd(red[0], red[1]);
     group_sync(bar);
     return s;
+}
+
+// Sacc = sum_gamma X'_g J X'_g^T = K Lambda_p K^T (packed upper, m x m), with Lambda_p
+// the snapshot's sum over the Cholesky vectors (energy_lambda_kernel): P = K Lambda
+// into the X' region, then Sacc_ab = sum_nu P_a,nu K_b,nu.  K and Lambda_p are read
+// from global memory (both stay in L2: one walker's K serves all its tiles).
+__device__ inline void build_Sacc(int n, int m, const cd *__restrict__ Kw, const cd *__restrict__ Lp,
+                                  cd *__restrict__ Pm, int lx, cd *__restrict__ Sacc, const uint16_t *__restrict__ tab,
+                                  int t, int bar) {
+    const int n2 = 2 * n, T = tri_count(m);
+    for (int e = t; e < m * n2; e += kGroup) {
+        const int a = e / n2, nu = e - a * n2;
+        const cd *kr = Kw + a * n2;
+        cd s = cmk(0.0, 0.0);
+        for (int mu = 0; mu < n2; ++mu)
+            if (mu != nu) cfma(s, kr[mu], mu < nu ? Lp[tri_index(mu, nu)] : cneg(Lp[tri_index(nu, mu)]));
+        Pm[a * lx + nu] = s;
+    }
+    group_sync(bar);
+    for (int u = t; u < T; u += kGroup) {
+        int a, b;
+        pair_of(tab, u, a, b);
+        const cd *pa = Pm + a * lx, *kb = Kw + b * n2;
+        cd s = cmk(0.0, 0.0);
+        for (int nu = 0; nu < n2; ++nu) cfma(s, pa[nu], kb[nu]);
+        Sacc[u] = s;
+    }
+    group_sync(bar);
 }
 
 // A' = X' J X^T + X J X'^T (plus 2 Sacc on the A'' pass) and, when acc_s, Sacc += X' J X'^T,
@@ -182,6 +214,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
             const cd *Utw = A.Ut + w * n * n;
             const cd *Kw = A.Kop + (size_t)w * A.nop * m * n2;
             const cd *K2w = A.K2 + (size_t)w * m * n2;
+            const cd *Kgw = A.Kg + (size_t)w * m * n2;
             for (int64_t pq = p0; pq < p1; ++pq) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
                 group_sync(bar);
@@ -230,8 +263,6 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                         node_factor(d2, 0, A.wnode + k0, nb, Sc, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t,
                                     bar, A.status);
                         node_inverse(d2, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
-                        if (k0 == 0)  // B is consumed (E formed); Sacc may share its storage
-                            for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
                         if (t < nb) {
                             cf[t] = cscale(cmul(A.gamma[k0 + t], cmul(pf0, pf[t])), 0.5);
                             acc[t] = cmk(0.0, 0.0);
@@ -245,6 +276,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                             const bool last = o == A.nop;
                             const bool second = !is_h && !last;  // a Cholesky vector: second derivative
                             const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
+                            if (last) build_Sacc(n, m, Kgw, A.Lam + pq * tri_count(n2), X1, lx, Sacc, tab, t, bar);
                             for (int e = t; e < m * n2; e += kGroup) {
                                 const int a = e / n2, c = e - a * n2;
                                 const cd *kr = Ko + a * n2;
@@ -257,7 +289,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                                 X1[a * lx + c] = s;
                             }
                             group_sync(bar);
-                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, second && k0 == 0, tab, t);
+                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, false, tab, t);
                             group_sync(bar);
                             // X' is consumed: its region holds W, G, V, H
                             cd *Wm = X1, *Gp = X1 + m * d2, *Vm = Gp + Tn, *Hp = Vm + ne * d2;
@@ -366,8 +398,6 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                         const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
                         node_factor(m, ne, A.wnode + k0, nb, Bs, Ns, g1v, g2v, pf, invh, pos, acth, kh, ph, tab, t, bar, A.status);
                         node_inverse(m, nb, Ns, g1v, g2v, y1v, y2v, invh, acth, kh, ph, t, bar);
-                        if (k0 == 0)  // B has been copied into the node matrices; Sacc may share its storage
-                            for (int e = t; e < T; e += kGroup) Sacc[e] = cmk(0.0, 0.0);
                         if (t < nb) {
                             cf[t] = cscale(cmul(A.gamma[k0 + t], pf[t]), 0.5);
                             acc[t] = cmk(0.0, 0.0);
@@ -382,6 +412,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                             const bool is_h = A.has_h && o == A.nchol;
                             const bool last = o == A.nop;
                             const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
+                            if (last) build_Sacc(n, m, Kgw, A.Lam + pq * tri_count(n2), X1, lx, Sacc, tab, t, bar);
                             // X1 = Ko Q'^T: X1[a][c] = sum_k Ko[a][2k] Re Qt[c][k] - Ko[a][2k+1] Im Qt[c][k]
                             for (int e = t; e < m * n2; e += kGroup) {
                                 const int a = e / n2, c = e - a * n2;
@@ -396,7 +427,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                             }
                             group_sync(bar);
                             // Ap = X1 J X^T + X J X1^T (+ 2 Sacc on the last pass); Sacc += X1 J X1^T
-                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, !is_h && k0 == 0, tab, t);
+                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, false, tab, t);
                             group_sync(bar);
                             for (int v = 0; v < nb; ++v) {
                                 const cd *Zv = Ns + v * T;  // A_v^-1
@@ -469,7 +500,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
 // Kop[w][o] = K ell_o and K2[w] = sum_gamma K ell_gamma^2.  One block per walker.
 __global__ void energy_prep_kernel(int n, int ne, int64_t W, int nchol, int has_h, const cd *__restrict__ Ut,
                                    const cd *__restrict__ Lg, const cd *__restrict__ h, cd *__restrict__ Kop,
-                                   cd *__restrict__ K2) {
+                                   cd *__restrict__ K2, cd *__restrict__ Kg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n2 = 2 * n, m = 2 * n - ne, nop = nchol + has_h;
     cd *K = reinterpret_cast<cd *>(smem_raw);   // m x 2n
@@ -486,6 +517,7 @@ __global__ void energy_prep_kernel(int n, int ne, int64_t W, int nchol, int has_
             const cd u = U[j * n + k];
             const cd ut = (c & 1) ? cmk(u.y, -u.x) : u;
             K[e] = a < ne ? ut : (((a - ne) & 1) ? cmk(-ut.y, 0.0) : cmk(ut.x, 0.0));
+            Kg[(size_t)w * m * n2 + e] = K[e];
             Ka[e] = cmk(0.0, 0.0);
         }
         __syncthreads();
@@ -521,6 +553,92 @@ __global__ void energy_prep_kernel(int n, int ne, int64_t W, int nchol, int has_
             __syncthreads();
         }
         for (int e = threadIdx.x; e < m * n2; e += blockDim.x) K2[(size_t)w * m * n2 + e] = Ka[e];
+        __syncthreads();
+    }
+}
+
+// Per parity +1 snapshot p (list order): Lambda_p = sum_gamma ell_gamma G_p ell_gamma^T over
+// the Cholesky vectors, packed upper (2n x 2n), with G_p = R J R^T and R the snapshot's
+// real rows (R[2k][c] = Re Qt[c][k], R[2k+1][c] = -Im Qt[c][k]).  Since every walker's
+// X'_gamma = K ell_gamma R, sum_gamma X'_g J X'_g^T = K Lambda_p K^T: the sum over the
+// Cholesky vectors is taken once per snapshot instead of once per pair.  One block per
+// snapshot; each thread owns up to kLamPer entries of Lambda.
+constexpr int kLamThreads = 256, kLamPer = 5;  // 256 x 5 >= tri(2 QCS_MAX_N) = 1128
+__global__ void __launch_bounds__(kLamThreads) energy_lambda_kernel(int n, int nchol, int64_t P, int all, const int *__restrict__ idx,
+                                     const int *__restrict__ d_count, const cd *__restrict__ Qt,
+                                     const cd *__restrict__ Lg, cd *__restrict__ Lam) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = 2 * n, T2 = tri_count(n2);
+    double *R = reinterpret_cast<double *>(smem_raw);  // 2n x 2n
+    double *G = R + n2 * n2;                           // 2n x 2n
+    cd *ell = reinterpret_cast<cd *>(G + n2 * n2);     // 2n x 2n
+    cd *M = ell + n2 * n2;                             // ell G
+    const int64_t L = all ? P : (int64_t)(*d_count);
+    for (int64_t pq = blockIdx.x; pq < L; pq += gridDim.x) {
+        const int64_t q = all ? pq : (int64_t)idx[pq];
+        for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+            const int mu = e / n2, c = e - mu * n2;
+            const cd v = Qt[(q * n2 + c) * n + (mu >> 1)];
+            R[e] = (mu & 1) ? -v.y : v.x;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+            const int mu = e / n2, nu = e - mu * n2;
+            double g = 0.0;
+            for (int j = 0; j < n; ++j) {
+                g = fma(R[mu * n2 + 2 * j], R[nu * n2 + 2 * j + 1], g);
+                g = fma(-R[mu * n2 + 2 * j + 1], R[nu * n2 + 2 * j], g);
+            }
+            G[e] = g;
+        }
+        cd acc[kLamPer];
+        int mus[kLamPer], nus[kLamPer];  // the (mu < nu) entries this thread owns
+#pragma unroll
+        for (int h = 0; h < kLamPer; ++h) {
+            acc[h] = cmk(0.0, 0.0);
+            const int u = threadIdx.x + h * blockDim.x;
+            int nu = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)u)) * 0.5f);
+            while (nu * (nu - 1) / 2 > u) --nu;
+            while ((nu + 1) * nu / 2 <= u) ++nu;
+            nus[h] = nu;
+            mus[h] = u - nu * (nu - 1) / 2;
+        }
+        for (int g = 0; g < nchol; ++g) {
+            const cd *Lo = Lg + (size_t)g * n * n;
+            __syncthreads();  // G complete; the previous vector's M and ell consumed
+            for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+                const int mu = e / n2, a = e - mu * n2, r = mu >> 1, qq = a >> 1;
+                const cd lrq = Lo[r * n + qq], lqr = Lo[qq * n + r];
+                const cd dif = cscale(csub(lqr, lrq), 0.5), sum = cscale(cadd(lrq, lqr), 0.5);
+                cd v;
+                if ((mu & 1) == (a & 1)) v = dif;
+                else if ((mu & 1) == 0) v = cmk(sum.y, -sum.x);  // -i sum
+                else v = cmk(-sum.y, sum.x);                     // i sum
+                ell[e] = v;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+                const int mu = e / n2, nu = e - mu * n2;
+                cd s = cmk(0.0, 0.0);
+                for (int k = 0; k < n2; ++k) crfma(s, ell[mu * n2 + k], G[k * n2 + nu]);
+                M[e] = s;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int h = 0; h < kLamPer; ++h) {
+                if (threadIdx.x + h * blockDim.x < T2) {
+                    const cd *mr = M + mus[h] * n2, *lr = ell + nus[h] * n2;
+                    cd s = acc[h];
+                    for (int k = 0; k < n2; ++k) cfma(s, mr[k], lr[k]);
+                    acc[h] = s;
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < kLamPer; ++h) {
+            const int u = threadIdx.x + h * blockDim.x;
+            if (u < T2) Lam[pq * T2 + u] = acc[h];
+        }
         __syncthreads();
     }
 }
@@ -644,9 +762,11 @@ extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int
     const size_t b_pref = align16(sizeof(cd) * (size_t)W);
     const size_t b_kop = align16(sizeof(cd) * (size_t)W * (nop > 0 ? nop : 1) * m * n2);
     const size_t b_k2 = align16(sizeof(cd) * (size_t)W * m * n2);
+    const size_t b_kg = align16(sizeof(cd) * (size_t)W * m * n2);
+    const size_t b_lam = align16(sizeof(cd) * (size_t)(s->P > 0 ? s->P : 1) * tri_count(n2));
     const size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * 3);
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_kop + b_k2 + b_part, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_kop + b_k2 + b_part + b_kg + b_lam, &base);
     if (ws != QCS_OK) return ws;
     char *pb = (char *)base;
     unsigned long long *counter = (unsigned long long *)pb;
@@ -655,6 +775,8 @@ extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int
     cd *Kop = (cd *)(pb + 16 + b_ut + b_pref);
     cd *K2 = (cd *)(pb + 16 + b_ut + b_pref + b_kop);
     cd *part = (cd *)(pb + 16 + b_ut + b_pref + b_kop + b_k2);
+    cd *Kg = (cd *)(pb + 16 + b_ut + b_pref + b_kop + b_k2 + b_part);
+    cd *Lam = (cd *)(pb + 16 + b_ut + b_pref + b_kop + b_k2 + b_part + b_kg);
     qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st);
     if (r != QCS_OK) return r;
     {
@@ -662,8 +784,17 @@ extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int
         if (qcs_set_smem(ctx, (const void *)energy_prep_kernel, sm) != QCS_OK) return QCS_ERR_CUDA;
         int64_t blocks = W < (int64_t)ctx->num_sms * 4 ? W : (int64_t)ctx->num_sms * 4;
         energy_prep_kernel<<<(unsigned)blocks, 256, sm, st>>>(n, ne, W, nchol, has_h, Ut, (const cd *)d_L,
-                                                               (const cd *)d_h, Kop, K2);
+                                                               (const cd *)d_h, Kop, K2, Kg);
         r = qcs_check_launch(ctx, "energy_prep_kernel");
+        if (r != QCS_OK) return r;
+    }
+    if (s->P > 0) {  // Lambda_p per parity +1 snapshot (zero without Cholesky vectors)
+        const size_t sm = (size_t)2 * n2 * n2 * sizeof(double) + (size_t)2 * n2 * n2 * sizeof(cd);
+        if (qcs_set_smem(ctx, (const void *)energy_lambda_kernel, sm) != QCS_OK) return QCS_ERR_CUDA;
+        int64_t blocks = s->P < (int64_t)ctx->num_sms * 4 ? s->P : (int64_t)ctx->num_sms * 4;
+        energy_lambda_kernel<<<(unsigned)blocks, kLamThreads, sm, st>>>(n, nchol, s->P, plan.all, s->idx, s->d_count,
+                                                                        s->Qt, (const cd *)d_L, Lam);
+        r = qcs_check_launch(ctx, "energy_lambda_kernel");
         if (r != QCS_OK) return r;
     }
     EnergyArgs A;
@@ -688,6 +819,8 @@ extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int
     A.d_count = s->d_count;
     A.Kop = Kop;
     A.K2 = K2;
+    A.Kg = Kg;
+    A.Lam = Lam;
     A.partial = part;
     A.counter = counter;
     A.status = ctx->d_status;
@@ -754,7 +887,6 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     // rows are occupied, complex x real where a row of X belongs to an empty mode
     const double c1 = ne * (ne - 1) / 2.0, c2 = ne * d2, c3 = d2 * (d2 - 1) / 2;
     const double aprime = 8.0 * n2 * (2.0 * c1 + c2) + 4.0 * n2 * (c2 + 2.0 * c3);
-    const double sacc = 8.0 * T * n2;             // X' J X'^T
     const double wg = 8.0 * m * d2 * ne + 8.0 * Tn * ne + 8.0 * To;  // W = A'F, G = F^T W, tr(P^-1 A'_oo)
     const double vh = 8.0 * ne * d2 * (ne - 1) + 8.0 * Tn * ne       // V = P^-1 W_o, H = -W_o^T V
                       + 8.0 * (ne * (ne + 1) / 2.0) * 2.0 * (ne - 1);  // tr((P^-1 A'_oo)^2)
@@ -762,6 +894,9 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     const double t2 = 8.0 * Tn + 8.0 * (d2 * (d2 + 1) / 2) * 2.0 * (d2 - 1);  // tr(Z_k H), tr((Z_k G)^2)
     const double npass = nchol + has_h + 1.0;                         // operators and the A'' pass
     f += npass * (xprime + aprime + wg + nev * t1);
-    f += nchol * (sacc + vh + nev * t2);
+    f += nchol * (vh + nev * t2);
+    // sum_gamma X'_g J X'_g^T = K Lambda_p K^T once per pair (Lambda_p per snapshot, shared by
+    // every walker, is the separate energy_lambda_kernel)
+    f += (nchol > 0 ? 1.0 : 0.0) * (8.0 * m * n2 * (n2 - 1) + 8.0 * T * n2);
     return f;
 }
