@@ -401,7 +401,7 @@ def run_precision(args, ctx, dev, barrier, ws):
     avg = kms / max(kl, 1)
     ach = f_pf * npar * wl.W / (avg * 1e-3) / 1e12
     ngroups = (wl.W + 3) // 4
-    tensor_flops = ngroups * ((npar + 7) // 8) * 3 * 2.0 * 128 * 256 * 32
+    tensor_flops = ngroups * ((npar + 3) // 4) * 3 * 2.0 * 128 * 128 * 32  # tiles of 4 walkers x 4 snapshots
     return {"metric": "walker x snapshot overlap pairs/s, split precision (3xTF32 congruence on tensor cores)",
             "value": ws * wl.W * wl.P * steps / t, "unit": "pairs/s", "ms_per_step": 1e3 * t / steps,
             "steps": steps, "dtype": "tf32x3 congruence / f32 B / f64 Pfaffian",

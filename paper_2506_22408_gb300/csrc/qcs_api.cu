@@ -355,8 +355,8 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     const bool split = o.precision == QCS_TF32X3;
     wk->split = split;
     // partial sums: FP64 path one per (walker, 16-snapshot chunk, warp); split path one
-    // per (walker, 8-snapshot chunk)
-    const int span = split ? 8 : kChunk * qcs_pair_warps_per_block();
+    // per (walker, tile of snapshots)
+    const int span = split ? qcs_split_snaps_per_tile() : kChunk * qcs_pair_warps_per_block();
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
     wk->nparts = split ? wk->nchunks : wk->nchunks * qcs_pair_warps_per_block();

@@ -128,6 +128,7 @@ int qcs_pair_warps_per_block();  // partial sums per overlap tile
 // Split precision (qcs_split.cu)
 qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
 size_t qcs_split_walker_bytes(int64_t W);
+int qcs_split_snaps_per_tile();  // snapshots per split-precision tile (partial sums per walker)
 qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st);
 qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launch *Ls, unsigned long long *counter,
                                     cudaStream_t st);

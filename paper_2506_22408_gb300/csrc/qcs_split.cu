@@ -5,7 +5,7 @@
 // Qt = C + iD,
 //     [T_re; T_im] = M_w N_q^T,   M_w = [[A, -B], [B, A]]  (2n x 2n),
 //                                 N_q = [C, D]             (2n x 2n, rows c),
-// so a tile of 4 walkers x 8 snapshots is one 128 x 256 x 32 GEMM (n <= 16, rows
+// so a tile of 4 walkers x 4 snapshots is one 128 x 128 x 32 GEMM (n <= 16, rows
 // and K padded to 32).  It runs on the 5th-generation tensor cores as three
 // tcgen05.mma kind::tf32 passes over TF32 hi/lo splits of both operands
 // (hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory).  The operand
@@ -30,8 +30,8 @@ constexpr int kK = 32;           // padded contraction length (2n <= 32)
 constexpr int kRows = 32;        // padded rows per walker / snapshot
 constexpr int kSlabBytes = kRows * kK * 4;  // one operand slab (4 KB)
 constexpr int kWalkersPerTile = 4;          // M = 128
-constexpr int kSnapsPerTile = 8;            // N = 256
-constexpr uint32_t kTmemCols = 256;
+constexpr int kSnapsPerTile = 4;            // N = 128
+constexpr uint32_t kTmemCols = 128;         // 4 blocks x 128 columns fit the SM's 512
 constexpr uint32_t kWaitIter = 1u << 26;     // bounded mbarrier waits
 
 // hi/lo TF32 split of x written to slabs at (row, k)
@@ -85,6 +85,7 @@ struct SplitArgs {
     int region_bytes;            // operand / workspace union
     int warp_bytes;
     int off_T, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;
+    int vm;                      // entries per Gauss-vector buffer (the full matrix or NB complements)
     const float *Mhi, *Mlo;      // walker slabs
     const float *Nhi, *Nlo;      // snapshot slabs
     const cd *pref;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     __shared__ int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = A.n;
-    // region: operands [A_hi 16K | A_lo 16K | B_hi 32K | B_lo 32K], later the warps' workspaces
+    // region: operands [A_hi 16K | A_lo 16K | B_hi 16K | B_lo 16K], later the warps' workspaces
     unsigned char *region = smem_raw;
     float *Ahi = reinterpret_cast<float *>(region);
     float *Alo = Ahi + kWalkersPerTile * kSlabBytes / 4;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
     int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = wbase + A.off_act;
-    uint8_t *act1 = act0 + A.NB * A.m;
+    uint8_t *act1 = act0 + A.vm;
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
     const int ldT = 2 * n + 1;
 
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
         bool ok = mbar_wait_bounded(&mbar_load, phase, kWaitIter);
         if (ok && tid == 0) {
             fence_after_sync();
-            const uint32_t id = idesc_tf32(128, 256);
+            const uint32_t id = idesc_tf32(kWalkersPerTile * kRows, kSnapsPerTile * kRows);
             const float *Ap[3] = {Ahi, Ahi, Alo};
             const float *Bp[3] = {Bhi, Blo, Bhi};
             for (int pass = 0; pass < 3; ++pass)
@@ -300,9 +301,10 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
             cd pf0;
             const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
             const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
+            const int NBr = shared ? A.NB : 1;  // the rare full eliminations run one node per round
             cd S = cmk(0.0, 0.0);
-            for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
-                const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
+            for (int k0 = 0; k0 < A.nev; k0 += NBr) {
+                const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
                 node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
@@ -334,8 +336,11 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
 
 // Per-warp workspace of the split kernel for nb node matrices.
 size_t split_warp_layout(SplitArgs &A, int NB) {
-    const int n = A.n, m = A.m, T = tri_count(m);
-    size_t nodes = (size_t)NB * T * sizeof(cd);
+    const int n = A.n, m = A.m, T = tri_count(m), d2 = m - A.ne;
+    // node matrices: one full copy of B (shared elimination; the rare full eliminations,
+    // one node per round) or NB complements of 2d x 2d
+    size_t nodes = (size_t)(T > NB * tri_count(d2) ? T : NB * tri_count(d2)) * sizeof(cd);
+    A.vm = m > NB * d2 ? m : NB * d2;
     size_t tbytes = (size_t)n * (2 * n + 1) * sizeof(float2);
     // T is consumed (into B) before the node matrices are written: they may share
     size_t o = align16(nodes > tbytes ? nodes : tbytes);
@@ -343,9 +348,9 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
     A.off_B = (int)o;
     o = align16(o + (size_t)T * sizeof(cd));
     A.off_U = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
+    o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_V = (int)o;
-    o = align16(o + (size_t)NB * m * sizeof(cd));
+    o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_inv = (int)o;
@@ -353,9 +358,9 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
     A.off_int = (int)o;
     o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
-    o = align16(o + (size_t)2 * NB * m);
+    o = align16(o + (size_t)2 * A.vm);
     A.off_pv = (int)o;
-    o = align16(o + (size_t)NB * (m / 2) * sizeof(cd));
+    o = align16(o + (size_t)(A.vm / 2) * sizeof(cd));
     return o;
 }
 
@@ -378,6 +383,8 @@ qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStrea
 }
 
 size_t qcs_split_walker_bytes(int64_t W) { return (size_t)(W > 0 ? W : 1) * kSlabBytes; }
+
+int qcs_split_snaps_per_tile() { return kSnapsPerTile; }
 
 qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st) {
     const int n = L.n;
@@ -406,7 +413,7 @@ qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, 
     const size_t operands = (size_t)(2 * kWalkersPerTile + 2 * kSnapsPerTile) * kSlabBytes;
     const size_t tab = align16((size_t)T * sizeof(uint16_t));
     // largest node round (<= kMaxNB, balanced) whose four workspaces fit in the operand
-    // region, so that two blocks fit per SM
+    // region
     int NB = 1;
     for (int rounds = 1; rounds <= A.nev; ++rounds) {
         int nb = (A.nev + rounds - 1) / rounds;
@@ -438,15 +445,13 @@ qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, 
         A.gamma[k] = L.plan.gamma[k];
     }
     const size_t smem = (size_t)A.region_bytes + tab;
-    // + the kernel's static words; at least 76 KB per block keeps the blocks per SM at two,
-    // which is what the 2 x 256 tensor-memory columns allow
-    if (smem + 1024 > ctx->smem_optin || smem < (76u << 10))
-        return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split kernel: shared memory");
+    if (smem + 1024 > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split kernel: shared memory");
     if (qcs_set_smem(ctx, (const void *)split_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
     // blocks per SM from the SM's shared memory (static words and the 1 KB the driver
-    // reserves per block included), at most 2 (tensor memory: 2 x 256 columns per SM)
+    // reserves per block included), and at most 512 / kTmemCols so that every block's
+    // tensor-memory allocation is granted at once
     int per_sm = (int)(ctx->smem_per_sm / (smem + 1024 + 1024));
-    if (per_sm > 2) per_sm = 2;
+    if (per_sm > (int)(512 / kTmemCols)) per_sm = (int)(512 / kTmemCols);
     if (per_sm < 1) per_sm = 1;
     const int64_t ntiles = A.ngroups * A.nchunks;
     int64_t blocks = (int64_t)ctx->num_sms * per_sm;
