@@ -79,7 +79,7 @@ typedef enum {
     QCS_ERR_NONFINITE = 4,   /* device: a non-finite input or pivot was met */
     QCS_ERR_SINGULAR = 8,    /* device: A(z_k) singular where its inverse was needed */
     QCS_ERR_TIMEOUT = 16,    /* device: a bounded wait expired */
-    QCS_ERR_UNSUPPORTED = 32 /* request outside what this build implements */
+    QCS_ERR_UNSUPPORTED = 32 /* request outside what the library implements */
 } qcs_status;
 
 typedef enum {
