@@ -82,3 +82,19 @@ def test_without_one_body_operator(ctx):
     assert e1 is None
     _, _, o2 = orc.local_energy(Phi, Q, b, L)
     assert np.all(np.abs(e2.cpu().numpy() - o2) <= TOL * np.maximum(1.0, np.abs(o2)))
+
+
+def test_one_body_operator_only(ctx):
+    """No Cholesky vectors (nchol = 0): the per-snapshot sum over vectors is empty, e2 is
+    exactly zero and e1 still matches the oracle."""
+    Q, b, Phi, L, h = case(73, 8, 4, 3, 20, 1, bits="parity")
+    n = Q.shape[1] // 2
+    s = qcs.Snapshots(ctx, dev(Q), dev(b))
+    L0 = torch.zeros((0, n, n), dtype=torch.complex128, device="cuda")
+    ov, e1, e2 = qcs.local_energy(ctx, s, dev(Phi), L0, dev(h))
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert np.all(e2.cpu().numpy() == 0)
+    _, o1, _ = orc.local_energy(Phi, Q, b, L[:0], h=h)
+    got = e1.cpu().numpy()
+    assert np.all(np.abs(got - o1) <= TOL * np.maximum(1.0, np.abs(o1)))
