@@ -591,6 +591,15 @@ extern "C" qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int
 
 static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, double *part);
 
+// The cotangent products Gamma1 = G_X[occ] Qt, Gamma2 = Ht conj(Qt) (n x n entries of 2n
+// complex terms): three real products per term when B's and Y's regions (tri(m)
+// entries) hold the staged sums, else four.
+static double grad_gamma_flops(int n, int ne) {
+    const int m = 2 * n - ne;
+    if (tri_count(m) >= n * n) return 6.0 * n * n * 2 * n + 2.0 * (2.0 * n * n) + 3.0 * n * n;
+    return 8.0 * n * n * 2 * n;
+}
+
 extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
     qcs_node_plan plan;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
@@ -606,7 +615,7 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     f += (node + 8.0 * tri_count(2 * d)) * plan.nev;                // + the weighted sum of the Z_k
     for (int rv = 2 * d; rv <= m - 2; rv += 2) f += bstep(rv);      // backward over the shared steps
     f += (double)m * 2 * n * (8.0 * ne + 4.0 * (m - ne));           // G_X = Y (X J)
-    f += (double)n * n * 2 * n * 8.0 + 2.0 * d * 2 * n;             // Gamma1 / Gamma2
+    f += grad_gamma_flops(n, ne) + 2.0 * d * 2 * n;                 // Gamma1 / Gamma2
     return f;
 }
 
@@ -622,8 +631,8 @@ extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int node
 extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
     const double f = qcs_grad_flops_per_pair(n, ne, nodes, flags);
     // T is a gather; each of the n x n cotangent entries takes 2 complex additions
-    // instead of 2n complex MACs
-    return f > 0.0 ? f - 16.0 * (double)n * n * n - ((double)n * n * 2 * n * 8.0 - (double)n * n * 2 * 2.0) : 0.0;
+    // instead of 2n complex multiply-adds
+    return f > 0.0 ? f - 16.0 * (double)n * n * n - (grad_gamma_flops(n, ne) - (double)n * n * 2 * 2.0) : 0.0;
 }
 
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {

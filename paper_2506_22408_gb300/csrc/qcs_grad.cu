@@ -232,6 +232,40 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                         }
                         Gs[e] = acc;
                     }
+                } else if (T >= n * n) {
+                    // three real products per complex multiply-add: with s = re + im of the
+                    // snapshot entries (staged in B's region, free by now) and, per cotangent
+                    // row, re + im (occupied rows) or re - im (the Ht rows) staged in Y's,
+                    //   G q:       Re = p1 - p2, Im = p3 - p1 - p2,   p3 = sum (g_r + g_i) s
+                    //   H conj(q): Re = p1 + p2, Im = p1 - p2 - p3,   p3 = sum (h_r - h_i) s
+                    double *qsum = reinterpret_cast<double *>(Bs);  // 2n x n
+                    double *gsum = reinterpret_cast<double *>(Ys);  // n x 2n (row j: occupied j or Ht)
+                    for (int e = t; e < n2 * n; e += kGroup) {
+                        const int c = e / n, k = e - c * n;
+                        const cd q = Qs[c * lq + k];
+                        qsum[e] = q.x + q.y;
+                    }
+                    for (int e = t; e < n * n2; e += kGroup) {
+                        const int j = e / n2, c = e - j * n2;
+                        const cd g = GX[(j < ne ? j : ne + 2 * (j - ne)) * n2 + c];
+                        gsum[e] = j < ne ? g.x + g.y : g.x - g.y;
+                    }
+                    group_sync(bar);
+                    for (int e = t; e < n * n; e += kGroup) {
+                        const int j = e / n, k = e - j * n;
+                        const cd *g = GX + (j < ne ? j : ne + 2 * (j - ne)) * n2;
+                        const double *gs = gsum + j * n2;
+                        double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+                        for (int c = 0; c < n2; ++c) {
+                            const cd gv = g[c], q = Qs[c * lq + k];
+                            p1 = fma(gv.x, q.x, p1);
+                            p2 = fma(gv.y, q.y, p2);
+                            p3 = fma(gs[c], qsum[c * n + k], p3);
+                        }
+                        const cd acc = Gs[e];
+                        Gs[e] = j < ne ? cmk(acc.x + (p1 - p2), acc.y + (p3 - p1 - p2))
+                                       : cmk(acc.x + (p1 + p2), acc.y + (p1 - p2 - p3));
+                    }
                 } else for (int e = t; e < n * n; e += kGroup) {
                     const int j = e / n, k = e - j * n;
                     cd acc = Gs[e];
