@@ -4,6 +4,9 @@ matrices from the oracle (no GPU):
 * the node matrices B + w D differ only in their empty x empty block, so eliminating the
   occupied block first (pivots restricted to it) gives pf(B + w D) = pf0 pf(S + w D_ee)
   for every node w, S the Schur complement of the occupied block;
+* the adjoint's backward pass over those shared steps is affine in the inverse Z of the
+  complement, so one pass started from sum_k c_k Z_k (each step's constant scaled by
+  sum_k c_k) gives sum_k c_k A_k^{-1};
 * the estimator is multilinear and alternating in the occupied orbitals:
   o(Phi W) = det(W) o(Phi) for any ne x ne matrix W, which is what lets the walker prep
   rotate the occupied orbitals to echelon form and fold det W into det R.
@@ -118,3 +121,61 @@ def test_occupied_orbitals_alternating():
         o1, _, _, _ = orc.overlap((Phi @ Wx)[None], Q, b, per_pair=True)
         assert abs(o1[0] - np.linalg.det(Wx) * o0[0]) <= 1e-12 * abs(np.linalg.det(Wx)) * sc.mean()
     assert abs(np.linalg.det(refl) + 1) < 1e-12
+
+
+def backward_block(B, ne, Zc, c):
+    """The adjoint's backward pass over the shared occupied steps, restated in numpy:
+    forward elimination with the kernel's pivots keeping (k, p, 1/a, active list) per
+    step, then from the last step back: new entries -Z g1, -Z g2 and c(-1/a) + g1^T Z g2,
+    starting from Zc on the empty indices.  Returns the m x m result."""
+    A = B.astype(complex).copy()
+    m = A.shape[0]
+    act = list(range(m))
+    hist = []
+    for s in range(ne // 2):
+        ro = ne - 2 * s
+        best = max((key(A[act[a], act[b]]), -b * 1000 - a) for b in range(1, ro) for a in range(b))
+        ap, ak = divmod(-best[1], 1000)
+        k, p = act[ak], act[ap]
+        piv = A[k, p]
+        rest = [act[x] for x in range(len(act)) if x not in (ak, ap)]
+        hist.append((k, p, 1.0 / piv, rest, A[np.ix_(rest, [k])].ravel().copy(), A[np.ix_(rest, [p])].ravel().copy()))
+        u, v = A[rest, k] / piv, A[rest, p]
+        A[np.ix_(rest, rest)] -= np.outer(u, v) - np.outer(v, u)
+        act = rest
+    Y = np.zeros((m, m), complex)
+    Y[np.ix_(act, act)] = Zc
+    for k, p, ia, rest, aik, aip in reversed(hist):
+        g1 = aip * ia          # v / a, v_i = A_{i,p}
+        g2 = -aik * ia         # -u / a, u_i = A_{i,k}
+        Z = Y[np.ix_(rest, rest)]
+        y1, y2 = Z @ g1, Z @ g2
+        Y[rest, k], Y[k, rest] = -y1, y1
+        Y[rest, p], Y[p, rest] = -y2, y2
+        Y[k, p] = c * (-ia) + g1 @ Z @ g2
+        Y[p, k] = -Y[k, p]
+    return Y
+
+
+@pytest.mark.parametrize("n,ne", [(16, 8), (10, 4), (8, 8)])
+def test_weighted_backward_pass_gives_weighted_inverse(n, ne):
+    """One backward pass over the shared steps, started from sum_k c_k Z_k with the
+    constants scaled by sum_k c_k, equals sum_k c_k A_k^{-1} (the adjoint's block form)."""
+    rng = np.random.default_rng(200 + n + ne)
+    Q = synth.haar_orthogonal(rng, 2 * n, 3)
+    b = synth.parity_consistent_bits(rng, Q)  # parity -1 makes B singular when ne = n
+    Phi = synth.walkers(rng, n, ne, 1)[0]
+    D = node_D(n, ne)
+    nodes = np.exp(-1j * np.array([0.3, 1.4, 2.6]))
+    cs = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    for p in range(3):
+        B, _, _ = orc.pair_matrices(Q[p], b[p], Phi)
+        r = shared_elimination(B, ne)
+        assert r is not None
+        _, S, _ = r
+        m = B.shape[0]
+        d2 = m - ne
+        Zc = sum(c * np.linalg.inv(S + z * D[ne:, ne:]) for c, z in zip(cs, nodes)) if d2 else np.zeros((0, 0))
+        got = backward_block(B, ne, Zc, cs.sum())
+        ref = sum(c * np.linalg.inv(B + z * D) for c, z in zip(cs, nodes))
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
