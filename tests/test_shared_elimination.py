@@ -7,6 +7,8 @@ matrices from the oracle (no GPU):
 * the adjoint's backward pass over those shared steps is affine in the inverse Z of the
   complement, so one pass started from sum_k c_k Z_k (each step's constant scaled by
   sum_k c_k) gives sum_k c_k A_k^{-1};
+* the local-energy traces follow from A_k^{-1} = F0 + F Z_k F^T with 2d x 2d work per
+  node;
 * the estimator is multilinear and alternating in the occupied orbitals:
   o(Phi W) = det(W) o(Phi) for any ne x ne matrix W, which is what lets the walker prep
   rotate the occupied orbitals to echelon form and fold det W into det R.
@@ -179,3 +181,35 @@ def test_weighted_backward_pass_gives_weighted_inverse(n, ne):
         got = backward_block(B, ne, Zc, cs.sum())
         ref = sum(c * np.linalg.inv(B + z * D) for c, z in zip(cs, nodes))
         assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,ne", [(16, 8), (12, 4)])
+def test_block_form_traces(n, ne):
+    """The local-energy kernel's traces from the block form of A_k^{-1}:
+    with E = P^-1 B_oe, F = [-E; I], W = A'F, G = F^T W, H = -W_o^T P^-1 W_o,
+    tr(A_k^-1 A') = tr(P^-1 A'_oo) + tr(Z_k G) and
+    tr((A_k^-1 A')^2) = tr((P^-1 A'_oo)^2) + 2 tr(Z_k H) + tr((Z_k G)^2)."""
+    rng = np.random.default_rng(300 + n + ne)
+    Q = synth.haar_orthogonal(rng, 2 * n, 2)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 1)[0]
+    D = node_D(n, ne)
+    B, _, _ = orc.pair_matrices(Q[0], b[0], Phi)
+    m = B.shape[0]
+    X = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    Ap = X - X.T
+    Pinv = np.linalg.inv(B[:ne, :ne])
+    E = Pinv @ B[:ne, ne:]
+    S0 = B[ne:, ne:] + B[:ne, ne:].T @ E
+    W = -Ap[:, :ne] @ E + Ap[:, ne:]
+    G = -E.T @ W[:ne] + W[ne:]
+    H = -W[:ne].T @ (Pinv @ W[:ne])
+    PA = Pinv @ Ap[:ne, :ne]
+    for z in np.exp(-1j * np.array([0.3, 1.4, 2.6])):
+        Ai = np.linalg.inv(B + z * D)
+        Z = np.linalg.inv(S0 + z * D[ne:, ne:])
+        t1, t2 = np.trace(Ai @ Ap), np.trace(Ai @ Ap @ Ai @ Ap)
+        b1 = np.trace(PA) + np.trace(Z @ G)
+        b2 = np.trace(PA @ PA) + 2 * np.trace(Z @ H) + np.trace(Z @ G @ Z @ G)
+        assert abs(b1 - t1) <= 1e-10 * max(1.0, abs(t1))
+        assert abs(b2 - t2) <= 1e-10 * max(1.0, abs(t2))
