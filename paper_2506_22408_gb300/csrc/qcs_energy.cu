@@ -348,6 +348,15 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                                 }
                                 c0 = group_sum(c0, red, t, bar);
                             }
+                            // tr((Z G)^2) by three real products per complex multiply-add: re + im
+                            // of G and of each node's Z staged in A''s region (A' is consumed)
+                            const bool sums = second && (A.NB + 1) * Tn <= 2 * T;
+                            double *gsm = reinterpret_cast<double *>(Ap), *zsm = gsm + Tn;
+                            if (sums) {
+                                for (int e = t; e < Tn; e += kGroup) gsm[e] = Gp[e].x + Gp[e].y;
+                                for (int e = t; e < nb * Tn; e += kGroup) zsm[e] = Ns[e].x + Ns[e].y;
+                                group_sync(bar);
+                            }
                             for (int v = 0; v < nb; ++v) {
                                 const cd *Zv = Ns + v * Tn;  // Z_v, packed upper
                                 cd zg = cmk(0.0, 0.0), zh = cmk(0.0, 0.0);
@@ -374,9 +383,34 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                                     }
                                     const int b = a + r;
                                     cd pab = cmk(0.0, 0.0), pba = cmk(0.0, 0.0);
-                                    for (int c = 0; c < d2; ++c) {
-                                        if (c != a && c != b) cfma(pab, skew_get(Zv, a, c), skew_get(Gp, c, b));
-                                        if (c != b && c != a) cfma(pba, skew_get(Zv, b, c), skew_get(Gp, c, a));
+                                    if (sums) {
+                                        const double *zs = zsm + v * Tn;
+                                        double p1 = 0.0, p2 = 0.0, p3 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+                                        for (int c = 0; c < d2; ++c) {
+                                            if (c == a || c == b) continue;
+                                            // Z(a,c) G(c,b) and Z(b,c) G(c,a) from the packed upper triangles
+                                            const int iz = a < c ? tri_index(a, c) : tri_index(c, a);
+                                            const int ig = c < b ? tri_index(c, b) : tri_index(b, c);
+                                            const int jz = b < c ? tri_index(b, c) : tri_index(c, b);
+                                            const int jg = c < a ? tri_index(c, a) : tri_index(a, c);
+                                            const bool s1 = (a > c) != (c > b), s2 = (b > c) != (c > a);
+                                            const cd z1 = flip_if(Zv[iz], s1), z2 = flip_if(Zv[jz], s2);
+                                            const double w1 = s1 ? -zs[iz] : zs[iz], w2 = s2 ? -zs[jz] : zs[jz];
+                                            const cd g1 = Gp[ig], g2 = Gp[jg];
+                                            p1 = fma(z1.x, g1.x, p1);
+                                            p2 = fma(z1.y, g1.y, p2);
+                                            p3 = fma(w1, gsm[ig], p3);
+                                            q1 = fma(z2.x, g2.x, q1);
+                                            q2 = fma(z2.y, g2.y, q2);
+                                            q3 = fma(w2, gsm[jg], q3);
+                                        }
+                                        pab = cmk(p1 - p2, p3 - p1 - p2);
+                                        pba = cmk(q1 - q2, q3 - q1 - q2);
+                                    } else {
+                                        for (int c = 0; c < d2; ++c) {
+                                            if (c != a && c != b) cfma(pab, skew_get(Zv, a, c), skew_get(Gp, c, b));
+                                            if (c != b && c != a) cfma(pba, skew_get(Zv, b, c), skew_get(Gp, c, a));
+                                        }
                                     }
                                     const cd pr = cmul(pab, pba);
                                     t2 = (a == b) ? cadd(t2, pr) : cadd(t2, cscale(pr, 2.0));
@@ -891,7 +925,13 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     const double vh = 8.0 * ne * d2 * (ne - 1) + 8.0 * Tn * ne       // V = P^-1 W_o, H = -W_o^T V
                       + 8.0 * (ne * (ne + 1) / 2.0) * 2.0 * (ne - 1);  // tr((P^-1 A'_oo)^2)
     const double t1 = 8.0 * Tn;                                       // tr(Z_k G) per node
-    const double t2 = 8.0 * Tn + 8.0 * (d2 * (d2 + 1) / 2) * 2.0 * (d2 - 1);  // tr(Z_k H), tr((Z_k G)^2)
+    // tr(Z_k H), tr((Z_k G)^2): three real products per complex multiply-add where the
+    // sums of G and of the round's Z_k fit in A''s region (NB as the launcher takes it when
+    // the workspace fits), else four
+    const int nbr = plan.nev < kMaxNBG ? plan.nev : kMaxNBG;
+    const bool sums = (nbr + 1) * Tn <= 2 * T;
+    const double items = d2 * (d2 + 1) / 2;
+    const double t2 = 8.0 * Tn + (sums ? items * 2.0 * (6.0 * (d2 - 1) + 3.0) : items * 2.0 * 8.0 * (d2 - 1));
     const double npass = nchol + has_h + 1.0;                         // operators and the A'' pass
     f += npass * (xprime + aprime + wg + nev * t1);
     f += nchol * (vh + nev * t2);
