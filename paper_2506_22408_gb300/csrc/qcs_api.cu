@@ -539,9 +539,10 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
     size_t b_u = b_ut;
     size_t b_r = align16(sizeof(cd) * (size_t)W * ne * ne);
+    size_t b_w = align16(sizeof(cd) * (size_t)W * ((size_t)ne * ne + 1));
     size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * (1 + (size_t)n * n));
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w, &base);
     if (ws != QCS_OK) return ws;
     unsigned long long *gcounter = (unsigned long long *)base;
     char *pb = (char *)base + 16;
@@ -550,7 +551,11 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     cd *U = (cd *)(pb + b_ut + b_pref);
     cd *R = (cd *)(pb + b_ut + b_pref + b_u);
     cd *part = (cd *)(pb + b_ut + b_pref + b_u + b_r);
-    qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st, U, R);
+    cd *Wrot = (cd *)(pb + b_ut + b_pref + b_u + b_r + b_part);
+    // echelon-form walker rows (the congruence skips their zeros); U is the rotated unitary,
+    // R the QR's triangular factor and Wrot the occupied columns' rotation for the epilogue
+    qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st, U, R, true, nullptr,
+                                          Wrot);
     if (r != QCS_OK) return r;
     qcs_grad_launch L;
     L.n = n;
@@ -562,6 +567,7 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     L.Ut = Ut;
     L.U = U;
     L.R = R;
+    L.Wrot = Wrot;
     L.pref = pref;
     L.s = s;
     L.partial = part;
@@ -605,8 +611,10 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
     const int d = n - ne, m = 2 * n - ne;
-    // forward: dense T, B, the occupied block once, each node's 2d x 2d complement
+    // forward: T over the echelon-form walker rows, B, the occupied block once, each
+    // node's 2d x 2d complement
     double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);
+    f -= 16.0 * n * ((double)tri_count(ne) + tri_count(d));      // the echelon zeros of Ut
     f -= (double)(plan.nev - 1) * qcs_pf_elim_flops(m, 2 * d);  // the occupied steps once, not per node
     // backward step with rv later indices: g1, g2 (12 rv), Z g1 and Z g2 (16 rv^2), corner (8 rv)
     auto bstep = [](int rv) { return 16.0 * rv * rv + 20.0 * rv; };
@@ -630,9 +638,11 @@ extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int node
 
 extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
     const double f = qcs_grad_flops_per_pair(n, ne, nodes, flags);
+    if (!(f > 0.0)) return 0.0;
     // T is a gather; each of the n x n cotangent entries takes 2 complex additions
     // instead of 2n complex multiply-adds
-    return f > 0.0 ? f - 16.0 * (double)n * n * n - (grad_gamma_flops(n, ne) - (double)n * n * 2 * 2.0) : 0.0;
+    const double t_products = 16.0 * n * ((double)n * n - tri_count(ne) - tri_count(n - ne));
+    return f - t_products - (grad_gamma_flops(n, ne) - (double)n * n * 2 * 2.0);
 }
 
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {

@@ -17,7 +17,9 @@
 //     g^T = (c0 / P) adj(R) [ S U_occ^dagger + Lambda (I - U_occ U_occ^dagger) ],
 //     c0 = 2 i^{ne/2} / 2^{n - ne/2},  S = sum_p S_p,
 // with adj(R) = det(R) R^{-1} formed without divisions, so rank-deficient
-// walkers need no special case.
+// walkers need no special case.  The walker rows of Ut are in echelon form
+// (qcs_walker.cu): U_occ = U_qr W, and R above is W^H R_qr, so the epilogue
+// takes adj(R_qr) det(conj W) W and det(conj W) det(R_qr).
 //
 // A'_k^{-1} is recomputed per pair and node, never stored in global memory: the
 // Parlett-Reid elimination (as in the overlap kernel, original index order)
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                 }
                 group_sync(bar);
                 if (sp) build_T_gather(n, Uts, gq, Ts, t, kGroup);
-                else build_T(n, Uts, Qs, Ts, t, kGroup);
+                else build_T_echelon(n, ne, Uts, Qs, Ts, t, kGroup);  // walker rows in echelon form
                 group_sync(bar);
                 build_B(n, ne, Ts, Bs, tab, t, kGroup);
                 group_sync(bar);
@@ -291,7 +293,8 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
 //   Lambda = sqrt2 Gacc1 - U_occ^dagger Gacc2^T U^dagger
 // where Gacc1 = Gamma1 / 2 and Gacc2 = Gamma2 as accumulated by grad_pair_kernel.
 __global__ void grad_epilogue_kernel(int n, int ne, int64_t W, int64_t P, int nchunks, const cd *__restrict__ partial,
-                                     const cd *__restrict__ U, const cd *__restrict__ R, cd *__restrict__ overlap,
+                                     const cd *__restrict__ U, const cd *__restrict__ R,
+                                     const cd *__restrict__ Wrot, cd *__restrict__ overlap,
                                      cd *__restrict__ grad, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -385,19 +388,30 @@ __global__ void grad_epilogue_kernel(int n, int ne, int64_t W, int64_t P, int nc
         }
         const double invP = P > 0 ? 1.0 / (double)P : 0.0;
         const cd c0 = cscale(ip, 2.0 * ldexp(1.0, -(n - ne / 2)) * invP);
-        // grad[w][l][a] = (g^T)[a][l] = c0 sum_b adj[a][b] Mm[b][l]
+        // The kernel's rows are those of U_occ = U_qr W (echelon form), so the factor is
+        // W^H R: adj(W^H R) = adj(R) det(conj W) W, with det(conj W) W stored in Wrot.
+        const cd *Ww = Wrot + w * ((size_t)ne * ne + 1);
+        cd *Ad2 = V1;  // free again
+        for (int e = lane; e < ne * ne; e += 32) {
+            const int a = e / ne, b = e - a * ne;
+            cd acc = cmk(0.0, 0.0);
+            for (int c = a; c < ne; ++c) cfma(acc, Ad[a * ne + c], Ww[c * ne + b]);
+            Ad2[e] = acc;
+        }
+        __syncwarp();
+        // grad[w][l][a] = (g^T)[a][l] = c0 sum_b adj(W^H R)[a][b] Mm[b][l]
         for (int e = lane; e < n * ne; e += 32) {
             int l = e / ne, a = e - l * ne;
             cd acc = cmk(0.0, 0.0);
-            for (int b = a; b < ne; ++b) cfma(acc, Ad[a * ne + b], Mm[b * n + l]);
+            for (int b = 0; b < ne; ++b) cfma(acc, Ad2[a * ne + b], Mm[b * n + l]);
             acc = cmul(c0, acc);
             if (!cfinite(acc)) raise_status(status, QCS_ERR_NONFINITE);
             grad[w * n * ne + e] = acc;
         }
         if (lane == 0) {
-            cd detR = cmk(1.0, 0.0);
+            cd detR = cmk(1.0, 0.0);  // det(W^H R) = det(conj W) det R
             for (int i = 0; i < ne; ++i) detR = cmul(detR, Rs[i * ne + i]);
-            overlap[w] = cmul(c0, cmul(detR, S));
+            overlap[w] = cmul(c0, cscale(cmul(detR, S), Ww[ne * ne].x));
         }
         __syncwarp();
     }
@@ -566,7 +580,7 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     if (qcs_set_smem(ctx, (const void *)grad_epilogue_kernel, esm) != QCS_OK) return QCS_ERR_CUDA;
     int64_t eb = (L.W + ewpb - 1) / ewpb;
     if (eb > (int64_t)ctx->num_sms * 8) eb = (int64_t)ctx->num_sms * 8;
-    grad_epilogue_kernel<<<(unsigned)eb, ewpb * 32, esm, st>>>(n, ne, L.W, L.P, L.nchunks, L.partial, L.U, L.R,
+    grad_epilogue_kernel<<<(unsigned)eb, ewpb * 32, esm, st>>>(n, ne, L.W, L.P, L.nchunks, L.partial, L.U, L.R, L.Wrot,
                                                                L.overlap, L.grad, ctx->d_status);
     return qcs_check_launch(ctx, "grad_epilogue_kernel");
 }

@@ -85,15 +85,16 @@ double qcs_pf_elim_flops(int m, int stop);  // Pfaffian elimination steps from r
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
                                   cudaStream_t st, cd *Uout = nullptr, cd *Rout = nullptr, bool echelon = false,
-                                  int *mode = nullptr);
+                                  int *mode = nullptr, cd *Wout = nullptr);
 
 struct qcs_grad_launch {
     int n, ne;
     int64_t W, P;
     int chunk, nchunks;
     const cd *Ut;
-    const cd *U;
-    const cd *R;
+    const cd *U;      // the walker's unitary with its occupied and empty columns in echelon form
+    const cd *R;      // the QR's triangular factor
+    const cd *Wrot;   // per walker: det(conj W) W (ne x ne), then det(conj W); U_occ = U_qr W
     const cd *pref;
     const qcs_snapshots *s;
     cd *partial;     // W x nchunks x (1 + n*n)

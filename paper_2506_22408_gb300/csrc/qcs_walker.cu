@@ -32,15 +32,16 @@ namespace {
 
 __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restrict__ Phi, cd *__restrict__ Ut,
                                    cd *__restrict__ pref, cd *__restrict__ Uout, cd *__restrict__ Rout, int echelon,
-                                   int *__restrict__ mode, unsigned *status) {
+                                   int *__restrict__ mode, cd *__restrict__ Wout, unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const size_t per_warp = (size_t)n * ne + (size_t)n * n + n;
+    const size_t per_warp = (size_t)n * ne + (size_t)n * n + n + (Wout ? (size_t)ne * ne : 0);
     cd *A = reinterpret_cast<cd *>(smem_raw) + warp * per_warp;
     cd *U = A + n * ne;
     cd *v = U + n * n;
+    cd *Wr = v + n;  // the occupied columns' rotation W of the echelon form (ne x ne)
     for (int64_t w = (int64_t)blockIdx.x * wpb + warp; w < W; w += (int64_t)gridDim.x * wpb) {
         const cd *Pw = Phi + w * n * ne;
         bool bad = false;
@@ -88,6 +89,10 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
             detR = cmul(detR, alpha);
         }
         if (echelon) {
+            if (Wout) {  // Wr has room in this warp's slot only when the rotation is requested
+                for (int e = lane; e < ne * ne; e += 32) Wr[e] = cmk((e / ne) == (e % ne) ? 1.0 : 0.0, 0.0);
+                __syncwarp();
+            }
             int nref = 0;  // reflections on the occupied columns (det -1 each)
             for (int blk = 0; blk < 2; ++blk) {
                 const int c0 = blk == 0 ? 0 : ne, c1 = blk == 0 ? ne : n;
@@ -111,6 +116,12 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
                         sr = cscale(sr, tau);
                         for (int c = cs; c < c1; ++c) cfms(U[lane * n + c], sr, cconj(v[c]));
                     }
+                    if (Wout && blk == 0 && lane < ne) {  // W <- W (I - tau v v^H), same columns
+                        cd sr = cmk(0.0, 0.0);
+                        for (int c = cs; c < c1; ++c) cfma(sr, Wr[lane * ne + c], v[c]);
+                        sr = cscale(sr, tau);
+                        for (int c = cs; c < c1; ++c) cfms(Wr[lane * ne + c], sr, cconj(v[c]));
+                    }
                     __syncwarp();
                     if (lane > cs && lane < c1) U[row * n + lane] = cmk(0.0, 0.0);  // exact zeros
                     __syncwarp();
@@ -118,6 +129,13 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
                 }
             }
             if (nref & 1) detR = cneg(detR);  // det R' = conj(det W) det R, det W = (-1)^nref
+            if (Wout) {  // det(conj W) W, then det(conj W) itself: adj(W^H R) = adj(R) det(conj W) W
+                __syncwarp();
+                const double sg = (nref & 1) ? -1.0 : 1.0;
+                cd *Wo = Wout + w * ((size_t)ne * ne + 1);
+                for (int e = lane; e < ne * ne; e += 32) Wo[e] = cscale(Wr[e], sg);
+                if (lane == 0) Wo[ne * ne] = cmk(sg, 0.0);
+            }
             if (mode) {
                 // X L = U_bot by back substitution over the columns (lane = row of U_bot)
                 bool ok = true;
@@ -182,15 +200,16 @@ __global__ void walker_prep_kernel(int n, int ne, int64_t W, const cd *__restric
 }  // namespace
 
 qcs_status qcs_launch_walker_prep(qcs_ctx *ctx, int n, int ne, int64_t W, const cd *walkers, cd *Ut, cd *pref,
-                                  cudaStream_t st, cd *Uout, cd *Rout, bool echelon, int *mode) {
+                                  cudaStream_t st, cd *Uout, cd *Rout, bool echelon, int *mode, cd *Wout) {
     if (W == 0) return QCS_OK;
     const int wpb = 4;
-    size_t smem = (size_t)wpb * ((size_t)n * ne + (size_t)n * n + n) * sizeof(cd);
+    if (!echelon) Wout = nullptr;
+    size_t smem = (size_t)wpb * ((size_t)n * ne + (size_t)n * n + n + (Wout ? (size_t)ne * ne : 0)) * sizeof(cd);
     if (qcs_set_smem(ctx, (const void *)walker_prep_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
     int64_t blocks = (W + wpb - 1) / wpb;
     if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
     walker_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(n, ne, W, walkers, Ut, pref, Uout, Rout,
                                                                    echelon ? 1 : 0, echelon ? mode : nullptr,
-                                                                   ctx->d_status);
+                                                                   Wout, ctx->d_status);
     return qcs_check_launch(ctx, "walker_prep_kernel");
 }
