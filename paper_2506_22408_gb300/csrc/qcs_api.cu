@@ -606,6 +606,14 @@ static double grad_gamma_flops(int n, int ne) {
     return 8.0 * n * n * 2 * n;
 }
 
+// T over the echelon-form walker rows as the gradient kernel forms it: at n = 16 three
+// real products per complex multiply-add (with re + im of each snapshot entry and the
+// two sums per entry), else four.
+static double grad_T_flops(int n, int ne) {
+    const double macs = 2.0 * n * ((double)n * n - tri_count(ne) - tri_count(n - ne));
+    return n == 16 ? 6.0 * macs + 3.0 * 2.0 * n * n + 2.0 * n * n : 8.0 * macs;
+}
+
 extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
     qcs_node_plan plan;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
@@ -614,7 +622,7 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     // forward: T over the echelon-form walker rows, B, the occupied block once, each
     // node's 2d x 2d complement
     double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);
-    f -= 16.0 * n * ((double)tri_count(ne) + tri_count(d));      // the echelon zeros of Ut
+    f += grad_T_flops(n, ne) - 16.0 * n * n * n;                 // instead of a dense T
     f -= (double)(plan.nev - 1) * qcs_pf_elim_flops(m, 2 * d);  // the occupied steps once, not per node
     // backward step with rv later indices: g1, g2 (12 rv), Z g1 and Z g2 (16 rv^2), corner (8 rv)
     auto bstep = [](int rv) { return 16.0 * rv * rv + 20.0 * rv; };
@@ -641,8 +649,7 @@ extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, 
     if (!(f > 0.0)) return 0.0;
     // T is a gather; each of the n x n cotangent entries takes 2 complex additions
     // instead of 2n complex multiply-adds
-    const double t_products = 16.0 * n * ((double)n * n - tri_count(ne) - tri_count(n - ne));
-    return f - t_products - (grad_gamma_flops(n, ne) - (double)n * n * 2 * 2.0);
+    return f - grad_T_flops(n, ne) - (grad_gamma_flops(n, ne) - (double)n * n * 2 * 2.0);
 }
 
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {

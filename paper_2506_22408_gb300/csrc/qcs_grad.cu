@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
     cd *Gs = reinterpret_cast<cd *>(wb + A.off_G);
     cd *Ns = reinterpret_cast<cd *>(wb + A.off_NZ);  // node factors, then their inverses, then G_X
     cd *GX = Ns;
+    double *Uss = reinterpret_cast<double *>(Ns);  // while T is formed (n = 16): re + im of Ut
     cd *g1v = reinterpret_cast<cd *>(wb + A.off_g1);  // forward: U vectors
     cd *g2v = reinterpret_cast<cd *>(wb + A.off_g2);  // forward: V vectors
     cd *y1v = reinterpret_cast<cd *>(wb + A.off_y1);
@@ -132,9 +133,17 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                     }
                 } else {
                     load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
+                    if (n == 16)  // re + im of the walker rows for build_T_reg, in G_X's region (free here)
+                        for (int e = t; e < n * n; e += kGroup) {
+                            const int j = e / n, k = e - j * n;
+                            const cd u = Uts[j * lu + k];
+                            Uss[j * lu + k] = u.x + u.y;
+                        }
                 }
                 group_sync(bar);
                 if (sp) build_T_gather(n, Uts, gq, Ts, t, kGroup);
+                else if (n == 16)  // lane = column of T, the two warps take alternate rows
+                    build_T_reg<16>(ne, Uts, Uss, Qs, Ts, t & 31, false, lq, t >> 5, kGroup / 32);
                 else build_T_echelon(n, ne, Uts, Qs, Ts, t, kGroup);  // walker rows in echelon form
                 group_sync(bar);
                 build_B(n, ne, Ts, Bs, tab, t, kGroup);

@@ -82,13 +82,16 @@ __device__ inline void build_T_echelon(int n, int ne, const cd *__restrict__ Uts
         p3 = fma(us[K], qs[K], p3);           \
         break;                                \
     }
+// Qg holds the snapshot's rows with stride ldq (global memory or staged); rows
+// j0, j0 + jstep, ... of T are formed, so that several warps can share one T.
 template <int N>
 __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const double *__restrict__ Uss,
-                                   const cd *__restrict__ Qg, cd *__restrict__ Ts, int lane, bool reduced) {
+                                   const cd *__restrict__ Qg, cd *__restrict__ Ts, int lane, bool reduced,
+                                   int ldq = N, int j0 = 0, int jstep = 1) {
     static_assert(N == 16, "one lane per column of T: 2N must be the warp width");
     const int lu = ld_ut(N), lt = ld_t(N);
     double qr[N], qi[N], qs[N];
-    const cd *qrow = Qg + lane * N;
+    const cd *qrow = Qg + lane * ldq;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const cd q = qrow[k];
@@ -96,7 +99,7 @@ __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const dou
         qi[k] = q.y;
         qs[k] = q.x + q.y;
     }
-    for (int j = 0; j < N; ++j) {
+    for (int j = j0; j < N; j += jstep) {
         const cd *ur = Uts + j * lu;
         const double *us = Uss + j * lu;
         double p1 = 0.0, p2 = 0.0, p3 = 0.0;
