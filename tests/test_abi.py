@@ -58,3 +58,33 @@ def test_flop_accounting_host_only():
     assert p12["T"] == 8 * 2 * n * (n * n - tri(ne) - tri(d))
     assert lib.qcs_overlap_flops_per_pair(n, ne, 0, 0) == sum(p12.values())
     assert lib.qcs_overlap_flops_per_pair(16, 7, 0, 0) == 0.0  # odd ne rejected
+
+
+def test_gradient_flop_accounting_host_only():
+    lib = qcs.load()
+
+    def tri(k):
+        return k * (k - 1) // 2
+
+    def step(r):  # one elimination step of an r x r Pfaffian
+        return 16 * tri(r - 2) + 6 * (r - 2)
+
+    def bstep(rv):  # one backward step of the inverse with rv later indices
+        return 16 * rv * rv + 20 * rv
+
+    n, ne, nev = 16, 8, 3  # Gauss plan: 3 nodes
+    d, m = n - ne, 2 * n - ne
+    macs = 2 * n * (n * n - tri(ne) - tri(d))       # echelon-form walker rows
+    t = 6 * macs + 3 * 2 * n * n + 2 * n * n        # three real products per term
+    b = 16 * n * tri(ne) + 8 * n * ne * 2 * d + 4 * n * tri(2 * d)
+    elim = sum(step(r) for r in range(m, 2 * d, -2)) + nev * sum(step(r) for r in range(2 * d, 2, -2))
+    inv = nev * (sum(bstep(rv) for rv in range(2 * d - 2, 0, -2)) + 8 * tri(2 * d))
+    inv += sum(bstep(rv) for rv in range(2 * d, m - 1, 2))
+    gx = m * 2 * n * (8 * ne + 4 * (m - ne))        # G_X = Y (X J), real rows of the empty modes
+    gam = 6 * n * n * 2 * n + 2 * 2 * n * n + 3 * n * n + 2 * d * 2 * n
+    f = lib.qcs_grad_flops_per_pair(16, 8, 0, 0)
+    assert f == t + b + elim + inv + gx + gam
+    # signed permutations: T is a gather, each cotangent entry two complex additions
+    fs = lib.qcs_grad_flops_per_pair_signed_perm(16, 8, 0, 0)
+    assert fs == f - t - (gam - 2 * d * 2 * n) + 4 * n * n
+    assert lib.qcs_grad_flops_per_pair(16, 7, 0, 0) == 0.0
