@@ -138,6 +138,18 @@ qcs_status qcs_sync_status(qcs_ctx *ctx, void *stream);
 /* Bytes of device workspace currently held by the context. */
 size_t qcs_workspace_bytes(const qcs_ctx *ctx);
 
+/* Self-test of the device time-out path (failure detection without a fault).
+ * Every device wait of the library (the split-precision kernel's mbarrier waits
+ * for its bulk copies and MMAs) is bounded: when the limit runs out the kernel
+ * ORs QCS_ERR_TIMEOUT into the status word, drains and returns.  This call
+ * launches one block that waits, through the same bounded wait, on an mbarrier
+ * whose one expected arrival never happens, polling at most max_iter times;
+ * no copy or MMA is issued, so nothing is in flight when it returns.
+ * Arguments: max_iter in [1, 2^20]; stream a cudaStream_t (NULL = default).
+ * Returns QCS_OK once launched (read QCS_ERR_TIMEOUT with qcs_sync_status),
+ * QCS_ERR_ARG for max_iter out of range, QCS_ERR_CUDA if the launch fails. */
+qcs_status qcs_selftest_bounded_wait(qcs_ctx *ctx, uint32_t max_iter, void *stream);
+
 /* ---------------------------------------------------------- snapshots */
 
 /* Build the device representation of P snapshots (Q_p, b_p).

@@ -39,6 +39,7 @@ EXPORTED = [
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
     "qcs_local_energy", "qcs_local_energy_flops_per_pair", "qcs_overlap_flops_breakdown",
+    "qcs_selftest_bounded_wait",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_sync_status.argtypes = [P, P]
         lib.qcs_workspace_bytes.argtypes = [P]
         lib.qcs_workspace_bytes.restype = ctypes.c_size_t
+        lib.qcs_selftest_bounded_wait.argtypes = [P, u32, P]
         lib.qcs_build_snapshots.argtypes = [P, i32, i64, P, P, ctypes.POINTER(P), P]
         lib.qcs_snapshots_free.argtypes = [P]
         lib.qcs_snapshots_parity.argtypes = [P, P, P]
@@ -195,6 +197,11 @@ class Context:
 
     def workspace_bytes(self) -> int:
         return int(self.lib.qcs_workspace_bytes(self.h))
+
+    def selftest_bounded_wait(self, max_iter: int = 64) -> int:
+        """Run the device time-out self-test; returns the status bits it raised."""
+        self.check(self.lib.qcs_selftest_bounded_wait(self.h, max_iter, _stream()))
+        return self.sync_status()
 
     def profile(self, enable: bool = True):
         self.check(self.lib.qcs_profile_enable(self.h, 1 if enable else 0))

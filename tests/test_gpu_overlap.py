@@ -232,6 +232,29 @@ def test_nonfinite_input_sets_status(ctx):
     assert st & 4
 
 
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """Failure detection without a fault: a device wait on an mbarrier that nothing
+    completes gives up after its iteration limit, raises QCS_ERR_TIMEOUT in the
+    status word and returns; the context keeps working afterwards."""
+    assert ctx.sync_status() == 0
+    for it in (1, 64, 4096):
+        assert ctx.selftest_bounded_wait(it) == qcs.QCS_ERR_TIMEOUT
+    with pytest.raises(qcs.QCSError):
+        ctx.selftest_bounded_wait(0)
+    with pytest.raises(qcs.QCSError):
+        ctx.selftest_bounded_wait((1 << 20) + 1)
+    rng = np.random.default_rng(12)
+    n, ne = 6, 2
+    Q = synth.haar_orthogonal(rng, 2 * n, 8)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 2)
+    ov, pp, par, st = run_gpu(ctx, dict(Phi=Phi, Q=Q, b=b))
+    assert st == 0
+    oo, opp, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    check_pairs(pp, opp, sc, par)
+    check_walkers(ov, oo, sc)
+
+
 def test_paper_shaped_full_size_sampled(ctx):
     """n = 16, ne = 8, 1024 walkers x 20000 snapshots as timed by bench.py: sampled
     pairs and three whole walkers are recomputed by the oracle."""
