@@ -24,8 +24,10 @@
 //     tr((A_k^-1 A')^2) = tr((P^-1 A'_oo)^2) + 2 tr(Z_k H) + tr((Z_k G)^2).
 // P^-1 comes from the backward recursion over the shared steps (qcs_group.cuh) run
 // with Z = 0; pairs whose occupied block would grow the complement beyond 2^5 take
-// the full inverse per node.  Per Cholesky vector the pair costs
-// O(m (2n)^2 + m^2 d + nodes d^3).  The second-order term's sum_gamma X'_g J X'_g^T is
+// the full inverse per node.  The snapshot enters the operator terms through
+// Mt = (Q'^T J X^T)^T, formed once per pair: X' J X^T = (K ell) Mt^T, so A' is
+// (K ell) Mt^T minus its transpose and X' itself is never formed.  Per Cholesky vector
+// the pair costs O(m^2 n + m^2 d + nodes d^3).  The second-order term's sum_gamma X'_g J X'_g^T is
 // K Lambda_p K^T with Lambda_p = sum_gamma ell_gamma G_p ell_gamma^T formed once per
 // snapshot (energy_lambda_kernel).
 #include "qcs_group.cuh"
@@ -93,72 +95,112 @@ __device__ inline void build_Sacc(int n, int m, const cd *__restrict__ Kw, const
     group_sync(bar);
 }
 
-// A' = X' J X^T + X J X'^T (plus 2 Sacc on the A'' pass) and, when acc_s, Sacc += X' J X'^T,
-// in three uniform loops over the pairs a < b: both occupied, occupied x empty, both empty.
-// The rows of X for empty modes are real (Re T_j, -Im T_j), so products with them take
-// two real multiply-adds instead of four.
-__device__ inline void build_Ap(int n, int ne, int m, const cd *__restrict__ X1, int lx, const cd *__restrict__ Ts,
-                                int lt, cd *__restrict__ Ap, cd *__restrict__ Sacc, bool last, bool acc_s,
+// Mt[b][mu] = (Q'^T J X^T)[mu][b] = sum_k Q'[2k][mu] X[b][2k+1] - Q'[2k+1][mu] X[b][2k], so that
+// X' J X^T = (K ell) Q'^T J X^T = (K ell) Mt^T for every operator: the snapshot enters once
+// per pair instead of once per operator.  Q'[c][2k] = Re Qt[c][k], Q'[c][2k+1] = -Im Qt[c][k];
+// the rows of X for empty modes are real (Re T_j, -Im T_j), and so are those rows of Mt
+// (stored with a zero imaginary part).
+__device__ inline void build_Mt(int n, int ne, int m, const cd *__restrict__ Qs, int lq, const cd *__restrict__ Ts,
+                                int lt, cd *__restrict__ Mt, int lx, int t) {
+    const int n2 = 2 * n;
+    for (int e = t; e < m * n2; e += kGroup) {
+        const int b = e / n2, mu = e - b * n2, kq = mu >> 1;
+        const bool odd = (mu & 1) != 0;
+        if (b < ne) {
+            const cd *xb = Ts + b * lt;
+            cd v = cmk(0.0, 0.0);
+            for (int k = 0; k < n; ++k) {
+                const cd q0 = Qs[(2 * k) * lq + kq], q1 = Qs[(2 * k + 1) * lq + kq];
+                crfma(v, xb[2 * k + 1], odd ? -q0.y : q0.x);
+                crfma(v, xb[2 * k], odd ? q1.y : -q1.x);
+            }
+            Mt[b * lx + mu] = v;
+        } else {
+            const int r = b - ne;
+            const cd *tr = Ts + (ne + (r >> 1)) * lt;
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const cd q0 = Qs[(2 * k) * lq + kq], q1 = Qs[(2 * k + 1) * lq + kq];
+                const double x1 = (r & 1) ? -tr[2 * k + 1].y : tr[2 * k + 1].x;
+                const double x0 = (r & 1) ? -tr[2 * k].y : tr[2 * k].x;
+                v = fma(x1, odd ? -q0.y : q0.x, v);
+                v = fma(x0, odd ? q1.y : -q1.x, v);
+            }
+            Mt[b * lx + mu] = cmk(v, 0.0);
+        }
+    }
+}
+
+// A' = N - N^T with N = X' J X^T = Ks Mt^T (Ks: the operator's rows K ell staged in shared
+// memory, Mt from build_Mt), plus 2 Sacc on the A'' pass:
+//     A'_ab = sum_mu Ks[a][mu] Mt[b][mu] - Ks[b][mu] Mt[a][mu],
+// in three uniform loops over the pairs a < b: both occupied, occupied x empty, both
+// empty.  The rows of Mt for empty modes are real, so products with them take two real
+// multiply-adds instead of four.
+__device__ inline void build_Ap(int n, int ne, int m, const cd *__restrict__ Ks, int lx, const cd *__restrict__ Mt,
+                                cd *__restrict__ Ap, const cd *__restrict__ Sacc, bool last,
                                 const uint16_t *__restrict__ tab, int t) {
-    const int d2 = m - ne, c1 = tri_count(ne), c2 = ne * d2, c3 = tri_count(d2);
-    auto xre = [&](int r, int c) {  // X row ne + r (real) at column c
-        const cd v = Ts[(ne + (r >> 1)) * lt + c];
-        return (r & 1) ? -v.y : v.x;
-    };
+    const int n2 = 2 * n, d2 = m - ne, c1 = tri_count(ne), c2 = ne * d2, c3 = tri_count(d2);
     auto finish = [&](int a, int b, cd v) {
         const int e = tri_index(a, b);
-        if (last) {
-            v = cadd(v, cscale(Sacc[e], 2.0));
-        } else if (acc_s) {
-            const cd *xa = X1 + a * lx, *xb = X1 + b * lx;
-            cd s = cmk(0.0, 0.0);
-            for (int j = 0; j < n; ++j) {
-                cfma(s, xa[2 * j], xb[2 * j + 1]);
-                cfms(s, xa[2 * j + 1], xb[2 * j]);
-            }
-            Sacc[e] = cadd(Sacc[e], s);
-        }
+        if (last) v = cadd(v, cscale(Sacc[e], 2.0));
         Ap[e] = v;
     };
-    for (int u = t; u < c1; u += kGroup) {  // occupied x occupied: complex rows
+    for (int u = t; u < c1; u += kGroup) {  // occupied x occupied: complex rows of Mt
         int a, b;
         pair_of(tab, u, a, b);
-        const cd *xa = X1 + a * lx, *xb = X1 + b * lx, *ta = Ts + a * lt, *tb = Ts + b * lt;
+        const cd *ka = Ks + a * lx, *kb = Ks + b * lx, *ma = Mt + a * lx, *mb = Mt + b * lx;
         cd v = cmk(0.0, 0.0);
-        for (int j = 0; j < n; ++j) {
-            cfma(v, xa[2 * j], tb[2 * j + 1]);
-            cfms(v, xa[2 * j + 1], tb[2 * j]);
-            cfma(v, ta[2 * j], xb[2 * j + 1]);
-            cfms(v, ta[2 * j + 1], xb[2 * j]);
+        for (int mu = 0; mu < n2; ++mu) {
+            cfma(v, ka[mu], mb[mu]);
+            cfms(v, kb[mu], ma[mu]);
         }
         finish(a, b, v);
     }
     for (int u = t; u < c2; u += kGroup) {  // occupied a x empty b = ne + r
         const int a = u / d2, r = u - a * d2, b = ne + r;
-        const cd *xa = X1 + a * lx, *xb = X1 + b * lx, *ta = Ts + a * lt;
+        const cd *ka = Ks + a * lx, *kb = Ks + b * lx, *ma = Mt + a * lx, *mb = Mt + b * lx;
         cd v = cmk(0.0, 0.0);
-        for (int j = 0; j < n; ++j) {
-            crfma(v, xa[2 * j], xre(r, 2 * j + 1));
-            crfma(v, xa[2 * j + 1], -xre(r, 2 * j));
-            cfma(v, ta[2 * j], xb[2 * j + 1]);
-            cfms(v, ta[2 * j + 1], xb[2 * j]);
+        for (int mu = 0; mu < n2; ++mu) {
+            crfma(v, ka[mu], mb[mu].x);
+            cfms(v, kb[mu], ma[mu]);
         }
         finish(a, b, v);
     }
-    for (int u = t; u < c3; u += kGroup) {  // empty x empty: real rows of X
+    for (int u = t; u < c3; u += kGroup) {  // empty x empty: real rows of Mt
         int ra, rb;
         pair_of(tab, u, ra, rb);
         const int a = ne + ra, b = ne + rb;
-        const cd *xa = X1 + a * lx, *xb = X1 + b * lx;
+        const cd *ka = Ks + a * lx, *kb = Ks + b * lx, *ma = Mt + a * lx, *mb = Mt + b * lx;
         cd v = cmk(0.0, 0.0);
-        for (int j = 0; j < n; ++j) {
-            crfma(v, xa[2 * j], xre(rb, 2 * j + 1));
-            crfma(v, xa[2 * j + 1], -xre(rb, 2 * j));
-            crfma(v, xb[2 * j + 1], xre(ra, 2 * j));
-            crfma(v, xb[2 * j], -xre(ra, 2 * j + 1));
+        for (int mu = 0; mu < n2; ++mu) {
+            crfma(v, ka[mu], mb[mu].x);
+            crfma(v, kb[mu], -ma[mu].x);
         }
         finish(a, b, v);
     }
+}
+
+// Per pair, before the first operator: Mt into the X' region (free between the node
+// rounds and the operator loop), then into the snapshot-row and T regions, which are
+// contiguous and no longer needed for this pair.
+__device__ inline void stage_Mt(int n, int ne, int m, const cd *__restrict__ Qs, int lq, const cd *__restrict__ Ts,
+                                int lt, cd *__restrict__ X1, int lx, cd *__restrict__ Mt, int t, int bar) {
+    build_Mt(n, ne, m, Qs, lq, Ts, lt, X1, lx, t);
+    group_sync(bar);
+    for (int e = t; e < m * lx; e += kGroup) Mt[e] = X1[e];
+    group_sync(bar);
+}
+
+// The operator's rows K ell (global memory, m x 2n) into the X' region, row stride lx.
+__device__ inline void stage_Ko(int n, int m, const cd *__restrict__ Ko, cd *__restrict__ Ks, int lx, int t,
+                                int bar) {
+    const int n2 = 2 * n;
+    for (int e = t; e < m * n2; e += kGroup) {
+        const int a = e / n2, c = e - a * n2;
+        Ks[a * lx + c] = Ko[e];
+    }
+    group_sync(bar);
 }
 
 __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_constant__ EnergyArgs A) {
@@ -191,7 +233,8 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
     uint8_t *acth = wb + A.off_acth;
     uint8_t *kh = wb + A.off_kh;
     uint8_t *ph = wb + A.off_ph;
-    cd *X1 = reinterpret_cast<cd *>(wb + A.off_X1);     // X' (or X'') rows, m x (2n+1)
+    cd *X1 = reinterpret_cast<cd *>(wb + A.off_X1);     // K ell (or K ell^2) rows, m x (2n+1)
+    cd *Mt = Qs;  // from the operator loop on: Mt (m x (2n+1)) over the snapshot-row and T regions
     cd *Ap = reinterpret_cast<cd *>(wb + A.off_Ap);     // A' (packed upper skew)
     cd *Sacc = reinterpret_cast<cd *>(wb + A.off_Sacc); // sum_gamma X'_g J X'_g^T (packed)
     cd *red = reinterpret_cast<cd *>(wb + A.off_red);   // 2 entries
@@ -271,25 +314,15 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                         if (t == 0)
                             for (int v = 0; v < nb; ++v) cfma(Sop, A.gamma[k0 + v], cmul(pf0, pf[v]));
                         group_sync(bar);
+                        if (k0 == 0) stage_Mt(n, ne, m, Qs, lq, Ts, lt, X1, lx, Mt, t, bar);
                         for (int o = 0; o <= A.nop; ++o) {
                             const bool is_h = A.has_h && o == A.nchol;
                             const bool last = o == A.nop;
                             const bool second = !is_h && !last;  // a Cholesky vector: second derivative
                             const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
                             if (last) build_Sacc(n, m, Kgw, A.Lam + pq * tri_count(n2), X1, lx, Sacc, tab, t, bar);
-                            for (int e = t; e < m * n2; e += kGroup) {
-                                const int a = e / n2, c = e - a * n2;
-                                const cd *kr = Ko + a * n2;
-                                const cd *qr = Qs + c * lq;
-                                cd s = cmk(0.0, 0.0);
-                                for (int k = 0; k < n; ++k) {
-                                    crfma(s, kr[2 * k], qr[k].x);
-                                    crfma(s, kr[2 * k + 1], -qr[k].y);
-                                }
-                                X1[a * lx + c] = s;
-                            }
-                            group_sync(bar);
-                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, false, tab, t);
+                            stage_Ko(n, m, Ko, X1, lx, t, bar);
+                            build_Ap(n, ne, m, X1, lx, Mt, Ap, Sacc, last, tab, t);
                             group_sync(bar);
                             // X' is consumed: its region holds W, G, V, H
                             cd *Wm = X1, *Gp = X1 + m * d2, *Vm = Gp + Tn, *Hp = Vm + ne * d2;
@@ -440,6 +473,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                         if (t == 0)
                             for (int v = 0; v < nb; ++v) cfma(Sop, A.gamma[k0 + v], pf[v]);
                         group_sync(bar);
+                        if (k0 == 0) stage_Mt(n, ne, m, Qs, lq, Ts, lt, X1, lx, Mt, t, bar);
                         // operators: Cholesky vectors (second derivative), then h (first derivative);
                         // the last pass (o = nop) forms A'' = X'' J X^T + X J X''^T + 2 Sacc
                         for (int o = 0; o <= A.nop; ++o) {
@@ -447,21 +481,8 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                             const bool last = o == A.nop;
                             const cd *Ko = last ? K2w : Kw + (size_t)o * m * n2;
                             if (last) build_Sacc(n, m, Kgw, A.Lam + pq * tri_count(n2), X1, lx, Sacc, tab, t, bar);
-                            // X1 = Ko Q'^T: X1[a][c] = sum_k Ko[a][2k] Re Qt[c][k] - Ko[a][2k+1] Im Qt[c][k]
-                            for (int e = t; e < m * n2; e += kGroup) {
-                                const int a = e / n2, c = e - a * n2;
-                                const cd *kr = Ko + a * n2;
-                                const cd *qr = Qs + c * lq;
-                                cd s = cmk(0.0, 0.0);
-                                for (int k = 0; k < n; ++k) {
-                                    crfma(s, kr[2 * k], qr[k].x);
-                                    crfma(s, kr[2 * k + 1], -qr[k].y);
-                                }
-                                X1[a * lx + c] = s;
-                            }
-                            group_sync(bar);
-                            // Ap = X1 J X^T + X J X1^T (+ 2 Sacc on the last pass); Sacc += X1 J X1^T
-                            build_Ap(n, ne, m, X1, lx, Ts, lt, Ap, Sacc, last, false, tab, t);
+                            stage_Ko(n, m, Ko, X1, lx, t, bar);
+                            build_Ap(n, ne, m, X1, lx, Mt, Ap, Sacc, last, tab, t);
                             group_sync(bar);
                             for (int v = 0; v < nb; ++v) {
                                 const cd *Zv = Ns + v * T;  // A_v^-1
@@ -714,7 +735,9 @@ size_t energy_group_layout(EnergyArgs &A) {
     const size_t zoff = (size_t)(T > NB * Tn ? T : NB * Tn);
     if (zoff + To + (size_t)A.ne * d2 + Tn > nz) nz = zoff + To + (size_t)A.ne * d2 + Tn;
     o = align16(o + nz * sizeof(cd));
-    // shared region: Ut rows, then the recursion vectors, then X' (then W, G, V, H)
+    // shared region: Ut rows, then the recursion vectors, then Mt on its way to the Q and T
+    // regions (m (2n+1) <= 2n (n+1) + n (2n+1) entries, contiguous), then each operator's
+    // rows K ell (then W, G, V, H)
     size_t r = (size_t)m * (2 * n + 1);
     if ((size_t)n * ld_ut(n) > r) r = (size_t)n * ld_ut(n);
     if ((size_t)4 * NB * m > r) r = (size_t)4 * NB * m;
@@ -916,9 +939,11 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     double inv = 0.0;                                                 // each complement's inverse
     for (int rv = d2i - 2; rv > 0; rv -= 2) inv += bstep(rv);
     f += inv * nev;
-    const double xprime = 4.0 * m * n2 * n2;      // X' = (K ell) Q'^T, complex x real
-    // A' = X' J X^T + X J X'^T (upper triangle): complex x complex products where both
-    // rows are occupied, complex x real where a row of X belongs to an empty mode
+    // once per pair: Mt = (Q'^T J X^T)^T, real Q' against complex (occupied) or real
+    // (empty) rows of X, n steps of two products per entry
+    const double mt = n2 * n * (8.0 * ne + 4.0 * d2);
+    // A' = (K ell) Mt^T - its transpose (upper triangle): complex x complex products where
+    // the row of Mt is occupied, complex x real where it belongs to an empty mode
     const double c1 = ne * (ne - 1) / 2.0, c2 = ne * d2, c3 = d2 * (d2 - 1) / 2;
     const double aprime = 8.0 * n2 * (2.0 * c1 + c2) + 4.0 * n2 * (c2 + 2.0 * c3);
     const double wg = 8.0 * m * d2 * ne + 8.0 * Tn * ne + 8.0 * To;  // W = A'F, G = F^T W, tr(P^-1 A'_oo)
@@ -933,7 +958,7 @@ extern "C" double qcs_local_energy_flops_per_pair(int n, int ne, int nchol, int 
     const double items = d2 * (d2 + 1) / 2;
     const double t2 = 8.0 * Tn + (sums ? items * 2.0 * (6.0 * (d2 - 1) + 3.0) : items * 2.0 * 8.0 * (d2 - 1));
     const double npass = nchol + has_h + 1.0;                         // operators and the A'' pass
-    f += npass * (xprime + aprime + wg + nev * t1);
+    f += mt + npass * (aprime + wg + nev * t1);
     f += nchol * (vh + nev * t2);
     // sum_gamma X'_g J X'_g^T = K Lambda_p K^T once per pair (Lambda_p per snapshot, shared by
     // every walker, is the separate energy_lambda_kernel)
