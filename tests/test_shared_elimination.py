@@ -8,7 +8,8 @@ matrices from the oracle (no GPU):
   complement, so one pass started from sum_k c_k Z_k (each step's constant scaled by
   sum_k c_k) gives sum_k c_k A_k^{-1};
 * the local-energy traces follow from A_k^{-1} = F0 + F Z_k F^T with 2d x 2d work per
-  node;
+  node, and its operator matrices A' need the snapshot only through M^T = Q'^T J X^T,
+  formed once per pair;
 * the estimator is multilinear and alternating in the occupied orbitals:
   o(Phi W) = det(W) o(Phi) for any ne x ne matrix W, which is what lets the walker prep
   rotate the occupied orbitals to echelon form and fold det W into det R.
@@ -213,3 +214,44 @@ def test_block_form_traces(n, ne):
         b2 = np.trace(PA @ PA) + 2 * np.trace(Z @ H) + np.trace(Z @ G @ Z @ G)
         assert abs(b1 - t1) <= 1e-10 * max(1.0, abs(t1))
         assert abs(b2 - t2) <= 1e-10 * max(1.0, abs(t2))
+
+
+def J_matrix(n):
+    J = np.zeros((2 * n, 2 * n))
+    for k in range(n):
+        J[2 * k, 2 * k + 1], J[2 * k + 1, 2 * k] = 1.0, -1.0
+    return J
+
+
+@pytest.mark.parametrize("n,ne", [(16, 8), (12, 6), (16, 16), (10, 2)])
+def test_energy_snapshot_product_once_per_pair(n, ne):
+    """The local-energy kernel never forms X' = (K ell) Q'^T: with M^T = Q'^T J X^T, built
+    once per pair, X' J X^T = (K ell) M^T and A' = X' J X^T + X J X'^T is (K ell) M^T minus
+    its transpose.  Restates the kernel's index formulas (complexified snapshot rows
+    Qt[c][k] = Q'[c][2k] - i Q'[c][2k+1], the rows of X for empty modes (Re T_j, -Im T_j))
+    and compares with the definition formed by plain matrix products."""
+    rng = np.random.default_rng(400 + n + ne)
+    m, n2 = 2 * n - ne, 2 * n
+    Qp = synth.haar_orthogonal(rng, n2, 1)[0]               # Q' (real)
+    Qt = Qp[:, 0::2] - 1j * Qp[:, 1::2]                      # 2n x n
+    Ts = rng.standard_normal((n, n2)) + 1j * rng.standard_normal((n, n2))
+    X = np.zeros((m, n2), complex)
+    X[:ne] = Ts[:ne]
+    for r in range(m - ne):
+        X[ne + r] = -Ts[ne + r // 2].imag if r & 1 else Ts[ne + r // 2].real
+    Ko = rng.standard_normal((m, n2)) + 1j * rng.standard_normal((m, n2))  # K ell
+    J = J_matrix(n)
+    Xp = Ko @ Qp.T
+    ref = Xp @ J @ X.T + X @ J @ Xp.T
+    # the kernel's Mt[b][mu] = sum_k Q'[2k][mu] X[b][2k+1] - Q'[2k+1][mu] X[b][2k]
+    Mt = np.zeros((m, n2), complex)
+    for mu in range(n2):
+        kq, odd = mu >> 1, mu & 1
+        q0 = -Qt[0::2, kq].imag if odd else Qt[0::2, kq].real      # Q'[2k][mu]
+        q1 = -Qt[1::2, kq].imag if odd else Qt[1::2, kq].real      # Q'[2k+1][mu]
+        Mt[:, mu] = X[:, 1::2] @ q0 - X[:, 0::2] @ q1
+    assert np.all(Mt[ne:].imag == 0)  # real rows for the empty modes
+    N = Ko @ Mt.T
+    got = N - N.T
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(Mt.T - Qp.T @ J @ X.T).max() <= 1e-12 * np.abs(Mt).max()
