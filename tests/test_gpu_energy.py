@@ -60,6 +60,25 @@ def test_local_energy_matches_oracle(ctx, n, ne, W, P, nchol, ens):
         assert np.all(np.abs(got - ref) <= TOL * np.maximum(1.0, np.abs(ref))), (got, ref)
 
 
+@pytest.mark.parametrize("n,ne,flags", [(8, 4, qcs.QCS_FLAG_ALL_NODES), (12, 2, qcs.QCS_FLAG_ALL_NODES),
+                                         (20, 10, 0)])
+def test_node_rounds_and_larger_n(ctx, n, ne, flags):
+    """More node matrices than one round holds (all 2n+1 roots of unity: 5 and 11 parity +1
+    nodes, two and three rounds that repeat the per-operator work over the snapshot
+    product staged once per pair), and n > 16 with the default plan."""
+    Q, b, Phi, L, h = case(600 + n + ne, n, ne, 2, 12, 2, bits="parity")
+    s = qcs.Snapshots(ctx, dev(Q), dev(b))
+    ov, e1, e2 = qcs.local_energy(ctx, s, dev(Phi), dev(L), dev(h), flags=flags)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    oo, o1, o2 = orc.local_energy(Phi, Q, b, L, h=h)
+    _, _, sc, _ = orc.overlap(Phi, Q, b, per_pair=True)
+    assert np.all(np.abs(ov.cpu().numpy() - oo) <= 1e-10 * sc.mean(axis=1))
+    for got, ref in ((e1, o1), (e2, o2)):
+        got = got.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= TOL * np.maximum(1.0, np.abs(ref))), (got, ref)
+
+
 def test_one_body_term_matches_gradient_route(ctx):
     """e1 from qcs_local_energy equals tr(h G), G = Phi g^T / O, from the adjoint kernel and
     the force-bias kernel (i tr(L G) with L = h): two GPU routes."""
