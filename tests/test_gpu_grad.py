@@ -172,6 +172,13 @@ def test_force_bias(ctx):
     xo = orc.force_bias(L, Phi, oo, og)
     xg = qcs.force_bias(ctx, dev(L), dev(Phi), dev(ov), dev(g)).cpu().numpy()
     assert np.abs(xg - xo).max() <= 1e-7 * np.abs(xo).max()
+    # complex operators without symmetry: L and L^T give different force biases
+    Lc = rng.standard_normal((5, n, n)) + 1j * rng.standard_normal((5, n, n))
+    xc = qcs.force_bias(ctx, dev(Lc), dev(Phi), dev(ov), dev(g)).cpu().numpy()
+    refc = orc.force_bias(Lc, Phi, ov, g)
+    assert np.abs(xc - refc).max() <= 1e-12 * np.abs(refc).max()
+    refT = orc.force_bias(np.ascontiguousarray(Lc.transpose(0, 2, 1)), Phi, ov, g)
+    assert np.abs(refT - refc).max() > 1e-3 * np.abs(refc).max()
 
 
 def test_autograd_function(ctx):

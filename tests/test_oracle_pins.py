@@ -373,7 +373,9 @@ def test_gradient_exact_linearity_and_euler():
 
 def test_force_bias_exact_for_slater_trial():
     """With the exact signed-permutation group average (n = 3), the shadow overlap
-    and gradient are exact, so the force bias equals i tr(L Phi (Psi^dag Phi)^{-1} Psi^dag)."""
+    and gradient are exact, so the force bias equals i tr(L Phi (Psi^dag Phi)^{-1} Psi^dag),
+    and, for complex operators without symmetry (so that L and L^T differ), the Fock-space
+    mixed estimate i <Psi_T| sum_pq L_pq a_p^dag a_q |phi> / <Psi_T|phi> of Eq. (force_bias)."""
     rng = np.random.default_rng(900)
     n, ne = 3, 2
     F = Fock(n)
@@ -404,6 +406,14 @@ def test_force_bias_exact_for_slater_trial():
     assert np.abs(xb - ref).max() < 1e-11
     xb2 = orc.force_bias(L.astype(complex), Phi[None], np.array([O]), g[None], sqrt_dt=0.1)[0]
     assert np.allclose(xb2, -0.1 * ref, atol=1e-12)
+    Lc = rng.standard_normal((3, n, n)) + 1j * rng.standard_normal((3, n, n))
+    xc = orc.force_bias(Lc, Phi[None], np.array([O]), g[None], sqrt_dt=0.0)[0]
+    phi = F.slater(Phi)
+    Ofock = np.vdot(PsiT, phi)
+    for c in range(3):
+        v = sum(Lc[c, p, q] * (F.a[p].conj().T @ (F.a[q] @ phi)) for p in range(n) for q in range(n))
+        assert abs(xc[c] - 1j * np.vdot(PsiT, v) / Ofock) < 1e-11
+        assert abs(xc[c] - 1j * np.trace(Lc[c].T @ Gf)) > 1e-3  # the transposed operator differs
 
 
 # ------------------------------- shadow RDMs (Supplementary "Reduced Density Matrices")
