@@ -46,6 +46,10 @@ MUTATIONS = {
     8: "Pfaffian pivot swap without the sign flip",
     9: "V = U^T instead of U^dagger",
     10: "1-RDM off-diagonal: signs of the mixed Majorana terms swapped",
+    11: "gradient: column j not cleared before the unit entry is substituted",
+    12: "force bias: tr(L G^T) instead of tr(L G)",
+    13: "VCE factor: det R_c instead of its conjugate",
+    14: "local energy: factor 2 of the symmetric second-derivative pairs dropped",
 }
 
 

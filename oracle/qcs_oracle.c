@@ -574,7 +574,7 @@ int orc_overlap_grad(int n, int ne, int64_t W, int64_t P, const cplx *Phi, const
         if (e > 0) {
             k = (int)((e - 1) / ne);
             j = (int)((e - 1) % ne);
-            for (int r = 0; r < n; ++r) Pm[r * ne + j] = (r == k) ? 1.0 : 0.0;
+            for (int r = 0; r < n; ++r) Pm[r * ne + j] = (r == k) ? 1.0 : (MUT(11) ? Pm[r * ne + j] : 0.0);
         }
         walker_t wk;
         walker_setup(n, ne, Pm, &wk);
@@ -609,7 +609,7 @@ void orc_force_bias(int n, int ne, int64_t W, int nchol, const cplx *L, const cp
             const cplx *Lg = L + (size_t)g * n * n;
             cplx tr = 0.0;
             for (int p = 0; p < n; ++p)
-                for (int q = 0; q < n; ++q) tr += Lg[p * n + q] * Gf[q * n + p];
+                for (int q = 0; q < n; ++q) tr += Lg[p * n + q] * Gf[MUT(12) ? p * n + q : q * n + p];
             cplx v = I * tr;
             xbar[w * nchol + g] = (sqrt_dt != 0.0) ? -sqrt_dt * v : v;
         }
@@ -778,7 +778,7 @@ int orc_vce_transform(int NB, int nc, int na, int nea, const cplx *Phi, cplx *ac
             for (int k = 0; k < ne; ++k) s += Phi[(nc + r) * ne + k] * V[k * ne + nc + c];
             act[r * nea + c] = s;
         }
-    *factor = conj(detR) / cdet_lu(ne, V);
+    *factor = (MUT(13) ? detR : conj(detR)) / cdet_lu(ne, V);
     free(Ct);
     free(V);
     free(Rc);
@@ -887,7 +887,7 @@ int orc_local_energy(int n, int ne, int64_t W, int64_t P, const cplx *Phi, const
             for (int r = 0; r < nsingle; ++r) d1 += vo[r];
             for (int r = 0; r < npair; ++r) d2 += vo[nsingle + r];
             if (h && op == 0) n1 = d1;
-            else n2 += 2.0 * d2 + d1;
+            else n2 += (MUT(14) ? 1.0 : 2.0) * d2 + d1;
         }
         if (e1) e1[w] = (h && O != 0.0) ? n1 / O : 0.0;
         if (e2) e2[w] = (O != 0.0) ? n2 / O : 0.0;

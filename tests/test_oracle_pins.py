@@ -626,6 +626,55 @@ def _pin_suite_passes(v) -> bool:
                 return False
     if _rdm_group_check(v, 2, rng, rotate=False) > 1e-10:
         return False
+    # gradient: the Euler / antisymmetry identity g^T Phi = O I
+    n, ne, P = 5, 2, 12
+    Q = synth.haar_orthogonal(rng, 2 * n, P)
+    b = synth.parity_consistent_bits(rng, Q)
+    Phi = synth.walkers(rng, n, ne, 1)
+    ov, g, _ = v.overlap_grad(Phi, Q, b)
+    if np.abs(g[0].T @ Phi[0] - ov[0] * np.eye(ne)).max() > 1e-10 * np.abs(g[0]).max() * np.abs(Phi[0]).max() * n:
+        return False
+    # VCE: factor * det(chi^dag act) is the full-space determinant
+    NB, nc, na, nea = 14, 3, 6, 2
+    Phv = rng.standard_normal((NB, nc + nea)) + 1j * rng.standard_normal((NB, nc + nea))
+    act, f = v.vce_transform(Phv, nc, na, nea)
+    chi = rng.standard_normal((na, nea)) + 1j * rng.standard_normal((na, nea))
+    full = np.linalg.det(_embed_trial(nc, chi, NB).conj().T @ Phv)
+    if abs(f * np.linalg.det(chi.conj().T @ act) - full) > 1e-12 * max(1.0, abs(full)):
+        return False
+    # force bias for a Slater trial with its exact overlap and gradient
+    # (O = det S, S = Psi^dag Phi, dO/dPhi_kj = sum_i conj(Psi_ki) adj(S)_ji) against the
+    # Fock-space mixed estimate of i sum_pq L_pq a_p^dag a_q, L without symmetry
+    n, ne = 3, 2
+    F = Fock(n)
+    Psi, _ = np.linalg.qr(rng.standard_normal((n, ne)) + 1j * rng.standard_normal((n, ne)))
+    Phs = synth.walkers(rng, n, ne, 1)[0]
+    S = Psi.conj().T @ Phs
+    O = np.linalg.det(S)
+    g = Psi.conj() @ (O * np.linalg.inv(S)).T
+    Lc = rng.standard_normal((2, n, n)) + 1j * rng.standard_normal((2, n, n))
+    xb = v.force_bias(Lc, Phs[None], np.array([O]), g[None], sqrt_dt=0.0)[0]
+    phi, PsiT = F.slater(Phs), F.slater(Psi)
+    for c in range(2):
+        vphi = sum(Lc[c, p, q] * (F.a[p].conj().T @ (F.a[q] @ phi)) for p in range(n) for q in range(n))
+        ref = 1j * np.vdot(PsiT, vphi) / np.vdot(PsiT, phi)
+        if abs(xb[c] - ref) > 1e-10 * max(1.0, abs(ref)):
+            return False
+    # local energy: exact group average at n = 2 against Fock-space values
+    n, ne = 2, 2
+    F = Fock(n)
+    PsiT = _random_eta_state(rng, F, ne)
+    Psi2 = (F.vac + PsiT) / np.sqrt(2)
+    Phe = synth.walkers(rng, n, ne, 1)[0]
+    L = rng.standard_normal((2, n, n)) + 1j * rng.standard_normal((2, n, n))
+    group = np.array(list(signed_permutation_group(2 * n)))
+    Qs, bs, ws = _born_table(F, group, Psi2)
+    ov, _, e2 = v.local_energy(Phe[None], Qs, bs, L, w=ws)
+    phi = F.slater(Phe)
+    op = lambda M: sum(M[p, q] * F.a[p].conj().T @ F.a[q] for p in range(n) for q in range(n))  # noqa: E731
+    ref2 = sum(np.vdot(PsiT, op(Lg) @ (op(Lg) @ phi)) for Lg in L) / np.vdot(PsiT, phi)
+    if abs(e2[0] - ref2) > 1e-10 * max(1.0, abs(ref2)):
+        return False
     return True
 
 
