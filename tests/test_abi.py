@@ -88,3 +88,24 @@ def test_gradient_flop_accounting_host_only():
     fs = lib.qcs_grad_flops_per_pair_signed_perm(16, 8, 0, 0)
     assert fs == f - t - (gam - 2 * d * 2 * n) + 4 * n * n
     assert lib.qcs_grad_flops_per_pair(16, 7, 0, 0) == 0.0
+
+
+def test_host_only_size_checks():
+    """The host-only accounting calls accept every size the library supports
+    (1 <= n <= QCS_MAX_N, even ne with 2 <= ne <= n) and return 0 otherwise."""
+    lib = qcs.load()
+    maxn = 24
+    calls = [lambda n, ne: lib.qcs_overlap_flops_per_pair(n, ne, 0, 0),
+             lambda n, ne: lib.qcs_overlap_flops_per_pair_signed_perm(n, ne, 0, 0),
+             lambda n, ne: lib.qcs_grad_flops_per_pair(n, ne, 0, 0),
+             lambda n, ne: lib.qcs_grad_flops_per_pair_signed_perm(n, ne, 0, 0),
+             lambda n, ne: lib.qcs_local_energy_flops_per_pair(n, ne, 4, 1, 0, 0)]
+    for f in calls:
+        for n, ne in [(2, 2), (16, 8), (maxn, 2), (maxn, maxn), (maxn, 12)]:
+            assert f(n, ne) > 0.0, (n, ne)
+        for n, ne in [(maxn + 1, 2), (16, 7), (8, 10), (8, 0)]:
+            assert f(n, ne) == 0.0, (n, ne)
+    assert lib.qcs_shadow_rdm_flops(16, 1000) > 0.0
+    parts = (ctypes.c_double * 3)()
+    assert lib.qcs_overlap_flops_breakdown(maxn + 1, 2, 0, 0, parts) == qcs.QCS_ERR_ARG
+    assert lib.qcs_overlap_flops_breakdown(16, 8, 0, 0, None) == qcs.QCS_ERR_ARG
