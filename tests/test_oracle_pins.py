@@ -77,6 +77,33 @@ def test_pfaffian_block_canonical_and_congruence():
     assert abs(orc.pfaffian(Pm.T @ D @ Pm) - sgn * np.prod(a)) <= 1e-13 * abs(np.prod(a))
 
 
+@pytest.mark.parametrize("m", [4, 8, 12])
+def test_pfaffian_derivative_equations(m):
+    """Eqs. (Pfaffian_der) and (Pfaffian_2nd_der), on which the gradient and local-energy
+    kernels are built: for A(t) = A + t A' + t^2 A''/2,
+        d pf = (pf/2) tr(A^-1 A'),
+        d^2 pf = (pf/2) [tr(A^-1 A'') - tr(A^-1 A' A^-1 A') + tr(A^-1 A')^2 / 2].
+    pf(A(t)) is a polynomial of degree <= m in t, so its first two Taylor coefficients
+    follow exactly from the oracle's Pfaffian at K > m points of a circle (inverse DFT)."""
+    rng = np.random.default_rng(40 + m)
+    A, A1, A2 = rand_skew(rng, m), rand_skew(rng, m), rand_skew(rng, m)
+    K, r = m + 3, 0.25
+    ts = r * np.exp(2j * np.pi * np.arange(K) / K)
+    vals = np.array([orc.pfaffian(A + t * A1 + 0.5 * t * t * A2) for t in ts])
+    coef = np.array([np.sum(vals * np.exp(-2j * np.pi * np.arange(K) * x / K)) / K / r**x for x in range(3)])
+    pf = orc.pfaffian(A)
+    Ai = np.linalg.inv(A)
+    t1 = np.trace(Ai @ A1)
+    d1 = 0.5 * pf * t1
+    d2 = 0.5 * pf * (np.trace(Ai @ A2) - np.trace(Ai @ A1 @ Ai @ A1) + 0.5 * t1 * t1)
+    assert abs(coef[0] - pf) <= 1e-10 * abs(pf)
+    assert abs(coef[1] - d1) <= 1e-9 * abs(pf) * np.abs(t1).max()
+    assert abs(2 * coef[2] - d2) <= 1e-8 * abs(d2)
+    # a plausible slip in the second-order formula (the squared first-order term left out)
+    # is far outside that bound
+    assert abs(2 * coef[2] - 0.5 * pf * (np.trace(Ai @ A2) - np.trace(Ai @ A1 @ Ai @ A1))) > 1e-3 * abs(d2)
+
+
 def test_pfaffian_degenerate():
     rng = np.random.default_rng(31)
     A = rand_skew(rng, 6)
