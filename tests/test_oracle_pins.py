@@ -615,6 +615,61 @@ def test_local_energy_terms_exact_group_average(n):
     assert abs(e2[0] - ref2) <= 1e-11 * max(1.0, abs(ref2))
 
 
+def _majorana_form(F, L):
+    """ell with [Lhat, g_mu] = sum_a ell[mu][a] g_a for Lhat = sum_pq L_pq a_p^dag a_q, by
+    projecting the Fock-space commutator onto the Majoranas (tr(g_a g_b) = 2^n delta_ab)."""
+    n = F.n
+    Lh = sum(L[p, q] * F.a[p].conj().T @ F.a[q] for p in range(n) for q in range(n))
+    ell = np.zeros((2 * n, 2 * n), complex)
+    for mu in range(2 * n):
+        C = Lh @ F.gamma[mu] - F.gamma[mu] @ Lh
+        for a in range(2 * n):
+            ell[mu, a] = np.trace(F.gamma[a] @ C) / F.dim
+    return ell
+
+
+def test_operator_moves_the_snapshot_not_the_walker():
+    """Reading R19 (how lambda enters A in Eqs. energy_tb_diff, Pfaffian_2nd_der): since
+    <0| Lhat = 0, e^{lambda Lhat}|phi><0| = e^{lambda Lhat} (|phi><0|) e^{-lambda Lhat}, so the
+    pair estimate of the moved walker e^{lambda L} Phi equals that of Phi against the snapshot
+    with covariance R G R^T, R = e^{lambda ell}.  For anti-Hermitian L, R is a rotation and
+    that snapshot is Q R^T; checked pair by pair with the oracle.  Also pins the closed form
+    of ell that the local-energy kernel's preparation uses, for a general complex L:
+    ell[2r][2q] = ell[2r+1][2q+1] = (L_qr - L_rq)/2, ell[2r][2q+1] = -i (L_rq + L_qr)/2,
+    ell[2r+1][2q] = i (L_rq + L_qr)/2."""
+    from scipy.linalg import expm
+
+    rng = np.random.default_rng(950)
+    n, ne = 4, 2
+    F = Fock(n)
+    Lg = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    ell = _majorana_form(F, Lg)
+    cf = np.zeros((2 * n, 2 * n), complex)
+    for r in range(n):
+        for q in range(n):
+            cf[2 * r, 2 * q] = cf[2 * r + 1, 2 * q + 1] = (Lg[q, r] - Lg[r, q]) / 2
+            cf[2 * r, 2 * q + 1] = -1j * (Lg[r, q] + Lg[q, r]) / 2
+            cf[2 * r + 1, 2 * q] = 1j * (Lg[r, q] + Lg[q, r]) / 2
+    assert np.abs(ell - cf).max() < 1e-12
+    H = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    L = H - H.conj().T  # anti-Hermitian: e^{lambda Lhat} unitary, ell real
+    ell = _majorana_form(F, L)
+    assert np.abs(ell.imag).max() < 1e-12
+    lam = 0.37
+    R = expm(lam * ell.real)
+    assert np.abs(R @ R.T - np.eye(2 * n)).max() < 1e-12
+    Phi = synth.walkers(rng, n, ne, 1)[0]
+    Phi_moved = expm(lam * L) @ Phi
+    Q = synth.haar_orthogonal(rng, 2 * n, 6)
+    b = synth.parity_consistent_bits(rng, Q)
+    for p in range(6):
+        o_moved, _, sc = orc.pair(Q[p], b[p], Phi_moved)
+        o_snap, _, _ = orc.pair(Q[p] @ R.T, b[p], Phi)
+        assert abs(o_moved - o_snap) <= 1e-12 * max(sc, 1.0)
+        o_wrong, _, _ = orc.pair(Q[p] @ R, b[p], Phi)  # the other rotation sense does not hold
+        assert abs(o_moved - o_wrong) > 1e-6 * max(sc, 1.0)
+
+
 def test_local_energy_one_body_term_matches_gradient():
     """D O[h Phi] = sum_kj g_kj (h Phi)_kj with the oracle's gradient: two routes through
     the same column substitution agree, and e1 equals tr(h G) with G = Phi g^T / O."""
