@@ -1,9 +1,10 @@
 """CPU model of the split-precision congruence arithmetic (QCS_TF32X3), behind the
 error bound that the GPU split tests state.
 
-Each FP64 operand x is rounded to FP32 and split into a TF32 high part h (10
+Each FP64 operand x is rounded to FP32 and then to a TF32 high part h (10
 explicit mantissa bits, rounded to nearest with ties away from zero, as the
-conversion the kernel uses) and a TF32 low part l of the remainder; the tensor
+conversion the kernel uses); the remainder x - h, taken in FP64, gives the TF32
+low part l the same way; the tensor
 cores form h_a h_b + h_a l_b + l_a h_b (TF32 x TF32 products are exact in FP32)
 and accumulate in FP32.  The dropped l_a l_b term and the split itself cost about
 2^-21 of each product, the FP32 accumulation of 3 x 2n terms at most
@@ -23,9 +24,9 @@ def to_tf32(x32: np.ndarray) -> np.ndarray:
 
 
 def split(x: np.ndarray):
-    x32 = x.astype(np.float32)
-    hi = to_tf32(x32)
-    lo = to_tf32((x32 - hi).astype(np.float32))
+    """hi = tf32(fp32(x)), lo = tf32(fp32(x - hi)) with the remainder taken in FP64."""
+    hi = to_tf32(x.astype(np.float32))
+    lo = to_tf32((x - hi.astype(np.float64)).astype(np.float32))
     return hi, lo
 
 
