@@ -4,9 +4,8 @@ error bound that the GPU split tests state.
 Each FP64 operand x is rounded to FP32 and then to a TF32 high part h (10
 explicit mantissa bits, rounded to nearest with ties away from zero, as the
 conversion the kernel uses); the remainder x - h, taken in FP64, gives the TF32
-low part l the same way; the tensor
-cores form h_a h_b + h_a l_b + l_a h_b (TF32 x TF32 products are exact in FP32)
-and accumulate in FP32.  The dropped l_a l_b term and the split itself cost about
+low part l the same way.  The tensor cores form h_a h_b + h_a l_b + l_a h_b
+(TF32 x TF32 products are exact in FP32) and accumulate in FP32.  The dropped l_a l_b term and the split itself cost about
 2^-21 of each product, the FP32 accumulation of 3 x 2n terms at most
 3 * 2n * 2^-24 of the sum of magnitudes.
 """
