@@ -40,27 +40,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walker×snapshot overlap(+grad) pairs/s at n=16; % of FP64 peak vs plain GPU path"
 # FP64 ALU peak of a GB300 from unit counts: 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
-# maximum SM clock.  The sustained rate of register-only DFMA chains measured on this
-# pool's GB300 at 2070 MHz (paper_2506_22408_gb300/csrc/probes/fp64_fma_ceiling.cu) is
-# reported beside every FP64 roofline as context.
+# maximum SM clock.  The sustained rate of register-only FMA chains is measured in
+# each run on the same GPU (qcs_fp64_fma_rate) and reported beside every FP64 roofline.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-FP64_DFMA_MEASURED_TFLOPS = 1.056
 L2_FLUSH_BYTES = 256 << 20
 
 
-def add_dfma_context(obj):
-    """Beside every FP64 ("alu") roofline, the fraction of the measured DFMA rate."""
+def add_dfma_context(obj, rate):
+    """Beside every FP64 ("alu") roofline, the fraction of the measured FMA rate."""
     if isinstance(obj, dict):
         if obj.get("bound") == "alu" and isinstance(obj.get("achieved"), float):
-            obj["dfma_probe"] = {"tflops": FP64_DFMA_MEASURED_TFLOPS,
-                                 "frac": obj["achieved"] / FP64_DFMA_MEASURED_TFLOPS,
-                                 "source": "register-only DFMA chains at 2070 MHz "
-                                           "(csrc/probes/fp64_fma_ceiling.cu, profiles/fp64_fma_ceiling.md)"}
+            obj["dfma_probe"] = {"tflops": rate, "frac": obj["achieved"] / rate,
+                                 "source": "register-only FP64 FMA chains on this GPU in this run "
+                                           "(qcs_fp64_fma_rate)"}
         for v in list(obj.values()):
-            add_dfma_context(v)
+            add_dfma_context(v, rate)
     elif isinstance(obj, list):
         for v in obj:
-            add_dfma_context(v)
+            add_dfma_context(v, rate)
 
 
 def max_over_ranks(t: float, ws: int) -> float:
@@ -934,7 +931,7 @@ def main():
             "gpu_launches": args.steps * 5}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, data)
-    add_dfma_context(line)
+    add_dfma_context(line, ctx.fp64_fma_rate())
     if ws > 1:
         dist.barrier()
     if rank == 0:

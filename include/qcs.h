@@ -346,14 +346,16 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
 #define QCS_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* Shadow overlaps without any device allocation (the paper has no counterpart:
- * this is an embedding convenience).  Meant for callers that cannot allocate
- * device memory when they need overlaps -- code running under CUDA stream
- * capture, where cudaMalloc is not allowed, and hosts whose device memory is
- * owned by their own pool and that forbid libraries from allocating.
+ * this is an embedding convenience).  Meant for callers that cannot let a library
+ * allocate device memory when they need overlaps: hosts whose device memory is owned
+ * by their own pool allocator and that forbid libraries from allocating behind their
+ * back (and plug-ins running inside them), and real-time loops that must not stall on
+ * the implicit synchronisation of cudaMalloc.
  * Computes exactly what qcs_build_snapshots followed by qcs_overlap (default
  * options: FP64, Gauss node plan) computes, with every intermediate buffer in a
  * fixed file-scope device array of QCS_NOALLOC_SCRATCH_BYTES (32 MiB) that each
- * GPU loading the library holds until the process exits.  No context is used.
+ * GPU loading the library holds until the process exits.  No context is used; the
+ * call runs on the current device, and every pointer must be on that device.
  *   d_Q       : P x 2n x 2n doubles (device), d_b : P x n bytes (device)
  *   d_walkers : W x n x ne complex (device), d_overlap : W complex (device, written)
  *   d_status  : caller-owned device word into which numerical status bits are
@@ -361,12 +363,11 @@ qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, con
  * The scratch used is 32 n^2 P + 16 n^2 W + 16 W + 64 W ceil(P/16) + 5 P bytes
  * (each term rounded up to 16 bytes, plus 32); a call needing more than
  * QCS_NOALLOC_SCRATCH_BYTES returns QCS_ERR_ARG before enqueuing anything
- * (e.g. n = 16: about 2000 snapshots with 64 walkers).
+ * (e.g. n = 16 with 64 walkers: about 8.4 KB per snapshot, so about 3900 snapshots).
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
- * share the one array and leave their intermediates in it: calls whose work
- * overlaps in time on the GPU (different streams, or different host threads)
- * race and corrupt each other's results; serialise them.
+ * device current).  All calls share the one array and leave their intermediates
+ * in it: calls whose work overlaps in time on the GPU (different streams, or
+ * different host threads) race and corrupt each other's results; serialise them.
  * Errors: QCS_ERR_ARG (sizes, null pointers, odd ne), QCS_ERR_CUDA. */
 qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double *d_Q, const uint8_t *d_b, int64_t W,
                                const double *d_walkers, double *d_overlap, unsigned *d_status, void *stream);
@@ -395,6 +396,15 @@ qcs_status qcs_set_config(qcs_ctx *ctx, int n, int ne, int nodes, unsigned flags
  * previous read, and clears the record.  Errors: QCS_ERR_ARG, QCS_ERR_CUDA. */
 qcs_status qcs_profile_enable(qcs_ctx *ctx, int enable);
 qcs_status qcs_profile_read(qcs_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* Sustained FP64 fused multiply-add rate of the context's device in TFLOP/s (no
+ * counterpart in the paper; the ceiling that the FP64 kernels' roofline fractions are
+ * read against, beside the unit-count peak).  Runs register-only FMA chains, eight
+ * independent chains per thread and eight warps per SM, for about 2.5 s (a warm-up
+ * that lets the clocks settle under load, then five timed launches); uses context
+ * workspace and waits for `stream`.  *tflops: host double (2 flop per FMA).
+ * Errors: QCS_ERR_ARG (null pointers), QCS_ERR_CUDA. */
+qcs_status qcs_fp64_fma_rate(qcs_ctx *ctx, double *tflops, void *stream);
 
 /* ----------------------------------------------------------- accounting */
 

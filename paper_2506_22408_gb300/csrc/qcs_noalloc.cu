@@ -1,18 +1,17 @@
 // qcs_noalloc.cu -- qcs_overlap_noalloc: the overlap path without any device allocation.
 //
-// Some callers cannot allocate device memory at the point where they need
-// overlaps: code running while a stream is being captured into a CUDA graph
-// (cudaMalloc is not allowed there), hosts whose device memory is owned by
-// their own pool allocator and that forbid libraries from allocating behind
-// their back, and real-time loops that must not synchronise on an allocation.
-// For them this entry point runs the same kernels as qcs_build_snapshots +
-// qcs_overlap, but every intermediate buffer (snapshot rows, parity list, walker
-// rows, tile partial sums) lives in one file-scope device array of fixed size,
-// and no context is needed.
+// Some callers cannot let a library allocate device memory at the point where they
+// need overlaps: hosts whose device memory is owned by their own pool allocator and
+// that forbid libraries from allocating behind their back, plug-ins that run inside
+// such hosts, and real-time loops that must not stall on the implicit
+// synchronisation of cudaMalloc.  For them this entry point runs the same kernels
+// as qcs_build_snapshots + qcs_overlap, but every intermediate buffer (snapshot
+// rows, parity list, walker rows, tile partial sums) lives in one file-scope device
+// array of fixed size, and no context is needed.
 //
-// The device address of the array is looked up once per device, with that
-// device current, by cudaGetSymbolAddress on the first call made on that device
-// (so the first call on a device should come before any stream capture).
+// The device address of the array is looked up once per device, with that device
+// current, by cudaGetSymbolAddress on the first call made on that device.  The
+// call runs on the current device; every pointer passed must be on it.
 #include <mutex>
 
 #include "qcs_internal.h"
@@ -65,6 +64,9 @@ extern "C" qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1) || P < 0 || W < 0) return QCS_ERR_ARG;
     if ((P > 0 && (!d_Q || !d_b)) || (W > 0 && (!d_walkers || !d_overlap))) return QCS_ERR_ARG;
     if (P > (int64_t)INT32_MAX) return QCS_ERR_ARG;
+    // a walker alone needs 16 n^2 bytes of scratch: larger W cannot fit, and bounding it
+    // here keeps the byte count below from overflowing
+    if (W > (int64_t)(QCS_NOALLOC_SCRATCH_BYTES / (16u * (unsigned)n * (unsigned)n))) return QCS_ERR_ARG;
     const size_t need = noalloc_bytes(n, P, W);
     if (need > (size_t)QCS_NOALLOC_SCRATCH_BYTES) return QCS_ERR_ARG;  // beyond the static scratch
     if (W == 0) return QCS_OK;

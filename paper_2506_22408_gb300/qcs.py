@@ -39,7 +39,7 @@ EXPORTED = [
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
     "qcs_local_energy", "qcs_local_energy_flops_per_pair", "qcs_overlap_flops_breakdown",
-    "qcs_selftest_bounded_wait",
+    "qcs_selftest_bounded_wait", "qcs_fp64_fma_rate",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_workspace_bytes.argtypes = [P]
         lib.qcs_workspace_bytes.restype = ctypes.c_size_t
         lib.qcs_selftest_bounded_wait.argtypes = [P, u32, P]
+        lib.qcs_fp64_fma_rate.argtypes = [P, ctypes.POINTER(f64), P]
         lib.qcs_build_snapshots.argtypes = [P, i32, i64, P, P, ctypes.POINTER(P), P]
         lib.qcs_snapshots_free.argtypes = [P]
         lib.qcs_snapshots_parity.argtypes = [P, P, P]
@@ -202,6 +203,12 @@ class Context:
         """Run the device time-out self-test; returns the status bits it raised."""
         self.check(self.lib.qcs_selftest_bounded_wait(self.h, max_iter, _stream()))
         return self.sync_status()
+
+    def fp64_fma_rate(self) -> float:
+        """Sustained FP64 FMA rate of this device in TFLOP/s (about 2.5 s of chains)."""
+        t = ctypes.c_double()
+        self.check(self.lib.qcs_fp64_fma_rate(self.h, ctypes.byref(t), _stream()))
+        return float(t.value)
 
     def profile(self, enable: bool = True):
         self.check(self.lib.qcs_profile_enable(self.h, 1 if enable else 0))
@@ -341,15 +348,33 @@ def overlap_noalloc(Q: torch.Tensor, b: torch.Tensor, walkers: torch.Tensor, out
                     status: torch.Tensor | None = None) -> None:
     """qcs_overlap_noalloc: overlaps into ``out`` (W complex128) with no device allocation by
     the library (its scratch is a fixed 32 MiB device array).  ``status`` is an optional
-    int32 CUDA tensor of one element into which device status bits are OR-ed."""
+    int32 CUDA tensor of at least one element into which device status bits are OR-ed.
+    Every tensor must live on the same device; the call runs there."""
     _need_cuda(Q, "Q", torch.float64)
     _need_cuda(b, "b", torch.uint8)
     _need_cuda(walkers, "walkers", torch.complex128)
     _need_cuda(out, "out", torch.complex128)
-    P, N, _ = Q.shape
+    if walkers.dim() != 3:
+        raise ValueError("walkers must be (W, n, ne)")
     W, n, ne = walkers.shape
-    rc = load().qcs_overlap_noalloc(n, ne, P, _ptr(Q), _ptr(b), W, _ptr(walkers), _ptr(out), _ptr(status),
-                                    _stream())
+    if Q.dim() != 3 or Q.shape[1:] != (2 * n, 2 * n):
+        raise ValueError(f"Q must be (P, {2 * n}, {2 * n}) for walkers with n = {n}")
+    P = Q.shape[0]
+    if tuple(b.shape) != (P, n):
+        raise ValueError(f"b must be ({P}, {n})")
+    if out.numel() < W:
+        raise ValueError(f"out must hold at least {W} overlaps")
+    if status is not None:
+        _need_cuda(status, "status", torch.int32)
+        if status.numel() < 1:
+            raise ValueError("status must hold one int32")
+    dev = walkers.device
+    for t, nm in ((Q, "Q"), (b, "b"), (out, "out"), (status, "status")):
+        if t is not None and t.device != dev:
+            raise ValueError(f"{nm} lives on {t.device}, the walkers on {dev}")
+    with torch.cuda.device(dev):
+        rc = load().qcs_overlap_noalloc(n, ne, P, _ptr(Q), _ptr(b), W, _ptr(walkers), _ptr(out), _ptr(status),
+                                        _stream())
     if rc != QCS_OK:
         why = ("the sizes need more than the fixed 32 MiB scratch, or invalid arguments" if rc == 1 else "")
         raise QCSError(rc, f"qcs_overlap_noalloc failed: {why}")

@@ -1,8 +1,9 @@
 """qcs_overlap_noalloc, the allocation-free overlap entry point.
 
-It exists for callers that cannot allocate device memory when they need
-overlaps (stream capture, pool-owning hosts); its scratch is a fixed device
-array inside the library.  These tests call it through the C ABI twice in a
+It exists for callers that cannot let a library allocate device memory when
+they need overlaps (hosts whose pool allocator owns all device memory, real-time
+loops that must not stall on cudaMalloc); its scratch is a fixed device array
+inside the library.  These tests call it through the C ABI twice in a
 row, with different sizes, and compare each result with the ordinary entry
 point (qcs_build_snapshots + qcs_overlap) within the parity tolerance used by
 the other GPU tests (1e-10 times the mean magnitude of the pair terms, taken
