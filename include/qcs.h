@@ -96,6 +96,11 @@ typedef enum {
                                  snapshot (disables the parity shortcuts described at qcs_overlap) */
 #define QCS_FLAG_DFT_NODES 2u /* roots of unity with the parity shortcuts, also when nodes = 0
                                  (then N = n-ne+1) */
+#define QCS_FLAG_FP64_ALU 4u  /* qcs_overlap, QCS_FP64: form the congruence on the FP64 ALU (the
+                                 default for n != 16) instead of on tensor cores */
+#define QCS_FLAG_FP64_TC 8u   /* qcs_overlap, QCS_FP64: form the congruence on tensor cores at FP64
+                                 accuracy (the default for n = 16) for any n <= 16; not with
+                                 QCS_FLAG_ALL_NODES (QCS_ERR_UNSUPPORTED) */
 
 /* Node plans (how sum_x c_x C(2n,2x)/C(n,x) is obtained from Pfaffians):
  *  - default (nodes = 0, no node flag): a Gauss rule.  For parity +1 snapshots
@@ -205,6 +210,17 @@ int qcs_snapshots_modes(const qcs_snapshots *s);
  * Errors: QCS_ERR_ARG, QCS_ERR_CUDA; device bits via qcs_sync_status. */
 qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                        double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream);
+/* Congruence of the FP64 path.  Every entry of B^(s) is a signed sum of entries of
+ * P = M H_p M^T, M the walker's real 2n x 2n form and H_p = N^T J N (N the snapshot's
+ * real rows, J the canonical skew form), formed once per snapshot.  At n = 16 by
+ * default (any n <= 16 with QCS_FLAG_FP64_TC) the two products Z = H_p M^T and P = M Z
+ * run on tensor cores by error-free slicing: each FP64 row is cut into seven 8-bit
+ * slices exact in BF16, the 28 slice products of the leading levels accumulate exactly
+ * in FP32, and the levels are combined exactly in 64-bit fixed point, so each entry of P
+ * carries an error of about 2^-53 times the row scales, like an FP64 product; the
+ * Pfaffians stay on the FP64 pipe.  The snapshot set then holds 57,856 bytes per four
+ * parity +1 snapshots of slice records (formed by qcs_build_snapshots at n = 16,
+ * otherwise on first use), and the context workspace 14,464 bytes per walker. */
 
 /* ---------------------------------------------------- local energy terms */
 

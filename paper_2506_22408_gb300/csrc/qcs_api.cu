@@ -273,6 +273,9 @@ extern "C" qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const 
         return qcs_fail(ctx, QCS_ERR_CUDA, std::string("snapshot cudaMalloc: ") + cudaGetErrorString(e));
     }
     qcs_status st = qcs_launch_snapshot_build(ctx, s, d_Q, d_b, (cudaStream_t)stream);
+    // the tensor-core congruence is the default FP64 path at n = 16: its per-snapshot
+    // records are formed with the set
+    if (st == QCS_OK && n == 16) st = qcs_tc_prepare_snapshots(ctx, s, (cudaStream_t)stream);
     if (st != QCS_OK) {
         qcs_snapshots_free(s);
         return st;
@@ -304,6 +307,7 @@ extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
     if (s->gth) cudaFree(s->gth);
     if (s->split_hi) cudaFree(s->split_hi);
     if (s->split_lo) cudaFree(s->split_lo);
+    if (s->tc_rec) cudaFree(s->tc_rec);
     delete s;
     return QCS_OK;
 }
@@ -328,11 +332,32 @@ const int kChunk = 4;  // snapshots per warp in an overlap tile
 struct OverlapWork {
     cd *Ut, *pref, *partial;
     unsigned long long *counter;
-    float *Mhi, *Mlo;  // split precision: walker operand slabs
-    int *mode;         // FP64 path: per-walker form of the occupied rows (walker prep)
+    float *Mhi, *Mlo;          // split precision: walker operand slabs
+    unsigned char *walk_rec;   // tensor-core congruence: walker slice records
+    int *mode;                 // FP64 ALU path: per-walker form of the occupied rows (walker prep)
     int nchunks, nparts;
-    bool split;
+    bool split, tc;
 };
+
+// The FP64 overlap runs its congruence on tensor cores (qcs_tcpair.cu) by default at
+// n = 16, on request (QCS_FLAG_FP64_TC) for any n <= 16, and on the FP64 ALU
+// otherwise (QCS_FLAG_FP64_ALU, n > 16, or every node of every snapshot).
+qcs_status choose_tc(qcs_ctx *ctx, int n, const qcs_opts &o, bool *tc) {
+    *tc = false;
+    if (o.precision != QCS_FP64) return QCS_OK;
+    if ((o.flags & QCS_FLAG_FP64_TC) && (o.flags & QCS_FLAG_FP64_ALU))
+        return qcs_fail(ctx, QCS_ERR_ARG, "QCS_FLAG_FP64_TC and QCS_FLAG_FP64_ALU exclude each other");
+    const bool possible = qcs_tc_supported(n) && !(o.flags & QCS_FLAG_ALL_NODES);
+    if (o.flags & QCS_FLAG_FP64_TC) {
+        if (!possible)
+            return qcs_fail(ctx, QCS_ERR_UNSUPPORTED,
+                            "the tensor-core congruence needs n <= 16 and the parity-compacted snapshot list");
+        *tc = true;
+        return QCS_OK;
+    }
+    *tc = possible && !(o.flags & QCS_FLAG_FP64_ALU) && n == 16;
+    return QCS_OK;
+}
 
 qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                           const qcs_opts *opts, cudaStream_t st, qcs_node_plan *plan, OverlapWork *wk) {
@@ -353,20 +378,26 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     if (qcs_make_node_plan(n, ne, o.nodes, o.flags, plan) != QCS_OK)
         return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
     const bool split = o.precision == QCS_TF32X3;
+    bool tc = false;
+    c = choose_tc(ctx, n, o, &tc);
+    if (c != QCS_OK) return c;
     wk->split = split;
-    // partial sums: FP64 path one per (walker, 16-snapshot chunk, warp); split path one
-    // per (walker, tile of snapshots)
-    const int span = split ? qcs_split_snaps_per_tile() : kChunk * qcs_pair_warps_per_block();
+    wk->tc = tc;
+    // partial sums: FP64 ALU path one per (walker, 16-snapshot chunk, warp); split path one
+    // per (walker, tile of snapshots); tensor-core path one per (walker, tile)
+    const int span = split ? qcs_split_snaps_per_tile() : tc ? qcs_tc_snaps_per_tile()
+                                                             : kChunk * qcs_pair_warps_per_block();
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
-    wk->nparts = split ? wk->nchunks : wk->nchunks * qcs_pair_warps_per_block();
+    wk->nparts = (split || tc) ? wk->nchunks : wk->nchunks * qcs_pair_warps_per_block();
     size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
     size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nparts);
     size_t b_slab = split ? align16(qcs_split_walker_bytes(W)) : 0;
-    size_t b_mode = split ? 0 : align16(sizeof(int) * (size_t)(W > 0 ? W : 1));
+    size_t b_rec = tc ? align16(qcs_tc_walker_bytes(W)) : 0;
+    size_t b_mode = (split || tc) ? 0 : align16(sizeof(int) * (size_t)(W > 0 ? W : 1));
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab + b_mode, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab + b_rec + b_mode, &base);
     if (ws != QCS_OK) return ws;
     char *pb = (char *)base;
     wk->counter = (unsigned long long *)pb;
@@ -375,9 +406,10 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     wk->partial = (cd *)(pb + 16 + b_ut + b_pref);
     wk->Mhi = split ? (float *)(pb + 16 + b_ut + b_pref + b_part) : nullptr;
     wk->Mlo = split ? (float *)(pb + 16 + b_ut + b_pref + b_part + b_slab) : nullptr;
-    // the reduced form of the occupied rows serves the FP64 pair kernel; the split path's
-    // TF32 operands keep the orthonormal echelon form
-    wk->mode = split ? nullptr : (int *)(pb + 16 + b_ut + b_pref + b_part + 2 * b_slab);
+    wk->walk_rec = tc ? (unsigned char *)(pb + 16 + b_ut + b_pref + b_part + 2 * b_slab) : nullptr;
+    // the reduced form of the occupied rows serves the FP64 ALU pair kernel; the tensor
+    // paths keep the orthonormal echelon form
+    wk->mode = (split || tc) ? nullptr : (int *)(pb + 16 + b_ut + b_pref + b_part + 2 * b_slab + b_rec);
     return qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, wk->Ut, wk->pref, st, nullptr, nullptr,
                                   true, wk->mode);
 }
@@ -423,6 +455,10 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
         r = qcs_split_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
         if (r != QCS_OK) return r;
         r = qcs_launch_split(ctx, L, wk.Mhi, wk.Mlo, st);
+    } else if (wk.tc) {
+        r = qcs_tc_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
+        if (r != QCS_OK) return r;
+        r = qcs_launch_tc_pairs(ctx, L, wk.walk_rec, st);
     } else {
         r = qcs_launch_pairs(ctx, L, st);
     }

@@ -43,6 +43,8 @@ struct qcs_snapshots {
                               // (k << 2) | phase, phase 0..3 = 1, i, -1, -i); first code 0xFF: dense
     void *split_hi = nullptr; // P x 4 KB TF32 operand slabs (split precision), built on first use
     void *split_lo = nullptr;
+    void *tc_rec = nullptr;   // tensor-core congruence: BF16 slices of H_p = N^T J N for the parity +1
+                              // list, four snapshots per record (57,856 bytes), built once
 };
 
 // Makes `dev` current for the scope of the guard, then restores the previous device.
@@ -131,6 +133,12 @@ qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStrea
 size_t qcs_split_walker_bytes(int64_t W);
 int qcs_split_snaps_per_tile();  // snapshots per split-precision tile (partial sums per walker)
 qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st);
+// FP64-accurate congruence on tensor cores (qcs_tcpair.cu)
+bool qcs_tc_supported(int n);      // n <= 16
+size_t qcs_tc_walker_bytes(int64_t W);
+int qcs_tc_snaps_per_tile();      // parity +1 snapshots per tile (one partial sum per walker and tile)
+qcs_status qcs_tc_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
+qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned char *walk_rec, cudaStream_t st);
 qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launch *Ls, unsigned long long *counter,
                                     cudaStream_t st);
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);

@@ -99,18 +99,6 @@ struct SplitArgs {
     cd gamma[QCS_MAX_NODES];
 };
 
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-        : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
-                 : "memory");
-}
-
 // B^(s) (FP64 packed upper) from T (FP32 complex, row stride ld) in FP32 arithmetic.
 __device__ void build_B_f32(int n, int ne, const float2 *__restrict__ Ts, int ld, cd *__restrict__ Bs,
                             const uint16_t *__restrict__ tab, int lane) {

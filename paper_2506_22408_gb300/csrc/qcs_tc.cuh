@@ -1,12 +1,13 @@
 // qcs_tc.cuh -- Blackwell tensor-core (tcgen05) building blocks used by the
-// split-precision congruence kernel: tensor-memory allocation, shared-memory
-// matrix descriptors, the instruction descriptor of kind::tf32, the MMA issue,
-// its completion through an mbarrier (bounded wait), and tensor-memory loads.
+// tensor-core congruence kernels: tensor-memory allocation, shared-memory matrix
+// descriptors, the instruction descriptors of kind::tf32 and kind::f16 (BF16
+// operands), the MMA issue, its completion through an mbarrier (bounded wait),
+// bulk asynchronous copies into shared memory, and tensor-memory loads.
 //
 // Operand layout: both operands are K-major without swizzle.  A row-block of 8
-// rows x 16 bytes (8 x 4 TF32) is a "core matrix" stored as 128 contiguous
-// bytes (row r at byte 16 r); core matrices adjacent along K are LBO bytes
-// apart, those adjacent along M (or N) SBO bytes apart.
+// rows x 16 bytes (8 x 4 TF32 or 8 x 8 BF16) is a "core matrix" stored as 128
+// contiguous bytes (row r at byte 16 r); core matrices adjacent along K are LBO
+// bytes apart, those adjacent along M (or N) SBO bytes apart.
 #pragma once
 #include <stdint.h>
 
@@ -45,6 +46,23 @@ __device__ __forceinline__ uint64_t desc_kmajor(const void *base, uint32_t lbo, 
 // 17-22, M >> 4 at bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16 with BF16 operands: D = F32
+// (bits 4-5 = 1), A = B = BF16 (format 1 at bits 7-9 and 10-12), both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T for kind::f16 (K = 16 per instruction), one thread.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
@@ -102,7 +120,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 8 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Bulk asynchronous copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16) completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+// Arrive on the mbarrier and add `bytes` to the transactions it waits for.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
 
 // Round to TF32 (10 explicit mantissa bits), nearest, ties away from zero.
 __device__ __forceinline__ float to_tf32(float x) {

@@ -1,0 +1,591 @@
+// qcs_tcpair.cu -- FP64-accurate overlaps with the congruence on tensor cores.
+//
+// For a pair (walker w, snapshot p) the Pfaffians of Eq. (a_mat) need B^(s), the
+// selected rows of the rotated covariance of Eq. (b_mat).  In real form, with the
+// walker's rows Ut = A + iB and the snapshot's complexified sign-folded rows
+// Qt = C + iD (see qcs_snapshots.cu),
+//     R = [Re T; Im T] = M N^T,   M = [[A, -B], [B, A]],  N = [C, D]   (2n x 2n each),
+// and every entry of B^(s) is a signed sum of entries of
+//     P = R J R^T = M H M^T,      H = N^T J N                          (2n x 2n, skew),
+// J the canonical skew form on the Majorana index.  H belongs to the snapshot alone
+// and is formed once per snapshot; per pair only the two products Z = H M^T and
+// P = M Z remain, two dense 32 x 32 x 32 contractions (n <= 16, padded with zeros).
+//
+// Both run on the 5th-generation tensor cores at FP64 accuracy by error-free operand
+// slicing (qcs_ozaki.cuh): each FP64 row is cut into seven 8-bit integer slices held
+// exactly in BF16, the 28 slice products of levels 2..8 are accumulated exactly in
+// FP32 in tensor memory (one accumulator per level), and the levels are combined
+// exactly into 64-bit fixed point on the integer pipe.  The walker's slices are
+// formed once per walker, the snapshot's once per snapshot; Z is re-sliced per pair
+// between the two products.  The FP64 pipe is left with the Pfaffians alone.
+//
+// Tiles: one walker and 32 consecutive parity +1 snapshots (eight sub-tiles of four);
+// a block of four warps owns a tile, warp i the pair of snapshot i of each sub-tile.
+//  1. bulk copies bring the four snapshots' H slices (the A operand, M = 128 rows)
+//     and, once per tile, the walker's M slices (the B operand, N = 32) into shared
+//     memory;
+//  2. 56 tcgen05.mma kind::f16 (28 slice products, K = 32 as two K = 16 steps) form
+//     Z_i = H_i M^T, level L in tensor-memory columns 32(L-2) .. 32(L-2)+31;
+//  3. each warp reads its 32 lanes (row k of Z_i), combines the levels into fixed
+//     point, transposes through shared memory so that lane b holds row b of Z_i^T,
+//     and writes its seven slices (row scale per b) as the next A operand;
+//  4. 56 more MMAs form P_i = M Z_i (lane b of warp i, column a: P_i[a][b]); each warp
+//     converts its lanes to FP64, assembles B^(s) and runs the node Pfaffians of the
+//     FP64 path (qcs_pair.cuh).
+// Every wait is bounded: a time-out raises QCS_ERR_TIMEOUT, drains and frees the
+// tensor memory.
+#include "qcs_internal.h"
+#include "qcs_ozaki.cuh"
+#include "qcs_pair.cuh"
+#include "qcs_tc.cuh"
+
+using namespace qcs_tc;
+using namespace qcs_oz;
+
+namespace {
+
+constexpr int kSnapsPerSub = 4;                               // M = 128 rows of the first product
+constexpr int kSubPerTile = 8;                                // snapshots per tile: 32
+constexpr int kSnapsPerTile = kSnapsPerSub * kSubPerTile;
+constexpr uint32_t kTmemCols = 256;                           // 7 levels x 32 columns, power of two
+constexpr uint32_t kWaitIter = 1u << 26;                      // bounded mbarrier waits
+constexpr int kSnapSlab = kSnapsPerSub * kSliceBytes;         // one slice of 4 snapshots: 8 KB
+constexpr int kSnapRecBytes = kSlices * kSnapSlab + kSnapsPerSub * kRowsPer * 4;  // + row exponents
+constexpr int kWalkRecBytes = kSlices * kSliceBytes + kRowsPer * 4;
+constexpr int kScratchBytes = 2 * kRowsPer * (kRowsPer + 1) * 4;  // per warp: transpose / P (32 x 33 doubles)
+
+static_assert(kSnapRecBytes % 16 == 0 && kWalkRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// ---------------------------------------------------------------- operand records
+
+// Walker records: warp per walker, lane r = row r of M (zero beyond 2n).
+__global__ void tc_walker_prep_kernel(int n, int64_t W, const cd *__restrict__ Ut, unsigned char *__restrict__ rec) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int64_t w = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); w < W; w += (int64_t)gridDim.x * wpb) {
+        const cd *U = Ut + w * n * n;
+        double x[kRowsPer];
+        const int r = lane;
+#pragma unroll
+        for (int kk = 0; kk < kRowsPer; ++kk) {
+            double v = 0.0;
+            if (r < 2 * n && kk < 2 * n) {
+                const int j = r < n ? r : r - n, k = kk < n ? kk : kk - n;
+                const cd u = U[j * n + k];
+                if (r < n) v = kk < n ? u.x : -u.y;  // [A_j, -B_j]
+                else v = kk < n ? u.y : u.x;         // [B_j,  A_j]
+            }
+            x[kk] = v;
+        }
+        int e = kNoRow;
+#pragma unroll
+        for (int kk = 0; kk < kRowsPer; ++kk)
+            if (x[kk] != 0.0) e = max(e, row_exp_of(x[kk]));
+        uint64_t u[kRowsPer];
+        uint32_t neg = 0u;
+#pragma unroll
+        for (int kk = 0; kk < kRowsPer; ++kk) {
+            u[kk] = e == kNoRow ? 0ull : fixed_of(x[kk], e);
+            neg |= (x[kk] < 0.0 ? 1u : 0u) << kk;
+        }
+        unsigned char *base = rec + (size_t)w * kWalkRecBytes;
+        store_row_slices(base, kSliceBytes, r, u, neg);
+        reinterpret_cast<int *>(base + kSlices * kSliceBytes)[r] = e;
+    }
+}
+
+// Snapshot records in the order of the parity +1 list, four per record: warp per list
+// slot, lane k = row k of H = N^T J N; slots at or beyond the list's length get zero
+// slices.  Shared memory: per warp the 32 x 32 matrix N (zero-padded), 8 KB.
+__global__ void tc_snapshot_prep_kernel(int n, int64_t nslots, const cd *__restrict__ Qt, const int *__restrict__ idx,
+                                        const int *__restrict__ d_count, unsigned char *__restrict__ rec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double *N = reinterpret_cast<double *>(smem_raw) + (size_t)warp * kRowsPer * kRowsPer;
+    const int64_t L = *d_count;
+    for (int64_t p = (int64_t)blockIdx.x * wpb + warp; p < nslots; p += (int64_t)gridDim.x * wpb) {
+        const bool live = p < L;
+        if (live) {
+            const cd *Qp = Qt + (int64_t)idx[p] * 2 * n * n;
+            for (int e = lane; e < kRowsPer * kRowsPer; e += 32) {
+                const int c = e / kRowsPer, kk = e - c * kRowsPer;
+                double v = 0.0;
+                if (c < 2 * n && kk < 2 * n) {
+                    const cd q = Qp[c * n + (kk < n ? kk : kk - n)];
+                    v = kk < n ? q.x : q.y;
+                }
+                N[e] = v;
+            }
+        }
+        __syncwarp();
+        double h[kRowsPer];
+        const int k = lane;
+#pragma unroll
+        for (int l = 0; l < kRowsPer; ++l) h[l] = 0.0;
+        if (live) {
+            // H[k][l] = sum_i N[2i][k] N[2i+1][l] - N[2i+1][k] N[2i][l]
+            for (int i = 0; i < n; ++i) {
+                const double a = N[(2 * i) * kRowsPer + k], b = N[(2 * i + 1) * kRowsPer + k];
+#pragma unroll
+                for (int l = 0; l < kRowsPer; ++l)
+                    h[l] = fma(a, N[(2 * i + 1) * kRowsPer + l], fma(-b, N[(2 * i) * kRowsPer + l], h[l]));
+            }
+        }
+        int e = kNoRow;
+#pragma unroll
+        for (int l = 0; l < kRowsPer; ++l)
+            if (h[l] != 0.0) e = max(e, row_exp_of(h[l]));
+        uint64_t u[kRowsPer];
+        uint32_t neg = 0u;
+#pragma unroll
+        for (int l = 0; l < kRowsPer; ++l) {
+            u[l] = e == kNoRow ? 0ull : fixed_of(h[l], e);
+            neg |= (h[l] < 0.0 ? 1u : 0u) << l;
+        }
+        unsigned char *base = rec + (size_t)(p / kSnapsPerSub) * kSnapRecBytes;
+        const int row = (int)(p % kSnapsPerSub) * kRowsPer + k;
+        store_row_slices(base, kSnapSlab, row, u, neg);
+        reinterpret_cast<int *>(base + kSlices * kSnapSlab)[row] = e;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- pair kernel
+
+struct TcArgs {
+    int n, ne, m, d, nev, NB;
+    int64_t W, P;
+    int nchunks;      // tiles per walker (chunks of kSnapsPerTile list slots)
+    int warp_bytes;   // Pfaffian workspace per warp (in the operand region)
+    int off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // in the warp's operand quarter
+    int vm;
+    int smem_scratch, smem_tab;  // byte offsets of the per-warp scratch and the pair table
+    const unsigned char *snap_rec;
+    const unsigned char *walk_rec;
+    const cd *pref;
+    const int *idx;
+    const int *d_count;
+    cd *partial;      // W x nchunks
+    cd *per_pair;
+    unsigned long long *counter;
+    unsigned *status;
+    cd wnode[QCS_MAX_NODES];
+    cd gamma[QCS_MAX_NODES];
+};
+
+// The 56 MMAs of one sliced product: level L = i + j (i the A slice, j the B slice)
+// into columns 32 (L - 2); A slabs kSnapSlab apart (M = 128), B slabs kSliceBytes
+// apart (N = 32).
+__device__ __forceinline__ void issue_sliced_product(uint32_t tbase, const unsigned char *A, const unsigned char *B) {
+    const uint32_t id = idesc_bf16(kSnapsPerSub * kRowsPer, kRowsPer);
+#pragma unroll 1
+    for (int L = 2; L <= kSlices + 1; ++L) {
+        uint32_t acc = 0u;
+        for (int i = (L - kSlices > 1 ? L - kSlices : 1); i <= (L - 1 < kSlices ? L - 1 : kSlices); ++i) {
+            const int j = L - i;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ad = desc_kmajor(A + (size_t)(i - 1) * kSnapSlab + 256 * ks, 128, 512);
+                const uint64_t bd = desc_kmajor(B + (size_t)(j - 1) * kSliceBytes + 256 * ks, 128, 512);
+                mma_f16(tbase + (uint32_t)(32 * (L - 2)), ad, bd, id, acc);
+                acc = 1u;
+            }
+        }
+    }
+}
+
+// Columns cb*8 .. cb*8+7 of the seven level accumulators of this thread's lane,
+// combined into fixed point.
+__device__ __forceinline__ void read_levels8(uint32_t taddr, int cb, long long (&z)[8]) {
+    float v[kLevels][8];
+#pragma unroll
+    for (int L = 0; L < kLevels; ++L) tmem_ld8(taddr + (uint32_t)(32 * L + 8 * cb), v[L]);
+    tmem_ld_wait();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float a[kLevels];
+#pragma unroll
+        for (int L = 0; L < kLevels; ++L) a[L] = v[L][c];
+        z[c] = combine_levels(a);
+    }
+}
+
+// B^(s) (packed upper, m x m) from P = R J R^T (row stride ldp), R = [Re T; Im T]:
+// selected row x < ne is T_x (= R[x] + i R[n+x]); x >= ne is Re T_j (even offset) or
+// -Im T_j (odd offset) for the empty mode j = ne + (x - ne)/2.
+__device__ void build_B_from_P(int n, int ne, int m, const double *__restrict__ Pd, int ldp, cd *__restrict__ Bs,
+                               const uint16_t *__restrict__ tab, int lane) {
+    const int T = tri_count(m);
+    for (int t = lane; t < T; t += 32) {
+        int x, y;
+        pair_of(tab, t, x, y);  // x < y
+        cd v;
+        if (y < ne) {  // occupied x occupied: (R_x + i R_nx) J (R_y + i R_ny)^T
+            const double prr = Pd[x * ldp + y], pii = Pd[(n + x) * ldp + n + y];
+            const double pri = Pd[x * ldp + n + y], pir = Pd[(n + x) * ldp + y];
+            v = cmk(prr - pii, pri + pir);
+        } else {
+            const int jy = ne + ((y - ne) >> 1);
+            const bool yim = (y - ne) & 1;
+            const int ry = yim ? n + jy : jy;
+            if (x < ne) {  // occupied x empty: (R_x + i R_nx) J (+-R_ry)^T
+                const double re = Pd[x * ldp + ry], im = Pd[(n + x) * ldp + ry];
+                v = yim ? cmk(-re, -im) : cmk(re, im);
+            } else {
+                const int jx = ne + ((x - ne) >> 1);
+                const bool xim = (x - ne) & 1;
+                const int rx = xim ? n + jx : jx;
+                const double re = Pd[rx * ldp + ry];
+                v = cmk((xim != yim) ? -re : re, 0.0);
+            }
+        }
+        Bs[t] = v;
+    }
+}
+
+__global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__ TcArgs A) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
+    __shared__ long long next_tile;
+    __shared__ int abort_flag;
+    __shared__ cd red[4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = A.n;
+    unsigned char *X = smem_tc;                                   // operands, then workspaces
+    unsigned char *Wrec = smem_tc + kSnapRecBytes;                // walker record
+    const int *g_exp = reinterpret_cast<const int *>(X + kSlices * kSnapSlab);   // snapshot row exponents
+    const int *e_exp = reinterpret_cast<const int *>(Wrec + kSlices * kSliceBytes);  // walker row exponents
+    unsigned char *scr = smem_tc + A.smem_scratch + (size_t)warp * kScratchBytes;
+    uint32_t *zlo = reinterpret_cast<uint32_t *>(scr);
+    uint32_t *zhi = zlo + kRowsPer * (kRowsPer + 1);
+    double *Pd = reinterpret_cast<double *>(scr);
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_tc + A.smem_tab);
+    build_pair_table(tab, tri_count(A.m));
+    unsigned char *wbase = X + (size_t)warp * A.warp_bytes;
+    cd *Ns = reinterpret_cast<cd *>(scr);  // node matrices: the scratch, once P is consumed
+    cd *Bs = reinterpret_cast<cd *>(wbase + A.off_B);
+    cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
+    cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
+    cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
+    cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
+    int *ints = reinterpret_cast<int *>(wbase + A.off_int);
+    uint8_t *act0 = wbase + A.off_act;
+    uint8_t *act1 = act0 + A.vm;
+    cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
+
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, kTmemCols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&mbar_load, 1);
+        mbar_init(&mbar_mma, 1);
+        abort_flag = 0;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+    const int64_t L = *A.d_count;
+    const int64_t ntiles = A.W * (int64_t)A.nchunks;
+    uint32_t ph_load = 0, ph_mma = 0;
+    bool ok = true;
+    for (;;) {
+        fence_proxy_async_smem();  // generic writes to the operand region precede the next bulk copies
+        fence_before_sync();
+        __syncthreads();
+        if (tid == 0) next_tile = (long long)atomicAdd(A.counter, 1ull);
+        __syncthreads();
+        const int64_t t = next_tile;
+        if (t >= ntiles || abort_flag) break;
+        const int ch = (int)(t / A.W);  // chunk-major: a chunk's records stay in L2 over the walkers
+        const int64_t w = t - (int64_t)ch * A.W;
+        const int64_t p0 = (int64_t)ch * kSnapsPerTile;
+        if (p0 >= L) {
+            if (tid == 0) A.partial[w * A.nchunks + ch] = cmk(0.0, 0.0);
+            continue;
+        }
+        const cd prefw = A.pref[w];
+        cd acc = cmk(0.0, 0.0);
+        for (int s = 0; s < kSubPerTile; ++s) {
+            const int64_t pb = p0 + (int64_t)s * kSnapsPerSub;
+            if (pb >= L) break;
+            if (tid == 0) {
+                const uint32_t bytes = kSnapRecBytes + (s == 0 ? kWalkRecBytes : 0);
+                mbar_expect_tx(&mbar_load, bytes);
+                bulk_copy(X, A.snap_rec + (size_t)(pb / kSnapsPerSub) * kSnapRecBytes, kSnapRecBytes, &mbar_load);
+                if (s == 0) bulk_copy(Wrec, A.walk_rec + (size_t)w * kWalkRecBytes, kWalkRecBytes, &mbar_load);
+            }
+            // every wait is bounded, and its outcome is made uniform over the block
+            ok = __syncthreads_and(mbar_wait_bounded(&mbar_load, ph_load, kWaitIter));
+            ph_load ^= 1u;
+            if (!ok) break;
+            if (tid == 0) {
+                fence_after_sync();
+                issue_sliced_product(tbase, X, Wrec);  // Z_i = H_i M^T
+                mma_commit(&mbar_mma);
+            }
+            ok = __syncthreads_and(mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter));
+            ph_mma ^= 1u;
+            if (!ok) break;
+            fence_after_sync();
+            // ---- Z_i: lane k holds row k; combine, transpose, re-slice as rows of Z_i^T
+#pragma unroll 1
+            for (int cb = 0; cb < 4; ++cb) {
+                long long z[8];
+                read_levels8(tlane, cb, z);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int o = lane * (kRowsPer + 1) + 8 * cb + c;
+                    zlo[o] = (uint32_t)(unsigned long long)z[c];
+                    zhi[o] = (uint32_t)((unsigned long long)z[c] >> 32);
+                }
+            }
+            __syncwarp();
+            int Fb = kNoRow;  // row scale of row b = lane of Z_i^T
+            {
+                const int b = lane;
+                const int eb = e_exp[b];
+                const int *gk = g_exp + warp * kRowsPer;
+                long long zk[kRowsPer];
+                int G = kNoRow;
+#pragma unroll
+                for (int k = 0; k < kRowsPer; ++k) {
+                    const int o = k * (kRowsPer + 1) + b;
+                    zk[k] = (long long)(((unsigned long long)zhi[o] << 32) | (unsigned long long)zlo[o]);
+                    if (zk[k] != 0) G = max(G, gk[k] + bitlen64(zk[k]));
+                }
+                uint64_t u[kRowsPer];
+                uint32_t neg = 0u;
+#pragma unroll
+                for (int k = 0; k < kRowsPer; ++k) {
+                    u[k] = (G == kNoRow || zk[k] == 0) ? 0ull : rescale_mag(zk[k], 56 + gk[k] - G);
+                    neg |= (zk[k] < 0 ? 1u : 0u) << k;
+                }
+                if (G != kNoRow && eb != kNoRow) Fb = eb + G - 56;
+                // the operand region held H_i, which the completed MMAs no longer read
+                store_row_slices(X, kSnapSlab, warp * kRowsPer + b, u, neg);
+            }
+            fence_proxy_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            if (tid == 0) {
+                issue_sliced_product(tbase, X, Wrec);  // P_i^T rows: (Z_i^T) M^T
+                mma_commit(&mbar_mma);
+            }
+            ok = __syncthreads_and(mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter));
+            ph_mma ^= 1u;
+            if (!ok) break;
+            fence_after_sync();
+            // ---- P_i: lane b, column a holds P_i[a][b] = z 2^{e_a + F_b - 56}
+#pragma unroll 1
+            for (int cb = 0; cb < 4; ++cb) {
+                long long z[8];
+                read_levels8(tlane, cb, z);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int a = 8 * cb + c;
+                    const int ea = e_exp[a];
+                    Pd[a * (kRowsPer + 1) + lane] =
+                        (Fb == kNoRow || ea == kNoRow) ? 0.0 : fixed_to_f64(z[c], ea + Fb - 56);
+                }
+            }
+            __syncwarp();
+            const int64_t slot = pb + warp;
+            if (slot < L) {
+                build_B_from_P(n, A.ne, A.m, Pd, kRowsPer + 1, Bs, tab, lane);
+                __syncwarp();
+                cd pf0;
+                const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
+                const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
+                const int NBr = shared ? A.NB : 1;  // the rare full eliminations run one node per round
+                cd S = cmk(0.0, 0.0);
+                for (int k0 = 0; k0 < A.nev; k0 += NBr) {
+                    const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
+                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
+                                   lane);
+                    if (lane == 0)
+                        for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
+                    __syncwarp();
+                }
+                if (lane == 0) {
+                    if (shared) S = cmul(S, pf0);
+                    if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
+                    acc = cadd(acc, S);
+                    if (A.per_pair) A.per_pair[w * A.P + A.idx[slot]] = cmul(prefw, S);
+                }
+            }
+            fence_proxy_async_smem();  // workspace writes precede the next sub-tile's bulk copy
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+        }
+        if (!ok) {
+            if (tid == 0) {
+                abort_flag = 1;
+                raise_status(A.status, QCS_ERR_TIMEOUT);
+            }
+            continue;  // every thread leaves through the abort check at the top
+        }
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (tid == 0) A.partial[w * A.nchunks + ch] = cadd(cadd(red[0], red[1]), cadd(red[2], red[3]));
+    }
+    if (abort_flag && tid == 0) {  // a wait gave up: let the copy or MMAs in flight land first
+        // the phase that timed out is the last one waited on (its parity bit was flipped
+        // after the wait); an earlier, completed phase returns at once
+        mbar_wait_bounded(&mbar_load, ph_load ^ 1u, kWaitIter);
+        mbar_wait_bounded(&mbar_mma, ph_mma ^ 1u, kWaitIter);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) tmem_dealloc(tbase, kTmemCols);
+}
+
+// Pfaffian workspace of one warp for nb node matrices: the node matrices take the
+// warp's scratch (free once B^(s) is assembled from P), the rest a quarter of the
+// operand region.  Returns the bytes in the operand region, or 0 when the node
+// matrices do not fit the scratch.
+size_t tc_warp_layout(TcArgs &A, int NB) {
+    const int m = A.m, T = tri_count(m), d2 = m - A.ne;
+    const size_t nodes = (size_t)(T > NB * tri_count(d2) ? T : NB * tri_count(d2)) * sizeof(cd);
+    if (nodes > (size_t)kScratchBytes) return 0;
+    A.vm = m > NB * d2 ? m : NB * d2;
+    size_t o = 0;
+    A.off_B = (int)o;
+    o = align16(o + (size_t)T * sizeof(cd));
+    A.off_U = (int)o;
+    o = align16(o + (size_t)A.vm * sizeof(cd));
+    A.off_V = (int)o;
+    o = align16(o + (size_t)A.vm * sizeof(cd));
+    A.off_pf = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(cd));
+    A.off_inv = (int)o;
+    o = align16(o + (size_t)kMaxNB * sizeof(cd));
+    A.off_int = (int)o;
+    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
+    A.off_act = (int)o;
+    o = align16(o + (size_t)2 * A.vm);
+    A.off_pv = (int)o;
+    o = align16(o + (size_t)(A.vm / 2) * sizeof(cd));
+    return o;
+}
+
+}  // namespace
+
+size_t qcs_tc_walker_bytes(int64_t W) { return (size_t)(W > 0 ? W : 1) * kWalkRecBytes; }
+
+int qcs_tc_snaps_per_tile() { return kSnapsPerTile; }
+
+bool qcs_tc_supported(int n) { return n >= 2 && 2 * n <= kRowsPer; }
+
+qcs_status qcs_tc_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st) {
+    if (s->tc_rec) return QCS_OK;
+    if (!qcs_tc_supported(s->n)) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tensor-core congruence needs n <= 16");
+    const int64_t nsub = (s->P + kSnapsPerSub - 1) / kSnapsPerSub;
+    const size_t bytes = (size_t)(nsub > 0 ? nsub : 1) * kSnapRecBytes;
+    cudaError_t e = cudaMalloc(&s->tc_rec, bytes);
+    if (e != cudaSuccess) {
+        s->tc_rec = nullptr;
+        return qcs_fail(ctx, QCS_ERR_CUDA, "tensor-core snapshot records: cudaMalloc");
+    }
+    if (nsub == 0) return QCS_OK;
+    const int wpb = 4;
+    const size_t smem = (size_t)wpb * kRowsPer * kRowsPer * sizeof(double);
+    if (qcs_set_smem(ctx, (const void *)tc_snapshot_prep_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    const int64_t nslots = nsub * kSnapsPerSub;
+    int64_t blocks = (nslots + wpb - 1) / wpb;
+    if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
+    tc_snapshot_prep_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(s->n, nslots, s->Qt, s->idx, s->d_count,
+                                                                       (unsigned char *)s->tc_rec);
+    return qcs_check_launch(ctx, "tc_snapshot_prep_kernel");
+}
+
+qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned char *walk_rec, cudaStream_t st) {
+    const int n = L.n;
+    if (!qcs_tc_supported(n)) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tensor-core congruence needs n <= 16");
+    if (!L.s->tc_rec) return qcs_fail(ctx, QCS_ERR_ARG, "snapshot records for the tensor-core path are missing");
+    if (L.W == 0) return QCS_OK;
+    {
+        const int wpb = 4;
+        int64_t blocks = (L.W + wpb - 1) / wpb;
+        if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
+        tc_walker_prep_kernel<<<(unsigned)blocks, wpb * 32, 0, st>>>(n, L.W, L.Ut, walk_rec);
+        qcs_status r = qcs_check_launch(ctx, "tc_walker_prep_kernel");
+        if (r != QCS_OK) return r;
+    }
+    TcArgs A;
+    memset(&A, 0, sizeof(A));
+    A.n = n;
+    A.ne = L.ne;
+    A.m = 2 * n - L.ne;
+    A.d = n - L.ne;
+    A.nev = L.plan.nev;
+    A.W = L.W;
+    A.P = L.P;
+    A.nchunks = L.nchunks;
+    // node matrices per round: the requested count, or the largest balanced count whose
+    // four workspaces fit in the operand region
+    const size_t region = (size_t)kSlices * kSnapSlab;
+    auto fits = [&](int nb) {
+        const size_t b = tc_warp_layout(A, nb);
+        return b > 0 && 4 * b <= region;
+    };
+    int NB = 1;
+    if (L.config > 0) {
+        NB = L.config < A.nev ? L.config : A.nev;
+        if (NB > kMaxNB) NB = kMaxNB;
+        while (NB > 1 && !fits(NB)) --NB;
+    } else {
+        for (int rounds = 1; rounds <= A.nev; ++rounds) {
+            const int nb = (A.nev + rounds - 1) / rounds;
+            if (nb > kMaxNB) continue;
+            if (fits(nb)) {
+                NB = nb;
+                break;
+            }
+        }
+    }
+    if (!fits(NB)) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tc kernel: workspace");
+    A.NB = NB;
+    A.warp_bytes = (int)tc_warp_layout(A, NB);
+    A.smem_scratch = kSnapRecBytes + kWalkRecBytes;
+    A.smem_tab = A.smem_scratch + 4 * kScratchBytes;
+    const size_t smem = (size_t)A.smem_tab + align16((size_t)tri_count(A.m) * sizeof(uint16_t));
+    A.snap_rec = (const unsigned char *)L.s->tc_rec;
+    A.walk_rec = walk_rec;
+    A.pref = L.pref;
+    A.idx = L.s->idx;
+    A.d_count = L.s->d_count;
+    A.partial = L.partial;
+    A.per_pair = L.per_pair;
+    A.counter = L.counter;
+    A.status = ctx->d_status;
+    for (int k = 0; k < L.plan.nev; ++k) {
+        A.wnode[k] = L.plan.wnode[k];
+        A.gamma[k] = L.plan.gamma[k];
+    }
+    if (smem + 1024 > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tc kernel: shared memory");
+    if (qcs_set_smem(ctx, (const void *)tc_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    // blocks per SM: what shared memory allows, and at most 512 / kTmemCols so that every
+    // block's tensor-memory allocation is granted at once
+    int per_sm = (int)(ctx->smem_per_sm / (smem + 1024 + 1024));
+    if (per_sm > (int)(512 / kTmemCols)) per_sm = (int)(512 / kTmemCols);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ntiles = A.W * (int64_t)A.nchunks;
+    int64_t blocks = (int64_t)ctx->num_sms * per_sm;
+    if (blocks > ntiles) blocks = ntiles;
+    if (blocks < 1) blocks = 1;
+    if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
+        return qcs_fail(ctx, QCS_ERR_CUDA, "tc tile counter reset");
+    qcs_prof_begin(ctx, st);
+    tc_pair_kernel<<<(unsigned)blocks, 128, smem, st>>>(A);
+    qcs_prof_end(ctx, st);
+    return qcs_check_launch(ctx, "tc_pair_kernel");
+}

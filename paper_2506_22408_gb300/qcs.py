@@ -26,6 +26,8 @@ QCS_FP64 = 0
 QCS_TF32X3 = 1
 QCS_FLAG_ALL_NODES = 1
 QCS_FLAG_DFT_NODES = 2
+QCS_FLAG_FP64_ALU = 4
+QCS_FLAG_FP64_TC = 8
 MAX_NODES = 49
 QCS_ERR_ARG, QCS_ERR_CUDA, QCS_ERR_NONFINITE, QCS_ERR_SINGULAR, QCS_ERR_TIMEOUT, QCS_ERR_UNSUPPORTED = 1, 2, 4, 8, 16, 32
 STATUS_BITS = {1: "ARG", 2: "CUDA", 4: "NONFINITE", 8: "SINGULAR", 16: "TIMEOUT", 32: "UNSUPPORTED"}

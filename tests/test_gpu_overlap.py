@@ -3,7 +3,8 @@
 Tolerance (plain FP64 path): for every pair |o_gpu - o_oracle| <= 1e-10 * s_p,
 where s_p = |prefactor| * sum_x |c_x| C(2n,2x)/C(n,x) is the magnitude of the
 estimator's terms before they cancel (returned by the oracle); for a walker
-mean, 1e-10 times the mean of s_p.  Parity -1 pairs must be exactly zero.
+mean, 1e-10 times the mean of s_p and 1e-10 relative to the walker's overlap
+(parity_checks.check_walkers_relative).  Parity -1 pairs must be exactly zero.
 """
 from __future__ import annotations
 
@@ -13,6 +14,7 @@ import torch
 
 import oracle.oracle as orc
 from paper_2506_22408_gb300 import qcs, synth
+from parity_checks import check_walkers_relative
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -50,6 +52,7 @@ def check_pairs(gpu_pp, orc_pp, scale, parity):
 def check_walkers(gpu_ov, orc_ov, scale):
     ms = scale.mean(axis=1)
     assert np.all(np.abs(gpu_ov - orc_ov) <= TOL * ms), np.max(np.abs(gpu_ov - orc_ov) / ms)
+    check_walkers_relative(gpu_ov, orc_ov, scale)
 
 
 def test_snapshot_parity_flags(ctx):
