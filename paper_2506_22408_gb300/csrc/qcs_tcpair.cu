@@ -27,11 +27,12 @@
 //  2. 56 tcgen05.mma kind::f16 (28 slice products, K = 32 as two K = 16 steps) form
 //     Z_i = H_i M^T, level L in tensor-memory columns 32(L-2) .. 32(L-2)+31;
 //  3. each warp reads its 32 lanes (row k of Z_i), combines the levels into fixed
-//     point, transposes through shared memory so that lane b holds row b of Z_i^T,
-//     and writes its seven slices (row scale per b) as the next A operand;
+//     point, takes the row scale of each row b of Z_i^T by a warp max-reduction and
+//     writes the seven slices straight from the lanes as the next A operand, laid out
+//     MN-major (lane k owns column k of Z_i^T);
 //  4. 56 more MMAs form P_i = M Z_i (lane b of warp i, column a: P_i[a][b]); each warp
-//     converts its lanes to FP64, assembles B^(s) and runs the node Pfaffians of the
-//     FP64 path (qcs_pair.cuh).
+//     converts its lanes to FP64, keeps the upper triangle of P_i, assembles B^(s) and
+//     runs the node Pfaffians of the FP64 path (qcs_pair.cuh).
 // Every wait is bounded: a time-out raises QCS_ERR_TIMEOUT, drains and frees the
 // tensor memory.
 #include "qcs_internal.h"
@@ -52,7 +53,8 @@ constexpr uint32_t kWaitIter = 1u << 26;                      // bounded mbarrie
 constexpr int kSnapSlab = kSnapsPerSub * kSliceBytes;         // one slice of 4 snapshots: 8 KB
 constexpr int kSnapRecBytes = kSlices * kSnapSlab + kSnapsPerSub * kRowsPer * 4;  // + row exponents
 constexpr int kWalkRecBytes = kSlices * kSliceBytes + kRowsPer * 4;
-constexpr int kScratchBytes = 2 * kRowsPer * (kRowsPer + 1) * 4;  // per warp: transpose / P (32 x 33 doubles)
+constexpr int kOperandBytes = kSlices * kSnapSlab;           // operand region: later four warp workspaces
+constexpr int kPuBytes = (kRowsPer * (kRowsPer - 1) / 2) * 8; // upper triangle of P (32 x 32), FP64
 
 static_assert(kSnapRecBytes % 16 == 0 && kWalkRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
@@ -157,11 +159,12 @@ __global__ void tc_snapshot_prep_kernel(int n, int64_t nslots, const cd *__restr
 struct TcArgs {
     int n, ne, m, d, nev, NB;
     int64_t W, P;
-    int nchunks;      // tiles per walker (chunks of kSnapsPerTile list slots)
-    int warp_bytes;   // Pfaffian workspace per warp (in the operand region)
-    int off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // in the warp's operand quarter
+    int nchunks;      // tiles per walker (chunks of kSnapsPerTile list positions)
+    int ws_bytes;     // Pfaffian workspace per warp
+    int ws_in_operands;  // 1: the workspaces are quarters of the operand region
+    int off_P, off_N, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // B^(s) at offset 0
     int vm;
-    int smem_scratch, smem_tab;  // byte offsets of the per-warp scratch and the pair table
+    int smem_tab, smem_ws;  // byte offsets of the pair table and (if separate) the workspaces
     const unsigned char *snap_rec;
     const unsigned char *walk_rec;
     const cd *pref;
@@ -175,29 +178,32 @@ struct TcArgs {
     cd gamma[QCS_MAX_NODES];
 };
 
-// The 56 MMAs of one sliced product: level L = i + j (i the A slice, j the B slice)
-// into columns 32 (L - 2); A slabs kSnapSlab apart (M = 128), B slabs kSliceBytes
-// apart (N = 32).
-__device__ __forceinline__ void issue_sliced_product(uint32_t tbase, const unsigned char *A, const unsigned char *B) {
-    const uint32_t id = idesc_bf16(kSnapsPerSub * kRowsPer, kRowsPer);
+// The MMAs of levels Lfirst..Llast of one sliced product: level L = i + j (i the A
+// slice, j the B slice) into columns 32 (L - Lfirst); A slabs kSnapSlab apart (M = 128),
+// B slabs kSliceBytes apart (N = 32); the A operand K-major (H slices) or MN-major
+// (slices of Z^T).
+__device__ __forceinline__ void issue_levels(uint32_t tbase, const unsigned char *A, const unsigned char *B, int Lfirst,
+                                             int Llast, bool a_mn_major) {
+    const uint32_t id = idesc_bf16(kSnapsPerSub * kRowsPer, kRowsPer) | (a_mn_major ? (1u << 15) : 0u);
 #pragma unroll 1
-    for (int L = 2; L <= kSlices + 1; ++L) {
+    for (int L = Lfirst; L <= Llast; ++L) {
         uint32_t acc = 0u;
-        for (int i = (L - kSlices > 1 ? L - kSlices : 1); i <= (L - 1 < kSlices ? L - 1 : kSlices); ++i) {
+        for (int i = 1; i <= (L - 1 < kSlices ? L - 1 : kSlices); ++i) {
             const int j = L - i;
+            if (j > kSlices) continue;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
+            for (int ks = 0; ks < 2; ++ks) {  // K = 32: two K = 16 steps, 2 core matrices (256 bytes) apart
                 const uint64_t ad = desc_kmajor(A + (size_t)(i - 1) * kSnapSlab + 256 * ks, 128, 512);
                 const uint64_t bd = desc_kmajor(B + (size_t)(j - 1) * kSliceBytes + 256 * ks, 128, 512);
-                mma_f16(tbase + (uint32_t)(32 * (L - 2)), ad, bd, id, acc);
+                mma_f16(tbase + (uint32_t)(32 * (L - Lfirst)), ad, bd, id, acc);
                 acc = 1u;
             }
         }
     }
 }
 
-// Columns cb*8 .. cb*8+7 of the seven level accumulators of this thread's lane,
-// combined into fixed point.
+// Columns cb*8 .. cb*8+7 of the seven level accumulators of this thread's lane (level L
+// in columns 32 (L - 2)), combined into fixed point: one wait for the seven loads.
 __device__ __forceinline__ void read_levels8(uint32_t taddr, int cb, long long (&z)[8]) {
     float v[kLevels][8];
 #pragma unroll
@@ -212,10 +218,15 @@ __device__ __forceinline__ void read_levels8(uint32_t taddr, int cb, long long (
     }
 }
 
-// B^(s) (packed upper, m x m) from P = R J R^T (row stride ldp), R = [Re T; Im T]:
-// selected row x < ne is T_x (= R[x] + i R[n+x]); x >= ne is Re T_j (even offset) or
-// -Im T_j (odd offset) for the empty mode j = ne + (x - ne)/2.
-__device__ void build_B_from_P(int n, int ne, int m, const double *__restrict__ Pd, int ldp, cd *__restrict__ Bs,
+// P[a][b] from the upper triangle Pu (P is skew-symmetric).
+__device__ __forceinline__ double pget(const double *__restrict__ Pu, int a, int b) {
+    return a < b ? Pu[tri_index(a, b)] : (a > b ? -Pu[tri_index(b, a)] : 0.0);
+}
+
+// B^(s) (packed upper, m x m) from P = R J R^T, R = [Re T; Im T]: selected row x < ne is
+// T_x (= R[x] + i R[n+x]); x >= ne is Re T_j (even offset) or -Im T_j (odd offset) for
+// the empty mode j = ne + (x - ne)/2.
+__device__ void build_B_from_P(int n, int ne, int m, const double *__restrict__ Pu, cd *__restrict__ Bs,
                                const uint16_t *__restrict__ tab, int lane) {
     const int T = tri_count(m);
     for (int t = lane; t < T; t += 32) {
@@ -223,26 +234,66 @@ __device__ void build_B_from_P(int n, int ne, int m, const double *__restrict__ 
         pair_of(tab, t, x, y);  // x < y
         cd v;
         if (y < ne) {  // occupied x occupied: (R_x + i R_nx) J (R_y + i R_ny)^T
-            const double prr = Pd[x * ldp + y], pii = Pd[(n + x) * ldp + n + y];
-            const double pri = Pd[x * ldp + n + y], pir = Pd[(n + x) * ldp + y];
+            const double prr = pget(Pu, x, y), pii = pget(Pu, n + x, n + y);
+            const double pri = pget(Pu, x, n + y), pir = pget(Pu, n + x, y);
             v = cmk(prr - pii, pri + pir);
         } else {
             const int jy = ne + ((y - ne) >> 1);
             const bool yim = (y - ne) & 1;
             const int ry = yim ? n + jy : jy;
             if (x < ne) {  // occupied x empty: (R_x + i R_nx) J (+-R_ry)^T
-                const double re = Pd[x * ldp + ry], im = Pd[(n + x) * ldp + ry];
+                const double re = pget(Pu, x, ry), im = pget(Pu, n + x, ry);
                 v = yim ? cmk(-re, -im) : cmk(re, im);
             } else {
                 const int jx = ne + ((x - ne) >> 1);
                 const bool xim = (x - ne) & 1;
-                const int rx = xim ? n + jx : jx;
-                const double re = Pd[rx * ldp + ry];
+                const double re = pget(Pu, xim ? n + jx : jx, ry);
                 v = cmk((xim != yim) ? -re : re, 0.0);
             }
         }
         Bs[t] = v;
     }
+}
+
+// Byte offset of element (row, k) of a 16-bit MN-major operand of 128 rows x 32 (K) with
+// no swizzle: 8 (rows) x 8 (K) core matrices with the rows contiguous (16 bytes per K
+// index), K-adjacent core matrices 128 bytes apart (LBO), row-adjacent ones 512 bytes
+// apart (SBO), as the descriptor of the K-major operands.
+__host__ __device__ __forceinline__ uint32_t mnmajor16(int row, int k) {
+    return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (k & 7) * 16 + (row & 7) * 2);
+}
+
+// Slices of Z_i^T, read from tensor memory (lane k holds row k of Z_i, z_kb worth
+// z 2^{g_k + e_b - 56}): row b of Z_i^T gets the scale 2^{F_b}, F_b = e_b + G_b - 56 with
+// G_b = max_k (g_k + bitlen z_kb) (a warp max-reduction); the slices go MN-major into
+// the A operand rows row0 + b.  Returns F_b for b = lane (kNoRow for a zero row).
+__device__ __forceinline__ int slice_zt(uint32_t tlane, int gk, int eb_lane, unsigned char *Abase, int row0, int lane) {
+    int Gl = kNoRow;
+#pragma unroll 1
+    for (int cb = 0; cb < 4; ++cb) {
+        long long z[8];
+        read_levels8(tlane, cb, z);
+        uint64_t u[8];
+        uint32_t neg = 0u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int t = z[c] != 0 ? gk + bitlen64(z[c]) : kNoRow;
+            const int G = __reduce_max_sync(QCS_FULL, t);
+            if (8 * cb + c == lane) Gl = G;
+            u[c] = (z[c] == 0 || G == kNoRow) ? 0ull : rescale_mag(z[c], 56 + gk - G);
+            neg |= (z[c] < 0 ? 1u : 0u) << c;
+        }
+#pragma unroll
+        for (int i = 1; i <= kSlices; ++i) {
+            uint4 w;
+            w.x = pack_bf16x2(slice_of(u[0], i, neg & 1u), slice_of(u[1], i, (neg >> 1) & 1u));
+            w.y = pack_bf16x2(slice_of(u[2], i, (neg >> 2) & 1u), slice_of(u[3], i, (neg >> 3) & 1u));
+            w.z = pack_bf16x2(slice_of(u[4], i, (neg >> 4) & 1u), slice_of(u[5], i, (neg >> 5) & 1u));
+            w.w = pack_bf16x2(slice_of(u[6], i, (neg >> 6) & 1u), slice_of(u[7], i, (neg >> 7) & 1u));
+            *reinterpret_cast<uint4 *>(Abase + (size_t)(i - 1) * kSnapSlab + mnmajor16(row0 + 8 * cb, lane)) = w;
+        }
+    }
+    return (Gl != kNoRow && eb_lane != kNoRow) ? eb_lane + Gl - 56 : kNoRow;
 }
 
 __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__ TcArgs A) {
@@ -254,19 +305,16 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     __shared__ cd red[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = A.n;
-    unsigned char *X = smem_tc;                                   // operands, then workspaces
+    unsigned char *X = smem_tc;                                   // operands, then (usually) workspaces
     unsigned char *Wrec = smem_tc + kSnapRecBytes;                // walker record
-    const int *g_exp = reinterpret_cast<const int *>(X + kSlices * kSnapSlab);   // snapshot row exponents
+    const int *g_exp = reinterpret_cast<const int *>(X + kOperandBytes);              // snapshot row exponents
     const int *e_exp = reinterpret_cast<const int *>(Wrec + kSlices * kSliceBytes);  // walker row exponents
-    unsigned char *scr = smem_tc + A.smem_scratch + (size_t)warp * kScratchBytes;
-    uint32_t *zlo = reinterpret_cast<uint32_t *>(scr);
-    uint32_t *zhi = zlo + kRowsPer * (kRowsPer + 1);
-    double *Pd = reinterpret_cast<double *>(scr);
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_tc + A.smem_tab);
     build_pair_table(tab, tri_count(A.m));
-    unsigned char *wbase = X + (size_t)warp * A.warp_bytes;
-    cd *Ns = reinterpret_cast<cd *>(scr);  // node matrices: the scratch, once P is consumed
-    cd *Bs = reinterpret_cast<cd *>(wbase + A.off_B);
+    unsigned char *wbase = (A.ws_in_operands ? X : smem_tc + A.smem_ws) + (size_t)warp * A.ws_bytes;
+    cd *Bs = reinterpret_cast<cd *>(wbase);
+    double *Pu = reinterpret_cast<double *>(wbase + A.off_P);
+    cd *Ns = reinterpret_cast<cd *>(wbase + A.off_N);  // aliases Pu: written once B^(s) is assembled
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
     cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
@@ -293,15 +341,31 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     const int64_t L = *A.d_count;
     const int64_t ntiles = A.W * (int64_t)A.nchunks;
     uint32_t ph_load = 0, ph_mma = 0;
+    bool load_pending = false, mma_pending = false;
     bool ok = true;
+    // one sliced product issued by thread 0, then a bounded wait whose outcome the block shares
+    auto product = [&](bool mn) {
+        if (tid == 0) {
+            fence_after_sync();
+            issue_levels(tbase, X, Wrec, 2, kSlices + 1, mn);
+            mma_commit(&mbar_mma);
+        }
+        mma_pending = true;
+        const bool r = __syncthreads_and(mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter));
+        if (r) {
+            ph_mma ^= 1u;
+            mma_pending = false;
+            fence_after_sync();
+        }
+        return r;
+    };
     for (;;) {
         fence_proxy_async_smem();  // generic writes to the operand region precede the next bulk copies
-        fence_before_sync();
         __syncthreads();
-        if (tid == 0) next_tile = (long long)atomicAdd(A.counter, 1ull);
+        if (tid == 0) next_tile = abort_flag ? (long long)ntiles : (long long)atomicAdd(A.counter, 1ull);
         __syncthreads();
         const int64_t t = next_tile;
-        if (t >= ntiles || abort_flag) break;
+        if (t >= ntiles) break;
         const int ch = (int)(t / A.W);  // chunk-major: a chunk's records stay in L2 over the walkers
         const int64_t w = t - (int64_t)ch * A.W;
         const int64_t p0 = (int64_t)ch * kSnapsPerTile;
@@ -320,69 +384,20 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
                 bulk_copy(X, A.snap_rec + (size_t)(pb / kSnapsPerSub) * kSnapRecBytes, kSnapRecBytes, &mbar_load);
                 if (s == 0) bulk_copy(Wrec, A.walk_rec + (size_t)w * kWalkRecBytes, kWalkRecBytes, &mbar_load);
             }
-            // every wait is bounded, and its outcome is made uniform over the block
+            load_pending = true;
             ok = __syncthreads_and(mbar_wait_bounded(&mbar_load, ph_load, kWaitIter));
+            if (!ok) break;
             ph_load ^= 1u;
-            if (!ok) break;
-            if (tid == 0) {
-                fence_after_sync();
-                issue_sliced_product(tbase, X, Wrec);  // Z_i = H_i M^T
-                mma_commit(&mbar_mma);
-            }
-            ok = __syncthreads_and(mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter));
-            ph_mma ^= 1u;
-            if (!ok) break;
-            fence_after_sync();
-            // ---- Z_i: lane k holds row k; combine, transpose, re-slice as rows of Z_i^T
-#pragma unroll 1
-            for (int cb = 0; cb < 4; ++cb) {
-                long long z[8];
-                read_levels8(tlane, cb, z);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int o = lane * (kRowsPer + 1) + 8 * cb + c;
-                    zlo[o] = (uint32_t)(unsigned long long)z[c];
-                    zhi[o] = (uint32_t)((unsigned long long)z[c] >> 32);
-                }
-            }
-            __syncwarp();
-            int Fb = kNoRow;  // row scale of row b = lane of Z_i^T
-            {
-                const int b = lane;
-                const int eb = e_exp[b];
-                const int *gk = g_exp + warp * kRowsPer;
-                long long zk[kRowsPer];
-                int G = kNoRow;
-#pragma unroll
-                for (int k = 0; k < kRowsPer; ++k) {
-                    const int o = k * (kRowsPer + 1) + b;
-                    zk[k] = (long long)(((unsigned long long)zhi[o] << 32) | (unsigned long long)zlo[o]);
-                    if (zk[k] != 0) G = max(G, gk[k] + bitlen64(zk[k]));
-                }
-                uint64_t u[kRowsPer];
-                uint32_t neg = 0u;
-#pragma unroll
-                for (int k = 0; k < kRowsPer; ++k) {
-                    u[k] = (G == kNoRow || zk[k] == 0) ? 0ull : rescale_mag(zk[k], 56 + gk[k] - G);
-                    neg |= (zk[k] < 0 ? 1u : 0u) << k;
-                }
-                if (G != kNoRow && eb != kNoRow) Fb = eb + G - 56;
-                // the operand region held H_i, which the completed MMAs no longer read
-                store_row_slices(X, kSnapSlab, warp * kRowsPer + b, u, neg);
-            }
+            load_pending = false;
+            // ---- Z_i = H_i M^T: lane k holds row k; sliced by rows of Z_i^T (MN-major)
+            if (!(ok = product(false))) break;
+            // the operand region held H_i, which the completed MMAs no longer read
+            const int Fb = slice_zt(tlane, g_exp[warp * kRowsPer + lane], e_exp[lane], X, warp * kRowsPer, lane);
             fence_proxy_async_smem();
             fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            if (tid == 0) {
-                issue_sliced_product(tbase, X, Wrec);  // P_i^T rows: (Z_i^T) M^T
-                mma_commit(&mbar_mma);
-            }
-            ok = __syncthreads_and(mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter));
-            ph_mma ^= 1u;
-            if (!ok) break;
-            fence_after_sync();
-            // ---- P_i: lane b, column a holds P_i[a][b] = z 2^{e_a + F_b - 56}
+            __syncthreads();  // every warp's tensor-memory reads and operand writes are done
+            // ---- P_i = M Z_i: lane b, column a holds P_i[a][b] = z 2^{e_a + F_b - 56}
+            if (!(ok = product(true))) break;
 #pragma unroll 1
             for (int cb = 0; cb < 4; ++cb) {
                 long long z[8];
@@ -390,15 +405,17 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int a = 8 * cb + c;
-                    const int ea = e_exp[a];
-                    Pd[a * (kRowsPer + 1) + lane] =
-                        (Fb == kNoRow || ea == kNoRow) ? 0.0 : fixed_to_f64(z[c], ea + Fb - 56);
+                    if (a < lane) {  // the operand region is free: the upper triangle of P_i
+                        const int ea = e_exp[a];
+                        Pu[tri_index(a, lane)] = (Fb == kNoRow || ea == kNoRow) ? 0.0 : fixed_to_f64(z[c], ea + Fb - 56);
+                    }
                 }
             }
+            fence_before_sync();  // this warp's tensor-memory reads precede the next sub-tile's MMAs
             __syncwarp();
             const int64_t slot = pb + warp;
             if (slot < L) {
-                build_B_from_P(n, A.ne, A.m, Pd, kRowsPer + 1, Bs, tab, lane);
+                build_B_from_P(n, A.ne, A.m, Pu, Bs, tab, lane);
                 __syncwarp();
                 cd pf0;
                 const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
@@ -421,9 +438,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
                 }
             }
             fence_proxy_async_smem();  // workspace writes precede the next sub-tile's bulk copy
-            fence_before_sync();
             __syncthreads();
-            fence_after_sync();
         }
         if (!ok) {
             if (tid == 0) {
@@ -436,11 +451,9 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
         __syncthreads();
         if (tid == 0) A.partial[w * A.nchunks + ch] = cadd(cadd(red[0], red[1]), cadd(red[2], red[3]));
     }
-    if (abort_flag && tid == 0) {  // a wait gave up: let the copy or MMAs in flight land first
-        // the phase that timed out is the last one waited on (its parity bit was flipped
-        // after the wait); an earlier, completed phase returns at once
-        mbar_wait_bounded(&mbar_load, ph_load ^ 1u, kWaitIter);
-        mbar_wait_bounded(&mbar_mma, ph_mma ^ 1u, kWaitIter);
+    if (abort_flag && tid == 0) {  // a wait gave up: let a copy or MMAs in flight land first
+        if (load_pending) mbar_wait_bounded(&mbar_load, ph_load, kWaitIter);
+        if (mma_pending) mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter);
     }
     fence_before_sync();
     __syncthreads();
@@ -448,18 +461,16 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     if (warp == 0) tmem_dealloc(tbase, kTmemCols);
 }
 
-// Pfaffian workspace of one warp for nb node matrices: the node matrices take the
-// warp's scratch (free once B^(s) is assembled from P), the rest a quarter of the
-// operand region.  Returns the bytes in the operand region, or 0 when the node
-// matrices do not fit the scratch.
+// Pfaffian workspace of one warp for nb node matrices: B^(s), then the upper triangle
+// of P aliased by the node matrices (written once B^(s) is assembled), then the Gauss
+// vectors and the step records; returns its bytes.
 size_t tc_warp_layout(TcArgs &A, int NB) {
     const int m = A.m, T = tri_count(m), d2 = m - A.ne;
     const size_t nodes = (size_t)(T > NB * tri_count(d2) ? T : NB * tri_count(d2)) * sizeof(cd);
-    if (nodes > (size_t)kScratchBytes) return 0;
     A.vm = m > NB * d2 ? m : NB * d2;
-    size_t o = 0;
-    A.off_B = (int)o;
-    o = align16(o + (size_t)T * sizeof(cd));
+    size_t o = align16((size_t)T * sizeof(cd));
+    A.off_P = A.off_N = (int)o;
+    o = align16(o + (nodes > (size_t)kPuBytes ? nodes : (size_t)kPuBytes));
     A.off_U = (int)o;
     o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_V = (int)o;
@@ -530,13 +541,12 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     A.W = L.W;
     A.P = L.P;
     A.nchunks = L.nchunks;
+    A.smem_tab = kSnapRecBytes + kWalkRecBytes;
+    A.smem_ws = A.smem_tab + (int)align16((size_t)tri_count(A.m) * sizeof(uint16_t));
     // node matrices per round: the requested count, or the largest balanced count whose
-    // four workspaces fit in the operand region
-    const size_t region = (size_t)kSlices * kSnapSlab;
-    auto fits = [&](int nb) {
-        const size_t b = tc_warp_layout(A, nb);
-        return b > 0 && 4 * b <= region;
-    };
+    // four workspaces fit in the operand region; when even one node per round does not
+    // fit there (large m), the workspaces get their own shared memory
+    auto fits = [&](int nb) { return 4 * tc_warp_layout(A, nb) <= (size_t)kOperandBytes; };
     int NB = 1;
     if (L.config > 0) {
         NB = L.config < A.nev ? L.config : A.nev;
@@ -552,12 +562,10 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
             }
         }
     }
-    if (!fits(NB)) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tc kernel: workspace");
     A.NB = NB;
-    A.warp_bytes = (int)tc_warp_layout(A, NB);
-    A.smem_scratch = kSnapRecBytes + kWalkRecBytes;
-    A.smem_tab = A.smem_scratch + 4 * kScratchBytes;
-    const size_t smem = (size_t)A.smem_tab + align16((size_t)tri_count(A.m) * sizeof(uint16_t));
+    A.ws_in_operands = fits(NB) ? 1 : 0;
+    A.ws_bytes = (int)tc_warp_layout(A, NB);
+    const size_t smem = (size_t)A.smem_ws + (A.ws_in_operands ? 0 : 4 * (size_t)A.ws_bytes);
     A.snap_rec = (const unsigned char *)L.s->tc_rec;
     A.walk_rec = walk_rec;
     A.pref = L.pref;
@@ -573,8 +581,9 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     }
     if (smem + 1024 > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tc kernel: shared memory");
     if (qcs_set_smem(ctx, (const void *)tc_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
-    // blocks per SM: what shared memory allows, and at most 512 / kTmemCols so that every
-    // block's tensor-memory allocation is granted at once
+    // blocks per SM: what shared memory allows (static words and the 1 KB the driver
+    // reserves per block included), and at most 512 / kTmemCols so that every block's
+    // tensor-memory allocation is granted at once
     int per_sm = (int)(ctx->smem_per_sm / (smem + 1024 + 1024));
     if (per_sm > (int)(512 / kTmemCols)) per_sm = (int)(512 / kTmemCols);
     if (per_sm < 1) per_sm = 1;
