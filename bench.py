@@ -46,6 +46,20 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
+def measured_peaks() -> dict:
+    """The machine's measured peaks (MEASURED_PEAKS.json at the repository root), else the
+    fallback figures of one earlier GB300 measurement (HBM 6.8 TB/s, BF16 1.9 PFLOP/s burst,
+    1.7 sustained), marked as such."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def add_dfma_context(obj, rate):
     """Beside every FP64 ("alu") roofline, the fraction of the measured FMA rate."""
     if isinstance(obj, dict):
@@ -138,6 +152,7 @@ CSRC = os.path.join(ROOT, "paper_2506_22408_gb300", "csrc")
 # Source files each timed kernel is compiled from; the committed DRAM figure of a
 # kernel is used only while all of them are unchanged.
 KERNEL_SOURCES = {
+    "tc_pair_kernel": ["qcs_tcpair.cu", "qcs_ozaki.cuh", "qcs_tc.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
     "pair_overlap_kernel": ["qcs_overlap.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
     "split_pair_kernel": ["qcs_split.cu", "qcs_pair.cuh", "qcs_tc.cuh", "qcs_common.cuh"],
     "grad_pair_kernel": ["qcs_grad.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
@@ -448,22 +463,68 @@ def run_dft_plan(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
     kms, kl = ctx.profile_read()
     assert ctx.sync_status() == 0
     t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
-    fpp = qcs.flops_per_pair(wl.n, wl.ne, 0, flags)
+    fpp = qcs.tc_work_per_pair(wl.n, wl.ne, 0, flags)["fp64"]
     avg = kms / max(kl, 1)
     ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
     return {"metric": "walker x snapshot overlap pairs/s, roots-of-unity node plan", "value": ws * wl.W * wl.P * steps / t,
             "unit": "pairs/s", "steps": steps, "ms_per_step": 1e3 * t / steps,
             "nodes": f"{len(qcs.node_plan(wl.n, wl.ne, 0, flags)[0])} of {wl.n - wl.ne + 1} roots of unity",
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "pair_overlap_kernel", "kernel_ms": avg,
+                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "tc_pair_kernel", "kernel_ms": avg,
                          "flops_per_launch": fpp * npar * wl.W}}
+
+
+def run_alu_path(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
+    """The same workload (1024 x 20000, n=16, ne=8, Gauss plan) with the congruence on
+    the FP64 ALU (QCS_FLAG_FP64_ALU), the plain GPU path the tensor-core congruence is
+    measured against."""
+    import torch
+
+    from paper_2506_22408_gb300 import qcs
+
+    flags = qcs.QCS_FLAG_FP64_ALU
+    tuned = ctx.autotune(wl.n, wl.ne, 0, flags, use_cache=True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        snaps = qcs.Snapshots(ctx, Qd, bd)
+        qcs.overlap(ctx, snaps, Pd, flags=flags)
+        return snaps
+
+    for _ in range(2):
+        step()
+    barrier()
+    ctx.profile(True)
+    ctx.profile_read()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    ctx.profile(False)
+    kms, kl = ctx.profile_read()
+    assert ctx.sync_status() == 0
+    t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+    fpp = qcs.flops_per_pair(wl.n, wl.ne, 0, flags)
+    avg = kms / max(kl, 1)
+    ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
+    return {"metric": "walker x snapshot overlap pairs/s, congruence on the FP64 ALU", "value": ws * wl.W * wl.P * steps / t,
+            "unit": "pairs/s", "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "nontrivial_pairs_per_s": ws * wl.W * npar * steps / t,
+            "kernel_config": {"node_matrices_per_warp_round": tuned},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "kernel": "pair_overlap_kernel", "kernel_ms": avg,
+                         "flops_per_launch": fpp * npar * wl.W,
+                         "traffic": traffic_for("pair_overlap_kernel", wl.name)}}
 
 
 def run_variants(args, ctx, dev, flush, barrier, ws, steps=3):
     """The paper-shaped size (1024 x 20000, n=16, ne=8) with other snapshot
     ensembles: b uniform over the parity-consistent strings (every pair
-    non-trivial), and signed-permutation snapshots (the paper's ensemble; the
-    congruence is then a gather), with uniform and with parity-consistent b."""
+    non-trivial), and signed-permutation snapshots (the paper's ensemble), with
+    uniform and with parity-consistent b; the default (tensor-core) path."""
     import dataclasses
 
     import torch
@@ -504,14 +565,14 @@ def run_variants(args, ctx, dev, flush, barrier, ws, steps=3):
         kms, kl = ctx.profile_read()
         assert ctx.sync_status() == 0
         t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
-        fpp = (qcs.flops_per_pair_signed_perm(wl.n, wl.ne) if nsp == wl.P else qcs.flops_per_pair(wl.n, wl.ne))
+        fpp = qcs.tc_work_per_pair(wl.n, wl.ne)["fp64"]  # the default path at n = 16: tensor-core congruence
         avg = kms / max(kl, 1)
         ach = fpp * npar * wl.W / (avg * 1e-3) / 1e12
         out[key] = {"value": ws * wl.W * wl.P * steps / t, "unit": "pairs/s",
                     "nontrivial_pairs_per_s": ws * wl.W * npar * steps / t, "steps": steps,
                     "parity_plus_snapshots": npar, "signed_perm_snapshots": nsp,
                     "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                 "frac": ach / FP64_PEAK_TFLOPS, "kernel": "pair_overlap_kernel", "kernel_ms": avg,
+                                 "frac": ach / FP64_PEAK_TFLOPS, "kernel": "tc_pair_kernel", "kernel_ms": avg,
                                  "flops_per_pair": fpp}}
         del Qd, bd, Pd
     return out
@@ -672,8 +733,16 @@ def run_energy(args, ctx, dev, flush, barrier, ws, steps=2):
                          "traffic": traffic_for("energy_pair_kernel", f"local energy n={n} ne={ne} {W}x{P} nchol={nchol}")}}
 
 
-def cpu_baseline(wl, data, target_s=10.0):
-    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+def cpu_baseline(wl, data, gpu_overlap, gpu_sample, target_s=10.0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload; the same oracle
+    results also give the parity of the GPU path at the benchmark's size: every pair of
+    the sample (|o_gpu - o_oracle| / s_p, s_p the magnitude of the pair's terms before
+    they cancel, and exact zeros for parity -1), the sample's walker means, and three
+    whole walkers over all snapshots against the overlaps of the timed steps (relative
+    to |O|).  gpu_sample(Wc, Pc) returns the GPU's per-pair and walker outputs on the
+    sample; gpu_overlap holds the timed steps' walker overlaps."""
+    import numpy as np
+
     import oracle.oracle as orc
 
     cores = orc.max_threads()
@@ -685,20 +754,38 @@ def cpu_baseline(wl, data, target_s=10.0):
     # grow the sample to about target_s seconds of CPU work
     Pc2 = int(min(wl.P, max(Pc, Pc * target_s / max(dt, 1e-3))))
     t0 = time.perf_counter()
-    _, _, _, used = orc.overlap(data["Phi"][:Wc], data["Q"][:Pc2], data["b"][:Pc2], threads=cores)
+    oo, opp, sc, used = orc.overlap(data["Phi"][:Wc], data["Q"][:Pc2], data["b"][:Pc2], threads=cores, per_pair=True)
     dt = time.perf_counter() - t0
     # the same oracle on one host thread, on a smaller sample (about 2 s)
     P1 = max(1, min(Pc2, int(Pc2 * 2.0 / max(dt * used, 1e-3))))
     t0 = time.perf_counter()
     orc.overlap(data["Phi"][:Wc], data["Q"][:P1], data["b"][:P1], threads=1)
     dt1 = time.perf_counter() - t0
+    # parity: the sample pair by pair, its walker means, and three whole walkers
+    gov, gpp, gpar = gpu_sample(Wc, Pc2)
+    ok = gpar == 1
+    pair_err = np.abs(gpp[:, ok] - opp[:, ok]) / sc[:, ok]
+    sample_rel = np.abs(gov - oo) / np.abs(oo)
+    sel = np.array([0, wl.W // 2, wl.W - 1])
+    fo, _, fsc, _ = orc.overlap(data["Phi"][sel], data["Q"], data["b"], threads=cores, per_pair=True)
+    full_rel = np.abs(gpu_overlap[sel] - fo) / np.abs(fo)
     orc.overlap(data["Phi"][:1], data["Q"][:1], data["b"][:1], threads=cores)  # restore the thread count
+    parity = {"pairs": int(ok.sum()) * Wc, "pair_err_over_scale_max": float(pair_err.max()),
+              "pair_err_over_scale_median": float(np.median(pair_err)),
+              "parity_minus_pairs_exactly_zero": bool(np.all(gpp[:, ~ok] == 0)),
+              "sample_walkers": Wc, "sample_walker_rel_err_max": float(sample_rel.max()),
+              "sample_walker_rel_err_median": float(np.median(sample_rel)),
+              "full_walkers": sel.tolist(), "full_walker_rel_err": [float(x) for x in full_rel],
+              "full_walker_cancellation": [float(x) for x in fsc.mean(axis=1) / np.abs(fo)],
+              "tolerance": "pairs 1e-10 s_p, walkers 1e-10 relative",
+              "within_tolerance": bool(pair_err.max() <= 1e-10 and sample_rel.max() <= 1e-10
+                                       and full_rel.max() <= 1e-10 and np.all(gpp[:, ~ok] == 0))}
     return {"value": Wc * Pc2 / dt, "unit": "pairs/s", "cores": int(used), "kind": "oracle",
             "sample": f"{Wc} walkers x {Pc2} snapshots of the same workload (first rows), "
                       f"{dt:.1f} s, FP64, 2n+1 roots-of-unity nodes, OpenMP over pairs",
             "one_thread": {"value": Wc * P1 / dt1, "unit": "pairs/s",
                            "sample": f"{Wc} walkers x {P1} snapshots, {dt1:.1f} s"},
-            "cpu_model": cpu_model()}
+            "cpu_model": cpu_model(), "parity": parity}
 
 
 def cpu_model() -> str:
@@ -769,6 +856,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batching workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
     ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
+    ap.add_argument("--no-alu-path", action="store_true", help="skip the FP64 ALU congruence comparison")
     ap.add_argument("--no-rdm", action="store_true", help="skip the shadow RDM workload")
     ap.add_argument("--no-vce", action="store_true", help="skip the virtual-correlation-energy workload")
     ap.add_argument("--no-energy", action="store_true", help="skip the local-energy workload")
@@ -778,7 +866,7 @@ def main():
                     help="skip the parity-consistent and signed-permutation snapshot ensembles")
     ap.add_argument("--prec-walkers", type=int, default=0, help="override the split-precision walkers (profiling)")
     ap.add_argument("--batch-steps", type=int, default=50, help="AFQMC steps captured in the batching graph")
-    ap.add_argument("--batch-walker-scale", type=float, default=0.25,
+    ap.add_argument("--batch-walker-scale", type=float, default=1.0,
                     help="scale of the batching walker counts (1.0: 1024/512/256/128/64 walkers)")
     ap.add_argument("--grad-snapshots", type=int, default=0, help="override the differentiation snapshots")
     ap.add_argument("--walkers", type=int, default=0, help="override the walker count (profiling cases)")
@@ -850,6 +938,7 @@ def main():
         barrier()
     ctx.profile(False)
     kern_ms, kern_launches = ctx.profile_read()
+    ov_timed = ov.cpu().numpy()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
     t_total = max_over_ranks(t_total, ws)
@@ -886,6 +975,9 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, data, dev, step, barrier, ws, wl)
+    alu = None
+    if not args.no_alu_path:
+        alu = run_alu_path(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar)
     grad = None
     if not args.no_grad:
         grad = run_grad(args, ctx, dev, barrier, ws)
@@ -896,16 +988,28 @@ def main():
     if not args.no_precision:
         precision = run_precision(args, ctx, dev, barrier, ws)
 
-    # ---------------- roofline of the dominant kernel
-    fpp = qcs.flops_per_pair(wl.n, wl.ne)
-    flops_launch = fpp * npar * wl.W
+    # ---------------- roofline of the dominant kernel (tensor-core congruence, n = 16)
+    work = qcs.tc_work_per_pair(wl.n, wl.ne)
+    fpp, tpp = work["fp64"], work["tensor"]
+    alu_fpp = qcs.flops_per_pair(wl.n, wl.ne, 0, qcs.QCS_FLAG_FP64_ALU)
     avg_ms = kern_ms / max(kern_launches, 1)
-    achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+    pairs_launch = npar * wl.W
+    achieved = fpp * pairs_launch / (avg_ms * 1e-3) / 1e12
+    tensor_ach = tpp * pairs_launch / (avg_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for("pair_overlap_kernel", wl.name),
-            "kernel": "pair_overlap_kernel", "kernel_ms": avg_ms, "flops_per_launch": flops_launch,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for("tc_pair_kernel", wl.name),
+            "kernel": "tc_pair_kernel", "kernel_ms": avg_ms, "flops_per_launch": fpp * pairs_launch,
+            "fp64_flops_per_pair": fpp,
             "peak_source": "FP64 ALU: 152 SM x 4 flop/clk x 2.07 GHz (derived from unit counts and the maximum "
-                           "clock; MEASURED_PEAKS.json carries no FP64 figure)"}
+                           "clock; MEASURED_PEAKS.json carries no FP64 figure)",
+            "tensor": {"achieved": tensor_ach, "peak": bf16, "unit": "TFLOP/s",
+                       "frac": tensor_ach / bf16 if bf16 else None, "bf16_flops_per_pair": tpp,
+                       "peak_source": f"bf16_tflops_sustained ({peaks['source']}; cuBLAS bf16 timed inside a long loop)"},
+            "fp64_alu_equivalent": {"flops_per_pair": alu_fpp,
+                                    "tflops": alu_fpp * pairs_launch / (avg_ms * 1e-3) / 1e12,
+                                    "note": "FP64 work the ALU congruence executes for the same result"}}
 
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
@@ -920,6 +1024,7 @@ def main():
             "e2e": e2e,
             "roofline": roof,
             "clocks": clk.summary(),
+            "fp64_alu_congruence": alu,
             "grad": grad,
             "batch": batch,
             "precision": precision,
@@ -928,9 +1033,17 @@ def main():
             "rdm": rdm,
             "vce": vce,
             "local_energy": energy,
-            "gpu_launches": args.steps * 5}
+            # per step: snapshot build (prepare, compaction, tensor-core records) and the
+            # overlap (walker prep, walker slices, pair kernel, reduction)
+            "gpu_launches": args.steps * 7}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, data)
+        def gpu_sample(Wc, Pc):
+            s2 = qcs.Snapshots(ctx, Qd[:Pc].contiguous(), bd[:Pc].contiguous())
+            o2, pp2 = qcs.overlap(ctx, s2, Pd[:Wc].contiguous(), per_pair=True)
+            torch.cuda.synchronize()
+            return o2.cpu().numpy(), pp2.cpu().numpy(), s2.parity().cpu().numpy()
+
+        line["cpu_baseline"] = cpu_baseline(wl, data, ov_timed, gpu_sample)
     add_dfma_context(line, ctx.fp64_fma_rate())
     if ws > 1:
         dist.barrier()

@@ -322,8 +322,9 @@ typedef struct {
 /* Overlaps of up to QCS_MAX_SYSTEMS systems with different active spaces, walker
  * and snapshot counts, with ONE launch of the pair kernel: a persistent grid
  * pulls (system, walker, snapshot-chunk) tiles from a device counter, costliest
- * systems first.  Each system's result equals that of qcs_overlap on it (same
- * per-tile arithmetic and reduction order).  opts (NULL = defaults) applies to
+ * systems first.  The launch runs the FP64 ALU pair kernel: each system's result
+ * equals that of qcs_overlap on it with QCS_FLAG_FP64_ALU (same per-tile arithmetic
+ * and reduction order), and that of the default path up to rounding.  opts (NULL = defaults) applies to
  * every system; opts->config = 0 takes each system's tuned configuration.
  * The call allocates nothing once the context workspace has grown to the
  * batch's size, so after one warm-up call it can be captured in a CUDA graph.
@@ -453,6 +454,14 @@ double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned
  * sums that form the two results and the snapshot row's re + im); elsewhere four
  * (8 flop).  parts: host array of 3 doubles.  Errors: QCS_ERR_ARG. */
 qcs_status qcs_overlap_flops_breakdown(int n, int ne, int nodes, unsigned flags, double *parts);
+
+/* Host only: the work per non-trivial pair of qcs_overlap when the congruence runs on
+ * tensor cores (QCS_FP64 at n = 16, or QCS_FLAG_FP64_TC): *fp64 receives the FP64 flops
+ * (the assembly of B^(s) from P and the Pfaffian eliminations, as in
+ * qcs_overlap_flops_breakdown's parts[2]), *tensor the BF16 tensor-core flops of the two
+ * sliced products (28 slice products of 32 x 32 x 32 each).  fp64, tensor: host doubles.
+ * Errors: QCS_ERR_ARG (sizes outside n <= 16, nodes out of range, null pointers). */
+qcs_status qcs_overlap_tc_work_per_pair(int n, int ne, int nodes, unsigned flags, double *fp64, double *tensor);
 
 /* Host only (no device work): the node plan that (n, ne, nodes, flags) selects.
  * *nev receives the number of Pfaffians evaluated per pair; wnode and gamma

@@ -750,6 +750,23 @@ extern "C" qcs_status qcs_overlap_flops_breakdown(int n, int ne, int nodes, unsi
     return QCS_OK;
 }
 
+extern "C" qcs_status qcs_overlap_tc_work_per_pair(int n, int ne, int nodes, unsigned flags, double *fp64,
+                                                   double *tensor) {
+    if (!fp64 || !tensor || n < 1 || !qcs_tc_supported(n) || ne < 2 || ne > n || (ne & 1)) return QCS_ERR_ARG;
+    qcs_node_plan plan;
+    qcs_status r = qcs_make_node_plan(n, ne, nodes, flags, &plan);
+    if (r != QCS_OK) return r;
+    double part[3];
+    overlap_flops_parts(n, ne, plan.nev, true, part);
+    // B^(s) from P: each occupied x occupied entry takes two real additions; the rest are
+    // copies and sign changes
+    *fp64 = part[2] + 2.0 * tri_count(ne);
+    // two sliced products per pair, 28 slice products each of a 32 x 32 x 32 BF16
+    // multiply-add (rows and contraction padded to 32)
+    *tensor = 2.0 * 28.0 * 2.0 * 32.0 * 32.0 * 32.0;
+    return QCS_OK;
+}
+
 extern "C" qcs_status qcs_node_plan_get(int n, int ne, int nodes, unsigned flags, int *nev, double *wnode,
                                         double *gamma) {
     if (!nev || !wnode || !gamma) return QCS_ERR_ARG;

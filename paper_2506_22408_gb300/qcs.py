@@ -41,7 +41,7 @@ EXPORTED = [
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
     "qcs_local_energy", "qcs_local_energy_flops_per_pair", "qcs_overlap_flops_breakdown",
-    "qcs_selftest_bounded_wait", "qcs_fp64_fma_rate",
+    "qcs_selftest_bounded_wait", "qcs_fp64_fma_rate", "qcs_overlap_tc_work_per_pair",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_workspace_bytes.restype = ctypes.c_size_t
         lib.qcs_selftest_bounded_wait.argtypes = [P, u32, P]
         lib.qcs_fp64_fma_rate.argtypes = [P, ctypes.POINTER(f64), P]
+        lib.qcs_overlap_tc_work_per_pair.argtypes = [i32, i32, i32, u32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
         lib.qcs_build_snapshots.argtypes = [P, i32, i64, P, P, ctypes.POINTER(P), P]
         lib.qcs_snapshots_free.argtypes = [P]
         lib.qcs_snapshots_parity.argtypes = [P, P, P]
@@ -393,6 +394,16 @@ def flops_breakdown(n: int, ne: int, nodes: int = 0, flags: int = 0) -> dict:
     if rc != QCS_OK:
         raise QCSError(rc, "qcs_overlap_flops_breakdown: sizes or nodes out of range")
     return {"T": out[0], "B": out[1], "pfaffian": out[2]}
+
+
+def tc_work_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> dict:
+    """Host-only: FP64 flops and BF16 tensor-core flops per non-trivial pair when the
+    congruence runs on tensor cores."""
+    f, t = ctypes.c_double(), ctypes.c_double()
+    rc = load().qcs_overlap_tc_work_per_pair(n, ne, nodes, flags, ctypes.byref(f), ctypes.byref(t))
+    if rc != QCS_OK:
+        raise QCSError(rc, "qcs_overlap_tc_work_per_pair: sizes or nodes out of range")
+    return {"fp64": f.value, "tensor": t.value}
 
 
 def grad_flops_per_pair(n: int, ne: int, nodes: int = 0, flags: int = 0) -> float:

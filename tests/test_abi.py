@@ -109,3 +109,18 @@ def test_host_only_size_checks():
     parts = (ctypes.c_double * 3)()
     assert lib.qcs_overlap_flops_breakdown(maxn + 1, 2, 0, 0, parts) == qcs.QCS_ERR_ARG
     assert lib.qcs_overlap_flops_breakdown(16, 8, 0, 0, None) == qcs.QCS_ERR_ARG
+
+
+def test_tensor_core_work_accounting_host_only():
+    """The tensor-core congruence's work per non-trivial pair: the FP64 part is the
+    Pfaffian eliminations of the ALU count plus two additions per occupied x occupied
+    entry of B^(s); the tensor part two sliced products of 28 slice products each."""
+    parts = qcs.flops_breakdown(16, 8)
+    w = qcs.tc_work_per_pair(16, 8)
+    assert w["fp64"] == parts["pfaffian"] + 2 * (8 * 7 // 2)
+    assert w["tensor"] == 2 * 28 * 2 * 32 ** 3
+    w_dft = qcs.tc_work_per_pair(16, 8, 0, qcs.QCS_FLAG_DFT_NODES)
+    assert w_dft["fp64"] == qcs.flops_breakdown(16, 8, 0, qcs.QCS_FLAG_DFT_NODES)["pfaffian"] + 56
+    import pytest
+    with pytest.raises(qcs.QCSError):
+        qcs.tc_work_per_pair(20, 10)  # n > 16 has no tensor-core congruence

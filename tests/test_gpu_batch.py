@@ -38,8 +38,9 @@ def test_batched_equals_per_system(ctx):
     torch.cuda.synchronize()
     assert ctx.sync_status() == 0
     for y, r in zip(systems, res):
-        single, _ = qcs.overlap(ctx, y["s"], y["walkers"])
-        assert torch.equal(r, single)  # same tiles, same reduction order
+        # the batched launch runs the FP64 ALU pair kernel: same tiles, same reduction order
+        single, _ = qcs.overlap(ctx, y["s"], y["walkers"], flags=qcs.QCS_FLAG_FP64_ALU)
+        assert torch.equal(r, single)
     y = systems[0]
     oo, _, sc, _ = orc.overlap(y["Phi"], y["Q"], y["b"], per_pair=True)
     assert np.all(np.abs(res[0].cpu().numpy() - oo) <= 1e-10 * sc.mean(axis=1))
