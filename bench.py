@@ -293,11 +293,12 @@ def run_batch(args, ctx, dev, barrier, ws):
     from paper_2506_22408_gb300 import qcs, synth
 
     rng = np.random.default_rng(7)
-    systems, Us, outs = [], [], []
+    systems, Us, outs, tuned = [], [], [], []
     for wl0 in synth.BATCH_SYSTEMS:
         wl = dataclasses.replace(wl0, W=max(1, int(round(wl0.W * args.batch_walker_scale))))
         d = wl.generate(seed=0)
-        ctx.autotune(wl.n, wl.ne)
+        # the batched launch runs the FP64 ALU pair kernel: tune that path for each system
+        tuned.append(ctx.autotune(wl.n, wl.ne, 0, qcs.QCS_FLAG_FP64_ALU, use_cache=args.tune_cache))
         s = qcs.Snapshots(ctx, torch.from_numpy(d["Q"]).to(dev), torch.from_numpy(d["b"]).to(dev))
         walkers = torch.from_numpy(d["Phi"]).to(dev)
         K = rng.standard_normal((wl.n, wl.n)) + 1j * rng.standard_normal((wl.n, wl.n))
@@ -338,10 +339,28 @@ def run_batch(args, ctx, dev, barrier, ws):
     barrier()
     t = e0.elapsed_time(e1) / 1e3
     t = max_over_ranks(t, ws)
+    # the pair kernel's own time per step (one batched call outside the graph, timed on its
+    # launch), and each system alone in the same kernel, for context
+    ctx.profile(True)
+    ctx.profile_read()
+    qcs.overlap_batched(ctx, arg, outs=outs)
+    torch.cuda.synchronize()
+    kms, _ = ctx.profile_read()
+    per_sys = []
+    for (wl, s, w) in systems:
+        qcs.overlap_batched(ctx, [(s, w)])
+        torch.cuda.synchronize()
+        ms1, _ = ctx.profile_read()
+        per_sys.append({"n": wl.n, "pairs_per_s_alone": wl.W * wl.P / (ms1 * 1e-3), "kernel_ms_alone": ms1})
+    ctx.profile(False)
+    assert ctx.sync_status() == 0
+    kach = flops_step / (kms * 1e-3) / 1e12
     return {"metric": "walker x snapshot overlap pairs/s, batched active spaces under a CUDA graph",
             "value": ws * pairs_step * args.batch_steps / t, "unit": "pairs/s",
             "ms_per_step": 1e3 * t / args.batch_steps, "graph_steps": args.batch_steps,
-            "config": {"systems": [{"n": wl.n, "ne": wl.ne, "walkers": wl.W, "snapshots": wl.P} for wl, _, _ in systems],
+            "config": {"systems": [{"n": wl.n, "ne": wl.ne, "walkers": wl.W, "snapshots": wl.P,
+                                    "tuned": qcs.decode_config(tc)} for (wl, _, _), tc in zip(systems, tuned)],
+                       "picked_by": "qcs_autotune (QCS_FLAG_FP64_ALU, staged search: node rounds, tile, warps per pair)",
                        "walker_scale": args.batch_walker_scale,
                        "pairs_per_step": pairs_step,
                        "step": "stand-in propagation (torch matmul) + one qcs_overlap_batched launch sequence"},
@@ -349,6 +368,11 @@ def run_batch(args, ctx, dev, barrier, ws):
                          "unit": "TFLOP/s", "frac": flops_step * args.batch_steps / t / 1e12 / FP64_PEAK_TFLOPS,
                          "kernel": "pair_overlap_kernel (batched)",
                          "timing": "whole graph step (propagation, walker prep, pair kernel, reductions)"},
+            "pair_kernel": {"kernel_ms_per_step": kms, "share_of_graph_step": kms / (1e3 * t / args.batch_steps),
+                            "roofline": {"bound": "alu", "achieved": kach, "peak": FP64_PEAK_TFLOPS,
+                                         "unit": "TFLOP/s", "frac": kach / FP64_PEAK_TFLOPS,
+                                         "timing": "one batched launch outside the graph, events on its stream"}},
+            "systems_alone": per_sys,
             "gpu_launches_per_step": 5 + 1 + 5}
 
 
@@ -439,7 +463,7 @@ def run_dft_plan(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
     from paper_2506_22408_gb300 import qcs
 
     flags = qcs.QCS_FLAG_DFT_NODES
-    ctx.autotune(wl.n, wl.ne, 0, flags, use_cache=True)
+    ctx.autotune(wl.n, wl.ne, 0, flags, use_cache=args.tune_cache)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -483,7 +507,7 @@ def run_alu_path(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
     from paper_2506_22408_gb300 import qcs
 
     flags = qcs.QCS_FLAG_FP64_ALU
-    tuned = ctx.autotune(wl.n, wl.ne, 0, flags, use_cache=True)
+    tuned = ctx.autotune(wl.n, wl.ne, 0, flags, use_cache=args.tune_cache)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -513,7 +537,7 @@ def run_alu_path(args, ctx, wl, Qd, bd, Pd, flush, barrier, ws, npar, steps=3):
     return {"metric": "walker x snapshot overlap pairs/s, congruence on the FP64 ALU", "value": ws * wl.W * wl.P * steps / t,
             "unit": "pairs/s", "steps": steps, "ms_per_step": 1e3 * t / steps,
             "nontrivial_pairs_per_s": ws * wl.W * npar * steps / t,
-            "kernel_config": {"node_matrices_per_warp_round": tuned},
+            "kernel_config": {**qcs.decode_config(tuned), "picked_by": "qcs_autotune (QCS_FLAG_FP64_ALU)"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": ach / FP64_PEAK_TFLOPS, "kernel": "pair_overlap_kernel", "kernel_ms": avg,
                          "flops_per_launch": fpp * npar * wl.W,
@@ -857,6 +881,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision workload")
     ap.add_argument("--no-dft-plan", action="store_true", help="skip the roots-of-unity node-plan comparison")
     ap.add_argument("--no-alu-path", action="store_true", help="skip the FP64 ALU congruence comparison")
+    ap.add_argument("--tune-cache", action="store_true",
+                    help="take the autotuner's choices from its cache file when present (default: tune in this run)")
     ap.add_argument("--no-rdm", action="store_true", help="skip the shadow RDM workload")
     ap.add_argument("--no-vce", action="store_true", help="skip the virtual-correlation-energy workload")
     ap.add_argument("--no-energy", action="store_true", help="skip the local-energy workload")
@@ -900,7 +926,7 @@ def main():
 
     data = wl.generate(seed=0)
     ctx = qcs.Context(local)
-    tuned = ctx.autotune(wl.n, wl.ne, use_cache=True)  # pair-kernel configuration for this GPU (cached)
+    tuned = ctx.autotune(wl.n, wl.ne, use_cache=args.tune_cache)  # kernel configuration for this GPU
     Qd = torch.from_numpy(data["Q"]).to(dev)
     bd = torch.from_numpy(data["b"]).to(dev)
     Pd = torch.from_numpy(data["Phi"]).to(dev)
@@ -1017,7 +1043,7 @@ def main():
             "config": {"workload": wl.name + " (Haar Q, uniform b, seed 0)", "n": wl.n, "ne": wl.ne,
                        "walkers": wl.W, "snapshots": wl.P, "parity_plus_snapshots": npar,
                        "nodes": f"Gauss plan: {len(qcs.node_plan(wl.n, wl.ne)[0])} Pfaffians per parity +1 pair",
-                       "kernel_config": {"node_matrices_per_warp_round": tuned, "picked_by": "qcs_autotune"},
+                       "kernel_config": {**qcs.decode_config(tuned), "picked_by": "qcs_autotune"},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "snapshot set (164 MB) larger than L2, and L2 flushed between timed steps"},
             "nontrivial_pairs_per_s": ws * npar * wl.W * args.steps / t_total,

@@ -120,8 +120,17 @@ typedef struct {
                       N > 0 = N roots of unity, n-ne+1 <= N <= QCS_MAX_NODES */
     unsigned flags;
     int config;    /* kernel configuration: 0 = the context's tuned choice for these sizes
-                      (qcs_autotune / qcs_set_config) or the built-in default;
-                      k >= 1 = k node matrices per warp round in the pair kernel */
+                      (qcs_autotune / qcs_set_config) or the built-in defaults; else the
+                      fields below, 0 in a field taking its default:
+                        bits 0-3   node matrices per warp round, 1..8 (so a plain k keeps
+                                   meaning k matrices per round)
+                        bits 4-7   FP64 ALU pair kernel: snapshots per warp in a tile (4)
+                        bits 8-9   FP64 ALU pair kernel, n > 16: 1 = one warp per pair,
+                                   2 = two warps per pair (2)
+                        bits 10-11 FP64 overlaps at n <= 16 without a path flag: 1 = congruence
+                                   on the FP64 ALU, 2 = on tensor cores (tensor cores at n = 16)
+                        bits 12-15 tensor-core pair kernel: sub-tiles of four snapshots per
+                                   tile (8) */
 } qcs_opts;
 
 /* ------------------------------------------------------------- context */
@@ -325,7 +334,8 @@ typedef struct {
  * systems first.  The launch runs the FP64 ALU pair kernel: each system's result
  * equals that of qcs_overlap on it with QCS_FLAG_FP64_ALU (same per-tile arithmetic
  * and reduction order), and that of the default path up to rounding.  opts (NULL = defaults) applies to
- * every system; opts->config = 0 takes each system's tuned configuration.
+ * every system; opts->config = 0 takes each system's tuned configuration (one tuned with
+ * QCS_FLAG_FP64_ALU added to the options first, the path this launch runs).
  * The call allocates nothing once the context workspace has grown to the
  * batch's size, so after one warm-up call it can be captured in a CUDA graph.
  * Errors: QCS_ERR_ARG, QCS_ERR_CUDA, QCS_ERR_UNSUPPORTED. */
@@ -391,11 +401,15 @@ qcs_status qcs_overlap_noalloc(int n, int ne, int64_t P, const double *d_Q, cons
 
 /* ------------------------------------------------------------ tuning */
 
-/* Autotuner of the pair kernel (no counterpart in the paper).  Times every
- * configuration (node matrices per warp round, 1..min(nodes evaluated, 8)) of
- * qcs_overlap for (n, ne, nodes, flags) on a synthetic sample on the context's
- * device (allocates and frees its own sample; synchronises), records the
- * fastest in the context and returns it in *config (may be NULL).
+/* Autotuner of the overlap kernels (no counterpart in the paper).  Times configurations
+ * (qcs_opts.config) of qcs_overlap for (n, ne, nodes, flags) on a synthetic sample on the
+ * context's device in stages, keeping the best so far: the congruence path (FP64 ALU or
+ * tensor cores, n <= 16 and no path flag), then node matrices per warp round
+ * (1..min(nodes evaluated, 8)), then the tile (ALU: 2/4/8 snapshots per warp; tensor
+ * cores: 2/4/8/15 sub-tiles of four snapshots), then for n > 16 one or two warps per
+ * pair.  Records the fastest in the context (calls with config = 0 take it, and so does
+ * qcs_overlap_batched for its systems, which keeps the ALU path) and returns it in
+ * *config (may be NULL).  Allocates and frees its own sample; synchronises.
  * Errors: QCS_ERR_ARG, QCS_ERR_CUDA. */
 qcs_status qcs_autotune(qcs_ctx *ctx, int n, int ne, int nodes, unsigned flags, int *config);
 

@@ -336,13 +336,23 @@ struct OverlapWork {
     unsigned char *walk_rec;   // tensor-core congruence: walker slice records
     int *mode;                 // FP64 ALU path: per-walker form of the occupied rows (walker prep)
     int nchunks, nparts;
+    int config, chunk;         // resolved kernel configuration, ALU snapshots per warp in a tile
     bool split, tc;
 };
+
+// The configuration of an overlap call: opts->config, else the context's tuned entry for
+// these sizes and options, else 0 (built-in defaults).
+int resolve_config(qcs_ctx *ctx, int n, int ne, const qcs_opts &o) {
+    if (o.config > 0) return o.config;
+    auto it = ctx->tuned.find(std::make_tuple(n, ne, o.nodes, o.flags));
+    return it != ctx->tuned.end() ? it->second : 0;
+}
 
 // The FP64 overlap runs its congruence on tensor cores (qcs_tcpair.cu) by default at
 // n = 16, on request (QCS_FLAG_FP64_TC) for any n <= 16, and on the FP64 ALU
 // otherwise (QCS_FLAG_FP64_ALU, n > 16, or every node of every snapshot).
-qcs_status choose_tc(qcs_ctx *ctx, int n, const qcs_opts &o, bool *tc) {
+// A configured path (qcs_config.path, from the autotuner) applies when no flag names one.
+qcs_status choose_tc(qcs_ctx *ctx, int n, const qcs_opts &o, int config, bool *tc) {
     *tc = false;
     if (o.precision != QCS_FP64) return QCS_OK;
     if ((o.flags & QCS_FLAG_FP64_TC) && (o.flags & QCS_FLAG_FP64_ALU))
@@ -355,7 +365,9 @@ qcs_status choose_tc(qcs_ctx *ctx, int n, const qcs_opts &o, bool *tc) {
         *tc = true;
         return QCS_OK;
     }
-    *tc = possible && !(o.flags & QCS_FLAG_FP64_ALU) && n == 16;
+    if (o.flags & QCS_FLAG_FP64_ALU) return QCS_OK;
+    const int path = qcs_decode_config(config).path;
+    *tc = possible && (path == 2 || (path == 0 && n == 16));
     return QCS_OK;
 }
 
@@ -378,15 +390,19 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     if (qcs_make_node_plan(n, ne, o.nodes, o.flags, plan) != QCS_OK)
         return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
     const bool split = o.precision == QCS_TF32X3;
+    // the tuned table belongs to the FP64 pair kernels
+    wk->config = split ? o.config : resolve_config(ctx, n, ne, o);
+    const qcs_config cfg = qcs_decode_config(wk->config);
     bool tc = false;
-    c = choose_tc(ctx, n, o, &tc);
+    c = choose_tc(ctx, n, o, wk->config, &tc);
     if (c != QCS_OK) return c;
     wk->split = split;
     wk->tc = tc;
-    // partial sums: FP64 ALU path one per (walker, 16-snapshot chunk, warp); split path one
-    // per (walker, tile of snapshots); tensor-core path one per (walker, tile)
-    const int span = split ? qcs_split_snaps_per_tile() : tc ? qcs_tc_snaps_per_tile()
-                                                             : kChunk * qcs_pair_warps_per_block();
+    wk->chunk = cfg.chunk > 0 ? cfg.chunk : kChunk;
+    // partial sums: FP64 ALU path one per (walker, tile, warp); split path one per
+    // (walker, tile of snapshots); tensor-core path one per (walker, tile)
+    const int span = split ? qcs_split_snaps_per_tile() : tc ? qcs_tc_snaps_per_tile(cfg.subs)
+                                                             : wk->chunk * qcs_pair_warps_per_block();
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
     wk->nparts = (split || tc) ? wk->nchunks : wk->nchunks * qcs_pair_warps_per_block();
@@ -436,7 +452,7 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
     L.ne = ne;
     L.W = W;
     L.P = s->P;
-    L.chunk = kChunk;
+    L.chunk = wk.chunk;
     L.nchunks = wk.nchunks;
     L.Ut = wk.Ut;
     L.pref = wk.pref;
@@ -446,11 +462,7 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
     L.per_pair = (cd *)d_per_pair;
     L.plan = plan;
     L.counter = wk.counter;
-    L.config = opts ? opts->config : 0;
-    if (L.config == 0 && !wk.split) {  // the tuned table belongs to the FP64 pair kernel
-        auto it = ctx->tuned.find(std::make_tuple(s->n, ne, opts ? opts->nodes : 0, opts ? opts->flags : 0u));
-        if (it != ctx->tuned.end()) L.config = it->second;
-    }
+    L.config = wk.config;
     if (wk.split) {
         r = qcs_split_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
         if (r != QCS_OK) return r;
@@ -496,17 +508,19 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         L.ne = y.ne;
         L.W = y.W;
         L.P = s->P;
-        L.chunk = kChunk;
-        L.nchunks = (int)((s->P + kChunk * wpb - 1) / (kChunk * wpb));
+        // the batched launch runs the FP64 ALU pair kernel: a configuration tuned for that
+        // path first, then one tuned for these options
+        qcs_opts oa = o;
+        oa.flags |= QCS_FLAG_FP64_ALU;
+        L.config = o.config > 0 ? o.config : resolve_config(ctx, s->n, y.ne, oa);
+        if (L.config == 0) L.config = resolve_config(ctx, s->n, y.ne, o);
+        const qcs_config cfg = qcs_decode_config(L.config);
+        L.chunk = cfg.chunk > 0 ? cfg.chunk : kChunk;
+        L.nchunks = (int)((s->P + L.chunk * wpb - 1) / (L.chunk * wpb));
         if (L.nchunks < 1) L.nchunks = 1;
         L.s = s;
         L.per_pair = nullptr;
         L.counter = nullptr;
-        L.config = o.config;
-        if (L.config == 0) {
-            auto it = ctx->tuned.find(std::make_tuple(s->n, y.ne, o.nodes, o.flags));
-            if (it != ctx->tuned.end()) L.config = it->second;
-        }
         off[i][0] = total;
         total += align16(sizeof(cd) * (size_t)y.W * s->n * s->n);
         off[i][1] = total;

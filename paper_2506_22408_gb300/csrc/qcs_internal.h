@@ -111,6 +111,29 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
 qcs_status qcs_launch_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const cd *L, const cd *walkers,
                                  const cd *overlap, const cd *grad, double sqrt_dt, cd *xbar, cudaStream_t st);
 
+// A kernel configuration (qcs_opts.config, the autotuner's result), field by field; 0 in a
+// field takes the built-in default.  Encoded as nb | chunk << 4 | warps << 8 | path << 10 |
+// subs << 12, so that a plain k (1..8) keeps its meaning of k node matrices per round.
+struct qcs_config {
+    int nb;     // node matrices per warp round (pair kernels), 1..8
+    int chunk;  // FP64 ALU pair kernel: snapshots per warp in a tile, 1..15 (default 4)
+    int warps;  // FP64 ALU pair kernel, n > 16: 1 = one warp per pair, 2 = two (default)
+    int path;   // FP64 overlaps, n <= 16: 1 = congruence on the FP64 ALU, 2 = on tensor cores
+    int subs;   // tensor-core pair kernel: sub-tiles of four snapshots per tile, 1..15 (default 8)
+};
+inline qcs_config qcs_decode_config(int c) {
+    qcs_config r;
+    r.nb = c & 15;
+    r.chunk = (c >> 4) & 15;
+    r.warps = (c >> 8) & 3;
+    r.path = (c >> 10) & 3;
+    r.subs = (c >> 12) & 15;
+    return r;
+}
+inline int qcs_encode_config(const qcs_config &r) {
+    return (r.nb & 15) | ((r.chunk & 15) << 4) | ((r.warps & 3) << 8) | ((r.path & 3) << 10) | ((r.subs & 15) << 12);
+}
+
 struct qcs_pair_launch {
     int n, ne;
     int64_t W, P;
@@ -122,7 +145,7 @@ struct qcs_pair_launch {
     cd *partial;     // W x nchunks x warps-per-block
     cd *per_pair;    // W x P or null
     qcs_node_plan plan;
-    int config;      // node matrices per warp round; 0 = heuristic
+    int config;      // qcs_config encoding; 0 = heuristic
     unsigned long long *counter;  // device tile counter (reset by the launcher)
 };
 
@@ -136,7 +159,7 @@ qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, 
 // FP64-accurate congruence on tensor cores (qcs_tcpair.cu)
 bool qcs_tc_supported(int n);      // n <= 16
 size_t qcs_tc_walker_bytes(int64_t W);
-int qcs_tc_snaps_per_tile();      // parity +1 snapshots per tile (one partial sum per walker and tile)
+int qcs_tc_snaps_per_tile(int subs);  // parity +1 snapshots per tile (subs sub-tiles; 0 = default)
 qcs_status qcs_tc_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
 qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned char *walk_rec, cudaStream_t st);
 qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launch *Ls, unsigned long long *counter,

@@ -379,8 +379,9 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.nchunks = L.nchunks;
     A.W = L.W;
     A.P = L.P;
+    const qcs_config cfg = qcs_decode_config(L.config);
     A.reg = L.n == 16;
-    A.grp = L.n > 16;
+    A.grp = L.n > 16 && cfg.warps != 1;  // n > 16: two warps per pair unless one is configured
     const int n = A.n, m = A.m, T = tri_count(m);
     const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
@@ -390,8 +391,8 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     // path) or two blocks fit on an SM.
     int NB = 1;
     const int nbmax = A.grp ? kMaxNBG : kMaxNB;
-    if (L.config > 0) {
-        NB = L.config < A.nev ? L.config : A.nev;
+    if (cfg.nb > 0) {
+        NB = cfg.nb < A.nev ? cfg.nb : A.nev;
         if (NB > nbmax) NB = nbmax;
         while (NB > 1 && (size_t)A.tab_bytes + A.ut_bytes + (size_t)wpb * pair_warp_layout(A, NB) > ctx->smem_optin)
             --NB;

@@ -411,7 +411,8 @@ qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, 
             break;
         }
     }
-    if (L.config > 0) NB = L.config < A.nev ? (L.config < kMaxNB ? L.config : kMaxNB) : A.nev;
+    const int cnb = qcs_decode_config(L.config).nb;
+    if (cnb > 0) NB = cnb < A.nev ? (cnb < kMaxNB ? cnb : kMaxNB) : A.nev;
     A.NB = NB;
     A.warp_bytes = (int)split_warp_layout(A, NB);
     size_t region = (size_t)kWalkersPerTile * A.warp_bytes;

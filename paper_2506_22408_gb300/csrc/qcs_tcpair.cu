@@ -19,7 +19,8 @@
 // formed once per walker, the snapshot's once per snapshot; Z is re-sliced per pair
 // between the two products.  The FP64 pipe is left with the Pfaffians alone.
 //
-// Tiles: one walker and 32 consecutive parity +1 snapshots (eight sub-tiles of four);
+// Tiles: one walker and 4 subs consecutive parity +1 snapshots (subs sub-tiles of four,
+// 8 by default, tuned by qcs_autotune);
 // a block of four warps owns a tile, warp i the pair of snapshot i of each sub-tile.
 //  1. bulk copies bring the four snapshots' H slices (the A operand, M = 128 rows)
 //     and, once per tile, the walker's M slices (the B operand, N = 32) into shared
@@ -46,8 +47,7 @@ using namespace qcs_oz;
 namespace {
 
 constexpr int kSnapsPerSub = 4;                               // M = 128 rows of the first product
-constexpr int kSubPerTile = 8;                                // snapshots per tile: 32
-constexpr int kSnapsPerTile = kSnapsPerSub * kSubPerTile;
+constexpr int kSubPerTile = 8;                                // default sub-tiles per tile: 32 snapshots
 constexpr uint32_t kTmemCols = 256;                           // 7 levels x 32 columns, power of two
 constexpr uint32_t kWaitIter = 1u << 26;                      // bounded mbarrier waits
 constexpr int kSnapSlab = kSnapsPerSub * kSliceBytes;         // one slice of 4 snapshots: 8 KB
@@ -159,7 +159,8 @@ __global__ void tc_snapshot_prep_kernel(int n, int64_t nslots, const cd *__restr
 struct TcArgs {
     int n, ne, m, d, nev, NB;
     int64_t W, P;
-    int nchunks;      // tiles per walker (chunks of kSnapsPerTile list positions)
+    int nchunks;      // tiles per walker (chunks of 4 subs list positions)
+    int subs;         // sub-tiles of kSnapsPerSub snapshots per tile
     int ws_bytes;     // Pfaffian workspace per warp
     int ws_in_operands;  // 1: the workspaces are quarters of the operand region
     int off_P, off_N, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // B^(s) at offset 0
@@ -368,14 +369,14 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
         if (t >= ntiles) break;
         const int ch = (int)(t / A.W);  // chunk-major: a chunk's records stay in L2 over the walkers
         const int64_t w = t - (int64_t)ch * A.W;
-        const int64_t p0 = (int64_t)ch * kSnapsPerTile;
+        const int64_t p0 = (int64_t)ch * (kSnapsPerSub * A.subs);
         if (p0 >= L) {
             if (tid == 0) A.partial[w * A.nchunks + ch] = cmk(0.0, 0.0);
             continue;
         }
         const cd prefw = A.pref[w];
         cd acc = cmk(0.0, 0.0);
-        for (int s = 0; s < kSubPerTile; ++s) {
+        for (int s = 0; s < A.subs; ++s) {
             const int64_t pb = p0 + (int64_t)s * kSnapsPerSub;
             if (pb >= L) break;
             if (tid == 0) {
@@ -492,7 +493,7 @@ size_t tc_warp_layout(TcArgs &A, int NB) {
 
 size_t qcs_tc_walker_bytes(int64_t W) { return (size_t)(W > 0 ? W : 1) * kWalkRecBytes; }
 
-int qcs_tc_snaps_per_tile() { return kSnapsPerTile; }
+int qcs_tc_snaps_per_tile(int subs) { return kSnapsPerSub * (subs > 0 ? subs : kSubPerTile); }
 
 bool qcs_tc_supported(int n) { return n >= 2 && 2 * n <= kRowsPer; }
 
@@ -548,8 +549,10 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     // fit there (large m), the workspaces get their own shared memory
     auto fits = [&](int nb) { return 4 * tc_warp_layout(A, nb) <= (size_t)kOperandBytes; };
     int NB = 1;
-    if (L.config > 0) {
-        NB = L.config < A.nev ? L.config : A.nev;
+    const qcs_config cfg = qcs_decode_config(L.config);
+    A.subs = cfg.subs > 0 ? cfg.subs : kSubPerTile;
+    if (cfg.nb > 0) {
+        NB = cfg.nb < A.nev ? cfg.nb : A.nev;
         if (NB > kMaxNB) NB = kMaxNB;
         while (NB > 1 && !fits(NB)) --NB;
     } else {

@@ -1,11 +1,18 @@
-// qcs_tune.cu -- autotuner of the pair kernel's configuration.
+// qcs_tune.cu -- autotuner of the overlap kernels' configuration.
 //
-// The pair kernel evaluates nb node matrices per warp round.  More matrices
-// per round share the per-step pivot and reciprocal work and fill more lanes,
-// but need more shared memory per warp, which lowers the number of resident
-// warps that hide latency.  The best trade-off depends on n, ne and the node
-// count, so it is measured: every nb in 1..min(nodes evaluated, 8) is timed on
-// a synthetic sample and the fastest is recorded in the context.
+// The choices (qcs_config) trade shared memory, resident warps and per-step work:
+//  - the congruence path at n <= 16: on the FP64 ALU or on tensor cores;
+//  - node matrices per warp round: more share the per-step pivot and reciprocal work
+//    and fill more lanes, but need more shared memory per warp;
+//  - the tile: snapshots per warp in an FP64 ALU tile (longer tiles amortise the walker's
+//    staging, shorter ones balance the tail), sub-tiles per tensor-core tile (the walker's
+//    slice record is loaded once per tile);
+//  - warps per pair for n > 16 on the ALU kernel: one warp (more pairs in flight) or two
+//    (half the shared memory per warp, more blocks per SM).
+// The best choice depends on n, ne, the node plan and the GPU, so it is measured: a staged
+// search (the path with its defaults, then node rounds, then the tile, then warps per pair,
+// each stage keeping the best so far) times each configuration of qcs_overlap on a synthetic
+// sample, and the fastest is recorded in the context.
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -73,30 +80,97 @@ extern "C" qcs_status qcs_autotune(qcs_ctx *ctx, int n, int ne, int nodes, unsig
     rc = qcs_build_snapshots(ctx, n, P, dQ, db, &s, st);
     if (rc != QCS_OK) goto done;
     {
-        const int maxnb = plan.nev < 8 ? plan.nev : 8;
-        for (int cfg = 1; cfg <= maxnb; ++cfg) {
+        // minimum over three timed calls after a warm-up; a configuration the kernels
+        // cannot run (shared memory) counts as infinitely slow
+        auto time_cfg = [&](int cfg, float *ms_out) -> qcs_status {
             qcs_opts o = {QCS_FP64, nodes, flags, cfg};
-            rc = qcs_overlap(ctx, s, ne, W, dPhi, dOv, nullptr, &o, st);  // warm-up
-            if (rc != QCS_OK) goto done;
-            float ms_min = 1e30f;
+            *ms_out = 1e30f;
+            qcs_status r = qcs_overlap(ctx, s, ne, W, dPhi, dOv, nullptr, &o, st);
+            if (r == QCS_ERR_UNSUPPORTED) return QCS_OK;
+            if (r != QCS_OK) return r;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = qcs_overlap(ctx, s, ne, W, dPhi, dOv, nullptr, &o, st);
+                r = qcs_overlap(ctx, s, ne, W, dPhi, dOv, nullptr, &o, st);
                 cudaEventRecord(e1, st);
-                if (rc != QCS_OK) goto done;
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = qcs_fail(ctx, QCS_ERR_CUDA, "autotune: event");
-                    goto done;
-                }
+                if (r != QCS_OK) return r;
+                if (cudaEventSynchronize(e1) != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "autotune: event");
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < ms_min) ms_min = ms;
+                if (ms < *ms_out) *ms_out = ms;
             }
-            if (ms_min < best_ms) {
-                best_ms = ms_min;
-                best = cfg;
+            return QCS_OK;
+        };
+        auto try_cfg = [&](const qcs_config &c) -> qcs_status {
+            float ms = 0.f;
+            qcs_status r = time_cfg(qcs_encode_config(c), &ms);
+            if (r == QCS_OK && ms < best_ms) {
+                best_ms = ms;
+                best = qcs_encode_config(c);
             }
+            return r;
+        };
+        const bool path_free = !(flags & (QCS_FLAG_FP64_ALU | QCS_FLAG_FP64_TC | QCS_FLAG_ALL_NODES)) && n <= 16;
+        const bool tc_forced = (flags & QCS_FLAG_FP64_TC) != 0;
+        const int maxnb = plan.nev < 8 ? plan.nev : 8;
+        qcs_config cand[2];
+        int ncand = 0;
+        // stage 1: the path with its defaults
+        if (path_free) {
+            cand[ncand++] = {0, 0, 0, 1, 0};
+            cand[ncand++] = {0, 0, 0, 2, 0};
+        } else {
+            cand[ncand++] = {0, 0, 0, 0, 0};
         }
+        qcs_config bc = cand[0];
+        for (int i = 0; i < ncand; ++i) {
+            const float before = best_ms;
+            rc = try_cfg(cand[i]);
+            if (rc != QCS_OK) goto done;
+            if (best_ms < before) bc = cand[i];
+        }
+        const bool on_tc = tc_forced || bc.path == 2;
+        // stage 2: node matrices per round
+        for (int nb = 1; nb <= maxnb; ++nb) {
+            qcs_config c = bc;
+            c.nb = nb;
+            const float before = best_ms;
+            rc = try_cfg(c);
+            if (rc != QCS_OK) goto done;
+            if (best_ms < before) bc = c;
+        }
+        // stage 3: the tile
+        if (on_tc) {
+            for (int subs : {2, 4, 8, 15}) {
+                qcs_config c = bc;
+                c.subs = subs;
+                const float before = best_ms;
+                rc = try_cfg(c);
+                if (rc != QCS_OK) goto done;
+                if (best_ms < before) bc = c;
+            }
+        } else {
+            for (int chunk : {2, 4, 8}) {
+                qcs_config c = bc;
+                c.chunk = chunk;
+                const float before = best_ms;
+                rc = try_cfg(c);
+                if (rc != QCS_OK) goto done;
+                if (best_ms < before) bc = c;
+            }
+            // stage 4: warps per pair (n > 16)
+            if (n > 16)
+                for (int warps : {1, 2}) {
+                    qcs_config c = bc;
+                    c.warps = warps;
+                    const float before = best_ms;
+                    rc = try_cfg(c);
+                    if (rc != QCS_OK) goto done;
+                    if (best_ms < before) bc = c;
+                }
+        }
+        best = qcs_encode_config(bc);
+        // 0 would clear the entry: name the default tile explicitly instead
+        if (best == 0) best = qcs_encode_config(on_tc ? qcs_config{0, 0, 0, 0, 8} : qcs_config{0, 4, 0, 0, 0});
     }
     ctx->tuned[std::make_tuple(n, ne, nodes, flags)] = best;
     if (config) *config = best;

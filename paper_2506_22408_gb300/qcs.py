@@ -65,6 +65,21 @@ class _Opts(ctypes.Structure):
                 ("config", ctypes.c_int)]
 
 
+def decode_config(config: int) -> dict:
+    """The fields of a kernel configuration (qcs_opts.config); 0 in a field = default."""
+    c = int(config)
+    return {"node_matrices_per_round": c & 15, "alu_snapshots_per_warp": (c >> 4) & 15,
+            "alu_warps_per_pair": (c >> 8) & 3, "path": {0: "default", 1: "fp64_alu", 2: "tensor_cores"}[(c >> 10) & 3],
+            "tc_subtiles_per_tile": (c >> 12) & 15}
+
+
+def encode_config(node_matrices_per_round=0, alu_snapshots_per_warp=0, alu_warps_per_pair=0, path=0,
+                  tc_subtiles_per_tile=0) -> int:
+    """qcs_opts.config from its fields (path: 0 default, 1 FP64 ALU, 2 tensor cores)."""
+    return ((node_matrices_per_round & 15) | (alu_snapshots_per_warp & 15) << 4 | (alu_warps_per_pair & 3) << 8
+            | (path & 3) << 10 | (tc_subtiles_per_tile & 15) << 12)
+
+
 def library_path() -> str:
     return _build.LIB
 

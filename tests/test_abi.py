@@ -124,3 +124,16 @@ def test_tensor_core_work_accounting_host_only():
     import pytest
     with pytest.raises(qcs.QCSError):
         qcs.tc_work_per_pair(20, 10)  # n > 16 has no tensor-core congruence
+
+
+def test_config_encoding_round_trip():
+    """qcs_opts.config fields (host-side helpers): a plain k is k node matrices per round,
+    and every field survives encode -> decode."""
+    assert qcs.decode_config(3) == {"node_matrices_per_round": 3, "alu_snapshots_per_warp": 0,
+                                    "alu_warps_per_pair": 0, "path": "default", "tc_subtiles_per_tile": 0}
+    c = qcs.encode_config(node_matrices_per_round=5, alu_snapshots_per_warp=8, alu_warps_per_pair=1, path=2,
+                          tc_subtiles_per_tile=15)
+    assert c == 5 | 8 << 4 | 1 << 8 | 2 << 10 | 15 << 12
+    f = qcs.decode_config(c)
+    assert (f["node_matrices_per_round"], f["alu_snapshots_per_warp"], f["alu_warps_per_pair"], f["path"],
+            f["tc_subtiles_per_tile"]) == (5, 8, 1, "tensor_cores", 15)

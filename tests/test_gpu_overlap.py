@@ -295,6 +295,8 @@ def test_every_kernel_configuration_agrees(ctx):
         check_pairs(pp, opp, sc, par)
         check_walkers(ov, oo, sc)
     best = ctx.autotune(n, ne, save=False)
-    assert 1 <= best <= 5
+    fields = qcs.decode_config(best)
+    assert best > 0 and 0 <= fields["node_matrices_per_round"] <= 3 and fields["path"] in ("fp64_alu", "tensor_cores")
     ov, pp, par, st = run_gpu(ctx, data)
     check_pairs(pp, opp, sc, par)
+    ctx.set_config(n, ne, 0)  # back to the built-in defaults for the other tests
