@@ -51,10 +51,11 @@
  *   rejected: measurement outcomes are even operators, so the shadow
  *   estimator of an odd-particle overlap is identically zero.
  * - Scratch memory: a context owns one device workspace that grows (with
- *   cudaMalloc, synchronously) when a call needs more than it holds.  Call
- *   each entry point once with the largest sizes before capturing it in a
- *   CUDA graph so that no allocation happens during capture.  Calls on the
- *   same context must not overlap in time on different streams.
+ *   cudaMalloc, synchronously, or with the caller's allocator set by
+ *   qcs_set_allocator) when a call needs more than it holds.  Call each entry
+ *   point once with the largest sizes before capturing it in a CUDA graph so
+ *   that no allocation happens during capture.  Calls on the same context must
+ *   not overlap in time on different streams.
  */
 #ifndef QCS_H
 #define QCS_H
@@ -151,6 +152,26 @@ qcs_status qcs_sync_status(qcs_ctx *ctx, void *stream);
 
 /* Bytes of device workspace currently held by the context. */
 size_t qcs_workspace_bytes(const qcs_ctx *ctx);
+
+/* Device allocator callbacks (the ownership convention of the boundary: the library's
+ * scratch may come from the caller's allocator, e.g. PyTorch's caching allocator).
+ *   alloc_fn(bytes, stream, user) returns a device pointer of at least `bytes` on the
+ *     context's device, usable in stream order on `stream` (the stream of the call that
+ *     needs it), or NULL on failure (the call then returns QCS_ERR_CUDA);
+ *   free_fn(ptr, bytes, stream, user) releases it; the library calls it only after the
+ *     device has finished all work that used the memory, with stream = NULL.
+ * Once set, the context's workspace, the buffers of snapshot sets built on the context
+ * (which remember the allocator they were built with), the tensor-core slice records and
+ * the autotuner's sample come from alloc_fn; the context's 4-byte status word and its
+ * pinned host mirror, made at qcs_create, do not.  Setting an allocator releases the
+ * current workspace (after synchronising the device) so that later growth uses the new
+ * one; alloc_fn = free_fn = NULL restores cudaMalloc / cudaFree.  The callbacks run on the
+ * calling host thread, inside the library call that needs memory; a call allocates only
+ * when the workspace must grow, so after one call with the largest sizes none does.
+ * Errors: QCS_ERR_ARG (ctx NULL, or only one of the two functions given), QCS_ERR_CUDA. */
+typedef void *(*qcs_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*qcs_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+qcs_status qcs_set_allocator(qcs_ctx *ctx, qcs_alloc_fn alloc_fn, qcs_free_fn free_fn, void *user);
 
 /* Self-test of the device time-out path (failure detection without a fault).
  * Every device wait of the library (the split-precision kernel's mbarrier waits

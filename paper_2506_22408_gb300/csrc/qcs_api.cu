@@ -36,20 +36,53 @@ qcs_status qcs_set_smem(qcs_ctx *ctx, const void *func, size_t bytes) {
     return QCS_OK;
 }
 
-qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out) {
+qcs_status qcs_dev_alloc(const qcs_allocator &a, void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (a.alloc) {
+        *p = a.alloc(bytes, (void *)st, a.user);
+        return *p ? QCS_OK : QCS_ERR_CUDA;
+    }
+    return cudaMalloc(p, bytes) == cudaSuccess ? QCS_OK : QCS_ERR_CUDA;
+}
+
+void qcs_dev_free(const qcs_allocator &a, void *p, size_t bytes) {
+    if (!p) return;
+    if (a.free) a.free(p, bytes, nullptr, a.user);
+    else cudaFree(p);
+}
+
+qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out, cudaStream_t st) {
     bytes = align16(bytes < 16 ? 16 : bytes);
     if (bytes > ctx->work_bytes) {
         if (ctx->work) {
             cudaDeviceSynchronize();
-            cudaFree(ctx->work);
+            qcs_dev_free(ctx->alloc, ctx->work, ctx->work_bytes);
             ctx->work = nullptr;
             ctx->work_bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&ctx->work, bytes);
-        if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+        if (qcs_dev_alloc(ctx->alloc, &ctx->work, bytes, st) != QCS_OK)
+            return qcs_fail(ctx, QCS_ERR_CUDA, ctx->alloc.alloc ? "workspace: the allocator callback returned NULL"
+                                                                 : "workspace: cudaMalloc failed");
         ctx->work_bytes = bytes;
     }
     *out = ctx->work;
+    return QCS_OK;
+}
+
+extern "C" qcs_status qcs_set_allocator(qcs_ctx *ctx, qcs_alloc_fn alloc_fn, qcs_free_fn free_fn, void *user) {
+    if (!ctx) return QCS_ERR_ARG;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return qcs_fail(ctx, QCS_ERR_ARG, "qcs_set_allocator: give both functions or neither");
+    DeviceGuard g(ctx->device);
+    if (ctx->work) {  // later growth comes from the new allocator
+        if (cudaDeviceSynchronize() != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "qcs_set_allocator: synchronise");
+        qcs_dev_free(ctx->alloc, ctx->work, ctx->work_bytes);
+        ctx->work = nullptr;
+        ctx->work_bytes = 0;
+    }
+    ctx->alloc.alloc = alloc_fn;
+    ctx->alloc.free = free_fn;
+    ctx->alloc.user = user;
     return QCS_OK;
 }
 
@@ -197,7 +230,7 @@ extern "C" qcs_status qcs_destroy(qcs_ctx *ctx) {
     if (!ctx) return QCS_ERR_ARG;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    if (ctx->work) cudaFree(ctx->work);
+    qcs_dev_free(ctx->alloc, ctx->work, ctx->work_bytes);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     for (auto &ev : ctx->prof_events) ctx->prof_pool.push_back(ev);
@@ -262,15 +295,17 @@ extern "C" qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const 
     s->n = n;
     s->P = P;
     s->device = ctx->device;
+    s->alloc = ctx->alloc;
     const int64_t Pa = P > 0 ? P : 1;
-    cudaError_t e = cudaMalloc(&s->Qt, sizeof(cd) * (size_t)Pa * 2 * n * n);
-    if (e == cudaSuccess) e = cudaMalloc(&s->parity, (size_t)Pa);
-    if (e == cudaSuccess) e = cudaMalloc(&s->idx, sizeof(int) * (size_t)Pa);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_count, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&s->gth, (size_t)Pa * 2 * n);
-    if (e != cudaSuccess) {
+    const cudaStream_t cs = (cudaStream_t)stream;
+    qcs_status ae = qcs_dev_alloc(s->alloc, (void **)&s->Qt, sizeof(cd) * (size_t)Pa * 2 * n * n, cs);
+    if (ae == QCS_OK) ae = qcs_dev_alloc(s->alloc, (void **)&s->parity, (size_t)Pa, cs);
+    if (ae == QCS_OK) ae = qcs_dev_alloc(s->alloc, (void **)&s->idx, sizeof(int) * (size_t)Pa, cs);
+    if (ae == QCS_OK) ae = qcs_dev_alloc(s->alloc, (void **)&s->d_count, 2 * sizeof(int), cs);
+    if (ae == QCS_OK) ae = qcs_dev_alloc(s->alloc, (void **)&s->gth, (size_t)Pa * 2 * n, cs);
+    if (ae != QCS_OK) {
         qcs_snapshots_free(s);
-        return qcs_fail(ctx, QCS_ERR_CUDA, std::string("snapshot cudaMalloc: ") + cudaGetErrorString(e));
+        return qcs_fail(ctx, QCS_ERR_CUDA, "snapshot set: device allocation failed");
     }
     qcs_status st = qcs_launch_snapshot_build(ctx, s, d_Q, d_b, (cudaStream_t)stream);
     // the tensor-core congruence is the default FP64 path at n = 16: its per-snapshot
@@ -300,14 +335,16 @@ extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
     if (!s) return QCS_ERR_ARG;
     DeviceGuard g(s->device);
     cudaDeviceSynchronize();
-    if (s->Qt) cudaFree(s->Qt);
-    if (s->parity) cudaFree(s->parity);
-    if (s->idx) cudaFree(s->idx);
-    if (s->d_count) cudaFree(s->d_count);
-    if (s->gth) cudaFree(s->gth);
-    if (s->split_hi) cudaFree(s->split_hi);
-    if (s->split_lo) cudaFree(s->split_lo);
-    if (s->tc_rec) cudaFree(s->tc_rec);
+    const int n = s->n;
+    const size_t Pa = (size_t)(s->P > 0 ? s->P : 1);
+    qcs_dev_free(s->alloc, s->Qt, sizeof(cd) * Pa * 2 * n * n);
+    qcs_dev_free(s->alloc, s->parity, Pa);
+    qcs_dev_free(s->alloc, s->idx, sizeof(int) * Pa);
+    qcs_dev_free(s->alloc, s->d_count, 2 * sizeof(int));
+    qcs_dev_free(s->alloc, s->gth, Pa * 2 * n);
+    qcs_dev_free(s->alloc, s->split_hi, s->split_bytes);
+    qcs_dev_free(s->alloc, s->split_lo, s->split_bytes);
+    qcs_dev_free(s->alloc, s->tc_rec, s->tc_bytes);
     delete s;
     return QCS_OK;
 }
@@ -413,7 +450,7 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     size_t b_rec = tc ? align16(qcs_tc_walker_bytes(W)) : 0;
     size_t b_mode = (split || tc) ? 0 : align16(sizeof(int) * (size_t)(W > 0 ? W : 1));
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab + b_rec + b_mode, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_part + 2 * b_slab + b_rec + b_mode, &base, st);
     if (ws != QCS_OK) return ws;
     char *pb = (char *)base;
     wk->counter = (unsigned long long *)pb;
@@ -531,7 +568,7 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         total += align16(sizeof(int) * (size_t)(y.W > 0 ? y.W : 1));
     }
     void *base = nullptr;
-    qcs_status r = qcs_workspace(ctx, total, &base);
+    qcs_status r = qcs_workspace(ctx, total, &base, st);
     if (r != QCS_OK) return r;
     char *pb = (char *)base;
     for (int i = 0; i < nsys; ++i) {
@@ -592,7 +629,7 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     size_t b_w = align16(sizeof(cd) * (size_t)W * ((size_t)ne * ne + 1));
     size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * (1 + (size_t)n * n));
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w, &base, st);
     if (ws != QCS_OK) return ws;
     unsigned long long *gcounter = (unsigned long long *)base;
     char *pb = (char *)base + 16;

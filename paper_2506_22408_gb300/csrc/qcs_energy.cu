@@ -823,7 +823,7 @@ extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int
     const size_t b_lam = align16(sizeof(cd) * (size_t)(s->P > 0 ? s->P : 1) * tri_count(n2));
     const size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * 3);
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_kop + b_k2 + b_part + b_kg + b_lam, &base);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_kop + b_k2 + b_part + b_kg + b_lam, &base, st);
     if (ws != QCS_OK) return ws;
     char *pb = (char *)base;
     unsigned long long *counter = (unsigned long long *)pb;

@@ -11,6 +11,16 @@
 
 #include "qcs_common.cuh"
 
+// The device allocator of a context or snapshot set: the caller's callbacks, or (both
+// null) cudaMalloc / cudaFree.
+struct qcs_allocator {
+    qcs_alloc_fn alloc = nullptr;
+    qcs_free_fn free = nullptr;
+    void *user = nullptr;
+};
+qcs_status qcs_dev_alloc(const qcs_allocator &a, void **p, size_t bytes, cudaStream_t st);
+void qcs_dev_free(const qcs_allocator &a, void *p, size_t bytes);
+
 struct qcs_ctx {
     int device = 0;
     int num_sms = 0;
@@ -20,6 +30,7 @@ struct qcs_ctx {
     unsigned *h_status = nullptr;  // pinned host mirror
     void *work = nullptr;          // device workspace
     size_t work_bytes = 0;
+    qcs_allocator alloc;           // where the workspace and snapshot buffers come from
     std::string last_error;
     std::map<std::tuple<int, int, int, unsigned>, int> tuned;  // (n, ne, nodes, flags) -> config
     bool profiling = false;
@@ -45,6 +56,8 @@ struct qcs_snapshots {
     void *split_lo = nullptr;
     void *tc_rec = nullptr;   // tensor-core congruence: BF16 slices of H_p = N^T J N for the parity +1
                               // list, four snapshots per record (57,856 bytes), built once
+    size_t split_bytes = 0, tc_bytes = 0;  // sizes of the lazily built buffers (for the allocator)
+    qcs_allocator alloc;      // the allocator the set's buffers came from
 };
 
 // Makes `dev` current for the scope of the guard, then restores the previous device.
@@ -63,7 +76,7 @@ struct DeviceGuard {
 qcs_status qcs_fail(qcs_ctx *ctx, qcs_status code, const std::string &msg);
 qcs_status qcs_check_launch(qcs_ctx *ctx, const char *what);
 qcs_status qcs_set_smem(qcs_ctx *ctx, const void *func, size_t bytes);
-qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out);
+qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out, cudaStream_t st = nullptr);
 
 // Launchers implemented in the kernel translation units
 qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const double *d_Q, const uint8_t *d_b,

@@ -267,7 +267,7 @@ extern "C" qcs_status qcs_shadow_rdm(qcs_ctx *ctx, const qcs_snapshots *s, const
     size_t b_part = align16(sizeof(double) * (size_t)nrow * npair);
     size_t b_s2 = d_gam4 ? align16(sizeof(double) * (size_t)nks * npair * npair) : 0;
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, b_gu + b_part + b_s2, &base);
+    qcs_status ws = qcs_workspace(ctx, b_gu + b_part + b_s2, &base, st);
     if (ws != QCS_OK) return ws;
     double *Gu = (double *)base;
     double *part = (double *)((char *)base + b_gu);

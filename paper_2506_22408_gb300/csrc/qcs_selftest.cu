@@ -64,7 +64,7 @@ extern "C" qcs_status qcs_fp64_fma_rate(qcs_ctx *ctx, double *tflops, void *stre
     cudaStream_t st = (cudaStream_t)stream;
     const int blocks = ctx->num_sms;
     void *buf = nullptr;
-    qcs_status r = qcs_workspace(ctx, sizeof(double) * (size_t)blocks * kRateThreads, &buf);
+    qcs_status r = qcs_workspace(ctx, sizeof(double) * (size_t)blocks * kRateThreads, &buf, st);
     if (r != QCS_OK) return r;
     double *out = (double *)buf;
     const int iters = 1 << 16;  // about 0.1 s per launch at 1 TFLOP/s on 152 SMs

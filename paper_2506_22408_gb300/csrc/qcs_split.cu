@@ -357,9 +357,10 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
 qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st) {
     if (s->split_hi) return QCS_OK;
     const size_t bytes = (size_t)(s->P > 0 ? s->P : 1) * kSlabBytes;
-    cudaError_t e = cudaMalloc(&s->split_hi, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&s->split_lo, bytes);
-    if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, "split snapshot slabs: cudaMalloc");
+    qcs_status e = qcs_dev_alloc(s->alloc, &s->split_hi, bytes, st);
+    if (e == QCS_OK) e = qcs_dev_alloc(s->alloc, &s->split_lo, bytes, st);
+    s->split_bytes = bytes;
+    if (e != QCS_OK) return qcs_fail(ctx, QCS_ERR_CUDA, "split snapshot slabs: device allocation failed");
     if (s->P > 0) {
         int64_t tot = s->P * kRows * kK;
         int64_t blocks = (tot + 255) / 256;

@@ -502,11 +502,11 @@ qcs_status qcs_tc_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t
     if (!qcs_tc_supported(s->n)) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tensor-core congruence needs n <= 16");
     const int64_t nsub = (s->P + kSnapsPerSub - 1) / kSnapsPerSub;
     const size_t bytes = (size_t)(nsub > 0 ? nsub : 1) * kSnapRecBytes;
-    cudaError_t e = cudaMalloc(&s->tc_rec, bytes);
-    if (e != cudaSuccess) {
+    if (qcs_dev_alloc(s->alloc, &s->tc_rec, bytes, st) != QCS_OK) {
         s->tc_rec = nullptr;
-        return qcs_fail(ctx, QCS_ERR_CUDA, "tensor-core snapshot records: cudaMalloc");
+        return qcs_fail(ctx, QCS_ERR_CUDA, "tensor-core snapshot records: device allocation failed");
     }
+    s->tc_bytes = bytes;
     if (nsub == 0) return QCS_OK;
     const int wpb = 4;
     const size_t smem = (size_t)wpb * kRowsPer * kRowsPer * sizeof(double);

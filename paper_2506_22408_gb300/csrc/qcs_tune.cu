@@ -63,11 +63,14 @@ extern "C" qcs_status qcs_autotune(qcs_ctx *ctx, int n, int ne, int nodes, unsig
     qcs_status rc = QCS_OK;
     int best = 1;
     float best_ms = 1e30f;
-    cudaError_t e = cudaMalloc(&dQ, sizeof(double) * hQ.size());
-    if (e == cudaSuccess) e = cudaMalloc(&dPhi, sizeof(double) * hPhi.size());
-    if (e == cudaSuccess) e = cudaMalloc(&dOv, sizeof(double) * 2 * W);
-    if (e == cudaSuccess) e = cudaMalloc(&db, hb.size());
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {  // the sample comes from the context's allocator
+        const bool got = qcs_dev_alloc(ctx->alloc, (void **)&dQ, sizeof(double) * hQ.size(), st) == QCS_OK &&
+                         qcs_dev_alloc(ctx->alloc, (void **)&dPhi, sizeof(double) * hPhi.size(), st) == QCS_OK &&
+                         qcs_dev_alloc(ctx->alloc, (void **)&dOv, sizeof(double) * 2 * W, st) == QCS_OK &&
+                         qcs_dev_alloc(ctx->alloc, (void **)&db, hb.size(), st) == QCS_OK;
+        if (!got) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemcpy(dQ, hQ.data(), sizeof(double) * hQ.size(), cudaMemcpyHostToDevice);
@@ -176,10 +179,11 @@ extern "C" qcs_status qcs_autotune(qcs_ctx *ctx, int n, int ne, int nodes, unsig
     if (config) *config = best;
 done:
     if (s) qcs_snapshots_free(s);
-    if (dQ) cudaFree(dQ);
-    if (dPhi) cudaFree(dPhi);
-    if (dOv) cudaFree(dOv);
-    if (db) cudaFree(db);
+    if (st) cudaStreamSynchronize(st);
+    qcs_dev_free(ctx->alloc, dQ, sizeof(double) * hQ.size());
+    qcs_dev_free(ctx->alloc, dPhi, sizeof(double) * hPhi.size());
+    qcs_dev_free(ctx->alloc, dOv, sizeof(double) * 2 * W);
+    qcs_dev_free(ctx->alloc, db, hb.size());
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);

@@ -41,11 +41,15 @@ EXPORTED = [
     "qcs_snapshots_signed_perm_count", "qcs_overlap_flops_per_pair_signed_perm",
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
     "qcs_local_energy", "qcs_local_energy_flops_per_pair", "qcs_overlap_flops_breakdown",
-    "qcs_selftest_bounded_wait", "qcs_fp64_fma_rate", "qcs_overlap_tc_work_per_pair",
+    "qcs_selftest_bounded_wait", "qcs_fp64_fma_rate", "qcs_overlap_tc_work_per_pair", "qcs_set_allocator",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
 NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class QCSError(RuntimeError):
@@ -107,6 +111,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_selftest_bounded_wait.argtypes = [P, u32, P]
         lib.qcs_fp64_fma_rate.argtypes = [P, ctypes.POINTER(f64), P]
         lib.qcs_overlap_tc_work_per_pair.argtypes = [i32, i32, i32, u32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+        lib.qcs_set_allocator.argtypes = [P, _ALLOC_FN, _FREE_FN, P]
         lib.qcs_build_snapshots.argtypes = [P, i32, i64, P, P, ctypes.POINTER(P), P]
         lib.qcs_snapshots_free.argtypes = [P]
         lib.qcs_snapshots_parity.argtypes = [P, P, P]
@@ -221,6 +226,34 @@ class Context:
         """Run the device time-out self-test; returns the status bits it raised."""
         self.check(self.lib.qcs_selftest_bounded_wait(self.h, max_iter, _stream()))
         return self.sync_status()
+
+    def use_torch_allocator(self):
+        """Back the context's device memory (workspace, snapshot sets built afterwards,
+        tensor-core records, the autotuner's sample) with PyTorch's caching allocator
+        (qcs_set_allocator).  alloc_calls / free_calls count the callbacks."""
+        dev = self.device
+        self.alloc_calls = 0
+        self.free_calls = 0
+
+        def _alloc(nbytes, stream, user):
+            try:
+                self.alloc_calls += 1
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=int(stream or 0))
+            except Exception:  # the library reports QCS_ERR_CUDA for a NULL result
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            self.free_calls += 1
+            torch.cuda.caching_allocator_delete(ptr)
+
+        cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+        self.check(self.lib.qcs_set_allocator(self.h, cbs[0], cbs[1], None))
+        self._allocator_callbacks = cbs  # kept alive as long as the context (and its snapshot sets)
+
+    def use_cuda_malloc(self):
+        """Back later device memory with cudaMalloc again (snapshot sets already built keep
+        the allocator they were built with, and the callbacks stay alive for them)."""
+        self.check(self.lib.qcs_set_allocator(self.h, _ALLOC_FN(), _FREE_FN(), None))
 
     def fp64_fma_rate(self) -> float:
         """Sustained FP64 FMA rate of this device in TFLOP/s (about 2.5 s of chains)."""
