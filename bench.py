@@ -446,7 +446,7 @@ def run_precision(args, ctx, dev, barrier, ws):
                               "pair_rel_max": float(rel_pair.max().item()),
                               "pair_rel_median": float(rel_pair.median().item()),
                               "walker_rel_max": float(rel_walker.max().item()),
-                              "normalisation": "mean |o_p| of the walker on the FP64 path"},
+                              "normalisation": "mean |o_p| of the walker on the FP64 path (per pair over s_p: cpu_baseline.parity.split_tf32x3)"},
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": ach / FP64_PEAK_TFLOPS, "kernel": "split_pair_kernel", "kernel_ms": avg,
                          "flops_counted": "FP64 Pfaffian work only (congruence on tensor cores)",
@@ -763,8 +763,9 @@ def cpu_baseline(wl, data, gpu_overlap, gpu_sample, target_s=10.0):
     the sample (|o_gpu - o_oracle| / s_p, s_p the magnitude of the pair's terms before
     they cancel, and exact zeros for parity -1), the sample's walker means, and three
     whole walkers over all snapshots against the overlaps of the timed steps (relative
-    to |O|).  gpu_sample(Wc, Pc) returns the GPU's per-pair and walker outputs on the
-    sample; gpu_overlap holds the timed steps' walker overlaps."""
+    to |O|).  gpu_sample(Wc, Pc) returns the GPU's walker and per-pair outputs on the
+    sample, the parity flags and a dict of per-pair outputs of other paths (checked pair
+    by pair against s_p as well); gpu_overlap holds the timed steps' walker overlaps."""
     import numpy as np
 
     import oracle.oracle as orc
@@ -786,7 +787,7 @@ def cpu_baseline(wl, data, gpu_overlap, gpu_sample, target_s=10.0):
     orc.overlap(data["Phi"][:Wc], data["Q"][:P1], data["b"][:P1], threads=1)
     dt1 = time.perf_counter() - t0
     # parity: the sample pair by pair, its walker means, and three whole walkers
-    gov, gpp, gpar = gpu_sample(Wc, Pc2)
+    gov, gpp, gpar, other_paths = gpu_sample(Wc, Pc2)
     ok = gpar == 1
     pair_err = np.abs(gpp[:, ok] - opp[:, ok]) / sc[:, ok]
     sample_rel = np.abs(gov - oo) / np.abs(oo)
@@ -804,6 +805,13 @@ def cpu_baseline(wl, data, gpu_overlap, gpu_sample, target_s=10.0):
               "tolerance": "pairs 1e-10 s_p, walkers 1e-10 relative",
               "within_tolerance": bool(pair_err.max() <= 1e-10 and sample_rel.max() <= 1e-10
                                        and full_rel.max() <= 1e-10 and np.all(gpp[:, ~ok] == 0))}
+    # the same sample through the FP64 ALU congruence and the split precision (bound 2e-5 s_p)
+    for name, opp_path in other_paths.items():
+        e = np.abs(opp_path[:, ok] - opp[:, ok]) / sc[:, ok]
+        parity[name] = {"pair_err_over_scale_max": float(e.max()),
+                        "pair_err_over_scale_median": float(np.median(e)),
+                        "parity_minus_pairs_exactly_zero": bool(np.all(opp_path[:, ~ok] == 0)),
+                        "bound": 2e-5 if name.startswith("split") else 1e-10}
     return {"value": Wc * Pc2 / dt, "unit": "pairs/s", "cores": int(used), "kind": "oracle",
             "sample": f"{Wc} walkers x {Pc2} snapshots of the same workload (first rows), "
                       f"{dt:.1f} s, FP64, 2n+1 roots-of-unity nodes, OpenMP over pairs",
@@ -1066,8 +1074,15 @@ def main():
         def gpu_sample(Wc, Pc):
             s2 = qcs.Snapshots(ctx, Qd[:Pc].contiguous(), bd[:Pc].contiguous())
             o2, pp2 = qcs.overlap(ctx, s2, Pd[:Wc].contiguous(), per_pair=True)
+            others = {}
+            if wl.n == 16:  # the other two congruence paths on the same sample
+                others["fp64_alu"] = qcs.overlap(ctx, s2, Pd[:Wc].contiguous(), per_pair=True,
+                                                 flags=qcs.QCS_FLAG_FP64_ALU)[1]
+                others["split_tf32x3"] = qcs.overlap(ctx, s2, Pd[:Wc].contiguous(), per_pair=True,
+                                                     precision=qcs.QCS_TF32X3)[1]
             torch.cuda.synchronize()
-            return o2.cpu().numpy(), pp2.cpu().numpy(), s2.parity().cpu().numpy()
+            return (o2.cpu().numpy(), pp2.cpu().numpy(), s2.parity().cpu().numpy(),
+                    {k: v.cpu().numpy() for k, v in others.items()})
 
         line["cpu_baseline"] = cpu_baseline(wl, data, ov_timed, gpu_sample)
     add_dfma_context(line, ctx.fp64_fma_rate())

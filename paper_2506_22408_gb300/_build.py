@@ -37,24 +37,37 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+# Build variants: the release library, and a debug build whose kernels check their
+# shared-memory, tile and queue indices (QCS_BOUNDS: a violation raises
+# QCS_ERR_BOUNDS in the status word and skips the access).
+VARIANTS = {None: [], "bounds": ["-DQCS_BOUNDS"]}
+
+
+def lib_path(variant=None) -> str:
+    return LIB if variant is None else os.path.join(BUILD, f"libqcs_{variant}.so")
+
+
+def stale(variant=None) -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    if not force and not stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=None, variant=None) -> str:
+    lib = lib_path(variant)
+    if not force and not stale(variant):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                    "--expt-relaxed-constexpr"] + list(extra or [])
+                    "--expt-relaxed-constexpr"] + VARIANTS[variant] + list(extra or [])
     objs = []
+    suffix = "" if variant is None else f".{variant}"
 
     def comp(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", f"{suffix}.o"))
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -65,13 +78,13 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(comp, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

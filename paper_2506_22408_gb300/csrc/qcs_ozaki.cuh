@@ -14,8 +14,8 @@
 // the rounding error of an FP64 dot product of the same length (Ozaki, Ogita, Oishi
 // and Rump's error-free splitting of matrix products, with integer-valued slices).
 //
-// The level sums are read back as FP32 integers and combined exactly on the integer
-// pipe into one 64-bit fixed-point value z = sum_{L=2..7} acc_L 2^{8(7-L)} +
+// The level sums are read back as FP32 integers, converted exactly (one F2I each) and
+// combined exactly in integer arithmetic into one 64-bit fixed-point value z = sum_{L=2..7} acc_L 2^{8(7-L)} +
 // floor(acc_8 / 2^8), worth z 2^{e+f-56}; |z| < 2^62.  Nothing in this file issues
 // an FP64 instruction except the out-of-range branch of fixed_to_f64.
 #pragma once
@@ -38,24 +38,31 @@ __host__ __device__ __forceinline__ uint32_t kmajor16(int row, int k) {
     return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// BF16 bit pattern of a signed integer |v| <= 255 (exact): the upper half of the FP32
-// bit pattern of v, formed as 1.5 * 2^23 + v minus 1.5 * 2^23 (exact for |v| < 2^22).
-__device__ __forceinline__ uint32_t bf16_of_small_int(int v) {
-    const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
-    return __float_as_uint(f) >> 16;
+// Sign factors of the slices of one entry: s = +-1 and -s 2^23.
+struct SliceSign {
+    float s, m;
+};
+__device__ __forceinline__ SliceSign slice_sign(bool neg) {
+    return neg ? SliceSign{-1.0f, 8388608.0f} : SliceSign{1.0f, -8388608.0f};
 }
 
-// Two BF16 patterns in one 32-bit word (lo = first element in memory).
-__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
-    const float flo = __int_as_float(0x4B400000 + lo) - 12582912.0f;
-    const float fhi = __int_as_float(0x4B400000 + hi) - 12582912.0f;
-    return __byte_perm(__float_as_uint(flo), __float_as_uint(fhi), 0x7632);
+// Slice i (1..7) of the fixed-point magnitude u < 2^56 with sign s, as an FP32: byte
+// 7 - i of u is placed under the exponent of 2^23 (bit pattern 0x4B0000bb, the value
+// 2^23 + byte) by one byte permutation, and s (2^23 + byte) - s 2^23 = s byte is exact.
+// With i a compile-time constant the word and byte selection fold away.
+__device__ __forceinline__ float slice_f32(uint64_t u, int i, SliceSign g) {
+    const int byte = 7 - i;
+    const uint32_t w = byte >= 4 ? (uint32_t)(u >> 32) : (uint32_t)u;
+    const uint32_t bits = __byte_perm(w, 0x4B000000u, (uint32_t)(byte & 3) | 0x7440u);
+    return fmaf(__uint_as_float(bits), g.s, g.m);
 }
 
-// Slice i (1..7) of the fixed-point magnitude u < 2^56 with sign s (true = negative).
-__device__ __forceinline__ int slice_of(uint64_t u, int i, bool s) {
-    const int a = (int)((u >> (56 - 8 * i)) & 255u);
-    return s ? -a : a;
+// Two FP32 values that BF16 holds exactly (integers of magnitude <= 255) as one BF16
+// pair, lo first in memory (the lower half of the word).
+__device__ __forceinline__ uint32_t bf16x2_of(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // Exponent e with |x| < 2^e for a finite nonzero x (the binary exponent of |x| plus one),
@@ -76,17 +83,6 @@ __device__ __forceinline__ uint64_t fixed_of(double x, int e) {
     return sh <= -64 ? 0ull : m >> (-sh);
 }
 
-// Exact integer value of an FP32 that holds an integer of magnitude below 2^24 (the
-// level sums are bounded by 7 * 32 * 255^2 < 2^24, so the exponent field is <= 150).
-__device__ __forceinline__ long long int_of_f32(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const int ex = (int)((b >> 23) & 0xffu);
-    if (ex < 127) return 0ll;  // zero (a level sum is an integer: |f| < 1 means f = 0)
-    const uint32_t m = (b & 0x7fffffu) | 0x800000u;  // |f| = m 2^{ex-150}
-    const long long v = (long long)(m >> (150 - (ex < 150 ? ex : 150)));
-    return (b >> 31) ? -v : v;
-}
-
 // |z| 2^sh as an unsigned fixed-point magnitude (shift left or right; the caller keeps
 // the result below 2^56).
 __device__ __forceinline__ uint64_t rescale_mag(long long z, int sh) {
@@ -96,11 +92,20 @@ __device__ __forceinline__ uint64_t rescale_mag(long long z, int sh) {
 }
 
 // z = sum_{L=2..7} acc[L-2] 2^{8(7-L)} + floor(acc[6] / 2^8) for the seven level sums
-// acc[0..6] (levels 2..8) of one output entry.
+// acc[0..6] (levels 2..8) of one output entry.  Each sum is an integer of magnitude
+// below 2^24, so one round-to-nearest conversion gives it exactly; levels 2 and 3
+// only touch the upper word ((2^8 acc_2 + acc_3) 2^32, |2^8 acc_2 + acc_3| < 2^30),
+// the others enter by widening multiply-adds.
 __device__ __forceinline__ long long combine_levels(const float (&acc)[kLevels]) {
-    long long z = int_of_f32(acc[6]) >> 8;
+    int x[kLevels];
 #pragma unroll
-    for (int L = 7; L >= 2; --L) z += int_of_f32(acc[L - 2]) * (1ll << (8 * (7 - L)));
+    for (int L = 0; L < kLevels; ++L) x[L] = __float2int_rn(acc[L]);
+    long long z = (long long)(x[0] * 256 + x[1]) * 4294967296ll;
+    z += (long long)x[2] * 16777216ll;
+    z += (long long)x[3] * 65536ll;
+    z += (long long)x[4] * 256ll;
+    z += (long long)x[5];
+    z += (long long)(x[6] >> 8);  // arithmetic shift: the floor of acc_8 / 2^8
     return z;
 }
 
@@ -119,14 +124,13 @@ __device__ __forceinline__ double fixed_to_f64(long long z, int E) {
     const unsigned long long u = z < 0 ? (unsigned long long)(-z) : (unsigned long long)z;
     const int lz = __clzll((long long)u);
     const unsigned long long nrm = u << lz;  // top bit set
-    unsigned long long mant = (nrm >> 11) + ((nrm >> 10) & 1ull);
-    int ex = 63 - lz + E;
-    if (mant >> 53) {
-        mant >>= 1;
-        ++ex;
-    }
+    // 53 significant bits, rounded on the first dropped bit.  Added to the exponent
+    // field (ex + 1022), the leading bit 2^52 of mant raises it to ex + 1023; after a
+    // rounding carry mant is 2^53, which gives ex + 1024 with a zero fraction: 2^(ex+1).
+    const unsigned long long mant = (nrm >> 11) + ((nrm >> 10) & 1ull);
+    const int ex = 63 - lz + E;
     if (ex < -1020 || ex > 1020) return ldexp((double)z, E);
-    return __longlong_as_double((long long)(sg | ((unsigned long long)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+    return __longlong_as_double((long long)(sg | (((unsigned long long)(ex + 1022) << 52) + mant)));
 }
 
 // Write the seven slices of a 32-entry row (fixed-point magnitudes u[k], signs in the
@@ -134,6 +138,9 @@ __device__ __forceinline__ double fixed_to_f64(long long z, int E) {
 // slab_stride bytes, the row is `row` of its operand.  Four 16-byte stores per slice.
 __device__ __forceinline__ void store_row_slices(unsigned char *base, uint32_t slab_stride, int row,
                                                  const uint64_t (&u)[kRowsPer], uint32_t neg) {
+    SliceSign g[kRowsPer];
+#pragma unroll
+    for (int k = 0; k < kRowsPer; ++k) g[k] = slice_sign((neg >> k) & 1u);
 #pragma unroll
     for (int i = 1; i <= kSlices; ++i) {
         unsigned char *slab = base + (size_t)(i - 1) * slab_stride;
@@ -144,7 +151,7 @@ __device__ __forceinline__ void store_row_slices(unsigned char *base, uint32_t s
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int k = 8 * kb + 2 * t;
-                wp[t] = pack_bf16x2(slice_of(u[k], i, (neg >> k) & 1u), slice_of(u[k + 1], i, (neg >> (k + 1)) & 1u));
+                wp[t] = bf16x2_of(slice_f32(u[k], i, g[k]), slice_f32(u[k + 1], i, g[k + 1]));
             }
             *reinterpret_cast<uint4 *>(slab + kmajor16(row, 8 * kb)) = w;
         }

@@ -275,22 +275,22 @@ __device__ __forceinline__ int slice_zt(uint32_t tlane, int gk, int eb_lane, uns
         long long z[8];
         read_levels8(tlane, cb, z);
         uint64_t u[8];
-        uint32_t neg = 0u;
+        SliceSign g[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int t = z[c] != 0 ? gk + bitlen64(z[c]) : kNoRow;
             const int G = __reduce_max_sync(QCS_FULL, t);
             if (8 * cb + c == lane) Gl = G;
             u[c] = (z[c] == 0 || G == kNoRow) ? 0ull : rescale_mag(z[c], 56 + gk - G);
-            neg |= (z[c] < 0 ? 1u : 0u) << c;
+            g[c] = slice_sign(z[c] < 0);
         }
 #pragma unroll
         for (int i = 1; i <= kSlices; ++i) {
             uint4 w;
-            w.x = pack_bf16x2(slice_of(u[0], i, neg & 1u), slice_of(u[1], i, (neg >> 1) & 1u));
-            w.y = pack_bf16x2(slice_of(u[2], i, (neg >> 2) & 1u), slice_of(u[3], i, (neg >> 3) & 1u));
-            w.z = pack_bf16x2(slice_of(u[4], i, (neg >> 4) & 1u), slice_of(u[5], i, (neg >> 5) & 1u));
-            w.w = pack_bf16x2(slice_of(u[6], i, (neg >> 6) & 1u), slice_of(u[7], i, (neg >> 7) & 1u));
+            w.x = bf16x2_of(slice_f32(u[0], i, g[0]), slice_f32(u[1], i, g[1]));
+            w.y = bf16x2_of(slice_f32(u[2], i, g[2]), slice_f32(u[3], i, g[3]));
+            w.z = bf16x2_of(slice_f32(u[4], i, g[4]), slice_f32(u[5], i, g[5]));
+            w.w = bf16x2_of(slice_f32(u[6], i, g[6]), slice_f32(u[7], i, g[7]));
             *reinterpret_cast<uint4 *>(Abase + (size_t)(i - 1) * kSnapSlab + mnmajor16(row0 + 8 * cb, lane)) = w;
         }
     }

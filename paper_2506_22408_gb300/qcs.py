@@ -85,7 +85,13 @@ def encode_config(node_matrices_per_round=0, alu_snapshots_per_warp=0, alu_warps
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: libqcs.so in the source tree, or what the
+    environment variable QCS_LIBRARY names ("bounds" for the bounds-checked debug build
+    libqcs_bounds.so, built in-tree on first use; otherwise a path to a libqcs build)."""
+    sel = os.environ.get("QCS_LIBRARY", "")
+    if sel == "bounds":
+        return _build.lib_path("bounds")
+    return sel or _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -94,9 +100,10 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing and _build.stale():
-            _build.build()
+        path = library_path()
+        sel = os.environ.get("QCS_LIBRARY", "")
+        if build_if_missing and sel in ("", "bounds") and _build.stale(sel or None):
+            _build.build(variant=sel or None)
         if not os.path.exists(path):
             raise RuntimeError(f"libqcs.so not found at {path}; run __graft_entry__.build()")
         lib = ctypes.CDLL(path)
