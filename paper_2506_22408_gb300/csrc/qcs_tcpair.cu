@@ -25,13 +25,14 @@
 //  1. bulk copies bring the four snapshots' H slices (the A operand, M = 128 rows)
 //     and, once per tile, the walker's M slices (the B operand, N = 32) into shared
 //     memory;
-//  2. 56 tcgen05.mma kind::f16 (28 slice products, K = 32 as two K = 16 steps) form
-//     Z_i = H_i M^T, level L in tensor-memory columns 32(L-2) .. 32(L-2)+31;
+//  2. 14 tcgen05.mma kind::f16 (the 28 slice products, one N = 32 (8 - i) instruction
+//     per A slice i and K = 16 step) form Z_i = H_i M^T, level L in tensor-memory
+//     columns 32(L-2) .. 32(L-2)+31;
 //  3. each warp reads its 32 lanes (row k of Z_i), combines the levels into fixed
 //     point, takes the row scale of each row b of Z_i^T by a warp max-reduction and
 //     writes the seven slices straight from the lanes as the next A operand, laid out
 //     MN-major (lane k owns column k of Z_i^T);
-//  4. 56 more MMAs form P_i = M Z_i (lane b of warp i, column a: P_i[a][b]); each warp
+//  4. 14 more MMAs form P_i = M Z_i (lane b of warp i, column a: P_i[a][b]); each warp
 //     converts its lanes to FP64, keeps the upper triangle of P_i, assembles B^(s) and
 //     runs the node Pfaffians of the FP64 path (qcs_pair.cuh).
 // Every wait is bounded: a time-out raises QCS_ERR_TIMEOUT, drains and frees the
@@ -179,26 +180,25 @@ struct TcArgs {
     cd gamma[QCS_MAX_NODES];
 };
 
-// The MMAs of levels Lfirst..Llast of one sliced product: level L = i + j (i the A
-// slice, j the B slice) into columns 32 (L - Lfirst); A slabs kSnapSlab apart (M = 128),
-// B slabs kSliceBytes apart (N = 32); the A operand K-major (H slices) or MN-major
-// (slices of Z^T).
-__device__ __forceinline__ void issue_levels(uint32_t tbase, const unsigned char *A, const unsigned char *B, int Lfirst,
-                                             int Llast, bool a_mn_major) {
-    const uint32_t id = idesc_bf16(kSnapsPerSub * kRowsPer, kRowsPer) | (a_mn_major ? (1u << 15) : 0u);
-#pragma unroll 1
-    for (int L = Lfirst; L <= Llast; ++L) {
-        uint32_t acc = 0u;
-        for (int i = 1; i <= (L - 1 < kSlices ? L - 1 : kSlices); ++i) {
-            const int j = L - i;
-            if (j > kSlices) continue;
+// The MMAs of one sliced product, levels 2..8: per A slice i one instruction pair
+// (K = 32 as two K = 16 steps, 2 core matrices = 256 bytes apart) against the B slices
+// j = 1 .. 8 - i taken as one operand of N = 32 (8 - i) rows (the B slabs are
+// contiguous, so slab j continues the row groups of slab j - 1), with D at column
+// 32 (i - 1): the columns of slice j land in 32 (i + j - 2), the accumulator of level
+// i + j.  Slice 1 spans all seven levels and starts them (no accumulate on its first
+// step).  A slabs kSnapSlab apart (M = 128), K-major (H slices) or MN-major (slices of
+// Z^T).
+__device__ __forceinline__ void issue_products(uint32_t tbase, const unsigned char *A, const unsigned char *B,
+                                               bool a_mn_major) {
+    const uint32_t tr = a_mn_major ? (1u << 15) : 0u;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {  // K = 32: two K = 16 steps, 2 core matrices (256 bytes) apart
-                const uint64_t ad = desc_kmajor(A + (size_t)(i - 1) * kSnapSlab + 256 * ks, 128, 512);
-                const uint64_t bd = desc_kmajor(B + (size_t)(j - 1) * kSliceBytes + 256 * ks, 128, 512);
-                mma_f16(tbase + (uint32_t)(32 * (L - Lfirst)), ad, bd, id, acc);
-                acc = 1u;
-            }
+    for (int i = 1; i <= kSlices; ++i) {
+        const uint32_t id = idesc_bf16(kSnapsPerSub * kRowsPer, kRowsPer * (kSlices + 1 - i)) | tr;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ad = desc_kmajor(A + (size_t)(i - 1) * kSnapSlab + 256 * ks, 128, 512);
+            const uint64_t bd = desc_kmajor(B + 256 * ks, 128, 512);
+            mma_f16(tbase + (uint32_t)(kRowsPer * (i - 1)), ad, bd, id, (i > 1 || ks > 0) ? 1u : 0u);
         }
     }
 }
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     auto product = [&](bool mn) {
         if (tid == 0) {
             fence_after_sync();
-            issue_levels(tbase, X, Wrec, 2, kSlices + 1, mn);
+            issue_products(tbase, X, Wrec, mn);
             mma_commit(&mbar_mma);
         }
         mma_pending = true;
