@@ -185,6 +185,14 @@ qcs_status qcs_set_allocator(qcs_ctx *ctx, qcs_alloc_fn alloc_fn, qcs_free_fn fr
  * QCS_ERR_ARG for max_iter out of range, QCS_ERR_CUDA if the launch fails. */
 qcs_status qcs_selftest_bounded_wait(qcs_ctx *ctx, uint32_t max_iter, void *stream);
 
+/* Self-test of the reciprocal the eliminations use for their pivots (Newton-Raphson
+ * steps from a single-precision seed instead of an IEEE division): r[i] = 1/d[i] for
+ * n values d[i] >= 0, both device arrays of doubles owned by the caller, through the
+ * same device function as the pair kernels.  The result is within 2 ulp of the
+ * correctly rounded 1/d; d = 0 gives +inf, as the division does.
+ * Errors: QCS_ERR_ARG (ctx NULL, n < 0, null pointers with n > 0), QCS_ERR_CUDA. */
+qcs_status qcs_selftest_reciprocal(qcs_ctx *ctx, const double *d, double *r, int64_t n, void *stream);
+
 /* ---------------------------------------------------------- snapshots */
 
 /* Build the device representation of P snapshots (Q_p, b_p).

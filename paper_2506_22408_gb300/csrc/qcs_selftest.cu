@@ -1,4 +1,5 @@
-// qcs_selftest.cu -- self-test of the device time-out path, and the FP64 FMA rate.
+// qcs_selftest.cu -- self-tests of the device time-out path and of the pivot
+// reciprocal, and the FP64 FMA rate.
 //
 // The split-precision kernel waits for its bulk copies and tensor-core MMAs on
 // mbarriers, each wait bounded by an iteration limit after which the kernel raises
@@ -26,6 +27,12 @@ __global__ void bounded_wait_selftest_kernel(uint32_t max_iter, unsigned *status
     if (threadIdx.x == 0) mbar_init(&mbar, 1);  // one arrival expected, none will come
     __syncthreads();
     if (threadIdx.x == 0 && !mbar_wait_bounded(&mbar, 0, max_iter)) raise_status(status, QCS_ERR_TIMEOUT);
+}
+
+// One thread per value: r[i] = recip_nonneg(d[i]), the reciprocal of the eliminations.
+__global__ void reciprocal_selftest_kernel(const double *__restrict__ d, double *__restrict__ r, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = recip_nonneg(d[i]);
 }
 
 constexpr int kRateChains = 8;
@@ -56,6 +63,17 @@ extern "C" qcs_status qcs_selftest_bounded_wait(qcs_ctx *ctx, uint32_t max_iter,
     DeviceGuard g(ctx->device);
     bounded_wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(max_iter, ctx->d_status);
     return qcs_check_launch(ctx, "bounded_wait_selftest_kernel");
+}
+
+extern "C" qcs_status qcs_selftest_reciprocal(qcs_ctx *ctx, const double *d, double *r, int64_t n, void *stream) {
+    if (!ctx) return QCS_ERR_ARG;
+    if (n < 0 || (n > 0 && (!d || !r))) return qcs_fail(ctx, QCS_ERR_ARG, "qcs_selftest_reciprocal: n < 0 or null array");
+    if (n == 0) return QCS_OK;
+    DeviceGuard g(ctx->device);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)ctx->num_sms * 8) blocks = (int64_t)ctx->num_sms * 8;
+    reciprocal_selftest_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
+    return qcs_check_launch(ctx, "reciprocal_selftest_kernel");
 }
 
 extern "C" qcs_status qcs_fp64_fma_rate(qcs_ctx *ctx, double *tflops, void *stream) {

@@ -42,6 +42,7 @@ EXPORTED = [
     "qcs_grad_flops_per_pair_signed_perm", "qcs_shadow_rdm", "qcs_shadow_rdm_flops", "qcs_vce_transform",
     "qcs_local_energy", "qcs_local_energy_flops_per_pair", "qcs_overlap_flops_breakdown",
     "qcs_selftest_bounded_wait", "qcs_fp64_fma_rate", "qcs_overlap_tc_work_per_pair", "qcs_set_allocator",
+    "qcs_selftest_reciprocal",
 ]
 MAX_SYSTEMS = 8
 TUNE_CACHE = os.environ.get("QCS_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qcs", "tune.json"))
@@ -116,6 +117,7 @@ def load(build_if_missing: bool = True):
         lib.qcs_workspace_bytes.argtypes = [P]
         lib.qcs_workspace_bytes.restype = ctypes.c_size_t
         lib.qcs_selftest_bounded_wait.argtypes = [P, u32, P]
+        lib.qcs_selftest_reciprocal.argtypes = [P, P, P, i64, P]
         lib.qcs_fp64_fma_rate.argtypes = [P, ctypes.POINTER(f64), P]
         lib.qcs_overlap_tc_work_per_pair.argtypes = [i32, i32, i32, u32, ctypes.POINTER(f64), ctypes.POINTER(f64)]
         lib.qcs_set_allocator.argtypes = [P, _ALLOC_FN, _FREE_FN, P]
@@ -233,6 +235,19 @@ class Context:
         """Run the device time-out self-test; returns the status bits it raised."""
         self.check(self.lib.qcs_selftest_bounded_wait(self.h, max_iter, _stream()))
         return self.sync_status()
+
+    def selftest_reciprocal(self, d):
+        """r = 1/d through the eliminations' pivot reciprocal (qcs_selftest_reciprocal);
+        d a float64 CUDA tensor of values >= 0 on this context's device."""
+        import torch
+
+        if d.dtype != torch.float64 or not d.is_cuda or d.device.index != self.device:
+            raise ValueError("d must be a float64 tensor on the context's device")
+        d = d.contiguous()
+        r = torch.empty_like(d)
+        with torch.cuda.device(self.device):
+            self.check(self.lib.qcs_selftest_reciprocal(self.h, _ptr(d), _ptr(r), d.numel(), _stream()))
+        return r
 
     def use_torch_allocator(self):
         """Back the context's device memory (workspace, snapshot sets built afterwards,

@@ -109,6 +109,7 @@ def test_host_only_size_checks():
     parts = (ctypes.c_double * 3)()
     assert lib.qcs_overlap_flops_breakdown(maxn + 1, 2, 0, 0, parts) == qcs.QCS_ERR_ARG
     assert lib.qcs_overlap_flops_breakdown(16, 8, 0, 0, None) == qcs.QCS_ERR_ARG
+    assert lib.qcs_selftest_reciprocal(None, None, None, 0, None) == qcs.QCS_ERR_ARG  # no context: no device work
 
 
 def test_tensor_core_work_accounting_host_only():
