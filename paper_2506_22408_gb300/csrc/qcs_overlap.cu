@@ -83,8 +83,6 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
     cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
-    cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
-    int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = reinterpret_cast<uint8_t *>(wbase + A.off_act);
     uint8_t *act1 = act0 + A.vm;
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
@@ -210,7 +208,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             cd S = cmk(0.0, 0.0);
             for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                 int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
+                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
                     for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
@@ -310,10 +308,6 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_inv = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_int = (int)o;
-    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * A.vm);
     A.off_pv = (int)o;

@@ -351,21 +351,28 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
 
 // Pfaffians of nb node matrices B + wnode[v] D held in Ns (packed upper), m x m with
 // ne occupied rows first.  On return pf[v] holds pf(B + wnode[v] D); m = 0 gives 1.
+// The warp is cut into segments of seg lanes (seg = 32 / nb rounded up to a power of
+// two); segment v owns node v through each Parlett-Reid step: it finds the pivot of the
+// active first row, takes the pivot's reciprocal (every lane of the segment, so no lane
+// waits on a divergent branch or a shared-memory round trip) and forms the Gauss
+// vectors, after which the rank-2 updates of all nodes are spread over the whole warp.
+// The steps run down to four active indices, whose Pfaffian closes the product in
+// three terms, a01 a23 - a02 a13 + a03 a12 (two indices: a01).
 __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnode, int nb,
-                                      const cd *__restrict__ Bs, cd *__restrict__ Ns,
-                               cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf, cd *__restrict__ inv,
-                               int *__restrict__ ints,
-                               uint8_t *__restrict__ act0, uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
-                               cd *__restrict__ pv, int lane) {
+                                      const cd *__restrict__ Bs, cd *__restrict__ Ns, cd *__restrict__ Uv,
+                                      cd *__restrict__ Vv, cd *__restrict__ pf, uint8_t *__restrict__ act0,
+                                      uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
+                                      cd *__restrict__ pv, int lane) {
     if (m == 0) {
         if (lane < nb) pf[lane] = cmk(1.0, 0.0);
         __syncwarp();
         return;
     }
-    const int S = m / 2;  // elimination steps; the signed pivots of node v go to pv[v*S + s]
+    // records per node in pv: the signed pivots of the (m - 4) / 2 steps and the closing
+    // Pfaffian (a single record for m = 2 or 4)
+    const int S = m >= 4 ? m / 2 - 1 : 1;
     const int d = (m - ne) / 2;
     const int T = tri_count(m);
-    int *pos = ints, *kk = ints + kMaxNB, *pp = ints + 2 * kMaxNB;
     for (int e = lane; e < nb * T; e += 32) {
         int v = e / T, t = e - v * T;
         Ns[v * T + t] = Bs[t];
@@ -381,69 +388,57 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
         *x = cadd(*x, wnode[v]);
     }
     __syncwarp();
+    const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
+    const int v = lane / seg, sl = lane - v * seg;
+    const bool live = v < nb;
+    const int vr = live ? v : 0;  // lanes past the last node read node 0 and write nothing
+    const cd *__restrict__ Nv = Ns + vr * T;
     uint8_t *cur = act0, *nxt = act1;
-    for (int r = m, s = 0; r >= 2; r -= 2, ++s) {
-        // pivot: largest |A_{k,i}| over the active row of k = cur[0].  Lanes form nb
-        // segments of seg lanes; each lane scans every seg-th candidate, then a
-        // shuffle reduction inside the segment (no atomics, no shared round trip).
-        const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
+    int s = 0;
+    for (int r = m; r > 4; r -= 2, ++s) {
+        // pivot: largest |A_{k,i}| over the active row of k = cur[0], each lane scanning
+        // every seg-th candidate, then a shuffle reduction inside the segment; the key's
+        // low bits prefer the first candidate among equal magnitudes
+        const int k = cur[vr * m];
         unsigned long long bk = 0ull;
-        {
-            const int v = lane / seg, sl = lane - (lane / seg) * seg;
-            if (v < nb) {
-                const int k = cur[v * m];
-                for (int a = 1 + sl; a < r; a += seg) {
-                    const unsigned key = pivot_key(Ns[v * T + tri_index(k, cur[v * m + a])]);
-                    const unsigned long long c =
-                        ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
-                    bk = c > bk ? c : bk;
-                }
-            }
-            for (int o = seg >> 1; o > 0; o >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
-                bk = ob > bk ? ob : bk;
-            }
-            bk = __shfl_sync(QCS_FULL, bk, (lane < nb ? lane : 0) * seg);
+        for (int a = 1 + sl; a < r; a += seg) {
+            const unsigned key = pivot_key(Nv[tri_index(k, cur[vr * m + a])]);
+            const unsigned long long c = ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
+            bk = c > bk ? c : bk;
         }
-        if (lane < nb) {
-            int a = 0xffff - (int)(bk & 0xffffull);
-            int k = cur[lane * m], p = cur[lane * m + a];
-            cd piv = Ns[lane * T + tri_index(k, p)];
-            pv[lane * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
-            if (r > 2) inv[lane] = cinv(piv);  // the last step has no Gauss vectors
-            pos[lane] = a;
-            kk[lane] = k;
-            pp[lane] = p;
+        for (int o = seg >> 1; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+            bk = ob > bk ? ob : bk;
         }
-        __syncwarp();
-        if (r == 2) break;
+        const int a = 0xffff - (int)(bk & 0xffffull);  // 1 .. r - 1 (candidate a = 1 always exists)
+        const int p = cur[vr * m + a];
+        const cd piv = Nv[tri_index(k, p)];
+        if (live && sl == 0) pv[v * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
+        const cd iv = cinv(piv);
         // Gauss vectors over the remaining indices (original order kept)
         const int rv = r - 2;
-        for (int e = lane; e < nb * rv; e += 32) {
-            int v = e / rv, a2 = e - v * rv;
-            int a = a2 + 1 + ((a2 + 1 >= pos[v]) ? 1 : 0);
-            int i = cur[v * m + a], k = kk[v], p = pp[v];
-            const cd *Nv = Ns + v * T;
-            cd u = Nv[tri_index(k, i)];          // A_{k,i}; A_{i,k} = -u
-            cd ut = cnegmul(u, inv[v]);          // A_{i,k} / A_{k,p}
-            cd vv = (i < p) ? Nv[tri_index(i, p)] : flip_if(Nv[tri_index(p, i)], true);  // A_{i,p}
-            Uv[v * m + a2] = ut;
-            Vv[v * m + a2] = vv;
-            nxt[v * m + a2] = (uint8_t)i;
+        if (live) {
+            for (int a2 = sl; a2 < rv; a2 += seg) {
+                const int aa = a2 + 1 + ((a2 + 1 >= a) ? 1 : 0);
+                const int i = cur[v * m + aa];
+                Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);  // A_{i,k} / A_{k,p}, A_{i,k} = -A_{k,i}
+                Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : flip_if(Nv[tri_index(p, i)], true);  // A_{i,p}
+                nxt[v * m + a2] = (uint8_t)i;
+            }
         }
         __syncwarp();
-        // rank-2 update A_ij -= ut_i v_j - v_i ut_j on the remaining pairs
+        // rank-2 update A_ij -= ut_i v_j - v_i ut_j on the remaining pairs of every node
         const int Tr = tri_count(rv);
         for (int e = lane; e < nb * Tr; e += 32) {
-            int v = e / Tr, t = e - v * Tr;
-            int a, b;
-            pair_of(tab, t, a, b);
-            int i = nxt[v * m + a], j = nxt[v * m + b];
-            cd *x = Ns + v * T + tri_index(i, j);
+            int w = e / Tr, t = e - w * Tr;
+            int ia, ib;
+            pair_of(tab, t, ia, ib);
+            int i = nxt[w * m + ia], j = nxt[w * m + ib];
+            cd *x = Ns + w * T + tri_index(i, j);
             cd y = *x;
-            const cd *U_ = Uv + v * m, *V_ = Vv + v * m;
-            cfms(y, U_[a], V_[b]);
-            cfma(y, V_[a], U_[b]);
+            const cd *U_ = Uv + w * m, *V_ = Vv + w * m;
+            cfms(y, U_[ia], V_[ib]);
+            cfma(y, V_[ia], U_[ib]);
             *x = y;
         }
         __syncwarp();
@@ -451,6 +446,20 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
         cur = nxt;
         nxt = t;
     }
+    // the closing Pfaffian of the last four (or two) active indices, ascending
+    if (live && sl == 0) {
+        const uint8_t *c = cur + v * m;
+        cd q;
+        if (m >= 4) {
+            q = cmul(Nv[tri_index(c[0], c[1])], Nv[tri_index(c[2], c[3])]);
+            cfms(q, Nv[tri_index(c[0], c[2])], Nv[tri_index(c[1], c[3])]);
+            cfma(q, Nv[tri_index(c[0], c[3])], Nv[tri_index(c[1], c[2])]);
+        } else {
+            q = Nv[tri_index(c[0], c[1])];
+        }
+        pv[v * S + s] = q;
+    }
+    __syncwarp();
     // pf[v] = prod_s pv[v][s]: pairwise tree over the lanes; each level reads into
     // registers, then stores after a __syncwarp (nb * half <= 8 * 23 / 2 < 96 items)
     for (int len = S; len > 1; len = (len + 1) / 2) {
@@ -460,8 +469,8 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
         for (int t = 0; t < 3; ++t) {
             const int e = lane + 32 * t;
             if (e < nb * half) {
-                const int v = e / half, i = e - v * half;
-                r[t] = cmul(pv[v * S + 2 * i], pv[v * S + 2 * i + 1]);
+                const int w = e / half, i = e - w * half;
+                r[t] = cmul(pv[w * S + 2 * i], pv[w * S + 2 * i + 1]);
             }
         }
         cd tail = cmk(0.0, 0.0);
@@ -471,8 +480,8 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
         for (int t = 0; t < 3; ++t) {
             const int e = lane + 32 * t;
             if (e < nb * half) {
-                const int v = e / half, i = e - v * half;
-                pv[v * S + i] = r[t];
+                const int w = e / half, i = e - w * half;
+                pv[w * S + i] = r[t];
             }
         }
         if ((len & 1) && lane < nb) pv[lane * S + half] = tail;

@@ -84,7 +84,7 @@ struct SplitArgs {
     int64_t ngroups;             // walker groups of kWalkersPerTile
     int region_bytes;            // operand / workspace union
     int warp_bytes;
-    int off_T, off_B, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;
+    int off_T, off_B, off_U, off_V, off_pf, off_act, off_pv;
     int vm;                      // entries per Gauss-vector buffer (the full matrix or NB complements)
     const float *Mhi, *Mlo;      // walker slabs
     const float *Nhi, *Nlo;      // snapshot slabs
@@ -178,8 +178,6 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
     cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
-    cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
-    int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = wbase + A.off_act;
     uint8_t *act1 = act0 + A.vm;
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
@@ -293,7 +291,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
             cd S = cmk(0.0, 0.0);
             for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                 const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
+                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
                     for (int vv = 0; vv < nb; ++vv) cfma(S, A.gamma[k0 + vv], pf[vv]);
@@ -341,10 +339,6 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
     o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_inv = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_int = (int)o;
-    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * A.vm);
     A.off_pv = (int)o;

@@ -164,7 +164,7 @@ struct TcArgs {
     int subs;         // sub-tiles of kSnapsPerSub snapshots per tile
     int ws_bytes;     // Pfaffian workspace per warp
     int ws_in_operands;  // 1: the workspaces are quarters of the operand region
-    int off_P, off_N, off_U, off_V, off_pf, off_inv, off_int, off_act, off_pv;  // B^(s) at offset 0
+    int off_P, off_N, off_U, off_V, off_pf, off_act, off_pv;  // B^(s) at offset 0
     int vm;
     int smem_tab, smem_ws;  // byte offsets of the pair table and (if separate) the workspaces
     const unsigned char *snap_rec;
@@ -319,8 +319,6 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
     cd *pf = reinterpret_cast<cd *>(wbase + A.off_pf);
-    cd *inv = reinterpret_cast<cd *>(wbase + A.off_inv);
-    int *ints = reinterpret_cast<int *>(wbase + A.off_int);
     uint8_t *act0 = wbase + A.off_act;
     uint8_t *act1 = act0 + A.vm;
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
@@ -425,7 +423,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
                 cd S = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                     const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, inv, ints, act0, act1, tab, pv,
+                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
                                    lane);
                     if (lane == 0)
                         for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
@@ -478,10 +476,6 @@ size_t tc_warp_layout(TcArgs &A, int NB) {
     o = align16(o + (size_t)A.vm * sizeof(cd));
     A.off_pf = (int)o;
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_inv = (int)o;
-    o = align16(o + (size_t)kMaxNB * sizeof(cd));
-    A.off_int = (int)o;
-    o = align16(o + (size_t)3 * kMaxNB * sizeof(int));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * A.vm);
     A.off_pv = (int)o;
