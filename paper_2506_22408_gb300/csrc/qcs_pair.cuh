@@ -414,15 +414,30 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
         const int p = cur[vr * m + a];
         const cd piv = Nv[tri_index(k, p)];
         if (live && sl == 0) pv[v * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
-        const cd iv = cinv(piv);
-        // Gauss vectors over the remaining indices (original order kept)
+        // Gauss vectors over the remaining indices (original order kept): u = A_{i,k} / A_{k,p}
+        // (A_{i,k} = -A_{k,i}) and v = A_{i,p}; the loads of a lane's first index are
+        // issued before the reciprocal, whose dependent FP64 chain they do not wait for
         const int rv = r - 2;
+        const bool g0 = live && sl < rv;
+        int i0 = 0;
+        cd u0 = cmk(0.0, 0.0), v0 = cmk(0.0, 0.0);
+        if (g0) {
+            i0 = cur[v * m + sl + 1 + ((sl + 1 >= a) ? 1 : 0)];
+            u0 = Nv[tri_index(k, i0)];
+            v0 = (i0 < p) ? Nv[tri_index(i0, p)] : flip_if(Nv[tri_index(p, i0)], true);
+        }
+        const cd iv = cinv(piv);
+        if (g0) {
+            Uv[v * m + sl] = cnegmul(u0, iv);
+            Vv[v * m + sl] = v0;
+            nxt[v * m + sl] = (uint8_t)i0;
+        }
         if (live) {
-            for (int a2 = sl; a2 < rv; a2 += seg) {
+            for (int a2 = sl + seg; a2 < rv; a2 += seg) {
                 const int aa = a2 + 1 + ((a2 + 1 >= a) ? 1 : 0);
                 const int i = cur[v * m + aa];
-                Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);  // A_{i,k} / A_{k,p}, A_{i,k} = -A_{k,i}
-                Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : flip_if(Nv[tri_index(p, i)], true);  // A_{i,p}
+                Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);
+                Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : flip_if(Nv[tri_index(p, i)], true);
                 nxt[v * m + a2] = (uint8_t)i;
             }
         }

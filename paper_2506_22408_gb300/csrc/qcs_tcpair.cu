@@ -219,40 +219,47 @@ __device__ __forceinline__ void read_levels8(uint32_t taddr, int cb, long long (
     }
 }
 
-// P[a][b] from the upper triangle Pu (P is skew-symmetric).
+// P[a][b] (a != b) from the upper triangle Pu (P is skew-symmetric): the sign of the
+// lower triangle flipped on the bit pattern, without a branch or an FP64 instruction.
 __device__ __forceinline__ double pget(const double *__restrict__ Pu, int a, int b) {
-    return a < b ? Pu[tri_index(a, b)] : (a > b ? -Pu[tri_index(b, a)] : 0.0);
+    const bool sw = a > b;
+    const long long v = __double_as_longlong(Pu[tri_index(sw ? b : a, sw ? a : b)]);
+    return __longlong_as_double(sw ? v ^ (long long)0x8000000000000000ull : v);
 }
 
 // B^(s) (packed upper, m x m) from P = R J R^T, R = [Re T; Im T]: selected row x < ne is
 // T_x (= R[x] + i R[n+x]); x >= ne is Re T_j (even offset) or -Im T_j (odd offset) for
-// the empty mode j = ne + (x - ne)/2.
+// the empty mode j = ne + (x - ne)/2.  One loop per block (occupied x occupied, occupied
+// x empty, empty x empty), so that no pass of the warp diverges across the three forms.
 __device__ void build_B_from_P(int n, int ne, int m, const double *__restrict__ Pu, cd *__restrict__ Bs,
                                const uint16_t *__restrict__ tab, int lane) {
-    const int T = tri_count(m);
-    for (int t = lane; t < T; t += 32) {
+    // occupied x occupied: (R_x + i R_nx) J (R_y + i R_ny)^T, the first tri(ne) entries
+    for (int t = lane; t < tri_count(ne); t += 32) {
         int x, y;
         pair_of(tab, t, x, y);  // x < y
-        cd v;
-        if (y < ne) {  // occupied x occupied: (R_x + i R_nx) J (R_y + i R_ny)^T
-            const double prr = pget(Pu, x, y), pii = pget(Pu, n + x, n + y);
-            const double pri = pget(Pu, x, n + y), pir = pget(Pu, n + x, y);
-            v = cmk(prr - pii, pri + pir);
-        } else {
-            const int jy = ne + ((y - ne) >> 1);
-            const bool yim = (y - ne) & 1;
-            const int ry = yim ? n + jy : jy;
-            if (x < ne) {  // occupied x empty: (R_x + i R_nx) J (+-R_ry)^T
-                const double re = pget(Pu, x, ry), im = pget(Pu, n + x, ry);
-                v = yim ? cmk(-re, -im) : cmk(re, im);
-            } else {
-                const int jx = ne + ((x - ne) >> 1);
-                const bool xim = (x - ne) & 1;
-                const double re = pget(Pu, xim ? n + jx : jx, ry);
-                v = cmk((xim != yim) ? -re : re, 0.0);
-            }
-        }
-        Bs[t] = v;
+        const double prr = pget(Pu, x, y), pii = pget(Pu, n + x, n + y);
+        const double pri = pget(Pu, x, n + y), pir = pget(Pu, n + x, y);
+        Bs[t] = cmk(prr - pii, pri + pir);
+    }
+    // occupied x empty: (R_x + i R_nx) J (+-R_ry)^T, column y = ne + c, row x < ne
+    const int d2 = m - ne;
+    for (int e = lane; e < d2 * ne; e += 32) {
+        const int c = e / ne, x = e - c * ne;
+        const int jy = ne + (c >> 1);
+        const bool yim = c & 1;
+        const int ry = yim ? n + jy : jy;
+        cd v = cmk(pget(Pu, x, ry), pget(Pu, n + x, ry));
+        Bs[tri_index(x, ne + c)] = flip_if(v, yim);
+    }
+    // empty x empty: (+-R_rx) J (+-R_ry)^T, real
+    for (int t = lane; t < tri_count(d2); t += 32) {
+        int cx, cy;
+        pair_of(tab, t, cx, cy);  // cx < cy
+        const int jx = ne + (cx >> 1), jy = ne + (cy >> 1);
+        const bool xim = cx & 1, yim = cy & 1;
+        const long long re = __double_as_longlong(pget(Pu, xim ? n + jx : jx, yim ? n + jy : jy));
+        Bs[tri_index(ne + cx, ne + cy)] =
+            cmk(__longlong_as_double(xim != yim ? re ^ (long long)0x8000000000000000ull : re), 0.0);
     }
 }
 
