@@ -17,7 +17,8 @@
 // The level sums are read back as FP32 integers, converted exactly (one F2I each) and
 // combined exactly in integer arithmetic into one 64-bit fixed-point value z = sum_{L=2..7} acc_L 2^{8(7-L)} +
 // floor(acc_8 / 2^8), worth z 2^{e+f-56}; |z| < 2^62.  Nothing in this file issues
-// an FP64 instruction except the out-of-range branch of fixed_to_f64.
+// an FP64 instruction except fixed_to_f64_exact, the path for exponents outside the
+// normal range.
 #pragma once
 #include <stdint.h>
 
@@ -84,11 +85,12 @@ __device__ __forceinline__ uint64_t fixed_of(double x, int e) {
 }
 
 // |z| 2^sh as an unsigned fixed-point magnitude (shift left or right; the caller keeps
-// the result below 2^56).
+// the result below 2^56).  Selects only, no branch.
 __device__ __forceinline__ uint64_t rescale_mag(long long z, int sh) {
     const uint64_t u = z < 0 ? (uint64_t)(-z) : (uint64_t)z;
-    if (sh >= 0) return u << (sh < 63 ? sh : 63);
-    return sh <= -64 ? 0ull : u >> (-sh);
+    const uint64_t l = u << (sh < 63 ? (sh > 0 ? sh : 0) : 63);
+    const uint64_t r = sh <= -64 ? 0ull : u >> (sh < 0 ? -sh : 0);
+    return sh >= 0 ? l : r;
 }
 
 // z = sum_{L=2..7} acc[L-2] 2^{8(7-L)} + floor(acc[6] / 2^8) for the seven level sums
@@ -115,23 +117,27 @@ __device__ __forceinline__ int bitlen64(long long z) {
     return 64 - __clzll((long long)u);
 }
 
-// z 2^E as an FP64 (round to nearest on the 11 dropped bits), assembled from the
-// bits; the branch for exponents outside the normal range is never taken for the
-// magnitudes of this library's matrices.
-__device__ __forceinline__ double fixed_to_f64(long long z, int E) {
-    if (z == 0) return 0.0;
+// z 2^E as an FP64 (round to nearest on the 11 dropped bits), assembled from the bits
+// with selects only, so that a warp converts its entries without diverging.  The
+// exponent of the result must lie in the normal range; range_ok is cleared otherwise
+// (zero is always in range), and the caller then takes fixed_to_f64_exact.
+__device__ __forceinline__ double fixed_to_f64(long long z, int E, bool &range_ok) {
     const unsigned long long sg = z < 0 ? (1ull << 63) : 0ull;
     const unsigned long long u = z < 0 ? (unsigned long long)(-z) : (unsigned long long)z;
-    const int lz = __clzll((long long)u);
-    const unsigned long long nrm = u << lz;  // top bit set
+    const int lz = __clzll((long long)u);               // 64 for z = 0
+    const unsigned long long nrm = u << (lz & 63);      // top bit set (0 for z = 0)
     // 53 significant bits, rounded on the first dropped bit.  Added to the exponent
     // field (ex + 1022), the leading bit 2^52 of mant raises it to ex + 1023; after a
     // rounding carry mant is 2^53, which gives ex + 1024 with a zero fraction: 2^(ex+1).
     const unsigned long long mant = (nrm >> 11) + ((nrm >> 10) & 1ull);
     const int ex = 63 - lz + E;
-    if (ex < -1020 || ex > 1020) return ldexp((double)z, E);
-    return __longlong_as_double((long long)(sg | (((unsigned long long)(ex + 1022) << 52) + mant)));
+    range_ok = range_ok && (u == 0ull || (ex >= -1020 && ex <= 1020));
+    const long long bits = (long long)(sg | (((unsigned long long)(ex + 1022) << 52) + mant));
+    return u == 0ull ? 0.0 : __longlong_as_double(bits);
 }
+
+// The same value for any exponent (subnormal, overflow), by ldexp.
+__device__ __forceinline__ double fixed_to_f64_exact(long long z, int E) { return ldexp((double)z, E); }
 
 // Write the seven slices of a 32-entry row (fixed-point magnitudes u[k], signs in the
 // bit mask neg) into the K-major slice slabs: slab i (1..7) starts at base + (i-1) *

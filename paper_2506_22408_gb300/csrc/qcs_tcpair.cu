@@ -408,12 +408,24 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
             for (int cb = 0; cb < 4; ++cb) {
                 long long z[8];
                 read_levels8(tlane, cb, z);
+                // every lane converts all eight entries (no divergence); the upper
+                // triangle of P_i (a < lane) is stored into the free operand region
+                bool in_range = true;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int a = 8 * cb + c;
-                    if (a < lane) {  // the operand region is free: the upper triangle of P_i
+                    const int ea = e_exp[a];
+                    const bool zero = Fb == kNoRow || ea == kNoRow;
+                    const double val = fixed_to_f64(zero ? 0ll : z[c], ea + Fb - 56, in_range);
+                    if (a < lane) Pu[tri_index(a, lane)] = val;
+                }
+                if (!__all_sync(QCS_FULL, in_range)) {  // an exponent outside the normal range
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int a = 8 * cb + c;
                         const int ea = e_exp[a];
-                        Pu[tri_index(a, lane)] = (Fb == kNoRow || ea == kNoRow) ? 0.0 : fixed_to_f64(z[c], ea + Fb - 56);
+                        if (a < lane && Fb != kNoRow && ea != kNoRow)
+                            Pu[tri_index(a, lane)] = fixed_to_f64_exact(z[c], ea + Fb - 56);
                     }
                 }
             }
