@@ -44,10 +44,9 @@ __device__ __forceinline__ cd cnegmul(cd a, cd b) {
 
 // Sign flip of both components by integer XOR on the sign bits (no FP64 work).
 __device__ __forceinline__ cd flip_if(cd z, bool f) {
-    if (f) {
-        z.x = __longlong_as_double(__double_as_longlong(z.x) ^ (long long)0x8000000000000000ull);
-        z.y = __longlong_as_double(__double_as_longlong(z.y) ^ (long long)0x8000000000000000ull);
-    }
+    const long long m = f ? (long long)0x8000000000000000ull : 0ll;
+    z.x = __longlong_as_double(__double_as_longlong(z.x) ^ m);
+    z.y = __longlong_as_double(__double_as_longlong(z.y) ^ m);
     return z;
 }
 
@@ -89,6 +88,15 @@ __device__ __forceinline__ cd cinv(cd a) {
 }
 
 __device__ __forceinline__ bool cfinite(cd a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Entry (i, j), i != j, of a skew-symmetric matrix stored as its packed strict upper
+// triangle: one load, and the sign of the lower triangle flipped on the bit patterns
+// (no branch, no FP64 instruction).
+__device__ __forceinline__ cd skew_get(const cd *__restrict__ N, int i, int j) {
+    const bool lo = i > j;
+    const int a = lo ? j : i, b = lo ? i : j;
+    return flip_if(N[(b * (b - 1)) / 2 + a], lo);
+}
 
 // Pivot magnitude key without floating-point work: the high 32 bits of
 // max(|re|, |im|) (sign, exponent and 20 mantissa bits) order magnitudes to a

@@ -203,9 +203,6 @@ struct SharedScratch {  // per-group scalars exchanged between the two warps
     cd pf0;
 };
 
-__device__ __forceinline__ cd skew_get(const cd *N, int i, int j) {  // A(i, j), i != j
-    return i < j ? N[tri_index(i, j)] : cneg(N[tri_index(j, i)]);
-}
 __device__ __forceinline__ void skew_put(cd *N, int i, int j, cd x) {  // A(i, j) = x, A(j, i) = -x
     if (i < j) N[tri_index(i, j)] = x;
     else N[tri_index(j, i)] = cneg(x);

@@ -306,8 +306,8 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
             if (a >= ak) ++a;
             if (a >= ap) ++a;
             const int i = cur[a];
-            const cd aik = i < k ? Ns[tri_index(i, k)] : cneg(Ns[tri_index(k, i)]);  // A_{i,k}
-            const cd aip = i < p ? Ns[tri_index(i, p)] : cneg(Ns[tri_index(p, i)]);  // A_{i,p}
+            const cd aik = skew_get(Ns, i, k);  // A_{i,k}
+            const cd aip = skew_get(Ns, i, p);  // A_{i,p}
             Uv[a2] = cmul(aik, iv);
             Vv[a2] = aip;
             nxt[a2] = (uint8_t)i;
@@ -424,7 +424,7 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
         if (g0) {
             i0 = cur[v * m + sl + 1 + ((sl + 1 >= a) ? 1 : 0)];
             u0 = Nv[tri_index(k, i0)];
-            v0 = (i0 < p) ? Nv[tri_index(i0, p)] : flip_if(Nv[tri_index(p, i0)], true);
+            v0 = skew_get(Nv, i0, p);
         }
         const cd iv = cinv(piv);
         if (g0) {
@@ -437,7 +437,7 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
                 const int aa = a2 + 1 + ((a2 + 1 >= a) ? 1 : 0);
                 const int i = cur[v * m + aa];
                 Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);
-                Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : flip_if(Nv[tri_index(p, i)], true);
+                Vv[v * m + a2] = skew_get(Nv, i, p);
                 nxt[v * m + a2] = (uint8_t)i;
             }
         }
