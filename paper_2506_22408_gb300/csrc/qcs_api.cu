@@ -438,7 +438,7 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     wk->chunk = cfg.chunk > 0 ? cfg.chunk : kChunk;
     // partial sums: FP64 ALU path one per (walker, tile, warp); split path one per
     // (walker, tile of snapshots); tensor-core path one per (walker, tile)
-    const int span = split ? qcs_split_snaps_per_tile() : tc ? qcs_tc_snaps_per_tile(cfg.subs)
+    const int span = split ? qcs_split_snaps_per_tile(cfg.subs) : tc ? qcs_tc_snaps_per_tile(cfg.subs)
                                                              : wk->chunk * qcs_pair_warps_per_block();
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;

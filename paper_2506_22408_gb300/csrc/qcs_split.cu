@@ -5,8 +5,10 @@
 // Qt = C + iD,
 //     [T_re; T_im] = M_w N_q^T,   M_w = [[A, -B], [B, A]]  (2n x 2n),
 //                                 N_q = [C, D]             (2n x 2n, rows c),
-// so a tile of 4 walkers x 4 snapshots is one 128 x 128 x 32 GEMM (n <= 16, rows
-// and K padded to 32).  It runs on the 5th-generation tensor cores as three
+// so 4 walkers x 4 snapshots are one 128 x 128 x 32 GEMM (n <= 16, rows and K padded
+// to 32).  A tile is 4 walkers x subs such sub-chunks of consecutive snapshots (8 by
+// default, tuned by qcs_autotune); each warp keeps its walker's sum over the tile in
+// registers and writes one partial sum per tile.  It runs on the 5th-generation tensor cores as three
 // tcgen05.mma kind::tf32 passes over TF32 hi/lo splits of both operands
 // (hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory).  The operand
 // slabs are precomputed once per walker and per snapshot in the K-major core-matrix
@@ -30,7 +32,8 @@ constexpr int kK = 32;           // padded contraction length (2n <= 32)
 constexpr int kRows = 32;        // padded rows per walker / snapshot
 constexpr int kSlabBytes = kRows * kK * 4;  // one operand slab (4 KB)
 constexpr int kWalkersPerTile = 4;          // M = 128
-constexpr int kSnapsPerTile = 4;            // N = 128
+constexpr int kSnapsPerSub = 4;             // N = 128: snapshots per MMA sub-chunk
+constexpr int kSubPerTile = 8;              // default sub-chunks per tile (32 snapshots)
 constexpr uint32_t kTmemCols = 128;         // 4 blocks x 128 columns fit the SM's 512
 constexpr uint32_t kWaitIter = 1u << 26;     // bounded mbarrier waits
 
@@ -80,7 +83,8 @@ __global__ void split_walkers_kernel(int n, int64_t W, const cd *__restrict__ Ut
 struct SplitArgs {
     int n, ne, m, d, nev, NB, all;
     int64_t W, P;
-    int nchunks;                 // snapshot chunks of kSnapsPerTile
+    int nchunks;                 // snapshot chunks of kSnapsPerSub * subs
+    int subs;                    // MMA sub-chunks per tile
     int64_t ngroups;             // walker groups of kWalkersPerTile
     int region_bytes;            // operand / workspace union
     int warp_bytes;
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     float *Ahi = reinterpret_cast<float *>(region);
     float *Alo = Ahi + kWalkersPerTile * kSlabBytes / 4;
     float *Bhi = Alo + kWalkersPerTile * kSlabBytes / 4;
-    float *Blo = Bhi + kSnapsPerTile * kSlabBytes / 4;
+    float *Blo = Bhi + kSnapsPerSub * kSlabBytes / 4;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw + A.region_bytes);
     build_pair_table(tab, tri_count(A.m));
     unsigned char *wbase = region + (size_t)warp * A.warp_bytes;
@@ -199,120 +203,128 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     const int64_t L = A.all ? A.P : (int64_t)(*A.d_count);
     const int64_t ntiles = A.ngroups * A.nchunks;
     uint32_t phase = 0;
-    uint32_t last_phase = 0;
+    bool load_pending = false, mma_pending = false;
     for (;;) {
         fence_proxy_async_smem();  // this thread's workspace writes precede the next bulk copies
         __syncthreads();           // previous tile fully consumed (workspaces overlay the operands)
-        if (tid == 0) next_tile = (long long)atomicAdd(A.counter, 1ull);
+        if (tid == 0) next_tile = abort_flag ? (long long)ntiles : (long long)atomicAdd(A.counter, 1ull);
         __syncthreads();
         const int64_t t = next_tile;
-        if (t >= ntiles || abort_flag) break;
-        const int ch = (int)(t / A.ngroups);  // chunk-major: a snapshot chunk is fetched once
+        if (t >= ntiles) break;
+        const int ch = (int)(t / A.ngroups);  // chunk-major: a snapshot chunk stays in L2 over the walkers
         const int64_t g = t - (int64_t)ch * A.ngroups;
-        const int64_t p0 = (int64_t)ch * kSnapsPerTile;
-        if (p0 >= L) {  // no parity +1 snapshot left in this chunk: nothing to accumulate
-            if (lane == 0 && g * kWalkersPerTile + warp < A.W)
-                A.partial[(g * kWalkersPerTile + warp) * A.nchunks + ch] = cmk(0.0, 0.0);
-            continue;
-        }
-        const int nq = (int)((L - p0) < kSnapsPerTile ? (L - p0) : kSnapsPerTile);
-        // stage the operand slabs (bulk asynchronous copies on mbar_load)
-        if (tid == 0) {
-            uint32_t bytes = 0;
-            for (int s = 0; s < kWalkersPerTile; ++s) bytes += (g * kWalkersPerTile + s < A.W) ? 2 * kSlabBytes : 0;
-            bytes += 2 * kSlabBytes * nq;
-            mbar_expect_tx(&mbar_load, bytes);
-            for (int s = 0; s < kWalkersPerTile; ++s) {
-                const int64_t w = g * kWalkersPerTile + s;
-                if (w >= A.W) continue;
-                bulk_copy(Ahi + s * kSlabBytes / 4, A.Mhi + w * (kSlabBytes / 4), kSlabBytes, &mbar_load);
-                bulk_copy(Alo + s * kSlabBytes / 4, A.Mlo + w * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+        const int64_t p0 = (int64_t)ch * kSnapsPerSub * A.subs;
+        const int64_t w = g * kWalkersPerTile + warp;
+        cd acc = cmk(0.0, 0.0);
+        bool ok = true;
+        for (int sc = 0; sc < A.subs; ++sc) {
+            const int64_t pb = p0 + (int64_t)sc * kSnapsPerSub;
+            if (pb >= L) break;  // no parity +1 snapshot left in this chunk
+            if (sc > 0) {
+                fence_proxy_async_smem();  // the workspaces of the last sub-chunk overlay the operands
+                __syncthreads();
             }
-            for (int q = 0; q < nq; ++q) {
-                const int64_t sq = A.all ? p0 + q : (int64_t)A.idx[p0 + q];
-                bulk_copy(Bhi + q * kSlabBytes / 4, A.Nhi + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
-                bulk_copy(Blo + q * kSlabBytes / 4, A.Nlo + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
-            }
-        }
-        last_phase = phase;
-        bool ok = mbar_wait_bounded(&mbar_load, phase, kWaitIter);
-        if (ok && tid == 0) {
-            fence_after_sync();
-            const uint32_t id = idesc_tf32(kWalkersPerTile * kRows, kSnapsPerTile * kRows);
-            const float *Ap[3] = {Ahi, Ahi, Alo};
-            const float *Bp[3] = {Bhi, Blo, Bhi};
-            for (int pass = 0; pass < 3; ++pass)
-                for (int s = 0; s < kK / 8; ++s) {
-                    const uint64_t ad = desc_kmajor(Ap[pass] + 64 * s, 128, 32 * kK);
-                    const uint64_t bd = desc_kmajor(Bp[pass] + 64 * s, 128, 32 * kK);
-                    mma_tf32(tbase, ad, bd, id, (pass > 0 || s > 0) ? 1u : 0u);
+            const int nq = (int)((L - pb) < kSnapsPerSub ? (L - pb) : kSnapsPerSub);
+            // stage the operand slabs (bulk asynchronous copies on mbar_load); the
+            // walkers' slabs come again from L2 for every sub-chunk
+            if (tid == 0) {
+                uint32_t bytes = 0;
+                for (int s = 0; s < kWalkersPerTile; ++s) bytes += (g * kWalkersPerTile + s < A.W) ? 2 * kSlabBytes : 0;
+                bytes += 2 * kSlabBytes * nq;
+                mbar_expect_tx(&mbar_load, bytes);
+                for (int s = 0; s < kWalkersPerTile; ++s) {
+                    const int64_t ws = g * kWalkersPerTile + s;
+                    if (ws >= A.W) continue;
+                    bulk_copy(Ahi + s * kSlabBytes / 4, A.Mhi + ws * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+                    bulk_copy(Alo + s * kSlabBytes / 4, A.Mlo + ws * (kSlabBytes / 4), kSlabBytes, &mbar_load);
                 }
-            mma_commit(&mbar_mma);
+                for (int q = 0; q < nq; ++q) {
+                    const int64_t sq = A.all ? pb + q : (int64_t)A.idx[pb + q];
+                    bulk_copy(Bhi + q * kSlabBytes / 4, A.Nhi + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+                    bulk_copy(Blo + q * kSlabBytes / 4, A.Nlo + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
+                }
+            }
+            load_pending = true;
+            ok = __syncthreads_and(mbar_wait_bounded(&mbar_load, phase, kWaitIter));
+            if (!ok) break;
+            load_pending = false;
+            if (tid == 0) {
+                fence_after_sync();
+                const uint32_t id = idesc_tf32(kWalkersPerTile * kRows, kSnapsPerSub * kRows);
+                const float *Ap[3] = {Ahi, Ahi, Alo};
+                const float *Bp[3] = {Bhi, Blo, Bhi};
+                for (int pass = 0; pass < 3; ++pass)
+                    for (int s = 0; s < kK / 8; ++s) {
+                        const uint64_t ad = desc_kmajor(Ap[pass] + 64 * s, 128, 32 * kK);
+                        const uint64_t bd = desc_kmajor(Bp[pass] + 64 * s, 128, 32 * kK);
+                        mma_tf32(tbase, ad, bd, id, (pass > 0 || s > 0) ? 1u : 0u);
+                    }
+                mma_commit(&mbar_mma);
+            }
+            mma_pending = true;
+            ok = __syncthreads_and(mbar_wait_bounded(&mbar_mma, phase, kWaitIter));
+            if (!ok) break;
+            mma_pending = false;
+            phase ^= 1u;
+            fence_after_sync();  // all MMAs complete: the operand region becomes the warps' workspaces
+            for (int q = 0; q < nq; ++q) {
+                // T rows of this warp's walker for snapshot q: lane r holds row r of [T_re; T_im]
+                float v0[16], v1[16];
+                const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * q);
+                tmem_ld16(ta, v0);
+                tmem_ld16(ta + 16, v1);
+                tmem_ld_wait();
+                __syncwarp();
+                if (lane < 2 * n) {
+                    const int j = lane % n;
+                    const bool im = lane >= n;
+                    for (int c = 0; c < 2 * n; ++c) {
+                        const float x = c < 16 ? v0[c] : v1[c - 16];
+                        if (im) Ts[j * ldT + c].y = x;
+                        else Ts[j * ldT + c].x = x;
+                    }
+                }
+                __syncwarp();
+                if (w >= A.W) continue;
+                build_B_f32(n, A.ne, Ts, ldT, Bs, tab, lane);
+                __syncwarp();
+                // occupied block eliminated once for all nodes when that is stable
+                cd pf0;
+                const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
+                const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
+                const int NBr = shared ? A.NB : 1;  // the rare full eliminations run one node per round
+                cd S = cmk(0.0, 0.0);
+                for (int k0 = 0; k0 < A.nev; k0 += NBr) {
+                    const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
+                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv, lane);
+                    if (lane == 0)
+                        for (int vv = 0; vv < nb; ++vv) cfma(S, A.gamma[k0 + vv], pf[vv]);
+                    __syncwarp();
+                }
+                if (lane == 0) {
+                    if (shared) S = cmul(S, pf0);
+                    if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
+                    acc = cadd(acc, S);
+                    if (A.per_pair) {
+                        const int64_t sq = A.all ? pb + q : (int64_t)A.idx[pb + q];
+                        A.per_pair[w * A.P + sq] = cmul(A.pref[w], S);
+                    }
+                }
+            }
+            fence_before_sync();  // this warp's tensor-memory reads precede the next sub-chunk's MMAs
         }
-        if (ok) ok = mbar_wait_bounded(&mbar_mma, phase, kWaitIter);
-        phase ^= 1u;
         if (!ok) {
             if (tid == 0) {
                 abort_flag = 1;
                 raise_status(A.status, QCS_ERR_TIMEOUT);
             }
-            continue;  // every thread leaves through the abort check above
-        }
-        fence_after_sync();
-        __syncthreads();  // all MMAs complete: the operand region becomes the warps' workspaces
-        const int64_t w = g * kWalkersPerTile + warp;
-        cd acc = cmk(0.0, 0.0);
-        for (int q = 0; q < nq; ++q) {
-            // T rows of this warp's walker for snapshot q: lane r holds row r of [T_re; T_im]
-            float v0[16], v1[16];
-            const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * q);
-            tmem_ld16(ta, v0);
-            tmem_ld16(ta + 16, v1);
-            tmem_ld_wait();
-            __syncwarp();
-            if (lane < 2 * n) {
-                const int j = lane % n;
-                const bool im = lane >= n;
-                for (int c = 0; c < 2 * n; ++c) {
-                    const float x = c < 16 ? v0[c] : v1[c - 16];
-                    if (im) Ts[j * ldT + c].y = x;
-                    else Ts[j * ldT + c].x = x;
-                }
-            }
-            __syncwarp();
-            if (w >= A.W) continue;
-            build_B_f32(n, A.ne, Ts, ldT, Bs, tab, lane);
-            __syncwarp();
-            // occupied block eliminated once for all nodes when that is stable
-            cd pf0;
-            const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
-            const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
-            const int NBr = shared ? A.NB : 1;  // the rare full eliminations run one node per round
-            cd S = cmk(0.0, 0.0);
-            for (int k0 = 0; k0 < A.nev; k0 += NBr) {
-                const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
-                               lane);
-                if (lane == 0)
-                    for (int vv = 0; vv < nb; ++vv) cfma(S, A.gamma[k0 + vv], pf[vv]);
-                __syncwarp();
-            }
-            if (lane == 0) {
-                if (shared) S = cmul(S, pf0);
-                if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
-                acc = cadd(acc, S);
-                if (A.per_pair) {
-                    const int64_t sq = A.all ? p0 + q : (int64_t)A.idx[p0 + q];
-                    A.per_pair[w * A.P + sq] = cmul(A.pref[w], S);
-                }
-            }
+            continue;  // every thread leaves through the abort check at the top
         }
         if (lane == 0 && w < A.W) A.partial[w * A.nchunks + ch] = acc;
-        fence_before_sync();
     }
-    if (abort_flag && tid == 0) {  // a wait gave up: let the copies and MMAs in flight land first
-        mbar_wait_bounded(&mbar_load, last_phase, kWaitIter);
-        mbar_wait_bounded(&mbar_mma, last_phase, kWaitIter);
+    if (abort_flag && tid == 0) {  // a wait gave up: let a copy or MMAs in flight land first
+        if (load_pending) mbar_wait_bounded(&mbar_load, phase, kWaitIter);
+        if (mma_pending) mbar_wait_bounded(&mbar_mma, phase, kWaitIter);
     }
     fence_before_sync();
     __syncthreads();
@@ -367,7 +379,7 @@ qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStrea
 
 size_t qcs_split_walker_bytes(int64_t W) { return (size_t)(W > 0 ? W : 1) * kSlabBytes; }
 
-int qcs_split_snaps_per_tile() { return kSnapsPerTile; }
+int qcs_split_snaps_per_tile(int subs) { return kSnapsPerSub * (subs > 0 ? subs : kSubPerTile); }
 
 qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st) {
     const int n = L.n;
@@ -391,9 +403,13 @@ qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, 
     A.W = L.W;
     A.P = L.P;
     A.nchunks = L.nchunks;
+    {
+        const int cs = qcs_decode_config(L.config).subs;
+        A.subs = cs > 0 ? cs : kSubPerTile;
+    }
     A.ngroups = (L.W + kWalkersPerTile - 1) / kWalkersPerTile;
     const int T = tri_count(A.m);
-    const size_t operands = (size_t)(2 * kWalkersPerTile + 2 * kSnapsPerTile) * kSlabBytes;
+    const size_t operands = (size_t)(2 * kWalkersPerTile + 2 * kSnapsPerSub) * kSlabBytes;
     const size_t tab = align16((size_t)T * sizeof(uint16_t));
     // largest node round (<= kMaxNB, balanced) whose four workspaces fit in the operand
     // region

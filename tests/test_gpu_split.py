@@ -78,3 +78,22 @@ def test_split_rejects_large_n(ctx):
         qcs.overlap(ctx, s, torch.zeros((2, n, 10), dtype=torch.complex128, device="cuda"),
                     precision=qcs.QCS_TF32X3)
     assert e.value.code == 32
+
+
+@pytest.mark.parametrize("subs", [1, 2, 3, 15])
+def test_split_tile_sizes_agree(ctx, subs):
+    """A tile spans subs sub-chunks of 4 snapshots and each warp sums its walker's pairs
+    over the tile in registers: the per-pair values do not depend on the tile size
+    (bitwise), the walker sums only through their summation order."""
+    wl = synth.Workload("t", 16, 8, 9, 157)
+    d = wl.generate(seed=8)
+    s = qcs.Snapshots(ctx, dev(d["Q"]), dev(d["b"]))
+    Phi = dev(d["Phi"])
+    o_ref, p_ref = qcs.overlap(ctx, s, Phi, per_pair=True, precision=qcs.QCS_TF32X3)
+    cfg = qcs.encode_config(tc_subtiles_per_tile=subs)
+    o, p = qcs.overlap(ctx, s, Phi, per_pair=True, precision=qcs.QCS_TF32X3, config=cfg)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert torch.equal(p, p_ref)
+    scale = p_ref.abs().sum(dim=1)
+    assert ((o - o_ref).abs() / scale).max().item() <= 1e-14
