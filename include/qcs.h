@@ -80,7 +80,11 @@ typedef enum {
     QCS_ERR_NONFINITE = 4,   /* device: a non-finite input or pivot was met */
     QCS_ERR_SINGULAR = 8,    /* device: A(z_k) singular where its inverse was needed */
     QCS_ERR_TIMEOUT = 16,    /* device: a bounded wait expired */
-    QCS_ERR_UNSUPPORTED = 32 /* request outside what the library implements */
+    QCS_ERR_UNSUPPORTED = 32,/* request outside what the library implements */
+    QCS_ERR_BOUNDS = 64      /* device, bounds-checked debug build only (compiled with
+                                -DQCS_BOUNDS, libqcs_bounds.so): a kernel found a tile, queue,
+                                snapshot or output index, or its shared-memory layout, outside
+                                the buffer it addresses; the access was skipped */
 } qcs_status;
 
 typedef enum {

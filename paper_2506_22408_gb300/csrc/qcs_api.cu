@@ -2,9 +2,13 @@
 //
 // Host-side argument checking, the per-device context and its workspace, the
 // interpolation-node plan, and the kernel launch sequence of each entry point.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <complex>
+#include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -14,14 +18,41 @@
 
 // ------------------------------------------------------------ helpers
 
+int qcs_log_level() {
+    static const int level = [] {
+        const char *e = std::getenv("QCS_LOG");
+        const int v = e ? std::atoi(e) : 0;
+        return v < 0 ? 0 : (v > 3 ? 3 : v);
+    }();
+    return level;
+}
+
+void qcs_log(int level, const char *fmt, ...) {
+    if (level > qcs_log_level()) return;
+    va_list ap;
+    va_start(ap, fmt);
+    std::fputs("[qcs] ", stderr);
+    std::vfprintf(stderr, fmt, ap);
+    std::fputc('\n', stderr);
+    va_end(ap);
+}
+
+QcsRange::QcsRange(const char *name) {
+    nvtxRangePushA(name);
+    qcs_log(2, "%s", name);
+}
+QcsRange::~QcsRange() { nvtxRangePop(); }
+
 qcs_status qcs_fail(qcs_ctx *ctx, qcs_status code, const std::string &msg) {
     if (ctx) ctx->last_error = msg;
+    qcs_log(1, "error %d: %s", (int)code, msg.c_str());
     return code;
 }
 
 qcs_status qcs_check_launch(qcs_ctx *ctx, const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return qcs_fail(ctx, QCS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    qcs_log(3, "launched %s", what);
     return QCS_OK;
 }
 
@@ -220,9 +251,12 @@ extern "C" qcs_status qcs_create(qcs_ctx **ctx, int device) {
     if (e != cudaSuccess) {
         if (c->d_status) cudaFree(c->d_status);
         delete c;
+        qcs_log(1, "qcs_create(device %d): %s", device, cudaGetErrorString(e));
         return QCS_ERR_CUDA;
     }
     *ctx = c;
+    qcs_log(2, "qcs_create(device %d): %d SMs, %zu bytes of shared memory per block", device, c->num_sms,
+            c->smem_optin);
     return QCS_OK;
 }
 
@@ -285,6 +319,7 @@ extern "C" qcs_status qcs_sync_status(qcs_ctx *ctx, void *stream) {
 
 extern "C" qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const double *d_Q, const uint8_t *d_b,
                                           qcs_snapshots **out, void *stream) {
+    QcsRange range_("qcs_build_snapshots");
     if (!ctx || !out) return QCS_ERR_ARG;
     *out = nullptr;
     if (n < 1 || n > QCS_MAX_N) return qcs_fail(ctx, QCS_ERR_ARG, "n must be in [1, QCS_MAX_N]");
@@ -443,6 +478,9 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
     wk->nparts = (split || tc) ? wk->nchunks : wk->nchunks * qcs_pair_warps_per_block();
+    qcs_log(2, "  n=%d ne=%d W=%lld P=%lld nodes=%d path=%s config=0x%x tiles of %d snapshots", n, ne, (long long)W,
+            (long long)s->P, plan->nev, split ? "split-tf32x3" : (tc ? "fp64-tensor-core" : "fp64-alu"),
+            (unsigned)wk->config, span);
     size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
     size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nparts);
@@ -471,6 +509,7 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
 
 extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                                   double *d_overlap, double *d_per_pair, const qcs_opts *opts, void *stream) {
+    QcsRange range_("qcs_overlap");
     if (!ctx) return QCS_ERR_ARG;
     if (W > 0 && !d_overlap) return qcs_fail(ctx, QCS_ERR_ARG, "null overlap output");
     DeviceGuard g(ctx->device);
@@ -517,6 +556,7 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
 
 extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_system *systems, const qcs_opts *opts,
                                           void *stream) {
+    QcsRange range_("qcs_overlap_batched");
     if (!ctx) return QCS_ERR_ARG;
     if (nsys < 1 || nsys > QCS_MAX_SYSTEMS || !systems)
         return qcs_fail(ctx, QCS_ERR_ARG, "nsys must be in [1, QCS_MAX_SYSTEMS]");
@@ -594,6 +634,7 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
 extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W,
                                        const double *d_walkers, double *d_overlap, double *d_grad,
                                        const qcs_opts *opts, void *stream) {
+    QcsRange range_("qcs_overlap_grad");
     if (!ctx) return QCS_ERR_ARG;
     if (W > 0 && (!d_overlap || !d_grad)) return qcs_fail(ctx, QCS_ERR_ARG, "null overlap or gradient output");
     if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set");
@@ -668,6 +709,7 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
 extern "C" qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int nchol, const double *d_L,
                                      const double *d_walkers, const double *d_overlap, const double *d_grad,
                                      double sqrt_dt, double *d_xbar, void *stream) {
+    QcsRange range_("qcs_force_bias");
     if (!ctx) return QCS_ERR_ARG;
     DeviceGuard g(ctx->device);
     qcs_status c = check_sizes(ctx, n, ne);

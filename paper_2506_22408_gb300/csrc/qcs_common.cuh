@@ -126,4 +126,25 @@ __device__ __forceinline__ void raise_status(unsigned *status, unsigned bits) {
     if (status) atomicOr(status, bits);
 }
 
+// Bounds checks of the debug build (-DQCS_BOUNDS): QCS_IN_BOUNDS(cond, status) is cond,
+// and a false cond raises QCS_ERR_BOUNDS in the status word (the caller then skips the
+// access; nothing traps).  In the release build the macro is the constant true and
+// the checks compile away.
+#ifdef QCS_BOUNDS
+__device__ __forceinline__ bool qcs_in_bounds(bool ok, unsigned *status) {
+    if (!ok) raise_status(status, QCS_ERR_BOUNDS);
+    return ok;
+}
+#define QCS_IN_BOUNDS(cond, status) qcs_in_bounds((cond), (status))
+#else
+#define QCS_IN_BOUNDS(cond, status) true
+#endif
+
+// Dynamic shared memory of the running launch, in bytes.
+__device__ __forceinline__ uint32_t dyn_smem_bytes() {
+    uint32_t r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }

@@ -210,6 +210,11 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
     const int bar = 1 + gid;
     const int n = A.n, n2 = 2 * n, ne = A.ne, m = A.m, T = tri_count(m);
     const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n), lx = n2 + 1;
+    // the pair table and the groups' workspaces fit the launch's shared memory
+    if (!QCS_IN_BOUNDS(T * (int)sizeof(uint16_t) <= A.tab_bytes &&
+                           (size_t)A.tab_bytes + (size_t)(blockDim.x / kGroup) * A.group_bytes <= dyn_smem_bytes(),
+                       A.status))
+        return;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
     build_pair_table(tab, T);
     __syncthreads();
@@ -252,6 +257,10 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
         const int64_t w = tile - (int64_t)ch * A.W;
         const int64_t p0 = (int64_t)ch * A.chunk;
         const int64_t p1 = p0 + A.chunk < L ? p0 + A.chunk : L;
+        if (!QCS_IN_BOUNDS(ch < A.nchunks && L >= 0 && L <= A.P, A.status)) {  // group-uniform
+            group_sync(bar);  // every thread has read the slot before it is rewritten
+            continue;
+        }
         cd So = cmk(0.0, 0.0), S1 = cmk(0.0, 0.0), S2 = cmk(0.0, 0.0);
         if (p0 < L) {
             const cd *Utw = A.Ut + w * n * n;
@@ -260,6 +269,7 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
             const cd *Kgw = A.Kg + (size_t)w * m * n2;
             for (int64_t pq = p0; pq < p1; ++pq) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+                if (!QCS_IN_BOUNDS(q >= 0 && q < A.P, A.status)) continue;  // group-uniform
                 group_sync(bar);
                 load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
                 for (int e = t; e < n * n; e += kGroup) Uts[(e / n) * lu + (e % n)] = Utw[e];
@@ -787,6 +797,7 @@ extern "C" qcs_status qcs_local_energy(qcs_ctx *ctx, const qcs_snapshots *s, int
                                        const double *d_walkers, int nchol, const double *d_L, const double *d_h,
                                        double *d_overlap, double *d_e1, double *d_e2, const qcs_opts *opts,
                                        void *stream) {
+    QcsRange range_("qcs_local_energy");
     if (!ctx) return QCS_ERR_ARG;
     if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set");
     const int n = s->n;

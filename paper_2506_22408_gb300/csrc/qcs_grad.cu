@@ -68,6 +68,11 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
     const int bar = 1 + gid;
     const int n = A.n, n2 = 2 * n, ne = A.ne, m = A.m, T = tri_count(m);
     const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
+    // the pair table and the groups' workspaces fit the launch's shared memory
+    if (!QCS_IN_BOUNDS(T * (int)sizeof(uint16_t) <= A.tab_bytes &&
+                           (size_t)A.tab_bytes + (size_t)(blockDim.x / kGroup) * A.group_bytes <= dyn_smem_bytes(),
+                       A.status))
+        return;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
     build_pair_table(tab, T);
     __syncthreads();
@@ -112,6 +117,10 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
         const int64_t w = tile - (int64_t)ch * A.W;
         const int64_t p0 = (int64_t)ch * A.chunk;
         const int64_t p1 = p0 + A.chunk < L ? p0 + A.chunk : L;
+        if (!QCS_IN_BOUNDS(ch < A.nchunks && L >= 0 && L <= A.P, A.status)) {  // group-uniform
+            group_sync(bar);  // every thread has read the slot before it is rewritten
+            continue;
+        }
         cd *out = A.partial + (w * A.nchunks + ch) * rec;
         cd Ssum = cmk(0.0, 0.0);
         for (int e = t; e < n * n; e += kGroup) Gs[e] = cmk(0.0, 0.0);
@@ -120,6 +129,7 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
             for (int e = t; e < n * n; e += kGroup) Uts[(e / n) * lu + (e % n)] = Utw[e];
             for (int64_t pq = p0; pq < p1; ++pq) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+                if (!QCS_IN_BOUNDS(q >= 0 && q < A.P, A.status)) continue;  // group-uniform
                 const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
                 const bool sp = gq && gq[0] != 0xFF;  // signed permutation: gathers instead of products
                 group_sync(bar);

@@ -75,6 +75,20 @@ struct DeviceGuard {
 // Helpers implemented in qcs_api.cu
 qcs_status qcs_fail(qcs_ctx *ctx, qcs_status code, const std::string &msg);
 qcs_status qcs_check_launch(qcs_ctx *ctx, const char *what);
+
+// Observability.  QCS_LOG (environment, read once per process) sets what goes to
+// stderr: 0 nothing (default), 1 every error message, 2 also one line per entry-point
+// call (sizes, the path and configuration chosen), 3 also one line per kernel launch.
+// QcsRange brackets an entry point in an NVTX range (header-only NVTX 3: inert unless
+// a profiler that reads NVTX is attached) and logs the call at level 2.
+int qcs_log_level();
+void qcs_log(int level, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+struct QcsRange {
+    explicit QcsRange(const char *name);
+    ~QcsRange();
+    QcsRange(const QcsRange &) = delete;
+    QcsRange &operator=(const QcsRange &) = delete;
+};
 qcs_status qcs_set_smem(qcs_ctx *ctx, const void *func, size_t bytes);
 qcs_status qcs_workspace(qcs_ctx *ctx, size_t bytes, void **out, cudaStream_t st = nullptr);
 

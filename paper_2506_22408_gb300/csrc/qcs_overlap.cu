@@ -93,6 +93,9 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     const int64_t w = tile - (int64_t)ch * A.W;
     const int64_t p0 = (int64_t)ch * span;
     const int64_t p1 = p0 + span < L ? p0 + span : L;
+    // the tile from the queue and the parity +1 count address this system's buffers
+    // (block-uniform: every thread leaves before the first barrier)
+    if (!QCS_IN_BOUNDS(tile >= 0 && ch < A.nchunks && L >= 0 && L <= A.P, A.status)) return;
     __syncthreads();  // previous tile's readers of Uts are done
     if (p0 < L) {
         const cd *Utw = A.Ut + w * n * n;
@@ -130,6 +133,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             const cd prefw = A.pref[w];
             for (int64_t pq = p0 + g; pq < p1; pq += ng) {
                 const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+                if (!QCS_IN_BOUNDS(q >= 0 && q < A.P, A.status)) continue;  // group-uniform
                 const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
                 group_sync(bar);
                 if (gq && gq[0] != 0xFF) {
@@ -186,6 +190,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
         const cd prefw = A.pref[w];
         for (int64_t pq = p0 + warp; pq < p1; pq += wpb) {
             const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
+            if (!QCS_IN_BOUNDS(q >= 0 && q < A.P, A.status)) continue;  // warp-uniform
             const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
             __syncwarp();
             if (gq && gq[0] != 0xFF) {
@@ -246,6 +251,11 @@ __global__ void __launch_bounds__(128, GRP ? 2 : 3) pair_overlap_kernel(const __
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
+    // the pair table, the walker rows and the warps' workspaces fit the launch's shared memory
+    if (!QCS_IN_BOUNDS(tri_count(B.max_m) * (int)sizeof(uint16_t) <= B.tab_bytes &&
+                           (size_t)B.tab_bytes + B.ut_bytes + (size_t)wpb * B.warp_bytes <= dyn_smem_bytes(),
+                       B.sys[0].status))
+        return;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
     build_pair_table(tab, tri_count(B.max_m));
     cd *Uts = reinterpret_cast<cd *>(smem_raw + B.tab_bytes);

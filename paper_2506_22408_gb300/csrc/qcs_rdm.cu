@@ -240,6 +240,7 @@ __global__ void rdm_finalize_kernel(int n, int64_t P, int nrow, const double *__
 
 extern "C" qcs_status qcs_shadow_rdm(qcs_ctx *ctx, const qcs_snapshots *s, const double *d_R, double *d_gam2,
                                      double *d_gam4, double *d_rdm1, double *d_npart, void *stream) {
+    QcsRange range_("qcs_shadow_rdm");
     if (!ctx) return QCS_ERR_ARG;
     if (!s) return qcs_fail(ctx, QCS_ERR_ARG, "null snapshot set");
     if (s->device != ctx->device) return qcs_fail(ctx, QCS_ERR_ARG, "snapshot set lives on another device");

@@ -173,6 +173,12 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
     float *Alo = Ahi + kWalkersPerTile * kSlabBytes / 4;
     float *Bhi = Alo + kWalkersPerTile * kSlabBytes / 4;
     float *Blo = Bhi + kSnapsPerSub * kSlabBytes / 4;
+    // operands, workspaces and the pair table fit the launch's shared memory
+    if (!QCS_IN_BOUNDS((2 * kWalkersPerTile + 2 * kSnapsPerSub) * kSlabBytes <= A.region_bytes &&
+                           kWalkersPerTile * A.warp_bytes <= A.region_bytes &&
+                           A.region_bytes + tri_count(A.m) * (int)sizeof(uint16_t) <= (int)dyn_smem_bytes(),
+                       A.status))
+        return;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw + A.region_bytes);
     build_pair_table(tab, tri_count(A.m));
     unsigned char *wbase = region + (size_t)warp * A.warp_bytes;
@@ -215,6 +221,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
         const int64_t g = t - (int64_t)ch * A.ngroups;
         const int64_t p0 = (int64_t)ch * kSnapsPerSub * A.subs;
         const int64_t w = g * kWalkersPerTile + warp;
+        if (!QCS_IN_BOUNDS(ch < A.nchunks && L >= 0 && L <= A.P, A.status)) continue;  // block-uniform
         cd acc = cmk(0.0, 0.0);
         bool ok = true;
         for (int sc = 0; sc < A.subs; ++sc) {
@@ -230,7 +237,12 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
             if (tid == 0) {
                 uint32_t bytes = 0;
                 for (int s = 0; s < kWalkersPerTile; ++s) bytes += (g * kWalkersPerTile + s < A.W) ? 2 * kSlabBytes : 0;
-                bytes += 2 * kSlabBytes * nq;
+                for (int q = 0; q < nq; ++q) {
+                    const int64_t sq = A.all ? pb + q : (int64_t)A.idx[pb + q];
+                    const bool okq = sq >= 0 && sq < A.P;  // a bad index is skipped, in both loops
+                    (void)QCS_IN_BOUNDS(okq, A.status);
+                    bytes += okq ? 2 * kSlabBytes : 0;
+                }
                 mbar_expect_tx(&mbar_load, bytes);
                 for (int s = 0; s < kWalkersPerTile; ++s) {
                     const int64_t ws = g * kWalkersPerTile + s;
@@ -240,6 +252,7 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
                 }
                 for (int q = 0; q < nq; ++q) {
                     const int64_t sq = A.all ? pb + q : (int64_t)A.idx[pb + q];
+                    if (!(sq >= 0 && sq < A.P)) continue;
                     bulk_copy(Bhi + q * kSlabBytes / 4, A.Nhi + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
                     bulk_copy(Blo + q * kSlabBytes / 4, A.Nlo + sq * (kSlabBytes / 4), kSlabBytes, &mbar_load);
                 }

@@ -160,6 +160,7 @@ __global__ void tc_snapshot_prep_kernel(int n, int64_t nslots, const cd *__restr
 struct TcArgs {
     int n, ne, m, d, nev, NB;
     int64_t W, P;
+    int64_t nrec;     // snapshot records allocated (4 list slots each)
     int nchunks;      // tiles per walker (chunks of 4 subs list positions)
     int subs;         // sub-tiles of kSnapsPerSub snapshots per tile
     int ws_bytes;     // Pfaffian workspace per warp
@@ -317,6 +318,14 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     unsigned char *Wrec = smem_tc + kSnapRecBytes;                // walker record
     const int *g_exp = reinterpret_cast<const int *>(X + kOperandBytes);              // snapshot row exponents
     const int *e_exp = reinterpret_cast<const int *>(Wrec + kSlices * kSliceBytes);  // walker row exponents
+    // the operand records, the pair table and the four workspaces fit the launch's
+    // shared memory (block-uniform: nothing is allocated or issued yet)
+    if (!QCS_IN_BOUNDS(kSnapRecBytes + kWalkRecBytes <= A.smem_tab &&
+                           A.smem_tab + tri_count(A.m) * (int)sizeof(uint16_t) <= (int)dyn_smem_bytes() &&
+                           (A.ws_in_operands ? 4 * A.ws_bytes <= kOperandBytes
+                                             : A.smem_ws + 4 * A.ws_bytes <= (int)dyn_smem_bytes()),
+                       A.status))
+        return;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_tc + A.smem_tab);
     build_pair_table(tab, tri_count(A.m));
     unsigned char *wbase = (A.ws_in_operands ? X : smem_tc + A.smem_ws) + (size_t)warp * A.ws_bytes;
@@ -375,6 +384,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
         const int ch = (int)(t / A.W);  // chunk-major: a chunk's records stay in L2 over the walkers
         const int64_t w = t - (int64_t)ch * A.W;
         const int64_t p0 = (int64_t)ch * (kSnapsPerSub * A.subs);
+        if (!QCS_IN_BOUNDS(ch < A.nchunks && L >= 0 && L <= A.P, A.status)) continue;  // block-uniform
         if (p0 >= L) {
             if (tid == 0) A.partial[w * A.nchunks + ch] = cmk(0.0, 0.0);
             continue;
@@ -384,6 +394,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
         for (int s = 0; s < A.subs; ++s) {
             const int64_t pb = p0 + (int64_t)s * kSnapsPerSub;
             if (pb >= L) break;
+            if (!QCS_IN_BOUNDS(pb / kSnapsPerSub < A.nrec, A.status)) break;  // the record to copy exists
             if (tid == 0) {
                 const uint32_t bytes = kSnapRecBytes + (s == 0 ? kWalkRecBytes : 0);
                 mbar_expect_tx(&mbar_load, bytes);
@@ -432,7 +443,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
             fence_before_sync();  // this warp's tensor-memory reads precede the next sub-tile's MMAs
             __syncwarp();
             const int64_t slot = pb + warp;
-            if (slot < L) {
+            if (slot < L && QCS_IN_BOUNDS(A.idx[slot] >= 0 && A.idx[slot] < A.P, A.status)) {
                 build_B_from_P(n, A.ne, A.m, Pu, Bs, tab, lane);
                 __syncwarp();
                 cd pf0;
@@ -554,6 +565,7 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     A.nev = L.plan.nev;
     A.W = L.W;
     A.P = L.P;
+    A.nrec = (L.P + kSnapsPerSub - 1) / kSnapsPerSub;
     A.nchunks = L.nchunks;
     A.smem_tab = kSnapRecBytes + kWalkRecBytes;
     A.smem_ws = A.smem_tab + (int)align16((size_t)tri_count(A.m) * sizeof(uint16_t));

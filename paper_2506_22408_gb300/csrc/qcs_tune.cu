@@ -43,6 +43,7 @@ extern "C" qcs_status qcs_set_config(qcs_ctx *ctx, int n, int ne, int nodes, uns
 }
 
 extern "C" qcs_status qcs_autotune(qcs_ctx *ctx, int n, int ne, int nodes, unsigned flags, int *config) {
+    QcsRange range_("qcs_autotune");
     if (!ctx) return QCS_ERR_ARG;
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return qcs_fail(ctx, QCS_ERR_ARG, "bad sizes");
     qcs_node_plan plan;

@@ -116,6 +116,7 @@ __global__ void vce_kernel(int NB, int nc, int na, int nea, int64_t W, const cd 
 extern "C" qcs_status qcs_vce_transform(qcs_ctx *ctx, int NB, int nc, int na, int nea, int64_t W,
                                         const double *d_walkers, double *d_act, int64_t act_walker_stride,
                                         int act_row_stride, double *d_factor, void *stream) {
+    QcsRange range_("qcs_vce_transform");
     if (!ctx) return QCS_ERR_ARG;
     if (nc < 0 || na < 1 || na > QCS_MAX_N || nea < 0 || nea > na || nc + nea > kMaxVceNe || NB < nc + na)
         return qcs_fail(ctx, QCS_ERR_ARG, "vce: need 0 <= nc, 1 <= na <= QCS_MAX_N, 0 <= nea <= na, "

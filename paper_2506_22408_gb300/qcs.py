@@ -30,6 +30,7 @@ QCS_FLAG_FP64_ALU = 4
 QCS_FLAG_FP64_TC = 8
 MAX_NODES = 49
 QCS_ERR_ARG, QCS_ERR_CUDA, QCS_ERR_NONFINITE, QCS_ERR_SINGULAR, QCS_ERR_TIMEOUT, QCS_ERR_UNSUPPORTED = 1, 2, 4, 8, 16, 32
+QCS_ERR_BOUNDS = 64
 STATUS_BITS = {1: "ARG", 2: "CUDA", 4: "NONFINITE", 8: "SINGULAR", 16: "TIMEOUT", 32: "UNSUPPORTED"}
 
 EXPORTED = [
