@@ -21,7 +21,10 @@
 //
 // Tiles: one walker and 4 subs consecutive parity +1 snapshots (subs sub-tiles of four,
 // 8 by default, tuned by qcs_autotune);
-// a block of four warps owns a tile, warp i the pair of snapshot i of each sub-tile.
+// a team of four warps owns a tile, warp i the pair of snapshot i of each sub-tile, and
+// a block (one per SM) runs three teams that share the SM's tensor memory as two
+// 256-column accumulators, each held from the first product of a sub-tile to the end
+// of the readout of P.
 //  1. bulk copies bring the four snapshots' H slices (the A operand, M = 128 rows)
 //     and, once per tile, the walker's M slices (the B operand, N = 32) into shared
 //     memory;
@@ -50,6 +53,9 @@ namespace {
 constexpr int kSnapsPerSub = 4;                               // M = 128 rows of the first product
 constexpr int kSubPerTile = 8;                                // default sub-tiles per tile: 32 snapshots
 constexpr uint32_t kTmemCols = 256;                           // 7 levels x 32 columns, power of two
+constexpr int kTeamThreads = 128;                             // a team: four warps, one per lane quarter
+constexpr int kMaxTeams = 3;                                  // teams per block (one block per SM)
+constexpr uint32_t kTmemSlots = 2;                            // 256-column accumulators per block
 constexpr uint32_t kWaitIter = 1u << 26;                      // bounded mbarrier waits
 constexpr int kSnapSlab = kSnapsPerSub * kSliceBytes;         // one slice of 4 snapshots: 8 KB
 constexpr int kSnapRecBytes = kSlices * kSnapSlab + kSnapsPerSub * kRowsPer * 4;  // + row exponents
@@ -165,9 +171,12 @@ struct TcArgs {
     int subs;         // sub-tiles of kSnapsPerSub snapshots per tile
     int ws_bytes;     // Pfaffian workspace per warp
     int ws_in_operands;  // 1: the workspaces are quarters of the operand region
+    int teams;        // four-warp teams in the block
+    int team_bytes;   // shared bytes per team: records (and workspaces if not in them)
+    int tslots;       // tensor-memory accumulators of 256 columns
     int off_P, off_N, off_U, off_V, off_pf, off_act, off_pv;  // B^(s) at offset 0
     int vm;
-    int smem_tab, smem_ws;  // byte offsets of the pair table and (if separate) the workspaces
+    int smem_tab;     // byte offset of the pair table (after the teams' regions)
     const unsigned char *snap_rec;
     const unsigned char *walk_rec;
     const cd *pref;
@@ -305,30 +314,59 @@ __device__ __forceinline__ int slice_zt(uint32_t tlane, int gk, int eb_lane, uns
     return (Gl != kNoRow && eb_lane != kNoRow) ? eb_lane + Gl - 56 : kNoRow;
 }
 
-__global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__ TcArgs A) {
+// Team barrier (named barrier 1 + team over the team's 128 threads) and the same
+// barrier with an AND over a predicate, so that every thread of a team takes the same
+// branch after a bounded wait.
+__device__ __forceinline__ void team_sync(int team) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "n"(kTeamThreads) : "memory");
+}
+__device__ __forceinline__ bool team_and(int team, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1 + team), "n"(kTeamThreads)
+        : "memory");
+    return r != 0;
+}
+
+// One block per SM holds up to kMaxTeams teams of four warps.  Each team has its own
+// operand records (and, in them, its warps' Pfaffian workspaces) and runs the tile loop
+// of the header on its own: a team is what a block of four warps would be, except that
+// the tensor memory of the SM (512 columns) is shared as two 256-column accumulators.
+// A team holds one from its first product of a sub-tile to the end of the readout of
+// P (a bounded spin on a lock word in shared memory), so three teams, twelve warps per
+// SM, keep the FP64 pipe fed while the tensor memory would only allow two blocks of four.
+__global__ void __launch_bounds__(kTeamThreads * kMaxTeams, 1) tc_pair_kernel(const __grid_constant__ TcArgs A) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mbar_load, mbar_mma;
-    __shared__ long long next_tile;
+    __shared__ __align__(8) uint64_t mbar_load[kMaxTeams], mbar_mma[kMaxTeams];
+    __shared__ long long next_tile[kMaxTeams];
+    __shared__ int slot_of[kMaxTeams];
+    __shared__ int slot_owner[kTmemSlots];
     __shared__ int abort_flag;
-    __shared__ cd red[4];
+    __shared__ cd red[kMaxTeams][4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int team = warp >> 2, wt = warp & 3, ttid = tid & (kTeamThreads - 1);
     const int n = A.n;
-    unsigned char *X = smem_tc;                                   // operands, then (usually) workspaces
-    unsigned char *Wrec = smem_tc + kSnapRecBytes;                // walker record
+    unsigned char *X = smem_tc + (size_t)team * A.team_bytes;     // operands, then (usually) workspaces
+    unsigned char *Wrec = X + kSnapRecBytes;                      // walker record
     const int *g_exp = reinterpret_cast<const int *>(X + kOperandBytes);              // snapshot row exponents
     const int *e_exp = reinterpret_cast<const int *>(Wrec + kSlices * kSliceBytes);  // walker row exponents
-    // the operand records, the pair table and the four workspaces fit the launch's
-    // shared memory (block-uniform: nothing is allocated or issued yet)
-    if (!QCS_IN_BOUNDS(kSnapRecBytes + kWalkRecBytes <= A.smem_tab &&
+    // the teams' records, their workspaces and the pair table fit the launch's shared
+    // memory, and the block is a whole number of teams (block-uniform: nothing is
+    // allocated or issued yet)
+    if (!QCS_IN_BOUNDS((int)blockDim.x == kTeamThreads * A.teams && A.teams <= kMaxTeams &&
+                           A.tslots >= 1 && A.tslots <= (int)kTmemSlots &&
+                           A.teams * A.team_bytes <= A.smem_tab &&
                            A.smem_tab + tri_count(A.m) * (int)sizeof(uint16_t) <= (int)dyn_smem_bytes() &&
                            (A.ws_in_operands ? 4 * A.ws_bytes <= kOperandBytes
-                                             : A.smem_ws + 4 * A.ws_bytes <= (int)dyn_smem_bytes()),
+                                             : kSnapRecBytes + kWalkRecBytes + 4 * A.ws_bytes <= A.team_bytes),
                        A.status))
         return;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_tc + A.smem_tab);
     build_pair_table(tab, tri_count(A.m));
-    unsigned char *wbase = (A.ws_in_operands ? X : smem_tc + A.smem_ws) + (size_t)warp * A.ws_bytes;
+    unsigned char *wbase = (A.ws_in_operands ? X : X + kSnapRecBytes + kWalkRecBytes) + (size_t)wt * A.ws_bytes;
     cd *Bs = reinterpret_cast<cd *>(wbase);
     double *Pu = reinterpret_cast<double *>(wbase + A.off_P);
     cd *Ns = reinterpret_cast<cd *>(wbase + A.off_N);  // aliases Pu: written once B^(s) is assembled
@@ -340,33 +378,37 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
     cd *pv = reinterpret_cast<cd *>(wbase + A.off_pv);
 
     if (warp == 0) {
-        tmem_alloc(&tmem_base, kTmemCols);
+        tmem_alloc(&tmem_base, (uint32_t)A.tslots * kTmemCols);
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&mbar_load, 1);
-        mbar_init(&mbar_mma, 1);
+        for (int k = 0; k < kMaxTeams; ++k) {
+            mbar_init(&mbar_load[k], 1);
+            mbar_init(&mbar_mma[k], 1);
+        }
+        for (int k = 0; k < (int)kTmemSlots; ++k) slot_owner[k] = -1;
         abort_flag = 0;
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tbase = tmem_base;
-    const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+    const uint32_t tmem0 = tmem_base;
     const int64_t L = *A.d_count;
     const int64_t ntiles = A.W * (int64_t)A.nchunks;
     uint32_t ph_load = 0, ph_mma = 0;
     bool load_pending = false, mma_pending = false;
     bool ok = true;
-    // one sliced product issued by thread 0, then a bounded wait whose outcome the block shares
-    auto product = [&](bool mn) {
-        if (tid == 0) {
+    int held = -1;  // tensor-memory slot this team holds
+    // one sliced product issued by the team's first thread into the held slot, then a
+    // bounded wait whose outcome the team shares
+    auto product = [&](bool mn, uint32_t tbase) {
+        if (ttid == 0) {
             fence_after_sync();
             issue_products(tbase, X, Wrec, mn);
-            mma_commit(&mbar_mma);
+            mma_commit(&mbar_mma[team]);
         }
         mma_pending = true;
-        const bool r = __syncthreads_and(mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter));
+        const bool r = team_and(team, mbar_wait_bounded(&mbar_mma[team], ph_mma, kWaitIter));
         if (r) {
             ph_mma ^= 1u;
             mma_pending = false;
@@ -374,19 +416,47 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
         }
         return r;
     };
+    // a free accumulator slot for the team (bounded spin), shared with the team
+    auto acquire = [&]() {
+        if (ttid == 0) {
+            int got = -1;
+            for (uint32_t it = 0; it < kWaitIter && got < 0; ++it) {
+                if (*(volatile int *)&abort_flag) break;
+                for (int k = 0; k < A.tslots && got < 0; ++k)
+                    if (atomicCAS(&slot_owner[k], -1, team) == -1) got = k;
+                if (got < 0) __nanosleep(64);
+            }
+            __threadfence_block();
+            slot_of[team] = got;
+        }
+        team_sync(team);
+        held = slot_of[team];
+        return team_and(team, held >= 0);
+    };
+    // every warp's tensor-memory reads of the slot are done: hand it back
+    auto release = [&]() {
+        fence_before_sync();
+        team_sync(team);
+        if (ttid == 0 && held >= 0) {
+            __threadfence_block();
+            atomicExch(&slot_owner[held], -1);
+        }
+        held = -1;
+    };
     for (;;) {
         fence_proxy_async_smem();  // generic writes to the operand region precede the next bulk copies
-        __syncthreads();
-        if (tid == 0) next_tile = abort_flag ? (long long)ntiles : (long long)atomicAdd(A.counter, 1ull);
-        __syncthreads();
-        const int64_t t = next_tile;
+        team_sync(team);
+        if (ttid == 0)
+            next_tile[team] = *(volatile int *)&abort_flag ? (long long)ntiles : (long long)atomicAdd(A.counter, 1ull);
+        team_sync(team);
+        const int64_t t = next_tile[team];
         if (t >= ntiles) break;
         const int ch = (int)(t / A.W);  // chunk-major: a chunk's records stay in L2 over the walkers
         const int64_t w = t - (int64_t)ch * A.W;
         const int64_t p0 = (int64_t)ch * (kSnapsPerSub * A.subs);
-        if (!QCS_IN_BOUNDS(ch < A.nchunks && L >= 0 && L <= A.P, A.status)) continue;  // block-uniform
+        if (!QCS_IN_BOUNDS(ch < A.nchunks && L >= 0 && L <= A.P, A.status)) continue;  // team-uniform
         if (p0 >= L) {
-            if (tid == 0) A.partial[w * A.nchunks + ch] = cmk(0.0, 0.0);
+            if (ttid == 0) A.partial[w * A.nchunks + ch] = cmk(0.0, 0.0);
             continue;
         }
         const cd prefw = A.pref[w];
@@ -395,26 +465,31 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
             const int64_t pb = p0 + (int64_t)s * kSnapsPerSub;
             if (pb >= L) break;
             if (!QCS_IN_BOUNDS(pb / kSnapsPerSub < A.nrec, A.status)) break;  // the record to copy exists
-            if (tid == 0) {
+            if (ttid == 0) {
                 const uint32_t bytes = kSnapRecBytes + (s == 0 ? kWalkRecBytes : 0);
-                mbar_expect_tx(&mbar_load, bytes);
-                bulk_copy(X, A.snap_rec + (size_t)(pb / kSnapsPerSub) * kSnapRecBytes, kSnapRecBytes, &mbar_load);
-                if (s == 0) bulk_copy(Wrec, A.walk_rec + (size_t)w * kWalkRecBytes, kWalkRecBytes, &mbar_load);
+                mbar_expect_tx(&mbar_load[team], bytes);
+                bulk_copy(X, A.snap_rec + (size_t)(pb / kSnapsPerSub) * kSnapRecBytes, kSnapRecBytes,
+                          &mbar_load[team]);
+                if (s == 0) bulk_copy(Wrec, A.walk_rec + (size_t)w * kWalkRecBytes, kWalkRecBytes, &mbar_load[team]);
             }
             load_pending = true;
-            ok = __syncthreads_and(mbar_wait_bounded(&mbar_load, ph_load, kWaitIter));
+            ok = team_and(team, mbar_wait_bounded(&mbar_load[team], ph_load, kWaitIter));
             if (!ok) break;
             ph_load ^= 1u;
             load_pending = false;
-            // ---- Z_i = H_i M^T: lane k holds row k; sliced by rows of Z_i^T (MN-major)
-            if (!(ok = product(false))) break;
+            if (!(ok = acquire())) break;
+            fence_after_sync();
+            const uint32_t tbase = tmem0 + (uint32_t)held * kTmemCols;
+            const uint32_t tlane = tbase + ((uint32_t)(32 * wt) << 16);  // this warp's 32 lanes
+            // ---- Z_i = H_i M^T: lane k holds row k; sliced by rows of Z^T (MN-major)
+            if (!(ok = product(false, tbase))) break;
             // the operand region held H_i, which the completed MMAs no longer read
-            const int Fb = slice_zt(tlane, g_exp[warp * kRowsPer + lane], e_exp[lane], X, warp * kRowsPer, lane);
+            const int Fb = slice_zt(tlane, g_exp[wt * kRowsPer + lane], e_exp[lane], X, wt * kRowsPer, lane);
             fence_proxy_async_smem();
             fence_before_sync();
-            __syncthreads();  // every warp's tensor-memory reads and operand writes are done
+            team_sync(team);  // every warp's tensor-memory reads and operand writes are done
             // ---- P_i = M Z_i: lane b, column a holds P_i[a][b] = z 2^{e_a + F_b - 56}
-            if (!(ok = product(true))) break;
+            if (!(ok = product(true, tbase))) break;
 #pragma unroll 1
             for (int cb = 0; cb < 4; ++cb) {
                 long long z[8];
@@ -440,9 +515,8 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
                     }
                 }
             }
-            fence_before_sync();  // this warp's tensor-memory reads precede the next sub-tile's MMAs
-            __syncwarp();
-            const int64_t slot = pb + warp;
+            release();  // this team's tensor-memory reads are done; another team may use the slot
+            const int64_t slot = pb + wt;
             if (slot < L && QCS_IN_BOUNDS(A.idx[slot] >= 0 && A.idx[slot] < A.P, A.status)) {
                 build_B_from_P(n, A.ne, A.m, Pu, Bs, tab, lane);
                 __syncwarp();
@@ -453,8 +527,7 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
                 cd S = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                     const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
-                                   lane);
+                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv, lane);
                     if (lane == 0)
                         for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
                     __syncwarp();
@@ -467,27 +540,29 @@ __global__ void __launch_bounds__(128, 2) tc_pair_kernel(const __grid_constant__
                 }
             }
             fence_proxy_async_smem();  // workspace writes precede the next sub-tile's bulk copy
-            __syncthreads();
+            team_sync(team);
         }
         if (!ok) {
-            if (tid == 0) {
-                abort_flag = 1;
+            if (ttid == 0) {
+                atomicExch(&abort_flag, 1);
                 raise_status(A.status, QCS_ERR_TIMEOUT);
             }
-            continue;  // every thread leaves through the abort check at the top
+            // a held slot stays held: MMAs that missed their wait may still write it, and
+            // the other teams stop at the abort flag instead of waiting for it
+            continue;  // every thread of the team leaves through the abort check at the top
         }
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
-        if (tid == 0) A.partial[w * A.nchunks + ch] = cadd(cadd(red[0], red[1]), cadd(red[2], red[3]));
+        if (lane == 0) red[team][wt] = acc;
+        team_sync(team);
+        if (ttid == 0) A.partial[w * A.nchunks + ch] = cadd(cadd(red[team][0], red[team][1]), cadd(red[team][2], red[team][3]));
     }
-    if (abort_flag && tid == 0) {  // a wait gave up: let a copy or MMAs in flight land first
-        if (load_pending) mbar_wait_bounded(&mbar_load, ph_load, kWaitIter);
-        if (mma_pending) mbar_wait_bounded(&mbar_mma, ph_mma, kWaitIter);
+    if (ttid == 0 && (load_pending || mma_pending)) {  // a wait gave up: let a copy or MMAs in flight land first
+        if (load_pending) mbar_wait_bounded(&mbar_load[team], ph_load, kWaitIter);
+        if (mma_pending) mbar_wait_bounded(&mbar_mma[team], ph_mma, kWaitIter);
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (warp == 0) tmem_dealloc(tbase, kTmemCols);
+    if (warp == 0) tmem_dealloc(tmem0, (uint32_t)A.tslots * kTmemCols);
 }
 
 // Pfaffian workspace of one warp for nb node matrices: B^(s), then the upper triangle
@@ -567,8 +642,6 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     A.P = L.P;
     A.nrec = (L.P + kSnapsPerSub - 1) / kSnapsPerSub;
     A.nchunks = L.nchunks;
-    A.smem_tab = kSnapRecBytes + kWalkRecBytes;
-    A.smem_ws = A.smem_tab + (int)align16((size_t)tri_count(A.m) * sizeof(uint16_t));
     // node matrices per round: the requested count, or the largest balanced count whose
     // four workspaces fit in the operand region; when even one node per round does not
     // fit there (large m), the workspaces get their own shared memory
@@ -593,7 +666,17 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     A.NB = NB;
     A.ws_in_operands = fits(NB) ? 1 : 0;
     A.ws_bytes = (int)tc_warp_layout(A, NB);
-    const size_t smem = (size_t)A.smem_ws + (A.ws_in_operands ? 0 : 4 * (size_t)A.ws_bytes);
+    // teams per block: as many as the block's shared memory holds (about 1 KB kept for
+    // the static words), at most kMaxTeams; one block per SM
+    A.team_bytes = kSnapRecBytes + kWalkRecBytes + (A.ws_in_operands ? 0 : 4 * A.ws_bytes);
+    const size_t tab = align16((size_t)tri_count(A.m) * sizeof(uint16_t));
+    int teams = (int)((ctx->smem_optin - 1024 - tab) / (size_t)A.team_bytes);
+    if (teams > kMaxTeams) teams = kMaxTeams;
+    if (teams < 1) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tc kernel: shared memory");
+    A.teams = teams;
+    A.tslots = teams >= 2 ? 2 : 1;
+    A.smem_tab = teams * A.team_bytes;
+    const size_t smem = (size_t)A.smem_tab + tab;
     A.snap_rec = (const unsigned char *)L.s->tc_rec;
     A.walk_rec = walk_rec;
     A.pref = L.pref;
@@ -609,20 +692,18 @@ qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned 
     }
     if (smem + 1024 > ctx->smem_optin) return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "tc kernel: shared memory");
     if (qcs_set_smem(ctx, (const void *)tc_pair_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
-    // blocks per SM: what shared memory allows (static words and the 1 KB the driver
-    // reserves per block included), and at most 512 / kTmemCols so that every block's
-    // tensor-memory allocation is granted at once
-    int per_sm = (int)(ctx->smem_per_sm / (smem + 1024 + 1024));
-    if (per_sm > (int)(512 / kTmemCols)) per_sm = (int)(512 / kTmemCols);
-    if (per_sm < 1) per_sm = 1;
+    // one block per SM (its shared memory and its 2 x 256 tensor-memory columns take the
+    // SM), fewer when there are fewer tiles than teams
     const int64_t ntiles = A.W * (int64_t)A.nchunks;
-    int64_t blocks = (int64_t)ctx->num_sms * per_sm;
-    if (blocks > ntiles) blocks = ntiles;
+    int64_t blocks = (int64_t)ctx->num_sms;
+    if (blocks > (ntiles + teams - 1) / teams) blocks = (ntiles + teams - 1) / teams;
     if (blocks < 1) blocks = 1;
     if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return qcs_fail(ctx, QCS_ERR_CUDA, "tc tile counter reset");
+    qcs_log(3, "tc_pair_kernel: %lld blocks x %d teams, %zu bytes of shared memory, %d tensor-memory slots",
+            (long long)blocks, teams, smem, A.tslots);
     qcs_prof_begin(ctx, st);
-    tc_pair_kernel<<<(unsigned)blocks, 128, smem, st>>>(A);
+    tc_pair_kernel<<<(unsigned)blocks, kTeamThreads * teams, smem, st>>>(A);
     qcs_prof_end(ctx, st);
     return qcs_check_launch(ctx, "tc_pair_kernel");
 }
