@@ -89,11 +89,14 @@ typedef enum {
 
 typedef enum {
     QCS_FP64 = 0,  /* every product and the Pfaffians in FP64 */
-    QCS_TF32X3 = 1 /* qcs_overlap only, n <= 16: the congruence T = U^T Qt^T on tensor cores
-                      (tcgen05 kind::tf32, hi/lo splits, hi*hi + hi*lo + lo*hi accumulated in
-                      FP32), B^(s) in FP32; Pfaffians, pivoting and node sums in FP64.  The
-                      snapshot set gets TF32 operand slabs (8 KB per snapshot, allocated with
-                      cudaMalloc) on its first use in this mode. */
+    QCS_TF32X3 = 1 /* qcs_overlap only, any n <= QCS_MAX_N: the congruence T = U^T Qt^T on
+                      tensor cores (tcgen05 kind::tf32, hi/lo splits, hi*hi + hi*lo + lo*hi
+                      accumulated in FP32), B^(s) in FP32; Pfaffians, pivoting and node sums in
+                      FP64.  Rows and the contraction are padded to 32 for n <= 16 (tiles of 4
+                      walkers x 4 snapshots, a warp per pair) and to 64 x 48 for 16 < n <= 24
+                      (2 x 2 tiles, two warps per pair).  The snapshot set gets TF32 operand
+                      slabs (8 KB per snapshot for n <= 16, 24 KB above, from the context's
+                      allocator) on its first use in this mode. */
 } qcs_precision;
 
 /* qcs_opts.flags */

@@ -457,8 +457,6 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     if (opts) o = *opts;
     if (o.precision != QCS_FP64 && o.precision != QCS_TF32X3)
         return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "unknown precision mode");
-    if (o.precision == QCS_TF32X3 && n > 16)
-        return qcs_fail(ctx, QCS_ERR_UNSUPPORTED, "split precision supports n <= 16");
     if (qcs_make_node_plan(n, ne, o.nodes, o.flags, plan) != QCS_OK)
         return qcs_fail(ctx, QCS_ERR_ARG, "nodes must be 0 or in [n-ne+1, QCS_MAX_NODES]");
     const bool split = o.precision == QCS_TF32X3;
@@ -473,7 +471,7 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     wk->chunk = cfg.chunk > 0 ? cfg.chunk : kChunk;
     // partial sums: FP64 ALU path one per (walker, tile, warp); split path one per
     // (walker, tile of snapshots); tensor-core path one per (walker, tile)
-    const int span = split ? qcs_split_snaps_per_tile(cfg.subs) : tc ? qcs_tc_snaps_per_tile(cfg.subs)
+    const int span = split ? qcs_split_snaps_per_tile(n, cfg.subs) : tc ? qcs_tc_snaps_per_tile(cfg.subs)
                                                              : wk->chunk * qcs_pair_warps_per_block();
     wk->nchunks = (int)((s->P + span - 1) / span);
     if (wk->nchunks < 1) wk->nchunks = 1;
@@ -484,7 +482,7 @@ qcs_status overlap_common(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t 
     size_t b_ut = align16(sizeof(cd) * (size_t)W * n * n);
     size_t b_pref = align16(sizeof(cd) * (size_t)W);
     size_t b_part = align16(sizeof(cd) * (size_t)W * wk->nparts);
-    size_t b_slab = split ? align16(qcs_split_walker_bytes(W)) : 0;
+    size_t b_slab = split ? align16(qcs_split_walker_bytes(n, W)) : 0;
     size_t b_rec = tc ? align16(qcs_tc_walker_bytes(W)) : 0;
     size_t b_mode = (split || tc) ? 0 : align16(sizeof(int) * (size_t)(W > 0 ? W : 1));
     void *base = nullptr;

@@ -180,8 +180,8 @@ qcs_status qcs_launch_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, cudaStream_t
 int qcs_pair_warps_per_block();  // partial sums per overlap tile
 // Split precision (qcs_split.cu)
 qcs_status qcs_split_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
-size_t qcs_split_walker_bytes(int64_t W);
-int qcs_split_snaps_per_tile(int subs);  // snapshots per split-precision tile (subs sub-chunks; 0 = default)
+size_t qcs_split_walker_bytes(int n, int64_t W);
+int qcs_split_snaps_per_tile(int n, int subs);  // snapshots per split-precision tile (subs sub-chunks; 0 = default)
 qcs_status qcs_launch_split(qcs_ctx *ctx, const qcs_pair_launch &L, float *Mhi, float *Mlo, cudaStream_t st);
 // FP64-accurate congruence on tensor cores (qcs_tcpair.cu)
 bool qcs_tc_supported(int n);      // n <= 16

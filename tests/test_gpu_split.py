@@ -34,7 +34,8 @@ def dev(a):
 
 
 @pytest.mark.parametrize("n,ne,W,P", [(16, 8, 13, 91), (16, 4, 6, 40), (12, 6, 7, 45), (8, 4, 9, 61), (10, 4, 5, 23),
-                                      (16, 16, 5, 30)])
+                                      (16, 16, 5, 30), (20, 10, 5, 31), (24, 12, 3, 23), (17, 6, 4, 19),
+                                      (24, 2, 3, 17), (22, 22, 2, 9)])
 def test_split_matches_oracle_within_bound(ctx, n, ne, W, P):
     rng = np.random.default_rng(3000 + 10 * n + ne)
     Q = synth.haar_orthogonal(rng, 2 * n, P)
@@ -70,14 +71,23 @@ def test_split_agrees_with_fp64_path_and_is_deterministic(ctx):
     assert ((o1 - o64).abs() / scale).max().item() <= BOUND
 
 
-def test_split_rejects_large_n(ctx):
-    n = 20
-    Q = torch.from_numpy(synth.haar_orthogonal(np.random.default_rng(0), 2 * n, 4)).cuda()
-    s = qcs.Snapshots(ctx, Q, torch.zeros((4, n), dtype=torch.uint8, device="cuda"))
-    with pytest.raises(qcs.QCSError) as e:
-        qcs.overlap(ctx, s, torch.zeros((2, n, 10), dtype=torch.complex128, device="cuda"),
-                    precision=qcs.QCS_TF32X3)
-    assert e.value.code == 32
+def test_split_above_16_modes_uses_the_group_kernel(ctx):
+    """16 < n <= 24 runs on the 64-row, K = 48 tiles (two walkers x two snapshots per
+    MMA, one 64-thread group per walker): per-pair values are bitwise independent of the
+    tile size, as for n <= 16."""
+    wl = synth.Workload("t", 20, 10, 5, 37)
+    d = wl.generate(seed=9)
+    s = qcs.Snapshots(ctx, dev(d["Q"]), dev(d["b"]))
+    Phi = dev(d["Phi"])
+    o1, p1 = qcs.overlap(ctx, s, Phi, per_pair=True, precision=qcs.QCS_TF32X3)
+    o2, p2 = qcs.overlap(ctx, s, Phi, per_pair=True, precision=qcs.QCS_TF32X3,
+                         config=qcs.encode_config(tc_subtiles_per_tile=3))
+    o64, p64 = qcs.overlap(ctx, s, Phi, per_pair=True)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert torch.equal(p1, p2)
+    scale = p64.abs().mean(dim=1)
+    assert ((o1 - o64).abs() / scale).max().item() <= BOUND
 
 
 @pytest.mark.parametrize("subs", [1, 2, 3, 15])
