@@ -352,6 +352,19 @@ def run_batch(args, ctx, dev, barrier, ws):
         torch.cuda.synchronize()
         ms1, _ = ctx.profile_read()
         per_sys.append({"n": wl.n, "pairs_per_s_alone": wl.W * wl.P / (ms1 * 1e-3), "kernel_ms_alone": ms1})
+    # the same systems in split precision (QCS_TF32X3, one qcs_overlap per system; n = 20
+    # and 24 on the 64-row tiles), against the FP64 batched results of the same walkers
+    split_rows, split_ms = [], 0.0
+    for (wl, s, w), o_ref in zip(systems, outs):
+        qcs.overlap(ctx, s, w, precision=qcs.QCS_TF32X3)  # builds the snapshot slabs once
+        torch.cuda.synchronize()
+        ctx.profile_read()
+        o_split, _ = qcs.overlap(ctx, s, w, precision=qcs.QCS_TF32X3)
+        torch.cuda.synchronize()
+        ms1, _ = ctx.profile_read()
+        split_ms += ms1
+        split_rows.append({"n": wl.n, "pairs_per_s": wl.W * wl.P / (ms1 * 1e-3), "kernel_ms": ms1,
+                           "walker_rel_diff_vs_fp64_max": float(((o_split - o_ref).abs() / o_ref.abs()).max().item())})
     ctx.profile(False)
     assert ctx.sync_status() == 0
     kach = flops_step / (kms * 1e-3) / 1e12
@@ -373,6 +386,8 @@ def run_batch(args, ctx, dev, barrier, ws):
                                          "unit": "TFLOP/s", "frac": kach / FP64_PEAK_TFLOPS,
                                          "timing": "one batched launch outside the graph, events on its stream"}},
             "systems_alone": per_sys,
+            "split_precision": {"systems": split_rows, "pairs_per_s_all": pairs_step / (split_ms * 1e-3),
+                                "timing": "split kernel per system, events on its stream (no graph)"},
             "gpu_launches_per_step": 5 + 1 + 5}
 
 
