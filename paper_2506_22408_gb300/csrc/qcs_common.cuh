@@ -98,6 +98,15 @@ __device__ __forceinline__ cd skew_get(const cd *__restrict__ N, int i, int j) {
     return flip_if(N[(b * (b - 1)) / 2 + a], lo);
 }
 
+// The same with the diagonal (i == j) read as zero, without a branch: the diagonal
+// reads entry 0 and selects zero.
+__device__ __forceinline__ cd skew_get0(const cd *__restrict__ N, int i, int j) {
+    const bool lo = i > j, diag = i == j;
+    const int a = lo ? j : i, b = lo ? i : j;
+    const cd x = flip_if(N[diag ? 0 : (b * (b - 1)) / 2 + a], lo);
+    return diag ? make_double2(0.0, 0.0) : x;
+}
+
 // Pivot magnitude key without floating-point work: the high 32 bits of
 // max(|re|, |im|) (sign, exponent and 20 mantissa bits) order magnitudes to a
 // relative 2^-20, enough for partial pivoting.  NaN/Inf give the largest keys.

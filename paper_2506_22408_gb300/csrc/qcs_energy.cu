@@ -80,7 +80,7 @@ __device__ inline void build_Sacc(int n, int m, const cd *__restrict__ Kw, const
         const cd *kr = Kw + a * n2;
         cd s = cmk(0.0, 0.0);
         for (int mu = 0; mu < n2; ++mu)
-            if (mu != nu) cfma(s, kr[mu], mu < nu ? Lp[tri_index(mu, nu)] : cneg(Lp[tri_index(nu, mu)]));
+            cfma(s, kr[mu], skew_get0(Lp, mu, nu));  // the diagonal is zero
         Pm[a * lx + nu] = s;
     }
     group_sync(bar);
@@ -430,15 +430,20 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                                         const double *zs = zsm + v * Tn;
                                         double p1 = 0.0, p2 = 0.0, p3 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
                                         for (int c = 0; c < d2; ++c) {
-                                            if (c == a || c == b) continue;
-                                            // Z(a,c) G(c,b) and Z(b,c) G(c,a) from the packed upper triangles
-                                            const int iz = a < c ? tri_index(a, c) : tri_index(c, a);
-                                            const int ig = c < b ? tri_index(c, b) : tri_index(b, c);
-                                            const int jz = b < c ? tri_index(b, c) : tri_index(c, b);
-                                            const int jg = c < a ? tri_index(c, a) : tri_index(a, c);
+                                            // Z(a,c) G(c,b) and Z(b,c) G(c,a) from the packed upper
+                                            // triangles; c = a or c = b adds nothing (a zero diagonal),
+                                            // taken by selects so that no lane branches
+                                            const bool skip = c == a || c == b;
+                                            const int iz = skip ? 0 : (a < c ? tri_index(a, c) : tri_index(c, a));
+                                            const int ig = skip ? 0 : (c < b ? tri_index(c, b) : tri_index(b, c));
+                                            const int jz = skip ? 0 : (b < c ? tri_index(b, c) : tri_index(c, b));
+                                            const int jg = skip ? 0 : (c < a ? tri_index(c, a) : tri_index(a, c));
                                             const bool s1 = (a > c) != (c > b), s2 = (b > c) != (c > a);
-                                            const cd z1 = flip_if(Zv[iz], s1), z2 = flip_if(Zv[jz], s2);
-                                            const double w1 = s1 ? -zs[iz] : zs[iz], w2 = s2 ? -zs[jz] : zs[jz];
+                                            const cd zero = cmk(0.0, 0.0);
+                                            const cd z1 = skip ? zero : flip_if(Zv[iz], s1);
+                                            const cd z2 = skip ? zero : flip_if(Zv[jz], s2);
+                                            const double w1 = skip ? 0.0 : __longlong_as_double(__double_as_longlong(zs[iz]) ^ (s1 ? (long long)0x8000000000000000ull : 0ll));
+                                            const double w2 = skip ? 0.0 : __longlong_as_double(__double_as_longlong(zs[jz]) ^ (s2 ? (long long)0x8000000000000000ull : 0ll));
                                             const cd g1 = Gp[ig], g2 = Gp[jg];
                                             p1 = fma(z1.x, g1.x, p1);
                                             p2 = fma(z1.y, g1.y, p2);
@@ -450,9 +455,9 @@ __global__ void __launch_bounds__(128, 2) energy_pair_kernel(const __grid_consta
                                         pab = cmk(p1 - p2, p3 - p1 - p2);
                                         pba = cmk(q1 - q2, q3 - q1 - q2);
                                     } else {
-                                        for (int c = 0; c < d2; ++c) {
-                                            if (c != a && c != b) cfma(pab, skew_get(Zv, a, c), skew_get(Gp, c, b));
-                                            if (c != b && c != a) cfma(pba, skew_get(Zv, b, c), skew_get(Gp, c, a));
+                                        for (int c = 0; c < d2; ++c) {  // zero diagonals: c = a, b add nothing
+                                            cfma(pab, skew_get0(Zv, a, c), skew_get0(Gp, c, b));
+                                            cfma(pba, skew_get0(Zv, b, c), skew_get0(Gp, c, a));
                                         }
                                     }
                                     const cd pr = cmul(pab, pba);

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                         double x = (r & 1) ? -tt.y : tt.x;
                         crfma(acc, skew_at(Ys, a, ne + r), x);
                     }
-                    GX[e] = neg ? cneg(acc) : acc;
+                    GX[e] = flip_if(acc, neg);
                 }
                 group_sync(bar);
                 // empty rows: Ht_i = G[ne+2i] - i G[ne+2i+1] into row ne+2i (factor 1/2 applied at the end)
@@ -387,7 +387,7 @@ __global__ void grad_epilogue_kernel(int n, int ne, int64_t W, int64_t P, int nc
                     cfma(acc, cmul(Rs[i * ne + k], Dp), Ncol[k]);
                     Dp = cmul(Dp, Rs[k * ne + k]);
                 }
-                Ncol[i] = cneg(acc);
+                Ncol[i] = flip_if(acc, true);
             }
             cd post = cmk(1.0, 0.0);
             for (int k = j + 1; k < ne; ++k) post = cmul(post, Rs[k * ne + k]);

@@ -15,11 +15,7 @@ __device__ __forceinline__ void group_sync(int id) {
 }
 
 // Skew matrix entry (i, j) from its packed upper triangle.
-__device__ __forceinline__ cd skew_at(const cd *P, int i, int j) {
-    if (i == j) return cmk(0.0, 0.0);
-    int lo = i < j ? i : j, hi = i < j ? j : i;
-    return flip_if(P[tri_index(lo, hi)], i > j);
-}
+__device__ __forceinline__ cd skew_at(const cd *P, int i, int j) { return skew_get0(P, i, j); }
 
 // Forward Parlett-Reid elimination of nb node matrices B + wnode D (packed upper,
 // original index order) by the pair's 64 threads, keeping the step history (active
@@ -82,7 +78,7 @@ __device__ inline void node_factor(int m, int ne, const cd *__restrict__ wnode, 
                 const int k = cur[lane * hstride], p = cur[lane * hstride + a];
                 const cd piv = Ns[lane * T + tri_index(k, p)];
                 const cd f = cmul(pf[lane], piv);
-                pf[lane] = ((a - 1) & 1) ? cneg(f) : f;
+                pf[lane] = flip_if(f, (a - 1) & 1);
                 invh[lane * S + s] = cinv(piv);
                 pos[lane] = a;
                 kh[lane * S + s] = (uint8_t)k;
@@ -97,7 +93,7 @@ __device__ inline void node_factor(int m, int ne, const cd *__restrict__ wnode, 
             const int i = cur[v * hstride + a], k = kh[v * S + s], p = ph[v * S + s];
             const cd *Nv = Ns + v * T;
             Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], invh[v * S + s]);
-            Vv[v * m + a2] = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
+            Vv[v * m + a2] = skew_get(Nv, i, p);
             nxt[v * hstride + a2] = (uint8_t)i;
         }
         group_sync(bar);
@@ -138,7 +134,7 @@ __device__ inline void node_inverse(int m, int nb, cd *__restrict__ Ns, cd *__re
             const cd *Nv = Ns + v * T;
             const int i = acth[v * hstride + (s + 1) * m + a], k = kh[v * S + s], p = ph[v * S + s];
             const cd ia = invh[v * S + s];
-            const cd vi = (i < p) ? Nv[tri_index(i, p)] : cneg(Nv[tri_index(p, i)]);
+            const cd vi = skew_get(Nv, i, p);
             g1v[v * m + a] = cmul(vi, ia);
             g2v[v * m + a] = cmul(Nv[tri_index(k, i)], ia);
         }
@@ -153,11 +149,7 @@ __device__ inline void node_inverse(int m, int nb, cd *__restrict__ Ns, cd *__re
             const cd *g = (vec ? g2v : g1v) + v * m;
             const int i = rest[a];
             cd y = cmk(0.0, 0.0);
-            for (int b = 0; b < rv; ++b) {
-                const int j = rest[b];
-                if (j == i) continue;
-                cfma(y, flip_if(Zv[tri_index(i < j ? i : j, i < j ? j : i)], j < i), g[b]);
-            }
+            for (int b = 0; b < rv; ++b) cfma(y, skew_get0(Zv, i, rest[b]), g[b]);  // Z(i,i) = 0
             (vec ? y2v : y1v)[v * m + a] = y;
         }
         group_sync(bar);
@@ -180,8 +172,7 @@ __device__ inline void node_inverse(int m, int nb, cd *__restrict__ Ns, cd *__re
             const int i = acth[v * hstride + (s + 1) * m + a], k = kh[v * S + s], p = ph[v * S + s];
             Zv[tri_index(k, i)] = y1v[v * m + a];  // Z(k,i) = -Z(i,k) = (Z g1)_i
             const cd y2 = y2v[v * m + a];          // Z(i,p) = -y2_i
-            if (i < p) Zv[tri_index(i, p)] = cneg(y2);
-            else Zv[tri_index(p, i)] = y2;
+            Zv[i < p ? tri_index(i, p) : tri_index(p, i)] = flip_if(y2, i < p);
         }
         group_sync(bar);
     }
@@ -204,8 +195,7 @@ struct SharedScratch {  // per-group scalars exchanged between the two warps
 };
 
 __device__ __forceinline__ void skew_put(cd *N, int i, int j, cd x) {  // A(i, j) = x, A(j, i) = -x
-    if (i < j) N[tri_index(i, j)] = x;
-    else N[tri_index(j, i)] = cneg(x);
+    N[i < j ? tri_index(i, j) : tri_index(j, i)] = flip_if(x, i > j);
 }
 
 // Forward elimination of the ne occupied indices of Ns (a copy of B, m x m packed) by
@@ -344,11 +334,7 @@ __device__ inline void shared_inverse(int m, int ne, cd *__restrict__ Ns, cd *__
             const cd *g = vec ? g2v : g1v;
             const int i = rest[a];
             cd y = cmk(0.0, 0.0);
-            for (int b = 0; b < rv; ++b) {
-                const int j = rest[b];
-                if (j == i) continue;
-                cfma(y, skew_get(Ns, i, j), g[b]);
-            }
+            for (int b = 0; b < rv; ++b) cfma(y, skew_get0(Ns, i, rest[b]), g[b]);  // Z(i,i) = 0
             (vec ? y2v : y1v)[a] = y;
         }
         group_sync(bar);
@@ -362,7 +348,7 @@ __device__ inline void shared_inverse(int m, int ne, cd *__restrict__ Ns, cd *__
         for (int a = t; a < rv; a += kGroup) {
             const int i = rest[a];
             skew_put(Ns, k, i, y1v[a]);        // A^{-1}(k, i) = (Z g1)_i
-            skew_put(Ns, i, p, cneg(y2v[a]));  // A^{-1}(i, p) = -(Z g2)_i
+            skew_put(Ns, i, p, flip_if(y2v[a], true));  // A^{-1}(i, p) = -(Z g2)_i
         }
         group_sync(bar);
     }

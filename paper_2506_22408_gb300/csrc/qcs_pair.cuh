@@ -229,7 +229,7 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
             crfma(acc, Ta[2 * k], x1);
             crfma(acc, Ta[2 * k + 1], -x0);
         }
-        Bs[tri_index(a, ne + r)] = odd ? cneg(acc) : acc;
+        Bs[tri_index(a, ne + r)] = flip_if(acc, odd);
     }
     // empty x empty: real x real
     const int c3 = tri_count(twod);
