@@ -213,10 +213,10 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             cd S = cmk(0.0, 0.0);
             for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                 int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
+                node_pfaffians(mm, nee, A.wnode + k0, A.gamma + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
                                lane);
                 if (lane == 0)
-                    for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
+                    for (int v = 0; v < nb; ++v) S = cadd(S, pf[v]);  // pf[v] carries gamma
                 __syncwarp();
             }
             if (lane == 0) {
@@ -320,8 +320,8 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * A.vm);
-    A.off_pv = (int)o;
-    o = align16(o + (size_t)(A.vm / 2) * sizeof(cd));
+    A.off_pv = (int)o;  // node products: nb (m/2 + 1) records at most, gamma included
+    o = align16(o + (size_t)(A.vm / 2 + kMaxNB) * sizeof(cd));
     return o;
 }
 

@@ -297,7 +297,9 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
         pair_of(tab, (int)(0xffffffffu - (unsigned)(bk & 0xffffffffull)), ak, ap);
         const int k = cur[ak], p = cur[ap];
         const cd piv = Ns[tri_index(k, p)];
-        pf0 = cmul(pf0, flip_if(piv, ((ak + ap - 1) & 1) != 0));
+        const cd sp = flip_if(piv, ((ak + ap - 1) & 1) != 0);
+        if (s == 0) pf0 = sp;  // warp-uniform: the first signed pivot needs no product
+        else pf0 = cmul(pf0, sp);
         if (r == 2) break;  // no empty modes: the last pivot closes the Pfaffian
         const cd iv = cinv(piv);
         const int rv = r - 2;
@@ -350,7 +352,9 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
 }
 
 // Pfaffians of nb node matrices B + wnode[v] D held in Ns (packed upper), m x m with
-// ne occupied rows first.  On return pf[v] holds pf(B + wnode[v] D); m = 0 gives 1.
+// ne occupied rows first, each times its node weight: on return pf[v] holds
+// gamma[v] pf(B + wnode[v] D) (the weight enters the product tree as one more factor,
+// at no extra FP64 instruction); m = 0 gives gamma[v].
 // The warp is cut into segments of seg lanes (seg = 32 / nb rounded up to a power of
 // two); segment v owns node v through each Parlett-Reid step: it finds the pivot of the
 // active first row, takes the pivot's reciprocal (every lane of the segment, so no lane
@@ -358,19 +362,19 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
 // vectors, after which the rank-2 updates of all nodes are spread over the whole warp.
 // The steps run down to four active indices, whose Pfaffian closes the product in
 // three terms, a01 a23 - a02 a13 + a03 a12 (two indices: a01).
-__device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnode, int nb,
-                                      const cd *__restrict__ Bs, cd *__restrict__ Ns, cd *__restrict__ Uv,
+__device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnode, const cd *__restrict__ gamma,
+                                      int nb, const cd *__restrict__ Bs, cd *__restrict__ Ns, cd *__restrict__ Uv,
                                       cd *__restrict__ Vv, cd *__restrict__ pf, uint8_t *__restrict__ act0,
                                       uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
                                       cd *__restrict__ pv, int lane) {
     if (m == 0) {
-        if (lane < nb) pf[lane] = cmk(1.0, 0.0);
+        if (lane < nb) pf[lane] = gamma[lane];
         __syncwarp();
         return;
     }
-    // records per node in pv: the signed pivots of the (m - 4) / 2 steps and the closing
-    // Pfaffian (a single record for m = 2 or 4)
-    const int S = m >= 4 ? m / 2 - 1 : 1;
+    // records per node in pv: the signed pivots of the (m - 4) / 2 steps, the closing
+    // Pfaffian (a single record for m = 2 or 4) and the node weight
+    const int S = (m >= 4 ? m / 2 - 1 : 1) + 1;
     const int d = (m - ne) / 2;
     const int T = tri_count(m);
     for (int e = lane; e < nb * T; e += 32) {
@@ -473,6 +477,7 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
             q = Nv[tri_index(c[0], c[1])];
         }
         pv[v * S + s] = q;
+        pv[v * S + s + 1] = gamma[v];
     }
     __syncwarp();
     // pf[v] = prod_s pv[v][s]: pairwise tree over the lanes; each level reads into

@@ -321,9 +321,9 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
                 cd S = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                     const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                    node_pfaffians(mm, nee, A.wnode + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv, lane);
+                    node_pfaffians(mm, nee, A.wnode + k0, A.gamma + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv, lane);
                     if (lane == 0)
-                        for (int vv = 0; vv < nb; ++vv) cfma(S, A.gamma[k0 + vv], pf[vv]);
+                        for (int vv = 0; vv < nb; ++vv) S = cadd(S, pf[vv]);  // pf[vv] carries gamma
                     __syncwarp();
                 }
                 if (lane == 0) {
@@ -630,8 +630,8 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * A.vm);
-    A.off_pv = (int)o;
-    o = align16(o + (size_t)(A.vm / 2) * sizeof(cd));
+    A.off_pv = (int)o;  // node products: nb (m/2 + 1) records at most, gamma included
+    o = align16(o + (size_t)(A.vm / 2 + kMaxNB) * sizeof(cd));
     return o;
 }
 
