@@ -113,6 +113,148 @@ __device__ inline void node_factor(int m, int ne, const cd *__restrict__ wnode, 
     }
 }
 
+// Pfaffians of nb <= kMaxNBG node matrices B + wnode[v] D (packed upper in Ns, m x m with
+// ne occupied rows first) by the pair's 64 threads, for callers that need no inverse:
+// no step history is kept.  Node v belongs to warp v & 1, where a segment of seg lanes
+// owns it through each step (pivot of the active first row, reciprocal on every lane of
+// the segment, Gauss vectors); the rank-2 updates of all nodes are spread over the 64
+// threads.  The steps stop at four active indices, closed by the three-term Pfaffian.
+// On return pf[v] = gamma[v] pf(B + wnode[v] D) (the weight is one more factor of the
+// product tree).  Workspace: Ns (nb x tri(m)), Uv and Vv (nb x m), act0 and act1
+// (nb x m), pv (nb (m/2 + 1)).
+__device__ inline void group_node_pfaffians(int m, int ne, const cd *__restrict__ wnode, const cd *__restrict__ gamma,
+                                            int nb, const cd *__restrict__ Bs, cd *__restrict__ Ns,
+                                            cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ pf,
+                                            uint8_t *__restrict__ act0, uint8_t *__restrict__ act1,
+                                            cd *__restrict__ pv, const uint16_t *__restrict__ tab, int t, int bar) {
+    if (m == 0) {
+        if (t < nb) pf[t] = gamma[t];
+        group_sync(bar);
+        return;
+    }
+    const int S = (m >= 4 ? m / 2 - 1 : 1) + 1;  // pivots, the closing Pfaffian, the weight
+    const int d = (m - ne) / 2;
+    const int T = tri_count(m);
+    for (int e = t; e < nb * T; e += kGroup) {
+        const int v = e / T, u = e - v * T;
+        Ns[v * T + u] = Bs[u];
+    }
+    for (int e = t; e < nb * m; e += kGroup) {
+        const int v = e / m, a = e - v * m;
+        act0[v * m + a] = (uint8_t)a;
+    }
+    group_sync(bar);
+    for (int e = t; e < nb * d; e += kGroup) {
+        const int v = e / d, i = e - v * d;
+        cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
+        *x = cadd(*x, wnode[v]);
+    }
+    group_sync(bar);
+    const int wg = t >> 5, lane = t & 31;
+    const int npw = (nb + 1) >> 1;  // nodes per warp
+    const int seg = npw <= 1 ? 32 : 16;
+    const int slot = lane / seg, sl = lane - slot * seg;
+    const int v = 2 * slot + wg;
+    const bool live = slot < npw && v < nb;
+    const int vr = live ? v : 0;  // lanes without a node read node 0 and write nothing
+    const cd *__restrict__ Nv = Ns + vr * T;
+    uint8_t *cur = act0, *nxt = act1;
+    int s = 0;
+    for (int r = m; r > 4; r -= 2, ++s) {
+        const int k = cur[vr * m];
+        unsigned long long bk = 0ull;
+        for (int a = 1 + sl; a < r; a += seg) {
+            const unsigned key = pivot_key(Nv[tri_index(k, cur[vr * m + a])]);
+            const unsigned long long c = ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
+            bk = c > bk ? c : bk;
+        }
+        for (int o = seg >> 1; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+            bk = ob > bk ? ob : bk;
+        }
+        const int a = 0xffff - (int)(bk & 0xffffull);  // 1 .. r - 1
+        const int p = cur[vr * m + a];
+        const cd piv = Nv[tri_index(k, p)];
+        if (live && sl == 0) pv[v * S + s] = flip_if(piv, (a - 1) & 1);
+        const int rv = r - 2;
+        const bool g0 = live && sl < rv;
+        int i0 = 0;
+        cd u0 = cmk(0.0, 0.0), v0 = cmk(0.0, 0.0);
+        if (g0) {
+            i0 = cur[v * m + sl + 1 + ((sl + 1 >= a) ? 1 : 0)];
+            u0 = Nv[tri_index(k, i0)];
+            v0 = skew_get(Nv, i0, p);
+        }
+        const cd iv = cinv(piv);
+        if (g0) {
+            Uv[v * m + sl] = cnegmul(u0, iv);  // A_{i,k} / A_{k,p}, A_{i,k} = -A_{k,i}
+            Vv[v * m + sl] = v0;               // A_{i,p}
+            nxt[v * m + sl] = (uint8_t)i0;
+        }
+        if (live) {
+            for (int a2 = sl + seg; a2 < rv; a2 += seg) {
+                const int i = cur[v * m + a2 + 1 + ((a2 + 1 >= a) ? 1 : 0)];
+                Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);
+                Vv[v * m + a2] = skew_get(Nv, i, p);
+                nxt[v * m + a2] = (uint8_t)i;
+            }
+        }
+        group_sync(bar);
+        const int Tr = tri_count(rv);
+        for (int e = t; e < nb * Tr; e += kGroup) {
+            const int w = e / Tr, u = e - w * Tr;
+            int ia, ib;
+            pair_of(tab, u, ia, ib);
+            cd *x = Ns + w * T + tri_index(nxt[w * m + ia], nxt[w * m + ib]);
+            cd y = *x;
+            const cd *U_ = Uv + w * m, *V_ = Vv + w * m;
+            cfms(y, U_[ia], V_[ib]);
+            cfma(y, V_[ia], U_[ib]);
+            *x = y;
+        }
+        group_sync(bar);
+        uint8_t *tt = cur;
+        cur = nxt;
+        nxt = tt;
+    }
+    if (live && sl == 0) {
+        const uint8_t *c = cur + v * m;
+        cd q;
+        if (m >= 4) {
+            q = cmul(Nv[tri_index(c[0], c[1])], Nv[tri_index(c[2], c[3])]);
+            cfms(q, Nv[tri_index(c[0], c[2])], Nv[tri_index(c[1], c[3])]);
+            cfma(q, Nv[tri_index(c[0], c[3])], Nv[tri_index(c[1], c[2])]);
+        } else {
+            q = Nv[tri_index(c[0], c[1])];
+        }
+        pv[v * S + s] = q;
+        pv[v * S + s + 1] = gamma[v];
+    }
+    group_sync(bar);
+    // pf[v] = prod of the S records of node v: pairwise tree, one item per thread
+    // (nb * half <= 4 * 13 < 64)
+    for (int len = S; len > 1; len = (len + 1) / 2) {
+        const int half = len / 2;
+        cd r = cmk(0.0, 0.0);
+        const bool act = t < nb * half;
+        if (act) {
+            const int w = t / half, i = t - w * half;
+            r = cmul(pv[w * S + 2 * i], pv[w * S + 2 * i + 1]);
+        }
+        cd tail = cmk(0.0, 0.0);
+        if ((len & 1) && t < nb) tail = pv[t * S + len - 1];
+        group_sync(bar);
+        if (act) {
+            const int w = t / half, i = t - w * half;
+            pv[w * S + i] = r;
+        }
+        if ((len & 1) && t < nb) pv[t * S + half] = tail;
+        group_sync(bar);
+    }
+    if (t < nb) pf[t] = pv[t * S];
+    group_sync(bar);
+}
+
 // Backward recursion, in place: the factors of node v in Ns become the packed
 // upper triangle of the inverse of node matrix v.  Step s first reads its pivot
 // row and column (entries (k,i) and (i,p) for the indices i still active after

@@ -46,6 +46,7 @@ struct PairArgs {
     int grp;          // n > 16: two warps share a pair (64-thread groups, qcs_group.cuh)
     int vm;           // entries per Gauss-vector buffer (the full matrix or NB node complements)
     int off_kh, off_ph, off_scr, gz;  // group path: pivot history, scratch, S0 offset (entries) in Ns
+    int off_pvg;      // group path: the node products' records
     int64_t W, P;
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
@@ -123,11 +124,11 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
         cd *gVv = reinterpret_cast<cd *>(gb + A.off_V);
         cd *gpf = reinterpret_cast<cd *>(gb + A.off_pf);
         cd *ginvh = reinterpret_cast<cd *>(gb + A.off_inv);
-        int *gpos = reinterpret_cast<int *>(gb + A.off_int);
         uint8_t *gacth = gb + A.off_act;
         uint8_t *gkh = gb + A.off_kh;
         uint8_t *gph = gb + A.off_ph;
         SharedScratch *gscr = reinterpret_cast<SharedScratch *>(gb + A.off_scr);
+        cd *gpv = reinterpret_cast<cd *>(gb + A.off_pvg);
         const int m = A.m, ne = A.ne, d2 = A.m - A.ne, Tn = tri_count(d2);
         if (p0 < L) {
             const cd prefw = A.pref[w];
@@ -160,18 +161,18 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
                     group_sync(bar);
                     for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
                         const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                        node_factor(d2, 0, A.wnode + k0, nb, gSc, gNs, gUv, gVv, gpf, ginvh, gpos, gacth, gkh, gph,
-                                    tab, t, bar, nullptr);
+                        group_node_pfaffians(d2, 0, A.wnode + k0, A.gamma + k0, nb, gSc, gNs, gUv, gVv, gpf, gacth,
+                                             gacth + A.vm, gpv, tab, t, bar);
                         if (t == 0)
-                            for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], gpf[v]);
+                            for (int v = 0; v < nb; ++v) S = cadd(S, gpf[v]);  // gpf[v] carries gamma
                         group_sync(bar);
                     }
                     S = cmul(S, pf0);
                 } else {  // the rare full eliminations: one node matrix per round
                     for (int k0 = 0; k0 < A.nev; ++k0) {
-                        node_factor(m, ne, A.wnode + k0, 1, gBs, gNs, gUv, gVv, gpf, ginvh, gpos, gacth, gkh, gph,
-                                    tab, t, bar, nullptr);
-                        if (t == 0) cfma(S, A.gamma[k0], gpf[0]);
+                        group_node_pfaffians(m, ne, A.wnode + k0, A.gamma + k0, 1, gBs, gNs, gUv, gVv, gpf, gacth,
+                                             gacth + A.vm, gpv, tab, t, bar);
+                        if (t == 0) S = cadd(S, gpf[0]);
                         group_sync(bar);
                     }
                 }
@@ -361,6 +362,8 @@ size_t pair_group_layout(PairArgs &A, int NB) {
     o = align16(o + (size_t)hs);
     A.off_scr = (int)o;
     o = align16(o + sizeof(SharedScratch));
+    A.off_pvg = (int)o;  // records of the node products: NB (d2/2 + 1) or, for a full round, m/2 + 1
+    o = align16(o + (size_t)(NB * (d2 / 2 + 1) > S + 1 ? NB * (d2 / 2 + 1) : S + 1) * sizeof(cd));
     return o;
 }
 

@@ -100,7 +100,7 @@ struct SplitArgs {
     int warp_bytes;
     int off_T, off_B, off_U, off_V, off_pf, off_act, off_pv;
     int vm;                      // entries per Gauss-vector buffer (the full matrix or NB complements)
-    int off_inv, off_int, off_kh, off_ph, off_scr, gz;  // group kernel (16 < n <= 24): step history,
+    int off_inv, off_int, off_kh, off_ph, off_scr, gz, off_pvg;  // group kernel (16 < n <= 24): step history,
                                                         // scratch, S0 offset (entries) in Ns
     const float *Mhi, *Mlo;      // walker slabs
     const float *Nhi, *Nlo;      // snapshot slabs
@@ -395,11 +395,11 @@ __global__ void __launch_bounds__(128, 2) split_group_kernel(const __grid_consta
     cd *Vv = reinterpret_cast<cd *>(gb + A.off_V);
     cd *pf = reinterpret_cast<cd *>(gb + A.off_pf);
     cd *invh = reinterpret_cast<cd *>(gb + A.off_inv);
-    int *pos = reinterpret_cast<int *>(gb + A.off_int);
     uint8_t *acth = gb + A.off_act;
     uint8_t *kh = gb + A.off_kh;
     uint8_t *ph = gb + A.off_ph;
     SharedScratch *scr = reinterpret_cast<SharedScratch *>(gb + A.off_scr);
+    cd *pvg = reinterpret_cast<cd *>(gb + A.off_pvg);
     const int ldT = 2 * n + 1;
 
     if (warp == 0) {
@@ -524,18 +524,18 @@ __global__ void __launch_bounds__(128, 2) split_group_kernel(const __grid_consta
                         group_sync(bar);
                         for (int k0 = 0; k0 < A.nev; k0 += A.NB) {
                             const int nb = A.nev - k0 < A.NB ? A.nev - k0 : A.NB;
-                            node_factor(d2, 0, A.wnode + k0, nb, Sc, Ns, Uv, Vv, pf, invh, pos, acth, kh, ph, tab, t,
-                                        bar, nullptr);
+                            group_node_pfaffians(d2, 0, A.wnode + k0, A.gamma + k0, nb, Sc, Ns, Uv, Vv, pf, acth,
+                                                 acth + A.vm, pvg, tab, t, bar);
                             if (t == 0)
-                                for (int v = 0; v < nb; ++v) cfma(S, A.gamma[k0 + v], pf[v]);
+                                for (int v = 0; v < nb; ++v) S = cadd(S, pf[v]);  // pf[v] carries gamma
                             group_sync(bar);
                         }
                         S = cmul(S, pf0);
                     } else {  // the rare full eliminations: one node matrix per round
                         for (int k0 = 0; k0 < A.nev; ++k0) {
-                            node_factor(m, ne, A.wnode + k0, 1, Bs, Ns, Uv, Vv, pf, invh, pos, acth, kh, ph, tab, t,
-                                        bar, nullptr);
-                            if (t == 0) cfma(S, A.gamma[k0], pf[0]);
+                            group_node_pfaffians(m, ne, A.wnode + k0, A.gamma + k0, 1, Bs, Ns, Uv, Vv, pf, acth,
+                                                 acth + A.vm, pvg, tab, t, bar);
+                            if (t == 0) S = cadd(S, pf[0]);
                             group_sync(bar);
                         }
                     }
@@ -606,6 +606,8 @@ size_t split_group_layout(SplitArgs &A, int NB) {
     o = align16(o + (size_t)hs);
     A.off_scr = (int)o;
     o = align16(o + sizeof(SharedScratch));
+    A.off_pvg = (int)o;  // records of the node products: NB (d2/2 + 1) or, for a full round, m/2 + 1
+    o = align16(o + (size_t)(NB * (d2 / 2 + 1) > S + 1 ? NB * (d2 / 2 + 1) : S + 1) * sizeof(cd));
     return o;
 }
 
