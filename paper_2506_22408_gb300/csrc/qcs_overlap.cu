@@ -47,6 +47,7 @@ struct PairArgs {
     int vm;           // entries per Gauss-vector buffer (the full matrix or NB node complements)
     int off_kh, off_ph, off_scr, gz;  // group path: pivot history, scratch, S0 offset (entries) in Ns
     int off_pvg;      // group path: the node products' records
+    int off_qs;       // group path: re + im of the staged snapshot rows
     int64_t W, P;
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
@@ -104,7 +105,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const cd u = Utw[e];
             Uts[(e / n) * lu + (e % n)] = u;
-            if (A.reg) Uss[(e / n) * lu + (e % n)] = u.x + u.y;
+            if (A.reg || A.grp) Uss[(e / n) * lu + (e % n)] = u.x + u.y;
         }
     }
     __syncthreads();
@@ -117,6 +118,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
         unsigned char *gb = wbase - (size_t)(warp & 1) * wstride;
         cd *gQs = reinterpret_cast<cd *>(gb);
         cd *gTs = reinterpret_cast<cd *>(gb + A.off_T);
+        double *gqs = reinterpret_cast<double *>(gb + A.off_qs);  // re + im of the staged rows
         cd *gNs = reinterpret_cast<cd *>(gb);
         cd *gSc = gNs + A.gz;
         cd *gBs = reinterpret_cast<cd *>(gb + A.off_B);
@@ -141,9 +143,9 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
                     build_T_gather(n, Uts, gq, gTs, t, kGroup);
                 } else {
                     for (int h = 0; h < 2; ++h) {  // T by column halves: half of Qt staged at a time
-                        load_Qt_rows(n, A.Qt + (q * n2 + (int64_t)h * n) * n, gQs, t, kGroup);
+                        load_Qt_rows_sums(n, A.Qt + (q * n2 + (int64_t)h * n) * n, gQs, gqs, t, kGroup);
                         group_sync(bar);
-                        build_T_echelon_half(n, ne, Uts, gQs, gTs, h * n, t, kGroup);
+                        build_T_half3(n, ne, redw, Uts, Uss, gQs, gqs, gTs, h * n, t, kGroup);
                         group_sync(bar);
                     }
                 }
@@ -334,7 +336,8 @@ size_t pair_group_layout(PairArgs &A, int NB) {
     const int n = A.n, m = A.m, ne = A.ne, T = tri_count(m), d2 = m - ne, Tn = tri_count(d2), S = m / 2;
     const size_t qbytes = (size_t)n * ld_qt(n) * sizeof(cd);
     A.off_T = (int)align16(qbytes);
-    size_t R = (size_t)A.off_T + (size_t)n * ld_t(n) * sizeof(cd);
+    A.off_qs = (int)align16((size_t)A.off_T + (size_t)n * ld_t(n) * sizeof(cd));
+    size_t R = (size_t)A.off_qs + (size_t)n * n * sizeof(double);
     A.gz = T > NB * Tn ? T : NB * Tn;
     if ((size_t)(A.gz + Tn) * sizeof(cd) > R) R = (size_t)(A.gz + Tn) * sizeof(cd);
     A.vm = m > NB * d2 ? m : NB * d2;
@@ -392,7 +395,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     const int n = A.n, m = A.m, T = tri_count(m);
     const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
-    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * (sizeof(cd) + (A.reg ? sizeof(double) : 0)));
+    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * (sizeof(cd) + (A.reg || A.grp ? sizeof(double) : 0)));
     // Node matrices per round: the requested count, or by default the largest
     // count (balanced rounds, at most kMaxNB) for which three blocks (register
     // path) or two blocks fit on an SM.

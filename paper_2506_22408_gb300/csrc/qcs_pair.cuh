@@ -150,6 +150,49 @@ __device__ inline void build_T_echelon_half(int n, int ne, const cd *__restrict_
     }
 }
 
+// Columns c0 .. c0+n-1 of T from n staged rows of Qt (Qs, stride ld_qt) and their
+// re + im sums (qs, n x n), with three real products per complex multiply-add as in
+// build_T_reg (Uss: re + im of the walker rows): Re = sum ur qr - sum ui qi,
+// Im = sum us qs - sum ur qr - sum ui qi.  Walker rows in echelon form skip the zeros
+// of build_T_echelon_half; in reduced form (red: occupied rows [I; X] / sqrt2) an
+// occupied row j has one entry, at column j, among the columns k < ne.
+__device__ inline void build_T_half3(int n, int ne, bool red, const cd *__restrict__ Uts,
+                                     const double *__restrict__ Uss, const cd *__restrict__ Qs,
+                                     const double *__restrict__ qs, cd *__restrict__ Ts, int c0, int lane,
+                                     int nthr) {
+    const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
+    for (int e = lane; e < n * n; e += nthr) {
+        const int j = e / n, c = e - j * n;
+        const cd *ur = Uts + j * lu, *qr = Qs + c * lq;
+        const double *us = Uss + j * lu, *qsr = qs + c * n;
+        double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        int k0 = 0, k1 = 0;  // columns [k0, k1) before the tail, then [kt, n)
+        int kt = j;
+        if (j < ne) {
+            if (red) {
+                k0 = j;
+                k1 = j + 1;
+                kt = ne;
+            }
+        } else {
+            k1 = ne;  // the occupied columns, then the completion's tail from j = ne + j'
+        }
+        for (int k = k0; k < k1; ++k) {
+            const cd u = ur[k], q = qr[k];
+            p1 = fma(u.x, q.x, p1);
+            p2 = fma(u.y, q.y, p2);
+            p3 = fma(us[k], qsr[k], p3);
+        }
+        for (int k = kt; k < n; ++k) {
+            const cd u = ur[k], q = qr[k];
+            p1 = fma(u.x, q.x, p1);
+            p2 = fma(u.y, q.y, p2);
+            p3 = fma(us[k], qsr[k], p3);
+        }
+        Ts[j * lt + c0 + c] = cmk(p1 - p2, p3 - p1 - p2);
+    }
+}
+
 // x * ph for a phase code ph = 0..3 (1, i, -1, -i): a swap of the parts and sign
 // flips of the bit patterns, no floating-point arithmetic.
 __device__ __forceinline__ cd mul_phase(cd x, unsigned ph) {
@@ -187,6 +230,18 @@ __device__ inline void load_Qt_rows(int n, const cd *__restrict__ Qg, cd *__rest
     for (int e = lane; e < n * n; e += nthr) {
         int c = e / n, k = e - c * n;
         Qs[c * lq + k] = Qg[e];
+    }
+}
+
+// The same, also writing re + im of every staged entry to qs (n x n, row stride n).
+__device__ inline void load_Qt_rows_sums(int n, const cd *__restrict__ Qg, cd *__restrict__ Qs,
+                                         double *__restrict__ qs, int lane, int nthr) {
+    const int lq = ld_qt(n);
+    for (int e = lane; e < n * n; e += nthr) {
+        const int c = e / n, k = e - c * n;
+        const cd q = Qg[e];
+        Qs[c * lq + k] = q;
+        qs[e] = q.x + q.y;
     }
 }
 
