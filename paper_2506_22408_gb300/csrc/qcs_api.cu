@@ -801,9 +801,11 @@ double qcs_pf_elim_flops(int m, int stop) {
 // Parts of the count: [0] congruence T, [1] covariance B, [2] Pfaffian eliminations.
 static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, double *part) {
     const int d = n - ne, m = 2 * n - ne;
-    // skipped entries of Ut: echelon form, or for n >= 16 the reduced form of the
-    // occupied rows ([I; X], all but one of the columns k < ne zero)
-    const bool three = overlap_kernel && n >= 16;  // the register (n = 16) and group (n > 16) T
+    // skipped entries of Ut: the reduced form of the occupied rows ([I; X], all but one of
+    // the columns k < ne zero) and the echelon form of the completion; three real products
+    // per complex multiply-add (every T of the overlap kernel in its default
+    // configuration; n > 16 configured to one warp per pair takes four)
+    const bool three = overlap_kernel;
     const double occ_zeros = three ? (double)ne * (ne - 1) : (double)tri_count(ne);
     const double zeros = overlap_kernel ? occ_zeros + tri_count(d) : 0.0;
     const double macs = 2.0 * n * ((double)n * n - zeros);   // complex multiply-adds of T

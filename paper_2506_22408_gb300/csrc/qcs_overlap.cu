@@ -44,10 +44,11 @@ struct PairArgs {
     int n, ne, m, d, nev, NB, all, chunk, nchunks;
     int reg;          // n = 16: snapshot rows in registers, T by three real products (build_T_reg)
     int grp;          // n > 16: two warps share a pair (64-thread groups, qcs_group.cuh)
+    int t3;           // n < 16: T by three real products from staged rows and their sums
     int vm;           // entries per Gauss-vector buffer (the full matrix or NB node complements)
     int off_kh, off_ph, off_scr, gz;  // group path: pivot history, scratch, S0 offset (entries) in Ns
     int off_pvg;      // group path: the node products' records
-    int off_qs;       // group path: re + im of the staged snapshot rows
+    int off_qs;       // re + im of the staged snapshot rows (warp and group paths)
     int64_t W, P;
     int warp_bytes;   // shared bytes per warp
     int tab_bytes;    // shared bytes of the pair table (per block)
@@ -80,7 +81,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
     cd *Qs = Rg;  // staged snapshot rows (shared-memory path only)
     cd *Ts = reinterpret_cast<cd *>(wbase + A.off_T);
     cd *Ns = Rg;  // node matrices, once T is consumed
-    double *Uss = reinterpret_cast<double *>(Uts + n * ld_ut(n));  // re + im of Ut (register path)
+    double *Uss = reinterpret_cast<double *>(Uts + n * ld_ut(n));  // re + im of Ut
     cd *Bs = reinterpret_cast<cd *>(wbase + A.off_B);
     cd *Uv = reinterpret_cast<cd *>(wbase + A.off_U);
     cd *Vv = reinterpret_cast<cd *>(wbase + A.off_V);
@@ -105,7 +106,7 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const cd u = Utw[e];
             Uts[(e / n) * lu + (e % n)] = u;
-            if (A.reg || A.grp) Uss[(e / n) * lu + (e % n)] = u.x + u.y;
+            Uss[(e / n) * lu + (e % n)] = u.x + u.y;
         }
     }
     __syncthreads();
@@ -200,7 +201,16 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
                 build_T_gather(n, Uts, gq, Ts, lane);  // signed permutation: no products
             } else if (A.reg) {
                 build_T_reg<16>(A.ne, Uts, Uss, A.Qt + q * n2 * n, Ts, lane, redw);
-            } else {
+            } else if (A.t3) {
+                // staged rows and their re + im sums; T by three real products per
+                // complex multiply-add, skipping the zeros of the echelon or reduced form
+                double *qs = reinterpret_cast<double *>(wbase + A.off_qs);
+                load_Qt_rows_sums(n, A.Qt + q * n2 * n, Qs, qs, lane, 32);
+                load_Qt_rows_sums(n, A.Qt + (q * n2 + n) * n, Qs + n * ld_qt(n), qs + n * n, lane, 32);
+                __syncwarp();
+                build_T_half3(n, A.ne, redw, Uts, Uss, Qs, qs, Ts, 0, lane, 32);
+                build_T_half3(n, A.ne, redw, Uts, Uss, Qs + n * ld_qt(n), qs + n * n, Ts, n, lane, 32);
+            } else {  // n > 16 configured to one warp per pair: no room for the sums
                 load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
                 __syncwarp();
                 build_T_echelon(n, A.ne, Uts, Qs, Ts, lane);  // walker rows in echelon form
@@ -308,6 +318,8 @@ size_t pair_warp_layout(PairArgs &A, int NB) {
     const int n = A.n, m = A.m, T = tri_count(m), d2 = m - A.ne;
     const size_t qbytes = A.reg ? 0 : (size_t)2 * n * ld_qt(n) * sizeof(cd);
     size_t R = qbytes + (size_t)n * ld_t(n) * sizeof(cd);
+    A.off_qs = (int)align16(R);  // staged rows' re + im sums (shared-memory path)
+    if (A.t3) R = (size_t)A.off_qs + (size_t)2 * n * n * sizeof(double);
     if ((size_t)T * sizeof(cd) > R) R = (size_t)T * sizeof(cd);
     if ((size_t)NB * tri_count(d2) * sizeof(cd) > R) R = (size_t)NB * tri_count(d2) * sizeof(cd);
     A.vm = m > NB * d2 ? m : NB * d2;
@@ -392,10 +404,11 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     const qcs_config cfg = qcs_decode_config(L.config);
     A.reg = L.n == 16;
     A.grp = L.n > 16 && cfg.warps != 1;  // n > 16: two warps per pair unless one is configured
+    A.t3 = L.n < 16;
     const int n = A.n, m = A.m, T = tri_count(m);
     const int wpb = qcs_pair_warps_per_block();
     A.tab_bytes = (int)align16((size_t)T * sizeof(uint16_t));
-    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * (sizeof(cd) + (A.reg || A.grp ? sizeof(double) : 0)));
+    A.ut_bytes = (int)align16((size_t)n * ld_ut(n) * (sizeof(cd) + sizeof(double)));  // rows and re + im
     // Node matrices per round: the requested count, or by default the largest
     // count (balanced rounds, at most kMaxNB) for which three blocks (register
     // path) or two blocks fit on an SM.

@@ -131,31 +131,13 @@ __device__ inline void build_T_reg(int ne, const cd *__restrict__ Uts, const dou
 #undef QCS_T3M
 #undef QCS_T3M1
 
-// Columns c0 .. c0+n-1 of T from n staged rows of Qt (Qs rows 0 .. n-1 hold rows
-// c0 .. c0+n-1), walker rows in echelon form as in build_T_echelon.
-__device__ inline void build_T_echelon_half(int n, int ne, const cd *__restrict__ Uts, const cd *__restrict__ Qs,
-                                            cd *__restrict__ Ts, int c0, int lane, int nthr) {
-    const int lu = ld_ut(n), lq = ld_qt(n), lt = ld_t(n);
-    for (int e = lane; e < n * n; e += nthr) {
-        const int j = e / n, c = e - j * n;
-        const cd *ur = Uts + j * lu, *qr = Qs + c * lq;
-        cd s = cmk(0.0, 0.0);
-        if (j < ne) {
-            for (int k = j; k < n; ++k) cfma(s, ur[k], qr[k]);
-        } else {
-            for (int k = 0; k < ne; ++k) cfma(s, ur[k], qr[k]);
-            for (int k = j; k < n; ++k) cfma(s, ur[k], qr[k]);
-        }
-        Ts[j * lt + c0 + c] = s;
-    }
-}
-
 // Columns c0 .. c0+n-1 of T from n staged rows of Qt (Qs, stride ld_qt) and their
 // re + im sums (qs, n x n), with three real products per complex multiply-add as in
 // build_T_reg (Uss: re + im of the walker rows): Re = sum ur qr - sum ui qi,
-// Im = sum us qs - sum ur qr - sum ui qi.  Walker rows in echelon form skip the zeros
-// of build_T_echelon_half; in reduced form (red: occupied rows [I; X] / sqrt2) an
-// occupied row j has one entry, at column j, among the columns k < ne.
+// Im = sum us qs - sum ur qr - sum ui qi.  Walker rows in echelon form skip their zeros
+// (occupied row j: columns k < j; completion row ne + j': columns ne .. ne + j' - 1);
+// in reduced form (red: occupied rows [I; X] / sqrt2) an occupied row j has one entry,
+// at column j, among the columns k < ne.
 __device__ inline void build_T_half3(int n, int ne, bool red, const cd *__restrict__ Uts,
                                      const double *__restrict__ Uss, const cd *__restrict__ Qs,
                                      const double *__restrict__ qs, cd *__restrict__ Ts, int c0, int lane,

@@ -40,8 +40,9 @@ def test_flop_accounting_host_only():
 
     n, ne = 16, 8
     d, m = n - ne, 2 * n - ne
-    # n = 16: three real products per complex multiply-add over the non-zero walker
-    # entries, 3 sums per entry of T and re + im of each snapshot entry
+    # every n: three real products per complex multiply-add over the non-zero walker
+    # entries (occupied rows in reduced form), 3 sums per entry of T and re + im of each
+    # snapshot entry
     t_3m = 6 * 2 * n * (n * n - ne * (ne - 1) - tri(d)) + 3 * 2 * n * n + 2 * n * n  # reduced form
     b_flops = 16 * n * tri(ne) + 8 * n * ne * 2 * d + 4 * n * tri(2 * d)
     shared = sum(step(r) for r in range(m, 2 * d, -2))
@@ -51,12 +52,12 @@ def test_flop_accounting_host_only():
     assert lib.qcs_overlap_flops_per_pair_signed_perm(16, 8, 0, 0) == b_flops + shared + 3 * node
     parts = qcs.flops_breakdown(16, 8)
     assert (parts["T"], parts["B"], parts["pfaffian"]) == (t_3m, b_flops, shared + 3 * node)
-    # other n: four real products per complex multiply-add
-    n, ne = 12, 6
-    d, m = n - ne, 2 * n - ne
-    p12 = qcs.flops_breakdown(n, ne)
-    assert p12["T"] == 8 * 2 * n * (n * n - tri(ne) - tri(d))
-    assert lib.qcs_overlap_flops_per_pair(n, ne, 0, 0) == sum(p12.values())
+    # other n: the same form (the one-warp path below 16 modes, two-warp groups above)
+    for n, ne in ((12, 6), (20, 10), (24, 4)):
+        d = n - ne
+        p12 = qcs.flops_breakdown(n, ne)
+        assert p12["T"] == 6 * 2 * n * (n * n - ne * (ne - 1) - tri(d)) + 3 * 2 * n * n + 2 * n * n
+        assert lib.qcs_overlap_flops_per_pair(n, ne, 0, 0) == sum(p12.values())
     assert lib.qcs_overlap_flops_per_pair(16, 7, 0, 0) == 0.0  # odd ne rejected
 
 
