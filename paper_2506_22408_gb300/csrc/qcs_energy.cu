@@ -23,7 +23,7 @@
 //     tr(A_k^-1 A') = tr(P^-1 A'_oo) + tr(Z_k G),
 //     tr((A_k^-1 A')^2) = tr((P^-1 A'_oo)^2) + 2 tr(Z_k H) + tr((Z_k G)^2).
 // P^-1 comes from the backward recursion over the shared steps (qcs_group.cuh) run
-// with Z = 0; pairs whose occupied block would grow the complement beyond 2^5 take
+// with Z = 0; pairs whose occupied block would grow the complement beyond 2^8 take
 // the full inverse per node.  The snapshot enters the operator terms through
 // Mt = (Q'^T J X^T)^T, formed once per pair: X' J X^T = (K ell) Mt^T, so A' is
 // (K ell) Mt^T minus its transpose and X' itself is never formed.  Per Cholesky vector

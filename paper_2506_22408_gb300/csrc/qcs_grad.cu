@@ -33,7 +33,7 @@
 // inverts only its 2d x 2d complement, and since every backward step is affine in Z,
 // one backward pass over the shared steps, started from sum_k c_k Z_k, gives
 // Y_p = sum_k c_k A'_k^{-1} (shared_inverse).  Pairs whose occupied block would grow
-// the complement beyond 2^5 of max|B| take the full elimination per node.
+// the complement beyond 2^8 of max|B| take the full elimination per node.
 #include "qcs_internal.h"
 #include "qcs_group.cuh"
 

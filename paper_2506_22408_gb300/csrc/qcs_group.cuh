@@ -346,7 +346,7 @@ __device__ __forceinline__ void skew_put(cd *N, int i, int j, cd x) {  // A(i, j
 // (-1)^(ak+ap-1) A_kp to pf0.  Keeps the step history (active lists acth, pivot
 // indices kh/ph, pivot reciprocals invh) for shared_inverse.  Returns false (the same
 // on every thread) when a pivot is zero or the complement's largest entry exceeds
-// 2^5 times that of B; on success the empty x empty block of Ns holds S0 and sc->pf0
+// 2^8 times that of B; on success the empty x empty block of Ns holds S0 and sc->pf0
 // the product of the signed pivots.
 __device__ inline bool shared_factor(int m, int ne, const cd *__restrict__ Bs, cd *__restrict__ Ns,
                                      cd *__restrict__ Uv, cd *__restrict__ Vv, cd *__restrict__ invh,
@@ -446,7 +446,7 @@ __device__ inline bool shared_factor(int m, int ne, const cd *__restrict__ Bs, c
     if (lane == 0) sc->key[t >> 5] = ks;
     group_sync(bar);
     ks = sc->key[0] > sc->key[1] ? sc->key[0] : sc->key[1];
-    return ks <= kb + (5u << 20);
+    return ks <= kb + (8u << 20);
 }
 
 // Backward recursion over the occupied steps of shared_factor, in place on Ns, whose

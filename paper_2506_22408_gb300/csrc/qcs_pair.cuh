@@ -296,7 +296,7 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
 // first pair in packed order); a pivot pair at positions ak < ap of the active list
 // contributes (-1)^(ak+ap-1) A_kp, the sign of moving k and p to the front.  Works on a
 // copy of B in Ns.  Returns false, with Bs untouched, when a pivot is zero or the
-// largest entry of S exceeds 2^5 times the largest entry of B (the caller then
+// largest entry of S exceeds 2^8 times the largest entry of B (the caller then
 // eliminates each node matrix in full); on success Bs holds S, packed upper 2d x 2d.
 __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__restrict__ Ns,
                                       cd *__restrict__ Uv, cd *__restrict__ Vv, uint8_t *__restrict__ act0,
@@ -378,7 +378,7 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
         ks = k > ks ? k : ks;
     }
     ks = __reduce_max_sync(QCS_FULL, ks);
-    if (ks > kb + (5u << 20)) return false;  // keys order like |x|; +5 in the exponent field is x 2^5
+    if (ks > kb + (8u << 20)) return false;  // keys order like |x|; +8 in the exponent field is x 2^8
     for (int t = lane; t < T2; t += 32) {
         int a, b;
         pair_of(tab, t, a, b);

@@ -26,7 +26,7 @@ import pytest
 import oracle.oracle as orc
 from paper_2506_22408_gb300 import synth
 
-GROWTH = 2.0 ** 5  # the kernel's bound on max|S| / max|B| before it falls back
+GROWTH = 2.0 ** 8  # the kernel's bound on max|S| / max|B| before it falls back
 
 
 def key(x):
