@@ -76,6 +76,30 @@ def test_precision_full_size_sampled(ctx):
     assert np.all(np.abs(ov.cpu().numpy()[sel] - oo) <= 2e-5 * sc.mean(axis=1))
 
 
+@pytest.mark.parametrize("which", [3, 4])  # the n = 20 and n = 24 systems of the batching workload
+def test_precision_large_n_full_size_sampled(ctx, which):
+    """QCS_TF32X3 above 16 modes (64-row tiles, K = 48, a 64-thread group per walker) on the
+    batching workload's n = 20 (128 x 20000) and n = 24 (64 x 40000) systems: sampled
+    pairs against the oracle within the split path's bound, and one whole walker."""
+    wl = synth.BATCH_SYSTEMS[which]
+    assert wl.n > 16
+    data = wl.generate(seed=0)
+    s = qcs.Snapshots(ctx, dev(data["Q"]), dev(data["b"]))
+    ov, pp = qcs.overlap(ctx, s, dev(data["Phi"]), per_pair=True, precision=qcs.QCS_TF32X3)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    rng = np.random.default_rng(9 + which)
+    ws, ps = rng.integers(0, wl.W, 60), rng.integers(0, wl.P, 60)
+    got = pp[torch.from_numpy(ws).cuda(), torch.from_numpy(ps).cuda()].cpu().numpy()
+    for k, (w, p) in enumerate(zip(ws, ps)):
+        o, _, sc = orc.pair(data["Q"][p], data["b"][p], data["Phi"][w])
+        assert abs(got[k] - o) <= 2e-5 * sc
+    del pp
+    sel = np.array([wl.W - 1])
+    oo, _, sc, _ = orc.overlap(data["Phi"][sel], data["Q"], data["b"], per_pair=True)
+    assert np.all(np.abs(ov.cpu().numpy()[sel] - oo) <= 2e-5 * sc.mean(axis=1))
+
+
 def test_batch_full_size_sampled(ctx):
     """The five active spaces at full size in one persistent launch: two walkers of each
     system against the oracle."""
