@@ -667,8 +667,9 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     size_t b_r = align16(sizeof(cd) * (size_t)W * ne * ne);
     size_t b_w = align16(sizeof(cd) * (size_t)W * ((size_t)ne * ne + 1));
     size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * (1 + (size_t)n * n));
+    size_t b_qh = align16(sizeof(cd) * (size_t)s->P * 2 * n * n);
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w, &base, st);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w + b_qh, &base, st);
     if (ws != QCS_OK) return ws;
     unsigned long long *gcounter = (unsigned long long *)base;
     char *pb = (char *)base + 16;
@@ -678,6 +679,7 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     cd *R = (cd *)(pb + b_ut + b_pref + b_u);
     cd *part = (cd *)(pb + b_ut + b_pref + b_u + b_r);
     cd *Wrot = (cd *)(pb + b_ut + b_pref + b_u + b_r + b_part);
+    cd *Qh = (cd *)(pb + b_ut + b_pref + b_u + b_r + b_part + b_w);
     // echelon-form walker rows (the congruence skips their zeros); U is the rotated unitary,
     // R the QR's triangular factor and Wrot the occupied columns' rotation for the epilogue
     qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st, U, R, true, nullptr,
@@ -696,6 +698,7 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     L.Wrot = Wrot;
     L.pref = pref;
     L.s = s;
+    L.Qh = Qh;
     L.partial = part;
     L.overlap = (cd *)d_overlap;
     L.grad = (cd *)d_grad;
@@ -724,21 +727,44 @@ extern "C" qcs_status qcs_force_bias(qcs_ctx *ctx, int n, int ne, int64_t W, int
 
 static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, double *part);
 
-// The cotangent products Gamma1 = G_X[occ] Qt, Gamma2 = Ht conj(Qt) (n x n entries of 2n
-// complex terms): three real products per term when B's and Y's regions (tri(m)
-// entries) hold the staged sums, else four.
-static double grad_gamma_flops(int n, int ne) {
-    const int m = 2 * n - ne;
-    if (tri_count(m) >= n * n) return 6.0 * n * n * 2 * n + 2.0 * (2.0 * n * n) + 3.0 * n * n;
-    return 8.0 * n * n * 2 * n;
-}
-
-// T over the echelon-form walker rows as the gradient kernel forms it: at n = 16 three
-// real products per complex multiply-add (with re + im of each snapshot entry and the
-// two sums per entry), else four.
+// T over the echelon-form walker rows as the gradient kernel forms it (and K = Ut Qh^T, the
+// same product with the snapshot's rows [H1^T; G2^T] in place of Qt): at n = 16 three real
+// products per complex multiply-add (with re + im of each snapshot entry and the two sums
+// per entry), else four.
 static double grad_T_flops(int n, int ne) {
     const double macs = 2.0 * n * ((double)n * n - tri_count(ne) - tri_count(n - ne));
     return n == 16 ? 6.0 * macs + 3.0 * 2.0 * n * n + 2.0 * n * n : 8.0 * macs;
+}
+
+// B from T (build_B): occupied x occupied, occupied x empty, empty x empty.
+static double grad_B_from_T_flops(int n, int ne) {
+    const int d = n - ne;
+    return 8.0 * 2.0 * n * tri_count(ne) + 4.0 * 2.0 * n * ne * 2 * d + 2.0 * 2.0 * n * tri_count(2 * d);
+}
+
+// B from K (build_B_from_K): two n-term complex sums per work item (tri(ne) occupied
+// pairs, ne d occupied-empty pairs, tri(d + 1) empty pairs j1 <= j2), then the halved
+// sums and differences of the occupied-empty (8 flop) and distinct empty pairs (8 flop)
+// and one product per mode.
+static double grad_B_from_K_flops(int n, int ne) {
+    const int d = n - ne;
+    const double items = (double)tri_count(ne) + (double)ne * d + (double)tri_count(d + 1);
+    return 16.0 * n * items + 8.0 * ne * d + 8.0 * tri_count(d) + d;
+}
+
+// Cotangents from K: the coefficient rows (Yh = Y[ne+2i] - i Y[ne+2i+1] and the halved
+// combinations of each empty pair), then n x n entries of m complex multiply-adds.
+static double grad_gamma_from_K_flops(int n, int ne) {
+    const int d = n - ne, m = 2 * n - ne;
+    return 8.0 * ne * d + d * (16.0 * d + 2.0 * ne) + 8.0 * n * n * m;
+}
+
+// Signed-permutation snapshots: Yh (d x m), G_X on the occupied rows and Ht on the empty
+// modes (n rows of 2n, ne complex and 2d real terms each), two complex additions per
+// cotangent entry.
+static double grad_gamma_signed_perm_flops(int n, int ne) {
+    const int d = n - ne, m = 2 * n - ne;
+    return 2.0 * d * m + (double)n * 2 * n * (8.0 * ne + 4.0 * (m - ne)) + 4.0 * n * n;
 }
 
 extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned flags) {
@@ -746,10 +772,11 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     if (n < 1 || n > QCS_MAX_N || ne < 2 || ne > n || (ne & 1)) return 0.0;
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
     const int d = n - ne, m = 2 * n - ne;
-    // forward: T over the echelon-form walker rows, B, the occupied block once, each
-    // node's 2d x 2d complement
+    // forward: K over the echelon-form walker rows, B from K, the occupied block once,
+    // each node's 2d x 2d complement
     double f = qcs_overlap_flops_nev(n, ne, plan.nev, false);
     f += grad_T_flops(n, ne) - 16.0 * n * n * n;                 // instead of a dense T
+    f += grad_B_from_K_flops(n, ne) - grad_B_from_T_flops(n, ne);  // B from K, not from T
     f -= (double)(plan.nev - 1) * qcs_pf_elim_flops(m, 2 * d);  // the occupied steps once, not per node
     // backward step with rv later indices: g1, g2 (12 rv), Z g1 and Z g2 (16 rv^2), corner (8 rv)
     auto bstep = [](int rv) { return 16.0 * rv * rv + 20.0 * rv; };
@@ -757,8 +784,7 @@ extern "C" double qcs_grad_flops_per_pair(int n, int ne, int nodes, unsigned fla
     for (int rv = 2 * d - 2; rv > 0; rv -= 2) node += bstep(rv);
     f += (node + 8.0 * tri_count(2 * d)) * plan.nev;                // + the weighted sum of the Z_k
     for (int rv = 2 * d; rv <= m - 2; rv += 2) f += bstep(rv);      // backward over the shared steps
-    f += (double)m * 2 * n * (8.0 * ne + 4.0 * (m - ne));           // G_X = Y (X J)
-    f += grad_gamma_flops(n, ne) + 2.0 * d * 2 * n;                 // Gamma1 / Gamma2
+    f += grad_gamma_from_K_flops(n, ne);                            // Gamma1 / Gamma2
     return f;
 }
 
@@ -774,9 +800,9 @@ extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int node
 extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
     const double f = qcs_grad_flops_per_pair(n, ne, nodes, flags);
     if (!(f > 0.0)) return 0.0;
-    // T is a gather; each of the n x n cotangent entries takes 2 complex additions
-    // instead of 2n complex multiply-adds
-    return f - grad_T_flops(n, ne) - (grad_gamma_flops(n, ne) - (double)n * n * 2 * 2.0);
+    // T is a gather and B is formed from it; G_X and gathers of Qt give the cotangents
+    return f - grad_T_flops(n, ne) - grad_B_from_K_flops(n, ne) + grad_B_from_T_flops(n, ne) -
+           grad_gamma_from_K_flops(n, ne) + grad_gamma_signed_perm_flops(n, ne);
 }
 
 extern "C" double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags) {

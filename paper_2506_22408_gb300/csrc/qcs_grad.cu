@@ -48,6 +48,7 @@ struct GradArgs {
         off_int, off_tile, off_acth, off_kh, off_ph, off_kc, off_sacth, off_skh, off_sph, off_sinvh, off_scr;
     const cd *Ut;
     const cd *Qt;
+    const cd *Qh;        // per listed snapshot: the rows [H1^T; G2^T] (2n x n, the layout of Qt)
     const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
     const int *idx;
     const int *d_count;
@@ -57,6 +58,106 @@ struct GradArgs {
     cd wnode[QCS_MAX_NODES];
     cd gamma[QCS_MAX_NODES];
 };
+
+// Per listed snapshot with a dense Qt: Qh = [H1^T; G2^T] (2n x n, Qt's layout) with
+// H1 = Qt^T J Qt and G2 = Qt^T J conj(Qt) (n x n; J pairs the Majorana indices 2a, 2a + 1
+// with J[2a][2a+1] = 1).  Every pair product of the gradient then needs only
+// K = Ut Qh^T = [Ut H1 | Ut G2] (formed like T) instead of T:
+//     T_j J T_k^T = (Ut H1 Ut^T)[j][k],   T_j J conj(T_k)^T = (Ut G2 Ut^H)[j][k],
+//     T_j J Qt = (Ut H1)[j],              T_j J conj(Qt) = (Ut G2)[j],
+// so B and the cotangents Gamma1, Gamma2 follow from K without the 2n-wide G_X.
+__global__ void grad_hform_kernel(int n, int64_t P, int all, const int *__restrict__ idx,
+                                  const int *__restrict__ d_count, const cd *__restrict__ Qt,
+                                  const uint8_t *__restrict__ gth, cd *__restrict__ Qh, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cd *Qs = reinterpret_cast<cd *>(smem_raw);  // 2n x n
+    const int n2 = 2 * n;
+    if (!QCS_IN_BOUNDS((size_t)n2 * n * sizeof(cd) <= dyn_smem_bytes(), status)) return;
+    const int64_t L = all ? P : (int64_t)(*d_count);
+    for (int64_t pq = blockIdx.x; pq < L; pq += gridDim.x) {
+        const int64_t q = all ? pq : (int64_t)idx[pq];
+        if (!QCS_IN_BOUNDS(q >= 0 && q < P, status)) continue;  // block-uniform
+        if (gth && gth[q * n2] != 0xFF) continue;              // signed permutation: T is a gather
+        __syncthreads();
+        for (int e = threadIdx.x; e < n2 * n; e += blockDim.x) Qs[e] = Qt[q * n2 * n + e];
+        __syncthreads();
+        cd *out = Qh + q * n2 * n;
+        for (int e = threadIdx.x; e < n2 * n; e += blockDim.x) {
+            const int c = e / n, k = e - c * n;
+            const bool g2 = c >= n;  // row c of Qh: column c of H1, or column c - n of G2
+            const int l = g2 ? c - n : c;
+            cd acc = cmk(0.0, 0.0);
+            for (int a = 0; a < n; ++a) {
+                cd x = Qs[(2 * a + 1) * n + l], y = Qs[(2 * a) * n + l];
+                x.y = g2 ? -x.y : x.y;
+                y.y = g2 ? -y.y : y.y;
+                cfma(acc, Qs[(2 * a) * n + k], x);
+                cfms(acc, Qs[(2 * a + 1) * n + k], y);
+            }
+            out[e] = acc;
+        }
+    }
+}
+
+// B (packed upper, m x m) from K = [Ut H1 | Ut G2] (rows of Ks, stride ld_t) and the walker
+// rows Ut: with W1 = (Ut H1) Ut^T = T J T^T and W2 = (Ut G2) Ut^H = T J conj(T)^T, and the
+// empty rows R_j = Re T_j, I_j = -Im T_j of X,
+//     occupied a, b:          W1[a][b]
+//     occupied a, empty j:    (a, R_j) = (W1 + W2)[a][j] / 2,   (a, I_j) = i (W1 - W2)[a][j] / 2
+//     empty j1 <= j2, al = W1[j1][j2], be = W2[j1][j2]:
+//         (R, R) = Re(al + be)/2,  (R, I) = Im(be - al)/2,  (I, R) = -Im(al + be)/2,
+//         (I, I) = Re(be - al)/2;  within one mode (al = 0) only (R_j, I_j) = Im(be)/2.
+// Work items: the tri(ne) occupied pairs, the ne x d occupied-empty pairs and the
+// tri(d + 1) empty pairs j1 <= j2, each two n-term sums (the echelon zeros of Ut included,
+// so that every lane runs the same loop).
+__device__ inline void build_B_from_K(int n, int ne, const cd *__restrict__ Uts, const cd *__restrict__ Ks,
+                                      cd *__restrict__ Bs, const uint16_t *__restrict__ tab, int t, int nthr) {
+    const int d = n - ne, lu = ld_ut(n), lt = ld_t(n);
+    const int c1 = tri_count(ne), c2 = c1 + ne * d, c3 = c2 + tri_count(d + 1);
+    for (int it = t; it < c3; it += nthr) {
+        int a, b, kind;  // K row a, walker row b
+        if (it < c1) {
+            pair_of(tab, it, a, b);
+            kind = 0;
+        } else if (it < c2) {
+            const int e = it - c1, jj = e / ne;
+            a = e - jj * ne;
+            b = ne + jj;
+            kind = 1;
+        } else {
+            int x, y;
+            pair_of(tab, it - c2, x, y);  // x < y: empty modes x <= y - 1
+            a = ne + x;
+            b = ne + y - 1;
+            kind = 2;
+        }
+        const cd *kr = Ks + a * lt, *ur = Uts + b * lu;
+        cd w1 = cmk(0.0, 0.0), w2 = cmk(0.0, 0.0);
+        for (int k = 0; k < n; ++k) {
+            const cd u = ur[k];
+            cfma(w1, kr[k], u);
+            cfma(w2, kr[n + k], cconj(u));
+        }
+        if (kind == 0) {
+            Bs[tri_index(a, b)] = w1;
+        } else if (kind == 1) {
+            const int r = 2 * (b - ne);
+            const cd sp = cadd(w1, w2), dm = csub(w1, w2);
+            Bs[tri_index(a, ne + r)] = cscale(sp, 0.5);
+            Bs[tri_index(a, ne + r + 1)] = cmk(-0.5 * dm.y, 0.5 * dm.x);
+        } else {
+            const int r1 = 2 * (a - ne), r2 = 2 * (b - ne);
+            if (r1 < r2) {
+                Bs[tri_index(ne + r1, ne + r2)] = cmk(0.5 * (w1.x + w2.x), 0.0);
+                Bs[tri_index(ne + r1, ne + r2 + 1)] = cmk(0.5 * (w2.y - w1.y), 0.0);
+                Bs[tri_index(ne + r1 + 1, ne + r2)] = cmk(-0.5 * (w1.y + w2.y), 0.0);
+                Bs[tri_index(ne + r1 + 1, ne + r2 + 1)] = cmk(0.5 * (w2.x - w1.x), 0.0);
+            } else {
+                Bs[tri_index(ne + r1, ne + r1 + 1)] = cmk(0.5 * w2.y, 0.0);
+            }
+        }
+    }
+}
 
 // Two warps (a group of 64 threads) per pair; a block holds blockDim/64 groups,
 // each with its own workspace and named barrier.  Groups pull (walker, chunk)
@@ -142,7 +243,7 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                         kc[2 * k + slot] = (uint8_t)c;
                     }
                 } else {
-                    load_Qt(n, A.Qt + q * n2 * n, Qs, t, kGroup);
+                    load_Qt(n, A.Qh + q * n2 * n, Qs, t, kGroup);  // [H1^T; G2^T]: K = Ut Qh^T in T's place
                     if (n == 16)  // re + im of the walker rows for build_T_reg, in G_X's region (free here)
                         for (int e = t; e < n * n; e += kGroup) {
                             const int j = e / n, k = e - j * n;
@@ -156,7 +257,8 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                     build_T_reg<16>(ne, Uts, Uss, Qs, Ts, t & 31, false, lq, t >> 5, kGroup / 32);
                 else build_T_echelon(n, ne, Uts, Qs, Ts, t, kGroup);  // walker rows in echelon form
                 group_sync(bar);
-                build_B(n, ne, Ts, Bs, tab, t, kGroup);
+                if (sp) build_B(n, ne, Ts, Bs, tab, t, kGroup);
+                else build_B_from_K(n, ne, Uts, Ts, Bs, tab, t, kGroup);
                 group_sync(bar);
                 cd S = cmk(0.0, 0.0);
                 // Y = (1/2) sum_k gamma_k pf_k A_k^{-1}: block form when the occupied block
@@ -218,33 +320,36 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                     if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
                     Ssum = cadd(Ssum, S);
                 }
-                // G_X / 2 = Y (X J): (XJ)[b][2k] = -X[b][2k+1], (XJ)[b][2k+1] = X[b][2k]
-                for (int e = t; e < m * n2; e += kGroup) {
-                    const int a = e / n2, c = e - a * n2;
-                    const int cx = c ^ 1;
-                    const bool neg = !(c & 1);
-                    cd acc = cmk(0.0, 0.0);
-                    for (int b = 0; b < ne; ++b) cfma(acc, skew_at(Ys, a, b), Ts[b * lt + cx]);
-                    for (int r = 0; r < m - ne; ++r) {
-                        cd tt = Ts[(ne + (r >> 1)) * lt + cx];
-                        double x = (r & 1) ? -tt.y : tt.x;
-                        crfma(acc, skew_at(Ys, a, ne + r), x);
-                    }
-                    GX[e] = flip_if(acc, neg);
-                }
-                group_sync(bar);
-                // empty rows: Ht_i = G[ne+2i] - i G[ne+2i+1] into row ne+2i (factor 1/2 applied at the end)
-                for (int e = t; e < A.d * n2; e += kGroup) {
-                    const int i = e / n2, c = e - i * n2;
-                    cd g0 = GX[(ne + 2 * i) * n2 + c], g1 = GX[(ne + 2 * i + 1) * n2 + c];
-                    GX[(ne + 2 * i) * n2 + c] = cmk(g0.x + g1.y, g0.y - g1.x);
-                }
-                group_sync(bar);
-                // Gamma1 (rows < ne) += G[occ] Qt ; Gamma2 (rows >= ne) += Ht conj(Qt)
+                // Cotangents: Gamma1 (rows < ne) += G_X[occ] Qt and Gamma2 (rows >= ne) += Ht conj(Qt),
+                // G_X / 2 = Y (X J) and Ht_i = G[ne+2i] - i G[ne+2i+1] = Yh_i (X J), where
+                // Yh_i = Y[ne+2i] - i Y[ne+2i+1] (G_X is linear in Y's rows).
                 if (sp) {
+                    // signed permutation: G_X on the occupied rows and Ht, then gathers of Qt
+                    cd *Yh = GX + n * n2;  // d x m, after G_X's n x 2n entries
+                    for (int e = t; e < A.d * m; e += kGroup) {
+                        const int i = e / m, b = e - i * m;
+                        const cd y0 = skew_at(Ys, ne + 2 * i, b), y1 = skew_at(Ys, ne + 2 * i + 1, b);
+                        Yh[e] = cmk(y0.x + y1.y, y0.y - y1.x);
+                    }
+                    group_sync(bar);
+                    // (XJ)[b][2k] = -X[b][2k+1], (XJ)[b][2k+1] = X[b][2k]; row ne + i of GX is Ht_i
+                    for (int e = t; e < n * n2; e += kGroup) {
+                        const int a = e / n2, c = e - a * n2;
+                        const int cx = c ^ 1;
+                        const bool occ = a < ne;
+                        const cd *yh = Yh + (occ ? 0 : (a - ne) * m);
+                        cd acc = cmk(0.0, 0.0);
+                        for (int b = 0; b < ne; ++b) cfma(acc, occ ? skew_at(Ys, a, b) : yh[b], Ts[b * lt + cx]);
+                        for (int r = 0; r < m - ne; ++r) {
+                            const cd tt = Ts[(ne + (r >> 1)) * lt + cx];
+                            crfma(acc, occ ? skew_at(Ys, a, ne + r) : yh[ne + r], (r & 1) ? -tt.y : tt.x);
+                        }
+                        GX[e] = flip_if(acc, !(c & 1));
+                    }
+                    group_sync(bar);
                     for (int e = t; e < n * n; e += kGroup) {
                         const int j = e / n, k = e - j * n;
-                        const cd *g = GX + (j < ne ? j : ne + 2 * (j - ne)) * n2;
+                        const cd *g = GX + j * n2;
                         cd acc = Gs[e];
                         for (int h = 0; h < 2; ++h) {
                             const int c = kc[2 * k + h];
@@ -253,51 +358,48 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                         }
                         Gs[e] = acc;
                     }
-                } else if (T >= n * n) {
-                    // three real products per complex multiply-add: with s = re + im of the
-                    // snapshot entries (staged in B's region, free by now) and, per cotangent
-                    // row, re + im (occupied rows) or re - im (the Ht rows) staged in Y's,
-                    //   G q:       Re = p1 - p2, Im = p3 - p1 - p2,   p3 = sum (g_r + g_i) s
-                    //   H conj(q): Re = p1 + p2, Im = p1 - p2 - p3,   p3 = sum (h_r - h_i) s
-                    double *qsum = reinterpret_cast<double *>(Bs);  // 2n x n
-                    double *gsum = reinterpret_cast<double *>(Ys);  // n x 2n (row j: occupied j or Ht)
-                    for (int e = t; e < n2 * n; e += kGroup) {
-                        const int c = e / n, k = e - c * n;
-                        const cd q = Qs[c * lq + k];
-                        qsum[e] = q.x + q.y;
-                    }
-                    for (int e = t; e < n * n2; e += kGroup) {
-                        const int j = e / n2, c = e - j * n2;
-                        const cd g = GX[(j < ne ? j : ne + 2 * (j - ne)) * n2 + c];
-                        gsum[e] = j < ne ? g.x + g.y : g.x - g.y;
+                } else {
+                    // dense: X J Qt and X J conj(Qt) are rows of K = [Ut H1 | Ut G2]: occupied row b
+                    // gives K1_b and K2_b; the empty rows R_j, I_j give (K1_j + conj K2_j)/2,
+                    // i (K1_j - conj K2_j)/2 and their conjugates.  So with the source row y (Y[r]
+                    // for r < ne, Yh_{r-ne} else) and c_j = (y[R_j] + i y[I_j])/2,
+                    // c'_j = (y[R_j] - i y[I_j])/2,
+                    //     Gamma1[r] += sum_b y[b] K1_b + sum_j (c_j K1_j + c'_j conj K2_j)
+                    //     Gamma2[r] += sum_b y[b] K2_b + sum_j (c_j K2_j + c'_j conj K1_j)
+                    // (n x m coefficients Cf in the node region, then n x n entries of m terms).
+                    cd *Cf = Ns;
+                    for (int e = t; e < n * m; e += kGroup) {
+                        const int r = e / m, b = e - r * m;
+                        const bool occ = r < ne;
+                        const int r0 = occ ? r : ne + 2 * (r - ne), r1 = occ ? r : r0 + 1;
+                        const bool pair = b >= ne;
+                        const int b0 = pair ? ne + ((b - ne) & ~1) : b;
+                        // y at columns b0 and bi = b0 + 1 (the second only for an empty pair)
+                        const int bi = pair ? b0 + 1 : b0;
+                        cd y0 = skew_at(Ys, r0, b0), y1 = skew_at(Ys, r1, b0);
+                        const cd yb = occ ? y0 : cmk(y0.x + y1.y, y0.y - y1.x);
+                        y0 = skew_at(Ys, r0, bi);
+                        y1 = skew_at(Ys, r1, bi);
+                        const cd yi = occ ? y0 : cmk(y0.x + y1.y, y0.y - y1.x);
+                        // c = (yb + i yi) / 2 at even offsets, c' = (yb - i yi) / 2 at odd ones
+                        const bool odd = (b - ne) & 1;
+                        const cd iy = flip_if(cmk(-yi.y, yi.x), odd);
+                        Cf[e] = pair ? cmk(0.5 * (yb.x + iy.x), 0.5 * (yb.y + iy.y)) : yb;
                     }
                     group_sync(bar);
                     for (int e = t; e < n * n; e += kGroup) {
-                        const int j = e / n, k = e - j * n;
-                        const cd *g = GX + (j < ne ? j : ne + 2 * (j - ne)) * n2;
-                        const double *gs = gsum + j * n2;
-                        double p1 = 0.0, p2 = 0.0, p3 = 0.0;
-                        for (int c = 0; c < n2; ++c) {
-                            const cd gv = g[c], q = Qs[c * lq + k];
-                            p1 = fma(gv.x, q.x, p1);
-                            p2 = fma(gv.y, q.y, p2);
-                            p3 = fma(gs[c], qsum[c * n + k], p3);
+                        const int r = e / n, k = e - r * n;
+                        const int o1 = r < ne ? 0 : n, o2 = n - o1;
+                        const cd *cf = Cf + r * m;
+                        cd acc = Gs[e];
+                        for (int b = 0; b < ne; ++b) cfma(acc, cf[b], Ts[b * lt + o1 + k]);
+                        for (int j = 0; j < A.d; ++j) {
+                            const cd *kr = Ts + (ne + j) * lt;
+                            cfma(acc, cf[ne + 2 * j], kr[o1 + k]);
+                            cfma(acc, cf[ne + 2 * j + 1], cconj(kr[o2 + k]));
                         }
-                        const cd acc = Gs[e];
-                        Gs[e] = j < ne ? cmk(acc.x + (p1 - p2), acc.y + (p3 - p1 - p2))
-                                       : cmk(acc.x + (p1 + p2), acc.y + (p1 - p2 - p3));
+                        Gs[e] = acc;
                     }
-                } else for (int e = t; e < n * n; e += kGroup) {
-                    const int j = e / n, k = e - j * n;
-                    cd acc = Gs[e];
-                    if (j < ne) {
-                        const cd *g = GX + j * n2;
-                        for (int c = 0; c < n2; ++c) cfma(acc, g[c], Qs[c * lq + k]);
-                    } else {
-                        const cd *g = GX + (ne + 2 * (j - ne)) * n2;
-                        for (int c = 0; c < n2; ++c) cfma(acc, g[c], cconj(Qs[c * lq + k]));
-                    }
-                    Gs[e] = acc;
                 }
             }
         }
@@ -539,6 +641,7 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     A.tab_bytes = (int)align16((size_t)tri_count(A.m) * sizeof(uint16_t));
     A.Ut = L.Ut;
     A.Qt = L.s->Qt;
+    A.Qh = L.Qh;
     A.gth = L.s->gth;
     A.idx = L.s->idx;
     A.d_count = L.s->d_count;
@@ -588,6 +691,17 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     if (blocks < 1) blocks = 1;
     if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return qcs_fail(ctx, QCS_ERR_CUDA, "grad tile counter reset");
+    {  // the listed dense snapshots' rows [H1^T; G2^T]
+        const size_t hsm = (size_t)2 * L.n * L.n * sizeof(cd);
+        if (qcs_set_smem(ctx, (const void *)grad_hform_kernel, hsm) != QCS_OK) return QCS_ERR_CUDA;
+        int64_t hb = (int64_t)ctx->num_sms * 8;
+        if (hb > L.P) hb = L.P;
+        if (hb < 1) hb = 1;
+        grad_hform_kernel<<<(unsigned)hb, 256, hsm, st>>>(L.n, L.P, A.all, A.idx, A.d_count, A.Qt, A.gth, L.Qh,
+                                                         ctx->d_status);
+        const qcs_status hr = qcs_check_launch(ctx, "grad_hform_kernel");
+        if (hr != QCS_OK) return hr;
+    }
     qcs_prof_begin(ctx, st);
     grad_pair_kernel<<<(unsigned)blocks, threads, smem, st>>>(A);
     qcs_prof_end(ctx, st);

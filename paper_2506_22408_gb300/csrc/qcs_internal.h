@@ -126,6 +126,7 @@ struct qcs_grad_launch {
     const cd *Wrot;   // per walker: det(conj W) W (ne x ne), then det(conj W); U_occ = U_qr W
     const cd *pref;
     const qcs_snapshots *s;
+    cd *Qh;          // P x 2n x n: the snapshots' rows [H1^T; G2^T] (written by the launcher)
     cd *partial;     // W x nchunks x (1 + n*n)
     cd *overlap;     // W
     cd *grad;        // W x n x ne

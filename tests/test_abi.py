@@ -81,13 +81,17 @@ def test_gradient_flop_accounting_host_only():
     elim = sum(step(r) for r in range(m, 2 * d, -2)) + nev * sum(step(r) for r in range(2 * d, 2, -2))
     inv = nev * (sum(bstep(rv) for rv in range(2 * d - 2, 0, -2)) + 8 * tri(2 * d))
     inv += sum(bstep(rv) for rv in range(2 * d, m - 1, 2))
-    gx = m * 2 * n * (8 * ne + 4 * (m - ne))        # G_X = Y (X J), real rows of the empty modes
-    gam = 6 * n * n * 2 * n + 2 * 2 * n * n + 3 * n * n + 2 * d * 2 * n
+    # B from K = Ut [H1 | G2] instead of from T: two n-term complex sums per work item
+    bk = 16 * n * (tri(ne) + ne * d + tri(d + 1)) + 8 * ne * d + 8 * tri(d) + d
+    # cotangents from K: coefficient rows, then n x n entries of m complex multiply-adds
+    gam = 8 * ne * d + d * (16 * d + 2 * ne) + 8 * n * n * m
     f = lib.qcs_grad_flops_per_pair(16, 8, 0, 0)
-    assert f == t + b + elim + inv + gx + gam
-    # signed permutations: T is a gather, each cotangent entry two complex additions
+    assert f == t + bk + elim + inv + gam
+    # signed permutations: T is a gather, B from T, G_X on the occupied rows and Ht = Yh (X J)
+    # on the empty modes (Yh = Y[ne+2i] - i Y[ne+2i+1]), each cotangent entry two complex additions
+    gx = 2 * d * m + n * 2 * n * (8 * ne + 4 * (m - ne)) + 4 * n * n
     fs = lib.qcs_grad_flops_per_pair_signed_perm(16, 8, 0, 0)
-    assert fs == f - t - (gam - 2 * d * 2 * n) + 4 * n * n
+    assert fs == f - t - bk + b - gam + gx
     assert lib.qcs_grad_flops_per_pair(16, 7, 0, 0) == 0.0
 
 
