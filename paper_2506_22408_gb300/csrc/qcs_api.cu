@@ -743,20 +743,22 @@ static double grad_B_from_T_flops(int n, int ne) {
 }
 
 // B from K (build_B_from_K): two n-term complex sums per work item (tri(ne) occupied
-// pairs, ne d occupied-empty pairs, tri(d + 1) empty pairs j1 <= j2), then the halved
-// sums and differences of the occupied-empty (8 flop) and distinct empty pairs (8 flop)
-// and one product per mode.
+// pairs, ne d occupied-empty pairs, tri(d + 1) empty pairs j1 <= j2) with three real
+// products per term and three additions per sum, then the halved sums and differences of
+// the occupied-empty (8 flop) and distinct empty pairs (8 flop) and one product per mode;
+// the staged sums re - im of Ut (n^2), re + im of K (2 n^2) and re - im of K's empty rows.
 static double grad_B_from_K_flops(int n, int ne) {
     const int d = n - ne;
     const double items = (double)tri_count(ne) + (double)ne * d + (double)tri_count(d + 1);
-    return 16.0 * n * items + 8.0 * ne * d + 8.0 * tri_count(d) + d;
+    return (12.0 * n + 6.0) * items + 8.0 * ne * d + 8.0 * tri_count(d) + d + 3.0 * n * n + 2.0 * d * n;
 }
 
 // Cotangents from K: the coefficient rows (Yh = Y[ne+2i] - i Y[ne+2i+1] and the halved
-// combinations of each empty pair), then n x n entries of m complex multiply-adds.
+// combinations of each empty pair) and their sums re + im, then n x n entries of m
+// complex multiply-adds with three real products each and five additions per entry.
 static double grad_gamma_from_K_flops(int n, int ne) {
     const int d = n - ne, m = 2 * n - ne;
-    return 8.0 * ne * d + d * (16.0 * d + 2.0 * ne) + 8.0 * n * n * m;
+    return 8.0 * ne * d + d * (16.0 * d + 2.0 * ne) + (double)n * m + 6.0 * n * n * m + 5.0 * n * n;
 }
 
 // Signed-permutation snapshots: Yh (d x m), G_X on the occupied rows and Ht on the empty

@@ -56,14 +56,16 @@ __device__ __forceinline__ void crfma(cd &acc, cd a, double r) {
     acc.y = fma(a.y, r, acc.y);
 }
 
-// 1/d for d = |a|^2 >= 0 by Newton-Raphson iteration for the reciprocal,
-// r <- r + r (1 - d r), from a single-precision seed (the method of Markstein, "Computation
-// of elementary functions on the IBM RISC System/6000 processor", IBM J. Res. Dev. 34,
-// 1990): the seed is the hardware's approximate FP32 reciprocal of d truncated to 20
-// mantissa bits, both conversions done on the bit patterns, so its relative error is
-// below 2^-19; each step squares it, and two steps leave only the rounding of the last
-// FMA (within 2 ulp of 1/d).  Four FP64 FMAs against the longer sequence of an IEEE
-// division; exponents outside the FP32 range (and zero, infinity, NaN) take the division.
+// 1/d for d = |a|^2 >= 0 from a single-precision seed r refined by one third-order step:
+// with e = 1 - d r, 1/d = r / (1 - e) = r (1 + e + e^2 + e^3 + ...), and the step keeps
+// r (1 + e + e^2), i.e. r + r (e + e^2) in two FMAs (the iteration for the reciprocal in
+// Markstein, "Computation of elementary functions on the IBM RISC System/6000 processor",
+// IBM J. Res. Dev. 34, 1990, carried one term further).  The seed is the hardware's
+// approximate FP32 reciprocal of d truncated to 20 mantissa bits, both conversions done on
+// the bit patterns, so |e| < 2^-19 and the truncation error e^3 is below 2^-57 relative:
+// the result is within one rounding of the last FMA (1 ulp) of 1/d.  Three FP64 FMAs
+// against the longer sequence of an IEEE division; exponents outside the FP32 range (and
+// zero, infinity, NaN) take the division.
 __device__ __forceinline__ double recip_nonneg(double d) {
     const unsigned hi = (unsigned)__double2hiint(d);
     const int E = (int)(hi >> 20) - 1023;  // d >= 0: no sign bit
@@ -71,12 +73,10 @@ __device__ __forceinline__ double recip_nonneg(double d) {
     float rf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(((unsigned)(E + 127) << 23) | ((hi & 0xfffffu) << 3))));
     const unsigned rb = __float_as_uint(rf);
-    double r = __hiloint2double((int)(((((rb >> 23) & 0xffu) + 1023u - 127u) << 20) | ((rb & 0x7fffffu) >> 3)),
-                                (int)((rb & 7u) << 29));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
+    const double r = __hiloint2double((int)(((((rb >> 23) & 0xffu) + 1023u - 127u) << 20) | ((rb & 0x7fffffu) >> 3)),
+                                      (int)((rb & 7u) << 29));
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // 1/a for complex a; returns 0 when a == 0.

@@ -110,9 +110,11 @@ __global__ void grad_hform_kernel(int n, int64_t P, int all, const int *__restri
 // Work items: the tri(ne) occupied pairs, the ne x d occupied-empty pairs and the
 // tri(d + 1) empty pairs j1 <= j2, each two n-term sums (the echelon zeros of Ut included,
 // so that every lane runs the same loop).
-__device__ inline void build_B_from_K(int n, int ne, const cd *__restrict__ Uts, const cd *__restrict__ Ks,
-                                      cd *__restrict__ Bs, const uint16_t *__restrict__ tab, int t, int nthr) {
-    const int d = n - ne, lu = ld_ut(n), lt = ld_t(n);
+__device__ inline void build_B_from_K(int n, int ne, const cd *__restrict__ Uts, const double *__restrict__ Uss,
+                                      const double *__restrict__ Usd, const cd *__restrict__ Ks,
+                                      const double *__restrict__ Ksum, cd *__restrict__ Bs,
+                                      const uint16_t *__restrict__ tab, int t, int nthr) {
+    const int d = n - ne, lu = ld_ut(n), lt = ld_t(n), n2 = 2 * n;
     const int c1 = tri_count(ne), c2 = c1 + ne * d, c3 = c2 + tri_count(d + 1);
     for (int it = t; it < c3; it += nthr) {
         int a, b, kind;  // K row a, walker row b
@@ -131,13 +133,21 @@ __device__ inline void build_B_from_K(int n, int ne, const cd *__restrict__ Uts,
             b = ne + y - 1;
             kind = 2;
         }
+        // three real products per complex term: K1 u with the sums re + im of both factors,
+        // K2 conj(u) with re + im of K2 and re - im of u
         const cd *kr = Ks + a * lt, *ur = Uts + b * lu;
-        cd w1 = cmk(0.0, 0.0), w2 = cmk(0.0, 0.0);
+        const double *ks = Ksum + a * n2, *us = Uss + b * lu, *ud = Usd + b * lu;
+        double p1 = 0.0, p2 = 0.0, p3 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
         for (int k = 0; k < n; ++k) {
-            const cd u = ur[k];
-            cfma(w1, kr[k], u);
-            cfma(w2, kr[n + k], cconj(u));
+            const cd u = ur[k], k1 = kr[k], k2 = kr[n + k];
+            p1 = fma(k1.x, u.x, p1);
+            p2 = fma(k1.y, u.y, p2);
+            p3 = fma(ks[k], us[k], p3);
+            q1 = fma(k2.x, u.x, q1);
+            q2 = fma(k2.y, u.y, q2);
+            q3 = fma(ks[n + k], ud[k], q3);
         }
+        const cd w1 = cmk(p1 - p2, p3 - p1 - p2), w2 = cmk(q1 + q2, q3 - q1 + q2);
         if (kind == 0) {
             Bs[tri_index(a, b)] = w1;
         } else if (kind == 1) {
@@ -186,7 +196,10 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
     cd *Gs = reinterpret_cast<cd *>(wb + A.off_G);
     cd *Ns = reinterpret_cast<cd *>(wb + A.off_NZ);  // node factors, then their inverses, then G_X
     cd *GX = Ns;
-    double *Uss = reinterpret_cast<double *>(Ns);  // while T is formed (n = 16): re + im of Ut
+    double *Uss = reinterpret_cast<double *>(Ns);  // while T (or K) and B are formed: re + im of Ut
+    double *Usd = Uss + n * lu;                     // and re - im of Ut
+    double *Ksum = reinterpret_cast<double *>(Qs);  // once K is formed: re + im of K (n x 2n)
+    double *Kdif = Ksum + n * n2;                   // and re - im of K's empty rows (d x 2n)
     cd *g1v = reinterpret_cast<cd *>(wb + A.off_g1);  // forward: U vectors
     cd *g2v = reinterpret_cast<cd *>(wb + A.off_g2);  // forward: V vectors
     cd *y1v = reinterpret_cast<cd *>(wb + A.off_y1);
@@ -244,12 +257,14 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                     }
                 } else {
                     load_Qt(n, A.Qh + q * n2 * n, Qs, t, kGroup);  // [H1^T; G2^T]: K = Ut Qh^T in T's place
-                    if (n == 16)  // re + im of the walker rows for build_T_reg, in G_X's region (free here)
-                        for (int e = t; e < n * n; e += kGroup) {
-                            const int j = e / n, k = e - j * n;
-                            const cd u = Uts[j * lu + k];
-                            Uss[j * lu + k] = u.x + u.y;
-                        }
+                    // re + im (for build_T_reg and B) and re - im (for B's conjugate products) of
+                    // the walker rows, in the node region (free here)
+                    for (int e = t; e < n * n; e += kGroup) {
+                        const int j = e / n, k = e - j * n;
+                        const cd u = Uts[j * lu + k];
+                        Uss[j * lu + k] = u.x + u.y;
+                        Usd[j * lu + k] = u.x - u.y;
+                    }
                 }
                 group_sync(bar);
                 if (sp) build_T_gather(n, Uts, gq, Ts, t, kGroup);
@@ -257,8 +272,18 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                     build_T_reg<16>(ne, Uts, Uss, Qs, Ts, t & 31, false, lq, t >> 5, kGroup / 32);
                 else build_T_echelon(n, ne, Uts, Qs, Ts, t, kGroup);  // walker rows in echelon form
                 group_sync(bar);
-                if (sp) build_B(n, ne, Ts, Bs, tab, t, kGroup);
-                else build_B_from_K(n, ne, Uts, Ts, Bs, tab, t, kGroup);
+                if (sp) {
+                    build_B(n, ne, Ts, Bs, tab, t, kGroup);
+                } else {
+                    for (int e = t; e < n * n2; e += kGroup) {  // Qh is no longer needed
+                        const int j = e / n2, c = e - j * n2;
+                        const cd k = Ts[j * lt + c];
+                        Ksum[e] = k.x + k.y;
+                        if (j >= ne) Kdif[e - ne * n2] = k.x - k.y;
+                    }
+                    group_sync(bar);
+                    build_B_from_K(n, ne, Uts, Uss, Usd, Ts, Ksum, Bs, tab, t, kGroup);
+                }
                 group_sync(bar);
                 cd S = cmk(0.0, 0.0);
                 // Y = (1/2) sum_k gamma_k pf_k A_k^{-1}: block form when the occupied block
@@ -366,8 +391,11 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                     // c'_j = (y[R_j] - i y[I_j])/2,
                     //     Gamma1[r] += sum_b y[b] K1_b + sum_j (c_j K1_j + c'_j conj K2_j)
                     //     Gamma2[r] += sum_b y[b] K2_b + sum_j (c_j K2_j + c'_j conj K1_j)
-                    // (n x m coefficients Cf in the node region, then n x n entries of m terms).
+                    // (n x m coefficients Cf and their sums re + im in the node region, then n x n
+                    // entries of m terms, three real products each: with the sums of K's entries
+                    // (re - im for the conjugated ones), Re = p1 - p2 and Im = p3 - p1 - p2).
                     cd *Cf = Ns;
+                    double *Cs = reinterpret_cast<double *>(Ns + n * m);
                     for (int e = t; e < n * m; e += kGroup) {
                         const int r = e / m, b = e - r * m;
                         const bool occ = r < ne;
@@ -384,21 +412,36 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                         // c = (yb + i yi) / 2 at even offsets, c' = (yb - i yi) / 2 at odd ones
                         const bool odd = (b - ne) & 1;
                         const cd iy = flip_if(cmk(-yi.y, yi.x), odd);
-                        Cf[e] = pair ? cmk(0.5 * (yb.x + iy.x), 0.5 * (yb.y + iy.y)) : yb;
+                        const cd c = pair ? cmk(0.5 * (yb.x + iy.x), 0.5 * (yb.y + iy.y)) : yb;
+                        Cf[e] = c;
+                        Cs[e] = c.x + c.y;
                     }
                     group_sync(bar);
                     for (int e = t; e < n * n; e += kGroup) {
                         const int r = e / n, k = e - r * n;
                         const int o1 = r < ne ? 0 : n, o2 = n - o1;
                         const cd *cf = Cf + r * m;
-                        cd acc = Gs[e];
-                        for (int b = 0; b < ne; ++b) cfma(acc, cf[b], Ts[b * lt + o1 + k]);
+                        const double *cs = Cs + r * m;
+                        double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+                        for (int b = 0; b < ne; ++b) {
+                            const cd c = cf[b], v = Ts[b * lt + o1 + k];
+                            p1 = fma(c.x, v.x, p1);
+                            p2 = fma(c.y, v.y, p2);
+                            p3 = fma(cs[b], Ksum[b * n2 + o1 + k], p3);
+                        }
                         for (int j = 0; j < A.d; ++j) {
                             const cd *kr = Ts + (ne + j) * lt;
-                            cfma(acc, cf[ne + 2 * j], kr[o1 + k]);
-                            cfma(acc, cf[ne + 2 * j + 1], cconj(kr[o2 + k]));
+                            const cd c = cf[ne + 2 * j], v = kr[o1 + k];
+                            p1 = fma(c.x, v.x, p1);
+                            p2 = fma(c.y, v.y, p2);
+                            p3 = fma(cs[ne + 2 * j], Ksum[(ne + j) * n2 + o1 + k], p3);
+                            const cd c2 = cf[ne + 2 * j + 1], w = kr[o2 + k];  // c2 conj(w)
+                            p1 = fma(c2.x, w.x, p1);
+                            p2 = fma(-c2.y, w.y, p2);
+                            p3 = fma(cs[ne + 2 * j + 1], Kdif[j * n2 + o2 + k], p3);
                         }
-                        Gs[e] = acc;
+                        const cd acc = Gs[e];
+                        Gs[e] = cmk(acc.x + (p1 - p2), acc.y + (p3 - p1 - p2));
                     }
                 }
             }

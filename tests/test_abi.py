@@ -81,10 +81,13 @@ def test_gradient_flop_accounting_host_only():
     elim = sum(step(r) for r in range(m, 2 * d, -2)) + nev * sum(step(r) for r in range(2 * d, 2, -2))
     inv = nev * (sum(bstep(rv) for rv in range(2 * d - 2, 0, -2)) + 8 * tri(2 * d))
     inv += sum(bstep(rv) for rv in range(2 * d, m - 1, 2))
-    # B from K = Ut [H1 | G2] instead of from T: two n-term complex sums per work item
-    bk = 16 * n * (tri(ne) + ne * d + tri(d + 1)) + 8 * ne * d + 8 * tri(d) + d
-    # cotangents from K: coefficient rows, then n x n entries of m complex multiply-adds
-    gam = 8 * ne * d + d * (16 * d + 2 * ne) + 8 * n * n * m
+    # B from K = Ut [H1 | G2] instead of from T: two n-term complex sums per work item, three
+    # real products per term, plus the staged sums of Ut and K
+    items = tri(ne) + ne * d + tri(d + 1)
+    bk = (12 * n + 6) * items + 8 * ne * d + 8 * tri(d) + d + 3 * n * n + 2 * d * n
+    # cotangents from K: coefficient rows and their sums, then n x n entries of m complex
+    # multiply-adds with three real products each
+    gam = 8 * ne * d + d * (16 * d + 2 * ne) + n * m + 6 * n * n * m + 5 * n * n
     f = lib.qcs_grad_flops_per_pair(16, 8, 0, 0)
     assert f == t + bk + elim + inv + gam
     # signed permutations: T is a gather, B from T, G_X on the occupied rows and Ht = Yh (X J)

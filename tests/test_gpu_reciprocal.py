@@ -1,8 +1,9 @@
-"""The pivot reciprocal of the eliminations (Newton-Raphson steps from a single-precision
-seed, qcs_common.cuh) against the correctly rounded 1/d of the host's IEEE division: every
-pivot step of every FP64 path divides by |pivot|^2 through it, so its error enters each
-Gauss vector.  Bound: 2 ulp; the values outside the seed's exponent range take the
-device's IEEE division and must match exactly."""
+"""The pivot reciprocal of the eliminations (one third-order step r (1 + e + e^2) from a
+single-precision seed, qcs_common.cuh) against the correctly rounded 1/d of the host's IEEE
+division: every pivot step of every FP64 path divides by |pivot|^2 through it, so its error
+enters each Gauss vector.  Bound: 2 ulp (the step's truncation error e^3 < 2^-57 plus the
+last FMA's rounding); the values outside the seed's exponent range take the device's IEEE
+division and must match exactly."""
 from __future__ import annotations
 
 import numpy as np
