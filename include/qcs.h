@@ -389,7 +389,10 @@ qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_system *systems
  * such as unit-vector walkers with signed-permutation snapshots produce): the
  * formula needs A(z_k)^{-1}, and that node's term is then left out of the
  * gradient (the overlap itself stays exact).  Nearly singular node matrices
- * need no special case. */
+ * need no special case.  Context workspace: per walker its rows, QR factors and
+ * per-chunk records, and per snapshot of the set 32 n^2 bytes (the rows
+ * [H1^T; G2^T], H1 = Qt^T J Qt and G2 = Qt^T J conj(Qt), through which B and the
+ * cotangents of a dense snapshot are formed). */
 qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int ne, int64_t W, const double *d_walkers,
                             double *d_overlap, double *d_grad, const qcs_opts *opts, void *stream);
 
