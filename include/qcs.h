@@ -479,12 +479,16 @@ qcs_status qcs_fp64_fma_rate(qcs_ctx *ctx, double *tflops, void *stream);
 /* ----------------------------------------------------------- accounting */
 
 /* Algorithmic FP64 flop count per non-trivial (pi = +1) pair of qcs_overlap
- * for (n, ne, nodes), as implemented: congruence T = U^T Qtilde^T, the
- * selected covariance B^(s), and the rank-2 Pfaffian updates.  The walker's
+ * for (n, ne, nodes), as implemented on the FP64 ALU: the congruence K = U^T Qh^T
+ * (Qh the snapshot's rows [H1^T; G2^T], H1 = Qtilde^T J Qtilde, G2 = Qtilde^T J
+ * conj(Qtilde), formed once per snapshot set; K costs what T = U^T Qtilde^T would),
+ * the selected covariance B^(s) from K and the walker rows (T J T^T = U^T H1 U,
+ * T J conj(T)^T = U^T G2 conj(U), sums over the walker rows' non-zero entries
+ * only), and the rank-2 Pfaffian updates.  The walker's
  * orbitals are first rotated to echelon form (a reflection of the occupied
  * columns changes det R by its sign, one of the complement changes nothing),
  * which makes ne(ne-1)/2 + d(d-1)/2 entries of U exact zeros that T skips.
- * At n = 16 the occupied orbitals are further taken in reduced form [I; X]
+ * The occupied orbitals are further taken in reduced form [I; X]
  * (an invertible change of basis, det folded into det R), leaving one non-zero
  * among the first ne entries of each occupied row; walkers whose X would exceed
  * 16 in magnitude (about 3 % of random walkers) keep the echelon form and do
@@ -492,16 +496,16 @@ qcs_status qcs_fp64_fma_rate(qcs_ctx *ctx, double *tflops, void *stream);
  * The node matrices differ only in their empty x empty block, so the occupied
  * block is eliminated once per pair and each node then costs a 2d x 2d
  * Pfaffian; the count is that of this path (pairs whose occupied block would
- * grow the complement more than 32-fold, a few percent, take the full
- * elimination per node instead).  Used by the benchmark's roofline. */
+ * grow the complement more than 2^8-fold, rare, take the full elimination per
+ * node instead).  Used by the benchmark's roofline. */
 double qcs_overlap_flops_per_pair(int n, int ne, int nodes, unsigned flags);
 
 /* The same count for a pair whose snapshot is a signed permutation (no FP64
- * work in the congruence). */
+ * work in the congruence, B^(s) from the gathered T). */
 double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags);
 
 /* Host only: the parts of qcs_overlap_flops_per_pair, parts[0] the congruence T,
- * parts[1] the covariance B^(s), parts[2] the Pfaffian eliminations (the shared
+ * parts[1] the covariance B^(s) (from K), parts[2] the Pfaffian eliminations (the shared
  * occupied steps and the node complements).  At n = 16 the congruence takes three
  * real products per complex multiply-add (counted as executed: 6 flop, plus the
  * sums that form the two results and the snapshot row's re + im); elsewhere four

@@ -380,6 +380,7 @@ extern "C" qcs_status qcs_snapshots_free(qcs_snapshots *s) {
     qcs_dev_free(s->alloc, s->split_hi, s->split_bytes);
     qcs_dev_free(s->alloc, s->split_lo, s->split_bytes);
     qcs_dev_free(s->alloc, s->tc_rec, s->tc_bytes);
+    qcs_dev_free(s->alloc, s->Qh, s->qh_bytes);
     delete s;
     return QCS_OK;
 }
@@ -546,6 +547,8 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
         if (r != QCS_OK) return r;
         r = qcs_launch_tc_pairs(ctx, L, wk.walk_rec, st);
     } else {
+        r = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
+        if (r != QCS_OK) return r;
         r = qcs_launch_pairs(ctx, L, st);
     }
     if (r != QCS_OK) return r;
@@ -596,6 +599,8 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         L.s = s;
         L.per_pair = nullptr;
         L.counter = nullptr;
+        qcs_status hr = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
+        if (hr != QCS_OK) return hr;
         off[i][0] = total;
         total += align16(sizeof(cd) * (size_t)y.W * s->n * s->n);
         off[i][1] = total;
@@ -667,9 +672,8 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     size_t b_r = align16(sizeof(cd) * (size_t)W * ne * ne);
     size_t b_w = align16(sizeof(cd) * (size_t)W * ((size_t)ne * ne + 1));
     size_t b_part = align16(sizeof(cd) * (size_t)W * nchunks * (1 + (size_t)n * n));
-    size_t b_qh = align16(sizeof(cd) * (size_t)s->P * 2 * n * n);
     void *base = nullptr;
-    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w + b_qh, &base, st);
+    qcs_status ws = qcs_workspace(ctx, 16 + b_ut + b_pref + b_u + b_r + b_part + b_w, &base, st);
     if (ws != QCS_OK) return ws;
     unsigned long long *gcounter = (unsigned long long *)base;
     char *pb = (char *)base + 16;
@@ -679,11 +683,12 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     cd *R = (cd *)(pb + b_ut + b_pref + b_u);
     cd *part = (cd *)(pb + b_ut + b_pref + b_u + b_r);
     cd *Wrot = (cd *)(pb + b_ut + b_pref + b_u + b_r + b_part);
-    cd *Qh = (cd *)(pb + b_ut + b_pref + b_u + b_r + b_part + b_w);
     // echelon-form walker rows (the congruence skips their zeros); U is the rotated unitary,
     // R the QR's triangular factor and Wrot the occupied columns' rotation for the epilogue
     qcs_status r = qcs_launch_walker_prep(ctx, n, ne, W, (const cd *)d_walkers, Ut, pref, st, U, R, true, nullptr,
                                           Wrot);
+    if (r != QCS_OK) return r;
+    r = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
     if (r != QCS_OK) return r;
     qcs_grad_launch L;
     L.n = n;
@@ -698,7 +703,6 @@ extern "C" qcs_status qcs_overlap_grad(qcs_ctx *ctx, const qcs_snapshots *s, int
     L.Wrot = Wrot;
     L.pref = pref;
     L.s = s;
-    L.Qh = Qh;
     L.partial = part;
     L.overlap = (cd *)d_overlap;
     L.grad = (cd *)d_grad;
@@ -742,7 +746,21 @@ static double grad_B_from_T_flops(int n, int ne) {
     return 8.0 * 2.0 * n * tri_count(ne) + 4.0 * 2.0 * n * ne * 2 * d + 2.0 * 2.0 * n * tri_count(2 * d);
 }
 
-// B from K (build_B_from_K): two n-term complex sums per work item (tri(ne) occupied
+// B from K in the two-warp overlap kernel above 16 modes (build_B_from_K of qcs_pair.cuh):
+// each sum runs over the non-zero columns of its walker row with three real products per
+// term (6 flop) and three additions per sum: occupied pairs W1 alone over the reduced row's
+// 1 + d columns; completion row ne + j carries ne + j + 1 items of W1 and W2 over n - j
+// columns; 8 flop of halved sums and differences per occupied-empty or distinct empty pair,
+// 1 per mode; re + im of K's 2n^2 entries.
+static double alu_B_from_K_flops(int n, int ne) {
+    const int d = n - ne;
+    double rows = 0.0;
+    for (int j = 0; j < d; ++j) rows += (ne + j + 1.0) * (12.0 * (n - j) + 6.0);
+    return tri_count(ne) * (6.0 * (1 + d) + 3.0) + rows + 8.0 * ne * d + 8.0 * tri_count(d) + d +
+           2.0 * n * n;
+}
+
+// B from K in the gradient (build_B_from_K3): two n-term complex sums per work item (tri(ne) occupied
 // pairs, ne d occupied-empty pairs, tri(d + 1) empty pairs j1 <= j2) with three real
 // products per term and three additions per sum, then the halved sums and differences of
 // the occupied-empty (8 flop) and distinct empty pairs (8 flop) and one product per mode;
@@ -796,7 +814,7 @@ extern "C" double qcs_overlap_flops_per_pair_signed_perm(int n, int ne, int node
     if (qcs_make_node_plan(n, ne, nodes, flags, &plan) != QCS_OK) return 0.0;
     double part[3];
     overlap_flops_parts(n, ne, plan.nev, true, part);
-    return part[1] + part[2];  // T is a gather
+    return grad_B_from_T_flops(n, ne) + part[2];  // T is a gather, B is formed from it
 }
 
 extern "C" double qcs_grad_flops_per_pair_signed_perm(int n, int ne, int nodes, unsigned flags) {
@@ -843,9 +861,8 @@ static void overlap_flops_parts(int n, int ne, int nev, bool overlap_kernel, dou
         part[0] = 6.0 * macs + 3.0 * 2.0 * n * n + 2.0 * n * n;
     else
         part[0] = 8.0 * macs;
-    part[1] = 8.0 * 2.0 * (double)n * tri_count(ne)          // occupied x occupied
-              + 4.0 * 2.0 * (double)n * ne * 2 * d             // occupied x empty
-              + 2.0 * 2.0 * (double)n * tri_count(2 * d);      // empty x empty
+    // B: from K on the two-warp path above 16 modes, from T elsewhere
+    part[1] = overlap_kernel && n > 16 ? alu_B_from_K_flops(n, ne) : grad_B_from_T_flops(n, ne);
     double node = 0.0;
     if (overlap_kernel) {  // occupied block once, then each node's 2d x 2d complement
         part[2] = qcs_pf_elim_flops(m, 2 * d);

@@ -59,46 +59,6 @@ struct GradArgs {
     cd gamma[QCS_MAX_NODES];
 };
 
-// Per listed snapshot with a dense Qt: Qh = [H1^T; G2^T] (2n x n, Qt's layout) with
-// H1 = Qt^T J Qt and G2 = Qt^T J conj(Qt) (n x n; J pairs the Majorana indices 2a, 2a + 1
-// with J[2a][2a+1] = 1).  Every pair product of the gradient then needs only
-// K = Ut Qh^T = [Ut H1 | Ut G2] (formed like T) instead of T:
-//     T_j J T_k^T = (Ut H1 Ut^T)[j][k],   T_j J conj(T_k)^T = (Ut G2 Ut^H)[j][k],
-//     T_j J Qt = (Ut H1)[j],              T_j J conj(Qt) = (Ut G2)[j],
-// so B and the cotangents Gamma1, Gamma2 follow from K without the 2n-wide G_X.
-__global__ void grad_hform_kernel(int n, int64_t P, int all, const int *__restrict__ idx,
-                                  const int *__restrict__ d_count, const cd *__restrict__ Qt,
-                                  const uint8_t *__restrict__ gth, cd *__restrict__ Qh, unsigned *status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cd *Qs = reinterpret_cast<cd *>(smem_raw);  // 2n x n
-    const int n2 = 2 * n;
-    if (!QCS_IN_BOUNDS((size_t)n2 * n * sizeof(cd) <= dyn_smem_bytes(), status)) return;
-    const int64_t L = all ? P : (int64_t)(*d_count);
-    for (int64_t pq = blockIdx.x; pq < L; pq += gridDim.x) {
-        const int64_t q = all ? pq : (int64_t)idx[pq];
-        if (!QCS_IN_BOUNDS(q >= 0 && q < P, status)) continue;  // block-uniform
-        if (gth && gth[q * n2] != 0xFF) continue;              // signed permutation: T is a gather
-        __syncthreads();
-        for (int e = threadIdx.x; e < n2 * n; e += blockDim.x) Qs[e] = Qt[q * n2 * n + e];
-        __syncthreads();
-        cd *out = Qh + q * n2 * n;
-        for (int e = threadIdx.x; e < n2 * n; e += blockDim.x) {
-            const int c = e / n, k = e - c * n;
-            const bool g2 = c >= n;  // row c of Qh: column c of H1, or column c - n of G2
-            const int l = g2 ? c - n : c;
-            cd acc = cmk(0.0, 0.0);
-            for (int a = 0; a < n; ++a) {
-                cd x = Qs[(2 * a + 1) * n + l], y = Qs[(2 * a) * n + l];
-                x.y = g2 ? -x.y : x.y;
-                y.y = g2 ? -y.y : y.y;
-                cfma(acc, Qs[(2 * a) * n + k], x);
-                cfms(acc, Qs[(2 * a + 1) * n + k], y);
-            }
-            out[e] = acc;
-        }
-    }
-}
-
 // B (packed upper, m x m) from K = [Ut H1 | Ut G2] (rows of Ks, stride ld_t) and the walker
 // rows Ut: with W1 = (Ut H1) Ut^T = T J T^T and W2 = (Ut G2) Ut^H = T J conj(T)^T, and the
 // empty rows R_j = Re T_j, I_j = -Im T_j of X,
@@ -110,7 +70,7 @@ __global__ void grad_hform_kernel(int n, int64_t P, int all, const int *__restri
 // Work items: the tri(ne) occupied pairs, the ne x d occupied-empty pairs and the
 // tri(d + 1) empty pairs j1 <= j2, each two n-term sums (the echelon zeros of Ut included,
 // so that every lane runs the same loop).
-__device__ inline void build_B_from_K(int n, int ne, const cd *__restrict__ Uts, const double *__restrict__ Uss,
+__device__ inline void build_B_from_K3(int n, int ne, const cd *__restrict__ Uts, const double *__restrict__ Uss,
                                       const double *__restrict__ Usd, const cd *__restrict__ Ks,
                                       const double *__restrict__ Ksum, cd *__restrict__ Bs,
                                       const uint16_t *__restrict__ tab, int t, int nthr) {
@@ -282,7 +242,7 @@ __global__ void __launch_bounds__(128, 2) grad_pair_kernel(const __grid_constant
                         if (j >= ne) Kdif[e - ne * n2] = k.x - k.y;
                     }
                     group_sync(bar);
-                    build_B_from_K(n, ne, Uts, Uss, Usd, Ts, Ksum, Bs, tab, t, kGroup);
+                    build_B_from_K3(n, ne, Uts, Uss, Usd, Ts, Ksum, Bs, tab, t, kGroup);
                 }
                 group_sync(bar);
                 cd S = cmk(0.0, 0.0);
@@ -684,7 +644,7 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     A.tab_bytes = (int)align16((size_t)tri_count(A.m) * sizeof(uint16_t));
     A.Ut = L.Ut;
     A.Qt = L.s->Qt;
-    A.Qh = L.Qh;
+    A.Qh = L.s->Qh;
     A.gth = L.s->gth;
     A.idx = L.s->idx;
     A.d_count = L.s->d_count;
@@ -734,17 +694,6 @@ qcs_status qcs_launch_grad(qcs_ctx *ctx, const qcs_grad_launch &L, cudaStream_t 
     if (blocks < 1) blocks = 1;
     if (cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st) != cudaSuccess)
         return qcs_fail(ctx, QCS_ERR_CUDA, "grad tile counter reset");
-    {  // the listed dense snapshots' rows [H1^T; G2^T]
-        const size_t hsm = (size_t)2 * L.n * L.n * sizeof(cd);
-        if (qcs_set_smem(ctx, (const void *)grad_hform_kernel, hsm) != QCS_OK) return QCS_ERR_CUDA;
-        int64_t hb = (int64_t)ctx->num_sms * 8;
-        if (hb > L.P) hb = L.P;
-        if (hb < 1) hb = 1;
-        grad_hform_kernel<<<(unsigned)hb, 256, hsm, st>>>(L.n, L.P, A.all, A.idx, A.d_count, A.Qt, A.gth, L.Qh,
-                                                         ctx->d_status);
-        const qcs_status hr = qcs_check_launch(ctx, "grad_hform_kernel");
-        if (hr != QCS_OK) return hr;
-    }
     qcs_prof_begin(ctx, st);
     grad_pair_kernel<<<(unsigned)blocks, threads, smem, st>>>(A);
     qcs_prof_end(ctx, st);

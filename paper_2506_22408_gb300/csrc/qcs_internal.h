@@ -56,7 +56,9 @@ struct qcs_snapshots {
     void *split_lo = nullptr;
     void *tc_rec = nullptr;   // tensor-core congruence: BF16 slices of H_p = N^T J N for the parity +1
                               // list, four snapshots per record (57,856 bytes), built once
-    size_t split_bytes = 0, tc_bytes = 0;  // sizes of the lazily built buffers (for the allocator)
+    cd *Qh = nullptr;         // P x 2n x n rows [H1^T; G2^T], H1 = Qt^T J Qt, G2 = Qt^T J conj(Qt), of
+                              // each dense snapshot (FP64 ALU overlaps, gradient), built on first use
+    size_t split_bytes = 0, tc_bytes = 0, qh_bytes = 0;  // sizes of the lazily built buffers (for the allocator)
     qcs_allocator alloc;      // the allocator the set's buffers came from
 };
 
@@ -126,7 +128,6 @@ struct qcs_grad_launch {
     const cd *Wrot;   // per walker: det(conj W) W (ne x ne), then det(conj W); U_occ = U_qr W
     const cd *pref;
     const qcs_snapshots *s;
-    cd *Qh;          // P x 2n x n: the snapshots' rows [H1^T; G2^T] (written by the launcher)
     cd *partial;     // W x nchunks x (1 + n*n)
     cd *overlap;     // W
     cd *grad;        // W x n x ne
@@ -189,6 +190,8 @@ bool qcs_tc_supported(int n);      // n <= 16
 size_t qcs_tc_walker_bytes(int64_t W);
 int qcs_tc_snaps_per_tile(int subs);  // parity +1 snapshots per tile (subs sub-tiles; 0 = default)
 qcs_status qcs_tc_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
+// The rows [H1^T; G2^T] of every dense snapshot into s->Qh (allocated and formed once).
+qcs_status qcs_hform_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
 qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned char *walk_rec, cudaStream_t st);
 qcs_status qcs_launch_pairs_batched(qcs_ctx *ctx, int nsys, const qcs_pair_launch *Ls, unsigned long long *counter,
                                     cudaStream_t st);

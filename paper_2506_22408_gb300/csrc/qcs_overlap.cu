@@ -58,6 +58,7 @@ struct PairArgs {
     const cd *pref;
     const int *wmode;  // per walker: occupied rows in reduced form (register path), or null
     const cd *Qt;
+    const cd *Qh;        // rows [H1^T; G2^T] of the dense snapshots (null: T and B from Qt)
     const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
     const int *idx;
     const int *d_count;
@@ -140,18 +141,34 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
                 if (!QCS_IN_BOUNDS(q >= 0 && q < A.P, A.status)) continue;  // group-uniform
                 const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
                 group_sync(bar);
-                if (gq && gq[0] != 0xFF) {
+                const bool gat = gq && gq[0] != 0xFF;
+                if (gat) {
                     build_T_gather(n, Uts, gq, gTs, t, kGroup);
                 } else {
-                    for (int h = 0; h < 2; ++h) {  // T by column halves: half of Qt staged at a time
-                        load_Qt_rows_sums(n, A.Qt + (q * n2 + (int64_t)h * n) * n, gQs, gqs, t, kGroup);
+                    // T (or K = Ut [H1 | G2] from the rows Qh) by column halves: half of the
+                    // snapshot's rows staged at a time
+                    const cd *Qr = (A.Qh ? A.Qh : A.Qt) + q * n2 * n;
+                    for (int h = 0; h < 2; ++h) {
+                        load_Qt_rows_sums(n, Qr + (int64_t)h * n * n, gQs, gqs, t, kGroup);
                         group_sync(bar);
                         build_T_half3(n, ne, redw, Uts, Uss, gQs, gqs, gTs, h * n, t, kGroup);
                         group_sync(bar);
                     }
                 }
                 group_sync(bar);
-                build_B(n, ne, gTs, gBs, tab, t, kGroup);
+                if (!gat && A.Qh) {
+                    // B from K: re + im of K1 and re - im of K2 into the staging region (free now)
+                    double *gks = reinterpret_cast<double *>(gQs);
+                    for (int e = t; e < n * n2; e += kGroup) {
+                        const int j = e / n2, c = e - j * n2;
+                        const cd k = gTs[j * ld_t(n) + c];
+                        gks[e] = c < n ? k.x + k.y : k.x - k.y;
+                    }
+                    group_sync(bar);
+                    build_B_from_K(n, ne, redw, Uts, Uss, gTs, gks, gBs, tab, t, kGroup);
+                } else {
+                    build_B(n, ne, gTs, gBs, tab, t, kGroup);
+                }
                 group_sync(bar);
                 cd S = cmk(0.0, 0.0);
                 if (shared_factor(m, ne, gBs, gNs, gUv, gVv, ginvh, gacth, gkh, gph, gscr, tab, t, bar)) {
@@ -196,22 +213,24 @@ __device__ void run_tile(const PairArgs &A, int64_t tile, int64_t L, unsigned ch
             const int64_t q = A.all ? pq : (int64_t)A.idx[pq];
             if (!QCS_IN_BOUNDS(q >= 0 && q < A.P, A.status)) continue;  // warp-uniform
             const uint8_t *gq = A.gth ? A.gth + q * n2 : nullptr;
+            const bool gat = gq && gq[0] != 0xFF;
+            const cd *Qr = A.Qt + q * n2 * n;
             __syncwarp();
-            if (gq && gq[0] != 0xFF) {
+            if (gat) {
                 build_T_gather(n, Uts, gq, Ts, lane);  // signed permutation: no products
             } else if (A.reg) {
-                build_T_reg<16>(A.ne, Uts, Uss, A.Qt + q * n2 * n, Ts, lane, redw);
+                build_T_reg<16>(A.ne, Uts, Uss, Qr, Ts, lane, redw);
             } else if (A.t3) {
                 // staged rows and their re + im sums; T by three real products per
                 // complex multiply-add, skipping the zeros of the echelon or reduced form
                 double *qs = reinterpret_cast<double *>(wbase + A.off_qs);
-                load_Qt_rows_sums(n, A.Qt + q * n2 * n, Qs, qs, lane, 32);
-                load_Qt_rows_sums(n, A.Qt + (q * n2 + n) * n, Qs + n * ld_qt(n), qs + n * n, lane, 32);
+                load_Qt_rows_sums(n, Qr, Qs, qs, lane, 32);
+                load_Qt_rows_sums(n, Qr + n * n, Qs + n * ld_qt(n), qs + n * n, lane, 32);
                 __syncwarp();
                 build_T_half3(n, A.ne, redw, Uts, Uss, Qs, qs, Ts, 0, lane, 32);
                 build_T_half3(n, A.ne, redw, Uts, Uss, Qs + n * ld_qt(n), qs + n * n, Ts, n, lane, 32);
             } else {  // n > 16 configured to one warp per pair: no room for the sums
-                load_Qt(n, A.Qt + q * n2 * n, Qs, lane);
+                load_Qt(n, Qr, Qs, lane);
                 __syncwarp();
                 build_T_echelon(n, A.ne, Uts, Qs, Ts, lane);  // walker rows in echelon form
             }
@@ -437,6 +456,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.pref = L.pref;
     A.wmode = L.mode;
     A.Qt = L.s->Qt;
+    A.Qh = A.grp ? L.s->Qh : nullptr;  // the group path forms K and B from K; the warp path T
     A.gth = L.s->gth;
     A.idx = L.s->idx;
     A.d_count = L.s->d_count;

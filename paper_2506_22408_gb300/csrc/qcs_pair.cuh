@@ -288,6 +288,103 @@ __device__ inline void build_B(int n, int ne, const cd *__restrict__ Ts, cd *__r
 }
 
 
+// B^(s) (packed upper, m x m) from K = Ut [H1 | G2] (n x 2n, rows of Ks with T's stride)
+// and the walker rows Ut, for a snapshot with H1 = Qt^T J Qt, G2 = Qt^T J conj(Qt) (its rows
+// [H1^T; G2^T] staged in place of Qt, so that K is formed exactly like T).  With
+// W1 = K1 Ut^T = T J T^T and W2 = K2 Ut^H = T J conj(T)^T and the empty rows
+// R_j = Re T_j, I_j = -Im T_j of the selection,
+//     occupied a < b:             W1[a][b]
+//     occupied a, empty mode j:   (a, R_j) = (W1 + W2)[a][j] / 2,  (a, I_j) = i (W1 - W2)[a][j] / 2
+//     empty modes j1 <= j2 (al = W1, be = W2 at [j1][j2]):
+//         (R, R) = Re(al + be)/2, (R, I) = Im(be - al)/2, (I, R) = -Im(al + be)/2,
+//         (I, I) = Re(be - al)/2; within one mode only (R_j, I_j) = Im(be)/2.
+// Each sum runs over the non-zero columns of walker row b only: column b and [ne, n) for
+// an occupied row in reduced form (red), [b, n) in echelon form, [0, ne) and [b, n) for a
+// completion row b >= ne.  Three real products per complex term (Gauss's form, with the
+// staged sums Ksum = re + im of K1 and re - im of K2, and Uss = re + im of Ut):
+//     K1 u:       Re = p1 - p2, Im = p3 - p1 - p2,   p3 = sum (k1r + k1i)(ur + ui)
+//     K2 conj(u) = conj(conj(K2) u): Re = q1 + q2, Im = q1 - q2 - q3,
+//                 q3 = sum (k2r - k2i)(ur + ui)   (q1 = sum k2r ur, q2 = sum k2i ui).
+// The occupied-empty and empty-empty items share their sums' shape, so they run in one loop
+// ordered by completion row b (the ne occupied rows a, then the empty modes up to b):
+// neighbouring lanes share their loop bounds.
+__device__ inline void build_B_from_K(int n, int ne, bool red, const cd *__restrict__ Uts,
+                                      const double *__restrict__ Uss, const cd *__restrict__ Ks,
+                                      const double *__restrict__ Ksum,
+                                      cd *__restrict__ Bs, const uint16_t *__restrict__ tab, int lane,
+                                      int nthr) {
+    const int d = n - ne, lu = ld_ut(n), lt = ld_t(n), n2 = 2 * n;
+    const int c1 = tri_count(ne);
+    for (int e = lane; e < c1; e += nthr) {  // occupied x occupied: W1 alone
+        int a, b;
+        pair_of(tab, e, a, b);
+        const cd *kr = Ks + a * lt, *ur = Uts + b * lu;
+        const double *ks = Ksum + a * n2, *us = Uss + b * lu;
+        double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        if (red) {
+            p1 = kr[b].x * ur[b].x;
+            p2 = kr[b].y * ur[b].y;
+            p3 = ks[b] * us[b];
+        }
+        for (int k = red ? ne : b; k < n; ++k) {
+            const cd kk = kr[k], u = ur[k];
+            p1 = fma(kk.x, u.x, p1);
+            p2 = fma(kk.y, u.y, p2);
+            p3 = fma(ks[k], us[k], p3);
+        }
+        Bs[tri_index(a, b)] = cmk(p1 - p2, p3 - p1 - p2);
+    }
+    const int c2 = ne * d + tri_count(d + 1);
+    for (int e = lane; e < c2; e += nthr) {
+        // completion row b = ne + jj carries ne + jj + 1 items
+        int jj = 0, base = 0;
+        while (jj + 1 < d && base + ne + jj + 1 <= e) {
+            base += ne + jj + 1;
+            ++jj;
+        }
+        const int i = e - base, b = ne + jj;
+        const bool occ = i < ne;
+        const int a = i;  // K row: occupied row i (i < ne), or that of empty mode i - ne
+        const cd *kr = Ks + a * lt, *ur = Uts + b * lu;
+        const double *ks = Ksum + a * n2, *us = Uss + b * lu;
+        double p1 = 0.0, p2 = 0.0, p3 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+        for (int k = 0; k < ne; ++k) {
+            const cd u = ur[k], k1 = kr[k], k2 = kr[n + k];
+            p1 = fma(k1.x, u.x, p1);
+            p2 = fma(k1.y, u.y, p2);
+            p3 = fma(ks[k], us[k], p3);
+            q1 = fma(k2.x, u.x, q1);
+            q2 = fma(k2.y, u.y, q2);
+            q3 = fma(ks[n + k], us[k], q3);
+        }
+        for (int k = b; k < n; ++k) {
+            const cd u = ur[k], k1 = kr[k], k2 = kr[n + k];
+            p1 = fma(k1.x, u.x, p1);
+            p2 = fma(k1.y, u.y, p2);
+            p3 = fma(ks[k], us[k], p3);
+            q1 = fma(k2.x, u.x, q1);
+            q2 = fma(k2.y, u.y, q2);
+            q3 = fma(ks[n + k], us[k], q3);
+        }
+        const cd w1 = cmk(p1 - p2, p3 - p1 - p2), w2 = cmk(q1 + q2, q1 - q2 - q3);
+        if (occ) {
+            const cd sp = cadd(w1, w2), dm = csub(w1, w2);
+            Bs[tri_index(a, ne + 2 * jj)] = cscale(sp, 0.5);
+            Bs[tri_index(a, ne + 2 * jj + 1)] = cmk(-0.5 * dm.y, 0.5 * dm.x);
+        } else {
+            const int r1 = 2 * (i - ne), r2 = 2 * jj;
+            if (r1 < r2) {
+                Bs[tri_index(ne + r1, ne + r2)] = cmk(0.5 * (w1.x + w2.x), 0.0);
+                Bs[tri_index(ne + r1, ne + r2 + 1)] = cmk(0.5 * (w2.y - w1.y), 0.0);
+                Bs[tri_index(ne + r1 + 1, ne + r2)] = cmk(-0.5 * (w1.y + w2.y), 0.0);
+                Bs[tri_index(ne + r1 + 1, ne + r2 + 1)] = cmk(0.5 * (w2.x - w1.x), 0.0);
+            } else {
+                Bs[tri_index(ne + r1, ne + r1 + 1)] = cmk(0.5 * w2.y, 0.0);
+            }
+        }
+    }
+}
+
 // Elimination of the occupied block, shared by every node matrix.  The node matrices
 // B + w D differ only in their empty x empty block (D pairs the empty modes), so
 // eliminating the ne occupied indices first is the same for all of them:

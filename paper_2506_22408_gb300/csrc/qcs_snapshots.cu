@@ -168,6 +168,43 @@ __global__ void snapshot_compact_kernel(int64_t P, const int8_t *__restrict__ pa
     if (tid == 0) *count = base;
 }
 
+// Per dense snapshot (gather code 0xFF, or no codes): Qh = [H1^T; G2^T] (2n x n, Qt's
+// layout) with H1 = Qt^T J Qt and G2 = Qt^T J conj(Qt) (n x n; J pairs the Majorana
+// indices 2a, 2a + 1 with J[2a][2a+1] = 1).  The FP64 ALU overlap kernel and the gradient
+// form K = Ut Qh^T = [Ut H1 | Ut G2] in place of T = Ut Qt^T, from which
+//     T_j J T_k^T = (Ut H1 Ut^T)[j][k],   T_j J conj(T_k)^T = (Ut G2 Ut^H)[j][k],
+//     T_j J Qt = (Ut H1)[j],              T_j J conj(Qt) = (Ut G2)[j]
+// give B^(s) and the gradient's cotangents over n-term sums instead of 2n-term ones.
+// One block per snapshot (grid-stride), the snapshot's rows staged in shared memory.
+__global__ void hform_kernel(int n, int64_t P, const cd *__restrict__ Qt, const uint8_t *__restrict__ gth,
+                             cd *__restrict__ Qh, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cd *Qs = reinterpret_cast<cd *>(smem_raw);  // 2n x n
+    const int n2 = 2 * n;
+    if (!QCS_IN_BOUNDS((size_t)n2 * n * sizeof(cd) <= dyn_smem_bytes(), status)) return;
+    for (int64_t q = blockIdx.x; q < P; q += gridDim.x) {
+        if (gth && gth[q * n2] != 0xFF) continue;  // signed permutation: its kernels gather instead
+        __syncthreads();
+        for (int e = threadIdx.x; e < n2 * n; e += blockDim.x) Qs[e] = Qt[q * n2 * n + e];
+        __syncthreads();
+        cd *out = Qh + q * n2 * n;
+        for (int e = threadIdx.x; e < n2 * n; e += blockDim.x) {
+            const int c = e / n, k = e - c * n;
+            const bool g2 = c >= n;  // row c of Qh: column c of H1, or column c - n of G2
+            const int l = g2 ? c - n : c;
+            cd acc = cmk(0.0, 0.0);
+            for (int a = 0; a < n; ++a) {
+                cd x = Qs[(2 * a + 1) * n + l], y = Qs[(2 * a) * n + l];
+                x.y = g2 ? -x.y : x.y;
+                y.y = g2 ? -y.y : y.y;
+                cfma(acc, Qs[(2 * a) * n + k], x);
+                cfms(acc, Qs[(2 * a + 1) * n + k], y);
+            }
+            out[e] = acc;
+        }
+    }
+}
+
 }  // namespace
 
 qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const double *d_Q, const uint8_t *d_b,
@@ -188,4 +225,22 @@ qcs_status qcs_launch_snapshot_build(qcs_ctx *ctx, qcs_snapshots *s, const doubl
     }
     snapshot_compact_kernel<<<1, 1024, 0, st>>>(s->P, s->parity, s->idx, s->d_count);
     return qcs_check_launch(ctx, "snapshot_compact_kernel");
+}
+
+qcs_status qcs_hform_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st) {
+    if (s->Qh) return QCS_OK;
+    const int n = s->n;
+    const size_t bytes = sizeof(cd) * (size_t)(s->P > 0 ? s->P : 1) * 2 * n * n;
+    if (qcs_dev_alloc(s->alloc, (void **)&s->Qh, bytes, st) != QCS_OK) {
+        s->Qh = nullptr;
+        return qcs_fail(ctx, QCS_ERR_CUDA, "snapshot rows [H1^T; G2^T]: device allocation failed");
+    }
+    s->qh_bytes = bytes;
+    if (s->P == 0) return QCS_OK;
+    const size_t smem = (size_t)2 * n * n * sizeof(cd);
+    if (qcs_set_smem(ctx, (const void *)hform_kernel, smem) != QCS_OK) return QCS_ERR_CUDA;
+    int64_t blocks = (int64_t)ctx->num_sms * 8;
+    if (blocks > s->P) blocks = s->P;
+    hform_kernel<<<(unsigned)blocks, 256, smem, st>>>(n, s->P, s->Qt, s->gth, s->Qh, ctx->d_status);
+    return qcs_check_launch(ctx, "hform_kernel");
 }

@@ -44,7 +44,19 @@ def test_flop_accounting_host_only():
     # entries (occupied rows in reduced form), 3 sums per entry of T and re + im of each
     # snapshot entry
     t_3m = 6 * 2 * n * (n * n - ne * (ne - 1) - tri(d)) + 3 * 2 * n * n + 2 * n * n  # reduced form
+    # B from T: 2n-term sums per entry (n <= 16, and signed-permutation snapshots)
     b_flops = 16 * n * tri(ne) + 8 * n * ne * 2 * d + 4 * n * tri(2 * d)
+
+    def b_from_k(n, ne):
+        # above 16 modes, B from K = U^T [H1 | G2] over the walker rows' non-zero columns, three
+        # real products per term: occupied rows in reduced form (1 + d columns, W1 alone),
+        # completion row ne + j with ne + j + 1 items of W1 and W2 over n - j columns, halved
+        # sums and differences per occupied-empty and empty pair, re + im of K
+        d = n - ne
+        oo = tri(ne) * (6 * (1 + d) + 3)
+        rows = sum((ne + j + 1) * (12 * (n - j) + 6) for j in range(d))
+        return oo + rows + 8 * ne * d + 8 * tri(d) + d + 2 * n * n
+
     shared = sum(step(r) for r in range(m, 2 * d, -2))
     node = sum(step(r) for r in range(2 * d, 2, -2))
     assert f16 == t_3m + b_flops + shared + 3 * node
@@ -53,10 +65,14 @@ def test_flop_accounting_host_only():
     parts = qcs.flops_breakdown(16, 8)
     assert (parts["T"], parts["B"], parts["pfaffian"]) == (t_3m, b_flops, shared + 3 * node)
     # other n: the same form (the one-warp path below 16 modes, two-warp groups above)
-    for n, ne in ((12, 6), (20, 10), (24, 4)):
+    for n, ne in ((12, 6), (20, 10), (24, 4), (24, 12)):
         d = n - ne
         p12 = qcs.flops_breakdown(n, ne)
         assert p12["T"] == 6 * 2 * n * (n * n - ne * (ne - 1) - tri(d)) + 3 * 2 * n * n + 2 * n * n
+        bt = 16 * n * tri(ne) + 8 * n * ne * 2 * d + 4 * n * tri(2 * d)
+        assert p12["B"] == (b_from_k(n, ne) if n > 16 else bt)
+        if n > 16:
+            assert p12["B"] < bt
         assert lib.qcs_overlap_flops_per_pair(n, ne, 0, 0) == sum(p12.values())
     assert lib.qcs_overlap_flops_per_pair(16, 7, 0, 0) == 0.0  # odd ne rejected
 

@@ -98,4 +98,6 @@ def test_back_to_cuda_malloc():
     oo, _, sc, _ = orc.overlap(d["Phi"], d["Q"], d["b"], per_pair=True)
     assert np.all(np.abs(ov.cpu().numpy() - oo) <= 1e-10 * sc.mean(axis=1))
     s.close()  # the set frees through the allocator it was built with
-    assert ctx.free_calls == f + 1 + 5  # n = 12: no tensor-core records by default
+    # n = 12: no tensor-core records by default; Qt, parity, list, counts, gather codes and
+    # the rows [H1^T; G2^T] the FP64 ALU path formed on first use
+    assert ctx.free_calls == f + 1 + 6
