@@ -385,20 +385,27 @@ __device__ inline void build_B_from_K(int n, int ne, bool red, const cd *__restr
     }
 }
 
+// Records of node_pfaffians' product trees per warp for NB node matrices per round (vm:
+// the entries of the kernel's Gauss-vector buffers, the full matrix or NB complements);
+// the ne/2 signed pivots of the shared occupied elimination follow them.
+__host__ __device__ inline int pv_records(int vm, int NB, int ne) { return vm / 2 + kMaxNB + NB * (ne / 2); }
+
 // Elimination of the occupied block, shared by every node matrix.  The node matrices
 // B + w D differ only in their empty x empty block (D pairs the empty modes), so
 // eliminating the ne occupied indices first is the same for all of them:
 // pf(B + w D) = pf0 pf(S + w D_ee), S the Schur complement of the occupied block.
 // Pivots are taken inside the occupied block (its largest active entry, ties to the
 // first pair in packed order); a pivot pair at positions ak < ap of the active list
-// contributes (-1)^(ak+ap-1) A_kp, the sign of moving k and p to the front.  Works on a
-// copy of B in Ns.  Returns false, with Bs untouched, when a pivot is zero or the
-// largest entry of S exceeds 2^8 times the largest entry of B (the caller then
-// eliminates each node matrix in full); on success Bs holds S, packed upper 2d x 2d.
+// contributes (-1)^(ak+ap-1) A_kp, the sign of moving k and p to the front; the ne/2
+// signed pivots go to pvo (their product pf0 enters each node's product tree, see
+// node_pfaffians).  Works on a copy of B in Ns.  Returns false, with Bs untouched, when a
+// pivot is zero or the largest entry of S exceeds 2^8 times the largest entry of B (the
+// caller then eliminates each node matrix in full); on success Bs holds S, packed upper
+// 2d x 2d.
 __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__restrict__ Ns,
                                       cd *__restrict__ Uv, cd *__restrict__ Vv, uint8_t *__restrict__ act0,
-                                      uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab, cd &pf0,
-                                      int lane) {
+                                      uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
+                                      cd *__restrict__ pvo, int lane) {
     const int T = tri_count(m);
     unsigned kb = 0u;
     for (int e = lane; e < T; e += 32) {
@@ -410,7 +417,6 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
     for (int a = lane; a < m; a += 32) act0[a] = (uint8_t)a;
     kb = __reduce_max_sync(QCS_FULL, kb);
     __syncwarp();
-    pf0 = cmk(1.0, 0.0);
     uint8_t *cur = act0, *nxt = act1;
     for (int s = 0, r = m; s < ne / 2; ++s, r -= 2) {
         const int ro = ne - 2 * s;  // the active occupied indices sit at positions 0 .. ro-1
@@ -431,9 +437,7 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
         pair_of(tab, (int)(0xffffffffu - (unsigned)(bk & 0xffffffffull)), ak, ap);
         const int k = cur[ak], p = cur[ap];
         const cd piv = Ns[tri_index(k, p)];
-        const cd sp = flip_if(piv, ((ak + ap - 1) & 1) != 0);
-        if (s == 0) pf0 = sp;  // warp-uniform: the first signed pivot needs no product
-        else pf0 = cmul(pf0, sp);
+        if (lane == 0) pvo[s] = flip_if(piv, ((ak + ap - 1) & 1) != 0);
         if (r == 2) break;  // no empty modes: the last pivot closes the Pfaffian
         const cd iv = cinv(piv);
         const int rv = r - 2;
@@ -486,9 +490,11 @@ __device__ inline bool schur_occupied(int m, int ne, cd *__restrict__ Bs, cd *__
 }
 
 // Pfaffians of nb node matrices B + wnode[v] D held in Ns (packed upper), m x m with
-// ne occupied rows first, each times its node weight: on return pf[v] holds
-// gamma[v] pf(B + wnode[v] D) (the weight enters the product tree as one more factor,
-// at no extra FP64 instruction); m = 0 gives gamma[v].
+// ne occupied rows first, each times its node weight and the npo factors pvo (the signed
+// pivots of a shared occupied elimination, or none): on return pf[v] holds
+// gamma[v] prod(pvo) pf(B + wnode[v] D), those factors entering the product tree as more
+// records (a tree level costs one complex product whatever its width); m = 0 gives
+// gamma[v] prod(pvo).
 // The warp is cut into segments of seg lanes (seg = 32 / nb rounded up to a power of
 // two); segment v owns node v through each Parlett-Reid step: it finds the pivot of the
 // active first row, takes the pivot's reciprocal (every lane of the segment, so no lane
@@ -500,122 +506,128 @@ __device__ inline void node_pfaffians(int m, int ne, const cd *__restrict__ wnod
                                       int nb, const cd *__restrict__ Bs, cd *__restrict__ Ns, cd *__restrict__ Uv,
                                       cd *__restrict__ Vv, cd *__restrict__ pf, uint8_t *__restrict__ act0,
                                       uint8_t *__restrict__ act1, const uint16_t *__restrict__ tab,
-                                      cd *__restrict__ pv, int lane) {
-    if (m == 0) {
-        if (lane < nb) pf[lane] = gamma[lane];
-        __syncwarp();
-        return;
-    }
+                                      cd *__restrict__ pv, int npo, const cd *__restrict__ pvo, int lane) {
     // records per node in pv: the signed pivots of the (m - 4) / 2 steps, the closing
-    // Pfaffian (a single record for m = 2 or 4) and the node weight
-    const int S = (m >= 4 ? m / 2 - 1 : 1) + 1;
-    const int d = (m - ne) / 2;
-    const int T = tri_count(m);
-    for (int e = lane; e < nb * T; e += 32) {
-        int v = e / T, t = e - v * T;
-        Ns[v * T + t] = Bs[t];
+    // Pfaffian (a single record for m = 2 or 4; none for m = 0), the node weight, then
+    // the npo factors pvo
+    const int S0 = m == 0 ? 0 : (m >= 4 ? m / 2 - 1 : 1), S = S0 + 1 + npo;
+    for (int e = lane; e < nb * npo; e += 32) {
+        const int v = e / npo, i = e - v * npo;
+        pv[v * S + S0 + 1 + i] = pvo[i];
     }
-    for (int e = lane; e < nb * m; e += 32) {
-        int v = e / m, a = e - v * m;
-        act0[v * m + a] = (uint8_t)a;
-    }
-    __syncwarp();
-    for (int e = lane; e < nb * d; e += 32) {
-        int v = e / d, i = e - v * d;
-        cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
-        *x = cadd(*x, wnode[v]);
-    }
-    __syncwarp();
-    const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
-    const int v = lane / seg, sl = lane - v * seg;
-    const bool live = v < nb;
-    const int vr = live ? v : 0;  // lanes past the last node read node 0 and write nothing
-    const cd *__restrict__ Nv = Ns + vr * T;
-    uint8_t *cur = act0, *nxt = act1;
-    int s = 0;
-    for (int r = m; r > 4; r -= 2, ++s) {
-        // pivot: largest |A_{k,i}| over the active row of k = cur[0], each lane scanning
-        // every seg-th candidate, then a shuffle reduction inside the segment; the key's
-        // low bits prefer the first candidate among equal magnitudes
-        const int k = cur[vr * m];
-        unsigned long long bk = 0ull;
-        for (int a = 1 + sl; a < r; a += seg) {
-            const unsigned key = pivot_key(Nv[tri_index(k, cur[vr * m + a])]);
-            const unsigned long long c = ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
-            bk = c > bk ? c : bk;
+    if (m == 0) {
+        if (lane < nb) pv[lane * S] = gamma[lane];
+        __syncwarp();
+    } else {
+        const int d = (m - ne) / 2;
+        const int T = tri_count(m);
+        for (int e = lane; e < nb * T; e += 32) {
+            int v = e / T, t = e - v * T;
+            Ns[v * T + t] = Bs[t];
         }
-        for (int o = seg >> 1; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
-            bk = ob > bk ? ob : bk;
+        for (int e = lane; e < nb * m; e += 32) {
+            int v = e / m, a = e - v * m;
+            act0[v * m + a] = (uint8_t)a;
         }
-        const int a = 0xffff - (int)(bk & 0xffffull);  // 1 .. r - 1 (candidate a = 1 always exists)
-        const int p = cur[vr * m + a];
-        const cd piv = Nv[tri_index(k, p)];
-        if (live && sl == 0) pv[v * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
-        // Gauss vectors over the remaining indices (original order kept): u = A_{i,k} / A_{k,p}
-        // (A_{i,k} = -A_{k,i}) and v = A_{i,p}; the loads of a lane's first index are
-        // issued before the reciprocal, whose dependent FP64 chain they do not wait for
-        const int rv = r - 2;
-        const bool g0 = live && sl < rv;
-        int i0 = 0;
-        cd u0 = cmk(0.0, 0.0), v0 = cmk(0.0, 0.0);
-        if (g0) {
-            i0 = cur[v * m + sl + 1 + ((sl + 1 >= a) ? 1 : 0)];
-            u0 = Nv[tri_index(k, i0)];
-            v0 = skew_get(Nv, i0, p);
+        __syncwarp();
+        for (int e = lane; e < nb * d; e += 32) {
+            int v = e / d, i = e - v * d;
+            cd *x = Ns + v * T + tri_index(ne + 2 * i, ne + 2 * i + 1);
+            *x = cadd(*x, wnode[v]);
         }
-        const cd iv = cinv(piv);
-        if (g0) {
-            Uv[v * m + sl] = cnegmul(u0, iv);
-            Vv[v * m + sl] = v0;
-            nxt[v * m + sl] = (uint8_t)i0;
-        }
-        if (live) {
-            for (int a2 = sl + seg; a2 < rv; a2 += seg) {
-                const int aa = a2 + 1 + ((a2 + 1 >= a) ? 1 : 0);
-                const int i = cur[v * m + aa];
-                Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);
-                Vv[v * m + a2] = skew_get(Nv, i, p);
-                nxt[v * m + a2] = (uint8_t)i;
+        __syncwarp();
+        const int seg = nb <= 1 ? 32 : nb <= 2 ? 16 : nb <= 4 ? 8 : 4;
+        const int v = lane / seg, sl = lane - v * seg;
+        const bool live = v < nb;
+        const int vr = live ? v : 0;  // lanes past the last node read node 0 and write nothing
+        const cd *__restrict__ Nv = Ns + vr * T;
+        uint8_t *cur = act0, *nxt = act1;
+        int s = 0;
+        for (int r = m; r > 4; r -= 2, ++s) {
+            // pivot: largest |A_{k,i}| over the active row of k = cur[0], each lane scanning
+            // every seg-th candidate, then a shuffle reduction inside the segment; the key's
+            // low bits prefer the first candidate among equal magnitudes
+            const int k = cur[vr * m];
+            unsigned long long bk = 0ull;
+            for (int a = 1 + sl; a < r; a += seg) {
+                const unsigned key = pivot_key(Nv[tri_index(k, cur[vr * m + a])]);
+                const unsigned long long c = ((unsigned long long)key << 32) | (unsigned long long)(0xffffu - (unsigned)a);
+                bk = c > bk ? c : bk;
             }
+            for (int o = seg >> 1; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(QCS_FULL, bk, o);
+                bk = ob > bk ? ob : bk;
+            }
+            const int a = 0xffff - (int)(bk & 0xffffull);  // 1 .. r - 1 (candidate a = 1 always exists)
+            const int p = cur[vr * m + a];
+            const cd piv = Nv[tri_index(k, p)];
+            if (live && sl == 0) pv[v * S + s] = flip_if(piv, (a - 1) & 1);  // sign (-1)^{a-1} of the Laplace expansion
+            // Gauss vectors over the remaining indices (original order kept): u = A_{i,k} / A_{k,p}
+            // (A_{i,k} = -A_{k,i}) and v = A_{i,p}; the loads of a lane's first index are
+            // issued before the reciprocal, whose dependent FP64 chain they do not wait for
+            const int rv = r - 2;
+            const bool g0 = live && sl < rv;
+            int i0 = 0;
+            cd u0 = cmk(0.0, 0.0), v0 = cmk(0.0, 0.0);
+            if (g0) {
+                i0 = cur[v * m + sl + 1 + ((sl + 1 >= a) ? 1 : 0)];
+                u0 = Nv[tri_index(k, i0)];
+                v0 = skew_get(Nv, i0, p);
+            }
+            const cd iv = cinv(piv);
+            if (g0) {
+                Uv[v * m + sl] = cnegmul(u0, iv);
+                Vv[v * m + sl] = v0;
+                nxt[v * m + sl] = (uint8_t)i0;
+            }
+            if (live) {
+                for (int a2 = sl + seg; a2 < rv; a2 += seg) {
+                    const int aa = a2 + 1 + ((a2 + 1 >= a) ? 1 : 0);
+                    const int i = cur[v * m + aa];
+                    Uv[v * m + a2] = cnegmul(Nv[tri_index(k, i)], iv);
+                    Vv[v * m + a2] = skew_get(Nv, i, p);
+                    nxt[v * m + a2] = (uint8_t)i;
+                }
+            }
+            __syncwarp();
+            // rank-2 update A_ij -= ut_i v_j - v_i ut_j on the remaining pairs of every node
+            const int Tr = tri_count(rv);
+            for (int e = lane; e < nb * Tr; e += 32) {
+                int w = e / Tr, t = e - w * Tr;
+                int ia, ib;
+                pair_of(tab, t, ia, ib);
+                int i = nxt[w * m + ia], j = nxt[w * m + ib];
+                cd *x = Ns + w * T + tri_index(i, j);
+                cd y = *x;
+                const cd *U_ = Uv + w * m, *V_ = Vv + w * m;
+                cfms(y, U_[ia], V_[ib]);
+                cfma(y, V_[ia], U_[ib]);
+                *x = y;
+            }
+            __syncwarp();
+            uint8_t *t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        // the closing Pfaffian of the last four (or two) active indices, ascending
+        if (live && sl == 0) {
+            const uint8_t *c = cur + v * m;
+            cd q;
+            if (m >= 4) {
+                q = cmul(Nv[tri_index(c[0], c[1])], Nv[tri_index(c[2], c[3])]);
+                cfms(q, Nv[tri_index(c[0], c[2])], Nv[tri_index(c[1], c[3])]);
+                cfma(q, Nv[tri_index(c[0], c[3])], Nv[tri_index(c[1], c[2])]);
+            } else {
+                q = Nv[tri_index(c[0], c[1])];
+            }
+            pv[v * S + s] = q;
+            pv[v * S + s + 1] = gamma[v];
         }
         __syncwarp();
-        // rank-2 update A_ij -= ut_i v_j - v_i ut_j on the remaining pairs of every node
-        const int Tr = tri_count(rv);
-        for (int e = lane; e < nb * Tr; e += 32) {
-            int w = e / Tr, t = e - w * Tr;
-            int ia, ib;
-            pair_of(tab, t, ia, ib);
-            int i = nxt[w * m + ia], j = nxt[w * m + ib];
-            cd *x = Ns + w * T + tri_index(i, j);
-            cd y = *x;
-            const cd *U_ = Uv + w * m, *V_ = Vv + w * m;
-            cfms(y, U_[ia], V_[ib]);
-            cfma(y, V_[ia], U_[ib]);
-            *x = y;
-        }
-        __syncwarp();
-        uint8_t *t = cur;
-        cur = nxt;
-        nxt = t;
     }
-    // the closing Pfaffian of the last four (or two) active indices, ascending
-    if (live && sl == 0) {
-        const uint8_t *c = cur + v * m;
-        cd q;
-        if (m >= 4) {
-            q = cmul(Nv[tri_index(c[0], c[1])], Nv[tri_index(c[2], c[3])]);
-            cfms(q, Nv[tri_index(c[0], c[2])], Nv[tri_index(c[1], c[3])]);
-            cfma(q, Nv[tri_index(c[0], c[3])], Nv[tri_index(c[1], c[2])]);
-        } else {
-            q = Nv[tri_index(c[0], c[1])];
-        }
-        pv[v * S + s] = q;
-        pv[v * S + s + 1] = gamma[v];
-    }
-    __syncwarp();
     // pf[v] = prod_s pv[v][s]: pairwise tree over the lanes; each level reads into
-    // registers, then stores after a __syncwarp (nb * half <= 8 * 23 / 2 < 96 items)
+    // registers, then stores after a __syncwarp (S <= n + 1 - ne/2 <= 24 with the occupied
+    // pivots, S <= m/2 + 1 <= 24 for a full elimination of one node: nb * half <= 96 items)
     for (int len = S; len > 1; len = (len + 1) / 2) {
         const int half = len / 2;
         cd r[3];

@@ -314,20 +314,20 @@ __global__ void __launch_bounds__(128) split_pair_kernel(const __grid_constant__
                 build_B_f32(n, A.ne, Ts, ldT, Bs, tab, lane);
                 __syncwarp();
                 // occupied block eliminated once for all nodes when that is stable
-                cd pf0;
-                const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pf0, lane);
+                cd *pvo = pv + pv_records(A.vm, A.NB, A.ne);  // the occupied pivots
+                const bool shared = schur_occupied(A.m, A.ne, Bs, Ns, Uv, Vv, act0, act1, tab, pvo, lane);
                 const int mm = shared ? A.m - A.ne : A.m, nee = shared ? 0 : A.ne;
                 const int NBr = shared ? A.NB : 1;  // the rare full eliminations run one node per round
                 cd S = cmk(0.0, 0.0);
                 for (int k0 = 0; k0 < A.nev; k0 += NBr) {
                     const int nb = A.nev - k0 < NBr ? A.nev - k0 : NBr;
-                    node_pfaffians(mm, nee, A.wnode + k0, A.gamma + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv, lane);
+                    node_pfaffians(mm, nee, A.wnode + k0, A.gamma + k0, nb, Bs, Ns, Uv, Vv, pf, act0, act1, tab, pv,
+                                   shared ? A.ne / 2 : 0, pvo, lane);
                     if (lane == 0)
                         for (int vv = 0; vv < nb; ++vv) S = cadd(S, pf[vv]);  // pf[vv] carries gamma
                     __syncwarp();
                 }
                 if (lane == 0) {
-                    if (shared) S = cmul(S, pf0);
                     if (!cfinite(S)) raise_status(A.status, QCS_ERR_NONFINITE);
                     acc = cadd(acc, S);
                     if (A.per_pair) {
@@ -632,8 +632,8 @@ size_t split_warp_layout(SplitArgs &A, int NB) {
     o = align16(o + (size_t)kMaxNB * sizeof(cd));
     A.off_act = (int)o;
     o = align16(o + (size_t)2 * A.vm);
-    A.off_pv = (int)o;  // node products: nb (m/2 + 1) records at most, gamma included
-    o = align16(o + (size_t)(A.vm / 2 + kMaxNB) * sizeof(cd));
+    A.off_pv = (int)o;  // node products (gamma and the occupied pivots included), then those pivots
+    o = align16(o + (size_t)(pv_records(A.vm, NB, A.ne) + A.ne / 2) * sizeof(cd));
     return o;
 }
 
