@@ -547,8 +547,10 @@ extern "C" qcs_status qcs_overlap(qcs_ctx *ctx, const qcs_snapshots *s, int ne, 
         if (r != QCS_OK) return r;
         r = qcs_launch_tc_pairs(ctx, L, wk.walk_rec, st);
     } else {
-        r = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
-        if (r != QCS_OK) return r;
+        if (qcs_pair_forms_K(s->n, L.config)) {
+            r = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
+            if (r != QCS_OK) return r;
+        }
         r = qcs_launch_pairs(ctx, L, st);
     }
     if (r != QCS_OK) return r;
@@ -599,8 +601,10 @@ extern "C" qcs_status qcs_overlap_batched(qcs_ctx *ctx, int nsys, const qcs_syst
         L.s = s;
         L.per_pair = nullptr;
         L.counter = nullptr;
-        qcs_status hr = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
-        if (hr != QCS_OK) return hr;
+        if (qcs_pair_forms_K(s->n, L.config)) {
+            qcs_status hr = qcs_hform_prepare_snapshots(ctx, const_cast<qcs_snapshots *>(s), st);
+            if (hr != QCS_OK) return hr;
+        }
         off[i][0] = total;
         total += align16(sizeof(cd) * (size_t)y.W * s->n * s->n);
         off[i][1] = total;

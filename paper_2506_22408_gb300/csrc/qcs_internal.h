@@ -190,6 +190,9 @@ bool qcs_tc_supported(int n);      // n <= 16
 size_t qcs_tc_walker_bytes(int64_t W);
 int qcs_tc_snaps_per_tile(int subs);  // parity +1 snapshots per tile (subs sub-tiles; 0 = default)
 qcs_status qcs_tc_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
+// Whether the FP64 ALU pair kernel runs (n, config) on its two-warp path, which forms
+// K = Ut [H1 | G2] from the set's rows [H1^T; G2^T] and B from K.
+bool qcs_pair_forms_K(int n, int config);
 // The rows [H1^T; G2^T] of every dense snapshot into s->Qh (allocated and formed once).
 qcs_status qcs_hform_prepare_snapshots(qcs_ctx *ctx, qcs_snapshots *s, cudaStream_t st);
 qcs_status qcs_launch_tc_pairs(qcs_ctx *ctx, const qcs_pair_launch &L, unsigned char *walk_rec, cudaStream_t st);

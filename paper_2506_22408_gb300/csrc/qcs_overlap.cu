@@ -404,6 +404,8 @@ size_t pair_group_layout(PairArgs &A, int NB) {
 
 int qcs_pair_warps_per_block() { return 4; }
 
+bool qcs_pair_forms_K(int n, int config) { return n > 16 && qcs_decode_config(config).warps != 1; }
+
 namespace {
 
 // Fill the per-system arguments and shared layout of one pair launch.
@@ -421,7 +423,7 @@ void setup_pair_args(qcs_ctx *ctx, const qcs_pair_launch &L, PairArgs &A) {
     A.P = L.P;
     const qcs_config cfg = qcs_decode_config(L.config);
     A.reg = L.n == 16;
-    A.grp = L.n > 16 && cfg.warps != 1;  // n > 16: two warps per pair unless one is configured
+    A.grp = qcs_pair_forms_K(L.n, L.config);  // n > 16: two warps per pair unless one is configured
     A.t3 = L.n < 16;
     const int n = A.n, m = A.m, T = tri_count(m);
     const int wpb = qcs_pair_warps_per_block();

@@ -98,6 +98,33 @@ def test_back_to_cuda_malloc():
     oo, _, sc, _ = orc.overlap(d["Phi"], d["Q"], d["b"], per_pair=True)
     assert np.all(np.abs(ov.cpu().numpy() - oo) <= 1e-10 * sc.mean(axis=1))
     s.close()  # the set frees through the allocator it was built with
-    # n = 12: no tensor-core records by default; Qt, parity, list, counts, gather codes and
-    # the rows [H1^T; G2^T] the FP64 ALU path formed on first use
-    assert ctx.free_calls == f + 1 + 6
+    # n = 12: no tensor-core records by default, and the one-warp FP64 ALU path forms no
+    # rows [H1^T; G2^T]: Qt, parity, list, counts and gather codes
+    assert ctx.free_calls == f + 1 + 5
+
+
+def test_rows_for_K_are_formed_once_per_set():
+    """Above 16 modes the FP64 ALU path forms K = U^T [H1 | G2] from rows [H1^T; G2^T] that
+    the snapshot set builds on first use, through the set's allocator; later calls reuse
+    them, and closing the set frees them."""
+    d = make(5, n=20, ne=10, W=8, P=64)
+    ctx = qcs.Context(0)
+    ctx.use_torch_allocator()
+    s = qcs.Snapshots(ctx, dev(d["Q"]), dev(d["b"]))
+    n_set = ctx.alloc_calls
+    assert n_set == 5  # rows, parity, list, counts, gather codes (no tensor-core records above 16)
+    walkers = dev(d["Phi"])
+    ov, _ = qcs.overlap(ctx, s, walkers)
+    torch.cuda.synchronize()
+    assert ctx.alloc_calls == n_set + 2  # the workspace and the rows [H1^T; G2^T]
+    ov2, _ = qcs.overlap(ctx, s, walkers)
+    torch.cuda.synchronize()
+    assert ctx.alloc_calls == n_set + 2 and ctx.sync_status() == 0
+    assert torch.equal(ov, ov2)
+    oo, _, sc, _ = orc.overlap(d["Phi"], d["Q"], d["b"], per_pair=True)
+    got = ov.cpu().numpy()
+    assert np.all(np.abs(got - oo) <= 1e-10 * sc.mean(axis=1))
+    check_walkers_relative(got, oo, sc)
+    f = ctx.free_calls
+    s.close()
+    assert ctx.free_calls == f + n_set + 1
