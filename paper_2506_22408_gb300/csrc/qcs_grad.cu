@@ -48,7 +48,7 @@ struct GradArgs {
         off_int, off_tile, off_acth, off_kh, off_ph, off_kc, off_sacth, off_skh, off_sph, off_sinvh, off_scr;
     const cd *Ut;
     const cd *Qt;
-    const cd *Qh;        // per listed snapshot: the rows [H1^T; G2^T] (2n x n, the layout of Qt)
+    const cd *Qh;        // per dense snapshot of the set: the rows [H1^T; G2^T] (2n x n, the layout of Qt)
     const uint8_t *gth;  // gather codes of signed-permutation snapshots (or null)
     const int *idx;
     const int *d_count;
