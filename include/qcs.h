@@ -192,8 +192,8 @@ qcs_status qcs_set_allocator(qcs_ctx *ctx, qcs_alloc_fn alloc_fn, qcs_free_fn fr
  * QCS_ERR_ARG for max_iter out of range, QCS_ERR_CUDA if the launch fails. */
 qcs_status qcs_selftest_bounded_wait(qcs_ctx *ctx, uint32_t max_iter, void *stream);
 
-/* Self-test of the reciprocal the eliminations use for their pivots (Newton-Raphson
- * steps from a single-precision seed instead of an IEEE division): r[i] = 1/d[i] for
+/* Self-test of the reciprocal the eliminations use for their pivots (one third-order
+ * step r (1 + e + e^2) from a single-precision seed instead of an IEEE division): r[i] = 1/d[i] for
  * n values d[i] >= 0, both device arrays of doubles owned by the caller, through the
  * same device function as the pair kernels.  The result is within 2 ulp of the
  * correctly rounded 1/d; d = 0 gives +inf, as the division does.
