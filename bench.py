@@ -158,7 +158,13 @@ KERNEL_SOURCES = {
     "grad_pair_kernel": ["qcs_grad.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
     "rdm_syrk_kernel": ["qcs_rdm.cu"],
     "energy_pair_kernel": ["qcs_energy.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
+    # the FP64 ALU pair kernel in its batched launch over the five systems of the batching
+    # workload (a record of its own: another workload)
+    "pair_overlap_kernel_batched": ["qcs_overlap.cu", "qcs_group.cuh", "qcs_pair.cuh", "qcs_common.cuh"],
 }
+
+# workload name of the batched launch's traffic record
+BATCH_WORKLOAD = "batch n=8,12,16,20,24 ne=n/2, 1024/512/256/128/64 walkers, 2000/5000/10000/20000/40000 snapshots"
 
 
 def kernel_source_sha(kernel: str) -> str:
@@ -384,7 +390,9 @@ def run_batch(args, ctx, dev, barrier, ws):
             "pair_kernel": {"kernel_ms_per_step": kms, "share_of_graph_step": kms / (1e3 * t / args.batch_steps),
                             "roofline": {"bound": "alu", "achieved": kach, "peak": FP64_PEAK_TFLOPS,
                                          "unit": "TFLOP/s", "frac": kach / FP64_PEAK_TFLOPS,
-                                         "timing": "one batched launch outside the graph, events on its stream"}},
+                                         "timing": "one batched launch outside the graph, events on its stream",
+                                         "traffic": (traffic_for("pair_overlap_kernel_batched", BATCH_WORKLOAD)
+                                                     if args.batch_walker_scale == 1.0 else None)}},
             "systems_alone": per_sys,
             "split_precision": {"systems": split_rows, "pairs_per_s_all": pairs_step / (split_ms * 1e-3),
                                 "timing": "split kernel per system, events on its stream (no graph)"},
