@@ -42,7 +42,8 @@ def mixed_set(rng, n, P, frac_sp):
 
 
 @pytest.mark.parametrize("n,ne,W,P,frac", [(16, 8, 6, 120, 1.0), (16, 8, 5, 90, 0.5), (8, 4, 4, 64, 1.0),
-                                           (12, 2, 3, 40, 0.7), (24, 12, 2, 16, 1.0), (7, 4, 3, 30, 0.6)])
+                                           (12, 2, 3, 40, 0.7), (24, 12, 2, 16, 1.0), (7, 4, 3, 30, 0.6),
+                                           (20, 10, 3, 40, 0.5)])
 def test_overlaps_match_oracle(ctx, n, ne, W, P, frac):
     rng = np.random.default_rng(300 + n + ne)
     Q, sp = mixed_set(rng, n, P, frac)
@@ -61,7 +62,8 @@ def test_overlaps_match_oracle(ctx, n, ne, W, P, frac):
         assert np.all(np.abs(ov - oo) <= TOL * sc.mean(axis=1) + floor)
 
 
-@pytest.mark.parametrize("n,ne,W,P,frac", [(16, 8, 3, 40, 1.0), (8, 4, 4, 33, 0.5), (10, 6, 2, 21, 1.0)])
+@pytest.mark.parametrize("n,ne,W,P,frac", [(16, 8, 3, 40, 1.0), (8, 4, 4, 33, 0.5), (10, 6, 2, 21, 1.0),
+                                           (18, 8, 2, 24, 0.5)])
 def test_gradient_matches_oracle(ctx, n, ne, W, P, frac):
     rng = np.random.default_rng(400 + n + ne)
     Q, sp = mixed_set(rng, n, P, frac)
