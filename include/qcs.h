@@ -168,13 +168,16 @@ size_t qcs_workspace_bytes(const qcs_ctx *ctx);
  *   free_fn(ptr, bytes, stream, user) releases it; the library calls it only after the
  *     device has finished all work that used the memory, with stream = NULL.
  * Once set, the context's workspace, the buffers of snapshot sets built on the context
- * (which remember the allocator they were built with), the tensor-core slice records and
- * the autotuner's sample come from alloc_fn; the context's 4-byte status word and its
+ * (which remember the allocator they were built with, including those a set forms on its
+ * first use by a path: the split-precision slabs, and for the FP64 ALU path above 16 modes
+ * and the gradient the rows [H1^T; G2^T]), the tensor-core slice records and the
+ * autotuner's sample come from alloc_fn; the context's 4-byte status word and its
  * pinned host mirror, made at qcs_create, do not.  Setting an allocator releases the
  * current workspace (after synchronising the device) so that later growth uses the new
  * one; alloc_fn = free_fn = NULL restores cudaMalloc / cudaFree.  The callbacks run on the
  * calling host thread, inside the library call that needs memory; a call allocates only
- * when the workspace must grow, so after one call with the largest sizes none does.
+ * when the workspace must grow or a set forms a buffer of a path for the first time, so
+ * after one call of each path with the largest sizes none does.
  * Errors: QCS_ERR_ARG (ctx NULL, or only one of the two functions given), QCS_ERR_CUDA. */
 typedef void *(*qcs_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*qcs_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
