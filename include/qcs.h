@@ -215,6 +215,10 @@ qcs_status qcs_selftest_reciprocal(qcs_ctx *ctx, const double *d, double *r, int
  * pi_p = det Q_p (-1)^{|b_p|} = det Q'_p.  *out is owned by the library
  * (free with qcs_snapshots_free).  Inputs are only read during the call's
  * kernels; the caller may reuse them once `stream` has passed this call.
+ * Some paths add per-set buffers on their first use (the split-precision slabs; for the
+ * FP64 ALU path above 16 modes and for the gradient the rows [H1^T; G2^T]), formed on
+ * that call's stream: a call on another stream that uses the same set must be ordered
+ * after the first call of that path (or that first call made on the same stream).
  * Errors: QCS_ERR_ARG (n out of range, P < 0, null pointers), QCS_ERR_CUDA. */
 qcs_status qcs_build_snapshots(qcs_ctx *ctx, int n, int64_t P, const double *d_Q, const uint8_t *d_b,
                                qcs_snapshots **out, void *stream);
